@@ -57,7 +57,8 @@ def lib():
                                         _I64, ctypes.c_int64, _U8]
             L.oracle_backward.restype = ctypes.c_int
             L.oracle_backward.argtypes = [ctypes.c_int64, _D, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int,
-                                          ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D]
+                                          ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D,
+                                          _I64, ctypes.c_int64]
             L.oracle_sh_basis.restype = ctypes.c_int
             L.oracle_sh_basis.argtypes = [ctypes.c_int64, _D, ctypes.c_int, _D]
             L.oracle_select_lod.restype = ctypes.c_int
@@ -186,7 +187,7 @@ def render(scene, cams, opts: Opts | None = None, affines=None, tile_subset=None
     return RenderResult(img, mark, sig, pairs, gmark, list(cams))
 
 
-def backward(scene, cams, up_grads, opts: Opts | None = None, affines=None, want_g2d=False):
+def backward(scene, cams, up_grads, opts: Opts | None = None, affines=None, want_g2d=False, tile_subset=None):
     """Analytic gradients of L = <up_grads, outputs>; up_grads is [sum HW, 6]
     (d rgb 3, d depth_acc, d depth_exp, d alpha). Returns a dict of float64 arrays."""
     opts = opts or Opts()
@@ -202,11 +203,13 @@ def backward(scene, cams, up_grads, opts: Opts | None = None, affines=None, want
                opacities=np.zeros(n), sh=np.zeros((n, K, 3)), affine=np.zeros((C, 12)),
                absgrad=np.zeros((n, 2)))
     g2d = np.zeros((C * n, 12)) if want_g2d else None
+    sub = None if tile_subset is None else np.ascontiguousarray(np.asarray(tile_subset, np.int64))
+    nsub = 0 if sub is None else sub.size
     rc = lib().oracle_backward(n, _p(means, _D), _p(scales, _D), _p(quats, _D), _p(opac, _D), _p(sh, _D), K, deg,
                                C, _p(rows, _D), _p(aff, _D), _p(opts.row(), _D), _p(up, _D),
                                _p(out["means"], _D), _p(out["scales"], _D), _p(out["quats"], _D),
                                _p(out["opacities"], _D), _p(out["sh"], _D), _p(out["affine"], _D),
-                               _p(out["absgrad"], _D), _p(g2d, _D))
+                               _p(out["absgrad"], _D), _p(g2d, _D), _p(sub, _I64), nsub)
     if rc != 0:
         raise ValueError("oracle_backward: invalid arguments")
     if want_g2d:

@@ -447,58 +447,95 @@ void bin_all(const SceneD& s, const std::vector<CamD>& cams, const OptsD& o, Bin
 #pragma omp parallel for schedule(dynamic, 1024)
     for (int64_t g = 0; g < n; ++g) B->proj[c * n + g] = project_d(s, g, cams[c], o);
   }
-  // Gaussian-level knife edges (serial: touches tile marks)
-  for (int c = 0; c < C; ++c) {
+  // Gaussian-level knife edges: decided per (camera, Gaussian) in parallel; the tiles they
+  // make uncertain are marked afterwards
+  const int64_t CN = static_cast<int64_t>(C) * n;
+  std::vector<Rect> mark_rect(CN, Rect{0, 0, 0, 0});
+#pragma omp parallel for schedule(dynamic, 1024)
+  for (int64_t id = 0; id < CN; ++id) {
+    const int c = static_cast<int>(id / n);
+    const int64_t g = id % n;
     const CamD& cam = cams[c];
-    for (int64_t g = 0; g < n; ++g) {
-      const Proj<double>& p = B->proj[c * n + g];
-      bool near_plane = std::fabs(p.z_val - cam.znear) <= 1e-6 * std::max(1.0, std::fabs(p.z_val)) ||
-                        std::fabs(p.z_val - cam.zfar) <= 1e-6 * std::max(1.0, std::fabs(p.z_val));
-      bool near_det = std::isfinite(p.det_val) && std::fabs(p.det_val) <= 1e-5 * std::fabs(p.ac_val);
-      if (near_plane || near_det) {
-        // The Gaussian may exist in one precision and not in the other: mark every tile it
-        // could touch, taking its rectangle from a camera with the depth range widened a little.
-        B->gmark[c * n + g] = 1;
-        CamD wide = cam;
-        wide.znear = cam.znear * (1.0 - 1e-5);
-        wide.zfar = cam.zfar * (1.0 + 1e-5);
-        Proj<double> q = project_d(s, g, wide, o);
-        if (q.r > 0) {
-          for (int ty = q.rect.y0; ty < q.rect.y1; ++ty)
-            for (int tx = q.rect.x0; tx < q.rect.x1; ++tx) B->tile_mark[B->tile_off[c] + ty * cam.tiles_x + tx] = 1;
-        }
-      }
-      if (!p.vis) continue;
-      Rect U;
-      if (rect_knife_edge(p, cam, &U)) {
-        B->gmark[c * n + g] = 1;
-        for (int ty = U.y0; ty < U.y1; ++ty)
-          for (int tx = U.x0; tx < U.x1; ++tx) B->tile_mark[B->tile_off[c] + ty * cam.tiles_x + tx] = 1;
-      }
+    const Proj<double>& p = B->proj[id];
+    const bool near_plane = std::fabs(p.z_val - cam.znear) <= 1e-6 * std::max(1.0, std::fabs(p.z_val)) ||
+                            std::fabs(p.z_val - cam.zfar) <= 1e-6 * std::max(1.0, std::fabs(p.z_val));
+    const bool near_det = std::isfinite(p.det_val) && std::fabs(p.det_val) <= 1e-5 * std::fabs(p.ac_val);
+    if (near_plane || near_det) {
+      // The Gaussian may exist in one precision and not in the other: every tile it could touch
+      // is uncertain; its rectangle comes from a camera with the depth range widened a little.
+      B->gmark[id] = 1;
+      CamD wide = cam;
+      wide.znear = cam.znear * (1.0 - 1e-5);
+      wide.zfar = cam.zfar * (1.0 + 1e-5);
+      Proj<double> q = project_d(s, g, wide, o);
+      if (q.r > 0) mark_rect[id] = q.rect;
+    }
+    if (!p.vis) continue;
+    Rect U;
+    if (rect_knife_edge(p, cam, &U)) {
+      B->gmark[id] = 1;
+      mark_rect[id] = U;
     }
   }
-  // binning
-  for (int c = 0; c < C; ++c) {
-    const CamD& cam = cams[c];
-    for (int64_t g = 0; g < n; ++g) {
-      const Proj<double>& p = B->proj[c * n + g];
-      if (!p.vis) continue;
-      for (int ty = p.rect.y0; ty < p.rect.y1; ++ty)
-        for (int tx = p.rect.x0; tx < p.rect.x1; ++tx) {
-          const int64_t tile = B->tile_off[c] + ty * cam.tiles_x + tx;
-          if (o.tile_cull) {
-            double m = tile_cull_margin(p, cam, tx, ty);
-            double rd = tile_min_maha(p, cam, tx, ty);
-            if (std::fabs(m) < 1e-4 * (1.0 + 0.5 * rd)) {
-              B->gmark[c * n + g] = 1;
-              B->tile_mark[tile] = 1;
-            }
-            if (m < 0.0) continue;
-          }
-          B->lists[tile].push_back(c * n + g);
-        }
-    }
+  for (int64_t id = 0; id < CN; ++id) {
+    const Rect& U = mark_rect[id];
+    if (!B->gmark[id]) continue;
+    const int c = static_cast<int>(id / n);
+    for (int ty = U.y0; ty < U.y1; ++ty)
+      for (int tx = U.x0; tx < U.x1; ++tx) B->tile_mark[B->tile_off[c] + ty * cams[c].tiles_x + tx] = 1;
   }
+  // binning: count kept tiles per (camera, Gaussian), then fill, both in parallel
+  std::vector<int64_t> cnt(CN + 1, 0);
+  std::vector<uint8_t> cull_knife(CN, 0);
+  auto visit = [&](int64_t id, auto&& emit) {
+    const int c = static_cast<int>(id / n);
+    const CamD& cam = cams[c];
+    const Proj<double>& p = B->proj[id];
+    if (!p.vis) return;
+    for (int ty = p.rect.y0; ty < p.rect.y1; ++ty)
+      for (int tx = p.rect.x0; tx < p.rect.x1; ++tx) {
+        const int64_t tile = B->tile_off[c] + ty * cam.tiles_x + tx;
+        bool keep = true;
+        if (o.tile_cull) {
+          const double rd = tile_min_maha(p, cam, tx, ty);
+          const double m = std::log(p.op) - 0.5 * rd - std::log(kAlphaMin);
+          if (std::fabs(m) < 1e-4 * (1.0 + 0.5 * rd)) emit(tile, -1);
+          keep = m >= 0.0;
+        }
+        if (keep) emit(tile, id);
+      }
+  };
+#pragma omp parallel for schedule(dynamic, 1024)
+  for (int64_t id = 0; id < CN; ++id) {
+    int64_t k = 0;
+    visit(id, [&](int64_t, int64_t who) {
+      if (who >= 0) ++k;
+      else cull_knife[id] = 1;
+    });
+    cnt[id + 1] = k;
+  }
+  for (int64_t id = 0; id < CN; ++id) cnt[id + 1] += cnt[id];
+  std::vector<int64_t> ptile(cnt[CN]), pid(cnt[CN]);
+#pragma omp parallel for schedule(dynamic, 1024)
+  for (int64_t id = 0; id < CN; ++id) {
+    int64_t k = cnt[id];
+    visit(id, [&](int64_t tile, int64_t who) {
+      if (who >= 0) { ptile[k] = tile; pid[k] = who; ++k; }
+    });
+  }
+  // a tile-cull decision within FP32 reach marks the Gaussian and that tile
+  for (int64_t id = 0; id < CN; ++id)
+    if (cull_knife[id]) {
+      B->gmark[id] = 1;
+      visit(id, [&](int64_t tile, int64_t who) {
+        if (who < 0) B->tile_mark[tile] = 1;
+      });
+    }
+  // bucket the pairs by tile, keeping (camera, Gaussian) order inside a tile
+  std::vector<int64_t> tcnt(B->lists.size(), 0);
+  for (int64_t k = 0; k < cnt[CN]; ++k) ++tcnt[ptile[k]];
+  for (size_t t = 0; t < B->lists.size(); ++t) B->lists[t].reserve(tcnt[t]);
+  for (int64_t k = 0; k < cnt[CN]; ++k) B->lists[ptile[k]].push_back(pid[k]);
   // depth order within each tile: key (float32(z), index)
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t t = 0; t < static_cast<int64_t>(B->lists.size()); ++t) {
@@ -714,11 +751,14 @@ int64_t oracle_render(int64_t n, const double* means, const double* scales, cons
 //   g_affine[C][12] or NULL; g_absgrad[n][2] or NULL (sum over pixels of |dL/dmean2d| per axis)
 //   g2d[C*n][12] or NULL: per (camera, Gaussian) gradients of mean2d x/y, conic a/b/c,
 //                         opacity', rgb, depth, |mean2d| x/y
+//   tile_subset[n_subset] or NULL: only the pixels of these global tiles enter L (the result
+//                         equals the full gradient when up_grads is zero on every other pixel)
 int oracle_backward(int64_t n, const double* means, const double* scales, const double* quats,
                     const double* opac, const double* sh, int K, int deg, int C, const double* cams,
                     const double* affines, const double* opts, const double* up_grads,
                     double* g_means, double* g_scales, double* g_quats, double* g_opac, double* g_sh,
-                    double* g_affine, double* g_absgrad, double* g2d_out) {
+                    double* g_affine, double* g_absgrad, double* g2d_out, const int64_t* tile_subset,
+                    int64_t n_subset) {
   if (!valid_inputs(n, means, scales, quats, opac, sh, K, deg, C, cams)) return -1;
   SceneD s{n, means, scales, quats, opac, sh, K, deg};
   std::vector<CamD> cv = load_cams(C, cams, affines);
@@ -733,8 +773,13 @@ int oracle_backward(int64_t n, const double* means, const double* scales, const 
   constexpr int G2 = 12;
   std::vector<double> pairbuf(static_cast<size_t>(P) * G2, 0.0);
   std::vector<double> tile_aff(static_cast<size_t>(ntiles) * 12, 0.0);
+  std::vector<uint8_t> use_tile(ntiles, tile_subset ? 0 : 1);
+  if (tile_subset)
+    for (int64_t k = 0; k < n_subset; ++k)
+      if (tile_subset[k] >= 0 && tile_subset[k] < ntiles) use_tile[tile_subset[k]] = 1;
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t t = 0; t < ntiles; ++t) {
+    if (!use_tile[t]) continue;
     int c = 0;
     while (t >= B.tile_off[c + 1]) ++c;
     const CamD& cam = cv[c];

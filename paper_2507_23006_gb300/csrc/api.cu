@@ -1,0 +1,943 @@
+// C ABI of libgsr: context, workspace, forward / backward orchestration, detail-level selection.
+//
+// Forward launch sequence on the caller's stream (Sec. 3.1, Eq. 2 and the tile-based binning):
+//   preprocess (projection + colour + cull, compacted by a chained scan)
+//   -> radix sort of the visible records by depth (4 onesweep passes)
+//   -> [tile-cull counts] -> chained scan of per-record tile counts (pair offsets)
+//   -> one stream synchronisation to read V and P and size the pair buffers
+//   -> duplicate-with-keys -> radix sort of the pairs by tile (stable; 1-3 passes)
+//   -> tile ranges -> blend.
+// Sorting by depth first and then stably by tile yields the (tile, depth, index) order with
+// 32-bit keys only.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/gsr.h"
+#include "gsr_internal.cuh"
+
+using namespace gsr;
+
+namespace {
+
+struct Buf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+}  // namespace
+
+struct gsr_ctx {
+  int device = 0;
+  gsr_allocator alloc{};
+  bool has_alloc = false;
+  std::string last_error;
+  size_t held = 0;
+  // scratch
+  Buf seg_begin, seg_start;
+  Buf rec, dkeys, dvals, touched, vis_base, vis_mask;  // binning (recompute / no-state mode)
+  Buf dkeys_s, dvals_s, sort_ktmp, sort_vtmp, sort_hist, sort_status, sort_counters;
+  Buf cnt_sorted, offsets, pre_status, misc;
+  Buf pkeys, pvals, pkeys_s, pvals_s, ranges;  // pairs (no-state mode)
+  Buf pix_T, pix_n, pix_D;                     // per-pixel state (no-state mode)
+  Buf g2d, gaff;
+  // host pinned staging: [0] V (u32), [1] err (int), [2..3] P (u64)
+  void* pinned = nullptr;
+  int* d_err = nullptr;  // 64 bytes: error word at 0, blend counters (4 x u64) at byte 8
+  // profiling
+  bool prof = false;
+  bool count_evals = false;
+  struct Rec3 {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec3> prof_recs;
+  std::vector<cudaEvent_t> ev_pool;
+};
+
+struct gsr_fwd_state {
+  gsr_ctx* ctx = nullptr;
+  gsr_state_info info{};
+  bool has_bins = false;
+  int tile_bits = 1;
+  Buf rec, vis_base, vis_mask, pvals_s, ranges;
+  Buf T_final, n_contrib, D;
+  // the pieces of Buf above that were allocated by this state
+  std::vector<Buf*> owned;
+};
+
+namespace {
+
+gsr_status set_err(gsr_ctx* ctx, gsr_status st, const char* msg) {
+  if (ctx) ctx->last_error = msg ? msg : "";
+  return st;
+}
+
+gsr_status cuda_err(gsr_ctx* ctx, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return GSR_OK;
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  if (ctx) ctx->last_error = m;
+  return e == cudaErrorMemoryAllocation ? GSR_ERR_OOM : GSR_ERR_CUDA;
+}
+
+void* raw_alloc(gsr_ctx* ctx, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  if (ctx->has_alloc) return ctx->alloc.alloc(bytes, reinterpret_cast<gsr_stream>(s), ctx->alloc.user);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void raw_free(gsr_ctx* ctx, void* p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  if (ctx->has_alloc) ctx->alloc.free(p, bytes, reinterpret_cast<gsr_stream>(s), ctx->alloc.user);
+  else cudaFree(p);
+}
+
+// Grows `b` to hold at least `bytes` (contents are not preserved).
+bool ensure(gsr_ctx* ctx, Buf& b, size_t bytes, cudaStream_t s) {
+  if (b.cap >= bytes && b.p) return true;
+  if (b.p) {
+    raw_free(ctx, b.p, b.cap, s);
+    ctx->held -= b.cap;
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  size_t want = std::max<size_t>(bytes + bytes / 8, 256);
+  want = (want + 255) & ~static_cast<size_t>(255);
+  b.p = raw_alloc(ctx, want, s);
+  if (!b.p) return false;
+  b.cap = want;
+  ctx->held += want;
+  return true;
+}
+
+void release(gsr_ctx* ctx, Buf& b, cudaStream_t s) {
+  if (b.p) {
+    raw_free(ctx, b.p, b.cap, s);
+    ctx->held -= b.cap;
+  }
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+template <typename T>
+T* as(Buf& b) {
+  return static_cast<T*>(b.p);
+}
+
+unsigned long long* counters_of(gsr_ctx* ctx) {
+  return ctx->count_evals ? reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(ctx->d_err) + 8) : nullptr;
+}
+
+cudaEvent_t take_event(gsr_ctx* ctx) {
+  if (!ctx->ev_pool.empty()) {
+    cudaEvent_t e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Records CUDA events around one stage while profiling is on.
+struct StageTimer {
+  gsr_ctx* ctx;
+  int stage;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  StageTimer(gsr_ctx* c, int st, cudaStream_t str) : ctx(c), stage(st), s(str) {
+    if (ctx->prof && (a = take_event(ctx))) cudaEventRecord(a, s);
+  }
+  ~StageTimer() {
+    if (!a) return;
+    cudaEvent_t b = take_event(ctx);
+    if (!b) {
+      ctx->ev_pool.push_back(a);
+      return;
+    }
+    cudaEventRecord(b, s);
+    ctx->prof_recs.push_back({stage, a, b});
+  }
+};
+
+bool finite3x4(const float* v) {
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+gsr_status validate(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_camera* cams, int32_t C, const gsr_opts* o) {
+  if (!ctx) return GSR_ERR_INVALID_ARG;
+  if (!g || !cams || !o) return set_err(ctx, GSR_ERR_INVALID_ARG, "null gaussians, cameras or opts");
+  if (C < 1 || C > kMaxCams) return set_err(ctx, GSR_ERR_INVALID_ARG, "n_cams must be in 1..32");
+  if (g->n < 0) return set_err(ctx, GSR_ERR_INVALID_ARG, "negative n");
+  if (g->n > 0 && (!g->means || !g->scales || !g->quats || !g->opacities || !g->sh))
+    return set_err(ctx, GSR_ERR_INVALID_ARG, "null Gaussian array with n > 0");
+  if (g->sh_degree < 0 || g->sh_degree > 3) return set_err(ctx, GSR_ERR_INVALID_ARG, "sh_degree must be 0..3");
+  if (g->sh_coeffs < (g->sh_degree + 1) * (g->sh_degree + 1) || g->sh_coeffs > 16)
+    return set_err(ctx, GSR_ERR_INVALID_ARG, "sh_coeffs must be in (deg+1)^2..16");
+  if (g->attr_dtype < 0 || g->attr_dtype > 2 || g->sh_dtype < 0 || g->sh_dtype > 2)
+    return set_err(ctx, GSR_ERR_INVALID_ARG, "unknown dtype");
+  if (g->nsegs < 0 || (g->nsegs > 0 && !g->segs)) return set_err(ctx, GSR_ERR_INVALID_ARG, "bad segment list");
+  for (int s = 0; s < g->nsegs; ++s) {
+    const gsr_segment& sg = g->segs[s];
+    if (sg.begin < 0 || sg.count < 0 || sg.begin + sg.count > g->n)
+      return set_err(ctx, GSR_ERR_INVALID_ARG, "segment outside the arrays");
+  }
+  for (int c = 0; c < C; ++c) {
+    const gsr_camera& k = cams[c];
+    if (!(k.fx > 0.f) || !(k.fy > 0.f) || !std::isfinite(k.fx) || !std::isfinite(k.fy))
+      return set_err(ctx, GSR_ERR_INVALID_ARG, "fx, fy must be positive");
+    if (k.width < 1 || k.height < 1 || k.width > 16384 || k.height > 16384)
+      return set_err(ctx, GSR_ERR_INVALID_ARG, "width and height must be in 1..16384");
+    if (!(k.near_plane > 0.f) || !(k.far_plane > k.near_plane))
+      return set_err(ctx, GSR_ERR_INVALID_ARG, "need 0 < near < far");
+    if (!finite3x4(k.viewmat) || !std::isfinite(k.cx) || !std::isfinite(k.cy))
+      return set_err(ctx, GSR_ERR_INVALID_ARG, "non-finite camera");
+  }
+  if (!(o->eps2d >= 0.f)) return set_err(ctx, GSR_ERR_INVALID_ARG, "eps2d must be >= 0");
+  return GSR_OK;
+}
+
+long long render_count(const gsr_gaussians* g) {
+  if (!g->segs) return g->n;
+  long long s = 0;
+  for (int k = 0; k < g->nsegs; ++k) s += g->segs[k].count;
+  return s;
+}
+
+CamBatch make_cams(const gsr_camera* cams, int C, long long* npix) {
+  CamBatch cb;
+  std::memset(&cb, 0, sizeof(cb));
+  cb.C = C;
+  int tiles = 0;
+  long long pix = 0;
+  for (int c = 0; c < C; ++c) {
+    const gsr_camera& k = cams[c];
+    DevCam& d = cb.cam[c];
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j) d.R[i * 3 + j] = k.viewmat[i * 4 + j];
+      d.t[i] = k.viewmat[i * 4 + 3];
+    }
+    d.fx = k.fx; d.fy = k.fy; d.cx = k.cx; d.cy = k.cy;
+    d.limx = 1.3f * (0.5f * k.width) / k.fx;
+    d.limy = 1.3f * (0.5f * k.height) / k.fy;
+    d.znear = k.near_plane;
+    d.zfar = k.far_plane;
+    for (int j = 0; j < 3; ++j) {
+      double s = 0;
+      for (int i = 0; i < 3; ++i) s += static_cast<double>(k.viewmat[i * 4 + j]) * k.viewmat[i * 4 + 3];
+      d.center[j] = static_cast<float>(-s);
+    }
+    d.W = k.width;
+    d.H = k.height;
+    d.tiles_x = (k.width + kTile - 1) / kTile;
+    d.tiles_y = (k.height + kTile - 1) / kTile;
+    d.tile_off = tiles;
+    d.pix_off = pix;
+    d.aff = k.appearance;
+    tiles += d.tiles_x * d.tiles_y;
+    pix += static_cast<long long>(k.width) * k.height;
+  }
+  cb.total_tiles = tiles;
+  *npix = pix;
+  return cb;
+}
+
+int bits_for(long long v) {
+  int b = 1;
+  while ((1ll << b) < v) ++b;
+  return b;
+}
+
+#define GSR_TRY_ALLOC(buf, bytes)                                          \
+  do {                                                                     \
+    if (!ensure(ctx, (buf), (bytes), s)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed"); \
+  } while (0)
+
+struct BinOut {
+  Buf* rec;
+  Buf* vis_base;
+  Buf* vis_mask;
+  Buf* pvals_s;
+  Buf* ranges;
+};
+
+// Preprocess + sort + bin into `bo`. Returns V and P through the pointers.
+gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb, const gsr_opts* o, BinOut bo,
+                       long long* V_out, long long* P_out, cudaStream_t s) {
+  const long long N = render_count(g);
+  const int C = cb.C;
+  const long long capv = std::max<long long>(1, N * C);
+  // segment map
+  GaussArgs ga;
+  ga.n_render = N;
+  ga.segs.nsegs = 0;
+  ga.segs.begin = nullptr;
+  ga.segs.start = nullptr;
+  if (g->segs) {
+    const int ns = std::max(g->nsegs, 1);
+    GSR_TRY_ALLOC(ctx->seg_begin, sizeof(long long) * ns);
+    GSR_TRY_ALLOC(ctx->seg_start, sizeof(long long) * ns);
+    std::vector<long long> hb(ns, 0), hs(ns, 0);
+    long long acc = 0;
+    for (int k = 0; k < g->nsegs; ++k) {
+      hb[k] = g->segs[k].begin;
+      hs[k] = acc;
+      acc += g->segs[k].count;
+    }
+    // skip empty segments by giving them the start of the next one (search takes the last)
+    cudaError_t e = cudaMemcpyAsync(ctx->seg_begin.p, hb.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->seg_start.p, hs.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "segment upload");
+    // the host vectors must outlive the copies
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "segment upload sync");
+    ga.segs.nsegs = g->nsegs;
+    ga.segs.begin = as<long long>(ctx->seg_begin);
+    ga.segs.start = as<long long>(ctx->seg_start);
+  }
+  ga.means = g->means;
+  ga.scales = g->scales;
+  ga.quats = g->quats;
+  ga.opac = g->opacities;
+  ga.sh = g->sh;
+  ga.K = g->sh_coeffs;
+  ga.deg = g->sh_degree;
+  ga.attr_dtype = g->attr_dtype;
+  ga.sh_dtype = g->sh_dtype;
+
+  const int pre_blocks = static_cast<int>((N + 255) / 256);
+  GSR_TRY_ALLOC(*bo.rec, sizeof(Rec) * capv);
+  GSR_TRY_ALLOC(*bo.vis_base, sizeof(uint32_t) * std::max<long long>(N, 1));
+  GSR_TRY_ALLOC(*bo.vis_mask, sizeof(uint32_t) * std::max<long long>(N, 1));
+  GSR_TRY_ALLOC(ctx->dkeys, sizeof(uint32_t) * capv);
+  GSR_TRY_ALLOC(ctx->dvals, sizeof(uint32_t) * capv);
+  GSR_TRY_ALLOC(ctx->touched, sizeof(uint32_t) * capv);
+  GSR_TRY_ALLOC(ctx->dkeys_s, sizeof(uint32_t) * capv);
+  GSR_TRY_ALLOC(ctx->dvals_s, sizeof(uint32_t) * capv);
+  GSR_TRY_ALLOC(ctx->offsets, sizeof(uint32_t) * capv);
+  GSR_TRY_ALLOC(ctx->pre_status, sizeof(unsigned long long) * std::max(pre_blocks, 1));
+  const long long scan_blocks = (capv + kScanThreads * kScanItems - 1) / (kScanThreads * kScanItems);
+  // misc: [0] pre counter, [1] V, [2] scan counter, [3] pad, [4..5] P (u64), then scan statuses
+  GSR_TRY_ALLOC(ctx->misc, 64 + sizeof(unsigned long long) * (scan_blocks + 1));
+  uint32_t* misc = as<uint32_t>(ctx->misc);
+  uint32_t* d_counter = misc + 0;
+  uint32_t* d_V = misc + 1;
+  uint32_t* d_scan_counter = misc + 2;
+  unsigned long long* d_P = reinterpret_cast<unsigned long long*>(misc + 4);
+  unsigned long long* d_scan_status = reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->misc.p) + 64);
+  // sort scratch, sized for the larger of the two sorts later
+  cudaError_t e = cudaMemsetAsync(ctx->pre_status.p, 0, sizeof(unsigned long long) * std::max(pre_blocks, 1), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->misc.p, 0, 64, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
+
+  PreOut po;
+  po.rec = as<Rec>(*bo.rec);
+  po.depth_keys = as<uint32_t>(ctx->dkeys);
+  po.depth_vals = as<uint32_t>(ctx->dvals);
+  po.touched = as<uint32_t>(ctx->touched);
+  po.vis_base = as<uint32_t>(*bo.vis_base);
+  po.vis_mask = as<uint32_t>(*bo.vis_mask);
+  po.status = as<unsigned long long>(ctx->pre_status);
+  po.counter = d_counter;
+  po.v_total = d_V;
+  po.err = ctx->d_err;
+  {
+    StageTimer tm(ctx, GSR_STAGE_PREPROCESS, s);
+    launch_preprocess_fwd(ga, cb, o->eps2d, o->antialiased, po, pre_blocks, s);
+  }
+
+  // depth sort of the visible records (V read on the device)
+  auto ensure_sort = [&](long long n) -> bool {
+    const size_t words = sort_status_words(n) * 4;
+    return ensure(ctx, ctx->sort_ktmp, sizeof(uint32_t) * n, s) && ensure(ctx, ctx->sort_vtmp, sizeof(uint32_t) * n, s) &&
+           ensure(ctx, ctx->sort_hist, sizeof(uint32_t) * 4 * 256, s) &&
+           ensure(ctx, ctx->sort_status, sizeof(uint32_t) * std::max<size_t>(words, 256), s) &&
+           ensure(ctx, ctx->sort_counters, sizeof(uint32_t) * 4, s);
+  };
+  if (!ensure_sort(capv)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
+  SortScratch sc;
+  sc.keys_tmp = as<uint32_t>(ctx->sort_ktmp);
+  sc.vals_tmp = as<uint32_t>(ctx->sort_vtmp);
+  sc.hist = as<uint32_t>(ctx->sort_hist);
+  sc.status = as<uint32_t>(ctx->sort_status);
+  sc.counters = as<uint32_t>(ctx->sort_counters);
+  if (N * C > 0) {
+    StageTimer tm(ctx, GSR_STAGE_DEPTH_SORT, s);
+    radix_sort_u32(as<uint32_t>(ctx->dkeys), as<uint32_t>(ctx->dvals), as<uint32_t>(ctx->dkeys_s),
+                   as<uint32_t>(ctx->dvals_s), d_V, capv, 0, 32, sc, ctx->d_err, s);
+  }
+
+  const uint32_t* cnt_sorted = nullptr;
+  if (o->tile_cull && N * C > 0) {
+    GSR_TRY_ALLOC(ctx->cnt_sorted, sizeof(uint32_t) * capv);
+    StageTimer tm(ctx, GSR_STAGE_TILE_COUNT, s);
+    launch_duplicate(as<Rec>(*bo.rec), as<uint32_t>(ctx->dvals_s), nullptr, d_V, capv, cb, 1,
+                     as<uint32_t>(ctx->cnt_sorted), nullptr, nullptr, s);
+    cnt_sorted = as<uint32_t>(ctx->cnt_sorted);
+  }
+  {
+    StageTimer tm(ctx, GSR_STAGE_PAIR_SCAN, s);
+    pair_offsets_scan(as<uint32_t>(ctx->touched), as<uint32_t>(ctx->dvals_s), cnt_sorted, as<uint32_t>(ctx->offsets),
+                      d_V, capv, d_scan_status, d_scan_counter, d_P, ctx->d_err, s);
+  }
+  // read V, P and the error word
+  uint32_t* h = static_cast<uint32_t*>(ctx->pinned);
+  {
+    StageTimer tm(ctx, GSR_STAGE_READBACK, s);
+    e = cudaMemcpyAsync(h, misc, 32, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h + 8, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "binning");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "binning launch");
+  const long long V = N > 0 ? h[1] : 0;
+  unsigned long long Pu;
+  std::memcpy(&Pu, h + 4, sizeof(Pu));
+  const int derr = static_cast<int>(h[8]);
+  if (derr & kErrTimeout) return set_err(ctx, GSR_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out in binning");
+  if (derr & kErrOverflow) return set_err(ctx, GSR_ERR_UNSUPPORTED, "more than 2^32 (tile, Gaussian) pairs");
+  if (V > capv) return set_err(ctx, GSR_ERR_CUDA, "inconsistent visible count");
+  const long long P = V > 0 ? static_cast<long long>(Pu) : 0;
+  if (P >= (1ll << 30)) return set_err(ctx, GSR_ERR_UNSUPPORTED, "more than 2^30 (tile, Gaussian) pairs");
+  *V_out = V;
+  *P_out = P;
+
+  // duplicate, sort by tile, ranges
+  const long long Pc = std::max<long long>(P, 1);
+  GSR_TRY_ALLOC(ctx->pkeys, sizeof(uint32_t) * Pc);
+  GSR_TRY_ALLOC(ctx->pvals, sizeof(uint32_t) * Pc);
+  GSR_TRY_ALLOC(ctx->pkeys_s, sizeof(uint32_t) * Pc);
+  GSR_TRY_ALLOC(*bo.pvals_s, sizeof(uint32_t) * Pc);
+  GSR_TRY_ALLOC(*bo.ranges, sizeof(uint2) * std::max(cb.total_tiles, 1));
+  e = cudaMemsetAsync(bo.ranges->p, 0, sizeof(uint2) * std::max(cb.total_tiles, 1), s);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "memset ranges");
+  if (P > 0) {
+    if (!ensure_sort(Pc)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
+    sc.keys_tmp = as<uint32_t>(ctx->sort_ktmp);
+    sc.vals_tmp = as<uint32_t>(ctx->sort_vtmp);
+    sc.hist = as<uint32_t>(ctx->sort_hist);
+    sc.status = as<uint32_t>(ctx->sort_status);
+    sc.counters = as<uint32_t>(ctx->sort_counters);
+    {
+      StageTimer tm(ctx, GSR_STAGE_DUPLICATE, s);
+      launch_duplicate(as<Rec>(*bo.rec), as<uint32_t>(ctx->dvals_s), as<uint32_t>(ctx->offsets), d_V, capv, cb,
+                       o->tile_cull, nullptr, as<uint32_t>(ctx->pkeys), as<uint32_t>(ctx->pvals), s);
+    }
+    const int tb = bits_for(cb.total_tiles);
+    {
+      StageTimer tm(ctx, GSR_STAGE_TILE_SORT, s);
+      radix_sort_u32(as<uint32_t>(ctx->pkeys), as<uint32_t>(ctx->pvals), as<uint32_t>(ctx->pkeys_s),
+                     as<uint32_t>(*bo.pvals_s), nullptr, P, 0, tb, sc, ctx->d_err, s);
+    }
+    StageTimer tm(ctx, GSR_STAGE_RANGES, s);
+    launch_ranges(as<uint32_t>(ctx->pkeys_s), P, as<uint2>(*bo.ranges), s);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "pair launch");
+  return GSR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gsr_status_string(gsr_status s) {
+  switch (s) {
+    case GSR_OK: return "ok";
+    case GSR_WARN_OVER_BUDGET: return "over budget";
+    case GSR_ERR_INVALID_ARG: return "invalid argument";
+    case GSR_ERR_OOM: return "out of device memory";
+    case GSR_ERR_CUDA: return "CUDA error";
+    case GSR_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+    case GSR_ERR_UNSUPPORTED: return "unsupported size";
+  }
+  return "unknown status";
+}
+
+gsr_status gsr_create(gsr_ctx** out, int device, const gsr_allocator* alloc) {
+  if (!out) return GSR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (alloc && (!alloc->alloc || !alloc->free)) return GSR_ERR_INVALID_ARG;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return GSR_ERR_CUDA;
+  gsr_ctx* ctx = new (std::nothrow) gsr_ctx();
+  if (!ctx) return GSR_ERR_OOM;
+  ctx->device = device;
+  if (alloc) {
+    ctx->alloc = *alloc;
+    ctx->has_alloc = true;
+  }
+  if (cudaMallocHost(&ctx->pinned, 256) != cudaSuccess || cudaMalloc(&ctx->d_err, 64) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    delete ctx;
+    return GSR_ERR_OOM;
+  }
+  cudaMemset(ctx->d_err, 0, 64);
+  *out = ctx;
+  return GSR_OK;
+}
+
+void gsr_destroy(gsr_ctx* ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  Buf* all[] = {&ctx->seg_begin, &ctx->seg_start, &ctx->rec, &ctx->dkeys, &ctx->dvals, &ctx->touched,
+                &ctx->vis_base, &ctx->vis_mask, &ctx->dkeys_s, &ctx->dvals_s, &ctx->sort_ktmp, &ctx->sort_vtmp,
+                &ctx->sort_hist, &ctx->sort_status, &ctx->sort_counters, &ctx->cnt_sorted, &ctx->offsets,
+                &ctx->pre_status, &ctx->misc, &ctx->pkeys, &ctx->pvals, &ctx->pkeys_s, &ctx->pvals_s,
+                &ctx->ranges, &ctx->pix_T, &ctx->pix_n, &ctx->pix_D, &ctx->g2d, &ctx->gaff};
+  for (Buf* b : all) release(ctx, *b, nullptr);
+  for (auto& r : ctx->prof_recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  delete ctx;
+}
+
+const char* gsr_last_error(const gsr_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+size_t gsr_workspace_bytes(const gsr_ctx* ctx) { return ctx ? ctx->held : 0; }
+
+gsr_status gsr_workspace_query(gsr_ctx* ctx, int64_t n_render, const gsr_camera* cams, int32_t n_cams,
+                               int64_t expected_pairs, size_t* bytes_out) {
+  if (!ctx || !cams || !bytes_out || n_cams < 1 || n_cams > kMaxCams || n_render < 0 || expected_pairs < 0)
+    return GSR_ERR_INVALID_ARG;
+  long long npix = 0;
+  CamBatch cb = make_cams(cams, n_cams, &npix);
+  const size_t capv = static_cast<size_t>(std::max<int64_t>(1, n_render * n_cams));
+  const size_t P = static_cast<size_t>(std::max<int64_t>(1, expected_pairs));
+  size_t b = 0;
+  b += capv * (sizeof(Rec) + 7 * sizeof(uint32_t));           // records, keys, values, counts, offsets
+  b += static_cast<size_t>(n_render) * 2 * sizeof(uint32_t);  // visibility
+  b += std::max(capv, P) * 2 * sizeof(uint32_t) + sort_status_words(std::max(capv, P)) * 4 * sizeof(uint32_t);
+  b += P * 4 * sizeof(uint32_t);                              // pairs
+  b += static_cast<size_t>(cb.total_tiles) * sizeof(uint2);
+  b += static_cast<size_t>(npix) * 3 * sizeof(float);         // per-pixel state
+  *bytes_out = b;
+  return GSR_OK;
+}
+
+gsr_status gsr_render_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_camera* cams, int32_t n_cams,
+                              const gsr_opts* opts, const gsr_outputs* out, gsr_fwd_state** state_out,
+                              gsr_stream stream) {
+  gsr_status st = validate(ctx, g, cams, n_cams, opts);
+  if (st != GSR_OK) return st;
+  if (!out || !out->rgb) return set_err(ctx, GSR_ERR_INVALID_ARG, "rgb output is required");
+  if (state_out) *state_out = nullptr;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  long long npix = 0;
+  const CamBatch cb = make_cams(cams, n_cams, &npix);
+  const long long N = render_count(g);
+  if (N * n_cams >= (1ll << 31)) return set_err(ctx, GSR_ERR_UNSUPPORTED, "more than 2^31 (camera, Gaussian) pairs");
+
+  gsr_fwd_state* stt = nullptr;
+  if (state_out) {
+    stt = new (std::nothrow) gsr_fwd_state();
+    if (!stt) return set_err(ctx, GSR_ERR_OOM, "host allocation failed");
+    stt->ctx = ctx;
+    stt->has_bins = opts->save_state != 0;
+  }
+  BinOut bo;
+  if (stt && stt->has_bins) {
+    bo = BinOut{&stt->rec, &stt->vis_base, &stt->vis_mask, &stt->pvals_s, &stt->ranges};
+  } else {
+    bo = BinOut{&ctx->rec, &ctx->vis_base, &ctx->vis_mask, &ctx->pvals_s, &ctx->ranges};
+  }
+  long long V = 0, P = 0;
+  st = run_binning(ctx, g, cb, opts, bo, &V, &P, s);
+  if (st != GSR_OK) {
+    if (stt) gsr_state_release(ctx, stt);
+    return st;
+  }
+  Buf* pT = stt ? &stt->T_final : &ctx->pix_T;
+  Buf* pn = stt ? &stt->n_contrib : &ctx->pix_n;
+  Buf* pD = stt ? &stt->D : &ctx->pix_D;
+  if (!ensure(ctx, *pT, sizeof(float) * npix, s) || !ensure(ctx, *pn, sizeof(uint32_t) * npix, s) ||
+      !ensure(ctx, *pD, sizeof(float) * npix, s)) {
+    if (stt) gsr_state_release(ctx, stt);
+    return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
+  }
+  BlendFwdOut bf;
+  bf.rgb = out->rgb;
+  bf.depth_acc = out->depth_acc;
+  bf.depth_exp = out->depth_exp;
+  bf.alpha = out->alpha;
+  bf.T_final = as<float>(*pT);
+  bf.n_contrib = as<uint32_t>(*pn);
+  bf.D_state = as<float>(*pD);
+  {
+    StageTimer tm(ctx, GSR_STAGE_BLEND_FWD, s);
+    launch_blend_fwd(as<Rec>(*bo.rec), as<uint32_t>(*bo.pvals_s), as<uint2>(*bo.ranges), cb, opts->bg, bf,
+                     counters_of(ctx), s);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    if (stt) gsr_state_release(ctx, stt);
+    return cuda_err(ctx, e, "blend launch");
+  }
+  if (stt) {
+    stt->info.n_render = N;
+    stt->info.n_cams = n_cams;
+    stt->info.n_visible = V;
+    stt->info.n_pairs = P;
+    stt->info.n_tiles = cb.total_tiles;
+    stt->info.n_pixels = npix;
+    stt->tile_bits = bits_for(cb.total_tiles);
+    *state_out = stt;
+  }
+  return GSR_OK;
+}
+
+gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_camera* cams, int32_t n_cams,
+                               const gsr_opts* opts, const gsr_fwd_state* state, const gsr_out_grads* dout,
+                               const gsr_param_grads* grads, gsr_stream stream) {
+  gsr_status st = validate(ctx, g, cams, n_cams, opts);
+  if (st != GSR_OK) return st;
+  if (!state || state->ctx != ctx || !dout || !grads)
+    return set_err(ctx, GSR_ERR_INVALID_ARG, "null state, upstream or gradient struct");
+  if (g->n > 0 && (!grads->means || !grads->scales || !grads->quats || !grads->opacities || !grads->sh))
+    return set_err(ctx, GSR_ERR_INVALID_ARG, "null parameter gradient array");
+  const long long N = render_count(g);
+  if (N != state->info.n_render || n_cams != state->info.n_cams)
+    return set_err(ctx, GSR_ERR_INVALID_ARG, "inputs differ from the forward that made the state");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  long long npix = 0;
+  const CamBatch cb = make_cams(cams, n_cams, &npix);
+  gsr_fwd_state* ms = const_cast<gsr_fwd_state*>(state);
+  BinOut bo;
+  long long V = state->info.n_visible;
+  if (state->has_bins) {
+    bo = BinOut{&ms->rec, &ms->vis_base, &ms->vis_mask, &ms->pvals_s, &ms->ranges};
+  } else {
+    bo = BinOut{&ctx->rec, &ctx->vis_base, &ctx->vis_mask, &ctx->pvals_s, &ctx->ranges};
+    long long P = 0;
+    st = run_binning(ctx, g, cb, opts, bo, &V, &P, s);
+    if (st != GSR_OK) return st;
+    if (V != state->info.n_visible || P != state->info.n_pairs)
+      return set_err(ctx, GSR_ERR_INVALID_ARG, "recomputed binning differs from the forward");
+  }
+  const long long Vc = std::max<long long>(V, 1);
+  if (!ensure(ctx, ctx->g2d, sizeof(Grad2D) * Vc, s)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
+  e = cudaMemsetAsync(ctx->g2d.p, 0, sizeof(Grad2D) * Vc, s);
+  if (e == cudaSuccess && grads->appearance)
+    e = cudaMemsetAsync(grads->appearance, 0, sizeof(float) * 12 * n_cams, s);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
+  BlendBwdIn bi;
+  bi.d_rgb = dout->rgb;
+  bi.d_depth_acc = dout->depth_acc;
+  bi.d_depth_exp = dout->depth_exp;
+  bi.d_alpha = dout->alpha;
+  bi.T_final = static_cast<const float*>(state->T_final.p);
+  bi.n_contrib = static_cast<const uint32_t*>(state->n_contrib.p);
+  bi.D_state = static_cast<const float*>(state->D.p);
+  {
+    StageTimer tm(ctx, GSR_STAGE_BLEND_BWD, s);
+    launch_blend_bwd(as<Rec>(*bo.rec), as<uint32_t>(*bo.pvals_s), as<uint2>(*bo.ranges), cb, opts->bg, bi,
+                     as<Grad2D>(ctx->g2d), grads->appearance, opts->absgrad && grads->absgrad, counters_of(ctx), s);
+  }
+  if (g->segs && g->n > 0) {
+    // rows outside the segments are not visited by the kernel
+    const size_t n = static_cast<size_t>(g->n);
+    e = cudaMemsetAsync(grads->means, 0, sizeof(float) * 3 * n, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grads->scales, 0, sizeof(float) * 3 * n, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grads->quats, 0, sizeof(float) * 4 * n, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grads->opacities, 0, sizeof(float) * n, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grads->sh, 0, sizeof(float) * 3 * g->sh_coeffs * n, s);
+    if (e == cudaSuccess && grads->absgrad) e = cudaMemsetAsync(grads->absgrad, 0, sizeof(float) * 2 * n, s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
+  }
+  if (grads->absgrad && !opts->absgrad && !g->segs) {
+    e = cudaMemsetAsync(grads->absgrad, 0, sizeof(float) * 2 * static_cast<size_t>(g->n), s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
+  }
+  GaussArgs ga;
+  ga.n_render = N;
+  ga.segs.nsegs = g->segs ? g->nsegs : 0;
+  ga.segs.begin = g->segs ? as<long long>(ctx->seg_begin) : nullptr;
+  ga.segs.start = g->segs ? as<long long>(ctx->seg_start) : nullptr;
+  if (g->segs && state->has_bins) {
+    // the segment table may have been overwritten by another forward: upload it again
+    std::vector<long long> hb(std::max(g->nsegs, 1), 0), hs(std::max(g->nsegs, 1), 0);
+    long long acc = 0;
+    for (int k = 0; k < g->nsegs; ++k) { hb[k] = g->segs[k].begin; hs[k] = acc; acc += g->segs[k].count; }
+    if (!ensure(ctx, ctx->seg_begin, sizeof(long long) * hb.size(), s) ||
+        !ensure(ctx, ctx->seg_start, sizeof(long long) * hs.size(), s))
+      return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
+    e = cudaMemcpyAsync(ctx->seg_begin.p, hb.data(), sizeof(long long) * hb.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->seg_start.p, hs.data(), sizeof(long long) * hs.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "segment upload");
+    ga.segs.begin = as<long long>(ctx->seg_begin);
+    ga.segs.start = as<long long>(ctx->seg_start);
+  }
+  ga.means = g->means;
+  ga.scales = g->scales;
+  ga.quats = g->quats;
+  ga.opac = g->opacities;
+  ga.sh = g->sh;
+  ga.K = g->sh_coeffs;
+  ga.deg = g->sh_degree;
+  ga.attr_dtype = g->attr_dtype;
+  ga.sh_dtype = g->sh_dtype;
+  ParamGrads pg;
+  pg.means = grads->means;
+  pg.scales = grads->scales;
+  pg.quats = grads->quats;
+  pg.opac = grads->opacities;
+  pg.sh = grads->sh;
+  pg.absgrad = opts->absgrad ? grads->absgrad : nullptr;
+  {
+    StageTimer tm(ctx, GSR_STAGE_PREPROCESS_BWD, s);
+    launch_preprocess_bwd(ga, cb, opts->eps2d, opts->antialiased, as<Rec>(*bo.rec), as<uint32_t>(*bo.vis_base),
+                          as<uint32_t>(*bo.vis_mask), as<Grad2D>(ctx->g2d), pg, s);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "backward launch");
+  return GSR_OK;
+}
+
+void gsr_state_release(gsr_ctx* ctx, gsr_fwd_state* state) {
+  if (!state) return;
+  gsr_ctx* c = ctx ? ctx : state->ctx;
+  Buf* all[] = {&state->rec, &state->vis_base, &state->vis_mask, &state->pvals_s, &state->ranges,
+                &state->T_final, &state->n_contrib, &state->D};
+  if (c) {
+    cudaDeviceSynchronize();
+    for (Buf* b : all) release(c, *b, nullptr);
+  }
+  delete state;
+}
+
+gsr_status gsr_state_get_info(const gsr_fwd_state* state, gsr_state_info* info) {
+  if (!state || !info) return GSR_ERR_INVALID_ARG;
+  *info = state->info;
+  return GSR_OK;
+}
+
+gsr_status gsr_state_copy(const gsr_fwd_state* state, int32_t which, void* dst, size_t bytes, gsr_stream stream) {
+  if (!state || !dst) return GSR_ERR_INVALID_ARG;
+  const gsr_ctx* ctx = state->ctx;
+  const void* src = nullptr;
+  size_t have = 0;
+  auto pick = [&](const Buf& own, const Buf& scratch, size_t n) {
+    const Buf& b = state->has_bins ? own : scratch;
+    src = b.p;
+    have = std::min(n, b.cap);
+  };
+  const gsr_state_info& I = state->info;
+  switch (which) {
+    case GSR_BUF_RECORDS: pick(state->rec, ctx->rec, sizeof(Rec) * I.n_visible); break;
+    case GSR_BUF_VIS_BASE: pick(state->vis_base, ctx->vis_base, 4 * I.n_render); break;
+    case GSR_BUF_VIS_MASK: pick(state->vis_mask, ctx->vis_mask, 4 * I.n_render); break;
+    case GSR_BUF_PAIR_VALS: pick(state->pvals_s, ctx->pvals_s, 4 * I.n_pairs); break;
+    case GSR_BUF_RANGES: pick(state->ranges, ctx->ranges, 8 * I.n_tiles); break;
+    case GSR_BUF_T_FINAL: src = state->T_final.p; have = std::min<size_t>(4 * I.n_pixels, state->T_final.cap); break;
+    case GSR_BUF_N_CONTRIB: src = state->n_contrib.p; have = std::min<size_t>(4 * I.n_pixels, state->n_contrib.cap); break;
+    case GSR_BUF_DEPTH_ACC: src = state->D.p; have = std::min<size_t>(4 * I.n_pixels, state->D.cap); break;
+    default: return GSR_ERR_INVALID_ARG;
+  }
+  if (!src || bytes > have) return GSR_ERR_INVALID_ARG;
+  if (bytes == 0) return GSR_OK;
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GSR_OK : GSR_ERR_CUDA;
+}
+
+gsr_status gsr_sync_check(gsr_ctx* ctx, gsr_stream stream) {
+  if (!ctx) return GSR_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "sync");
+  if (h) {
+    cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s);
+    if (h & kErrTimeout) return set_err(ctx, GSR_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out");
+    return set_err(ctx, GSR_ERR_UNSUPPORTED, "a device count overflowed");
+  }
+  return GSR_OK;
+}
+
+gsr_status gsr_profile_enable(gsr_ctx* ctx, int32_t on, int32_t count_evals) {
+  if (!ctx) return GSR_ERR_INVALID_ARG;
+  ctx->prof = on != 0;
+  ctx->count_evals = count_evals != 0;
+  return GSR_OK;
+}
+
+gsr_status gsr_profile_collect(gsr_ctx* ctx, double* ms, int64_t* launches, int64_t* counters) {
+  if (!ctx) return GSR_ERR_INVALID_ARG;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  for (auto& r : ctx->prof_recs) {
+    float t = 0.f;
+    e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "profile events");
+    if (ms) ms[r.stage] += t;
+    if (launches) launches[r.stage] += 1;
+    ctx->ev_pool.push_back(r.a);
+    ctx->ev_pool.push_back(r.b);
+  }
+  ctx->prof_recs.clear();
+  unsigned long long h[4] = {0, 0, 0, 0};
+  e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(h, reinterpret_cast<char*>(ctx->d_err) + 8, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(reinterpret_cast<char*>(ctx->d_err) + 8, 0, sizeof(h));
+  if (e != cudaSuccess) return cuda_err(ctx, e, "profile counters");
+  if (counters)
+    for (int k = 0; k < GSR_NUM_COUNTERS; ++k) counters[k] += static_cast<int64_t>(h[k]);
+  return GSR_OK;
+}
+
+gsr_status gsr_sort_pairs_u32(gsr_ctx* ctx, const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                              uint32_t* vals_out, int64_t n, int32_t begin_bit, int32_t end_bit, gsr_stream stream) {
+  if (!ctx) return GSR_ERR_INVALID_ARG;
+  if (n < 0 || begin_bit < 0 || end_bit > 32 || end_bit < begin_bit)
+    return set_err(ctx, GSR_ERR_INVALID_ARG, "bad size or bit range");
+  if (n > 0 && (!keys_in || !vals_in || !keys_out || !vals_out))
+    return set_err(ctx, GSR_ERR_INVALID_ARG, "null pointer");
+  if (n >= (1ll << 30)) return set_err(ctx, GSR_ERR_UNSUPPORTED, "n must be below 2^30");
+  if (n == 0) return GSR_OK;
+  if (keys_out == keys_in || vals_out == vals_in) return set_err(ctx, GSR_ERR_INVALID_ARG, "outputs alias inputs");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  if (end_bit == begin_bit) {
+    e = cudaMemcpyAsync(keys_out, keys_in, 4 * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(vals_out, vals_in, 4 * n, cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? GSR_OK : cuda_err(ctx, e, "copy");
+  }
+  const size_t words = sort_status_words(n) * 4;
+  if (!ensure(ctx, ctx->sort_ktmp, 4 * n, s) || !ensure(ctx, ctx->sort_vtmp, 4 * n, s) ||
+      !ensure(ctx, ctx->sort_hist, 4 * 4 * 256, s) || !ensure(ctx, ctx->sort_status, 4 * std::max<size_t>(words, 256), s) ||
+      !ensure(ctx, ctx->sort_counters, 16, s))
+    return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
+  SortScratch sc;
+  sc.keys_tmp = as<uint32_t>(ctx->sort_ktmp);
+  sc.vals_tmp = as<uint32_t>(ctx->sort_vtmp);
+  sc.hist = as<uint32_t>(ctx->sort_hist);
+  sc.status = as<uint32_t>(ctx->sort_status);
+  sc.counters = as<uint32_t>(ctx->sort_counters);
+  radix_sort_u32(keys_in, vals_in, keys_out, vals_out, nullptr, n, begin_bit, end_bit, sc, ctx->d_err, s);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GSR_OK : cuda_err(ctx, e, "sort launch");
+}
+
+gsr_status gsr_select_lod(int32_t P, const double* aabb, int32_t L, const int64_t* level_offsets,
+                          const gsr_camera* cam, const double* thresholds, int64_t budget, int32_t* levels,
+                          gsr_segment* segs, int32_t* nsegs, int64_t* n_selected) {
+  if (P < 0 || L < 1 || !cam || !levels || !nsegs || !n_selected || (P > 0 && (!aabb || !level_offsets || !segs)) ||
+      (L > 1 && !thresholds))
+    return GSR_ERR_INVALID_ARG;
+  for (int k = 0; k + 1 < L - 1; ++k)
+    if (!(thresholds[k] <= thresholds[k + 1])) return GSR_ERR_INVALID_ARG;
+  // camera in double precision
+  double R[9], t[3], ctr[3];
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) R[i * 3 + j] = cam->viewmat[i * 4 + j];
+    t[i] = cam->viewmat[i * 4 + 3];
+  }
+  for (int j = 0; j < 3; ++j) ctr[j] = -(R[0 * 3 + j] * t[0] + R[1 * 3 + j] * t[1] + R[2 * 3 + j] * t[2]);
+  const double fx = cam->fx, fy = cam->fy, cx = cam->cx, cy = cam->cy, W = cam->width, H = cam->height;
+  const double zn = cam->near_plane, zf = cam->far_plane;
+  std::vector<double> dist(P, 0.0);
+  std::vector<int> lev(P, -1);
+  int64_t total = 0;
+  for (int p = 0; p < P; ++p) {
+    const double* b = aabb + 6 * p;
+    // corner k in camera space; culled iff all corners violate one half-space
+    unsigned out_all = 0x3f;
+    for (int k = 0; k < 8; ++k) {
+      const double wx = (k & 1) ? b[3] : b[0], wy = (k & 2) ? b[4] : b[1], wz = (k & 4) ? b[5] : b[2];
+      const double x = R[0] * wx + R[1] * wy + R[2] * wz + t[0];
+      const double y = R[3] * wx + R[4] * wy + R[5] * wz + t[1];
+      const double z = R[6] * wx + R[7] * wy + R[8] * wz + t[2];
+      unsigned o = 0;
+      if (z < zn) o |= 1;
+      if (z > zf) o |= 2;
+      if (fx * x + cx * z < 0.0) o |= 4;
+      if (fx * x + (cx - W) * z > 0.0) o |= 8;
+      if (fy * y + cy * z < 0.0) o |= 16;
+      if (fy * y + (cy - H) * z > 0.0) o |= 32;
+      out_all &= o;
+    }
+    double d2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      const double q = std::min(std::max(ctr[k], b[k]), b[3 + k]);
+      d2 += (ctr[k] - q) * (ctr[k] - q);
+    }
+    dist[p] = std::sqrt(d2);
+    if (out_all) continue;
+    int l = 0;
+    for (int k = 0; k < L - 1; ++k)
+      if (dist[p] < thresholds[k]) {
+        l = L - 1 - k;
+        break;
+      }
+    lev[p] = l;
+  }
+  auto cnt = [&](int p, int l) {
+    return level_offsets[static_cast<int64_t>(l) * (P + 1) + p + 1] - level_offsets[static_cast<int64_t>(l) * (P + 1) + p];
+  };
+  for (int p = 0; p < P; ++p)
+    if (lev[p] >= 0) total += cnt(p, lev[p]);
+  gsr_status status = GSR_OK;
+  if (budget > 0 && total > budget) {
+    // farthest first: order candidates once by (distance desc, index desc)
+    std::vector<int> order;
+    for (int p = 0; p < P; ++p)
+      if (lev[p] > 0) order.push_back(p);
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+      if (dist[a] != dist[b]) return dist[a] > dist[b];
+      return a > b;
+    });
+    for (int p : order) {
+      while (lev[p] > 0 && total > budget) {
+        total -= cnt(p, lev[p]);
+        lev[p] -= 1;
+        total += cnt(p, lev[p]);
+      }
+      if (total <= budget) break;
+    }
+    if (total > budget) status = GSR_WARN_OVER_BUDGET;
+  }
+  int ns = 0;
+  for (int p = 0; p < P; ++p) {
+    levels[p] = lev[p];
+    if (lev[p] < 0) continue;
+    const int64_t c = cnt(p, lev[p]);
+    if (c <= 0) continue;
+    segs[ns].begin = level_offsets[static_cast<int64_t>(lev[p]) * (P + 1) + p];
+    segs[ns].count = c;
+    ++ns;
+  }
+  *nsegs = ns;
+  *n_selected = total;
+  return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,194 @@
+// Internal declarations shared by the CUDA translation units of libgsr (sm_103a).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace gsr {
+
+constexpr int kTile = 16;           // tile edge in pixels
+constexpr int kTilePix = kTile * kTile;
+constexpr int kMaxCams = 32;        // cameras per launch (bit mask of visibility is 32 bits)
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 1e-4f;
+
+// Device error bits (ctx error word).
+constexpr int kErrTimeout = 1;      // a chained-scan look-back gave up
+constexpr int kErrOverflow = 2;     // a count did not fit the buffer it was sized for
+
+// Bound on the polls of one look-back step before it reports kErrTimeout (with a nanosleep of
+// up to 1 us between polls this is well under a second).
+constexpr unsigned kSpinLimit = 1u << 20;
+
+struct DevCam {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  float limx, limy;       // Jacobian clamp of X/Z and Y/Z
+  float znear, zfar;
+  float center[3];        // camera centre in world coordinates
+  int W, H, tiles_x, tiles_y;
+  int tile_off;           // first global tile index of this camera
+  long long pix_off;      // first packed pixel of this camera
+  const float* aff;       // [3,4] appearance transform or nullptr
+};
+
+struct CamBatch {
+  int C;
+  int total_tiles;
+  DevCam cam[kMaxCams];
+};
+
+// Selected-index -> array-index map for segment lists.
+struct SegMap {
+  int nsegs;                   // 0: identity
+  const long long* begin;      // [nsegs] array index of the segment's first Gaussian
+  const long long* start;      // [nsegs] selected index of the segment's first Gaussian
+};
+
+// Splat record: 48 bytes, read by the blend kernels through the sorted pair list.
+//   a = (mean2d x, mean2d y, opacity', view depth z)
+//   b = (conic a, conic b, conic c, red)
+//   c = (green, blue, bits(x0 | x1 << 16), bits(y0 | y1 << 16 | camera << 27))
+struct __align__(16) Rec {
+  float4 a, b, c;
+};
+
+template <typename T>
+__device__ __forceinline__ float ldf(const T* p, long long i);
+template <>
+__device__ __forceinline__ float ldf<float>(const float* p, long long i) { return __ldg(p + i); }
+template <>
+__device__ __forceinline__ float ldf<__half>(const __half* p, long long i) { return __half2float(p[i]); }
+template <>
+__device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16* p, long long i) {
+  return __bfloat162float(p[i]);
+}
+
+__device__ __forceinline__ long long seg_map(const SegMap& m, long long i) {
+  if (m.nsegs == 0) return i;
+  int lo = 0, hi = m.nsegs - 1;
+  while (lo < hi) {  // last segment with start <= i
+    int mid = (lo + hi + 1) >> 1;
+    if (m.start[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return m.begin[lo] + (i - m.start[lo]);
+}
+
+// ---- arguments of the kernels ---------------------------------------------------------------
+
+struct GaussArgs {
+  long long n_render;  // Gaussians rendered
+  SegMap segs;
+  const float* means;
+  const void* scales;
+  const void* quats;
+  const void* opac;
+  const void* sh;
+  int K;               // stored SH coefficients
+  int deg;
+  int attr_dtype;
+  int sh_dtype;
+};
+
+struct PreOut {
+  Rec* rec;                    // [cap_v]
+  uint32_t* depth_keys;        // [cap_v]
+  uint32_t* depth_vals;        // [cap_v]
+  uint32_t* touched;           // [cap_v] tiles in the rectangle
+  uint32_t* vis_base;          // [n_render]
+  uint32_t* vis_mask;          // [n_render]
+  unsigned long long* status;  // [blocks] chained-scan status words
+  uint32_t* counter;           // dynamic block index
+  uint32_t* v_total;           // out: V
+  int* err;
+};
+
+struct Grad2D {  // per visible record: 12 floats, three float4
+  float4 a;      // mean2d x, mean2d y, opacity', depth
+  float4 b;      // conic a, conic b, conic c, red
+  float4 c;      // green, blue, |mean2d x|, |mean2d y|
+};
+
+struct ParamGrads {
+  float* means;
+  float* scales;
+  float* quats;
+  float* opac;
+  float* sh;
+  float* absgrad;
+};
+
+// ---- host-side launchers (one per translation unit) -------------------------------------
+
+void launch_preprocess_fwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased,
+                           const PreOut& out, int blocks, cudaStream_t s);
+void launch_preprocess_bwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased,
+                           const Rec* rec, const uint32_t* vis_base, const uint32_t* vis_mask,
+                           const Grad2D* g2d, const ParamGrads& out, cudaStream_t s);
+
+// Stable radix sort by key bits [begin_bit, end_bit); n taken from *d_n when d_n != nullptr
+// (then max_n bounds it and sizes the launch), else n = max_n.
+struct SortScratch {
+  uint32_t* keys_tmp;
+  uint32_t* vals_tmp;
+  uint32_t* hist;      // [4][256]
+  uint32_t* status;    // [4][max_blocks][256]
+  uint32_t* counters;  // [4]
+  int max_blocks;
+};
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+size_t sort_status_words(long long max_n);
+void radix_sort_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
+                    const uint32_t* d_n, long long max_n, int begin_bit, int end_bit, const SortScratch& sc,
+                    int* err, cudaStream_t s);
+
+// Exclusive scan of per-record tile counts in depth order: counts[i] = touched[order[i]]
+// (or cnt_sorted[i] when given), offsets[i] out, *p_total = sum. n from *d_n.
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+void pair_offsets_scan(const uint32_t* touched, const uint32_t* order, const uint32_t* cnt_sorted,
+                       uint32_t* offsets, const uint32_t* d_n, long long max_n,
+                       unsigned long long* status, uint32_t* counter, unsigned long long* p_total, int* err,
+                       cudaStream_t s);
+
+// Duplicate-with-keys (warp-cooperative). count_only: writes cnt_sorted[i] (tile-culled counts).
+void launch_duplicate(const Rec* rec, const uint32_t* order, const uint32_t* offsets, const uint32_t* d_n,
+                      long long max_n, const CamBatch& cams, int tile_cull, uint32_t* cnt_sorted,
+                      uint32_t* pair_keys, uint32_t* pair_vals, cudaStream_t s);
+void launch_ranges(const uint32_t* sorted_keys, long long P, uint2* ranges, cudaStream_t s);
+
+struct BlendFwdOut {
+  float* rgb;
+  float* depth_acc;
+  float* depth_exp;
+  float* alpha;
+  float* T_final;
+  uint32_t* n_contrib;
+  float* D_state;
+};
+// counters (nullable): [0] evaluations, [1] contributions (forward), [2], [3] (backward)
+void launch_blend_fwd(const Rec* rec, const uint32_t* pair_vals, const uint2* ranges, const CamBatch& cams,
+                      const float* bg, const BlendFwdOut& out, unsigned long long* counters, cudaStream_t s);
+
+struct BlendBwdIn {
+  const float* d_rgb;
+  const float* d_depth_acc;
+  const float* d_depth_exp;
+  const float* d_alpha;
+  const float* T_final;
+  const uint32_t* n_contrib;
+  const float* D_state;
+};
+void launch_blend_bwd(const Rec* rec, const uint32_t* pair_vals, const uint2* ranges, const CamBatch& cams,
+                      const float* bg, const BlendBwdIn& in, Grad2D* g2d, float* g_aff, int absgrad,
+                      unsigned long long* counters, cudaStream_t s);
+
+}  // namespace gsr

@@ -1,0 +1,500 @@
+// Per-Gaussian preprocessing (projection, colour, culling) and its backward pass.
+//
+// Forward (Sec. 3.1: "the 3D Gaussians are first projected onto the image plane"):
+//   Sigma = R S S^T R^T (Eq. 1) from the quaternion and scale, then for every camera of the
+//   launch t = W mu + t_cam, T = J W with J the perspective Jacobian at the clamped direction,
+//   Sigma2D = T Sigma T^T + eps I, the Mip-Splatting opacity compensation (Sec. 3.5.4), the
+//   conic Sigma2D^-1, the 3-sigma tile rectangle, and the colour from degree <= 3 spherical
+//   harmonics. Culled: z outside (near, far), a zero or non-finite quaternion, det <= 0, an
+//   empty rectangle, any non-finite output.
+//
+// One thread owns one Gaussian and loops over the cameras, so each attribute is read from HBM
+// once per launch. Visible (camera, Gaussian) records are written compacted, in (block, thread,
+// camera) order, with the block offsets from a single-pass chained scan (Merrill & Garland
+// decoupled look-back) whose waits are bounded; within one camera the compacted index grows
+// with the Gaussian index, which gives the depth sort its tie-break.
+#include "gsr_internal.cuh"
+#include "scan_util.cuh"
+
+namespace gsr {
+namespace {
+
+// Real spherical-harmonic constants (Condon-Shortley phase), each the normalisation
+// sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times the Legendre and sqrt(2) factors of its term,
+// written as closed forms of pi.
+constexpr float kSH0 = 0.28209479177387814f;   // 1 / (2 sqrt(pi))
+constexpr float kSH1 = 0.48860251190291992f;   // sqrt(3 / (4 pi))
+constexpr float kSH2a = 1.0925484305920792f;   // sqrt(15 / pi) / 2
+constexpr float kSH2b = 0.31539156525252005f;  // sqrt(5 / pi) / 4
+constexpr float kSH2c = 0.54627421529603959f;  // sqrt(15 / pi) / 4
+constexpr float kSH3a = 0.59004358992664352f;  // sqrt(35 / (2 pi)) / 4
+constexpr float kSH3b = 2.8906114426405538f;   // sqrt(105 / pi) / 2
+constexpr float kSH3c = 0.45704579946446572f;  // sqrt(21 / (2 pi)) / 4
+constexpr float kSH3d = 0.37317633259011540f;  // sqrt(7 / pi) / 4
+constexpr float kSH3e = 1.4453057213202769f;   // sqrt(105 / pi) / 4
+
+// Basis at a unit direction, as homogeneous polynomials of (x, y, z).
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float* Y) {
+  Y[0] = kSH0;
+  if (deg < 1) return;
+  Y[1] = -kSH1 * y;
+  Y[2] = kSH1 * z;
+  Y[3] = -kSH1 * x;
+  if (deg < 2) return;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  Y[4] = kSH2a * x * y;
+  Y[5] = -kSH2a * y * z;
+  Y[6] = kSH2b * (2.f * zz - xx - yy);
+  Y[7] = -kSH2a * x * z;
+  Y[8] = kSH2c * (xx - yy);
+  if (deg < 3) return;
+  Y[9] = -kSH3a * y * (3.f * xx - yy);
+  Y[10] = kSH3b * x * y * z;
+  Y[11] = -kSH3c * y * (4.f * zz - xx - yy);
+  Y[12] = kSH3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+  Y[13] = -kSH3c * x * (4.f * zz - xx - yy);
+  Y[14] = kSH3e * z * (xx - yy);
+  Y[15] = -kSH3a * x * (xx - 3.f * yy);
+}
+
+// Accumulates sum_k w_k grad Y_k into (gx, gy, gz).
+__device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z, const float* w, float& gx,
+                                              float& gy, float& gz) {
+  gx = gy = gz = 0.f;
+  if (deg < 1) return;
+  gy -= kSH1 * w[1];
+  gz += kSH1 * w[2];
+  gx -= kSH1 * w[3];
+  if (deg < 2) return;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  gx += kSH2a * y * w[4];
+  gy += kSH2a * x * w[4];
+  gy -= kSH2a * z * w[5];
+  gz -= kSH2a * y * w[5];
+  gx -= 2.f * kSH2b * x * w[6];
+  gy -= 2.f * kSH2b * y * w[6];
+  gz += 4.f * kSH2b * z * w[6];
+  gx -= kSH2a * z * w[7];
+  gz -= kSH2a * x * w[7];
+  gx += 2.f * kSH2c * x * w[8];
+  gy -= 2.f * kSH2c * y * w[8];
+  if (deg < 3) return;
+  gx -= 6.f * kSH3a * x * y * w[9];
+  gy -= 3.f * kSH3a * (xx - yy) * w[9];
+  gx += kSH3b * y * z * w[10];
+  gy += kSH3b * x * z * w[10];
+  gz += kSH3b * x * y * w[10];
+  gx += 2.f * kSH3c * x * y * w[11];
+  gy -= kSH3c * (4.f * zz - xx - 3.f * yy) * w[11];
+  gz -= 8.f * kSH3c * y * z * w[11];
+  gx -= 6.f * kSH3d * x * z * w[12];
+  gy -= 6.f * kSH3d * y * z * w[12];
+  gz += kSH3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+  gx -= kSH3c * (4.f * zz - 3.f * xx - yy) * w[13];
+  gy += 2.f * kSH3c * x * y * w[13];
+  gz -= 8.f * kSH3c * x * z * w[13];
+  gx += 2.f * kSH3e * x * z * w[14];
+  gy -= 2.f * kSH3e * y * z * w[14];
+  gz += kSH3e * (xx - yy) * w[14];
+  gx -= 3.f * kSH3a * (xx - yy) * w[15];
+  gy += 6.f * kSH3a * x * y * w[15];
+}
+
+// Camera-independent part of a Gaussian.
+struct Geo {
+  float m[3];
+  float s[3];
+  float q[4];     // normalised (w, x, y, z)
+  float qinv;     // 1 / |q| of the stored quaternion
+  float R[9];
+  float S[6];     // Sigma: xx, xy, xz, yy, yz, zz
+  float opac;
+};
+
+template <typename AT>
+__device__ __forceinline__ bool load_geo(const GaussArgs& A, long long g, Geo& G) {
+  const AT* sc = static_cast<const AT*>(A.scales);
+  const AT* qt = static_cast<const AT*>(A.quats);
+  const AT* op = static_cast<const AT*>(A.opac);
+  G.m[0] = __ldg(A.means + 3 * g + 0);
+  G.m[1] = __ldg(A.means + 3 * g + 1);
+  G.m[2] = __ldg(A.means + 3 * g + 2);
+  G.s[0] = ldf(sc, 3 * g + 0);
+  G.s[1] = ldf(sc, 3 * g + 1);
+  G.s[2] = ldf(sc, 3 * g + 2);
+  float qw = ldf(qt, 4 * g + 0), qx = ldf(qt, 4 * g + 1), qy = ldf(qt, 4 * g + 2), qz = ldf(qt, 4 * g + 3);
+  G.opac = ldf(op, g);
+  const float n2 = qw * qw + qx * qx + qy * qy + qz * qz;
+  if (!(n2 > 0.f) || !isfinite(n2)) return false;
+  G.qinv = 1.f / sqrtf(n2);
+  qw *= G.qinv; qx *= G.qinv; qy *= G.qinv; qz *= G.qinv;
+  G.q[0] = qw; G.q[1] = qx; G.q[2] = qy; G.q[3] = qz;
+  float* R = G.R;
+  R[0] = 1.f - 2.f * (qy * qy + qz * qz); R[1] = 2.f * (qx * qy - qw * qz); R[2] = 2.f * (qx * qz + qw * qy);
+  R[3] = 2.f * (qx * qy + qw * qz); R[4] = 1.f - 2.f * (qx * qx + qz * qz); R[5] = 2.f * (qy * qz - qw * qx);
+  R[6] = 2.f * (qx * qz - qw * qy); R[7] = 2.f * (qy * qz + qw * qx); R[8] = 1.f - 2.f * (qx * qx + qy * qy);
+  float M[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) M[i * 3 + j] = R[i * 3 + j] * G.s[j];
+  G.S[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+  G.S[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+  G.S[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+  G.S[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+  G.S[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+  G.S[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+  return isfinite(G.S[0] + G.S[3] + G.S[5] + G.m[0] + G.m[1] + G.m[2]);
+}
+
+// Projection of one Gaussian into one camera, with the intermediates the backward needs.
+struct Proj {
+  float t[3], iz, u, w;
+  bool clx, cly;
+  float T0[3], T1[3];    // rows of J W
+  float ST0[3], ST1[3];  // Sigma T0, Sigma T1
+  float ar, br, cr;      // J W Sigma W^T J^T
+  float det, idet;
+  float comp;            // opacity compensation (1 when not anti-aliased)
+  float mx, my, ca, cb, cc, op;
+  int r, x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ int clamp_tile(float v, int hi) {
+  const float f = floorf(v);
+  return (f > 0.f) ? static_cast<int>(fminf(f, static_cast<float>(hi))) : 0;
+}
+
+__device__ __forceinline__ bool project(const Geo& G, const DevCam& c, float eps, int aa, Proj& P) {
+  const float* W = c.R;
+  P.t[0] = fmaf(W[0], G.m[0], fmaf(W[1], G.m[1], fmaf(W[2], G.m[2], c.t[0])));
+  P.t[1] = fmaf(W[3], G.m[0], fmaf(W[4], G.m[1], fmaf(W[5], G.m[2], c.t[1])));
+  P.t[2] = fmaf(W[6], G.m[0], fmaf(W[7], G.m[1], fmaf(W[8], G.m[2], c.t[2])));
+  if (!(P.t[2] > c.znear && P.t[2] < c.zfar)) return false;
+  P.iz = 1.f / P.t[2];
+  P.u = P.t[0] * P.iz;
+  P.w = P.t[1] * P.iz;
+  const float uc = fminf(fmaxf(P.u, -c.limx), c.limx);
+  const float wc = fminf(fmaxf(P.w, -c.limy), c.limy);
+  P.clx = (P.u < -c.limx) || (P.u > c.limx);
+  P.cly = (P.w < -c.limy) || (P.w > c.limy);
+  const float j00 = c.fx * P.iz, j02 = -c.fx * uc * P.iz;
+  const float j11 = c.fy * P.iz, j12 = -c.fy * wc * P.iz;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    P.T0[k] = j00 * W[k] + j02 * W[6 + k];
+    P.T1[k] = j11 * W[3 + k] + j12 * W[6 + k];
+  }
+  const float* S = G.S;
+  P.ST0[0] = S[0] * P.T0[0] + S[1] * P.T0[1] + S[2] * P.T0[2];
+  P.ST0[1] = S[1] * P.T0[0] + S[3] * P.T0[1] + S[4] * P.T0[2];
+  P.ST0[2] = S[2] * P.T0[0] + S[4] * P.T0[1] + S[5] * P.T0[2];
+  P.ST1[0] = S[0] * P.T1[0] + S[1] * P.T1[1] + S[2] * P.T1[2];
+  P.ST1[1] = S[1] * P.T1[0] + S[3] * P.T1[1] + S[4] * P.T1[2];
+  P.ST1[2] = S[2] * P.T1[0] + S[4] * P.T1[1] + S[5] * P.T1[2];
+  P.ar = P.T0[0] * P.ST0[0] + P.T0[1] * P.ST0[1] + P.T0[2] * P.ST0[2];
+  P.br = P.T0[0] * P.ST1[0] + P.T0[1] * P.ST1[1] + P.T0[2] * P.ST1[2];
+  P.cr = P.T1[0] * P.ST1[0] + P.T1[1] * P.ST1[1] + P.T1[2] * P.ST1[2];
+  const float a = P.ar + eps, b = P.br, cc = P.cr + eps;
+  P.det = a * cc - b * b;
+  if (!(P.det > 0.f)) return false;
+  P.idet = 1.f / P.det;
+  P.comp = 1.f;
+  if (aa) {
+    const float ratio = (P.ar * P.cr - P.br * P.br) * P.idet;
+    P.comp = ratio > 0.f ? sqrtf(ratio) : 0.f;
+  }
+  P.op = G.opac * P.comp;
+  P.ca = cc * P.idet;
+  P.cb = -b * P.idet;
+  P.cc = a * P.idet;
+  const float mid = 0.5f * (a + cc);
+  const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - P.det));
+  P.r = static_cast<int>(ceilf(3.f * sqrtf(lam)));
+  P.mx = c.fx * P.t[0] * P.iz + c.cx;
+  P.my = c.fy * P.t[1] * P.iz + c.cy;
+  const float r = static_cast<float>(P.r);
+  P.x0 = clamp_tile((P.mx - r) * (1.f / kTile), c.tiles_x);
+  P.x1 = clamp_tile((P.mx + r + (kTile - 1)) * (1.f / kTile), c.tiles_x);
+  P.y0 = clamp_tile((P.my - r) * (1.f / kTile), c.tiles_y);
+  P.y1 = clamp_tile((P.my + r + (kTile - 1)) * (1.f / kTile), c.tiles_y);
+  if ((P.x1 - P.x0) * (P.y1 - P.y0) <= 0) return false;
+  return isfinite(P.mx) && isfinite(P.my) && isfinite(P.ca) && isfinite(P.cb) && isfinite(P.cc) &&
+         isfinite(P.op);
+}
+
+template <typename ST>
+__device__ __forceinline__ void eval_color(const GaussArgs& A, long long g, const Geo& G, const DevCam& c,
+                                           float rgb[3], float dir[3], float& dnorm, float Y[16],
+                                           bool clamped[3]) {
+  const float dx = G.m[0] - c.center[0], dy = G.m[1] - c.center[1], dz = G.m[2] - c.center[2];
+  dnorm = sqrtf(dx * dx + dy * dy + dz * dz);
+  const float inv = 1.f / dnorm;
+  dir[0] = dx * inv; dir[1] = dy * inv; dir[2] = dz * inv;
+  sh_basis(A.deg, dir[0], dir[1], dir[2], Y);
+  const int nb = (A.deg + 1) * (A.deg + 1);
+  const ST* sh = static_cast<const ST*>(A.sh) + g * A.K * 3;
+  float v0 = 0.5f, v1 = 0.5f, v2 = 0.5f;
+  for (int k = 0; k < nb; ++k) {
+    v0 = fmaf(ldf(sh, 3 * k + 0), Y[k], v0);
+    v1 = fmaf(ldf(sh, 3 * k + 1), Y[k], v1);
+    v2 = fmaf(ldf(sh, 3 * k + 2), Y[k], v2);
+  }
+  clamped[0] = v0 < 0.f; clamped[1] = v1 < 0.f; clamped[2] = v2 < 0.f;
+  rgb[0] = fmaxf(v0, 0.f); rgb[1] = fmaxf(v1, 0.f); rgb[2] = fmaxf(v2, 0.f);
+}
+
+template <typename AT, typename ST>
+__global__ void __launch_bounds__(256) preprocess_fwd_kernel(GaussArgs A, CamBatch cams, float eps, int aa,
+                                                             PreOut out) {
+  __shared__ unsigned s_bid;
+  __shared__ unsigned long long s_excl;
+  if (threadIdx.x == 0) s_bid = atomicAdd(out.counter, 1u);
+  __syncthreads();
+  const unsigned bid = s_bid;
+  const long long i = static_cast<long long>(bid) * blockDim.x + threadIdx.x;
+  const bool valid = i < A.n_render;
+  long long g = 0;
+  Geo G;
+  uint32_t mask = 0;
+  if (valid) {
+    g = seg_map(A.segs, i);
+    if (load_geo<AT>(A, g, G)) {
+      for (int c = 0; c < cams.C; ++c) {
+        Proj P;
+        if (project(G, cams.cam[c], eps, aa, P)) mask |= 1u << c;
+      }
+    }
+  }
+  uint32_t total;
+  const uint32_t excl_t = block_excl_scan(__popc(mask), &total);
+  if (threadIdx.x == 0) s_excl = chained_prefix(out.status, bid, total, out.err);
+  __syncthreads();
+  const unsigned long long base = s_excl + excl_t;
+  if (valid) {
+    out.vis_base[i] = static_cast<uint32_t>(base);
+    out.vis_mask[i] = mask;
+  }
+  if (valid && i == A.n_render - 1) *out.v_total = static_cast<uint32_t>(s_excl + total);
+  if (!mask) return;
+  unsigned long long v = base;
+  for (int c = 0; c < cams.C; ++c) {
+    if (!(mask & (1u << c))) continue;
+    const DevCam& cam = cams.cam[c];
+    Proj P;
+    project(G, cam, eps, aa, P);
+    float rgb[3], dir[3], dn, Y[16];
+    bool cl[3];
+    eval_color<ST>(A, g, G, cam, rgb, dir, dn, Y, cl);
+    Rec r;
+    r.a = make_float4(P.mx, P.my, P.op, P.t[2]);
+    r.b = make_float4(P.ca, P.cb, P.cc, rgb[0]);
+    const uint32_t lo = static_cast<uint32_t>(P.x0) | (static_cast<uint32_t>(P.x1) << 16);
+    const uint32_t hi = static_cast<uint32_t>(P.y0) | (static_cast<uint32_t>(P.y1) << 16) |
+                        (static_cast<uint32_t>(c) << 27);
+    r.c = make_float4(rgb[1], rgb[2], __uint_as_float(lo), __uint_as_float(hi));
+    out.rec[v] = r;
+    out.depth_keys[v] = __float_as_uint(P.t[2]);
+    out.depth_vals[v] = static_cast<uint32_t>(v);
+    out.touched[v] = static_cast<uint32_t>((P.x1 - P.x0) * (P.y1 - P.y0));
+    ++v;
+  }
+}
+
+// Backward of the projection and colour for every (camera, Gaussian) with gradients in g2d.
+template <typename AT, typename ST>
+__global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussArgs A, CamBatch cams, float eps, int aa,
+                                                             const uint32_t* __restrict__ vis_base,
+                                                             const uint32_t* __restrict__ vis_mask,
+                                                             const Grad2D* __restrict__ g2d, ParamGrads out) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= A.n_render) return;
+  const long long g = seg_map(A.segs, i);
+  const uint32_t mask = vis_mask[i];
+  float dm[3] = {0, 0, 0}, ds[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, dopac = 0.f, dabs[2] = {0, 0};
+  const int KC = A.K * 3;
+  float dsh[48];
+#pragma unroll
+  for (int k = 0; k < 48; ++k) dsh[k] = 0.f;
+  Geo G;
+  if (mask && load_geo<AT>(A, g, G)) {
+    float dR[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long v = vis_base[i];
+    const int nb = (A.deg + 1) * (A.deg + 1);
+    const ST* sh = static_cast<const ST*>(A.sh) + g * KC;
+    for (int c = 0; c < cams.C; ++c) {
+      if (!(mask & (1u << c))) continue;
+      const DevCam& cam = cams.cam[c];
+      Proj P;
+      project(G, cam, eps, aa, P);
+      const Grad2D gd = g2d[v];
+      ++v;
+      const float dmx = gd.a.x, dmy = gd.a.y, dop = gd.a.z, ddepth = gd.a.w;
+      const float dca = gd.b.x, dcb = gd.b.y, dcc = gd.b.z;
+      float drgb[3] = {gd.b.w, gd.c.x, gd.c.y};
+      dabs[0] += gd.c.z;
+      dabs[1] += gd.c.w;
+      // colour: rgb = max(0, sum_k sh_k Y_k(dir) + 0.5)
+      float rgb[3], dir[3], dn, Y[16];
+      bool cl[3];
+      eval_color<ST>(A, g, G, cam, rgb, dir, dn, Y, cl);
+      float wY[16];
+      for (int ch = 0; ch < 3; ++ch)
+        if (cl[ch]) drgb[ch] = 0.f;
+      for (int k = 0; k < nb; ++k) {
+        dsh[3 * k + 0] += Y[k] * drgb[0];
+        dsh[3 * k + 1] += Y[k] * drgb[1];
+        dsh[3 * k + 2] += Y[k] * drgb[2];
+        wY[k] = ldf(sh, 3 * k) * drgb[0] + ldf(sh, 3 * k + 1) * drgb[1] + ldf(sh, 3 * k + 2) * drgb[2];
+      }
+      float gx, gy, gz;
+      sh_basis_grad(A.deg, dir[0], dir[1], dir[2], wY, gx, gy, gz);
+      const float proj = gx * dir[0] + gy * dir[1] + gz * dir[2];
+      const float idn = 1.f / dn;
+      dm[0] += (gx - dir[0] * proj) * idn;
+      dm[1] += (gy - dir[1] * proj) * idn;
+      dm[2] += (gz - dir[2] * proj) * idn;
+      // conic = inverse of the dilated Sigma2D: dSigma2D = -M G M
+      const float g00 = dca, g01 = 0.5f * dcb, g11 = dcc;
+      const float mg00 = P.ca * g00 + P.cb * g01, mg01 = P.ca * g01 + P.cb * g11;
+      const float mg10 = P.cb * g00 + P.cc * g01, mg11 = P.cb * g01 + P.cc * g11;
+      float da = -(mg00 * P.ca + mg01 * P.cb);
+      float db = -2.f * (mg00 * P.cb + mg01 * P.cc);
+      float dc = -(mg10 * P.cb + mg11 * P.cc);
+      // opacity' = opacity * sqrt(det_raw / det)
+      dopac += dop * P.comp;
+      if (aa && P.comp > 0.f) {
+        const float ratio = P.comp * P.comp;
+        const float dratio = dop * G.opac * 0.5f / P.comp;
+        const float ddr = dratio * P.idet;          // d det_raw
+        const float ddt = -dratio * ratio * P.idet; // d det
+        const float a = P.ar + eps, cc = P.cr + eps;
+        da += ddr * P.cr + ddt * cc;
+        dc += ddr * P.ar + ddt * a;
+        db += -2.f * P.br * (ddr + ddt);
+      }
+      // Sigma2D_raw = T Sigma T^T with T = J W
+      float dT0[3], dT1[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        dT0[k] = 2.f * da * P.ST0[k] + db * P.ST1[k];
+        dT1[k] = db * P.ST0[k] + 2.f * dc * P.ST1[k];
+      }
+      // dSigma (symmetrised) = 2 da T0 T0^T + db (T0 T1^T + T1 T0^T) + 2 dc T1 T1^T, then
+      // Sigma = M M^T: dM = dSigma_sym M.
+      float dS[9];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          dS[r * 3 + q] = 2.f * da * P.T0[r] * P.T0[q] + db * (P.T0[r] * P.T1[q] + P.T1[r] * P.T0[q]) +
+                          2.f * dc * P.T1[r] * P.T1[q];
+      float Mx[9];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) Mx[r * 3 + q] = G.R[r * 3 + q] * G.s[q];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const float dM = dS[r * 3 + 0] * Mx[0 * 3 + q] + dS[r * 3 + 1] * Mx[1 * 3 + q] + dS[r * 3 + 2] * Mx[2 * 3 + q];
+          dR[r * 3 + q] += dM * G.s[q];
+          ds[q] += dM * G.R[r * 3 + q];
+        }
+      // T = J W: dJ
+      const float* W = cam.R;
+      const float dJ00 = dT0[0] * W[0] + dT0[1] * W[1] + dT0[2] * W[2];
+      const float dJ02 = dT0[0] * W[6] + dT0[1] * W[7] + dT0[2] * W[8];
+      const float dJ11 = dT1[0] * W[3] + dT1[1] * W[4] + dT1[2] * W[5];
+      const float dJ12 = dT1[0] * W[6] + dT1[1] * W[7] + dT1[2] * W[8];
+      const float uc = fminf(fmaxf(P.u, -cam.limx), cam.limx);
+      const float wc = fminf(fmaxf(P.w, -cam.limy), cam.limy);
+      const float iz2 = P.iz * P.iz;
+      float dt[3] = {0.f, 0.f, 0.f};
+      dt[2] += -cam.fx * iz2 * dJ00 + cam.fx * uc * iz2 * dJ02 - cam.fy * iz2 * dJ11 + cam.fy * wc * iz2 * dJ12;
+      const float duc = -cam.fx * P.iz * dJ02, dwc = -cam.fy * P.iz * dJ12;
+      if (!P.clx) { dt[0] += duc * P.iz; dt[2] -= duc * P.u * P.iz; }
+      if (!P.cly) { dt[1] += dwc * P.iz; dt[2] -= dwc * P.w * P.iz; }
+      // mean2d = (fx X/Z + cx, fy Y/Z + cy); depth = Z
+      dt[0] += cam.fx * P.iz * dmx;
+      dt[1] += cam.fy * P.iz * dmy;
+      dt[2] += -cam.fx * P.t[0] * iz2 * dmx - cam.fy * P.t[1] * iz2 * dmy + ddepth;
+      // t = W mu + t_cam
+      dm[0] += W[0] * dt[0] + W[3] * dt[1] + W[6] * dt[2];
+      dm[1] += W[1] * dt[0] + W[4] * dt[1] + W[7] * dt[2];
+      dm[2] += W[2] * dt[0] + W[5] * dt[1] + W[8] * dt[2];
+    }
+    // rotation from the normalised quaternion, then through the normalisation
+    const float w = G.q[0], x = G.q[1], y = G.q[2], z = G.q[3];
+    float dqn[4];
+    dqn[0] = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+    dqn[1] = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
+                    2.f * x * dR[8]);
+    dqn[2] = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] -
+                    2.f * y * dR[8]);
+    dqn[3] = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
+                    x * dR[6] + y * dR[7]);
+    const float qd = w * dqn[0] + x * dqn[1] + y * dqn[2] + z * dqn[3];
+    for (int k = 0; k < 4; ++k) dq[k] = (dqn[k] - G.q[k] * qd) * G.qinv;
+  }
+  for (int k = 0; k < 3; ++k) out.means[3 * g + k] = dm[k];
+  for (int k = 0; k < 3; ++k) out.scales[3 * g + k] = ds[k];
+  for (int k = 0; k < 4; ++k) out.quats[4 * g + k] = dq[k];
+  out.opac[g] = dopac;
+  float* gsh = out.sh + g * KC;
+  for (int k = 0; k < KC; ++k) gsh[k] = k < 48 ? dsh[k] : 0.f;
+  if (out.absgrad) {
+    out.absgrad[2 * g] = dabs[0];
+    out.absgrad[2 * g + 1] = dabs[1];
+  }
+}
+
+template <typename AT, typename ST>
+void launch_fwd_t(const GaussArgs& g, const CamBatch& cams, float eps, int aa, const PreOut& out, int blocks,
+                  cudaStream_t s) {
+  preprocess_fwd_kernel<AT, ST><<<blocks, 256, 0, s>>>(g, cams, eps, aa, out);
+}
+
+template <typename AT, typename ST>
+void launch_bwd_t(const GaussArgs& g, const CamBatch& cams, float eps, int aa, const uint32_t* vb,
+                  const uint32_t* vm, const Grad2D* g2d, const ParamGrads& out, cudaStream_t s) {
+  const int blocks = static_cast<int>((g.n_render + 127) / 128);
+  if (blocks > 0) preprocess_bwd_kernel<AT, ST><<<blocks, 128, 0, s>>>(g, cams, eps, aa, vb, vm, g2d, out);
+}
+
+}  // namespace
+
+void launch_preprocess_fwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased,
+                           const PreOut& out, int blocks, cudaStream_t s) {
+  if (blocks <= 0) return;
+#define GSR_PRE(AT, ST) launch_fwd_t<AT, ST>(g, cams, eps2d, antialiased, out, blocks, s)
+  if (g.attr_dtype == 0 && g.sh_dtype == 0) GSR_PRE(float, float);
+  else if (g.attr_dtype == 0 && g.sh_dtype == 1) GSR_PRE(float, __half);
+  else if (g.attr_dtype == 0 && g.sh_dtype == 2) GSR_PRE(float, __nv_bfloat16);
+  else if (g.attr_dtype == 1 && g.sh_dtype == 1) GSR_PRE(__half, __half);
+  else if (g.attr_dtype == 2 && g.sh_dtype == 2) GSR_PRE(__nv_bfloat16, __nv_bfloat16);
+  else if (g.attr_dtype == 1 && g.sh_dtype == 0) GSR_PRE(__half, float);
+  else if (g.attr_dtype == 2 && g.sh_dtype == 0) GSR_PRE(__nv_bfloat16, float);
+  else if (g.attr_dtype == 1 && g.sh_dtype == 2) GSR_PRE(__half, __nv_bfloat16);
+  else GSR_PRE(__nv_bfloat16, __half);
+#undef GSR_PRE
+}
+
+void launch_preprocess_bwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased,
+                           const Rec* /*rec*/, const uint32_t* vis_base, const uint32_t* vis_mask,
+                           const Grad2D* g2d, const ParamGrads& out, cudaStream_t s) {
+#define GSR_PREB(AT, ST) launch_bwd_t<AT, ST>(g, cams, eps2d, antialiased, vis_base, vis_mask, g2d, out, s)
+  if (g.attr_dtype == 0 && g.sh_dtype == 0) GSR_PREB(float, float);
+  else if (g.attr_dtype == 0 && g.sh_dtype == 1) GSR_PREB(float, __half);
+  else if (g.attr_dtype == 0 && g.sh_dtype == 2) GSR_PREB(float, __nv_bfloat16);
+  else if (g.attr_dtype == 1 && g.sh_dtype == 1) GSR_PREB(__half, __half);
+  else if (g.attr_dtype == 2 && g.sh_dtype == 2) GSR_PREB(__nv_bfloat16, __nv_bfloat16);
+  else if (g.attr_dtype == 1 && g.sh_dtype == 0) GSR_PREB(__half, float);
+  else if (g.attr_dtype == 2 && g.sh_dtype == 0) GSR_PREB(__nv_bfloat16, float);
+  else if (g.attr_dtype == 1 && g.sh_dtype == 2) GSR_PREB(__half, __nv_bfloat16);
+  else GSR_PREB(__nv_bfloat16, __half);
+#undef GSR_PREB
+}
+
+}  // namespace gsr

@@ -1,0 +1,460 @@
+// Tile binning and the per-tile alpha blending of Sec. 3.1, Eq. 2, forward and backward.
+//
+//   duplicate:  every visible record, in depth order, emits one (tile, record) pair per tile of
+//               its 3-sigma rectangle, minus the tiles StopThePop culling drops (Sec. 3.4.2);
+//               a warp expands 32 records together, so one huge ground splat does not stall
+//               its neighbours.
+//   ranges:     [start, end) of each tile in the tile-sorted pair list.
+//   blend fwd:  one 16x16 CTA per tile; records are staged in shared memory 256 at a time;
+//               each pixel blends front to back and stops at T < 1e-4; the CTA stops loading
+//               once every pixel is done.
+//   blend bwd:  same tiling, contributors walked back to front recovering T_i = T_{i+1}/(1-a_i);
+//               per-Gaussian gradients are summed over the warp with shuffles, over the CTA in
+//               shared memory, and added to global memory once per (tile, Gaussian).
+#include "gsr_internal.cuh"
+
+namespace gsr {
+namespace {
+
+__device__ __forceinline__ int find_cam(const CamBatch& cams, int t) {
+  int c = 0;
+  while (c + 1 < cams.C && t >= cams.cam[c + 1].tile_off) ++c;
+  return c;
+}
+
+// Smallest Mahalanobis distance (p - m)^T Q (p - m) over the rectangle of pixel centres of a tile.
+__device__ __forceinline__ float tile_min_maha(float mx, float my, float a, float b, float c, float xlo,
+                                               float xhi, float ylo, float yhi) {
+  if (mx >= xlo && mx <= xhi && my >= ylo && my <= yhi) return 0.f;
+  float best = INFINITY;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const float dx = (e ? xhi : xlo) - mx;
+    const float dy = fminf(fmaxf(-b * dx / c, ylo - my), yhi - my);
+    best = fminf(best, a * dx * dx + 2.f * b * dx * dy + c * dy * dy);
+  }
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const float dy = (e ? yhi : ylo) - my;
+    const float dx = fminf(fmaxf(-b * dy / a, xlo - mx), xhi - mx);
+    best = fminf(best, a * dx * dx + 2.f * b * dx * dy + c * dy * dy);
+  }
+  return best;
+}
+
+template <bool kCull, bool kCount>
+__global__ void __launch_bounds__(256) duplicate_kernel(const Rec* __restrict__ rec, const uint32_t* __restrict__ order,
+                                                        const uint32_t* __restrict__ offsets, const uint32_t* d_n,
+                                                        long long max_n, CamBatch cams, uint32_t* __restrict__ cnt_sorted,
+                                                        uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals) {
+  __shared__ uint32_t s_cnt[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  long long n = static_cast<long long>(*d_n);
+  if (n > max_n) n = max_n;
+  const long long base_i = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) & ~31ll;
+  if (base_i >= n) return;  // warp-uniform
+  const long long i = base_i + lane;
+  const bool valid = i < n;
+  uint32_t v = 0, off = 0, area = 0, lo = 0, hi = 0;
+  float4 ra = make_float4(0, 0, 0, 0), rb = ra;
+  if (valid) {
+    v = order[i];
+    const Rec r = rec[v];
+    ra = r.a;
+    rb = r.b;
+    lo = __float_as_uint(r.c.z);
+    hi = __float_as_uint(r.c.w);
+    area = ((lo >> 16) - (lo & 0xffffu)) * (((hi >> 16) & 0x7ffu) - (hi & 0xffffu));
+    if (!kCount) off = offsets[i];
+  }
+  uint32_t incl = area;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  s_cnt[w][lane] = 0;
+  __syncwarp();
+  for (uint32_t r0 = 0; r0 < total; r0 += 32) {
+    const uint32_t k = r0 + lane;
+    const bool active = k < total;
+    int owner = 0;
+#pragma unroll
+    for (int b = 16; b > 0; b >>= 1) {
+      const uint32_t probe = __shfl_sync(0xffffffffu, incl, owner + b - 1);
+      if (probe <= k) owner += b;
+    }
+    owner = min(owner, 31);
+    const uint32_t o_incl = __shfl_sync(0xffffffffu, incl, owner);
+    const uint32_t o_area = __shfl_sync(0xffffffffu, area, owner);
+    const uint32_t o_lo = __shfl_sync(0xffffffffu, lo, owner);
+    const uint32_t o_hi = __shfl_sync(0xffffffffu, hi, owner);
+    const uint32_t o_v = __shfl_sync(0xffffffffu, v, owner);
+    const uint32_t o_off = __shfl_sync(0xffffffffu, off, owner);
+    const uint32_t q = k - (o_incl - o_area);
+    const uint32_t x0 = o_lo & 0xffffu, wdt = (o_lo >> 16) - x0;
+    const uint32_t y0 = o_hi & 0xffffu;
+    const int c = static_cast<int>(o_hi >> 27);
+    const uint32_t tx = active ? x0 + q % max(wdt, 1u) : 0;
+    const uint32_t ty = active ? y0 + q / max(wdt, 1u) : 0;
+    bool keep = active;
+    if (kCull) {
+      const float mx = __shfl_sync(0xffffffffu, ra.x, owner), my = __shfl_sync(0xffffffffu, ra.y, owner);
+      const float op = __shfl_sync(0xffffffffu, ra.z, owner);
+      const float ca = __shfl_sync(0xffffffffu, rb.x, owner), cb = __shfl_sync(0xffffffffu, rb.y, owner);
+      const float cc = __shfl_sync(0xffffffffu, rb.z, owner);
+      if (active) {
+        const DevCam& cam = cams.cam[c];
+        const float xlo = tx * kTile + 0.5f, xhi = fminf(static_cast<float>((tx + 1) * kTile), cam.W) - 0.5f;
+        const float ylo = ty * kTile + 0.5f, yhi = fminf(static_cast<float>((ty + 1) * kTile), cam.H) - 0.5f;
+        const float d2 = tile_min_maha(mx, my, ca, cb, cc, xlo, xhi, ylo, yhi);
+        keep = op > 0.f && 0.5f * d2 <= logf(op * 255.f);
+      }
+      const uint32_t kb = __ballot_sync(0xffffffffu, keep);
+      const uint32_t group = __match_any_sync(0xffffffffu, active ? static_cast<uint32_t>(owner) : 64u);
+      const uint32_t before = __popc(kb & group & ((1u << lane) - 1));
+      const uint32_t base_cnt = s_cnt[w][owner];
+      __syncwarp();
+      if (!kCount && keep) {
+        const uint32_t pos = o_off + base_cnt + before;
+        const DevCam& cam = cams.cam[c];
+        pkeys[pos] = static_cast<uint32_t>(cam.tile_off) + ty * cam.tiles_x + tx;
+        pvals[pos] = o_v;
+      }
+      if (active && lane == 31 - __clz(group)) s_cnt[w][owner] = base_cnt + __popc(kb & group);
+      __syncwarp();
+    } else if (active) {
+      const DevCam& cam = cams.cam[c];
+      const uint32_t pos = o_off + q;
+      pkeys[pos] = static_cast<uint32_t>(cam.tile_off) + ty * cam.tiles_x + tx;
+      pvals[pos] = o_v;
+    }
+  }
+  if (kCount && valid) cnt_sorted[i] = s_cnt[w][lane];
+}
+
+__global__ void ranges_kernel(const uint32_t* __restrict__ keys, long long P, uint2* __restrict__ ranges) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const uint32_t t = keys[i];
+  if (i == 0 || keys[i - 1] != t) ranges[t].x = static_cast<uint32_t>(i);
+  if (i == P - 1 || keys[i + 1] != t) ranges[t].y = static_cast<uint32_t>(i + 1);
+}
+
+__global__ void __launch_bounds__(kTilePix) blend_fwd_kernel(const Rec* __restrict__ rec,
+                                                             const uint32_t* __restrict__ pvals,
+                                                             const uint2* __restrict__ ranges, CamBatch cams,
+                                                             float3 bg, BlendFwdOut out,
+                                                             unsigned long long* counters) {
+  __shared__ float4 sA[kTilePix];
+  __shared__ float4 sB[kTilePix];
+  __shared__ float2 sC[kTilePix];
+  const int t = blockIdx.x;
+  const int c = find_cam(cams, t);
+  const DevCam& cam = cams.cam[c];
+  const int lt = t - cam.tile_off;
+  const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+  const int tid = threadIdx.x;
+  const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + (tid >> 4);
+  const bool inside = px < cam.W && py < cam.H;
+  const float fx = px + 0.5f, fy = py + 0.5f;
+  const uint2 range = ranges[t];
+  const int n = static_cast<int>(range.y - range.x);
+  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
+  uint32_t last = 0;
+  uint32_t n_eval = 0, n_blend = 0;
+  bool done = !inside;
+  for (int base = 0; base < n; base += kTilePix) {
+    if (__syncthreads_count(done) == kTilePix) break;
+    const int idx = base + tid;
+    if (idx < n) {
+      const Rec r = rec[pvals[range.x + idx]];
+      sA[tid] = r.a;
+      sB[tid] = r.b;
+      sC[tid] = make_float2(r.c.x, r.c.y);
+    }
+    __syncthreads();
+    const int cnt = min(kTilePix, n - base);
+    for (int j = 0; j < cnt && !done; ++j) {
+      const float4 a = sA[j];
+      const float4 b = sB[j];
+      ++n_eval;
+      const float dx = a.x - fx, dy = a.y - fy;
+      const float sigma = 0.5f * (b.x * dx * dx + b.z * dy * dy) + b.y * dx * dy;
+      if (sigma < 0.f) continue;
+      const float alpha = fminf(kAlphaMax, a.z * __expf(-sigma));
+      if (alpha < kAlphaMin) continue;
+      const float Tn = T * (1.f - alpha);
+      if (Tn < kTMin) {
+        done = true;
+        break;
+      }
+      const float wgt = alpha * T;
+      const float2 cc = sC[j];
+      C0 = fmaf(b.w, wgt, C0);
+      C1 = fmaf(cc.x, wgt, C1);
+      C2 = fmaf(cc.y, wgt, C2);
+      D = fmaf(a.w, wgt, D);
+      T = Tn;
+      last = static_cast<uint32_t>(base + j + 1);
+      ++n_blend;
+    }
+  }
+  if (counters) {
+    unsigned long long e = n_eval, b = n_blend;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      e += __shfl_xor_sync(0xffffffffu, e, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((tid & 31) == 0) {
+      atomicAdd(counters + 0, e);
+      atomicAdd(counters + 1, b);
+    }
+  }
+  if (!inside) return;
+  const long long pix = cam.pix_off + static_cast<long long>(py) * cam.W + px;
+  float r0, r1, r2;
+  if (cam.aff) {
+    const float* A = cam.aff;
+    const float o = 1.f - T;
+    r0 = A[0] * C0 + A[1] * C1 + A[2] * C2 + A[3] * o;
+    r1 = A[4] * C0 + A[5] * C1 + A[6] * C2 + A[7] * o;
+    r2 = A[8] * C0 + A[9] * C1 + A[10] * C2 + A[11] * o;
+  } else {
+    r0 = C0; r1 = C1; r2 = C2;
+  }
+  out.rgb[3 * pix + 0] = r0 + T * bg.x;
+  out.rgb[3 * pix + 1] = r1 + T * bg.y;
+  out.rgb[3 * pix + 2] = r2 + T * bg.z;
+  const float al = 1.f - T;
+  if (out.depth_acc) out.depth_acc[pix] = D;
+  if (out.depth_exp) out.depth_exp[pix] = D / fmaxf(al, 1e-10f);
+  if (out.alpha) out.alpha[pix] = al;
+  if (out.T_final) out.T_final[pix] = T;
+  if (out.n_contrib) out.n_contrib[pix] = last;
+  if (out.D_state) out.D_state[pix] = D;
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+constexpr int kGradVals = 12;
+
+__global__ void __launch_bounds__(kTilePix) blend_bwd_kernel(const Rec* __restrict__ rec,
+                                                             const uint32_t* __restrict__ pvals,
+                                                             const uint2* __restrict__ ranges, CamBatch cams,
+                                                             float3 bg, BlendBwdIn in, Grad2D* __restrict__ g2d,
+                                                             float* __restrict__ g_aff, int absgrad,
+                                                             unsigned long long* counters) {
+  __shared__ float4 sA[kTilePix];
+  __shared__ float4 sB[kTilePix];
+  __shared__ float2 sC[kTilePix];
+  __shared__ uint32_t sV[kTilePix];
+  __shared__ float sAcc[kTilePix][kGradVals + 1];
+  __shared__ uint32_t s_max;
+  __shared__ float s_aff[8][12];
+  const int t = blockIdx.x;
+  const int c = find_cam(cams, t);
+  const DevCam& cam = cams.cam[c];
+  const int lt = t - cam.tile_off;
+  const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + (tid >> 4);
+  const bool inside = px < cam.W && py < cam.H;
+  const float fx = px + 0.5f, fy = py + 0.5f;
+  const uint2 range = ranges[t];
+  if (tid == 0) s_max = 0;
+  __syncthreads();
+  float Tf = 1.f, D = 0.f;
+  uint32_t last = 0;
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f, gda = 0.f, gde = 0.f, gal = 0.f;
+  long long pix = 0;
+  if (inside) {
+    pix = cam.pix_off + static_cast<long long>(py) * cam.W + px;
+    Tf = in.T_final[pix];
+    last = in.n_contrib[pix];
+    D = in.D_state[pix];
+    if (in.d_rgb) { g0 = in.d_rgb[3 * pix]; g1 = in.d_rgb[3 * pix + 1]; g2 = in.d_rgb[3 * pix + 2]; }
+    if (in.d_depth_acc) gda = in.d_depth_acc[pix];
+    if (in.d_depth_exp) gde = in.d_depth_exp[pix];
+    if (in.d_alpha) gal = in.d_alpha[pix];
+    atomicMax(&s_max, last);
+  }
+  // upstream gradients of C = sum c a T, D = sum z a T and T_final
+  const float* A = cam.aff;
+  float GC0 = g0, GC1 = g1, GC2 = g2, bb0 = 0.f, bb1 = 0.f, bb2 = 0.f;
+  if (A) {
+    GC0 = A[0] * g0 + A[4] * g1 + A[8] * g2;
+    GC1 = A[1] * g0 + A[5] * g1 + A[9] * g2;
+    GC2 = A[2] * g0 + A[6] * g1 + A[10] * g2;
+    bb0 = A[3]; bb1 = A[7]; bb2 = A[11];
+  }
+  const float aout = 1.f - Tf;
+  const float GD = gda + gde / fmaxf(aout, 1e-10f);
+  const float ga_eff = gal + (aout > 1e-10f ? -gde * D / (aout * aout) : 0.f);
+  const float GT = g0 * (bg.x - bb0) + g1 * (bg.y - bb1) + g2 * (bg.z - bb2) - ga_eff;
+  __syncthreads();
+  const int n = static_cast<int>(s_max);
+  float T = Tf;
+  float S0 = 0.f, S1 = 0.f, S2 = 0.f, SD = 0.f;
+  uint32_t n_visit = 0, n_contrib = 0;
+  for (int base = 0; base < n; base += kTilePix) {
+    __syncthreads();
+    if (base + tid < n) {
+      const uint32_t pos = range.x + static_cast<uint32_t>(n - 1 - base - tid);
+      const uint32_t v = pvals[pos];
+      const Rec r = rec[v];
+      sA[tid] = r.a;
+      sB[tid] = r.b;
+      sC[tid] = make_float2(r.c.x, r.c.y);
+      sV[tid] = v;
+    }
+#pragma unroll
+    for (int k = 0; k < kGradVals; ++k) sAcc[tid][k] = 0.f;
+    __syncthreads();
+    const int cnt = min(kTilePix, n - base);
+    for (int j = 0; j < cnt; ++j) {
+      const uint32_t pos = static_cast<uint32_t>(n - 1 - base - j);
+      float gv[kGradVals];
+#pragma unroll
+      for (int k = 0; k < kGradVals; ++k) gv[k] = 0.f;
+      bool contrib = false;
+      if (inside && pos < last) {
+        ++n_visit;
+        const float4 a = sA[j];
+        const float4 b = sB[j];
+        const float dx = a.x - fx, dy = a.y - fy;
+        const float sigma = 0.5f * (b.x * dx * dx + b.z * dy * dy) + b.y * dx * dy;
+        if (sigma >= 0.f) {
+          const float G = __expf(-sigma);
+          const float araw = a.z * G;
+          const float alpha = fminf(kAlphaMax, araw);
+          if (alpha >= kAlphaMin) {
+            contrib = true;
+            ++n_contrib;
+            const float om = 1.f - alpha;
+            const float Ti = T / om;
+            const float2 cc = sC[j];
+            const float wgt = alpha * Ti;
+            const float dal = Ti * (GC0 * b.w + GC1 * cc.x + GC2 * cc.y + GD * a.w) -
+                              (GC0 * S0 + GC1 * S1 + GC2 * S2 + GD * SD + GT * Tf) / om;
+            S0 = fmaf(b.w, wgt, S0);
+            S1 = fmaf(cc.x, wgt, S1);
+            S2 = fmaf(cc.y, wgt, S2);
+            SD = fmaf(a.w, wgt, SD);
+            T = Ti;
+            const float draw = araw > kAlphaMax ? 0.f : dal;
+            const float dsig = -draw * araw;
+            gv[0] = (b.x * dx + b.y * dy) * dsig;
+            gv[1] = (b.y * dx + b.z * dy) * dsig;
+            gv[2] = draw * G;
+            gv[3] = GD * wgt;
+            gv[4] = 0.5f * dx * dx * dsig;
+            gv[5] = dx * dy * dsig;
+            gv[6] = 0.5f * dy * dy * dsig;
+            gv[7] = GC0 * wgt;
+            gv[8] = GC1 * wgt;
+            gv[9] = GC2 * wgt;
+            gv[10] = fabsf(gv[0]);
+            gv[11] = fabsf(gv[1]);
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+        for (int k = 0; k < kGradVals; ++k)
+          if (k < kGradVals - 2 || absgrad) gv[k] = warp_sum(gv[k]);
+        if (lane == 0) {
+#pragma unroll
+          for (int k = 0; k < kGradVals; ++k)
+            if (k < kGradVals - 2 || absgrad) atomicAdd(&sAcc[j][k], gv[k]);
+        }
+      }
+    }
+    __syncthreads();
+    if (tid < cnt) {
+      Grad2D* dst = g2d + sV[tid];
+      float* f = reinterpret_cast<float*>(dst);
+      const int nv = absgrad ? kGradVals : kGradVals - 2;
+      for (int k = 0; k < nv; ++k) {
+        const float val = sAcc[tid][k];
+        if (val != 0.f) atomicAdd(f + k, val);
+      }
+    }
+  }
+  if (counters) {
+    unsigned long long e = n_visit, b = n_contrib;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      e += __shfl_xor_sync(0xffffffffu, e, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      atomicAdd(counters + 2, e);
+      atomicAdd(counters + 3, b);
+    }
+  }
+  if (g_aff) {
+    // dA = g C^T, db = g (1 - T_final), per pixel, summed over the tile
+    float a12[12] = {g0 * S0, g0 * S1, g0 * S2, g0 * aout, g1 * S0, g1 * S1, g1 * S2, g1 * aout,
+                     g2 * S0, g2 * S1, g2 * S2, g2 * aout};
+    if (!inside)
+      for (int k = 0; k < 12; ++k) a12[k] = 0.f;
+    for (int k = 0; k < 12; ++k) {
+      const float s = warp_sum(a12[k]);
+      if (lane == 0) s_aff[wid][k] = s;
+    }
+    __syncthreads();
+    if (tid < 12) {
+      float s = 0.f;
+      for (int k = 0; k < 8; ++k) s += s_aff[k][tid];
+      if (s != 0.f) atomicAdd(g_aff + 12 * c + tid, s);
+    }
+  }
+}
+
+}  // namespace
+
+void launch_duplicate(const Rec* rec, const uint32_t* order, const uint32_t* offsets, const uint32_t* d_n,
+                      long long max_n, const CamBatch& cams, int tile_cull, uint32_t* cnt_sorted,
+                      uint32_t* pair_keys, uint32_t* pair_vals, cudaStream_t s) {
+  if (max_n <= 0) return;
+  const int blocks = static_cast<int>((max_n + 255) / 256);
+  if (cnt_sorted) {
+    duplicate_kernel<true, true><<<blocks, 256, 0, s>>>(rec, order, offsets, d_n, max_n, cams, cnt_sorted, nullptr,
+                                                        nullptr);
+  } else if (tile_cull) {
+    duplicate_kernel<true, false><<<blocks, 256, 0, s>>>(rec, order, offsets, d_n, max_n, cams, nullptr, pair_keys,
+                                                         pair_vals);
+  } else {
+    duplicate_kernel<false, false><<<blocks, 256, 0, s>>>(rec, order, offsets, d_n, max_n, cams, nullptr, pair_keys,
+                                                          pair_vals);
+  }
+}
+
+void launch_ranges(const uint32_t* sorted_keys, long long P, uint2* ranges, cudaStream_t s) {
+  if (P <= 0) return;
+  ranges_kernel<<<static_cast<int>((P + 255) / 256), 256, 0, s>>>(sorted_keys, P, ranges);
+}
+
+void launch_blend_fwd(const Rec* rec, const uint32_t* pair_vals, const uint2* ranges, const CamBatch& cams,
+                      const float* bg, const BlendFwdOut& out, unsigned long long* counters, cudaStream_t s) {
+  if (cams.total_tiles <= 0) return;
+  blend_fwd_kernel<<<cams.total_tiles, kTilePix, 0, s>>>(rec, pair_vals, ranges, cams, make_float3(bg[0], bg[1], bg[2]),
+                                                         out, counters);
+}
+
+void launch_blend_bwd(const Rec* rec, const uint32_t* pair_vals, const uint2* ranges, const CamBatch& cams,
+                      const float* bg, const BlendBwdIn& in, Grad2D* g2d, float* g_aff, int absgrad,
+                      unsigned long long* counters, cudaStream_t s) {
+  if (cams.total_tiles <= 0) return;
+  blend_bwd_kernel<<<cams.total_tiles, kTilePix, 0, s>>>(rec, pair_vals, ranges, cams, make_float3(bg[0], bg[1], bg[2]),
+                                                         in, g2d, g_aff, absgrad, counters);
+}
+
+}  // namespace gsr

@@ -1,0 +1,244 @@
+// Onesweep LSD radix sort (Adinets & Merrill 2022) of uint32 (key, value) pairs, and the
+// chained exclusive scan that turns per-record tile counts into pair offsets.
+//
+// The sort orders the binned (tile, Gaussian) pairs (the "tile-based" rasterizer of Sec. 3.4.2
+// and 3.1): first the visible records by depth, then the pairs stably by tile, which together
+// give the (tile, depth, index) order of the blend. Each pass reads every key once: a block
+// ranks its 4096 keys by the pass's 8-bit digit with warp match-any (stable), publishes its
+// per-digit counts, and takes its global digit offsets from its predecessors by a decoupled
+// look-back whose waits are bounded (a wait that runs out sets an error bit and the block
+// carries on, so the kernel always finishes). Blocks take their tile index from an atomic
+// counter at start, so a block only ever waits for blocks that are already running.
+#include <algorithm>
+
+#include "gsr_internal.cuh"
+#include "scan_util.cuh"
+
+namespace gsr {
+namespace {
+
+constexpr uint32_t kFlagA = 1u << 30;
+constexpr uint32_t kFlagP = 2u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1;
+
+__device__ __forceinline__ long long device_n(const uint32_t* d_n, long long max_n) {
+  if (!d_n) return max_n;
+  const long long n = static_cast<long long>(*d_n);
+  return n < max_n ? n : max_n;
+}
+
+__global__ void __launch_bounds__(256) hist_kernel(const uint32_t* __restrict__ keys, const uint32_t* d_n,
+                                                   long long max_n, int begin_bit, int end_bit, int passes,
+                                                   uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[4 * 256];
+  for (int k = threadIdx.x; k < 4 * 256; k += blockDim.x) sh[k] = 0;
+  __syncthreads();
+  const long long n = device_n(d_n, max_n);
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const uint32_t k = keys[i];
+    for (int p = 0; p < passes; ++p) {
+      const int shift = begin_bit + 8 * p;
+      const int width = min(8, end_bit - shift);
+      atomicAdd(&sh[p * 256 + ((k >> shift) & ((1u << width) - 1))], 1u);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < passes * 256; k += blockDim.x)
+    if (sh[k]) atomicAdd(&hist[k], sh[k]);
+}
+
+// Exclusive scan of each pass's 256 digit counts, in place.
+__global__ void __launch_bounds__(256) hist_scan_kernel(uint32_t* hist) {
+  uint32_t* h = hist + blockIdx.x * 256;
+  const uint32_t x = h[threadIdx.x];
+  uint32_t total;
+  const uint32_t e = block_excl_scan(x, &total);
+  h[threadIdx.x] = e;
+}
+
+__device__ __forceinline__ uint32_t lookback_digit(uint32_t* status, uint32_t bid, int d, uint32_t agg, int* err) {
+  cuda::atomic_ref<uint32_t, cuda::thread_scope_device> me(status[static_cast<size_t>(bid) * 256 + d]);
+  if (bid == 0) {
+    me.store(kFlagP | agg, cuda::memory_order_relaxed);
+    return 0;
+  }
+  me.store(kFlagA | agg, cuda::memory_order_relaxed);
+  uint32_t excl = 0;
+  long long j = static_cast<long long>(bid) - 1;
+  unsigned spins = 0, ns = 32;
+  while (j >= 0) {
+    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> st(status[static_cast<size_t>(j) * 256 + d]);
+    const uint32_t s = st.load(cuda::memory_order_relaxed);
+    const uint32_t f = s >> 30;
+    if (f == 0) {
+      if (++spins > kSpinLimit) {
+        atomicOr(err, kErrTimeout);
+        break;
+      }
+      __nanosleep(ns);
+      if (ns < 1024) ns <<= 1;
+      continue;
+    }
+    excl += s & kValMask;
+    if (f == 2) break;
+    --j;
+  }
+  me.store(kFlagP | ((excl + agg) & kValMask), cuda::memory_order_relaxed);
+  return excl;
+}
+
+__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, const uint32_t* d_n, long long max_n, int shift, int width,
+    const uint32_t* __restrict__ offsets, uint32_t* status, uint32_t* counter, int* err) {
+  constexpr int kWarps = kSortThreads / 32;
+  __shared__ uint32_t s_hist[kWarps][256];
+  __shared__ uint32_t s_base[256];
+  __shared__ uint32_t s_bid;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int k = tid; k < kWarps * 256; k += kSortThreads) (&s_hist[0][0])[k] = 0;
+  if (tid == 0) s_bid = atomicAdd(counter, 1u);
+  __syncthreads();
+  const uint32_t bid = s_bid;
+  const long long n = device_n(d_n, max_n);
+  const long long start = static_cast<long long>(bid) * kSortTile;
+  if (start >= n) return;
+  const uint32_t dmask = (1u << width) - 1;
+  const long long wbase = start + static_cast<long long>(w) * (32 * kSortItems);
+  uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+#pragma unroll
+  for (int j = 0; j < kSortItems; ++j) {
+    const long long idx = wbase + j * 32 + lane;
+    const bool ok = idx < n;
+    key[j] = ok ? kin[idx] : 0u;
+    val[j] = ok ? vin[idx] : 0u;
+  }
+  const uint32_t lt = (1u << lane) - 1;
+#pragma unroll
+  for (int j = 0; j < kSortItems; ++j) {
+    const long long idx = wbase + j * 32 + lane;
+    const uint32_t d = idx < n ? ((key[j] >> shift) & dmask) : 256u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t pre = d < 256u ? s_hist[w][d] : 0u;
+    __syncwarp();
+    if (d < 256u && lane == __ffs(peers) - 1) s_hist[w][d] = pre + __popc(peers);
+    __syncwarp();
+    rank[j] = pre + __popc(peers & lt);
+  }
+  __syncthreads();
+  {
+    const int d = tid;  // one thread per digit (kSortThreads == 256)
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kWarps; ++k) {
+      const uint32_t c = s_hist[k][d];
+      s_hist[k][d] = sum;
+      sum += c;
+    }
+    const uint32_t excl = lookback_digit(status, bid, d, sum, err);
+    s_base[d] = offsets[d] + excl;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kSortItems; ++j) {
+    const long long idx = wbase + j * 32 + lane;
+    if (idx < n) {
+      const uint32_t d = (key[j] >> shift) & dmask;
+      const uint32_t pos = s_base[d] + s_hist[w][d] + rank[j];
+      kout[pos] = key[j];
+      vout[pos] = val[j];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) pair_scan_kernel(
+    const uint32_t* __restrict__ touched, const uint32_t* __restrict__ order, const uint32_t* __restrict__ cnt_sorted,
+    uint32_t* __restrict__ offsets, const uint32_t* d_n, long long max_n, unsigned long long* status,
+    uint32_t* counter, unsigned long long* p_total, int* err) {
+  __shared__ uint32_t s_bid;
+  __shared__ unsigned long long s_base;
+  if (threadIdx.x == 0) s_bid = atomicAdd(counter, 1u);
+  __syncthreads();
+  const uint32_t bid = s_bid;
+  const long long n = device_n(d_n, max_n);
+  if (bid == 0 && n == 0 && threadIdx.x == 0) *p_total = 0;
+  const long long start = static_cast<long long>(bid) * (kScanThreads * kScanItems);
+  if (start >= n) return;
+  uint32_t x[kScanItems];
+  uint32_t sum = 0;
+  const long long first = start + static_cast<long long>(threadIdx.x) * kScanItems;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const long long idx = first + k;
+    x[k] = 0;
+    if (idx < n) x[k] = cnt_sorted ? cnt_sorted[idx] : touched[order[idx]];
+    sum += x[k];
+  }
+  uint32_t total;
+  const uint32_t excl = block_excl_scan(sum, &total);
+  if (threadIdx.x == 0) s_base = chained_prefix(status, bid, total, err);
+  __syncthreads();
+  unsigned long long run = s_base + excl;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const long long idx = first + k;
+    if (idx < n) {
+      if (run > 0xffffffffull) atomicOr(err, kErrOverflow);
+      offsets[idx] = static_cast<uint32_t>(run);
+      if (idx == n - 1) *p_total = run + x[k];
+    }
+    run += x[k];
+  }
+}
+
+}  // namespace
+
+size_t sort_status_words(long long max_n) {
+  const long long blocks = (max_n + kSortTile - 1) / kSortTile;
+  return static_cast<size_t>(blocks) * 256;
+}
+
+void radix_sort_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
+                    const uint32_t* d_n, long long max_n, int begin_bit, int end_bit, const SortScratch& sc,
+                    int* err, cudaStream_t s) {
+  if (max_n <= 0 || end_bit <= begin_bit) return;
+  const int passes = (end_bit - begin_bit + 7) / 8;
+  const int blocks = static_cast<int>((max_n + kSortTile - 1) / kSortTile);
+  cudaMemsetAsync(sc.hist, 0, sizeof(uint32_t) * 256 * passes, s);
+  cudaMemsetAsync(sc.counters, 0, sizeof(uint32_t) * passes, s);
+  cudaMemsetAsync(sc.status, 0, sizeof(uint32_t) * 256 * static_cast<size_t>(blocks) * passes, s);
+  const int hblocks = static_cast<int>(std::min<long long>(2 * 152, (max_n + 4095) / 4096));
+  hist_kernel<<<hblocks, 256, 0, s>>>(keys_in, d_n, max_n, begin_bit, end_bit, passes, sc.hist);
+  hist_scan_kernel<<<passes, 256, 0, s>>>(sc.hist);
+  // ping-pong so that the last pass lands in keys_out; the inputs are never written
+  const uint32_t* ksrc = keys_in;
+  const uint32_t* vsrc = vals_in;
+  for (int p = 0; p < passes; ++p) {
+    const bool to_out = ((passes - 1 - p) % 2) == 0;
+    uint32_t* kdst = to_out ? keys_out : sc.keys_tmp;
+    uint32_t* vdst = to_out ? vals_out : sc.vals_tmp;
+    const int shift = begin_bit + 8 * p;
+    const int width = std::min(8, end_bit - shift);
+    onesweep_kernel<<<blocks, kSortThreads, 0, s>>>(ksrc, vsrc, kdst, vdst, d_n, max_n, shift, width,
+                                                    sc.hist + 256 * p,
+                                                    sc.status + static_cast<size_t>(256) * blocks * p,
+                                                    sc.counters + p, err);
+    ksrc = kdst;
+    vsrc = vdst;
+  }
+}
+
+void pair_offsets_scan(const uint32_t* touched, const uint32_t* order, const uint32_t* cnt_sorted,
+                       uint32_t* offsets, const uint32_t* d_n, long long max_n, unsigned long long* status,
+                       uint32_t* counter, unsigned long long* p_total, int* err, cudaStream_t s) {
+  const long long per = kScanThreads * kScanItems;
+  const int blocks = static_cast<int>(std::max<long long>(1, (max_n + per - 1) / per));
+  cudaMemsetAsync(status, 0, sizeof(unsigned long long) * blocks, s);
+  cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
+  cudaMemsetAsync(p_total, 0, sizeof(unsigned long long), s);
+  pair_scan_kernel<<<blocks, kScanThreads, 0, s>>>(touched, order, cnt_sorted, offsets, d_n, max_n, status, counter,
+                                                   p_total, err);
+}
+
+}  // namespace gsr

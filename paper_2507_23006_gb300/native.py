@@ -1,0 +1,423 @@
+"""Python binding of libgsr (include/gsr.h): argument marshalling only.
+
+Every step of rendering runs in the CUDA library; this module converts torch tensors and
+camera descriptions into the C structs, passes device pointers and the current CUDA stream,
+and raises on any non-OK status. There is no fallback: if libgsr.so cannot be loaded, every
+entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_lib = None
+_lock = threading.Lock()
+
+GSR_OK = 0
+GSR_WARN_OVER_BUDGET = 1
+STATUS_NAMES = {0: "ok", 1: "over budget", -1: "invalid argument", -2: "out of device memory",
+                -3: "CUDA error", -4: "device wait timed out", -5: "unsupported size"}
+
+DTYPES = {torch.float32: 0, torch.float16: 1, torch.bfloat16: 2}
+
+BUF_RECORDS, BUF_VIS_BASE, BUF_VIS_MASK, BUF_PAIR_VALS, BUF_RANGES, BUF_T_FINAL, BUF_N_CONTRIB, BUF_DEPTH_ACC = range(8)
+
+EXPORTED = [
+    "gsr_create", "gsr_destroy", "gsr_status_string", "gsr_last_error", "gsr_workspace_query",
+    "gsr_workspace_bytes", "gsr_render_forward", "gsr_render_backward", "gsr_state_release",
+    "gsr_state_get_info", "gsr_state_copy", "gsr_sync_check", "gsr_sort_pairs_u32", "gsr_select_lod",
+    "gsr_profile_enable", "gsr_profile_collect",
+]
+
+STAGES = ["preprocess", "depth_sort", "tile_count", "pair_scan", "readback", "duplicate", "tile_sort", "ranges",
+          "blend_fwd", "blend_bwd", "preprocess_bwd"]
+COUNTERS = ["fwd_evals", "fwd_contribs", "bwd_evals", "bwd_contribs"]
+
+
+class GsrError(RuntimeError):
+    def __init__(self, status: int, detail: str = ""):
+        super().__init__(f"gsr: {STATUS_NAMES.get(status, status)}" + (f": {detail}" if detail else ""))
+        self.status = status
+
+
+class Segment(ctypes.Structure):
+    _fields_ = [("begin", ctypes.c_int64), ("count", ctypes.c_int64)]
+
+
+class CGaussians(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("means", ctypes.c_void_p), ("scales", ctypes.c_void_p),
+                ("quats", ctypes.c_void_p), ("opacities", ctypes.c_void_p), ("sh", ctypes.c_void_p),
+                ("sh_coeffs", ctypes.c_int32), ("sh_degree", ctypes.c_int32), ("attr_dtype", ctypes.c_int32),
+                ("sh_dtype", ctypes.c_int32), ("segs", ctypes.POINTER(Segment)), ("nsegs", ctypes.c_int32)]
+
+
+class CCamera(ctypes.Structure):
+    _fields_ = [("viewmat", ctypes.c_float * 12), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("near_plane", ctypes.c_float), ("far_plane", ctypes.c_float),
+                ("appearance", ctypes.c_void_p)]
+
+
+class COpts(ctypes.Structure):
+    _fields_ = [("eps2d", ctypes.c_float), ("antialiased", ctypes.c_int32), ("tile_cull", ctypes.c_int32),
+                ("bg", ctypes.c_float * 3), ("save_state", ctypes.c_int32), ("absgrad", ctypes.c_int32)]
+
+
+class COutputs(ctypes.Structure):
+    _fields_ = [("rgb", ctypes.c_void_p), ("depth_acc", ctypes.c_void_p), ("depth_exp", ctypes.c_void_p),
+                ("alpha", ctypes.c_void_p)]
+
+
+class COutGrads(ctypes.Structure):
+    _fields_ = [("rgb", ctypes.c_void_p), ("depth_acc", ctypes.c_void_p), ("depth_exp", ctypes.c_void_p),
+                ("alpha", ctypes.c_void_p)]
+
+
+class CParamGrads(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacities", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("appearance", ctypes.c_void_p),
+                ("absgrad", ctypes.c_void_p)]
+
+
+class CStateInfo(ctypes.Structure):
+    _fields_ = [("n_render", ctypes.c_int64), ("n_cams", ctypes.c_int32), ("n_visible", ctypes.c_int64),
+                ("n_pairs", ctypes.c_int64), ("n_tiles", ctypes.c_int64), ("n_pixels", ctypes.c_int64)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libgsr.so (building it first if it is missing and a toolkit is present)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise OSError(f"libgsr.so not built ({path}); run paper_2507_23006_gb300.build.build()")
+            _build.build()
+        L = ctypes.CDLL(path)
+        vp = ctypes.c_void_p
+        L.gsr_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp]
+        L.gsr_destroy.argtypes = [vp]
+        L.gsr_destroy.restype = None
+        L.gsr_status_string.argtypes = [ctypes.c_int]
+        L.gsr_status_string.restype = ctypes.c_char_p
+        L.gsr_last_error.argtypes = [vp]
+        L.gsr_last_error.restype = ctypes.c_char_p
+        L.gsr_workspace_query.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(CCamera), ctypes.c_int32, ctypes.c_int64,
+                                          ctypes.POINTER(ctypes.c_size_t)]
+        L.gsr_workspace_bytes.argtypes = [vp]
+        L.gsr_workspace_bytes.restype = ctypes.c_size_t
+        L.gsr_render_forward.argtypes = [vp, ctypes.POINTER(CGaussians), ctypes.POINTER(CCamera), ctypes.c_int32,
+                                         ctypes.POINTER(COpts), ctypes.POINTER(COutputs), ctypes.POINTER(vp), vp]
+        L.gsr_render_backward.argtypes = [vp, ctypes.POINTER(CGaussians), ctypes.POINTER(CCamera), ctypes.c_int32,
+                                          ctypes.POINTER(COpts), vp, ctypes.POINTER(COutGrads),
+                                          ctypes.POINTER(CParamGrads), vp]
+        L.gsr_state_release.argtypes = [vp, vp]
+        L.gsr_state_release.restype = None
+        L.gsr_state_get_info.argtypes = [vp, ctypes.POINTER(CStateInfo)]
+        L.gsr_state_copy.argtypes = [vp, ctypes.c_int32, vp, ctypes.c_size_t, vp]
+        L.gsr_sync_check.argtypes = [vp, vp]
+        L.gsr_sort_pairs_u32.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, vp]
+        L.gsr_select_lod.argtypes = [ctypes.c_int32, vp, ctypes.c_int32, vp, ctypes.POINTER(CCamera), vp,
+                                     ctypes.c_int64, vp, ctypes.POINTER(Segment), ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_int64)]
+        L.gsr_profile_enable.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+        L.gsr_profile_collect.argtypes = [vp, vp, vp, vp]
+        for name in EXPORTED:
+            getattr(L, name)
+        for name in ("gsr_create", "gsr_workspace_query", "gsr_render_forward", "gsr_render_backward",
+                     "gsr_state_get_info", "gsr_state_copy", "gsr_sync_check", "gsr_sort_pairs_u32",
+                     "gsr_select_lod", "gsr_profile_enable", "gsr_profile_collect"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+@dataclasses.dataclass
+class Gaussians:
+    """Device-resident Gaussians (structure of arrays)."""
+    means: torch.Tensor       # [n,3] float32
+    scales: torch.Tensor      # [n,3] attribute dtype, linear
+    quats: torch.Tensor       # [n,4] attribute dtype (w,x,y,z)
+    opacities: torch.Tensor   # [n] attribute dtype
+    sh: torch.Tensor          # [n,K,3] sh dtype
+    sh_degree: int = 3
+    segments: Optional[Sequence[tuple]] = None
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @staticmethod
+    def from_scene(scene, device="cuda", attr_dtype=torch.float32, sh_dtype=torch.float32) -> "Gaussians":
+        def t(a, dt):
+            return torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=dt).contiguous()
+        return Gaussians(t(scene.means, torch.float32), t(scene.scales, attr_dtype), t(scene.quats, attr_dtype),
+                         t(scene.opacities, attr_dtype), t(scene.sh, sh_dtype), int(scene.sh_degree))
+
+    def c_struct(self):
+        seg_arr = None
+        if self.segments is not None:
+            seg_arr = (Segment * max(len(self.segments), 1))()
+            for k, (b, c) in enumerate(self.segments):
+                seg_arr[k].begin = int(b)
+                seg_arr[k].count = int(c)
+        n = self.n
+        g = CGaussians(n, _ptr(self.means), _ptr(self.scales), _ptr(self.quats), _ptr(self.opacities),
+                       _ptr(self.sh), int(self.sh.shape[1]) if self.sh.dim() == 3 else 1, int(self.sh_degree),
+                       DTYPES[self.scales.dtype], DTYPES[self.sh.dtype],
+                       ctypes.cast(seg_arr, ctypes.POINTER(Segment)) if seg_arr is not None else None,
+                       len(self.segments) if self.segments is not None else 0)
+        if self.means.dtype != torch.float32:
+            raise ValueError("means must be float32")
+        if not (self.scales.dtype == self.quats.dtype == self.opacities.dtype):
+            raise ValueError("scales, quats and opacities must share one dtype")
+        return g, seg_arr
+
+    def render_count(self) -> int:
+        if self.segments is None:
+            return self.n
+        return int(sum(c for _, c in self.segments))
+
+
+def c_camera(cam, appearance: Optional[torch.Tensor] = None) -> CCamera:
+    vm = np.asarray(cam.viewmat, np.float64).reshape(12)
+    c = CCamera()
+    for k in range(12):
+        c.viewmat[k] = float(vm[k])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.near_plane, c.far_plane = float(cam.near), float(cam.far)
+    c.appearance = _ptr(appearance) if appearance is not None else None
+    return c
+
+
+def c_cameras(cams, appearances=None):
+    arr = (CCamera * len(cams))()
+    for k, cam in enumerate(cams):
+        arr[k] = c_camera(cam, None if appearances is None else appearances[k])
+    return arr
+
+
+@dataclasses.dataclass
+class Options:
+    eps2d: float = 0.3
+    antialiased: bool = True
+    tile_cull: bool = False
+    bg: tuple = (0.0, 0.0, 0.0)
+    save_state: bool = True
+    absgrad: bool = False
+
+    def c_struct(self) -> COpts:
+        o = COpts()
+        o.eps2d = float(self.eps2d)
+        o.antialiased = int(bool(self.antialiased))
+        o.tile_cull = int(bool(self.tile_cull))
+        for k in range(3):
+            o.bg[k] = float(self.bg[k])
+        o.save_state = int(bool(self.save_state))
+        o.absgrad = int(bool(self.absgrad))
+        return o
+
+
+class State:
+    """A forward state: what render_backward needs; released when garbage-collected."""
+
+    def __init__(self, ctx: "Context", handle: int):
+        self.ctx = ctx
+        self.handle = handle
+
+    def info(self) -> dict:
+        i = CStateInfo()
+        _check(self.ctx, load().gsr_state_get_info(self.handle, ctypes.byref(i)))
+        return dict(n_render=i.n_render, n_cams=i.n_cams, n_visible=i.n_visible, n_pairs=i.n_pairs,
+                    n_tiles=i.n_tiles, n_pixels=i.n_pixels)
+
+    def copy(self, which: int, count: int, dtype=torch.int32, width: int = 1) -> torch.Tensor:
+        out = torch.empty((count, width) if width > 1 else (count,), dtype=dtype, device=f"cuda:{self.ctx.device}")
+        nbytes = out.numel() * out.element_size()
+        if nbytes:
+            _check(self.ctx, load().gsr_state_copy(self.handle, which, _ptr(out), nbytes, _stream()))
+        return out
+
+    def release(self):
+        if self.handle:
+            load().gsr_state_release(self.ctx.handle, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class Context:
+    """One library context (workspace) bound to one device; use one per stream."""
+
+    def __init__(self, device: int = 0):
+        L = load()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        st = L.gsr_create(ctypes.byref(h), self.device, None)
+        if st != GSR_OK:
+            raise GsrError(st, "gsr_create")
+        self.handle = h.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().gsr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return load().gsr_last_error(self.handle).decode()
+
+    def workspace_bytes(self) -> int:
+        return int(load().gsr_workspace_bytes(self.handle))
+
+    def workspace_query(self, n_render: int, cams, expected_pairs: int) -> int:
+        arr = c_cameras(cams)
+        out = ctypes.c_size_t()
+        _check(self, load().gsr_workspace_query(self.handle, int(n_render), arr, len(cams), int(expected_pairs),
+                                                ctypes.byref(out)))
+        return int(out.value)
+
+    def sync_check(self, stream=None):
+        _check(self, load().gsr_sync_check(self.handle, _stream(stream)))
+
+    def profile(self, on: bool = True, count_evals: bool = False):
+        _check(self, load().gsr_profile_enable(self.handle, int(on), int(count_evals)))
+
+    def profile_collect(self) -> dict:
+        """Per-stage milliseconds and launches, and blend counters, since the last collect."""
+        ms = np.zeros(len(STAGES), np.float64)
+        launches = np.zeros(len(STAGES), np.int64)
+        cnt = np.zeros(len(COUNTERS), np.int64)
+        _check(self, load().gsr_profile_collect(self.handle, ms.ctypes.data, launches.ctypes.data, cnt.ctypes.data))
+        return dict(ms=dict(zip(STAGES, ms.tolist())), launches=dict(zip(STAGES, launches.tolist())),
+                    counters=dict(zip(COUNTERS, cnt.tolist())))
+
+
+def _check(ctx, st):
+    if st != GSR_OK and st != GSR_WARN_OVER_BUDGET:
+        raise GsrError(st, ctx.last_error() if ctx is not None else "")
+    return st
+
+
+def pixel_count(cams) -> int:
+    return int(sum(int(c.width) * int(c.height) for c in cams))
+
+
+def render_forward(ctx: Context, g: Gaussians, cams, opts: Options = None, appearances=None, want_state=True,
+                   outputs: Optional[dict] = None, stream=None):
+    """Renders cameras packed one after another. Returns (dict of outputs, State or None)."""
+    opts = opts or Options()
+    dev = f"cuda:{ctx.device}"
+    npix = pixel_count(cams)
+    if outputs is None:
+        outputs = dict(rgb=torch.empty((npix, 3), device=dev), depth_acc=torch.empty(npix, device=dev),
+                       depth_exp=torch.empty(npix, device=dev), alpha=torch.empty(npix, device=dev))
+    cg, seg_keep = g.c_struct()
+    carr = c_cameras(cams, appearances)
+    co = opts.c_struct()
+    out = COutputs(_ptr(outputs["rgb"]), _ptr(outputs.get("depth_acc")), _ptr(outputs.get("depth_exp")),
+                   _ptr(outputs.get("alpha")))
+    sh = ctypes.c_void_p()
+    st = load().gsr_render_forward(ctx.handle, ctypes.byref(cg), carr, len(cams), ctypes.byref(co), ctypes.byref(out),
+                                   ctypes.byref(sh) if want_state else None, _stream(stream))
+    _check(ctx, st)
+    del seg_keep
+    return outputs, (State(ctx, sh.value) if want_state else None)
+
+
+def render_backward(ctx: Context, g: Gaussians, cams, state: State, d_out: dict, opts: Options = None,
+                    appearances=None, grads: Optional[dict] = None, stream=None) -> dict:
+    """Gradients of L given dL/d(outputs) (keys rgb, depth_acc, depth_exp, alpha; missing = 0)."""
+    opts = opts or Options()
+    dev = f"cuda:{ctx.device}"
+    n = g.n
+    K = int(g.sh.shape[1])
+    if grads is None:
+        grads = dict(means=torch.empty((n, 3), device=dev), scales=torch.empty((n, 3), device=dev),
+                     quats=torch.empty((n, 4), device=dev), opacities=torch.empty(n, device=dev),
+                     sh=torch.empty((n, K, 3), device=dev),
+                     appearance=torch.empty((len(cams), 3, 4), device=dev),
+                     absgrad=torch.empty((n, 2), device=dev) if opts.absgrad else None)
+    cg, seg_keep = g.c_struct()
+    carr = c_cameras(cams, appearances)
+    co = opts.c_struct()
+    dg = COutGrads(_ptr(d_out.get("rgb")), _ptr(d_out.get("depth_acc")), _ptr(d_out.get("depth_exp")),
+                   _ptr(d_out.get("alpha")))
+    pg = CParamGrads(_ptr(grads["means"]), _ptr(grads["scales"]), _ptr(grads["quats"]), _ptr(grads["opacities"]),
+                     _ptr(grads["sh"]), _ptr(grads.get("appearance")), _ptr(grads.get("absgrad")))
+    st = load().gsr_render_backward(ctx.handle, ctypes.byref(cg), carr, len(cams), ctypes.byref(co), state.handle,
+                                    ctypes.byref(dg), ctypes.byref(pg), _stream(stream))
+    _check(ctx, st)
+    del seg_keep
+    return grads
+
+
+def sort_pairs_u32(ctx: Context, keys: torch.Tensor, vals: torch.Tensor, begin_bit=0, end_bit=32, stream=None):
+    """Stable radix sort of uint32 (stored as int32) key/value pairs by key bits [begin_bit, end_bit)."""
+    assert keys.dtype == torch.int32 and vals.dtype == torch.int32 and keys.shape == vals.shape
+    ko = torch.empty_like(keys)
+    vo = torch.empty_like(vals)
+    _check(ctx, load().gsr_sort_pairs_u32(ctx.handle, _ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo), keys.numel(),
+                                          int(begin_bit), int(end_bit), _stream(stream)))
+    return ko, vo
+
+
+def select_lod(aabb: np.ndarray, level_offsets: np.ndarray, cam, thresholds, budget: int = 0):
+    """Host-side detail-level selection -> (status, levels [P], segments [(begin, count)], n_selected)."""
+    aabb = np.ascontiguousarray(np.asarray(aabb, np.float64).reshape(-1, 6))
+    P = aabb.shape[0]
+    lo = np.ascontiguousarray(np.asarray(level_offsets, np.int64))
+    L = lo.shape[0]
+    thr = np.ascontiguousarray(np.asarray(thresholds, np.float64).reshape(-1))
+    if thr.size == 0:
+        thr = np.zeros(1)
+    levels = np.zeros(max(P, 1), np.int32)
+    segs = (Segment * max(P, 1))()
+    ns = ctypes.c_int32()
+    nsel = ctypes.c_int64()
+    cc = c_camera(cam)
+    st = load().gsr_select_lod(P, aabb.ctypes.data, L, lo.ctypes.data, ctypes.byref(cc), thr.ctypes.data, int(budget),
+                               levels.ctypes.data, segs, ctypes.byref(ns), ctypes.byref(nsel))
+    if st < 0:
+        raise GsrError(st, "gsr_select_lod")
+    return st, levels[:P], [(segs[k].begin, segs[k].count) for k in range(ns.value)], int(nsel.value)
