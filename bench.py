@@ -1,0 +1,398 @@
+"""Benchmark: fwd+bwd ms/step and render FPS of the Gaussian rasterizer at 6M Gaussians, 1080p.
+
+Workload ("city6m_1080p"): the seeded synthetic city (1x1 km grid of 100 m blocks, 20 m
+streets, 3-6 box buildings per block, heights 10-80 m; 60% of the Gaussians on the ground,
+40% on facades; 6,000,000 Gaussians; SH degree 3; FP32) seen by one 1920x1080 camera 150 m
+above the ground with a 45-degree pitch. A step is one training pass of the rasterizer:
+render_forward (preprocess, depth sort, binning, tile sort, blend) and render_backward (blend
+backward, projection backward) with fixed upstream gradients on rgb, depth and alpha.
+The inputs (1.4 GB of Gaussians) are larger than L2, so no flush is needed between steps.
+
+Prints one JSON line. `value` is the device-timed ms per fwd+bwd step (CUDA events, inputs
+resident in HBM); `e2e` repeats the step through the same API with the Gaussians in pinned
+host memory, copying them in and the parameter gradients out every step.
+`--impl reference` times the FP64 CPU oracle instead (a bounded sample of the same step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "render FPS and fwd+bwd ms/step at 6M Gaussians 1080p; serve p50/p99 latency"
+
+# Algorithmic work per unit (see the design notes): FP32 operations of one (pixel, Gaussian)
+# evaluation in the forward and backward blends, and bytes per unit of the HBM-bound stages.
+FLOPS_PER_FWD_EVAL = 20.0
+FLOPS_PER_BWD_EVAL = 60.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=6_000_000)
+    p.add_argument("--width", type=int, default=1920)
+    p.add_argument("--height", type=int, default=1080)
+    p.add_argument("--tile-cull", type=int, default=1)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-tiles", type=int, default=24)
+    return p.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"], samples=0)
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons), samples=len(sm))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def make_workload(n, width, height, rank=0):
+    from paper_2507_23006_gb300 import scenes
+    scene = scenes.city(2, n)
+    cam = scenes.aerial_camera(width, height, altitude=150.0, pitch_deg=45.0, azimuth_deg=90.0 + 45.0 * rank)
+    return scene, cam
+
+
+def cpu_reference(scene, cam, tile_cull, n_tiles_sample, seed=0):
+    """FP64 oracle fwd+bwd on a bounded sample: the full preprocess/binning of the frame plus
+    n_tiles_sample random tiles composited forward and backward, extrapolated by tile count."""
+    import oracle
+    opts = oracle.Opts(tile_cull=bool(tile_cull))
+    tiles_x = (cam.width + 15) // 16
+    tiles_y = (cam.height + 15) // 16
+    T = tiles_x * tiles_y
+    rng = np.random.default_rng(seed)
+    tiles = rng.choice(T, size=min(n_tiles_sample, T), replace=False)
+    npix = cam.width * cam.height
+    up = np.zeros((npix, 6))
+    pix = []
+    for t in tiles:
+        ty, tx = divmod(int(t), tiles_x)
+        for y in range(ty * 16, min(ty * 16 + 16, cam.height)):
+            pix.extend(range(y * cam.width + tx * 16, y * cam.width + min(tx * 16 + 16, cam.width)))
+    up[np.array(pix)] = rng.normal(size=(len(pix), 6))
+    t0 = time.perf_counter()
+    oracle.render(scene, [cam], opts, tile_subset=np.zeros(0, np.int64), want_pairs=False)
+    t_bin = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.render(scene, [cam], opts, tile_subset=tiles, want_pairs=False)
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.backward(scene, [cam], up, opts, tile_subset=np.zeros(0, np.int64))
+    t_bwd0 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.backward(scene, [cam], up, opts, tile_subset=tiles)
+    t_bwd = time.perf_counter() - t0
+    per_tile_f = max(t_fwd - t_bin, 0.0) / len(tiles)
+    per_tile_b = max(t_bwd - t_bwd0, 0.0) / len(tiles)
+    step_s = t_bin + per_tile_f * T + t_bwd0 + per_tile_b * T
+    return dict(ms_per_step=step_s * 1e3, sample_s=t_bin + t_fwd + t_bwd0 + t_bwd, cores=oracle.num_threads(),
+                sample=(f"full FP64 preprocess+binning of all {scene.n} Gaussians, forward and backward, plus "
+                        f"{len(tiles)} of {T} tiles composited forward and backward; extrapolated to the "
+                        f"frame by tile count"))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    scene, cam = make_workload(args.n, args.width, args.height)
+    steps = []
+    cores = None
+    sample = ""
+    for k in range(args.warmup + args.steps):
+        r = cpu_reference(scene, cam, args.tile_cull, max(4, args.cpu_tiles // 3), seed=k)
+        cores, sample = r["cores"], r["sample"]
+        if k >= args.warmup:
+            steps.append(r["ms_per_step"])
+    ms = float(np.mean(steps))
+    line = dict(metric=METRIC, value=ms, unit="ms/step", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=ms, higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic", impl="reference",
+                config=dict(workload="city6m_1080p", n_gaussians=args.n, width=args.width, height=args.height,
+                            tile_cull=bool(args.tile_cull), l2="inputs larger than L2"),
+                cpu_baseline=dict(value=ms, unit="ms/step", cores=cores, kind="oracle", sample=sample),
+                e2e=dict(value=ms, unit="ms/step", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2507_23006_gb300 import native
+
+    torch.cuda.set_device(local_rank)
+    dev = f"cuda:{local_rank}"
+    scene, cam = make_workload(args.n, args.width, args.height, rank)
+    ctx = native.Context(local_rank)
+    g = native.Gaussians.from_scene(scene, device=dev)
+    opts = native.Options(tile_cull=bool(args.tile_cull), save_state=True)
+    npix = cam.width * cam.height
+    gen = torch.Generator(device=dev).manual_seed(1234 + rank)
+    d_out = dict(rgb=torch.randn((npix, 3), device=dev, generator=gen),
+                 depth_acc=torch.randn(npix, device=dev, generator=gen) * 1e-2,
+                 alpha=torch.randn(npix, device=dev, generator=gen))
+    outs = dict(rgb=torch.empty((npix, 3), device=dev), depth_acc=torch.empty(npix, device=dev),
+                depth_exp=torch.empty(npix, device=dev), alpha=torch.empty(npix, device=dev))
+    n = g.n
+    K = int(g.sh.shape[1])
+    grads = dict(means=torch.empty((n, 3), device=dev), scales=torch.empty((n, 3), device=dev),
+                 quats=torch.empty((n, 4), device=dev), opacities=torch.empty(n, device=dev),
+                 sh=torch.empty((n, K, 3), device=dev), appearance=torch.empty((1, 3, 4), device=dev),
+                 absgrad=None)
+
+    def step():
+        _, st = native.render_forward(ctx, g, [cam], opts, outputs=outs)
+        native.render_backward(ctx, g, [cam], st, d_out, opts, grads=grads)
+        return st
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        st = step()
+    torch.cuda.synchronize()
+    info = st.info()
+    del st
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local_rank)
+    ctx.profile(True, False)
+    ctx.profile_collect()
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st = step()
+        del st
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    prof = ctx.profile_collect()
+    ctx.profile(False, False)
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # forward-only frames per second (render path without state)
+    for _ in range(2):
+        native.render_forward(ctx, g, [cam], opts, outputs=outs, want_state=False)
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        native.render_forward(ctx, g, [cam], opts, outputs=outs, want_state=False)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = f0.elapsed_time(f1) / args.steps
+    # blend evaluation counts (deterministic; one counting pass outside the timed region)
+    ctx.profile(True, True)
+    st = step()
+    torch.cuda.synchronize()
+    counts = ctx.profile_collect()["counters"]
+    ctx.profile(False, False)
+    del st
+
+    # end to end through the same API: Gaussians from pinned host memory in, gradients out
+    e2e = None
+    if not args.no_e2e:
+        host = {k: getattr(g, k).to("cpu").pin_memory() for k in ("means", "scales", "quats", "opacities", "sh")}
+        host_up = {k: v.to("cpu").pin_memory() for k, v in d_out.items()}
+        host_gr = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in grads.items() if v is not None}
+        h2d = sum(v.numel() * v.element_size() for v in host.values()) + \
+            sum(v.numel() * v.element_size() for v in host_up.values())
+        d2h = sum(v.numel() * v.element_size() for v in host_gr.values())
+
+        def e2e_step():
+            for k, v in host.items():
+                getattr(g, k).copy_(v, non_blocking=True)
+            for k, v in host_up.items():
+                d_out[k].copy_(v, non_blocking=True)
+            step()
+            for k, v in host_gr.items():
+                v.copy_(grads[k], non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        x0 = torch.cuda.Event(enable_timing=True)
+        x1 = torch.cuda.Event(enable_timing=True)
+        x0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        x1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = x0.elapsed_time(x1) / args.steps
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = dict(value=e2e_ms / world, unit="ms/step", h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
+
+    if rank != 0:
+        return 0
+    # roofline of the dominant kernel
+    stage_ms = {k: v / max(args.steps, 1) for k, v in prof["ms"].items()}
+    launches = {k: v / max(args.steps, 1) for k, v in prof["launches"].items()}
+    dom = max(stage_ms, key=stage_ms.get)
+    sm_mhz = clocks.get("sm_mhz") or 1455.0
+    props = torch.cuda.get_device_properties(local_rank)
+    sms = props.multi_processor_count
+    fp32_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled SM clock
+    hbm, hbm_kind = peaks()
+    V, P = info["n_visible"], info["n_pairs"]
+    if dom in ("blend_fwd", "blend_bwd"):
+        evals = counts["fwd_evals"] if dom == "blend_fwd" else counts["bwd_evals"]
+        flops = evals * (FLOPS_PER_FWD_EVAL if dom == "blend_fwd" else FLOPS_PER_BWD_EVAL)
+        achieved = flops / (stage_ms[dom] * 1e-3) / 1e12
+        roof = dict(kernel=dom, bound="alu", achieved=achieved, peak=fp32_peak, unit="TFLOP/s",
+                    frac=achieved / fp32_peak, traffic=None,
+                    peak_source=f"{sms} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sampled)")
+    else:
+        passes = (max(1, math.ceil(math.log2(max(info["n_tiles"], 2)))) + 7) // 8
+        per_unit = dict(preprocess=52.0 * n + 252.0 * V, depth_sort=68.0 * V, pair_scan=12.0 * V,
+                        tile_count=56.0 * V, duplicate=56.0 * V + 8.0 * P, tile_sort=(4.0 + 16.0 * passes) * P,
+                        ranges=4.0 * P + 8.0 * info["n_tiles"], preprocess_bwd=288.0 * n + 240.0 * V, readback=0.0)
+        bytes_ = per_unit.get(dom, 0.0)
+        achieved = bytes_ / (stage_ms[dom] * 1e-3) / 1e9
+        roof = dict(kernel=dom, bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm,
+                    traffic=None, peak_source=f"{hbm_kind} HBM copy bandwidth")
+    cpu = None
+    if not args.no_cpu_baseline:
+        r = cpu_reference(scene, cam, args.tile_cull, args.cpu_tiles)
+        cpu = dict(value=r["ms_per_step"], unit="ms/step", cores=r["cores"], kind="oracle", sample=r["sample"],
+                   sample_seconds=round(r["sample_s"], 1))
+    value = ms / world
+    line = dict(metric=METRIC, value=value, unit="ms/step", n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=ms, higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f32",
+                data="synthetic",
+                config=dict(workload="city6m_1080p", n_gaussians=n, width=cam.width, height=cam.height,
+                            tile_cull=bool(args.tile_cull), sh_degree=3, attributes="f32",
+                            l2="inputs larger than L2 (1.4 GB), no flush", parallelism=f"replicas{world}"),
+                render_fps=1000.0 / fwd_ms * world, fwd_ms=fwd_ms,
+                stages_ms=stage_ms, visible=V, pairs=P, counters=counts,
+                roofline=roof, cpu_baseline=cpu, e2e=e2e, clocks=clocks)
+    line["gpu_launches"] = int(args.steps * kernels_per_step(args.tile_cull, info))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def kernels_per_step(tile_cull, info):
+    """Kernels of ours launched per fwd+bwd step (memsets excluded)."""
+    k = 1                      # preprocess
+    k += 2 + 4                 # depth sort: histogram, histogram scan, 4 onesweep passes
+    k += 1 if tile_cull else 0  # tile-culled counts
+    k += 1                     # pair scan
+    tiles = int(info["n_tiles"])
+    bits = max(1, math.ceil(math.log2(max(tiles, 2))))
+    k += 1 + 2 + (bits + 7) // 8 + 1  # duplicate, tile sort (hist, scan, passes), ranges
+    k += 1                     # blend forward
+    k += 1 + 1                 # blend backward, preprocess backward
+    return k
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if world > 1:
+        import torch.distributed as dist
+        if args.impl == "ours":
+            import torch
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())
