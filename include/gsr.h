@@ -248,6 +248,26 @@ gsr_status gsr_sort_pairs_u32(gsr_ctx* ctx, const uint32_t* keys_in, const uint3
                               uint32_t* keys_out, uint32_t* vals_out, int64_t n, int32_t begin_bit,
                               int32_t end_bit, gsr_stream stream);
 
+/* The sort of gsr_sort_pairs_u32 for callers that cannot allocate device memory: code being
+ * recorded into a CUDA graph (an allocation cannot be captured, and cudaMalloc may
+ * synchronise the device), a loop that must keep a fixed memory footprint, or a callback that
+ * runs inside another framework's allocator. It calls no cudaMalloc, cudaFree or allocating
+ * library routine. The paper has no counterpart: this is a deployment variant of the sort.
+ *   Limit: n <= 262144 (2^18); a larger n returns GSR_ERR_UNSUPPORTED without doing anything.
+ *   Scratch: one static device array of about 2.3 MB inside libgsr, reserved on every GPU that
+ *     loads the library until the process exits and shared by every call. Calls that overlap
+ *     on the GPU (two streams, or two host threads) race on it and give wrong results:
+ *     serialise them on one stream. Each call clears what must start at zero (histograms,
+ *     block counters, look-back status words) with stream-ordered memsets before its kernels.
+ *   The first call on a device looks up the array's device address with that device current;
+ *     make that first call before any stream capture.
+ *   device_err: device int32, or NULL; a bounded wait that runs out ORs 1 into it (the output
+ *     is then invalid); the call never clears it.
+ * Asynchronous on `stream`; inputs are not modified; outputs must not alias the inputs. */
+gsr_status gsr_sort_pairs_u32_noalloc(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                                      uint32_t* vals_out, int64_t n, int32_t begin_bit, int32_t end_bit,
+                                      int32_t* device_err, gsr_stream stream);
+
 /* ---- detail levels (Sec. 3.4.2) -------------------------------------------------------- */
 
 /* Partition-level detail-level selection for one camera, host memory throughout.

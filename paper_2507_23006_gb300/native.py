@@ -34,7 +34,7 @@ EXPORTED = [
     "gsr_create", "gsr_destroy", "gsr_status_string", "gsr_last_error", "gsr_workspace_query",
     "gsr_workspace_bytes", "gsr_render_forward", "gsr_render_backward", "gsr_state_release",
     "gsr_state_get_info", "gsr_state_copy", "gsr_sync_check", "gsr_sort_pairs_u32", "gsr_select_lod",
-    "gsr_profile_enable", "gsr_profile_collect",
+    "gsr_profile_enable", "gsr_profile_collect", "gsr_sort_pairs_u32_noalloc",
 ]
 
 STAGES = ["preprocess", "depth_sort", "tile_count", "pair_scan", "readback", "duplicate", "tile_sort", "ranges",
@@ -134,13 +134,16 @@ def load(build_if_missing: bool = True):
         L.gsr_select_lod.argtypes = [ctypes.c_int32, vp, ctypes.c_int32, vp, ctypes.POINTER(CCamera), vp,
                                      ctypes.c_int64, vp, ctypes.POINTER(Segment), ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_int64)]
+        L.gsr_sort_pairs_u32_noalloc.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                                 vp, vp]
         L.gsr_profile_enable.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
         L.gsr_profile_collect.argtypes = [vp, vp, vp, vp]
         for name in EXPORTED:
             getattr(L, name)
         for name in ("gsr_create", "gsr_workspace_query", "gsr_render_forward", "gsr_render_backward",
                      "gsr_state_get_info", "gsr_state_copy", "gsr_sync_check", "gsr_sort_pairs_u32",
-                     "gsr_select_lod", "gsr_profile_enable", "gsr_profile_collect"):
+                     "gsr_select_lod", "gsr_profile_enable", "gsr_profile_collect",
+                     "gsr_sort_pairs_u32_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
