@@ -153,14 +153,15 @@ typedef struct gsr_state_info {
 
 /* Buffers of a forward state that gsr_state_copy can export (for tests and tools). */
 typedef enum gsr_state_buffer {
-  GSR_BUF_RECORDS = 0,    /* [V] 48-byte splat records (float4 x3, layout in the CUDA sources) */
-  GSR_BUF_VIS_BASE = 1,   /* [n_render] uint32: index of the Gaussian's first visible record */
-  GSR_BUF_VIS_MASK = 2,   /* [n_render] uint32: bit c set when visible in camera c */
-  GSR_BUF_PAIR_VALS = 3,  /* [P] uint32 record index, sorted by (tile, depth, index) */
-  GSR_BUF_RANGES = 4,     /* [n_tiles] uint32 x2: [start, end) into the pair list */
-  GSR_BUF_T_FINAL = 5,    /* [n_pixels] float32 final transmittance */
-  GSR_BUF_N_CONTRIB = 6,  /* [n_pixels] uint32 list positions walked up to the last contributor */
-  GSR_BUF_DEPTH_ACC = 7   /* [n_pixels] float32 accumulated depth */
+  GSR_BUF_RECORDS = 0,    /* [V] 64-byte splat records (float4 x4: mean2d, opacity', z | conic, red |
+                             green, blue, packed tile rectangle and camera | alpha >= 1/255 box) */
+  GSR_BUF_OWNER = 1,      /* [V] uint32: rendered index of each record's Gaussian; a Gaussian's
+                             records are consecutive, in camera order */
+  GSR_BUF_PAIR_VALS = 2,  /* [P] uint32 record index, sorted by (tile, depth, index) */
+  GSR_BUF_RANGES = 3,     /* [n_tiles] uint32 x2: [start, end) into the pair list */
+  GSR_BUF_T_FINAL = 4,    /* [n_pixels] float32 final transmittance */
+  GSR_BUF_N_CONTRIB = 5,  /* [n_pixels] uint32 list positions walked up to the last contributor */
+  GSR_BUF_DEPTH_ACC = 6   /* [n_pixels] float32 accumulated depth */
 } gsr_state_buffer;
 
 /* ---- context --------------------------------------------------------------------------- */
@@ -254,7 +255,7 @@ gsr_status gsr_sort_pairs_u32(gsr_ctx* ctx, const uint32_t* keys_in, const uint3
  * runs inside another framework's allocator. It calls no cudaMalloc, cudaFree or allocating
  * library routine. The paper has no counterpart: this is a deployment variant of the sort.
  *   Limit: n <= 262144 (2^18); a larger n returns GSR_ERR_UNSUPPORTED without doing anything.
- *   Scratch: one static device array of about 2.3 MB inside libgsr, reserved on every GPU that
+ *   Scratch: one static device array of about 2.6 MB inside libgsr, reserved on every GPU that
  *     loads the library until the process exits and shared by every call. Calls that overlap
  *     on the GPU (two streams, or two host threads) race on it and give wrong results:
  *     serialise them on one stream. Each call clears what must start at zero (histograms,

@@ -38,9 +38,9 @@ struct gsr_ctx {
   size_t held = 0;
   // scratch
   Buf seg_begin, seg_start;
-  Buf rec, dkeys, dvals, touched, vis_base, vis_mask;  // binning (recompute / no-state mode)
+  Buf rec, dkeys, dvals, touched, owner;  // binning (recompute / no-state mode)
   Buf dkeys_s, dvals_s, sort_ktmp, sort_vtmp, sort_hist, sort_status, sort_counters;
-  Buf cnt_sorted, offsets, pre_status, misc;
+  Buf cnt_sorted, offsets, pre_status, scan_status, misc;
   Buf pkeys, pvals, pkeys_s, pvals_s, ranges;  // pairs (no-state mode)
   Buf pix_T, pix_n, pix_D;                     // per-pixel state (no-state mode)
   Buf g2d, gaff;
@@ -56,6 +56,13 @@ struct gsr_ctx {
   };
   std::vector<Rec3> prof_recs;
   std::vector<cudaEvent_t> ev_pool;
+  // released forward states kept with their buffers for reuse (stream-ordered, no sync)
+  std::vector<gsr_fwd_state*> state_pool;
+  uint32_t epoch = 0;  // tag of the chained-scan status words of the latest launch
+  // a second stream for work that overlaps the caller's (joined back before returning)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int grid_cap = 304;  // resident blocks of the looping scan / sort kernels (2 per SM)
 };
 
 struct gsr_fwd_state {
@@ -63,10 +70,8 @@ struct gsr_fwd_state {
   gsr_state_info info{};
   bool has_bins = false;
   int tile_bits = 1;
-  Buf rec, vis_base, vis_mask, pvals_s, ranges;
+  Buf rec, owner, pvals_s, ranges;
   Buf T_final, n_contrib, D;
-  // the pieces of Buf above that were allocated by this state
-  std::vector<Buf*> owned;
 };
 
 namespace {
@@ -130,6 +135,45 @@ void release(gsr_ctx* ctx, Buf& b, cudaStream_t s) {
 template <typename T>
 T* as(Buf& b) {
   return static_cast<T*>(b.p);
+}
+
+// Like ensure(), but a new allocation is zeroed: status words of epoch 0 are never "ready".
+bool ensure_zeroed(gsr_ctx* ctx, Buf& b, size_t bytes, cudaStream_t s) {
+  const void* before = b.p;
+  if (!ensure(ctx, b, bytes, s)) return false;
+  if (b.p != before) cudaMemsetAsync(b.p, 0, b.cap, s);
+  return true;
+}
+
+// A fresh tag for the status words of one chained-scan launch. After 2^30 - 1 tags the status
+// arrays are cleared and the count restarts.
+uint32_t next_epoch(gsr_ctx* ctx, cudaStream_t s) {
+  if (++ctx->epoch >= (1u << 30)) {
+    Buf* st[] = {&ctx->pre_status, &ctx->scan_status, &ctx->sort_status};
+    for (Buf* b : st)
+      if (b->p) cudaMemsetAsync(b->p, 0, b->cap, s);
+    ctx->epoch = 1;
+  }
+  return ctx->epoch;
+}
+
+SortScratch sort_scratch(gsr_ctx* ctx) {
+  SortScratch sc;
+  sc.keys_tmp = as<uint32_t>(ctx->sort_ktmp);
+  sc.vals_tmp = as<uint32_t>(ctx->sort_vtmp);
+  sc.hist = as<uint32_t>(ctx->sort_hist);
+  sc.status = as<unsigned long long>(ctx->sort_status);
+  sc.counters = as<uint32_t>(ctx->sort_counters);
+  sc.grid_cap = ctx->grid_cap;
+  return sc;
+}
+
+bool ensure_sort(gsr_ctx* ctx, long long n, cudaStream_t s) {
+  const size_t words = sort_status_words(n) * 4;  // four passes at most
+  return ensure(ctx, ctx->sort_ktmp, sizeof(uint32_t) * n, s) && ensure(ctx, ctx->sort_vtmp, sizeof(uint32_t) * n, s) &&
+         ensure(ctx, ctx->sort_hist, sizeof(uint32_t) * 4 * 256, s) &&
+         ensure_zeroed(ctx, ctx->sort_status, sizeof(unsigned long long) * words, s) &&
+         ensure(ctx, ctx->sort_counters, sizeof(uint32_t) * 4, s);
 }
 
 unsigned long long* counters_of(gsr_ctx* ctx) {
@@ -268,8 +312,7 @@ int bits_for(long long v) {
 
 struct BinOut {
   Buf* rec;
-  Buf* vis_base;
-  Buf* vis_mask;
+  Buf* owner;
   Buf* pvals_s;
   Buf* ranges;
 };
@@ -318,30 +361,31 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   ga.deg = g->sh_degree;
   ga.attr_dtype = g->attr_dtype;
   ga.sh_dtype = g->sh_dtype;
+  ga.quat_vec4 = g->attr_dtype == GSR_F32 && (reinterpret_cast<uintptr_t>(g->quats) % 16 == 0);
 
-  const int pre_blocks = static_cast<int>((N + 255) / 256);
+  const int pre_blocks = static_cast<int>((N + kPreTile - 1) / kPreTile);
   GSR_TRY_ALLOC(*bo.rec, sizeof(Rec) * capv);
-  GSR_TRY_ALLOC(*bo.vis_base, sizeof(uint32_t) * std::max<long long>(N, 1));
-  GSR_TRY_ALLOC(*bo.vis_mask, sizeof(uint32_t) * std::max<long long>(N, 1));
+  GSR_TRY_ALLOC(*bo.owner, sizeof(uint32_t) * capv);
   GSR_TRY_ALLOC(ctx->dkeys, sizeof(uint32_t) * capv);
   GSR_TRY_ALLOC(ctx->dvals, sizeof(uint32_t) * capv);
   GSR_TRY_ALLOC(ctx->touched, sizeof(uint32_t) * capv);
   GSR_TRY_ALLOC(ctx->dkeys_s, sizeof(uint32_t) * capv);
   GSR_TRY_ALLOC(ctx->dvals_s, sizeof(uint32_t) * capv);
   GSR_TRY_ALLOC(ctx->offsets, sizeof(uint32_t) * capv);
-  GSR_TRY_ALLOC(ctx->pre_status, sizeof(unsigned long long) * std::max(pre_blocks, 1));
+  if (!ensure_zeroed(ctx, ctx->pre_status, sizeof(unsigned long long) * std::max(pre_blocks, 1), s))
+    return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
   const long long scan_blocks = (capv + kScanThreads * kScanItems - 1) / (kScanThreads * kScanItems);
-  // misc: [0] pre counter, [1] V, [2] scan counter, [3] pad, [4..5] P (u64), then scan statuses
-  GSR_TRY_ALLOC(ctx->misc, 64 + sizeof(unsigned long long) * (scan_blocks + 1));
+  if (!ensure_zeroed(ctx, ctx->scan_status, sizeof(unsigned long long) * (scan_blocks + 1), s))
+    return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
+  // misc: [0] preprocess block counter, [1] V, [2] scan block counter, [3] pad, [4..5] P (u64)
+  GSR_TRY_ALLOC(ctx->misc, 64);
   uint32_t* misc = as<uint32_t>(ctx->misc);
   uint32_t* d_counter = misc + 0;
   uint32_t* d_V = misc + 1;
   uint32_t* d_scan_counter = misc + 2;
   unsigned long long* d_P = reinterpret_cast<unsigned long long*>(misc + 4);
-  unsigned long long* d_scan_status = reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->misc.p) + 64);
-  // sort scratch, sized for the larger of the two sorts later
-  cudaError_t e = cudaMemsetAsync(ctx->pre_status.p, 0, sizeof(unsigned long long) * std::max(pre_blocks, 1), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->misc.p, 0, 64, s);
+  unsigned long long* d_scan_status = as<unsigned long long>(ctx->scan_status);
+  cudaError_t e = cudaMemsetAsync(ctx->misc.p, 0, 64, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
 
@@ -350,36 +394,24 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   po.depth_keys = as<uint32_t>(ctx->dkeys);
   po.depth_vals = as<uint32_t>(ctx->dvals);
   po.touched = as<uint32_t>(ctx->touched);
-  po.vis_base = as<uint32_t>(*bo.vis_base);
-  po.vis_mask = as<uint32_t>(*bo.vis_mask);
+  po.owner = as<uint32_t>(*bo.owner);
   po.status = as<unsigned long long>(ctx->pre_status);
   po.counter = d_counter;
   po.v_total = d_V;
   po.err = ctx->d_err;
+  po.epoch = next_epoch(ctx, s);
   {
     StageTimer tm(ctx, GSR_STAGE_PREPROCESS, s);
     launch_preprocess_fwd(ga, cb, o->eps2d, o->antialiased, po, pre_blocks, s);
   }
 
   // depth sort of the visible records (V read on the device)
-  auto ensure_sort = [&](long long n) -> bool {
-    const size_t words = sort_status_words(n) * 4;
-    return ensure(ctx, ctx->sort_ktmp, sizeof(uint32_t) * n, s) && ensure(ctx, ctx->sort_vtmp, sizeof(uint32_t) * n, s) &&
-           ensure(ctx, ctx->sort_hist, sizeof(uint32_t) * 4 * 256, s) &&
-           ensure(ctx, ctx->sort_status, sizeof(uint32_t) * std::max<size_t>(words, 256), s) &&
-           ensure(ctx, ctx->sort_counters, sizeof(uint32_t) * 4, s);
-  };
-  if (!ensure_sort(capv)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
-  SortScratch sc;
-  sc.keys_tmp = as<uint32_t>(ctx->sort_ktmp);
-  sc.vals_tmp = as<uint32_t>(ctx->sort_vtmp);
-  sc.hist = as<uint32_t>(ctx->sort_hist);
-  sc.status = as<uint32_t>(ctx->sort_status);
-  sc.counters = as<uint32_t>(ctx->sort_counters);
+  if (!ensure_sort(ctx, capv, s)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
+  SortScratch sc = sort_scratch(ctx);
   if (N * C > 0) {
     StageTimer tm(ctx, GSR_STAGE_DEPTH_SORT, s);
     radix_sort_u32(as<uint32_t>(ctx->dkeys), as<uint32_t>(ctx->dvals), as<uint32_t>(ctx->dkeys_s),
-                   as<uint32_t>(ctx->dvals_s), d_V, capv, 0, 32, sc, ctx->d_err, s);
+                   as<uint32_t>(ctx->dvals_s), d_V, capv, 0, 32, sc, next_epoch(ctx, s), false, ctx->d_err, s);
   }
 
   const uint32_t* cnt_sorted = nullptr;
@@ -393,7 +425,7 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   {
     StageTimer tm(ctx, GSR_STAGE_PAIR_SCAN, s);
     pair_offsets_scan(as<uint32_t>(ctx->touched), as<uint32_t>(ctx->dvals_s), cnt_sorted, as<uint32_t>(ctx->offsets),
-                      d_V, capv, d_scan_status, d_scan_counter, d_P, ctx->d_err, s);
+                      d_V, capv, d_scan_status, d_scan_counter, d_P, ctx->d_err, next_epoch(ctx, s), ctx->grid_cap, s);
   }
   // read V, P and the error word
   uint32_t* h = static_cast<uint32_t*>(ctx->pinned);
@@ -428,12 +460,8 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   e = cudaMemsetAsync(bo.ranges->p, 0, sizeof(uint2) * std::max(cb.total_tiles, 1), s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "memset ranges");
   if (P > 0) {
-    if (!ensure_sort(Pc)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
-    sc.keys_tmp = as<uint32_t>(ctx->sort_ktmp);
-    sc.vals_tmp = as<uint32_t>(ctx->sort_vtmp);
-    sc.hist = as<uint32_t>(ctx->sort_hist);
-    sc.status = as<uint32_t>(ctx->sort_status);
-    sc.counters = as<uint32_t>(ctx->sort_counters);
+    if (!ensure_sort(ctx, Pc, s)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
+    sc = sort_scratch(ctx);
     {
       StageTimer tm(ctx, GSR_STAGE_DUPLICATE, s);
       launch_duplicate(as<Rec>(*bo.rec), as<uint32_t>(ctx->dvals_s), as<uint32_t>(ctx->offsets), d_V, capv, cb,
@@ -443,7 +471,7 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
     {
       StageTimer tm(ctx, GSR_STAGE_TILE_SORT, s);
       radix_sort_u32(as<uint32_t>(ctx->pkeys), as<uint32_t>(ctx->pvals), as<uint32_t>(ctx->pkeys_s),
-                     as<uint32_t>(*bo.pvals_s), nullptr, P, 0, tb, sc, ctx->d_err, s);
+                     as<uint32_t>(*bo.pvals_s), nullptr, P, 0, tb, sc, next_epoch(ctx, s), false, ctx->d_err, s);
     }
     StageTimer tm(ctx, GSR_STAGE_RANGES, s);
     launch_ranges(as<uint32_t>(ctx->pkeys_s), P, as<uint2>(*bo.ranges), s);
@@ -490,6 +518,17 @@ gsr_status gsr_create(gsr_ctx** out, int device, const gsr_allocator* alloc) {
     return GSR_ERR_OOM;
   }
   cudaMemset(ctx->d_err, 0, 64);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
+    ctx->grid_cap = 2 * sms;
+  cudaGetLastError();
+  if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    gsr_destroy(ctx);
+    return GSR_ERR_CUDA;
+  }
   *out = ctx;
   return GSR_OK;
 }
@@ -497,10 +536,16 @@ gsr_status gsr_create(gsr_ctx** out, int device, const gsr_allocator* alloc) {
 void gsr_destroy(gsr_ctx* ctx) {
   if (!ctx) return;
   cudaDeviceSynchronize();
+  for (gsr_fwd_state* st : ctx->state_pool) {
+    Buf* sb[] = {&st->rec, &st->owner, &st->pvals_s, &st->ranges, &st->T_final, &st->n_contrib, &st->D};
+    for (Buf* b : sb) release(ctx, *b, nullptr);
+    delete st;
+  }
+  ctx->state_pool.clear();
   Buf* all[] = {&ctx->seg_begin, &ctx->seg_start, &ctx->rec, &ctx->dkeys, &ctx->dvals, &ctx->touched,
-                &ctx->vis_base, &ctx->vis_mask, &ctx->dkeys_s, &ctx->dvals_s, &ctx->sort_ktmp, &ctx->sort_vtmp,
+                &ctx->owner, &ctx->dkeys_s, &ctx->dvals_s, &ctx->sort_ktmp, &ctx->sort_vtmp,
                 &ctx->sort_hist, &ctx->sort_status, &ctx->sort_counters, &ctx->cnt_sorted, &ctx->offsets,
-                &ctx->pre_status, &ctx->misc, &ctx->pkeys, &ctx->pvals, &ctx->pkeys_s, &ctx->pvals_s,
+                &ctx->pre_status, &ctx->scan_status, &ctx->misc, &ctx->pkeys, &ctx->pvals, &ctx->pkeys_s, &ctx->pvals_s,
                 &ctx->ranges, &ctx->pix_T, &ctx->pix_n, &ctx->pix_D, &ctx->g2d, &ctx->gaff};
   for (Buf* b : all) release(ctx, *b, nullptr);
   for (auto& r : ctx->prof_recs) {
@@ -508,6 +553,9 @@ void gsr_destroy(gsr_ctx* ctx) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->d_err) cudaFree(ctx->d_err);
   delete ctx;
@@ -526,9 +574,8 @@ gsr_status gsr_workspace_query(gsr_ctx* ctx, int64_t n_render, const gsr_camera*
   const size_t capv = static_cast<size_t>(std::max<int64_t>(1, n_render * n_cams));
   const size_t P = static_cast<size_t>(std::max<int64_t>(1, expected_pairs));
   size_t b = 0;
-  b += capv * (sizeof(Rec) + 7 * sizeof(uint32_t));           // records, keys, values, counts, offsets
-  b += static_cast<size_t>(n_render) * 2 * sizeof(uint32_t);  // visibility
-  b += std::max(capv, P) * 2 * sizeof(uint32_t) + sort_status_words(std::max(capv, P)) * 4 * sizeof(uint32_t);
+  b += capv * (sizeof(Rec) + 8 * sizeof(uint32_t));  // records, owners, keys, values, counts, offsets
+  b += std::max(capv, P) * 2 * sizeof(uint32_t) + sort_status_words(std::max(capv, P)) * 4 * sizeof(unsigned long long);
   b += P * 4 * sizeof(uint32_t);                              // pairs
   b += static_cast<size_t>(cb.total_tiles) * sizeof(uint2);
   b += static_cast<size_t>(npix) * 3 * sizeof(float);         // per-pixel state
@@ -553,16 +600,22 @@ gsr_status gsr_render_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_ca
 
   gsr_fwd_state* stt = nullptr;
   if (state_out) {
-    stt = new (std::nothrow) gsr_fwd_state();
-    if (!stt) return set_err(ctx, GSR_ERR_OOM, "host allocation failed");
+    if (!ctx->state_pool.empty()) {
+      stt = ctx->state_pool.back();
+      ctx->state_pool.pop_back();
+    } else {
+      stt = new (std::nothrow) gsr_fwd_state();
+      if (!stt) return set_err(ctx, GSR_ERR_OOM, "host allocation failed");
+    }
     stt->ctx = ctx;
+    stt->info = gsr_state_info{};
     stt->has_bins = opts->save_state != 0;
   }
   BinOut bo;
   if (stt && stt->has_bins) {
-    bo = BinOut{&stt->rec, &stt->vis_base, &stt->vis_mask, &stt->pvals_s, &stt->ranges};
+    bo = BinOut{&stt->rec, &stt->owner, &stt->pvals_s, &stt->ranges};
   } else {
-    bo = BinOut{&ctx->rec, &ctx->vis_base, &ctx->vis_mask, &ctx->pvals_s, &ctx->ranges};
+    bo = BinOut{&ctx->rec, &ctx->owner, &ctx->pvals_s, &ctx->ranges};
   }
   long long V = 0, P = 0;
   st = run_binning(ctx, g, cb, opts, bo, &V, &P, s);
@@ -630,9 +683,9 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
   BinOut bo;
   long long V = state->info.n_visible;
   if (state->has_bins) {
-    bo = BinOut{&ms->rec, &ms->vis_base, &ms->vis_mask, &ms->pvals_s, &ms->ranges};
+    bo = BinOut{&ms->rec, &ms->owner, &ms->pvals_s, &ms->ranges};
   } else {
-    bo = BinOut{&ctx->rec, &ctx->vis_base, &ctx->vis_mask, &ctx->pvals_s, &ctx->ranges};
+    bo = BinOut{&ctx->rec, &ctx->owner, &ctx->pvals_s, &ctx->ranges};
     long long P = 0;
     st = run_binning(ctx, g, cb, opts, bo, &V, &P, s);
     if (st != GSR_OK) return st;
@@ -645,6 +698,21 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
   if (e == cudaSuccess && grads->appearance)
     e = cudaMemsetAsync(grads->appearance, 0, sizeof(float) * 12 * n_cams, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
+  // Every parameter-gradient row starts at zero; only rows of Gaussians with a record are then
+  // written. The fill runs on the side stream, overlapping the (ALU-bound) blend backward.
+  if (g->n > 0) {
+    const size_t n = static_cast<size_t>(g->n);
+    e = cudaEventRecord(ctx->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grads->means, 0, sizeof(float) * 3 * n, ctx->side);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grads->scales, 0, sizeof(float) * 3 * n, ctx->side);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grads->quats, 0, sizeof(float) * 4 * n, ctx->side);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grads->opacities, 0, sizeof(float) * n, ctx->side);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grads->sh, 0, sizeof(float) * 3 * g->sh_coeffs * n, ctx->side);
+    if (e == cudaSuccess && grads->absgrad) e = cudaMemsetAsync(grads->absgrad, 0, sizeof(float) * 2 * n, ctx->side);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
+  }
   BlendBwdIn bi;
   bi.d_rgb = dout->rgb;
   bi.d_depth_acc = dout->depth_acc;
@@ -658,20 +726,9 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
     launch_blend_bwd(as<Rec>(*bo.rec), as<uint32_t>(*bo.pvals_s), as<uint2>(*bo.ranges), cb, opts->bg, bi,
                      as<Grad2D>(ctx->g2d), grads->appearance, opts->absgrad && grads->absgrad, counters_of(ctx), s);
   }
-  if (g->segs && g->n > 0) {
-    // rows outside the segments are not visited by the kernel
-    const size_t n = static_cast<size_t>(g->n);
-    e = cudaMemsetAsync(grads->means, 0, sizeof(float) * 3 * n, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(grads->scales, 0, sizeof(float) * 3 * n, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(grads->quats, 0, sizeof(float) * 4 * n, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(grads->opacities, 0, sizeof(float) * n, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(grads->sh, 0, sizeof(float) * 3 * g->sh_coeffs * n, s);
-    if (e == cudaSuccess && grads->absgrad) e = cudaMemsetAsync(grads->absgrad, 0, sizeof(float) * 2 * n, s);
-    if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
-  }
-  if (grads->absgrad && !opts->absgrad && !g->segs) {
-    e = cudaMemsetAsync(grads->absgrad, 0, sizeof(float) * 2 * static_cast<size_t>(g->n), s);
-    if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
+  if (g->n > 0) {
+    e = cudaStreamWaitEvent(s, ctx->ev_join, 0);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "join");
   }
   GaussArgs ga;
   ga.n_render = N;
@@ -703,6 +760,7 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
   ga.deg = g->sh_degree;
   ga.attr_dtype = g->attr_dtype;
   ga.sh_dtype = g->sh_dtype;
+  ga.quat_vec4 = g->attr_dtype == GSR_F32 && (reinterpret_cast<uintptr_t>(g->quats) % 16 == 0);
   ParamGrads pg;
   pg.means = grads->means;
   pg.scales = grads->scales;
@@ -710,10 +768,12 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
   pg.opac = grads->opacities;
   pg.sh = grads->sh;
   pg.absgrad = opts->absgrad ? grads->absgrad : nullptr;
+  pg.vec4 = (reinterpret_cast<uintptr_t>(grads->quats) % 16 == 0) && (reinterpret_cast<uintptr_t>(grads->sh) % 16 == 0) &&
+            ((3 * g->sh_coeffs) % 4 == 0);
   {
     StageTimer tm(ctx, GSR_STAGE_PREPROCESS_BWD, s);
-    launch_preprocess_bwd(ga, cb, opts->eps2d, opts->antialiased, as<Rec>(*bo.rec), as<uint32_t>(*bo.vis_base),
-                          as<uint32_t>(*bo.vis_mask), as<Grad2D>(ctx->g2d), pg, s);
+    launch_preprocess_bwd(ga, cb, opts->eps2d, opts->antialiased, V, as<Rec>(*bo.rec), as<uint32_t>(*bo.owner),
+                          as<Grad2D>(ctx->g2d), pg, s);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(ctx, e, "backward launch");
@@ -723,12 +783,17 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
 void gsr_state_release(gsr_ctx* ctx, gsr_fwd_state* state) {
   if (!state) return;
   gsr_ctx* c = ctx ? ctx : state->ctx;
-  Buf* all[] = {&state->rec, &state->vis_base, &state->vis_mask, &state->pvals_s, &state->ranges,
-                &state->T_final, &state->n_contrib, &state->D};
-  if (c) {
-    cudaDeviceSynchronize();
-    for (Buf* b : all) release(c, *b, nullptr);
+  // Keep up to a few released states with their buffers: the next forward on this context's
+  // stream reuses them in stream order, without a cudaFree or a device synchronisation.
+  constexpr size_t kPoolMax = 4;
+  if (c && c->state_pool.size() < kPoolMax) {
+    c->state_pool.push_back(state);
+    return;
   }
+  Buf* all[] = {&state->rec, &state->owner, &state->pvals_s, &state->ranges, &state->T_final, &state->n_contrib,
+                &state->D};
+  if (c)
+    for (Buf* b : all) release(c, *b, nullptr);
   delete state;
 }
 
@@ -751,8 +816,7 @@ gsr_status gsr_state_copy(const gsr_fwd_state* state, int32_t which, void* dst, 
   const gsr_state_info& I = state->info;
   switch (which) {
     case GSR_BUF_RECORDS: pick(state->rec, ctx->rec, sizeof(Rec) * I.n_visible); break;
-    case GSR_BUF_VIS_BASE: pick(state->vis_base, ctx->vis_base, 4 * I.n_render); break;
-    case GSR_BUF_VIS_MASK: pick(state->vis_mask, ctx->vis_mask, 4 * I.n_render); break;
+    case GSR_BUF_OWNER: pick(state->owner, ctx->owner, 4 * I.n_visible); break;
     case GSR_BUF_PAIR_VALS: pick(state->pvals_s, ctx->pvals_s, 4 * I.n_pairs); break;
     case GSR_BUF_RANGES: pick(state->ranges, ctx->ranges, 8 * I.n_tiles); break;
     case GSR_BUF_T_FINAL: src = state->T_final.p; have = std::min<size_t>(4 * I.n_pixels, state->T_final.cap); break;
@@ -831,18 +895,10 @@ gsr_status gsr_sort_pairs_u32(gsr_ctx* ctx, const uint32_t* keys_in, const uint3
     if (e == cudaSuccess) e = cudaMemcpyAsync(vals_out, vals_in, 4 * n, cudaMemcpyDeviceToDevice, s);
     return e == cudaSuccess ? GSR_OK : cuda_err(ctx, e, "copy");
   }
-  const size_t words = sort_status_words(n) * 4;
-  if (!ensure(ctx, ctx->sort_ktmp, 4 * n, s) || !ensure(ctx, ctx->sort_vtmp, 4 * n, s) ||
-      !ensure(ctx, ctx->sort_hist, 4 * 4 * 256, s) || !ensure(ctx, ctx->sort_status, 4 * std::max<size_t>(words, 256), s) ||
-      !ensure(ctx, ctx->sort_counters, 16, s))
-    return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
-  SortScratch sc;
-  sc.keys_tmp = as<uint32_t>(ctx->sort_ktmp);
-  sc.vals_tmp = as<uint32_t>(ctx->sort_vtmp);
-  sc.hist = as<uint32_t>(ctx->sort_hist);
-  sc.status = as<uint32_t>(ctx->sort_status);
-  sc.counters = as<uint32_t>(ctx->sort_counters);
-  radix_sort_u32(keys_in, vals_in, keys_out, vals_out, nullptr, n, begin_bit, end_bit, sc, ctx->d_err, s);
+  if (!ensure_sort(ctx, n, s)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
+  SortScratch sc = sort_scratch(ctx);
+  radix_sort_u32(keys_in, vals_in, keys_out, vals_out, nullptr, n, begin_bit, end_bit, sc, next_epoch(ctx, s), false,
+                 ctx->d_err, s);
   e = cudaGetLastError();
   return e == cudaSuccess ? GSR_OK : cuda_err(ctx, e, "sort launch");
 }

@@ -51,13 +51,17 @@ struct SegMap {
   const long long* start;      // [nsegs] selected index of the segment's first Gaussian
 };
 
-// Splat record: 48 bytes, read by the blend kernels through the sorted pair list.
+// Splat record: 64 bytes (two 32-byte sectors), read by the blend kernels through the sorted
+// pair list.
 //   a = (mean2d x, mean2d y, opacity', view depth z)
 //   b = (conic a, conic b, conic c, red)
 //   c = (green, blue, bits(x0 | x1 << 16), bits(y0 | y1 << 16 | camera << 27))
+//   d = (x min, x max, y min, y max) of the region where alpha can reach 1/255, slightly widened:
+//       the blend kernels skip a Gaussian for a whole warp whose pixels all lie outside it.
 struct __align__(16) Rec {
-  float4 a, b, c;
+  float4 a, b, c, d;
 };
+__device__ __forceinline__ int rec_cam(const Rec& r) { return static_cast<int>(__float_as_uint(r.c.w) >> 27); }
 
 template <typename T>
 __device__ __forceinline__ float ldf(const T* p, long long i);
@@ -94,6 +98,7 @@ struct GaussArgs {
   int deg;
   int attr_dtype;
   int sh_dtype;
+  int quat_vec4;       // float32 quaternions on a 16-byte boundary: load each as one float4
 };
 
 struct PreOut {
@@ -101,12 +106,12 @@ struct PreOut {
   uint32_t* depth_keys;        // [cap_v]
   uint32_t* depth_vals;        // [cap_v]
   uint32_t* touched;           // [cap_v] tiles in the rectangle
-  uint32_t* vis_base;          // [n_render]
-  uint32_t* vis_mask;          // [n_render]
-  unsigned long long* status;  // [blocks] chained-scan status words
+  uint32_t* owner;             // [cap_v] rendered index of the Gaussian of each record
+  unsigned long long* status;  // [blocks] chained-scan status words (epoch-tagged)
   uint32_t* counter;           // dynamic block index
   uint32_t* v_total;           // out: V
   int* err;
+  uint32_t epoch;              // tag of this launch's status words
 };
 
 struct Grad2D {  // per visible record: 12 floats, three float4
@@ -122,33 +127,41 @@ struct ParamGrads {
   float* opac;
   float* sh;
   float* absgrad;
+  int vec4;  // quats and SH rows may be stored as float4 (16-byte aligned, 3K % 4 == 0)
 };
 
 // ---- host-side launchers (one per translation unit) -------------------------------------
 
 void launch_preprocess_fwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased,
                            const PreOut& out, int blocks, cudaStream_t s);
-void launch_preprocess_bwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased,
-                           const Rec* rec, const uint32_t* vis_base, const uint32_t* vis_mask,
-                           const Grad2D* g2d, const ParamGrads& out, cudaStream_t s);
+// Runs over the V visible records; the first record of each Gaussian writes its gradient rows
+// (the rows of Gaussians with no record must already be zero).
+void launch_preprocess_bwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased, long long V,
+                           const Rec* rec, const uint32_t* owner, const Grad2D* g2d, const ParamGrads& out,
+                           cudaStream_t s);
+constexpr int kPreThreads = 256;
+constexpr int kPreItems = 4;
+constexpr int kPreTile = kPreThreads * kPreItems;
 
 // Stable radix sort by key bits [begin_bit, end_bit); n taken from *d_n when d_n != nullptr
 // (then max_n bounds it and sizes the launch), else n = max_n.
 struct SortScratch {
   uint32_t* keys_tmp;
   uint32_t* vals_tmp;
-  uint32_t* hist;      // [4][256]
-  uint32_t* status;    // [4][max_blocks][256]
-  uint32_t* counters;  // [4]
-  int max_blocks;
+  uint32_t* hist;                // [4][256]
+  unsigned long long* status;    // [4][tiles][256] epoch-tagged look-back words
+  uint32_t* counters;            // [4]
+  int grid_cap;                  // blocks per onesweep launch (resident blocks loop over tiles)
 };
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;
-size_t sort_status_words(long long max_n);
+size_t sort_status_words(long long max_n);  // 64-bit words per pass
+// epoch: tag for this call's status words (nonzero, below 2^30); clear_status: zero the status
+// words first instead of relying on the tag.
 void radix_sort_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
                     const uint32_t* d_n, long long max_n, int begin_bit, int end_bit, const SortScratch& sc,
-                    int* err, cudaStream_t s);
+                    uint32_t epoch, bool clear_status, int* err, cudaStream_t s);
 
 // Exclusive scan of per-record tile counts in depth order: counts[i] = touched[order[i]]
 // (or cnt_sorted[i] when given), offsets[i] out, *p_total = sum. n from *d_n.
@@ -157,7 +170,7 @@ constexpr int kScanItems = 8;
 void pair_offsets_scan(const uint32_t* touched, const uint32_t* order, const uint32_t* cnt_sorted,
                        uint32_t* offsets, const uint32_t* d_n, long long max_n,
                        unsigned long long* status, uint32_t* counter, unsigned long long* p_total, int* err,
-                       cudaStream_t s);
+                       uint32_t epoch, int grid_cap, cudaStream_t s);
 
 // Duplicate-with-keys (warp-cooperative). count_only: writes cnt_sorted[i] (tile-culled counts).
 void launch_duplicate(const Rec* rec, const uint32_t* order, const uint32_t* offsets, const uint32_t* d_n,

@@ -13,6 +13,8 @@
 // camera) order, with the block offsets from a single-pass chained scan (Merrill & Garland
 // decoupled look-back) whose waits are bounded; within one camera the compacted index grows
 // with the Gaussian index, which gives the depth sort its tie-break.
+#include <type_traits>
+
 #include "gsr_internal.cuh"
 #include "scan_util.cuh"
 
@@ -100,6 +102,8 @@ __device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z
   gy += 6.f * kSH3a * x * y * w[15];
 }
 
+constexpr int kBwdThreads = 128;
+
 // Camera-independent part of a Gaussian.
 struct Geo {
   float m[3];
@@ -122,7 +126,13 @@ __device__ __forceinline__ bool load_geo(const GaussArgs& A, long long g, Geo& G
   G.s[0] = ldf(sc, 3 * g + 0);
   G.s[1] = ldf(sc, 3 * g + 1);
   G.s[2] = ldf(sc, 3 * g + 2);
-  float qw = ldf(qt, 4 * g + 0), qx = ldf(qt, 4 * g + 1), qy = ldf(qt, 4 * g + 2), qz = ldf(qt, 4 * g + 3);
+  float qw, qx, qy, qz;
+  if (std::is_same<AT, float>::value && A.quat_vec4) {
+    const float4 q4 = __ldg(reinterpret_cast<const float4*>(A.quats) + g);
+    qw = q4.x; qx = q4.y; qy = q4.z; qz = q4.w;
+  } else {
+    qw = ldf(qt, 4 * g + 0); qx = ldf(qt, 4 * g + 1); qy = ldf(qt, 4 * g + 2); qz = ldf(qt, 4 * g + 3);
+  }
   G.opac = ldf(op, g);
   const float n2 = qw * qw + qx * qx + qy * qy + qz * qz;
   if (!(n2 > 0.f) || !isfinite(n2)) return false;
@@ -235,215 +245,272 @@ __device__ __forceinline__ void eval_color(const GaussArgs& A, long long g, cons
   const int nb = (A.deg + 1) * (A.deg + 1);
   const ST* sh = static_cast<const ST*>(A.sh) + g * A.K * 3;
   float v0 = 0.5f, v1 = 0.5f, v2 = 0.5f;
-  for (int k = 0; k < nb; ++k) {
-    v0 = fmaf(ldf(sh, 3 * k + 0), Y[k], v0);
-    v1 = fmaf(ldf(sh, 3 * k + 1), Y[k], v1);
-    v2 = fmaf(ldf(sh, 3 * k + 2), Y[k], v2);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    if (k < nb) {
+      v0 = fmaf(ldf(sh, 3 * k + 0), Y[k], v0);
+      v1 = fmaf(ldf(sh, 3 * k + 1), Y[k], v1);
+      v2 = fmaf(ldf(sh, 3 * k + 2), Y[k], v2);
+    }
   }
   clamped[0] = v0 < 0.f; clamped[1] = v1 < 0.f; clamped[2] = v2 < 0.f;
   rgb[0] = fmaxf(v0, 0.f); rgb[1] = fmaxf(v1, 0.f); rgb[2] = fmaxf(v2, 0.f);
 }
 
+// One block covers kPreTile = 1024 consecutive Gaussians, four per thread (thread t owns
+// i = base + j * 256 + t, so each load instruction is coalesced). Phase 1 only decides which
+// cameras see each Gaussian; the per-block count of visible records, packed as four 16-bit
+// lanes (one per j), is scanned in the block, and one warp gets the block's offset from its
+// predecessors' (decoupled look-back). Phase 2 recomputes the visible ones and writes their
+// records in (i, camera) order.
 template <typename AT, typename ST>
-__global__ void __launch_bounds__(256) preprocess_fwd_kernel(GaussArgs A, CamBatch cams, float eps, int aa,
-                                                             PreOut out) {
+__global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArgs A, CamBatch cams, float eps, int aa,
+                                                                       PreOut out) {
   __shared__ unsigned s_bid;
   __shared__ unsigned long long s_excl;
   if (threadIdx.x == 0) s_bid = atomicAdd(out.counter, 1u);
   __syncthreads();
   const unsigned bid = s_bid;
-  const long long i = static_cast<long long>(bid) * blockDim.x + threadIdx.x;
-  const bool valid = i < A.n_render;
-  long long g = 0;
-  Geo G;
-  uint32_t mask = 0;
-  if (valid) {
-    g = seg_map(A.segs, i);
-    if (load_geo<AT>(A, g, G)) {
-      for (int c = 0; c < cams.C; ++c) {
-        Proj P;
-        if (project(G, cams.cam[c], eps, aa, P)) mask |= 1u << c;
+  const long long base_i = static_cast<long long>(bid) * kPreTile;
+  uint32_t mask[kPreItems];
+  unsigned long long packed = 0;
+#pragma unroll
+  for (int j = 0; j < kPreItems; ++j) {
+    const long long i = base_i + j * kPreThreads + threadIdx.x;
+    mask[j] = 0;
+    if (i < A.n_render) {
+      Geo G;
+      if (load_geo<AT>(A, seg_map(A.segs, i), G)) {
+        for (int c = 0; c < cams.C; ++c) {
+          Proj P;
+          if (project(G, cams.cam[c], eps, aa, P)) mask[j] |= 1u << c;
+        }
       }
     }
+    packed |= static_cast<unsigned long long>(__popc(mask[j])) << (16 * j);
   }
-  uint32_t total;
-  const uint32_t excl_t = block_excl_scan(__popc(mask), &total);
-  if (threadIdx.x == 0) s_excl = chained_prefix(out.status, bid, total, out.err);
-  __syncthreads();
-  const unsigned long long base = s_excl + excl_t;
-  if (valid) {
-    out.vis_base[i] = static_cast<uint32_t>(base);
-    out.vis_mask[i] = mask;
-  }
-  if (valid && i == A.n_render - 1) *out.v_total = static_cast<uint32_t>(s_excl + total);
-  if (!mask) return;
-  unsigned long long v = base;
-  for (int c = 0; c < cams.C; ++c) {
-    if (!(mask & (1u << c))) continue;
-    const DevCam& cam = cams.cam[c];
-    Proj P;
-    project(G, cam, eps, aa, P);
-    float rgb[3], dir[3], dn, Y[16];
-    bool cl[3];
-    eval_color<ST>(A, g, G, cam, rgb, dir, dn, Y, cl);
-    Rec r;
-    r.a = make_float4(P.mx, P.my, P.op, P.t[2]);
-    r.b = make_float4(P.ca, P.cb, P.cc, rgb[0]);
-    const uint32_t lo = static_cast<uint32_t>(P.x0) | (static_cast<uint32_t>(P.x1) << 16);
-    const uint32_t hi = static_cast<uint32_t>(P.y0) | (static_cast<uint32_t>(P.y1) << 16) |
-                        (static_cast<uint32_t>(c) << 27);
-    r.c = make_float4(rgb[1], rgb[2], __uint_as_float(lo), __uint_as_float(hi));
-    out.rec[v] = r;
-    out.depth_keys[v] = __float_as_uint(P.t[2]);
-    out.depth_vals[v] = static_cast<uint32_t>(v);
-    out.touched[v] = static_cast<uint32_t>((P.x1 - P.x0) * (P.y1 - P.y0));
-    ++v;
-  }
-}
-
-// Backward of the projection and colour for every (camera, Gaussian) with gradients in g2d.
-template <typename AT, typename ST>
-__global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussArgs A, CamBatch cams, float eps, int aa,
-                                                             const uint32_t* __restrict__ vis_base,
-                                                             const uint32_t* __restrict__ vis_mask,
-                                                             const Grad2D* __restrict__ g2d, ParamGrads out) {
-  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= A.n_render) return;
-  const long long g = seg_map(A.segs, i);
-  const uint32_t mask = vis_mask[i];
-  float dm[3] = {0, 0, 0}, ds[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, dopac = 0.f, dabs[2] = {0, 0};
-  const int KC = A.K * 3;
-  float dsh[48];
+  unsigned long long tot_packed;
+  const unsigned long long excl_packed = block_excl_scan64(packed, &tot_packed);
+  uint32_t lane_base[kPreItems];
+  uint32_t total = 0;
 #pragma unroll
-  for (int k = 0; k < 48; ++k) dsh[k] = 0.f;
-  Geo G;
-  if (mask && load_geo<AT>(A, g, G)) {
-    float dR[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    unsigned long long v = vis_base[i];
-    const int nb = (A.deg + 1) * (A.deg + 1);
-    const ST* sh = static_cast<const ST*>(A.sh) + g * KC;
+  for (int j = 0; j < kPreItems; ++j) {
+    lane_base[j] = total;
+    total += static_cast<uint32_t>((tot_packed >> (16 * j)) & 0xffffu);
+  }
+  if (threadIdx.x < 32) {
+    const unsigned long long ex = warp_chained_prefix(out.status, bid, total, out.epoch, out.err);
+    if (threadIdx.x == 0) s_excl = ex;
+  }
+  __syncthreads();
+  const unsigned long long block_base = s_excl;
+  if (threadIdx.x == 0 && base_i <= A.n_render - 1 && A.n_render - 1 < base_i + kPreTile)
+    *out.v_total = static_cast<uint32_t>(block_base + total);
+#pragma unroll
+  for (int j = 0; j < kPreItems; ++j) {
+    if (!mask[j]) continue;
+    const long long i = base_i + j * kPreThreads + threadIdx.x;
+    const long long g = seg_map(A.segs, i);
+    Geo G;
+    load_geo<AT>(A, g, G);
+    unsigned long long v = block_base + lane_base[j] + ((excl_packed >> (16 * j)) & 0xffffu);
     for (int c = 0; c < cams.C; ++c) {
-      if (!(mask & (1u << c))) continue;
+      if (!(mask[j] & (1u << c))) continue;
       const DevCam& cam = cams.cam[c];
       Proj P;
       project(G, cam, eps, aa, P);
-      const Grad2D gd = g2d[v];
-      ++v;
-      const float dmx = gd.a.x, dmy = gd.a.y, dop = gd.a.z, ddepth = gd.a.w;
-      const float dca = gd.b.x, dcb = gd.b.y, dcc = gd.b.z;
-      float drgb[3] = {gd.b.w, gd.c.x, gd.c.y};
-      dabs[0] += gd.c.z;
-      dabs[1] += gd.c.w;
-      // colour: rgb = max(0, sum_k sh_k Y_k(dir) + 0.5)
       float rgb[3], dir[3], dn, Y[16];
       bool cl[3];
       eval_color<ST>(A, g, G, cam, rgb, dir, dn, Y, cl);
-      float wY[16];
-      for (int ch = 0; ch < 3; ++ch)
-        if (cl[ch]) drgb[ch] = 0.f;
-      for (int k = 0; k < nb; ++k) {
+      Rec r;
+      r.a = make_float4(P.mx, P.my, P.op, P.t[2]);
+      r.b = make_float4(P.ca, P.cb, P.cc, rgb[0]);
+      const uint32_t lo = static_cast<uint32_t>(P.x0) | (static_cast<uint32_t>(P.x1) << 16);
+      const uint32_t hi = static_cast<uint32_t>(P.y0) | (static_cast<uint32_t>(P.y1) << 16) |
+                          (static_cast<uint32_t>(c) << 27);
+      r.c = make_float4(rgb[1], rgb[2], __uint_as_float(lo), __uint_as_float(hi));
+      // Where op' exp(-d^T Q d / 2) >= 1/255, i.e. d^T Q d <= 2 ln(255 op'): an ellipse whose
+      // half-extents are sqrt(2 ln(255 op') Sigma_xx) and sqrt(2 ln(255 op') Sigma_yy), Sigma the
+      // dilated covariance. Widened by 0.1% + 0.01 px so FP32 evaluation never falls outside.
+      const float L = logf(255.f * P.op);
+      if (L > 0.f) {
+        const float ex = sqrtf(2.f * L * (P.ar + eps)) * 1.001f + 0.01f;
+        const float ey = sqrtf(2.f * L * (P.cr + eps)) * 1.001f + 0.01f;
+        r.d = make_float4(P.mx - ex, P.mx + ex, P.my - ey, P.my + ey);
+      } else {
+        r.d = make_float4(1.f, -1.f, 1.f, -1.f);  // empty: no pixel reaches 1/255
+      }
+      out.rec[v] = r;
+      out.depth_keys[v] = __float_as_uint(P.t[2]);
+      out.depth_vals[v] = static_cast<uint32_t>(v);
+      out.touched[v] = static_cast<uint32_t>((P.x1 - P.x0) * (P.y1 - P.y0));
+      out.owner[v] = static_cast<uint32_t>(i);
+      ++v;
+    }
+  }
+}
+
+// Backward of the projection and colour. One thread per visible record; the thread holding a
+// Gaussian's first record walks all of that Gaussian's cameras (its records are consecutive),
+// accumulates the parameter gradients in registers and writes the Gaussian's rows once.
+template <typename AT, typename ST>
+__global__ void __launch_bounds__(kBwdThreads) preprocess_bwd_kernel(
+    GaussArgs A, CamBatch cams, float eps, int aa, long long V, const Rec* __restrict__ rec,
+    const uint32_t* __restrict__ owner, const Grad2D* __restrict__ g2d, ParamGrads out) {
+  const long long v0 = static_cast<long long>(blockIdx.x) * kBwdThreads + threadIdx.x;
+  if (v0 >= V) return;
+  const uint32_t i = owner[v0];
+  if (v0 > 0 && owner[v0 - 1] == i) return;  // not the Gaussian's first record
+  const long long g = seg_map(A.segs, i);
+  Geo G;
+  if (!load_geo<AT>(A, g, G)) return;  // cannot happen for a Gaussian with a record
+  float dm[3] = {0, 0, 0}, ds[3] = {0, 0, 0}, dopac = 0.f, dabs[2] = {0, 0};
+  float dsh[48];
+#pragma unroll
+  for (int k = 0; k < 48; ++k) dsh[k] = 0.f;
+  float dR[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const int KC = A.K * 3;
+  const int nb = (A.deg + 1) * (A.deg + 1);
+  const ST* sh = static_cast<const ST*>(A.sh) + g * KC;
+  for (long long v = v0; v < V && owner[v] == i; ++v) {
+    const DevCam& cam = cams.cam[rec_cam(rec[v])];
+    Proj P;
+    project(G, cam, eps, aa, P);
+    const Grad2D gd = g2d[v];
+    const float dmx = gd.a.x, dmy = gd.a.y, dop = gd.a.z, ddepth = gd.a.w;
+    const float dca = gd.b.x, dcb = gd.b.y, dcc = gd.b.z;
+    float drgb[3] = {gd.b.w, gd.c.x, gd.c.y};
+    dabs[0] += gd.c.z;
+    dabs[1] += gd.c.w;
+    // colour: rgb = max(0, sum_k sh_k Y_k(dir) + 0.5)
+    float rgb[3], dir[3], dn, Y[16];
+    bool cl[3];
+    eval_color<ST>(A, g, G, cam, rgb, dir, dn, Y, cl);
+    for (int ch = 0; ch < 3; ++ch)
+      if (cl[ch]) drgb[ch] = 0.f;
+    float wY[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      wY[k] = 0.f;
+      if (k < nb) {
         dsh[3 * k + 0] += Y[k] * drgb[0];
         dsh[3 * k + 1] += Y[k] * drgb[1];
         dsh[3 * k + 2] += Y[k] * drgb[2];
         wY[k] = ldf(sh, 3 * k) * drgb[0] + ldf(sh, 3 * k + 1) * drgb[1] + ldf(sh, 3 * k + 2) * drgb[2];
       }
-      float gx, gy, gz;
-      sh_basis_grad(A.deg, dir[0], dir[1], dir[2], wY, gx, gy, gz);
-      const float proj = gx * dir[0] + gy * dir[1] + gz * dir[2];
-      const float idn = 1.f / dn;
-      dm[0] += (gx - dir[0] * proj) * idn;
-      dm[1] += (gy - dir[1] * proj) * idn;
-      dm[2] += (gz - dir[2] * proj) * idn;
-      // conic = inverse of the dilated Sigma2D: dSigma2D = -M G M
-      const float g00 = dca, g01 = 0.5f * dcb, g11 = dcc;
-      const float mg00 = P.ca * g00 + P.cb * g01, mg01 = P.ca * g01 + P.cb * g11;
-      const float mg10 = P.cb * g00 + P.cc * g01, mg11 = P.cb * g01 + P.cc * g11;
-      float da = -(mg00 * P.ca + mg01 * P.cb);
-      float db = -2.f * (mg00 * P.cb + mg01 * P.cc);
-      float dc = -(mg10 * P.cb + mg11 * P.cc);
-      // opacity' = opacity * sqrt(det_raw / det)
-      dopac += dop * P.comp;
-      if (aa && P.comp > 0.f) {
-        const float ratio = P.comp * P.comp;
-        const float dratio = dop * G.opac * 0.5f / P.comp;
-        const float ddr = dratio * P.idet;          // d det_raw
-        const float ddt = -dratio * ratio * P.idet; // d det
-        const float a = P.ar + eps, cc = P.cr + eps;
-        da += ddr * P.cr + ddt * cc;
-        dc += ddr * P.ar + ddt * a;
-        db += -2.f * P.br * (ddr + ddt);
-      }
-      // Sigma2D_raw = T Sigma T^T with T = J W
-      float dT0[3], dT1[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        dT0[k] = 2.f * da * P.ST0[k] + db * P.ST1[k];
-        dT1[k] = db * P.ST0[k] + 2.f * dc * P.ST1[k];
-      }
-      // dSigma (symmetrised) = 2 da T0 T0^T + db (T0 T1^T + T1 T0^T) + 2 dc T1 T1^T, then
-      // Sigma = M M^T: dM = dSigma_sym M.
-      float dS[9];
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-          dS[r * 3 + q] = 2.f * da * P.T0[r] * P.T0[q] + db * (P.T0[r] * P.T1[q] + P.T1[r] * P.T0[q]) +
-                          2.f * dc * P.T1[r] * P.T1[q];
-      float Mx[9];
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) Mx[r * 3 + q] = G.R[r * 3 + q] * G.s[q];
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const float dM = dS[r * 3 + 0] * Mx[0 * 3 + q] + dS[r * 3 + 1] * Mx[1 * 3 + q] + dS[r * 3 + 2] * Mx[2 * 3 + q];
-          dR[r * 3 + q] += dM * G.s[q];
-          ds[q] += dM * G.R[r * 3 + q];
-        }
-      // T = J W: dJ
-      const float* W = cam.R;
-      const float dJ00 = dT0[0] * W[0] + dT0[1] * W[1] + dT0[2] * W[2];
-      const float dJ02 = dT0[0] * W[6] + dT0[1] * W[7] + dT0[2] * W[8];
-      const float dJ11 = dT1[0] * W[3] + dT1[1] * W[4] + dT1[2] * W[5];
-      const float dJ12 = dT1[0] * W[6] + dT1[1] * W[7] + dT1[2] * W[8];
-      const float uc = fminf(fmaxf(P.u, -cam.limx), cam.limx);
-      const float wc = fminf(fmaxf(P.w, -cam.limy), cam.limy);
-      const float iz2 = P.iz * P.iz;
-      float dt[3] = {0.f, 0.f, 0.f};
-      dt[2] += -cam.fx * iz2 * dJ00 + cam.fx * uc * iz2 * dJ02 - cam.fy * iz2 * dJ11 + cam.fy * wc * iz2 * dJ12;
-      const float duc = -cam.fx * P.iz * dJ02, dwc = -cam.fy * P.iz * dJ12;
-      if (!P.clx) { dt[0] += duc * P.iz; dt[2] -= duc * P.u * P.iz; }
-      if (!P.cly) { dt[1] += dwc * P.iz; dt[2] -= dwc * P.w * P.iz; }
-      // mean2d = (fx X/Z + cx, fy Y/Z + cy); depth = Z
-      dt[0] += cam.fx * P.iz * dmx;
-      dt[1] += cam.fy * P.iz * dmy;
-      dt[2] += -cam.fx * P.t[0] * iz2 * dmx - cam.fy * P.t[1] * iz2 * dmy + ddepth;
-      // t = W mu + t_cam
-      dm[0] += W[0] * dt[0] + W[3] * dt[1] + W[6] * dt[2];
-      dm[1] += W[1] * dt[0] + W[4] * dt[1] + W[7] * dt[2];
-      dm[2] += W[2] * dt[0] + W[5] * dt[1] + W[8] * dt[2];
     }
-    // rotation from the normalised quaternion, then through the normalisation
-    const float w = G.q[0], x = G.q[1], y = G.q[2], z = G.q[3];
-    float dqn[4];
-    dqn[0] = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
-    dqn[1] = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
-                    2.f * x * dR[8]);
-    dqn[2] = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] -
-                    2.f * y * dR[8]);
-    dqn[3] = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
-                    x * dR[6] + y * dR[7]);
-    const float qd = w * dqn[0] + x * dqn[1] + y * dqn[2] + z * dqn[3];
-    for (int k = 0; k < 4; ++k) dq[k] = (dqn[k] - G.q[k] * qd) * G.qinv;
+    float gx, gy, gz;
+    sh_basis_grad(A.deg, dir[0], dir[1], dir[2], wY, gx, gy, gz);
+    const float proj = gx * dir[0] + gy * dir[1] + gz * dir[2];
+    const float idn = 1.f / dn;
+    dm[0] += (gx - dir[0] * proj) * idn;
+    dm[1] += (gy - dir[1] * proj) * idn;
+    dm[2] += (gz - dir[2] * proj) * idn;
+    // conic = inverse of the dilated Sigma2D: dSigma2D = -M G M
+    const float g00 = dca, g01 = 0.5f * dcb, g11 = dcc;
+    const float mg00 = P.ca * g00 + P.cb * g01, mg01 = P.ca * g01 + P.cb * g11;
+    const float mg10 = P.cb * g00 + P.cc * g01, mg11 = P.cb * g01 + P.cc * g11;
+    float da = -(mg00 * P.ca + mg01 * P.cb);
+    float db = -2.f * (mg00 * P.cb + mg01 * P.cc);
+    float dc = -(mg10 * P.cb + mg11 * P.cc);
+    // opacity' = opacity * sqrt(det_raw / det)
+    dopac += dop * P.comp;
+    if (aa && P.comp > 0.f) {
+      const float ratio = P.comp * P.comp;
+      const float dratio = dop * G.opac * 0.5f / P.comp;
+      const float ddr = dratio * P.idet;           // d det_raw
+      const float ddt = -dratio * ratio * P.idet;  // d det
+      const float a = P.ar + eps, cc = P.cr + eps;
+      da += ddr * P.cr + ddt * cc;
+      dc += ddr * P.ar + ddt * a;
+      db += -2.f * P.br * (ddr + ddt);
+    }
+    // Sigma2D_raw = T Sigma T^T with T = J W
+    float dT0[3], dT1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      dT0[k] = 2.f * da * P.ST0[k] + db * P.ST1[k];
+      dT1[k] = db * P.ST0[k] + 2.f * dc * P.ST1[k];
+    }
+    // dSigma (symmetrised) = 2 da T0 T0^T + db (T0 T1^T + T1 T0^T) + 2 dc T1 T1^T; Sigma = M M^T
+    float dS[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        dS[r * 3 + q] = 2.f * da * P.T0[r] * P.T0[q] + db * (P.T0[r] * P.T1[q] + P.T1[r] * P.T0[q]) +
+                        2.f * dc * P.T1[r] * P.T1[q];
+    float Mx[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) Mx[r * 3 + q] = G.R[r * 3 + q] * G.s[q];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float dM = dS[r * 3 + 0] * Mx[0 * 3 + q] + dS[r * 3 + 1] * Mx[1 * 3 + q] + dS[r * 3 + 2] * Mx[2 * 3 + q];
+        dR[r * 3 + q] += dM * G.s[q];
+        ds[q] += dM * G.R[r * 3 + q];
+      }
+    // T = J W: dJ
+    const float* W = cam.R;
+    const float dJ00 = dT0[0] * W[0] + dT0[1] * W[1] + dT0[2] * W[2];
+    const float dJ02 = dT0[0] * W[6] + dT0[1] * W[7] + dT0[2] * W[8];
+    const float dJ11 = dT1[0] * W[3] + dT1[1] * W[4] + dT1[2] * W[5];
+    const float dJ12 = dT1[0] * W[6] + dT1[1] * W[7] + dT1[2] * W[8];
+    const float uc = fminf(fmaxf(P.u, -cam.limx), cam.limx);
+    const float wc = fminf(fmaxf(P.w, -cam.limy), cam.limy);
+    const float iz2 = P.iz * P.iz;
+    float dt[3] = {0.f, 0.f, 0.f};
+    dt[2] += -cam.fx * iz2 * dJ00 + cam.fx * uc * iz2 * dJ02 - cam.fy * iz2 * dJ11 + cam.fy * wc * iz2 * dJ12;
+    const float duc = -cam.fx * P.iz * dJ02, dwc = -cam.fy * P.iz * dJ12;
+    if (!P.clx) { dt[0] += duc * P.iz; dt[2] -= duc * P.u * P.iz; }
+    if (!P.cly) { dt[1] += dwc * P.iz; dt[2] -= dwc * P.w * P.iz; }
+    // mean2d = (fx X/Z + cx, fy Y/Z + cy); depth = Z
+    dt[0] += cam.fx * P.iz * dmx;
+    dt[1] += cam.fy * P.iz * dmy;
+    dt[2] += -cam.fx * P.t[0] * iz2 * dmx - cam.fy * P.t[1] * iz2 * dmy + ddepth;
+    // t = W mu + t_cam
+    dm[0] += W[0] * dt[0] + W[3] * dt[1] + W[6] * dt[2];
+    dm[1] += W[1] * dt[0] + W[4] * dt[1] + W[7] * dt[2];
+    dm[2] += W[2] * dt[0] + W[5] * dt[1] + W[8] * dt[2];
   }
-  for (int k = 0; k < 3; ++k) out.means[3 * g + k] = dm[k];
-  for (int k = 0; k < 3; ++k) out.scales[3 * g + k] = ds[k];
-  for (int k = 0; k < 4; ++k) out.quats[4 * g + k] = dq[k];
+  // rotation from the normalised quaternion, then through the normalisation
+  const float w = G.q[0], x = G.q[1], y = G.q[2], z = G.q[3];
+  float dqn[4];
+  dqn[0] = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+  dqn[1] = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
+                  2.f * x * dR[8]);
+  dqn[2] = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] -
+                  2.f * y * dR[8]);
+  dqn[3] = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
+                  x * dR[6] + y * dR[7]);
+  const float qd = w * dqn[0] + x * dqn[1] + y * dqn[2] + z * dqn[3];
+  float dq[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) dq[k] = (dqn[k] - G.q[k] * qd) * G.qinv;
+  out.means[3 * g + 0] = dm[0];
+  out.means[3 * g + 1] = dm[1];
+  out.means[3 * g + 2] = dm[2];
+  out.scales[3 * g + 0] = ds[0];
+  out.scales[3 * g + 1] = ds[1];
+  out.scales[3 * g + 2] = ds[2];
   out.opac[g] = dopac;
-  float* gsh = out.sh + g * KC;
-  for (int k = 0; k < KC; ++k) gsh[k] = k < 48 ? dsh[k] : 0.f;
+  if (out.vec4) {
+    reinterpret_cast<float4*>(out.quats)[g] = make_float4(dq[0], dq[1], dq[2], dq[3]);
+    float4* row = reinterpret_cast<float4*>(out.sh + g * KC);
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+      if (4 * k < KC) row[k] = make_float4(dsh[4 * k], dsh[4 * k + 1], dsh[4 * k + 2], dsh[4 * k + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out.quats[4 * g + k] = dq[k];
+    float* row = out.sh + g * KC;
+#pragma unroll
+    for (int k = 0; k < 48; ++k)
+      if (k < KC) row[k] = dsh[k];
+  }
   if (out.absgrad) {
     out.absgrad[2 * g] = dabs[0];
     out.absgrad[2 * g + 1] = dabs[1];
@@ -453,14 +520,15 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussArgs A, CamBat
 template <typename AT, typename ST>
 void launch_fwd_t(const GaussArgs& g, const CamBatch& cams, float eps, int aa, const PreOut& out, int blocks,
                   cudaStream_t s) {
-  preprocess_fwd_kernel<AT, ST><<<blocks, 256, 0, s>>>(g, cams, eps, aa, out);
+  preprocess_fwd_kernel<AT, ST><<<blocks, kPreThreads, 0, s>>>(g, cams, eps, aa, out);
 }
 
 template <typename AT, typename ST>
-void launch_bwd_t(const GaussArgs& g, const CamBatch& cams, float eps, int aa, const uint32_t* vb,
-                  const uint32_t* vm, const Grad2D* g2d, const ParamGrads& out, cudaStream_t s) {
-  const int blocks = static_cast<int>((g.n_render + 127) / 128);
-  if (blocks > 0) preprocess_bwd_kernel<AT, ST><<<blocks, 128, 0, s>>>(g, cams, eps, aa, vb, vm, g2d, out);
+void launch_bwd_t(const GaussArgs& g, const CamBatch& cams, float eps, int aa, long long V, const Rec* rec,
+                  const uint32_t* owner, const Grad2D* g2d, const ParamGrads& out, cudaStream_t s) {
+  const int blocks = static_cast<int>((V + kBwdThreads - 1) / kBwdThreads);
+  if (blocks > 0)
+    preprocess_bwd_kernel<AT, ST><<<blocks, kBwdThreads, 0, s>>>(g, cams, eps, aa, V, rec, owner, g2d, out);
 }
 
 }  // namespace
@@ -481,10 +549,10 @@ void launch_preprocess_fwd(const GaussArgs& g, const CamBatch& cams, float eps2d
 #undef GSR_PRE
 }
 
-void launch_preprocess_bwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased,
-                           const Rec* /*rec*/, const uint32_t* vis_base, const uint32_t* vis_mask,
-                           const Grad2D* g2d, const ParamGrads& out, cudaStream_t s) {
-#define GSR_PREB(AT, ST) launch_bwd_t<AT, ST>(g, cams, eps2d, antialiased, vis_base, vis_mask, g2d, out, s)
+void launch_preprocess_bwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased, long long V,
+                           const Rec* rec, const uint32_t* owner, const Grad2D* g2d, const ParamGrads& out,
+                           cudaStream_t s) {
+#define GSR_PREB(AT, ST) launch_bwd_t<AT, ST>(g, cams, eps2d, antialiased, V, rec, owner, g2d, out, s)
   if (g.attr_dtype == 0 && g.sh_dtype == 0) GSR_PREB(float, float);
   else if (g.attr_dtype == 0 && g.sh_dtype == 1) GSR_PREB(float, __half);
   else if (g.attr_dtype == 0 && g.sh_dtype == 2) GSR_PREB(float, __nv_bfloat16);

@@ -42,6 +42,20 @@ __device__ __forceinline__ float tile_min_maha(float mx, float my, float a, floa
   return best;
 }
 
+// Bit w set when the Gaussian's alpha >= 1/255 box (record field d) meets the pixel centres
+// of warp w, i.e. rows 2w and 2w+1 of the tile (x in [x_lo, x_hi], rows from y_base).
+__device__ __forceinline__ uint32_t warp_rows_mask(const float4 d, float x_lo, float x_hi, float y_base) {
+  uint32_t m = 0;
+  if (d.y >= x_lo && d.x <= x_hi) {
+#pragma unroll
+    for (int w = 0; w < kTilePix / 32; ++w) {
+      const float yc = y_base + 2.f * w;
+      if (d.w >= yc && d.z <= yc + 1.f) m |= 1u << w;
+    }
+  }
+  return m;
+}
+
 template <bool kCull, bool kCount>
 __global__ void __launch_bounds__(256) duplicate_kernel(const Rec* __restrict__ rec, const uint32_t* __restrict__ order,
                                                         const uint32_t* __restrict__ offsets, const uint32_t* d_n,
@@ -150,15 +164,18 @@ __global__ void __launch_bounds__(kTilePix) blend_fwd_kernel(const Rec* __restri
   __shared__ float4 sA[kTilePix];
   __shared__ float4 sB[kTilePix];
   __shared__ float2 sC[kTilePix];
+  __shared__ uint32_t sM[kTilePix];
   const int t = blockIdx.x;
   const int c = find_cam(cams, t);
   const DevCam& cam = cams.cam[c];
   const int lt = t - cam.tile_off;
   const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, wid = tid >> 5;
   const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + (tid >> 4);
   const bool inside = px < cam.W && py < cam.H;
   const float fx = px + 0.5f, fy = py + 0.5f;
+  const float x_lo = tx * kTile + 0.5f, x_hi = fminf(static_cast<float>((tx + 1) * kTile), cam.W) - 0.5f;
+  const float y_base = ty * kTile + 0.5f;
   const uint2 range = ranges[t];
   const int n = static_cast<int>(range.y - range.x);
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
@@ -173,10 +190,12 @@ __global__ void __launch_bounds__(kTilePix) blend_fwd_kernel(const Rec* __restri
       sA[tid] = r.a;
       sB[tid] = r.b;
       sC[tid] = make_float2(r.c.x, r.c.y);
+      sM[tid] = warp_rows_mask(r.d, x_lo, x_hi, y_base);
     }
     __syncthreads();
     const int cnt = min(kTilePix, n - base);
     for (int j = 0; j < cnt && !done; ++j) {
+      if (!((sM[j] >> wid) & 1u)) continue;  // no pixel of this warp can reach alpha 1/255
       const float4 a = sA[j];
       const float4 b = sB[j];
       ++n_eval;
@@ -255,6 +274,7 @@ __global__ void __launch_bounds__(kTilePix) blend_bwd_kernel(const Rec* __restri
   __shared__ float4 sB[kTilePix];
   __shared__ float2 sC[kTilePix];
   __shared__ uint32_t sV[kTilePix];
+  __shared__ uint32_t sM[kTilePix];
   __shared__ float sAcc[kTilePix][kGradVals + 1];
   __shared__ uint32_t s_max;
   __shared__ float s_aff[8][12];
@@ -267,6 +287,8 @@ __global__ void __launch_bounds__(kTilePix) blend_bwd_kernel(const Rec* __restri
   const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + (tid >> 4);
   const bool inside = px < cam.W && py < cam.H;
   const float fx = px + 0.5f, fy = py + 0.5f;
+  const float x_lo = tx * kTile + 0.5f, x_hi = fminf(static_cast<float>((tx + 1) * kTile), cam.W) - 0.5f;
+  const float y_base = ty * kTile + 0.5f;
   const uint2 range = ranges[t];
   if (tid == 0) s_max = 0;
   __syncthreads();
@@ -298,6 +320,12 @@ __global__ void __launch_bounds__(kTilePix) blend_bwd_kernel(const Rec* __restri
   const float GD = gda + gde / fmaxf(aout, 1e-10f);
   const float ga_eff = gal + (aout > 1e-10f ? -gde * D / (aout * aout) : 0.f);
   const float GT = g0 * (bg.x - bb0) + g1 * (bg.y - bb1) + g2 * (bg.z - bb2) - ga_eff;
+  // Depths are carried relative to the pixel's expected depth zr: with z_i = zr + d_i the depth
+  // part of dL/dalpha_i, T_i z_i - S_D / (1 - a_i), equals T_i d_i - S_d / (1 - a_i)
+  // + zr T_final / (1 - a_i) (the weights behind i sum to T_{i+1} - T_final), which avoids the
+  // FP32 cancellation of two large, nearly equal terms when the contributors lie at similar depth.
+  const float zr = aout > 1e-10f ? D / aout : 0.f;
+  const float GTz = GD * zr - GT;
   __syncthreads();
   const int n = static_cast<int>(s_max);
   float T = Tf;
@@ -313,12 +341,14 @@ __global__ void __launch_bounds__(kTilePix) blend_bwd_kernel(const Rec* __restri
       sB[tid] = r.b;
       sC[tid] = make_float2(r.c.x, r.c.y);
       sV[tid] = v;
+      sM[tid] = warp_rows_mask(r.d, x_lo, x_hi, y_base);
     }
 #pragma unroll
     for (int k = 0; k < kGradVals; ++k) sAcc[tid][k] = 0.f;
     __syncthreads();
     const int cnt = min(kTilePix, n - base);
     for (int j = 0; j < cnt; ++j) {
+      if (!((sM[j] >> wid) & 1u)) continue;  // warp-uniform: no pixel of this warp is touched
       const uint32_t pos = static_cast<uint32_t>(n - 1 - base - j);
       float gv[kGradVals];
 #pragma unroll
@@ -341,12 +371,13 @@ __global__ void __launch_bounds__(kTilePix) blend_bwd_kernel(const Rec* __restri
             const float Ti = T / om;
             const float2 cc = sC[j];
             const float wgt = alpha * Ti;
-            const float dal = Ti * (GC0 * b.w + GC1 * cc.x + GC2 * cc.y + GD * a.w) -
-                              (GC0 * S0 + GC1 * S1 + GC2 * S2 + GD * SD + GT * Tf) / om;
+            const float dz = a.w - zr;
+            const float dal = Ti * (GC0 * b.w + GC1 * cc.x + GC2 * cc.y + GD * dz) +
+                              (GTz * Tf - (GC0 * S0 + GC1 * S1 + GC2 * S2 + GD * SD)) / om;
             S0 = fmaf(b.w, wgt, S0);
             S1 = fmaf(cc.x, wgt, S1);
             S2 = fmaf(cc.y, wgt, S2);
-            SD = fmaf(a.w, wgt, SD);
+            SD = fmaf(dz, wgt, SD);
             T = Ti;
             const float draw = araw > kAlphaMax ? 0.f : dal;
             const float dsig = -draw * araw;

@@ -1,4 +1,8 @@
-// Block-level scan helpers shared by the chained-scan kernels.
+// Block-level scan helpers and the decoupled look-back of the chained-scan kernels.
+//
+// Status words are 64 bits: [63:34] epoch, [33:32] flag (1 = aggregate, 2 = inclusive prefix),
+// [31:0] value. A word whose epoch differs from the launch's is "not ready", so the status
+// arrays never need clearing between launches: the host hands every launch a new epoch.
 #pragma once
 
 #include <cuda/atomic>
@@ -6,6 +10,26 @@
 #include "gsr_internal.cuh"
 
 namespace gsr {
+
+constexpr uint32_t kStatusAgg = 1u;
+constexpr uint32_t kStatusPrefix = 2u;
+
+__device__ __forceinline__ unsigned long long pack_status(uint32_t epoch, uint32_t flag, uint32_t value) {
+  return (static_cast<unsigned long long>(epoch) << 34) | (static_cast<unsigned long long>(flag) << 32) | value;
+}
+
+__device__ __forceinline__ void store_status(unsigned long long* p, unsigned long long v) {
+  cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>(*p).store(v, cuda::memory_order_relaxed);
+}
+
+__device__ __forceinline__ unsigned long long load_status(unsigned long long* p) {
+  return cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>(*p).load(cuda::memory_order_relaxed);
+}
+
+// Flag of a status word for this epoch (0 = not ready).
+__device__ __forceinline__ uint32_t status_flag(unsigned long long s, uint32_t epoch) {
+  return (static_cast<uint32_t>(s >> 34) == epoch) ? static_cast<uint32_t>((s >> 32) & 3u) : 0u;
+}
 
 // 256-thread exclusive scan of one value per thread; returns the block total through *total.
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* total) {
@@ -38,38 +62,83 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* total)
   return r;
 }
 
-// Decoupled look-back for block `bid`: publishes the block aggregate, waits (bounded) for the
-// predecessors' prefixes and returns this block's exclusive prefix. One thread per block.
-__device__ __forceinline__ unsigned long long chained_prefix(unsigned long long* status, unsigned bid, unsigned long long agg,
-                                             int* err) {
-  constexpr unsigned long long kA = 1ull << 62, kP = 2ull << 62, kMask = (1ull << 62) - 1;
-  cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> me(status[bid]);
+// 256-thread exclusive scan of one 64-bit value per thread (used with four independent 16-bit
+// lanes packed in one word: no lane's total may exceed 65535). Returns the block total too.
+__device__ __forceinline__ unsigned long long block_excl_scan64(unsigned long long x, unsigned long long* total) {
+  __shared__ unsigned long long warp_sums64[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) warp_sums64[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    const unsigned long long s = lane < nw ? warp_sums64[lane] : 0ull;
+    unsigned long long si = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, si, o);
+      if (lane >= o) si += y;
+    }
+    if (lane < nw) warp_sums64[lane] = si - s;
+    if (lane == nw - 1) warp_sums64[31] = si;
+  }
+  __syncthreads();
+  const unsigned long long r = warp_sums64[wid] + inc - x;
+  *total = warp_sums64[31];
+  __syncthreads();
+  return r;
+}
+
+// Decoupled look-back for tile `bid`, run by all 32 lanes of one warp: publishes the tile's
+// aggregate, then reads 32 predecessors at a time, waiting (bounded) until every one of them
+// up to the nearest inclusive prefix is ready, and sums them. Returns this tile's exclusive
+// prefix in every lane and publishes its inclusive prefix. Values are 32-bit; the running
+// total is 64-bit and the caller checks it for overflow.
+__device__ __forceinline__ unsigned long long warp_chained_prefix(unsigned long long* status, uint32_t bid,
+                                                                  uint32_t agg, uint32_t epoch, int* err) {
+  const int lane = threadIdx.x & 31;
   if (bid == 0) {
-    me.store(kP | agg, cuda::memory_order_relaxed);
+    if (lane == 0) store_status(status, pack_status(epoch, kStatusPrefix, agg));
     return 0;
   }
-  me.store(kA | agg, cuda::memory_order_relaxed);
+  if (lane == 0) store_status(status + bid, pack_status(epoch, kStatusAgg, agg));
   unsigned long long excl = 0;
-  long long j = static_cast<long long>(bid) - 1;
+  long long end = static_cast<long long>(bid) - 1;
   unsigned spins = 0, ns = 32;
-  while (j >= 0) {
-    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> st(status[j]);
-    const unsigned long long s = st.load(cuda::memory_order_relaxed);
-    const unsigned long long f = s >> 62;
-    if (f == 0) {
+  for (;;) {
+    const long long j = end - lane;
+    uint32_t flag = kStatusPrefix, val = 0;  // before tile 0: an inclusive prefix of 0
+    if (j >= 0) {
+      const unsigned long long s = load_status(status + j);
+      flag = status_flag(s, epoch);
+      val = static_cast<uint32_t>(s);
+    }
+    const uint32_t pm = __ballot_sync(0xffffffffu, flag == kStatusPrefix);
+    const uint32_t xm = __ballot_sync(0xffffffffu, flag == 0u);
+    const uint32_t upto = pm ? (((pm & (0u - pm)) << 1) - 1u) : 0xffffffffu;
+    if (xm & upto) {
       if (++spins > kSpinLimit) {
-        atomicOr(err, kErrTimeout);
+        if (lane == 0) atomicOr(err, kErrTimeout);
         break;
       }
       __nanosleep(ns);
       if (ns < 1024) ns <<= 1;
       continue;
     }
-    excl += s & kMask;
-    if (f == 2) break;
-    --j;
+    unsigned long long v = ((upto >> lane) & 1u) ? val : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    excl += v;
+    if (pm) break;
+    end -= 32;
   }
-  me.store(kP | (excl + agg), cuda::memory_order_relaxed);
+  if (lane == 0)
+    store_status(status + bid, pack_status(epoch, kStatusPrefix, static_cast<uint32_t>(excl + agg)));
   return excl;
 }
 

@@ -17,10 +17,6 @@
 namespace gsr {
 namespace {
 
-constexpr uint32_t kFlagA = 1u << 30;
-constexpr uint32_t kFlagP = 2u << 30;
-constexpr uint32_t kValMask = (1u << 30) - 1;
-
 __device__ __forceinline__ long long device_n(const uint32_t* d_n, long long max_n) {
   if (!d_n) return max_n;
   const long long n = static_cast<long long>(*d_n);
@@ -57,20 +53,20 @@ __global__ void __launch_bounds__(256) hist_scan_kernel(uint32_t* hist) {
   h[threadIdx.x] = e;
 }
 
-__device__ __forceinline__ uint32_t lookback_digit(uint32_t* status, uint32_t bid, int d, uint32_t agg, int* err) {
-  cuda::atomic_ref<uint32_t, cuda::thread_scope_device> me(status[static_cast<size_t>(bid) * 256 + d]);
+__device__ __forceinline__ uint32_t lookback_digit(unsigned long long* status, uint32_t bid, int d, uint32_t agg,
+                                                   uint32_t epoch, int* err) {
+  unsigned long long* me = status + static_cast<size_t>(bid) * 256 + d;
   if (bid == 0) {
-    me.store(kFlagP | agg, cuda::memory_order_relaxed);
+    store_status(me, pack_status(epoch, kStatusPrefix, agg));
     return 0;
   }
-  me.store(kFlagA | agg, cuda::memory_order_relaxed);
+  store_status(me, pack_status(epoch, kStatusAgg, agg));
   uint32_t excl = 0;
   long long j = static_cast<long long>(bid) - 1;
   unsigned spins = 0, ns = 32;
   while (j >= 0) {
-    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> st(status[static_cast<size_t>(j) * 256 + d]);
-    const uint32_t s = st.load(cuda::memory_order_relaxed);
-    const uint32_t f = s >> 30;
+    const unsigned long long s = load_status(status + static_cast<size_t>(j) * 256 + d);
+    const uint32_t f = status_flag(s, epoch);
     if (f == 0) {
       if (++spins > kSpinLimit) {
         atomicOr(err, kErrTimeout);
@@ -80,136 +76,149 @@ __device__ __forceinline__ uint32_t lookback_digit(uint32_t* status, uint32_t bi
       if (ns < 1024) ns <<= 1;
       continue;
     }
-    excl += s & kValMask;
-    if (f == 2) break;
+    excl += static_cast<uint32_t>(s);
+    if (f == kStatusPrefix) break;
     --j;
   }
-  me.store(kFlagP | ((excl + agg) & kValMask), cuda::memory_order_relaxed);
+  store_status(me, pack_status(epoch, kStatusPrefix, excl + agg));
   return excl;
 }
 
+// One LSD pass. Resident blocks loop: each takes the next 4096-key tile from `counter` (so a
+// tile only ever waits on tiles already taken by running blocks) until the keys run out.
 __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* d_n, long long max_n, int shift, int width,
-    const uint32_t* __restrict__ offsets, uint32_t* status, uint32_t* counter, int* err) {
+    const uint32_t* __restrict__ offsets, unsigned long long* status, uint32_t* counter, uint32_t epoch,
+    int* err) {
   constexpr int kWarps = kSortThreads / 32;
   __shared__ uint32_t s_hist[kWarps][256];
   __shared__ uint32_t s_base[256];
   __shared__ uint32_t s_bid;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  for (int k = tid; k < kWarps * 256; k += kSortThreads) (&s_hist[0][0])[k] = 0;
-  if (tid == 0) s_bid = atomicAdd(counter, 1u);
-  __syncthreads();
-  const uint32_t bid = s_bid;
   const long long n = device_n(d_n, max_n);
-  const long long start = static_cast<long long>(bid) * kSortTile;
-  if (start >= n) return;
   const uint32_t dmask = (1u << width) - 1;
-  const long long wbase = start + static_cast<long long>(w) * (32 * kSortItems);
-  uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
-#pragma unroll
-  for (int j = 0; j < kSortItems; ++j) {
-    const long long idx = wbase + j * 32 + lane;
-    const bool ok = idx < n;
-    key[j] = ok ? kin[idx] : 0u;
-    val[j] = ok ? vin[idx] : 0u;
-  }
   const uint32_t lt = (1u << lane) - 1;
+  for (;;) {
+    for (int k = tid; k < kWarps * 256; k += kSortThreads) (&s_hist[0][0])[k] = 0;
+    if (tid == 0) s_bid = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t bid = s_bid;
+    const long long start = static_cast<long long>(bid) * kSortTile;
+    if (start >= n) break;
+    const long long wbase = start + static_cast<long long>(w) * (32 * kSortItems);
+    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
 #pragma unroll
-  for (int j = 0; j < kSortItems; ++j) {
-    const long long idx = wbase + j * 32 + lane;
-    const uint32_t d = idx < n ? ((key[j] >> shift) & dmask) : 256u;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t pre = d < 256u ? s_hist[w][d] : 0u;
-    __syncwarp();
-    if (d < 256u && lane == __ffs(peers) - 1) s_hist[w][d] = pre + __popc(peers);
-    __syncwarp();
-    rank[j] = pre + __popc(peers & lt);
-  }
-  __syncthreads();
-  {
-    const int d = tid;  // one thread per digit (kSortThreads == 256)
-    uint32_t sum = 0;
-#pragma unroll
-    for (int k = 0; k < kWarps; ++k) {
-      const uint32_t c = s_hist[k][d];
-      s_hist[k][d] = sum;
-      sum += c;
+    for (int j = 0; j < kSortItems; ++j) {
+      const long long idx = wbase + j * 32 + lane;
+      const bool ok = idx < n;
+      key[j] = ok ? kin[idx] : 0u;
+      val[j] = ok ? vin[idx] : 0u;
     }
-    const uint32_t excl = lookback_digit(status, bid, d, sum, err);
-    s_base[d] = offsets[d] + excl;
-  }
-  __syncthreads();
 #pragma unroll
-  for (int j = 0; j < kSortItems; ++j) {
-    const long long idx = wbase + j * 32 + lane;
-    if (idx < n) {
-      const uint32_t d = (key[j] >> shift) & dmask;
-      const uint32_t pos = s_base[d] + s_hist[w][d] + rank[j];
-      kout[pos] = key[j];
-      vout[pos] = val[j];
+    for (int j = 0; j < kSortItems; ++j) {
+      const long long idx = wbase + j * 32 + lane;
+      const uint32_t d = idx < n ? ((key[j] >> shift) & dmask) : 256u;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t pre = d < 256u ? s_hist[w][d] : 0u;
+      __syncwarp();
+      if (d < 256u && lane == __ffs(peers) - 1) s_hist[w][d] = pre + __popc(peers);
+      __syncwarp();
+      rank[j] = pre + __popc(peers & lt);
     }
+    __syncthreads();
+    {
+      const int d = tid;  // one thread per digit (kSortThreads == 256)
+      uint32_t sum = 0;
+#pragma unroll
+      for (int k = 0; k < kWarps; ++k) {
+        const uint32_t c = s_hist[k][d];
+        s_hist[k][d] = sum;
+        sum += c;
+      }
+      const uint32_t excl = lookback_digit(status, bid, d, sum, epoch, err);
+      s_base[d] = offsets[d] + excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      const long long idx = wbase + j * 32 + lane;
+      if (idx < n) {
+        const uint32_t d = (key[j] >> shift) & dmask;
+        const uint32_t pos = s_base[d] + s_hist[w][d] + rank[j];
+        kout[pos] = key[j];
+        vout[pos] = val[j];
+      }
+    }
+    __syncthreads();
   }
 }
 
 __global__ void __launch_bounds__(kScanThreads) pair_scan_kernel(
     const uint32_t* __restrict__ touched, const uint32_t* __restrict__ order, const uint32_t* __restrict__ cnt_sorted,
     uint32_t* __restrict__ offsets, const uint32_t* d_n, long long max_n, unsigned long long* status,
-    uint32_t* counter, unsigned long long* p_total, int* err) {
+    uint32_t* counter, unsigned long long* p_total, uint32_t epoch, int* err) {
   __shared__ uint32_t s_bid;
   __shared__ unsigned long long s_base;
-  if (threadIdx.x == 0) s_bid = atomicAdd(counter, 1u);
-  __syncthreads();
-  const uint32_t bid = s_bid;
   const long long n = device_n(d_n, max_n);
-  if (bid == 0 && n == 0 && threadIdx.x == 0) *p_total = 0;
-  const long long start = static_cast<long long>(bid) * (kScanThreads * kScanItems);
-  if (start >= n) return;
-  uint32_t x[kScanItems];
-  uint32_t sum = 0;
-  const long long first = start + static_cast<long long>(threadIdx.x) * kScanItems;
+  for (;;) {
+    if (threadIdx.x == 0) s_bid = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t bid = s_bid;
+    const long long start = static_cast<long long>(bid) * (kScanThreads * kScanItems);
+    if (start >= n) break;
+    uint32_t x[kScanItems];
+    uint32_t sum = 0;
+    const long long first = start + static_cast<long long>(threadIdx.x) * kScanItems;
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    const long long idx = first + k;
-    x[k] = 0;
-    if (idx < n) x[k] = cnt_sorted ? cnt_sorted[idx] : touched[order[idx]];
-    sum += x[k];
-  }
-  uint32_t total;
-  const uint32_t excl = block_excl_scan(sum, &total);
-  if (threadIdx.x == 0) s_base = chained_prefix(status, bid, total, err);
-  __syncthreads();
-  unsigned long long run = s_base + excl;
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    const long long idx = first + k;
-    if (idx < n) {
-      if (run > 0xffffffffull) atomicOr(err, kErrOverflow);
-      offsets[idx] = static_cast<uint32_t>(run);
-      if (idx == n - 1) *p_total = run + x[k];
+    for (int k = 0; k < kScanItems; ++k) {
+      const long long idx = first + k;
+      x[k] = 0;
+      if (idx < n) x[k] = cnt_sorted ? cnt_sorted[idx] : touched[order[idx]];
+      sum += x[k];
     }
-    run += x[k];
+    uint32_t total;
+    const uint32_t excl = block_excl_scan(sum, &total);
+    if (threadIdx.x < 32) {
+      const unsigned long long ex = warp_chained_prefix(status, bid, total, epoch, err);
+      if (threadIdx.x == 0) s_base = ex;
+    }
+    __syncthreads();
+    unsigned long long run = s_base + excl;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const long long idx = first + k;
+      if (idx < n) {
+        if (run > 0xffffffffull) atomicOr(err, kErrOverflow);
+        offsets[idx] = static_cast<uint32_t>(run);
+        if (idx == n - 1) *p_total = run + x[k];
+      }
+      run += x[k];
+    }
+    __syncthreads();
   }
 }
 
 }  // namespace
 
 size_t sort_status_words(long long max_n) {
-  const long long blocks = (max_n + kSortTile - 1) / kSortTile;
-  return static_cast<size_t>(blocks) * 256;
+  const long long tiles = (max_n + kSortTile - 1) / kSortTile;
+  return static_cast<size_t>(std::max<long long>(tiles, 1)) * 256;
 }
 
 void radix_sort_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
                     const uint32_t* d_n, long long max_n, int begin_bit, int end_bit, const SortScratch& sc,
-                    int* err, cudaStream_t s) {
+                    uint32_t epoch, bool clear_status, int* err, cudaStream_t s) {
   if (max_n <= 0 || end_bit <= begin_bit) return;
   const int passes = (end_bit - begin_bit + 7) / 8;
-  const int blocks = static_cast<int>((max_n + kSortTile - 1) / kSortTile);
+  const long long tiles = (max_n + kSortTile - 1) / kSortTile;
+  const size_t words = sort_status_words(max_n);
+  const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>(tiles, sc.grid_cap)));
   cudaMemsetAsync(sc.hist, 0, sizeof(uint32_t) * 256 * passes, s);
   cudaMemsetAsync(sc.counters, 0, sizeof(uint32_t) * passes, s);
-  cudaMemsetAsync(sc.status, 0, sizeof(uint32_t) * 256 * static_cast<size_t>(blocks) * passes, s);
-  const int hblocks = static_cast<int>(std::min<long long>(2 * 152, (max_n + 4095) / 4096));
-  hist_kernel<<<hblocks, 256, 0, s>>>(keys_in, d_n, max_n, begin_bit, end_bit, passes, sc.hist);
+  if (clear_status) cudaMemsetAsync(sc.status, 0, sizeof(unsigned long long) * words * passes, s);
+  const int hblocks = static_cast<int>(std::min<long long>(sc.grid_cap, (max_n + 4095) / 4096));
+  hist_kernel<<<std::max(hblocks, 1), 256, 0, s>>>(keys_in, d_n, max_n, begin_bit, end_bit, passes, sc.hist);
   hist_scan_kernel<<<passes, 256, 0, s>>>(sc.hist);
   // ping-pong so that the last pass lands in keys_out; the inputs are never written
   const uint32_t* ksrc = keys_in;
@@ -220,10 +229,8 @@ void radix_sort_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
     uint32_t* vdst = to_out ? vals_out : sc.vals_tmp;
     const int shift = begin_bit + 8 * p;
     const int width = std::min(8, end_bit - shift);
-    onesweep_kernel<<<blocks, kSortThreads, 0, s>>>(ksrc, vsrc, kdst, vdst, d_n, max_n, shift, width,
-                                                    sc.hist + 256 * p,
-                                                    sc.status + static_cast<size_t>(256) * blocks * p,
-                                                    sc.counters + p, err);
+    onesweep_kernel<<<grid, kSortThreads, 0, s>>>(ksrc, vsrc, kdst, vdst, d_n, max_n, shift, width, sc.hist + 256 * p,
+                                                  sc.status + words * p, sc.counters + p, epoch, err);
     ksrc = kdst;
     vsrc = vdst;
   }
@@ -231,14 +238,14 @@ void radix_sort_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
 
 void pair_offsets_scan(const uint32_t* touched, const uint32_t* order, const uint32_t* cnt_sorted,
                        uint32_t* offsets, const uint32_t* d_n, long long max_n, unsigned long long* status,
-                       uint32_t* counter, unsigned long long* p_total, int* err, cudaStream_t s) {
+                       uint32_t* counter, unsigned long long* p_total, int* err, uint32_t epoch, int grid_cap,
+                       cudaStream_t s) {
   const long long per = kScanThreads * kScanItems;
-  const int blocks = static_cast<int>(std::max<long long>(1, (max_n + per - 1) / per));
-  cudaMemsetAsync(status, 0, sizeof(unsigned long long) * blocks, s);
+  const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>((max_n + per - 1) / per, grid_cap)));
   cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
   cudaMemsetAsync(p_total, 0, sizeof(unsigned long long), s);
-  pair_scan_kernel<<<blocks, kScanThreads, 0, s>>>(touched, order, cnt_sorted, offsets, d_n, max_n, status, counter,
-                                                   p_total, err);
+  pair_scan_kernel<<<grid, kScanThreads, 0, s>>>(touched, order, cnt_sorted, offsets, d_n, max_n, status, counter,
+                                                 p_total, epoch, err);
 }
 
 }  // namespace gsr

@@ -20,14 +20,16 @@ namespace {
 
 // Largest n this entry point accepts: 2^18 pairs.
 constexpr long long kMaxN = 1ll << 18;
-constexpr long long kMaxBlocks = (kMaxN + kSortTile - 1) / kSortTile;
+constexpr long long kMaxTiles = (kMaxN + kSortTile - 1) / kSortTile;
+// Layout in 32-bit words; the look-back status words are 64-bit, so their offset is even.
 constexpr size_t kKeysTmp = 0;
 constexpr size_t kValsTmp = kKeysTmp + kMaxN;
 constexpr size_t kHist = kValsTmp + kMaxN;
 constexpr size_t kStatus = kHist + 4 * 256;
-constexpr size_t kCounters = kStatus + 4 * kMaxBlocks * 256;
+constexpr size_t kCounters = kStatus + 2 * 4 * kMaxTiles * 256;
 constexpr size_t kErrWord = kCounters + 4;
-constexpr size_t kWords = kErrWord + 4;  // about 2.3 MB in all
+constexpr size_t kWords = kErrWord + 4;  // about 2.6 MB in all
+static_assert(kStatus % 2 == 0, "64-bit status words need an even word offset");
 
 static __device__ __align__(256) uint32_t g_sort_scratch[kWords];
 
@@ -79,17 +81,22 @@ extern "C" gsr_status gsr_sort_pairs_u32_noalloc(const uint32_t* keys_in, const 
   uint32_t* base = nullptr;
   const gsr_status st = scratch_address(&base);
   if (st != GSR_OK) return st;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return GSR_ERR_CUDA;
+  }
   SortScratch sc;
   sc.keys_tmp = base + kKeysTmp;
   sc.vals_tmp = base + kValsTmp;
   sc.hist = base + kHist;
-  sc.status = base + kStatus;
+  sc.status = reinterpret_cast<unsigned long long*>(base + kStatus);
   sc.counters = base + kCounters;
-  sc.max_blocks = static_cast<int>(kMaxBlocks);
+  sc.grid_cap = 2 * sms;
   int* err = device_err ? reinterpret_cast<int*>(device_err) : reinterpret_cast<int*>(base + kErrWord);
-  // radix_sort_u32 clears the histograms, block counters and status words it uses before its
+  // Every call clears the histograms, block counters and look-back status words before its
   // first kernel (stream-ordered memsets, no allocation); the ping-pong buffers need no clearing.
-  radix_sort_u32(keys_in, vals_in, keys_out, vals_out, nullptr, n, begin_bit, end_bit, sc, err, s);
+  radix_sort_u32(keys_in, vals_in, keys_out, vals_out, nullptr, n, begin_bit, end_bit, sc, 1u, true, err, s);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GSR_OK : GSR_ERR_CUDA;
 }

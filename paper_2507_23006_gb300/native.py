@@ -11,6 +11,7 @@ import ctypes
 import dataclasses
 import os
 import threading
+import weakref
 from typing import Optional, Sequence
 
 import numpy as np
@@ -28,7 +29,8 @@ STATUS_NAMES = {0: "ok", 1: "over budget", -1: "invalid argument", -2: "out of d
 
 DTYPES = {torch.float32: 0, torch.float16: 1, torch.bfloat16: 2}
 
-BUF_RECORDS, BUF_VIS_BASE, BUF_VIS_MASK, BUF_PAIR_VALS, BUF_RANGES, BUF_T_FINAL, BUF_N_CONTRIB, BUF_DEPTH_ACC = range(8)
+BUF_RECORDS, BUF_OWNER, BUF_PAIR_VALS, BUF_RANGES, BUF_T_FINAL, BUF_N_CONTRIB, BUF_DEPTH_ACC = range(7)
+REC_FLOATS = 16  # one splat record: four float4
 
 EXPORTED = [
     "gsr_create", "gsr_destroy", "gsr_status_string", "gsr_last_error", "gsr_workspace_query",
@@ -253,11 +255,13 @@ class Options:
 
 
 class State:
-    """A forward state: what render_backward needs; released when garbage-collected."""
+    """A forward state: what render_backward needs; released when garbage-collected, or when
+    its Context is closed (whichever comes first)."""
 
     def __init__(self, ctx: "Context", handle: int):
         self.ctx = ctx
         self.handle = handle
+        ctx._states.add(self)
 
     def info(self) -> dict:
         i = CStateInfo()
@@ -274,8 +278,11 @@ class State:
 
     def release(self):
         if self.handle:
-            load().gsr_state_release(self.ctx.handle, self.handle)
+            # a state must go back to a live context; a closed context already released it
+            if self.ctx.handle:
+                load().gsr_state_release(self.ctx.handle, self.handle)
             self.handle = None
+            self.ctx._states.discard(self)
 
     def __del__(self):
         try:
@@ -290,6 +297,8 @@ class Context:
     def __init__(self, device: int = 0):
         L = load()
         self.device = int(device)
+        self.handle = None
+        self._states = weakref.WeakSet()
         h = ctypes.c_void_p()
         st = L.gsr_create(ctypes.byref(h), self.device, None)
         if st != GSR_OK:
@@ -298,6 +307,8 @@ class Context:
 
     def close(self):
         if getattr(self, "handle", None):
+            for st in list(self._states):
+                st.release()
             load().gsr_destroy(self.handle)
             self.handle = None
 

@@ -26,24 +26,16 @@ def state_arrays(st):
     """Pulls the binning state to the host: records, (camera, Gaussian) of each record,
     sorted pair values, ranges, n_contrib, T_final."""
     info = st.info()
-    V, P, T, NP, N = info["n_visible"], info["n_pairs"], info["n_tiles"], info["n_pixels"], info["n_render"]
-    rec = st.copy(native.BUF_RECORDS, V * 12, torch.float32).cpu().numpy().reshape(V, 12)
-    vb = st.copy(native.BUF_VIS_BASE, N, torch.int32).cpu().numpy().view(np.uint32).astype(np.int64)
-    vm = st.copy(native.BUF_VIS_MASK, N, torch.int32).cpu().numpy().view(np.uint32).astype(np.int64)
+    V, P, T, NP = info["n_visible"], info["n_pairs"], info["n_tiles"], info["n_pixels"]
+    R = native.REC_FLOATS
+    rec = st.copy(native.BUF_RECORDS, V * R, torch.float32).cpu().numpy().reshape(V, R)
+    own = st.copy(native.BUF_OWNER, V, torch.int32).cpu().numpy().view(np.uint32).astype(np.int64)
     pv = st.copy(native.BUF_PAIR_VALS, P, torch.int32).cpu().numpy().view(np.uint32).astype(np.int64)
     rg = st.copy(native.BUF_RANGES, 2 * T, torch.int32).cpu().numpy().view(np.uint32).astype(np.int64).reshape(T, 2)
     nc = st.copy(native.BUF_N_CONTRIB, NP, torch.int32).cpu().numpy().view(np.uint32).astype(np.int64)
     tf = st.copy(native.BUF_T_FINAL, NP, torch.float32).cpu().numpy()
-    cam_of = np.full(V, -1, np.int64)
-    g_of = np.full(V, -1, np.int64)
-    for c in range(info["n_cams"]):
-        has = ((vm >> c) & 1).astype(bool)
-        below = vm & ((1 << c) - 1)
-        rank = np.array([bin(int(x)).count("1") for x in below]) if below.size else np.zeros(0, np.int64)
-        v = vb[has] + rank[has]
-        cam_of[v] = c
-        g_of[v] = np.nonzero(has)[0]
-    return dict(info=info, rec=rec, cam_of=cam_of, g_of=g_of, pair_vals=pv, ranges=rg, n_contrib=nc, T_final=tf)
+    cam_of = rec[:, 11].view(np.uint32).astype(np.int64) >> 27 if V else np.zeros(0, np.int64)
+    return dict(info=info, rec=rec, cam_of=cam_of, g_of=own, pair_vals=pv, ranges=rg, n_contrib=nc, T_final=tf)
 
 
 def unpack_rect(rec):
