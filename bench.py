@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--tile-cull", type=int, default=1)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp16", action="store_true")
     p.add_argument("--cpu-tiles", type=int, default=24)
     return p.parse_args()
 
@@ -272,6 +273,35 @@ def run_ours(args, rank, world, local_rank):
     ctx.profile(False, False)
     del st
 
+    # the same step with FP16 attribute and SH storage (FP32 projection, blending, gradients)
+    fp16 = None
+    if not args.no_fp16:
+        import torch as _t
+        g16 = native.Gaussians(g.means, g.scales.half(), g.quats.half(), g.opacities.half(), g.sh.half(), 3)
+        out16 = {k: _t.empty_like(v) for k, v in outs.items()}
+
+        def step16():
+            _, st16 = native.render_forward(ctx, g16, [cam], opts, outputs=out16)
+            native.render_backward(ctx, g16, [cam], st16, d_out, opts, grads=grads)
+
+        for _ in range(2):
+            step16()
+        native.render_forward(ctx, g, [cam], opts, outputs=outs, want_state=False)
+        torch.cuda.synchronize()
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for _ in range(args.steps):
+            step16()
+        h1.record(stream)
+        torch.cuda.synchronize()
+        native.render_forward(ctx, g16, [cam], opts, outputs=out16, want_state=False)
+        torch.cuda.synchronize()
+        fp16 = dict(ms_per_step=h0.elapsed_time(h1) / args.steps,
+                    rgb_max_abs_vs_fp32=float((out16["rgb"] - outs["rgb"]).abs().max()),
+                    rgb_mean_abs_vs_fp32=float((out16["rgb"] - outs["rgb"]).abs().mean()),
+                    bytes_per_gaussian=int(12 + 2 * (3 + 4 + 1) + 2 * 48))
+
     # end to end through the same API: Gaussians from pinned host memory in, gradients out
     e2e = None
     if not args.no_e2e:
@@ -351,7 +381,7 @@ def run_ours(args, rank, world, local_rank):
                             l2="inputs larger than L2 (1.4 GB), no flush", parallelism=f"replicas{world}"),
                 render_fps=1000.0 / fwd_ms * world, fwd_ms=fwd_ms,
                 stages_ms=stage_ms, visible=V, pairs=P, counters=counts,
-                roofline=roof, cpu_baseline=cpu, e2e=e2e, clocks=clocks)
+                roofline=roof, cpu_baseline=cpu, e2e=e2e, clocks=clocks, fp16_storage=fp16)
     line["gpu_launches"] = int(args.steps * kernels_per_step(args.tile_cull, info))
     print(json.dumps(line), flush=True)
     return 0

@@ -42,15 +42,22 @@ __device__ __forceinline__ float tile_min_maha(float mx, float my, float a, floa
   return best;
 }
 
+// The blend kernels run 128 threads per 16x16 tile; thread t owns column t % 16 and rows
+// 2 (t / 16) and 2 (t / 16) + 1, so warp w covers rows 4w .. 4w+3. Records are staged 256 at a
+// time.
+constexpr int kBlendThreads = 128;
+constexpr int kBlendWarps = kBlendThreads / 32;
+constexpr int kBatch = 256;
+
 // Bit w set when the Gaussian's alpha >= 1/255 box (record field d) meets the pixel centres
-// of warp w, i.e. rows 2w and 2w+1 of the tile (x in [x_lo, x_hi], rows from y_base).
+// of warp w (x in [x_lo, x_hi], rows y_base + 4w .. y_base + 4w + 3).
 __device__ __forceinline__ uint32_t warp_rows_mask(const float4 d, float x_lo, float x_hi, float y_base) {
   uint32_t m = 0;
   if (d.y >= x_lo && d.x <= x_hi) {
 #pragma unroll
-    for (int w = 0; w < kTilePix / 32; ++w) {
-      const float yc = y_base + 2.f * w;
-      if (d.w >= yc && d.z <= yc + 1.f) m |= 1u << w;
+    for (int w = 0; w < kBlendWarps; ++w) {
+      const float yc = y_base + 4.f * w;
+      if (d.w >= yc && d.z <= yc + 3.f) m |= 1u << w;
     }
   }
   return m;
@@ -156,68 +163,77 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, long long P, ui
   if (i == P - 1 || keys[i + 1] != t) ranges[t].y = static_cast<uint32_t>(i + 1);
 }
 
-__global__ void __launch_bounds__(kTilePix) blend_fwd_kernel(const Rec* __restrict__ rec,
-                                                             const uint32_t* __restrict__ pvals,
-                                                             const uint2* __restrict__ ranges, CamBatch cams,
-                                                             float3 bg, BlendFwdOut out,
-                                                             unsigned long long* counters) {
-  __shared__ float4 sA[kTilePix];
-  __shared__ float4 sB[kTilePix];
-  __shared__ float2 sC[kTilePix];
-  __shared__ uint32_t sM[kTilePix];
+__global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(const Rec* __restrict__ rec,
+                                                                  const uint32_t* __restrict__ pvals,
+                                                                  const uint2* __restrict__ ranges, CamBatch cams,
+                                                                  float3 bg, BlendFwdOut out,
+                                                                  unsigned long long* counters) {
+  __shared__ float4 sA[kBatch];
+  __shared__ float4 sB[kBatch];
+  __shared__ float2 sC[kBatch];
+  __shared__ uint32_t sM[kBatch];
   const int t = blockIdx.x;
   const int c = find_cam(cams, t);
   const DevCam& cam = cams.cam[c];
   const int lt = t - cam.tile_off;
   const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
   const int tid = threadIdx.x, wid = tid >> 5;
-  const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + (tid >> 4);
-  const bool inside = px < cam.W && py < cam.H;
-  const float fx = px + 0.5f, fy = py + 0.5f;
+  const int px = tx * kTile + (tid & (kTile - 1));
+  const int py0 = ty * kTile + 2 * (tid >> 4);
+  const float fx = px + 0.5f;
+  const float fy[2] = {py0 + 0.5f, py0 + 1.5f};
+  const bool inside[2] = {px < cam.W && py0 < cam.H, px < cam.W && py0 + 1 < cam.H};
   const float x_lo = tx * kTile + 0.5f, x_hi = fminf(static_cast<float>((tx + 1) * kTile), cam.W) - 0.5f;
   const float y_base = ty * kTile + 0.5f;
   const uint2 range = ranges[t];
   const int n = static_cast<int>(range.y - range.x);
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
-  uint32_t last = 0;
+  float T[2] = {1.f, 1.f}, C0[2] = {0.f, 0.f}, C1[2] = {0.f, 0.f}, C2[2] = {0.f, 0.f}, D[2] = {0.f, 0.f};
+  uint32_t last[2] = {0, 0};
+  bool done[2] = {!inside[0], !inside[1]};
   uint32_t n_eval = 0, n_blend = 0;
-  bool done = !inside;
-  for (int base = 0; base < n; base += kTilePix) {
-    if (__syncthreads_count(done) == kTilePix) break;
-    const int idx = base + tid;
-    if (idx < n) {
-      const Rec r = rec[pvals[range.x + idx]];
-      sA[tid] = r.a;
-      sB[tid] = r.b;
-      sC[tid] = make_float2(r.c.x, r.c.y);
-      sM[tid] = warp_rows_mask(r.d, x_lo, x_hi, y_base);
+  for (int base = 0; base < n; base += kBatch) {
+    if (__syncthreads_count(done[0] && done[1]) == kBlendThreads) break;
+    for (int k = tid; k < kBatch; k += kBlendThreads) {
+      const int idx = base + k;
+      if (idx < n) {
+        const Rec r = rec[pvals[range.x + idx]];
+        sA[k] = r.a;
+        sB[k] = r.b;
+        sC[k] = make_float2(r.c.x, r.c.y);
+        sM[k] = warp_rows_mask(r.d, x_lo, x_hi, y_base);
+      }
     }
     __syncthreads();
-    const int cnt = min(kTilePix, n - base);
-    for (int j = 0; j < cnt && !done; ++j) {
+    const int cnt = min(kBatch, n - base);
+    for (int j = 0; j < cnt && !(done[0] && done[1]); ++j) {
       if (!((sM[j] >> wid) & 1u)) continue;  // no pixel of this warp can reach alpha 1/255
       const float4 a = sA[j];
       const float4 b = sB[j];
-      ++n_eval;
-      const float dx = a.x - fx, dy = a.y - fy;
-      const float sigma = 0.5f * (b.x * dx * dx + b.z * dy * dy) + b.y * dx * dy;
-      if (sigma < 0.f) continue;
-      const float alpha = fminf(kAlphaMax, a.z * __expf(-sigma));
-      if (alpha < kAlphaMin) continue;
-      const float Tn = T * (1.f - alpha);
-      if (Tn < kTMin) {
-        done = true;
-        break;
+      const float dx = a.x - fx;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (done[q]) continue;
+        ++n_eval;
+        const float dy = a.y - fy[q];
+        const float sigma = 0.5f * (b.x * dx * dx + b.z * dy * dy) + b.y * dx * dy;
+        if (sigma < 0.f) continue;
+        const float alpha = fminf(kAlphaMax, a.z * __expf(-sigma));
+        if (alpha < kAlphaMin) continue;
+        const float Tn = T[q] * (1.f - alpha);
+        if (Tn < kTMin) {
+          done[q] = true;
+          continue;
+        }
+        const float wgt = alpha * T[q];
+        const float2 cc = sC[j];
+        C0[q] = fmaf(b.w, wgt, C0[q]);
+        C1[q] = fmaf(cc.x, wgt, C1[q]);
+        C2[q] = fmaf(cc.y, wgt, C2[q]);
+        D[q] = fmaf(a.w, wgt, D[q]);
+        T[q] = Tn;
+        last[q] = static_cast<uint32_t>(base + j + 1);
+        ++n_blend;
       }
-      const float wgt = alpha * T;
-      const float2 cc = sC[j];
-      C0 = fmaf(b.w, wgt, C0);
-      C1 = fmaf(cc.x, wgt, C1);
-      C2 = fmaf(cc.y, wgt, C2);
-      D = fmaf(a.w, wgt, D);
-      T = Tn;
-      last = static_cast<uint32_t>(base + j + 1);
-      ++n_blend;
     }
   }
   if (counters) {
@@ -232,28 +248,30 @@ __global__ void __launch_bounds__(kTilePix) blend_fwd_kernel(const Rec* __restri
       atomicAdd(counters + 1, b);
     }
   }
-  if (!inside) return;
-  const long long pix = cam.pix_off + static_cast<long long>(py) * cam.W + px;
-  float r0, r1, r2;
-  if (cam.aff) {
-    const float* A = cam.aff;
-    const float o = 1.f - T;
-    r0 = A[0] * C0 + A[1] * C1 + A[2] * C2 + A[3] * o;
-    r1 = A[4] * C0 + A[5] * C1 + A[6] * C2 + A[7] * o;
-    r2 = A[8] * C0 + A[9] * C1 + A[10] * C2 + A[11] * o;
-  } else {
-    r0 = C0; r1 = C1; r2 = C2;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    if (!inside[q]) continue;
+    const long long pix = cam.pix_off + static_cast<long long>(py0 + q) * cam.W + px;
+    float r0, r1, r2;
+    const float o = 1.f - T[q];
+    if (cam.aff) {
+      const float* A = cam.aff;
+      r0 = A[0] * C0[q] + A[1] * C1[q] + A[2] * C2[q] + A[3] * o;
+      r1 = A[4] * C0[q] + A[5] * C1[q] + A[6] * C2[q] + A[7] * o;
+      r2 = A[8] * C0[q] + A[9] * C1[q] + A[10] * C2[q] + A[11] * o;
+    } else {
+      r0 = C0[q]; r1 = C1[q]; r2 = C2[q];
+    }
+    out.rgb[3 * pix + 0] = r0 + T[q] * bg.x;
+    out.rgb[3 * pix + 1] = r1 + T[q] * bg.y;
+    out.rgb[3 * pix + 2] = r2 + T[q] * bg.z;
+    if (out.depth_acc) out.depth_acc[pix] = D[q];
+    if (out.depth_exp) out.depth_exp[pix] = D[q] / fmaxf(o, 1e-10f);
+    if (out.alpha) out.alpha[pix] = o;
+    if (out.T_final) out.T_final[pix] = T[q];
+    if (out.n_contrib) out.n_contrib[pix] = last[q];
+    if (out.D_state) out.D_state[pix] = D[q];
   }
-  out.rgb[3 * pix + 0] = r0 + T * bg.x;
-  out.rgb[3 * pix + 1] = r1 + T * bg.y;
-  out.rgb[3 * pix + 2] = r2 + T * bg.z;
-  const float al = 1.f - T;
-  if (out.depth_acc) out.depth_acc[pix] = D;
-  if (out.depth_exp) out.depth_exp[pix] = D / fmaxf(al, 1e-10f);
-  if (out.alpha) out.alpha[pix] = al;
-  if (out.T_final) out.T_final[pix] = T;
-  if (out.n_contrib) out.n_contrib[pix] = last;
-  if (out.D_state) out.D_state[pix] = D;
 }
 
 __device__ __forceinline__ float warp_sum(float x) {
@@ -264,157 +282,169 @@ __device__ __forceinline__ float warp_sum(float x) {
 
 constexpr int kGradVals = 12;
 
-__global__ void __launch_bounds__(kTilePix) blend_bwd_kernel(const Rec* __restrict__ rec,
-                                                             const uint32_t* __restrict__ pvals,
-                                                             const uint2* __restrict__ ranges, CamBatch cams,
-                                                             float3 bg, BlendBwdIn in, Grad2D* __restrict__ g2d,
-                                                             float* __restrict__ g_aff, int absgrad,
-                                                             unsigned long long* counters) {
-  __shared__ float4 sA[kTilePix];
-  __shared__ float4 sB[kTilePix];
-  __shared__ float2 sC[kTilePix];
-  __shared__ uint32_t sV[kTilePix];
-  __shared__ uint32_t sM[kTilePix];
-  __shared__ float sAcc[kTilePix][kGradVals + 1];
+__global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __restrict__ rec,
+                                                                  const uint32_t* __restrict__ pvals,
+                                                                  const uint2* __restrict__ ranges, CamBatch cams,
+                                                                  float3 bg, BlendBwdIn in, Grad2D* __restrict__ g2d,
+                                                                  float* __restrict__ g_aff, int absgrad,
+                                                                  unsigned long long* counters) {
+  __shared__ float4 sA[kBatch];
+  __shared__ float4 sB[kBatch];
+  __shared__ float2 sC[kBatch];
+  __shared__ uint32_t sV[kBatch];
+  __shared__ uint32_t sM[kBatch];
+  __shared__ float sAcc[kBatch][kGradVals + 1];
   __shared__ uint32_t s_max;
-  __shared__ float s_aff[8][12];
+  __shared__ float s_aff[kBlendWarps][12];
   const int t = blockIdx.x;
   const int c = find_cam(cams, t);
   const DevCam& cam = cams.cam[c];
   const int lt = t - cam.tile_off;
   const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + (tid >> 4);
-  const bool inside = px < cam.W && py < cam.H;
-  const float fx = px + 0.5f, fy = py + 0.5f;
+  const int px = tx * kTile + (tid & (kTile - 1));
+  const int py0 = ty * kTile + 2 * (tid >> 4);
+  const float fx = px + 0.5f;
+  const float fy[2] = {py0 + 0.5f, py0 + 1.5f};
+  const bool inside[2] = {px < cam.W && py0 < cam.H, px < cam.W && py0 + 1 < cam.H};
   const float x_lo = tx * kTile + 0.5f, x_hi = fminf(static_cast<float>((tx + 1) * kTile), cam.W) - 0.5f;
   const float y_base = ty * kTile + 0.5f;
   const uint2 range = ranges[t];
   if (tid == 0) s_max = 0;
   __syncthreads();
-  float Tf = 1.f, D = 0.f;
-  uint32_t last = 0;
-  float g0 = 0.f, g1 = 0.f, g2 = 0.f, gda = 0.f, gde = 0.f, gal = 0.f;
-  long long pix = 0;
-  if (inside) {
-    pix = cam.pix_off + static_cast<long long>(py) * cam.W + px;
-    Tf = in.T_final[pix];
-    last = in.n_contrib[pix];
-    D = in.D_state[pix];
-    if (in.d_rgb) { g0 = in.d_rgb[3 * pix]; g1 = in.d_rgb[3 * pix + 1]; g2 = in.d_rgb[3 * pix + 2]; }
-    if (in.d_depth_acc) gda = in.d_depth_acc[pix];
-    if (in.d_depth_exp) gde = in.d_depth_exp[pix];
-    if (in.d_alpha) gal = in.d_alpha[pix];
-    atomicMax(&s_max, last);
-  }
-  // upstream gradients of C = sum c a T, D = sum z a T and T_final
   const float* A = cam.aff;
-  float GC0 = g0, GC1 = g1, GC2 = g2, bb0 = 0.f, bb1 = 0.f, bb2 = 0.f;
-  if (A) {
-    GC0 = A[0] * g0 + A[4] * g1 + A[8] * g2;
-    GC1 = A[1] * g0 + A[5] * g1 + A[9] * g2;
-    GC2 = A[2] * g0 + A[6] * g1 + A[10] * g2;
-    bb0 = A[3]; bb1 = A[7]; bb2 = A[11];
+  const float bb0 = A ? A[3] : 0.f, bb1 = A ? A[7] : 0.f, bb2 = A ? A[11] : 0.f;
+  // per pixel: upstream gradients of C = sum c a T, of the depth part and of T_final
+  float Tf[2], T[2], g0[2], g1[2], g2[2], aout[2], GC0[2], GC1[2], GC2[2], GD[2], GTz[2], zr[2];
+  float S0[2] = {0.f, 0.f}, S1[2] = {0.f, 0.f}, S2[2] = {0.f, 0.f}, SD[2] = {0.f, 0.f};
+  uint32_t last[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    float D = 0.f, gda = 0.f, gde = 0.f, gal = 0.f;
+    Tf[q] = 1.f;
+    last[q] = 0;
+    g0[q] = g1[q] = g2[q] = 0.f;
+    if (inside[q]) {
+      const long long pix = cam.pix_off + static_cast<long long>(py0 + q) * cam.W + px;
+      Tf[q] = in.T_final[pix];
+      last[q] = in.n_contrib[pix];
+      D = in.D_state[pix];
+      if (in.d_rgb) { g0[q] = in.d_rgb[3 * pix]; g1[q] = in.d_rgb[3 * pix + 1]; g2[q] = in.d_rgb[3 * pix + 2]; }
+      if (in.d_depth_acc) gda = in.d_depth_acc[pix];
+      if (in.d_depth_exp) gde = in.d_depth_exp[pix];
+      if (in.d_alpha) gal = in.d_alpha[pix];
+      atomicMax(&s_max, last[q]);
+    }
+    GC0[q] = g0[q]; GC1[q] = g1[q]; GC2[q] = g2[q];
+    if (A) {
+      GC0[q] = A[0] * g0[q] + A[4] * g1[q] + A[8] * g2[q];
+      GC1[q] = A[1] * g0[q] + A[5] * g1[q] + A[9] * g2[q];
+      GC2[q] = A[2] * g0[q] + A[6] * g1[q] + A[10] * g2[q];
+    }
+    aout[q] = 1.f - Tf[q];
+    GD[q] = gda + gde / fmaxf(aout[q], 1e-10f);
+    const float ga_eff = gal + (aout[q] > 1e-10f ? -gde * D / (aout[q] * aout[q]) : 0.f);
+    const float GT = g0[q] * (bg.x - bb0) + g1[q] * (bg.y - bb1) + g2[q] * (bg.z - bb2) - ga_eff;
+    // Depths are carried relative to the pixel's expected depth zr: with z_i = zr + d_i the depth
+    // part of dL/dalpha_i, T_i z_i - S_D / (1 - a_i), equals T_i d_i - S_d / (1 - a_i)
+    // + zr T_final / (1 - a_i) (the weights behind i sum to T_{i+1} - T_final); this avoids the
+    // FP32 cancellation of two large, nearly equal terms when the contributors lie at similar depth.
+    zr[q] = aout[q] > 1e-10f ? D / aout[q] : 0.f;
+    GTz[q] = GD[q] * zr[q] - GT;
+    T[q] = Tf[q];
   }
-  const float aout = 1.f - Tf;
-  const float GD = gda + gde / fmaxf(aout, 1e-10f);
-  const float ga_eff = gal + (aout > 1e-10f ? -gde * D / (aout * aout) : 0.f);
-  const float GT = g0 * (bg.x - bb0) + g1 * (bg.y - bb1) + g2 * (bg.z - bb2) - ga_eff;
-  // Depths are carried relative to the pixel's expected depth zr: with z_i = zr + d_i the depth
-  // part of dL/dalpha_i, T_i z_i - S_D / (1 - a_i), equals T_i d_i - S_d / (1 - a_i)
-  // + zr T_final / (1 - a_i) (the weights behind i sum to T_{i+1} - T_final), which avoids the
-  // FP32 cancellation of two large, nearly equal terms when the contributors lie at similar depth.
-  const float zr = aout > 1e-10f ? D / aout : 0.f;
-  const float GTz = GD * zr - GT;
   __syncthreads();
   const int n = static_cast<int>(s_max);
-  float T = Tf;
-  float S0 = 0.f, S1 = 0.f, S2 = 0.f, SD = 0.f;
   uint32_t n_visit = 0, n_contrib = 0;
-  for (int base = 0; base < n; base += kTilePix) {
+  for (int base = 0; base < n; base += kBatch) {
     __syncthreads();
-    if (base + tid < n) {
-      const uint32_t pos = range.x + static_cast<uint32_t>(n - 1 - base - tid);
-      const uint32_t v = pvals[pos];
-      const Rec r = rec[v];
-      sA[tid] = r.a;
-      sB[tid] = r.b;
-      sC[tid] = make_float2(r.c.x, r.c.y);
-      sV[tid] = v;
-      sM[tid] = warp_rows_mask(r.d, x_lo, x_hi, y_base);
-    }
+    for (int k = tid; k < kBatch; k += kBlendThreads) {
+      if (base + k < n) {
+        const uint32_t pos = range.x + static_cast<uint32_t>(n - 1 - base - k);
+        const uint32_t v = pvals[pos];
+        const Rec r = rec[v];
+        sA[k] = r.a;
+        sB[k] = r.b;
+        sC[k] = make_float2(r.c.x, r.c.y);
+        sV[k] = v;
+        sM[k] = warp_rows_mask(r.d, x_lo, x_hi, y_base);
+      }
 #pragma unroll
-    for (int k = 0; k < kGradVals; ++k) sAcc[tid][k] = 0.f;
+      for (int m = 0; m < kGradVals; ++m) sAcc[k][m] = 0.f;
+    }
     __syncthreads();
-    const int cnt = min(kTilePix, n - base);
+    const int cnt = min(kBatch, n - base);
     for (int j = 0; j < cnt; ++j) {
       if (!((sM[j] >> wid) & 1u)) continue;  // warp-uniform: no pixel of this warp is touched
       const uint32_t pos = static_cast<uint32_t>(n - 1 - base - j);
       float gv[kGradVals];
 #pragma unroll
-      for (int k = 0; k < kGradVals; ++k) gv[k] = 0.f;
+      for (int m = 0; m < kGradVals; ++m) gv[m] = 0.f;
       bool contrib = false;
-      if (inside && pos < last) {
+      const float4 a = sA[j];
+      const float4 b = sB[j];
+      const float2 cc = sC[j];
+      const float dx = a.x - fx;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (!(inside[q] && pos < last[q])) continue;
         ++n_visit;
-        const float4 a = sA[j];
-        const float4 b = sB[j];
-        const float dx = a.x - fx, dy = a.y - fy;
+        const float dy = a.y - fy[q];
         const float sigma = 0.5f * (b.x * dx * dx + b.z * dy * dy) + b.y * dx * dy;
-        if (sigma >= 0.f) {
-          const float G = __expf(-sigma);
-          const float araw = a.z * G;
-          const float alpha = fminf(kAlphaMax, araw);
-          if (alpha >= kAlphaMin) {
-            contrib = true;
-            ++n_contrib;
-            const float om = 1.f - alpha;
-            const float Ti = T / om;
-            const float2 cc = sC[j];
-            const float wgt = alpha * Ti;
-            const float dz = a.w - zr;
-            const float dal = Ti * (GC0 * b.w + GC1 * cc.x + GC2 * cc.y + GD * dz) +
-                              (GTz * Tf - (GC0 * S0 + GC1 * S1 + GC2 * S2 + GD * SD)) / om;
-            S0 = fmaf(b.w, wgt, S0);
-            S1 = fmaf(cc.x, wgt, S1);
-            S2 = fmaf(cc.y, wgt, S2);
-            SD = fmaf(dz, wgt, SD);
-            T = Ti;
-            const float draw = araw > kAlphaMax ? 0.f : dal;
-            const float dsig = -draw * araw;
-            gv[0] = (b.x * dx + b.y * dy) * dsig;
-            gv[1] = (b.y * dx + b.z * dy) * dsig;
-            gv[2] = draw * G;
-            gv[3] = GD * wgt;
-            gv[4] = 0.5f * dx * dx * dsig;
-            gv[5] = dx * dy * dsig;
-            gv[6] = 0.5f * dy * dy * dsig;
-            gv[7] = GC0 * wgt;
-            gv[8] = GC1 * wgt;
-            gv[9] = GC2 * wgt;
-            gv[10] = fabsf(gv[0]);
-            gv[11] = fabsf(gv[1]);
-          }
-        }
+        if (sigma < 0.f) continue;
+        const float G = __expf(-sigma);
+        const float araw = a.z * G;
+        const float alpha = fminf(kAlphaMax, araw);
+        if (alpha < kAlphaMin) continue;
+        contrib = true;
+        ++n_contrib;
+        const float om = 1.f - alpha;
+        const float Ti = T[q] / om;
+        const float wgt = alpha * Ti;
+        const float dz = a.w - zr[q];
+        const float dal = Ti * (GC0[q] * b.w + GC1[q] * cc.x + GC2[q] * cc.y + GD[q] * dz) +
+                          (GTz[q] * Tf[q] - (GC0[q] * S0[q] + GC1[q] * S1[q] + GC2[q] * S2[q] + GD[q] * SD[q])) / om;
+        S0[q] = fmaf(b.w, wgt, S0[q]);
+        S1[q] = fmaf(cc.x, wgt, S1[q]);
+        S2[q] = fmaf(cc.y, wgt, S2[q]);
+        SD[q] = fmaf(dz, wgt, SD[q]);
+        T[q] = Ti;
+        const float draw = araw > kAlphaMax ? 0.f : dal;
+        const float dsig = -draw * araw;
+        const float dmx = (b.x * dx + b.y * dy) * dsig;
+        const float dmy = (b.y * dx + b.z * dy) * dsig;
+        gv[0] += dmx;
+        gv[1] += dmy;
+        gv[2] += draw * G;
+        gv[3] += GD[q] * wgt;
+        gv[4] += 0.5f * dx * dx * dsig;
+        gv[5] += dx * dy * dsig;
+        gv[6] += 0.5f * dy * dy * dsig;
+        gv[7] += GC0[q] * wgt;
+        gv[8] += GC1[q] * wgt;
+        gv[9] += GC2[q] * wgt;
+        gv[10] += fabsf(dmx);
+        gv[11] += fabsf(dmy);
       }
       if (__any_sync(0xffffffffu, contrib)) {
 #pragma unroll
-        for (int k = 0; k < kGradVals; ++k)
-          if (k < kGradVals - 2 || absgrad) gv[k] = warp_sum(gv[k]);
+        for (int m = 0; m < kGradVals; ++m)
+          if (m < kGradVals - 2 || absgrad) gv[m] = warp_sum(gv[m]);
         if (lane == 0) {
 #pragma unroll
-          for (int k = 0; k < kGradVals; ++k)
-            if (k < kGradVals - 2 || absgrad) atomicAdd(&sAcc[j][k], gv[k]);
+          for (int m = 0; m < kGradVals; ++m)
+            if (m < kGradVals - 2 || absgrad) atomicAdd(&sAcc[j][m], gv[m]);
         }
       }
     }
     __syncthreads();
-    if (tid < cnt) {
-      Grad2D* dst = g2d + sV[tid];
-      float* f = reinterpret_cast<float*>(dst);
-      const int nv = absgrad ? kGradVals : kGradVals - 2;
-      for (int k = 0; k < nv; ++k) {
-        const float val = sAcc[tid][k];
-        if (val != 0.f) atomicAdd(f + k, val);
+    for (int k = tid; k < cnt; k += kBlendThreads) {
+      float* f = reinterpret_cast<float*>(g2d + sV[k]);
+#pragma unroll
+      for (int m = 0; m < kGradVals; ++m) {
+        if (m >= kGradVals - 2 && !absgrad) continue;
+        const float val = sAcc[k][m];
+        if (val != 0.f) atomicAdd(f + m, val);
       }
     }
   }
@@ -432,19 +462,26 @@ __global__ void __launch_bounds__(kTilePix) blend_bwd_kernel(const Rec* __restri
   }
   if (g_aff) {
     // dA = g C^T, db = g (1 - T_final), per pixel, summed over the tile
-    float a12[12] = {g0 * S0, g0 * S1, g0 * S2, g0 * aout, g1 * S0, g1 * S1, g1 * S2, g1 * aout,
-                     g2 * S0, g2 * S1, g2 * S2, g2 * aout};
-    if (!inside)
-      for (int k = 0; k < 12; ++k) a12[k] = 0.f;
+    float a12[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) a12[k] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (!inside[q]) continue;
+      a12[0] += g0[q] * S0[q]; a12[1] += g0[q] * S1[q]; a12[2] += g0[q] * S2[q]; a12[3] += g0[q] * aout[q];
+      a12[4] += g1[q] * S0[q]; a12[5] += g1[q] * S1[q]; a12[6] += g1[q] * S2[q]; a12[7] += g1[q] * aout[q];
+      a12[8] += g2[q] * S0[q]; a12[9] += g2[q] * S1[q]; a12[10] += g2[q] * S2[q]; a12[11] += g2[q] * aout[q];
+    }
+#pragma unroll
     for (int k = 0; k < 12; ++k) {
-      const float s = warp_sum(a12[k]);
-      if (lane == 0) s_aff[wid][k] = s;
+      const float sum = warp_sum(a12[k]);
+      if (lane == 0) s_aff[wid][k] = sum;
     }
     __syncthreads();
     if (tid < 12) {
-      float s = 0.f;
-      for (int k = 0; k < 8; ++k) s += s_aff[k][tid];
-      if (s != 0.f) atomicAdd(g_aff + 12 * c + tid, s);
+      float sum = 0.f;
+      for (int k = 0; k < kBlendWarps; ++k) sum += s_aff[k][tid];
+      if (sum != 0.f) atomicAdd(g_aff + 12 * c + tid, sum);
     }
   }
 }
@@ -476,7 +513,7 @@ void launch_ranges(const uint32_t* sorted_keys, long long P, uint2* ranges, cuda
 void launch_blend_fwd(const Rec* rec, const uint32_t* pair_vals, const uint2* ranges, const CamBatch& cams,
                       const float* bg, const BlendFwdOut& out, unsigned long long* counters, cudaStream_t s) {
   if (cams.total_tiles <= 0) return;
-  blend_fwd_kernel<<<cams.total_tiles, kTilePix, 0, s>>>(rec, pair_vals, ranges, cams, make_float3(bg[0], bg[1], bg[2]),
+  blend_fwd_kernel<<<cams.total_tiles, kBlendThreads, 0, s>>>(rec, pair_vals, ranges, cams, make_float3(bg[0], bg[1], bg[2]),
                                                          out, counters);
 }
 
@@ -484,7 +521,7 @@ void launch_blend_bwd(const Rec* rec, const uint32_t* pair_vals, const uint2* ra
                       const float* bg, const BlendBwdIn& in, Grad2D* g2d, float* g_aff, int absgrad,
                       unsigned long long* counters, cudaStream_t s) {
   if (cams.total_tiles <= 0) return;
-  blend_bwd_kernel<<<cams.total_tiles, kTilePix, 0, s>>>(rec, pair_vals, ranges, cams, make_float3(bg[0], bg[1], bg[2]),
+  blend_bwd_kernel<<<cams.total_tiles, kBlendThreads, 0, s>>>(rec, pair_vals, ranges, cams, make_float3(bg[0], bg[1], bg[2]),
                                                          in, g2d, g_aff, absgrad, counters);
 }
 

@@ -66,11 +66,20 @@ def oracle_tile_lists(pairs):
 
 
 def grad_close(g, ref, name, rel=1e-3, group_rel=1e-3):
-    g = np.asarray(g, np.float64).reshape(-1)
-    ref = np.asarray(ref, np.float64).reshape(-1)
+    """|g - ref| <= rel * ||ref row|| + group_rel * rms(ref) elementwise, where a row is one
+    Gaussian's block of the parameter (its mean, scale, quaternion, opacity or SH block): a
+    single component of a row can be a near-cancelling sum of large per-pixel terms, so its
+    FP32 error scales with the row, not with the component."""
+    ref = np.asarray(ref, np.float64)
+    g = np.asarray(g, np.float64).reshape(ref.shape)
+    rows = ref.reshape(ref.shape[0], -1) if ref.ndim > 1 else ref.reshape(-1, 1)
+    row_norm = np.sqrt((rows ** 2).sum(axis=1, keepdims=True))
+    row_norm = np.broadcast_to(row_norm, rows.shape).reshape(-1)
+    g = g.reshape(-1)
+    ref = ref.reshape(-1)
     rms = np.sqrt(np.mean(ref ** 2)) if ref.size else 0.0
     err = np.abs(g - ref)
-    bound = rel * np.abs(ref) + group_rel * rms + 1e-12
+    bound = rel * row_norm + group_rel * rms + 1e-12
     bad = err > bound
     if bad.any():
         idx = np.nonzero(bad)[0]
