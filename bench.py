@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp16", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-rate", type=float, default=200.0)
+    p.add_argument("--serve-seconds", type=float, default=2.0)
     p.add_argument("--cpu-tiles", type=int, default=24)
     return p.parse_args()
 
@@ -339,6 +342,10 @@ def run_ours(args, rank, world, local_rank):
             e2e_ms = float(t.item())
         e2e = dict(value=e2e_ms / world, unit="ms/step", h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
 
+    serve_stats = None
+    if not args.no_serve:
+        serve_stats = run_serve(scene, args)
+
     if rank != 0:
         return 0
     # roofline of the dominant kernel
@@ -381,10 +388,57 @@ def run_ours(args, rank, world, local_rank):
                             l2="inputs larger than L2 (1.4 GB), no flush", parallelism=f"replicas{world}"),
                 render_fps=1000.0 / fwd_ms * world, fwd_ms=fwd_ms,
                 stages_ms=stage_ms, visible=V, pairs=P, counters=counts,
-                roofline=roof, cpu_baseline=cpu, e2e=e2e, clocks=clocks, fp16_storage=fp16)
+                roofline=roof, cpu_baseline=cpu, e2e=e2e, clocks=clocks, fp16_storage=fp16, serve=serve_stats)
     line["gpu_launches"] = int(args.steps * kernels_per_step(args.tile_cull, info))
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_serve(scene, args):
+    """Serving on the same city: detail levels (the 6M scene and two merged coarser levels,
+    0.3x the 20M / 6M / 1.5M of the reference configuration, budget scaled alike), Poisson
+    arrivals, resolutions drawn from 720p / 1080p / 4K, half walk-through and half aerial poses.
+    The FP16 LOD server and the plain FP32 full-detail renderer serve the same trace."""
+    import torch
+    from paper_2507_23006_gb300 import lod, scenes, serve
+    t0 = time.perf_counter()
+    mid = lod.merge_to_count(scene, int(0.3 * scene.n))
+    coarse = lod.merge_to_count(mid, int(0.075 * scene.n))
+    levels = lod.build_lod([coarse, mid, scene])
+    full = lod.build_lod([scene])
+    build_s = time.perf_counter() - t0
+    res_choices = [(1280, 720), (1920, 1080), (3840, 2160)]
+
+    def make_cam(rng):
+        w, h = res_choices[int(rng.integers(0, 3))]
+        if rng.uniform() < 0.5:
+            return scenes.walkthrough_camera(rng, w, h)
+        return scenes.aerial_camera(w, h, altitude=rng.uniform(80, 300), pitch_deg=rng.uniform(30, 89),
+                                    target=(rng.uniform(-500, 500), rng.uniform(-500, 500), 0.0),
+                                    azimuth_deg=rng.uniform(0, 360))
+
+    out = {}
+    budget = int(4_000_000 * scene.n / 20_000_000)
+    for name, lodscene, dt, gb in (("lod_fp16", levels, torch.float16, budget),
+                                   ("full_fp32", full, torch.float32, 0)):
+        srv = serve.RenderServer(slots=4, gaussian_budget=gb)
+        srv.add_scene("city", lodscene, attr_dtype=dt, sh_dtype=dt)
+        srv.run_trace(serve.poisson_trace(np.random.default_rng(7), args.serve_rate, 0.5, "city", make_cam))
+        st = srv.run_trace(serve.poisson_trace(np.random.default_rng(8), args.serve_rate, args.serve_seconds, "city",
+                                               make_cam))
+        # capacity: 200 requests that all arrive at once
+        rng = np.random.default_rng(9)
+        burst = srv.run_trace([(0.0, "city", make_cam(rng)) for _ in range(200)])
+        srv.close()
+        out[name] = {k: st[k] for k in ("p50_ms", "p99_ms", "mean_ms", "fps", "served", "failed", "max_in_flight",
+                                        "mean_batch", "mean_selected")}
+        out[name]["saturated_fps"] = burst["fps"]
+        del srv
+        torch.cuda.empty_cache()
+    out["config"] = dict(levels=levels.level_sizes, partitions=int(levels.aabb.shape[0]), gaussian_budget=budget,
+                         thresholds_m=[100.0, 200.0], rate_hz=args.serve_rate, seconds=args.serve_seconds,
+                         resolutions=["1280x720", "1920x1080", "3840x2160"], slots=4, lod_build_s=round(build_s, 1))
+    return out
 
 
 def kernels_per_step(tile_cull, info):

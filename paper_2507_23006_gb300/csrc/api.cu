@@ -63,6 +63,10 @@ struct gsr_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int grid_cap = 304;  // resident blocks of the looping scan / sort kernels (2 per SM)
+  // default allocator: a context-owned stream-ordered pool (growth and release never
+  // synchronise the device, which matters when several contexts serve concurrently)
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t last_stream = nullptr;
 };
 
 struct gsr_fwd_state {
@@ -92,7 +96,8 @@ void* raw_alloc(gsr_ctx* ctx, size_t bytes, cudaStream_t s) {
   if (bytes == 0) bytes = 16;
   if (ctx->has_alloc) return ctx->alloc.alloc(bytes, reinterpret_cast<gsr_stream>(s), ctx->alloc.user);
   void* p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+  const cudaError_t e = ctx->pool ? cudaMallocFromPoolAsync(&p, bytes, ctx->pool, s) : cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
@@ -102,6 +107,7 @@ void* raw_alloc(gsr_ctx* ctx, size_t bytes, cudaStream_t s) {
 void raw_free(gsr_ctx* ctx, void* p, size_t bytes, cudaStream_t s) {
   if (!p) return;
   if (ctx->has_alloc) ctx->alloc.free(p, bytes, reinterpret_cast<gsr_stream>(s), ctx->alloc.user);
+  else if (ctx->pool) cudaFreeAsync(p, s);
   else cudaFree(p);
 }
 
@@ -114,7 +120,7 @@ bool ensure(gsr_ctx* ctx, Buf& b, size_t bytes, cudaStream_t s) {
     b.p = nullptr;
     b.cap = 0;
   }
-  size_t want = std::max<size_t>(bytes + bytes / 8, 256);
+  size_t want = std::max<size_t>(bytes + bytes / 2, 256);
   want = (want + 255) & ~static_cast<size_t>(255);
   b.p = raw_alloc(ctx, want, s);
   if (!b.p) return false;
@@ -522,6 +528,19 @@ gsr_status gsr_create(gsr_ctx** out, int device, const gsr_allocator* alloc) {
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
     ctx->grid_cap = 2 * sms;
   cudaGetLastError();
+  if (!alloc) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&ctx->pool, &props) == cudaSuccess) {
+      unsigned long long keep = ~0ull;  // keep freed memory in the pool for reuse
+      cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      cudaGetLastError();
+      ctx->pool = nullptr;  // fall back to cudaMalloc / cudaFree
+    }
+  }
   if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
@@ -553,6 +572,8 @@ void gsr_destroy(gsr_ctx* ctx) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
+  cudaDeviceSynchronize();
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->side) cudaStreamDestroy(ctx->side);
@@ -593,6 +614,7 @@ gsr_status gsr_render_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_ca
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  ctx->last_stream = s;
   long long npix = 0;
   const CamBatch cb = make_cams(cams, n_cams, &npix);
   const long long N = render_count(g);
@@ -793,7 +815,7 @@ void gsr_state_release(gsr_ctx* ctx, gsr_fwd_state* state) {
   Buf* all[] = {&state->rec, &state->owner, &state->pvals_s, &state->ranges, &state->T_final, &state->n_contrib,
                 &state->D};
   if (c)
-    for (Buf* b : all) release(c, *b, nullptr);
+    for (Buf* b : all) release(c, *b, c->last_stream);
   delete state;
 }
 

@@ -284,3 +284,23 @@ def tiny_scene(seed: int, n: int, width: int = 32, height: int = 32, depth=(2.0,
     scales, quats, opac, sh = random_attributes(rng, n, log_scale_mean=log_scale_mean)
     cam = box_camera(width, height, f=f)
     return Scene(means, scales, quats, opac, sh), cam
+
+
+
+def walkthrough_camera(rng, width, height, extent=1000.0, block=100.0, street=20.0):
+    """A street-level camera (1.7-10 m up, pitch within 10 degrees of horizontal) on a street of
+    the city grid, looking along the street."""
+    half = extent / 2.0
+    k = int(rng.integers(0, int(extent / block)))
+    along = rng.uniform(-half, half)
+    pos = -half + k * block  # streets run along the block boundaries
+    hgt = rng.uniform(1.7, 10.0)
+    pitch = math.radians(rng.uniform(-10.0, 10.0))
+    if rng.uniform() < 0.5:
+        eye = np.array([pos, along, hgt])
+        fwd = np.array([0.0, rng.choice([-1.0, 1.0]), 0.0])
+    else:
+        eye = np.array([along, pos, hgt])
+        fwd = np.array([rng.choice([-1.0, 1.0]), 0.0, 0.0])
+    tgt = eye + 50.0 * fwd + np.array([0.0, 0.0, 50.0 * math.tan(pitch)])
+    return pinhole(look_at(eye, tgt), width, height)
