@@ -368,6 +368,7 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   ga.attr_dtype = g->attr_dtype;
   ga.sh_dtype = g->sh_dtype;
   ga.quat_vec4 = g->attr_dtype == GSR_F32 && (reinterpret_cast<uintptr_t>(g->quats) % 16 == 0);
+  ga.sh_vec4 = g->sh_dtype == GSR_F32 && (reinterpret_cast<uintptr_t>(g->sh) % 16 == 0) && ((3 * g->sh_coeffs) % 4 == 0);
 
   const int pre_blocks = static_cast<int>((N + kPreTile - 1) / kPreTile);
   GSR_TRY_ALLOC(*bo.rec, sizeof(Rec) * capv);
@@ -783,6 +784,7 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
   ga.attr_dtype = g->attr_dtype;
   ga.sh_dtype = g->sh_dtype;
   ga.quat_vec4 = g->attr_dtype == GSR_F32 && (reinterpret_cast<uintptr_t>(g->quats) % 16 == 0);
+  ga.sh_vec4 = g->sh_dtype == GSR_F32 && (reinterpret_cast<uintptr_t>(g->sh) % 16 == 0) && ((3 * g->sh_coeffs) % 4 == 0);
   ParamGrads pg;
   pg.means = grads->means;
   pg.scales = grads->scales;

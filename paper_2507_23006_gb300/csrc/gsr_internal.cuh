@@ -99,6 +99,7 @@ struct GaussArgs {
   int attr_dtype;
   int sh_dtype;
   int quat_vec4;       // float32 quaternions on a 16-byte boundary: load each as one float4
+  int sh_vec4;         // float32 SH rows on 16-byte boundaries (3K % 4 == 0): load as float4
 };
 
 struct PreOut {

@@ -116,16 +116,21 @@ struct Geo {
 };
 
 template <typename AT>
-__device__ __forceinline__ bool load_geo(const GaussArgs& A, long long g, Geo& G) {
+__device__ __forceinline__ void load_mean_scale(const GaussArgs& A, long long g, Geo& G) {
   const AT* sc = static_cast<const AT*>(A.scales);
-  const AT* qt = static_cast<const AT*>(A.quats);
-  const AT* op = static_cast<const AT*>(A.opac);
   G.m[0] = __ldg(A.means + 3 * g + 0);
   G.m[1] = __ldg(A.means + 3 * g + 1);
   G.m[2] = __ldg(A.means + 3 * g + 2);
   G.s[0] = ldf(sc, 3 * g + 0);
   G.s[1] = ldf(sc, 3 * g + 1);
   G.s[2] = ldf(sc, 3 * g + 2);
+}
+
+// The rest of the Gaussian (quaternion, opacity, Sigma) after load_mean_scale.
+template <typename AT>
+__device__ __forceinline__ bool finish_geo(const GaussArgs& A, long long g, Geo& G) {
+  const AT* qt = static_cast<const AT*>(A.quats);
+  const AT* op = static_cast<const AT*>(A.opac);
   float qw, qx, qy, qz;
   if (std::is_same<AT, float>::value && A.quat_vec4) {
     const float4 q4 = __ldg(reinterpret_cast<const float4*>(A.quats) + g);
@@ -155,6 +160,12 @@ __device__ __forceinline__ bool load_geo(const GaussArgs& A, long long g, Geo& G
   G.S[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
   G.S[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
   return isfinite(G.S[0] + G.S[3] + G.S[5] + G.m[0] + G.m[1] + G.m[2]);
+}
+
+template <typename AT>
+__device__ __forceinline__ bool load_geo(const GaussArgs& A, long long g, Geo& G) {
+  load_mean_scale<AT>(A, g, G);
+  return finish_geo<AT>(A, g, G);
 }
 
 // Projection of one Gaussian into one camera, with the intermediates the backward needs.
@@ -233,6 +244,28 @@ __device__ __forceinline__ bool project(const Geo& G, const DevCam& c, float eps
          isfinite(P.op);
 }
 
+// A cheap test that is true only when project() is certain to cull: depth outside (near, far)
+// (the same decision), or a tile rectangle that is empty even for an upper bound of the radius.
+// Bound: lambda_max of J W Sigma W^T J^T <= ||J||_F^2 max(scale)^2, the dilation adds eps and
+// the max(0.1, .) of the radius rule at most sqrt(0.1); 1% and 2 px of slack cover FP32 rounding.
+__device__ __forceinline__ bool surely_culled(const Geo& G, const DevCam& c, float eps) {
+  const float* W = c.R;
+  const float tz = fmaf(W[6], G.m[0], fmaf(W[7], G.m[1], fmaf(W[8], G.m[2], c.t[2])));
+  if (!(tz > c.znear && tz < c.zfar)) return true;
+  const float tx = fmaf(W[0], G.m[0], fmaf(W[1], G.m[1], fmaf(W[2], G.m[2], c.t[0])));
+  const float ty = fmaf(W[3], G.m[0], fmaf(W[4], G.m[1], fmaf(W[5], G.m[2], c.t[1])));
+  const float iz = 1.f / tz;
+  const float uc = fminf(fmaxf(tx * iz, -c.limx), c.limx);
+  const float wc = fminf(fmaxf(ty * iz, -c.limy), c.limy);
+  const float smax = fmaxf(G.s[0], fmaxf(G.s[1], G.s[2]));
+  const float jf2 = (c.fx * c.fx * (1.f + uc * uc) + c.fy * c.fy * (1.f + wc * wc)) * iz * iz;
+  const float rb = 3.f * sqrtf(jf2 * smax * smax + eps + 0.31623f) * 1.01f + 2.f;
+  const float mx = c.fx * tx * iz + c.cx;
+  const float my = c.fy * ty * iz + c.cy;
+  return (mx + rb < 1.f) || (mx - rb >= static_cast<float>(kTile * c.tiles_x)) || (my + rb < 1.f) ||
+         (my - rb >= static_cast<float>(kTile * c.tiles_y));
+}
+
 template <typename ST>
 __device__ __forceinline__ void eval_color(const GaussArgs& A, long long g, const Geo& G, const DevCam& c,
                                            float rgb[3], float dir[3], float& dnorm, float Y[16],
@@ -257,36 +290,130 @@ __device__ __forceinline__ void eval_color(const GaussArgs& A, long long g, cons
   rgb[0] = fmaxf(v0, 0.f); rgb[1] = fmaxf(v1, 0.f); rgb[2] = fmaxf(v2, 0.f);
 }
 
-// One block covers kPreTile = 1024 consecutive Gaussians, four per thread (thread t owns
-// i = base + j * 256 + t, so each load instruction is coalesced). Phase 1 only decides which
-// cameras see each Gaussian; the per-block count of visible records, packed as four 16-bit
-// lanes (one per j), is scanned in the block, and one warp gets the block's offset from its
-// predecessors' (decoupled look-back). Phase 2 recomputes the visible ones and writes their
-// records in (i, camera) order.
+// The Gaussian's SH coefficients of degree <= deg, in registers (zero beyond them).
+template <typename ST>
+__device__ __forceinline__ void load_sh_row(const GaussArgs& A, long long g, float shv[48]) {
+  const int n3 = (A.deg + 1) * (A.deg + 1) * 3;
+  const ST* sh = static_cast<const ST*>(A.sh) + g * A.K * 3;
+  if (std::is_same<ST, float>::value && A.sh_vec4) {
+    const float4* row = reinterpret_cast<const float4*>(sh);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const float4 v = 4 * k < n3 ? __ldg(row + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+      shv[4 * k] = v.x; shv[4 * k + 1] = v.y; shv[4 * k + 2] = v.z; shv[4 * k + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 48; ++k) shv[k] = k < n3 ? ldf(sh, k) : 0.f;
+  }
+#pragma unroll
+  for (int k = 0; k < 48; ++k)
+    if (k >= n3) shv[k] = 0.f;
+}
+
+// eval_color with the coefficients already in registers.
+__device__ __forceinline__ void eval_color_regs(int deg, const Geo& G, const DevCam& c, const float shv[48],
+                                                float rgb[3], float dir[3], float& dnorm, float Y[16],
+                                                bool clamped[3]) {
+  const float dx = G.m[0] - c.center[0], dy = G.m[1] - c.center[1], dz = G.m[2] - c.center[2];
+  dnorm = sqrtf(dx * dx + dy * dy + dz * dz);
+  const float inv = 1.f / dnorm;
+  dir[0] = dx * inv; dir[1] = dy * inv; dir[2] = dz * inv;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) Y[k] = 0.f;
+  sh_basis(deg, dir[0], dir[1], dir[2], Y);
+  float v0 = 0.5f, v1 = 0.5f, v2 = 0.5f;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    v0 = fmaf(shv[3 * k + 0], Y[k], v0);
+    v1 = fmaf(shv[3 * k + 1], Y[k], v1);
+    v2 = fmaf(shv[3 * k + 2], Y[k], v2);
+  }
+  clamped[0] = v0 < 0.f; clamped[1] = v1 < 0.f; clamped[2] = v2 < 0.f;
+  rgb[0] = fmaxf(v0, 0.f); rgb[1] = fmaxf(v1, 0.f); rgb[2] = fmaxf(v2, 0.f);
+}
+
+// Position of the n-th (0-based) set bit of m.
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int n) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1) {
+    const uint32_t lo = m & ((1u << w) - 1u);
+    const int c = __popc(lo);
+    if (n >= c) {
+      n -= c;
+      m >>= w;
+      pos += w;
+    } else {
+      m = lo;
+    }
+  }
+  return pos;
+}
+
+// One block covers kPreTile = 1024 consecutive Gaussians, four per thread (thread t owns slot
+// j * 256 + t, i = base + slot, so each load instruction is coalesced).
+//   1a: a cheap conservative test per (Gaussian, camera) drops what is certainly outside.
+//   1b: each warp gathers its surviving Gaussians (of its 128 slots) and spreads them over its
+//       32 lanes for the exact projection, so a warp does not run the long path for a few lanes.
+//   The per-block count of visible records (four 16-bit lanes, one per j) is scanned in the
+//   block and one warp takes the block's offset from its predecessors (decoupled look-back).
+//   2: visible (Gaussian, camera) records are spread over the lanes the same way and written
+//      in (i, camera) order.
 template <typename AT, typename ST>
 __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArgs A, CamBatch cams, float eps, int aa,
                                                                        PreOut out) {
   __shared__ unsigned s_bid;
   __shared__ unsigned long long s_excl;
+  __shared__ uint32_t s_aux[kPreTile];   // 1a: cameras that survive the cheap test; 2: record offset
+  __shared__ uint32_t s_mask[kPreTile];  // exact visibility bits per slot
   if (threadIdx.x == 0) s_bid = atomicAdd(out.counter, 1u);
   __syncthreads();
   const unsigned bid = s_bid;
   const long long base_i = static_cast<long long>(bid) * kPreTile;
+  const int lane = threadIdx.x & 31, wslot = threadIdx.x & ~31;
+  uint32_t bal[kPreItems], cum[kPreItems + 1];
+  cum[0] = 0;
+#pragma unroll
+  for (int j = 0; j < kPreItems; ++j) {
+    const long long i = base_i + j * kPreThreads + threadIdx.x;
+    uint32_t maybe = 0;
+    if (i < A.n_render) {
+      Geo G;
+      load_mean_scale<AT>(A, seg_map(A.segs, i), G);
+      for (int c = 0; c < cams.C; ++c)
+        if (!surely_culled(G, cams.cam[c], eps)) maybe |= 1u << c;
+    }
+    s_aux[j * kPreThreads + threadIdx.x] = maybe;
+    s_mask[j * kPreThreads + threadIdx.x] = 0;
+    bal[j] = __ballot_sync(0xffffffffu, maybe != 0);
+    cum[j + 1] = cum[j] + __popc(bal[j]);
+  }
+  __syncwarp();
+  for (uint32_t r = 0; r < cum[kPreItems]; r += 32) {
+    const uint32_t k = r + lane;
+    if (k < cum[kPreItems]) {
+      const int j = (k >= cum[1]) + (k >= cum[2]) + (k >= cum[3]);
+      const int slot = j * kPreThreads + wslot + nth_set_bit(bal[j], static_cast<int>(k - cum[j]));
+      const uint32_t maybe = s_aux[slot];
+      Geo G;
+      uint32_t vis = 0;
+      if (load_geo<AT>(A, seg_map(A.segs, base_i + slot), G)) {
+        for (int c = 0; c < cams.C; ++c) {
+          if (!(maybe & (1u << c))) continue;
+          Proj P;
+          if (project(G, cams.cam[c], eps, aa, P)) vis |= 1u << c;
+        }
+      }
+      s_mask[slot] = vis;
+    }
+  }
+  __syncwarp();
   uint32_t mask[kPreItems];
   unsigned long long packed = 0;
 #pragma unroll
   for (int j = 0; j < kPreItems; ++j) {
-    const long long i = base_i + j * kPreThreads + threadIdx.x;
-    mask[j] = 0;
-    if (i < A.n_render) {
-      Geo G;
-      if (load_geo<AT>(A, seg_map(A.segs, i), G)) {
-        for (int c = 0; c < cams.C; ++c) {
-          Proj P;
-          if (project(G, cams.cam[c], eps, aa, P)) mask[j] |= 1u << c;
-        }
-      }
-    }
+    mask[j] = s_mask[j * kPreThreads + threadIdx.x];
     packed |= static_cast<unsigned long long>(__popc(mask[j])) << (16 * j);
   }
   unsigned long long tot_packed;
@@ -306,29 +433,42 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
   const unsigned long long block_base = s_excl;
   if (threadIdx.x == 0 && base_i <= A.n_render - 1 && A.n_render - 1 < base_i + kPreTile)
     *out.v_total = static_cast<uint32_t>(block_base + total);
+  // phase 2: the first record index of every visible slot, then the records, spread over lanes
+  cum[0] = 0;
 #pragma unroll
   for (int j = 0; j < kPreItems; ++j) {
-    if (!mask[j]) continue;
-    const long long i = base_i + j * kPreThreads + threadIdx.x;
+    s_aux[j * kPreThreads + threadIdx.x] =
+        static_cast<uint32_t>(block_base + lane_base[j] + ((excl_packed >> (16 * j)) & 0xffffu));
+    bal[j] = __ballot_sync(0xffffffffu, mask[j] != 0);
+    cum[j + 1] = cum[j] + __popc(bal[j]);
+  }
+  __syncwarp();
+  for (uint32_t r = 0; r < cum[kPreItems]; r += 32) {
+    const uint32_t k = r + lane;
+    if (k >= cum[kPreItems]) continue;
+    const int j = (k >= cum[1]) + (k >= cum[2]) + (k >= cum[3]);
+    const int slot = j * kPreThreads + wslot + nth_set_bit(bal[j], static_cast<int>(k - cum[j]));
+    const uint32_t vis = s_mask[slot];
+    const long long i = base_i + slot;
     const long long g = seg_map(A.segs, i);
     Geo G;
     load_geo<AT>(A, g, G);
-    unsigned long long v = block_base + lane_base[j] + ((excl_packed >> (16 * j)) & 0xffffu);
+    unsigned long long v = s_aux[slot];
     for (int c = 0; c < cams.C; ++c) {
-      if (!(mask[j] & (1u << c))) continue;
+      if (!(vis & (1u << c))) continue;
       const DevCam& cam = cams.cam[c];
       Proj P;
       project(G, cam, eps, aa, P);
       float rgb[3], dir[3], dn, Y[16];
       bool cl[3];
       eval_color<ST>(A, g, G, cam, rgb, dir, dn, Y, cl);
-      Rec r;
-      r.a = make_float4(P.mx, P.my, P.op, P.t[2]);
-      r.b = make_float4(P.ca, P.cb, P.cc, rgb[0]);
+      Rec rr;
+      rr.a = make_float4(P.mx, P.my, P.op, P.t[2]);
+      rr.b = make_float4(P.ca, P.cb, P.cc, rgb[0]);
       const uint32_t lo = static_cast<uint32_t>(P.x0) | (static_cast<uint32_t>(P.x1) << 16);
       const uint32_t hi = static_cast<uint32_t>(P.y0) | (static_cast<uint32_t>(P.y1) << 16) |
                           (static_cast<uint32_t>(c) << 27);
-      r.c = make_float4(rgb[1], rgb[2], __uint_as_float(lo), __uint_as_float(hi));
+      rr.c = make_float4(rgb[1], rgb[2], __uint_as_float(lo), __uint_as_float(hi));
       // Where op' exp(-d^T Q d / 2) >= 1/255, i.e. d^T Q d <= 2 ln(255 op'): an ellipse whose
       // half-extents are sqrt(2 ln(255 op') Sigma_xx) and sqrt(2 ln(255 op') Sigma_yy), Sigma the
       // dilated covariance. Widened by 0.1% + 0.01 px so FP32 evaluation never falls outside.
@@ -336,11 +476,11 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
       if (L > 0.f) {
         const float ex = sqrtf(2.f * L * (P.ar + eps)) * 1.001f + 0.01f;
         const float ey = sqrtf(2.f * L * (P.cr + eps)) * 1.001f + 0.01f;
-        r.d = make_float4(P.mx - ex, P.mx + ex, P.my - ey, P.my + ey);
+        rr.d = make_float4(P.mx - ex, P.mx + ex, P.my - ey, P.my + ey);
       } else {
-        r.d = make_float4(1.f, -1.f, 1.f, -1.f);  // empty: no pixel reaches 1/255
+        rr.d = make_float4(1.f, -1.f, 1.f, -1.f);  // empty: no pixel reaches 1/255
       }
-      out.rec[v] = r;
+      out.rec[v] = rr;
       out.depth_keys[v] = __float_as_uint(P.t[2]);
       out.depth_vals[v] = static_cast<uint32_t>(v);
       out.touched[v] = static_cast<uint32_t>((P.x1 - P.x0) * (P.y1 - P.y0));
@@ -362,6 +502,8 @@ __global__ void __launch_bounds__(kBwdThreads) preprocess_bwd_kernel(
   const uint32_t i = owner[v0];
   if (v0 > 0 && owner[v0 - 1] == i) return;  // not the Gaussian's first record
   const long long g = seg_map(A.segs, i);
+  float shv[48];
+  load_sh_row<ST>(A, g, shv);
   Geo G;
   if (!load_geo<AT>(A, g, G)) return;  // cannot happen for a Gaussian with a record
   float dm[3] = {0, 0, 0}, ds[3] = {0, 0, 0}, dopac = 0.f, dabs[2] = {0, 0};
@@ -371,7 +513,6 @@ __global__ void __launch_bounds__(kBwdThreads) preprocess_bwd_kernel(
   float dR[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   const int KC = A.K * 3;
   const int nb = (A.deg + 1) * (A.deg + 1);
-  const ST* sh = static_cast<const ST*>(A.sh) + g * KC;
   for (long long v = v0; v < V && owner[v] == i; ++v) {
     const DevCam& cam = cams.cam[rec_cam(rec[v])];
     Proj P;
@@ -385,7 +526,7 @@ __global__ void __launch_bounds__(kBwdThreads) preprocess_bwd_kernel(
     // colour: rgb = max(0, sum_k sh_k Y_k(dir) + 0.5)
     float rgb[3], dir[3], dn, Y[16];
     bool cl[3];
-    eval_color<ST>(A, g, G, cam, rgb, dir, dn, Y, cl);
+    eval_color_regs(A.deg, G, cam, shv, rgb, dir, dn, Y, cl);
     for (int ch = 0; ch < 3; ++ch)
       if (cl[ch]) drgb[ch] = 0.f;
     float wY[16];
@@ -396,7 +537,7 @@ __global__ void __launch_bounds__(kBwdThreads) preprocess_bwd_kernel(
         dsh[3 * k + 0] += Y[k] * drgb[0];
         dsh[3 * k + 1] += Y[k] * drgb[1];
         dsh[3 * k + 2] += Y[k] * drgb[2];
-        wY[k] = ldf(sh, 3 * k) * drgb[0] + ldf(sh, 3 * k + 1) * drgb[1] + ldf(sh, 3 * k + 2) * drgb[2];
+        wY[k] = shv[3 * k] * drgb[0] + shv[3 * k + 1] * drgb[1] + shv[3 * k + 2] * drgb[2];
       }
     }
     float gx, gy, gz;

@@ -163,6 +163,11 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, long long P, ui
   if (i == P - 1 || keys[i + 1] != t) ranges[t].y = static_cast<uint32_t>(i + 1);
 }
 
+// sigma beyond which alpha = o' exp(-sigma) is certainly below 1/255: ln(255 o'), plus a margin
+// far above FP32 rounding, so that the cheap test never rejects what the exact test keeps.
+__device__ __forceinline__ float sigma_cutoff(float op) { return logf(255.f * op) * 1.001f + 1e-3f; }
+
+template <bool kCount>
 __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(const Rec* __restrict__ rec,
                                                                   const uint32_t* __restrict__ pvals,
                                                                   const uint2* __restrict__ ranges, CamBatch cams,
@@ -172,6 +177,7 @@ __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(const Rec* __r
   __shared__ float4 sB[kBatch];
   __shared__ float2 sC[kBatch];
   __shared__ uint32_t sM[kBatch];
+  __shared__ float sL[kBatch];
   const int t = blockIdx.x;
   const int c = find_cam(cams, t);
   const DevCam& cam = cams.cam[c];
@@ -201,6 +207,7 @@ __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(const Rec* __r
         sB[k] = r.b;
         sC[k] = make_float2(r.c.x, r.c.y);
         sM[k] = warp_rows_mask(r.d, x_lo, x_hi, y_base);
+        sL[k] = sigma_cutoff(r.a.z);
       }
     }
     __syncthreads();
@@ -209,14 +216,15 @@ __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(const Rec* __r
       if (!((sM[j] >> wid) & 1u)) continue;  // no pixel of this warp can reach alpha 1/255
       const float4 a = sA[j];
       const float4 b = sB[j];
+      const float cut = sL[j];
       const float dx = a.x - fx;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         if (done[q]) continue;
-        ++n_eval;
+        if (kCount) ++n_eval;
         const float dy = a.y - fy[q];
         const float sigma = 0.5f * (b.x * dx * dx + b.z * dy * dy) + b.y * dx * dy;
-        if (sigma < 0.f) continue;
+        if (sigma < 0.f || sigma > cut) continue;
         const float alpha = fminf(kAlphaMax, a.z * __expf(-sigma));
         if (alpha < kAlphaMin) continue;
         const float Tn = T[q] * (1.f - alpha);
@@ -232,11 +240,11 @@ __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(const Rec* __r
         D[q] = fmaf(a.w, wgt, D[q]);
         T[q] = Tn;
         last[q] = static_cast<uint32_t>(base + j + 1);
-        ++n_blend;
+        if (kCount) ++n_blend;
       }
     }
   }
-  if (counters) {
+  if (kCount) {
     unsigned long long e = n_eval, b = n_blend;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -282,6 +290,39 @@ __device__ __forceinline__ float warp_sum(float x) {
 
 constexpr int kGradVals = 12;
 
+// Sums 16 per-lane values over the warp with 16 shuffles instead of 16 x 5: at each halving
+// step a lane sends the half it gives up to its partner and keeps the sum of the other half.
+// Afterwards lanes 2k and 2k+1 both hold the warp total of value k (k < 16).
+__device__ __forceinline__ float warp_transpose_sum16(float v[16], int lane) {
+  float w8[8], w4[4], w2[2];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const bool up = lane & 16;
+    const float send = up ? v[k] : v[k + 8];
+    const float keep = up ? v[k + 8] : v[k];
+    w8[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const bool up = lane & 8;
+    const float send = up ? w8[k] : w8[k + 4];
+    const float keep = up ? w8[k + 4] : w8[k];
+    w4[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const bool up = lane & 4;
+    const float send = up ? w4[k] : w4[k + 2];
+    const float keep = up ? w4[k + 2] : w4[k];
+    w2[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  const bool up = lane & 2;
+  float x = (up ? w2[1] : w2[0]) + __shfl_xor_sync(0xffffffffu, up ? w2[0] : w2[1], 2);
+  x += __shfl_xor_sync(0xffffffffu, x, 1);
+  return x;
+}
+
+template <bool kCount>
 __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __restrict__ rec,
                                                                   const uint32_t* __restrict__ pvals,
                                                                   const uint2* __restrict__ ranges, CamBatch cams,
@@ -293,6 +334,7 @@ __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __r
   __shared__ float2 sC[kBatch];
   __shared__ uint32_t sV[kBatch];
   __shared__ uint32_t sM[kBatch];
+  __shared__ float sL[kBatch];
   __shared__ float sAcc[kBatch][kGradVals + 1];
   __shared__ uint32_t s_max;
   __shared__ float s_aff[kBlendWarps][12];
@@ -368,6 +410,7 @@ __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __r
         sC[k] = make_float2(r.c.x, r.c.y);
         sV[k] = v;
         sM[k] = warp_rows_mask(r.d, x_lo, x_hi, y_base);
+        sL[k] = sigma_cutoff(r.a.z);
       }
 #pragma unroll
       for (int m = 0; m < kGradVals; ++m) sAcc[k][m] = 0.f;
@@ -377,27 +420,28 @@ __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __r
     for (int j = 0; j < cnt; ++j) {
       if (!((sM[j] >> wid) & 1u)) continue;  // warp-uniform: no pixel of this warp is touched
       const uint32_t pos = static_cast<uint32_t>(n - 1 - base - j);
-      float gv[kGradVals];
+      float gv[16];
 #pragma unroll
-      for (int m = 0; m < kGradVals; ++m) gv[m] = 0.f;
+      for (int m = 0; m < 16; ++m) gv[m] = 0.f;
       bool contrib = false;
       const float4 a = sA[j];
       const float4 b = sB[j];
       const float2 cc = sC[j];
+      const float cut = sL[j];
       const float dx = a.x - fx;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         if (!(inside[q] && pos < last[q])) continue;
-        ++n_visit;
+        if (kCount) ++n_visit;
         const float dy = a.y - fy[q];
         const float sigma = 0.5f * (b.x * dx * dx + b.z * dy * dy) + b.y * dx * dy;
-        if (sigma < 0.f) continue;
+        if (sigma < 0.f || sigma > cut) continue;
         const float G = __expf(-sigma);
         const float araw = a.z * G;
         const float alpha = fminf(kAlphaMax, araw);
         if (alpha < kAlphaMin) continue;
         contrib = true;
-        ++n_contrib;
+        if (kCount) ++n_contrib;
         const float om = 1.f - alpha;
         const float Ti = T[q] / om;
         const float wgt = alpha * Ti;
@@ -427,14 +471,9 @@ __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __r
         gv[11] += fabsf(dmy);
       }
       if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-        for (int m = 0; m < kGradVals; ++m)
-          if (m < kGradVals - 2 || absgrad) gv[m] = warp_sum(gv[m]);
-        if (lane == 0) {
-#pragma unroll
-          for (int m = 0; m < kGradVals; ++m)
-            if (m < kGradVals - 2 || absgrad) atomicAdd(&sAcc[j][m], gv[m]);
-        }
+        const float tot = warp_transpose_sum16(gv, lane);
+        const int m = lane >> 1;
+        if (!(lane & 1) && m < kGradVals && (m < kGradVals - 2 || absgrad)) atomicAdd(&sAcc[j][m], tot);
       }
     }
     __syncthreads();
@@ -448,7 +487,7 @@ __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __r
       }
     }
   }
-  if (counters) {
+  if (kCount) {
     unsigned long long e = n_visit, b = n_contrib;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -513,16 +552,24 @@ void launch_ranges(const uint32_t* sorted_keys, long long P, uint2* ranges, cuda
 void launch_blend_fwd(const Rec* rec, const uint32_t* pair_vals, const uint2* ranges, const CamBatch& cams,
                       const float* bg, const BlendFwdOut& out, unsigned long long* counters, cudaStream_t s) {
   if (cams.total_tiles <= 0) return;
-  blend_fwd_kernel<<<cams.total_tiles, kBlendThreads, 0, s>>>(rec, pair_vals, ranges, cams, make_float3(bg[0], bg[1], bg[2]),
-                                                         out, counters);
+  const float3 b3 = make_float3(bg[0], bg[1], bg[2]);
+  if (counters)
+    blend_fwd_kernel<true><<<cams.total_tiles, kBlendThreads, 0, s>>>(rec, pair_vals, ranges, cams, b3, out, counters);
+  else
+    blend_fwd_kernel<false><<<cams.total_tiles, kBlendThreads, 0, s>>>(rec, pair_vals, ranges, cams, b3, out, nullptr);
 }
 
 void launch_blend_bwd(const Rec* rec, const uint32_t* pair_vals, const uint2* ranges, const CamBatch& cams,
                       const float* bg, const BlendBwdIn& in, Grad2D* g2d, float* g_aff, int absgrad,
                       unsigned long long* counters, cudaStream_t s) {
   if (cams.total_tiles <= 0) return;
-  blend_bwd_kernel<<<cams.total_tiles, kBlendThreads, 0, s>>>(rec, pair_vals, ranges, cams, make_float3(bg[0], bg[1], bg[2]),
-                                                         in, g2d, g_aff, absgrad, counters);
+  const float3 b3 = make_float3(bg[0], bg[1], bg[2]);
+  if (counters)
+    blend_bwd_kernel<true><<<cams.total_tiles, kBlendThreads, 0, s>>>(rec, pair_vals, ranges, cams, b3, in, g2d, g_aff,
+                                                                      absgrad, counters);
+  else
+    blend_bwd_kernel<false><<<cams.total_tiles, kBlendThreads, 0, s>>>(rec, pair_vals, ranges, cams, b3, in, g2d, g_aff,
+                                                                       absgrad, nullptr);
 }
 
 }  // namespace gsr
