@@ -219,7 +219,9 @@ typedef enum gsr_stage {
   GSR_STAGE_BLEND_FWD = 8,      /* forward compositing */
   GSR_STAGE_BLEND_BWD = 9,      /* backward compositing */
   GSR_STAGE_PREPROCESS_BWD = 10,/* projection and colour backward */
-  GSR_NUM_STAGES = 11
+  GSR_STAGE_BETWEEN = 11,       /* idle time between consecutive stages (memsets, host waits,
+                                   launch latency), gaps of 1 ms or more excluded */
+  GSR_NUM_STAGES = 12
 } gsr_stage;
 
 /* Counters gathered while profiling with count_evals = 1. */
@@ -234,6 +236,10 @@ typedef enum gsr_counter {
 /* on = 1 records CUDA events around every stage of later calls; count_evals = 1 also counts
  * blend evaluations (slightly slower kernels). */
 gsr_status gsr_profile_enable(gsr_ctx* ctx, int32_t on, int32_t count_evals);
+/* Restricts the recorded events to the stages whose bit is set in stage_mask (bit k = stage k;
+ * all stages by default). Timing one kernel inside a longer loop this way adds two events per
+ * launch instead of two per stage. GSR_STAGE_BETWEEN is only meaningful with all stages on. */
+gsr_status gsr_profile_select(gsr_ctx* ctx, uint32_t stage_mask);
 /* Waits for every recorded event, adds the elapsed milliseconds and launch counts of each stage
  * since the last collect into ms[GSR_NUM_STAGES] and launches[GSR_NUM_STAGES] (either may be
  * NULL), the counters into counters[GSR_NUM_COUNTERS] (may be NULL), then clears them. */
@@ -255,11 +261,11 @@ gsr_status gsr_sort_pairs_u32(gsr_ctx* ctx, const uint32_t* keys_in, const uint3
  * runs inside another framework's allocator. It calls no cudaMalloc, cudaFree or allocating
  * library routine. The paper has no counterpart: this is a deployment variant of the sort.
  *   Limit: n <= 262144 (2^18); a larger n returns GSR_ERR_UNSUPPORTED without doing anything.
- *   Scratch: one static device array of about 2.6 MB inside libgsr, reserved on every GPU that
+ *   Scratch: one static device array of about 2.9 MB inside libgsr, reserved on every GPU that
  *     loads the library until the process exits and shared by every call. Calls that overlap
  *     on the GPU (two streams, or two host threads) race on it and give wrong results:
- *     serialise them on one stream. Each call clears what must start at zero (histograms,
- *     block counters, look-back status words) with stream-ordered memsets before its kernels.
+ *     serialise them on one stream. Each call resets what must start at zero (histograms and
+ *     block counters by its own kernels, look-back status words by a stream-ordered memset).
  *   The first call on a device looks up the array's device address with that device current;
  *     make that first call before any stream capture.
  *   device_err: device int32, or NULL; a bounded wait that runs out ORs 1 into it (the output

@@ -39,7 +39,7 @@ struct gsr_ctx {
   // scratch
   Buf seg_begin, seg_start;
   Buf rec, dkeys, dvals, touched, owner;  // binning (recompute / no-state mode)
-  Buf dkeys_s, dvals_s, sort_ktmp, sort_vtmp, sort_hist, sort_status, sort_counters;
+  Buf dkeys_s, dvals_s, sort_ktmp, sort_vtmp, sort_hist, sort_hist_blocks, sort_status, sort_counters;
   Buf cnt_sorted, offsets, pre_status, scan_status, misc;
   Buf pkeys, pvals, pkeys_s, pvals_s, ranges;  // pairs (no-state mode)
   Buf pix_T, pix_n, pix_D;                     // per-pixel state (no-state mode)
@@ -55,6 +55,7 @@ struct gsr_ctx {
     cudaEvent_t a, b;
   };
   std::vector<Rec3> prof_recs;
+  uint32_t prof_mask = 0xffffffffu;  // stages whose events are recorded (bit k = stage k)
   std::vector<cudaEvent_t> ev_pool;
   // released forward states kept with their buffers for reuse (stream-ordered, no sync)
   std::vector<gsr_fwd_state*> state_pool;
@@ -168,6 +169,7 @@ SortScratch sort_scratch(gsr_ctx* ctx) {
   sc.keys_tmp = as<uint32_t>(ctx->sort_ktmp);
   sc.vals_tmp = as<uint32_t>(ctx->sort_vtmp);
   sc.hist = as<uint32_t>(ctx->sort_hist);
+  sc.hist_blocks = as<uint32_t>(ctx->sort_hist_blocks);
   sc.status = as<unsigned long long>(ctx->sort_status);
   sc.counters = as<uint32_t>(ctx->sort_counters);
   sc.grid_cap = ctx->grid_cap;
@@ -178,6 +180,7 @@ bool ensure_sort(gsr_ctx* ctx, long long n, cudaStream_t s) {
   const size_t words = sort_status_words(n) * 4;  // four passes at most
   return ensure(ctx, ctx->sort_ktmp, sizeof(uint32_t) * n, s) && ensure(ctx, ctx->sort_vtmp, sizeof(uint32_t) * n, s) &&
          ensure(ctx, ctx->sort_hist, sizeof(uint32_t) * 4 * 256, s) &&
+         ensure(ctx, ctx->sort_hist_blocks, sizeof(uint32_t) * 4 * 256 * kMaxHistBlocks, s) &&
          ensure_zeroed(ctx, ctx->sort_status, sizeof(unsigned long long) * words, s) &&
          ensure(ctx, ctx->sort_counters, sizeof(uint32_t) * 4, s);
 }
@@ -207,7 +210,7 @@ struct StageTimer {
   cudaStream_t s;
   cudaEvent_t a = nullptr;
   StageTimer(gsr_ctx* c, int st, cudaStream_t str) : ctx(c), stage(st), s(str) {
-    if (ctx->prof && (a = take_event(ctx))) cudaEventRecord(a, s);
+    if (ctx->prof && ((ctx->prof_mask >> st) & 1u) && (a = take_event(ctx))) cudaEventRecord(a, s);
   }
   ~StageTimer() {
     if (!a) return;
@@ -464,8 +467,6 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   GSR_TRY_ALLOC(ctx->pkeys_s, sizeof(uint32_t) * Pc);
   GSR_TRY_ALLOC(*bo.pvals_s, sizeof(uint32_t) * Pc);
   GSR_TRY_ALLOC(*bo.ranges, sizeof(uint2) * std::max(cb.total_tiles, 1));
-  e = cudaMemsetAsync(bo.ranges->p, 0, sizeof(uint2) * std::max(cb.total_tiles, 1), s);
-  if (e != cudaSuccess) return cuda_err(ctx, e, "memset ranges");
   if (P > 0) {
     if (!ensure_sort(ctx, Pc, s)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
     sc = sort_scratch(ctx);
@@ -480,8 +481,15 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
       radix_sort_u32(as<uint32_t>(ctx->pkeys), as<uint32_t>(ctx->pvals), as<uint32_t>(ctx->pkeys_s),
                      as<uint32_t>(*bo.pvals_s), nullptr, P, 0, tb, sc, next_epoch(ctx, s), false, ctx->d_err, s);
     }
+  }
+  {
     StageTimer tm(ctx, GSR_STAGE_RANGES, s);
-    launch_ranges(as<uint32_t>(ctx->pkeys_s), P, as<uint2>(*bo.ranges), s);
+    if (P > 0) {
+      launch_ranges(as<uint32_t>(ctx->pkeys_s), P, cb.total_tiles, as<uint2>(*bo.ranges), s);
+    } else {
+      e = cudaMemsetAsync(bo.ranges->p, 0, sizeof(uint2) * std::max(cb.total_tiles, 1), s);
+      if (e != cudaSuccess) return cuda_err(ctx, e, "memset ranges");
+    }
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(ctx, e, "pair launch");
@@ -542,7 +550,11 @@ gsr_status gsr_create(gsr_ctx** out, int device, const gsr_allocator* alloc) {
       ctx->pool = nullptr;  // fall back to cudaMalloc / cudaFree
     }
   }
-  if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+  // the side stream carries the gradient fill; high priority lets its blocks take the SM room
+  // the blend backward leaves instead of queueing behind that kernel's blocks
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  if (cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
@@ -564,7 +576,7 @@ void gsr_destroy(gsr_ctx* ctx) {
   ctx->state_pool.clear();
   Buf* all[] = {&ctx->seg_begin, &ctx->seg_start, &ctx->rec, &ctx->dkeys, &ctx->dvals, &ctx->touched,
                 &ctx->owner, &ctx->dkeys_s, &ctx->dvals_s, &ctx->sort_ktmp, &ctx->sort_vtmp,
-                &ctx->sort_hist, &ctx->sort_status, &ctx->sort_counters, &ctx->cnt_sorted, &ctx->offsets,
+                &ctx->sort_hist, &ctx->sort_hist_blocks, &ctx->sort_status, &ctx->sort_counters, &ctx->cnt_sorted, &ctx->offsets,
                 &ctx->pre_status, &ctx->scan_status, &ctx->misc, &ctx->pkeys, &ctx->pvals, &ctx->pkeys_s, &ctx->pvals_s,
                 &ctx->ranges, &ctx->pix_T, &ctx->pix_n, &ctx->pix_D, &ctx->g2d, &ctx->gaff};
   for (Buf* b : all) release(ctx, *b, nullptr);
@@ -727,12 +739,18 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
     const size_t n = static_cast<size_t>(g->n);
     e = cudaEventRecord(ctx->ev_fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
-    if (e == cudaSuccess) e = cudaMemsetAsync(grads->means, 0, sizeof(float) * 3 * n, ctx->side);
-    if (e == cudaSuccess) e = cudaMemsetAsync(grads->scales, 0, sizeof(float) * 3 * n, ctx->side);
-    if (e == cudaSuccess) e = cudaMemsetAsync(grads->quats, 0, sizeof(float) * 4 * n, ctx->side);
-    if (e == cudaSuccess) e = cudaMemsetAsync(grads->opacities, 0, sizeof(float) * n, ctx->side);
-    if (e == cudaSuccess) e = cudaMemsetAsync(grads->sh, 0, sizeof(float) * 3 * g->sh_coeffs * n, ctx->side);
-    if (e == cudaSuccess && grads->absgrad) e = cudaMemsetAsync(grads->absgrad, 0, sizeof(float) * 2 * n, ctx->side);
+    if (e == cudaSuccess) {
+      FillSpans f{};
+      const auto add = [&f](float* p, size_t len) { f.ptr[f.count] = p; f.len[f.count] = len; ++f.count; };
+      add(grads->means, 3 * n);
+      add(grads->scales, 3 * n);
+      add(grads->quats, 4 * n);
+      add(grads->opacities, n);
+      add(grads->sh, 3 * static_cast<size_t>(g->sh_coeffs) * n);
+      if (grads->absgrad) add(grads->absgrad, 2 * n);
+      launch_zero_fill(f, ctx->grid_cap / 2, ctx->side);
+      e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
     if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
   }
@@ -876,17 +894,33 @@ gsr_status gsr_profile_enable(gsr_ctx* ctx, int32_t on, int32_t count_evals) {
   return GSR_OK;
 }
 
+gsr_status gsr_profile_select(gsr_ctx* ctx, uint32_t stage_mask) {
+  if (!ctx) return GSR_ERR_INVALID_ARG;
+  ctx->prof_mask = stage_mask;
+  return GSR_OK;
+}
+
 gsr_status gsr_profile_collect(gsr_ctx* ctx, double* ms, int64_t* launches, int64_t* counters) {
   if (!ctx) return GSR_ERR_INVALID_ARG;
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  cudaEvent_t prev_end = nullptr;
   for (auto& r : ctx->prof_recs) {
-    float t = 0.f;
+    float t = 0.f, gap = 0.f;
     e = cudaEventSynchronize(r.b);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e == cudaSuccess && prev_end) e = cudaEventElapsedTime(&gap, prev_end, r.a);
     if (e != cudaSuccess) return cuda_err(ctx, e, "profile events");
-    if (ms) ms[r.stage] += t;
+    if (ms) {
+      ms[r.stage] += t;
+      // time between the end of one stage and the start of the next: memsets, host round
+      // trips, launch latency (gaps of 1 ms or more, between separate calls, are left out)
+      if (prev_end && gap > 0.f && gap < 1.0f) ms[GSR_STAGE_BETWEEN] += gap;
+    }
     if (launches) launches[r.stage] += 1;
+    prev_end = r.b;
+  }
+  for (auto& r : ctx->prof_recs) {
     ctx->ev_pool.push_back(r.a);
     ctx->ev_pool.push_back(r.b);
   }

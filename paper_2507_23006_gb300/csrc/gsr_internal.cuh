@@ -135,6 +135,14 @@ struct ParamGrads {
 
 void launch_preprocess_fwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased,
                            const PreOut& out, int blocks, cudaStream_t s);
+constexpr int kFillSpans = 6;
+struct FillSpans {
+  float* ptr[kFillSpans];
+  size_t len[kFillSpans];  // floats
+  int count;
+};
+// Sets `count` float arrays to zero with `blocks` resident blocks of 128 threads.
+void launch_zero_fill(const FillSpans& f, int blocks, cudaStream_t s);
 // Runs over the V visible records; the first record of each Gaussian writes its gradient rows
 // (the rows of Gaussians with no record must already be zero).
 void launch_preprocess_bwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased, long long V,
@@ -146,10 +154,12 @@ constexpr int kPreTile = kPreThreads * kPreItems;
 
 // Stable radix sort by key bits [begin_bit, end_bit); n taken from *d_n when d_n != nullptr
 // (then max_n bounds it and sizes the launch), else n = max_n.
+constexpr int kMaxHistBlocks = 512;  // blocks of the histogram pass (per-block rows, no atomics)
 struct SortScratch {
   uint32_t* keys_tmp;
   uint32_t* vals_tmp;
-  uint32_t* hist;                // [4][256]
+  uint32_t* hist;                // [4][256] exclusive digit offsets
+  uint32_t* hist_blocks;         // [kMaxHistBlocks][4][256] per-block histograms
   unsigned long long* status;    // [4][tiles][256] epoch-tagged look-back words
   uint32_t* counters;            // [4]
   int grid_cap;                  // blocks per onesweep launch (resident blocks loop over tiles)
@@ -177,7 +187,7 @@ void pair_offsets_scan(const uint32_t* touched, const uint32_t* order, const uin
 void launch_duplicate(const Rec* rec, const uint32_t* order, const uint32_t* offsets, const uint32_t* d_n,
                       long long max_n, const CamBatch& cams, int tile_cull, uint32_t* cnt_sorted,
                       uint32_t* pair_keys, uint32_t* pair_vals, cudaStream_t s);
-void launch_ranges(const uint32_t* sorted_keys, long long P, uint2* ranges, cudaStream_t s);
+void launch_ranges(const uint32_t* sorted_keys, long long P, int n_tiles, uint2* ranges, cudaStream_t s);
 
 struct BlendFwdOut {
   float* rgb;

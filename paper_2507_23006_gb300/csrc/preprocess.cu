@@ -690,6 +690,32 @@ void launch_preprocess_fwd(const GaussArgs& g, const CamBatch& cams, float eps2d
 #undef GSR_PRE
 }
 
+// Zero fill of up to kFillSpans float arrays in one launch: one 128-thread block per SM
+// (launched on a high-priority stream it is resident beside the blend backward, which leaves
+// room for it), 16-byte stores over each array's aligned body, scalar stores for the ends.
+__global__ void __launch_bounds__(128) zero_fill_kernel(FillSpans f) {
+  const size_t tid = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const size_t nthr = static_cast<size_t>(gridDim.x) * blockDim.x;
+  for (int k = 0; k < f.count; ++k) {
+    float* p = f.ptr[k];
+    const size_t n = f.len[k];
+    const size_t mis = (reinterpret_cast<uintptr_t>(p) >> 2) & 3u;
+    const size_t head = mis ? (4u - mis < n ? 4u - mis : n) : 0u;
+    const size_t n4 = (n - head) >> 2;
+    float4* body = reinterpret_cast<float4*>(p + head);
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (size_t i = tid; i < n4; i += nthr) body[i] = z;
+    const size_t done = head + 4 * n4;
+    if (tid < head) p[tid] = 0.f;
+    if (tid < n - done) p[done + tid] = 0.f;
+  }
+}
+
+void launch_zero_fill(const FillSpans& f, int blocks, cudaStream_t s) {
+  if (f.count <= 0) return;
+  zero_fill_kernel<<<blocks, 128, 0, s>>>(f);
+}
+
 void launch_preprocess_bwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased, long long V,
                            const Rec* rec, const uint32_t* owner, const Grad2D* g2d, const ParamGrads& out,
                            cudaStream_t s) {

@@ -155,12 +155,22 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const Rec* __restrict__ 
   if (kCount && valid) cnt_sorted[i] = s_cnt[w][lane];
 }
 
-__global__ void ranges_kernel(const uint32_t* __restrict__ keys, long long P, uint2* __restrict__ ranges) {
-  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= P) return;
-  const uint32_t t = keys[i];
-  if (i == 0 || keys[i - 1] != t) ranges[t].x = static_cast<uint32_t>(i);
-  if (i == P - 1 || keys[i + 1] != t) ranges[t].y = static_cast<uint32_t>(i + 1);
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__ a, uint32_t n, uint32_t key) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// One thread per tile: [first pair with key >= t, first pair with key >= t + 1) of the sorted
+// keys; every tile is written, so nothing needs clearing first.
+__global__ void ranges_kernel(const uint32_t* __restrict__ keys, uint32_t P, int n_tiles, uint2* __restrict__ ranges) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tiles) return;
+  ranges[t] = make_uint2(lower_bound_u32(keys, P, static_cast<uint32_t>(t)),
+                         lower_bound_u32(keys, P, static_cast<uint32_t>(t) + 1u));
 }
 
 // sigma beyond which alpha = o' exp(-sigma) is certainly below 1/255: ln(255 o'), plus a margin
@@ -544,9 +554,9 @@ void launch_duplicate(const Rec* rec, const uint32_t* order, const uint32_t* off
   }
 }
 
-void launch_ranges(const uint32_t* sorted_keys, long long P, uint2* ranges, cudaStream_t s) {
-  if (P <= 0) return;
-  ranges_kernel<<<static_cast<int>((P + 255) / 256), 256, 0, s>>>(sorted_keys, P, ranges);
+void launch_ranges(const uint32_t* sorted_keys, long long P, int n_tiles, uint2* ranges, cudaStream_t s) {
+  if (n_tiles <= 0) return;
+  ranges_kernel<<<(n_tiles + 255) / 256, 256, 0, s>>>(sorted_keys, static_cast<uint32_t>(P), n_tiles, ranges);
 }
 
 void launch_blend_fwd(const Rec* rec, const uint32_t* pair_vals, const uint2* ranges, const CamBatch& cams,

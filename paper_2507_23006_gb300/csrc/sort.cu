@@ -23,9 +23,11 @@ __device__ __forceinline__ long long device_n(const uint32_t* d_n, long long max
   return n < max_n ? n : max_n;
 }
 
+// Per-block digit histograms of every pass (no atomics on global memory, nothing to clear):
+// block b writes hist_blocks[b][pass][256].
 __global__ void __launch_bounds__(256) hist_kernel(const uint32_t* __restrict__ keys, const uint32_t* d_n,
                                                    long long max_n, int begin_bit, int end_bit, int passes,
-                                                   uint32_t* __restrict__ hist) {
+                                                   uint32_t* __restrict__ hist_blocks) {
   __shared__ uint32_t sh[4 * 256];
   for (int k = threadIdx.x; k < 4 * 256; k += blockDim.x) sh[k] = 0;
   __syncthreads();
@@ -40,17 +42,21 @@ __global__ void __launch_bounds__(256) hist_kernel(const uint32_t* __restrict__ 
     }
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < passes * 256; k += blockDim.x)
-    if (sh[k]) atomicAdd(&hist[k], sh[k]);
+  uint32_t* dst = hist_blocks + static_cast<size_t>(blockIdx.x) * 4 * 256;
+  for (int k = threadIdx.x; k < passes * 256; k += blockDim.x) dst[k] = sh[k];
 }
 
-// Exclusive scan of each pass's 256 digit counts, in place.
-__global__ void __launch_bounds__(256) hist_scan_kernel(uint32_t* hist) {
-  uint32_t* h = hist + blockIdx.x * 256;
-  const uint32_t x = h[threadIdx.x];
+// Sums the per-block histograms of pass blockIdx.x, writes the exclusive digit offsets to
+// hist[pass][256] and clears the pass's block counter.
+__global__ void __launch_bounds__(256) hist_scan_kernel(const uint32_t* __restrict__ hist_blocks, int nblocks,
+                                                        uint32_t* __restrict__ hist, uint32_t* counters) {
+  const int p = blockIdx.x;
+  uint32_t x = 0;
+  for (int b = 0; b < nblocks; ++b) x += hist_blocks[static_cast<size_t>(b) * 4 * 256 + p * 256 + threadIdx.x];
   uint32_t total;
   const uint32_t e = block_excl_scan(x, &total);
-  h[threadIdx.x] = e;
+  hist[p * 256 + threadIdx.x] = e;
+  if (threadIdx.x == 0) counters[p] = 0;
 }
 
 __device__ __forceinline__ uint32_t lookback_digit(unsigned long long* status, uint32_t bid, int d, uint32_t agg,
@@ -214,12 +220,11 @@ void radix_sort_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
   const long long tiles = (max_n + kSortTile - 1) / kSortTile;
   const size_t words = sort_status_words(max_n);
   const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>(tiles, sc.grid_cap)));
-  cudaMemsetAsync(sc.hist, 0, sizeof(uint32_t) * 256 * passes, s);
-  cudaMemsetAsync(sc.counters, 0, sizeof(uint32_t) * passes, s);
   if (clear_status) cudaMemsetAsync(sc.status, 0, sizeof(unsigned long long) * words * passes, s);
-  const int hblocks = static_cast<int>(std::min<long long>(sc.grid_cap, (max_n + 4095) / 4096));
-  hist_kernel<<<std::max(hblocks, 1), 256, 0, s>>>(keys_in, d_n, max_n, begin_bit, end_bit, passes, sc.hist);
-  hist_scan_kernel<<<passes, 256, 0, s>>>(sc.hist);
+  const int hblocks = std::max(1, static_cast<int>(std::min<long long>(std::min(sc.grid_cap, kMaxHistBlocks),
+                                                                       (max_n + 4095) / 4096)));
+  hist_kernel<<<hblocks, 256, 0, s>>>(keys_in, d_n, max_n, begin_bit, end_bit, passes, sc.hist_blocks);
+  hist_scan_kernel<<<passes, 256, 0, s>>>(sc.hist_blocks, hblocks, sc.hist, sc.counters);
   // ping-pong so that the last pass lands in keys_out; the inputs are never written
   const uint32_t* ksrc = keys_in;
   const uint32_t* vsrc = vals_in;

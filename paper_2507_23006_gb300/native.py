@@ -36,11 +36,11 @@ EXPORTED = [
     "gsr_create", "gsr_destroy", "gsr_status_string", "gsr_last_error", "gsr_workspace_query",
     "gsr_workspace_bytes", "gsr_render_forward", "gsr_render_backward", "gsr_state_release",
     "gsr_state_get_info", "gsr_state_copy", "gsr_sync_check", "gsr_sort_pairs_u32", "gsr_select_lod",
-    "gsr_profile_enable", "gsr_profile_collect", "gsr_sort_pairs_u32_noalloc",
+    "gsr_profile_enable", "gsr_profile_collect", "gsr_sort_pairs_u32_noalloc", "gsr_profile_select",
 ]
 
 STAGES = ["preprocess", "depth_sort", "tile_count", "pair_scan", "readback", "duplicate", "tile_sort", "ranges",
-          "blend_fwd", "blend_bwd", "preprocess_bwd"]
+          "blend_fwd", "blend_bwd", "preprocess_bwd", "between_stages"]
 COUNTERS = ["fwd_evals", "fwd_contribs", "bwd_evals", "bwd_contribs"]
 
 
@@ -140,12 +140,13 @@ def load(build_if_missing: bool = True):
                                                  vp, vp]
         L.gsr_profile_enable.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
         L.gsr_profile_collect.argtypes = [vp, vp, vp, vp]
+        L.gsr_profile_select.argtypes = [vp, ctypes.c_uint32]
         for name in EXPORTED:
             getattr(L, name)
         for name in ("gsr_create", "gsr_workspace_query", "gsr_render_forward", "gsr_render_backward",
                      "gsr_state_get_info", "gsr_state_copy", "gsr_sync_check", "gsr_sort_pairs_u32",
                      "gsr_select_lod", "gsr_profile_enable", "gsr_profile_collect",
-                     "gsr_sort_pairs_u32_noalloc"):
+                     "gsr_sort_pairs_u32_noalloc", "gsr_profile_select"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -334,7 +335,10 @@ class Context:
     def sync_check(self, stream=None):
         _check(self, load().gsr_sync_check(self.handle, _stream(stream)))
 
-    def profile(self, on: bool = True, count_evals: bool = False):
+    def profile(self, on: bool = True, count_evals: bool = False, stages=None):
+        """Stage events on or off; `stages` (names from STAGES) limits them to those stages."""
+        mask = 0xFFFFFFFF if stages is None else sum(1 << STAGES.index(k) for k in stages)
+        _check(self, load().gsr_profile_select(self.handle, mask))
         _check(self, load().gsr_profile_enable(self.handle, int(on), int(count_evals)))
 
     def profile_collect(self) -> dict:
