@@ -333,82 +333,136 @@ __device__ __forceinline__ void eval_color_regs(int deg, const Geo& G, const Dev
   rgb[0] = fmaxf(v0, 0.f); rgb[1] = fmaxf(v1, 0.f); rgb[2] = fmaxf(v2, 0.f);
 }
 
-// Position of the n-th (0-based) set bit of m.
-__device__ __forceinline__ int nth_set_bit(uint32_t m, int n) {
-  int pos = 0;
-#pragma unroll
-  for (int w = 16; w > 0; w >>= 1) {
-    const uint32_t lo = m & ((1u << w) - 1u);
-    const int c = __popc(lo);
-    if (n >= c) {
-      n -= c;
-      m >>= w;
-      pos += w;
-    } else {
-      m = lo;
-    }
+// The 64-byte record of a visible (Gaussian, camera c) projection, colour left at zero.
+__device__ __forceinline__ Rec record_geometry(const Proj& P, int c, float eps) {
+  Rec rr;
+  rr.a = make_float4(P.mx, P.my, P.op, P.t[2]);
+  rr.b = make_float4(P.ca, P.cb, P.cc, 0.f);
+  const uint32_t lo = static_cast<uint32_t>(P.x0) | (static_cast<uint32_t>(P.x1) << 16);
+  const uint32_t hi = static_cast<uint32_t>(P.y0) | (static_cast<uint32_t>(P.y1) << 16) | (static_cast<uint32_t>(c) << 27);
+  rr.c = make_float4(0.f, 0.f, __uint_as_float(lo), __uint_as_float(hi));
+  // Where op' exp(-d^T Q d / 2) >= 1/255, i.e. d^T Q d <= 2 ln(255 op'): an ellipse whose
+  // half-extents are sqrt(2 ln(255 op') Sigma_xx) and sqrt(2 ln(255 op') Sigma_yy), Sigma the
+  // dilated covariance. Widened by 0.1% + 0.01 px so FP32 evaluation never falls outside.
+  const float L = logf(255.f * P.op);
+  if (L > 0.f) {
+    const float ex = sqrtf(2.f * L * (P.ar + eps)) * 1.001f + 0.01f;
+    const float ey = sqrtf(2.f * L * (P.cr + eps)) * 1.001f + 0.01f;
+    rr.d = make_float4(P.mx - ex, P.mx + ex, P.my - ey, P.my + ey);
+  } else {
+    rr.d = make_float4(1.f, -1.f, 1.f, -1.f);  // empty: no pixel reaches 1/255
   }
-  return pos;
+  return rr;
 }
+
+__device__ __forceinline__ void write_record(const PreOut& out, long long v, const Rec& rr, long long i) {
+  const uint32_t lo = __float_as_uint(rr.c.z), hi = __float_as_uint(rr.c.w);
+  const uint32_t w = ((lo >> 16) & 0xffffu) - (lo & 0xffffu);
+  const uint32_t h = ((hi >> 16) & 0x7ffu) - (hi & 0xffffu);
+  out.rec[v] = rr;
+  out.depth_keys[v] = __float_as_uint(rr.a.w);
+  out.depth_vals[v] = static_cast<uint32_t>(v);
+  out.touched[v] = w * h;
+  out.owner[v] = static_cast<uint32_t>(i);
+}
+
+// Appends the slots of the lanes with `pred` to the block's list (order within the list is
+// arbitrary); one shared atomic per warp.
+__device__ __forceinline__ void list_append(bool pred, uint32_t slot, uint32_t* list, uint32_t* count, int lane) {
+  const uint32_t bal = __ballot_sync(0xffffffffu, pred);
+  if (!bal) return;
+  uint32_t base = 0;
+  if (lane == 0) base = atomicAdd(count, static_cast<uint32_t>(__popc(bal)));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (pred) list[base + __popc(bal & ((1u << lane) - 1u))] = slot;
+}
+
+constexpr int kPreStage = 256;  // records a block keeps in shared memory between its phases
 
 // One block covers kPreTile = 1024 consecutive Gaussians, four per thread (thread t owns slot
 // j * 256 + t, i = base + slot, so each load instruction is coalesced).
-//   1a: a cheap conservative test per (Gaussian, camera) drops what is certainly outside.
-//   1b: each warp gathers its surviving Gaussians (of its 128 slots) and spreads them over its
-//       32 lanes for the exact projection, so a warp does not run the long path for a few lanes.
-//   The per-block count of visible records (four 16-bit lanes, one per j) is scanned in the
-//   block and one warp takes the block's offset from its predecessors (decoupled look-back).
-//   2: visible (Gaussian, camera) records are spread over the lanes the same way and written
-//      in (i, camera) order.
+//   1a: a cheap conservative test per (Gaussian, camera) drops what is certainly outside; the
+//       survivors' slots go to a block-wide list.
+//   1b: the block's threads share out the list for the exact projection (full warps however
+//       sparse the survivors are); the geometry of each visible (Gaussian, camera) record is
+//       staged in shared memory.
+//   The block's record counts are scanned in slot order and the block total is published for
+//   its successors at once. The colour of the staged records is evaluated while the
+//   predecessors finish; then one warp takes the block's offset (decoupled look-back) and the
+//   staged records are written at their places, so the records are in (i, camera) order.
+//   Records beyond the stage's capacity are computed again in full after the offset is known.
 template <typename AT, typename ST>
 __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArgs A, CamBatch cams, float eps, int aa,
                                                                        PreOut out) {
   __shared__ unsigned s_bid;
   __shared__ unsigned long long s_excl;
-  __shared__ uint32_t s_aux[kPreTile];   // 1a: cameras that survive the cheap test; 2: record offset
-  __shared__ uint32_t s_mask[kPreTile];  // exact visibility bits per slot
-  if (threadIdx.x == 0) s_bid = atomicAdd(out.counter, 1u);
+  __shared__ uint32_t s_count[2];         // survivors of the cheap test; visible records
+  __shared__ uint32_t s_list[kPreTile];   // slots of the survivors
+  __shared__ uint32_t s_aux[kPreTile];    // 1a: cameras surviving the cheap test; then first record per slot
+  __shared__ uint32_t s_mask[kPreTile];   // exact visibility bits per slot
+  __shared__ uint32_t s_unstaged[kPreTile / 32];
+  __shared__ float4 s_rec[kPreStage][4];
+  __shared__ uint32_t s_meta[kPreStage];  // slot | camera << 16
+  if (threadIdx.x == 0) {
+    s_bid = atomicAdd(out.counter, 1u);
+    s_count[0] = 0;
+    s_count[1] = 0;
+  }
+  if (threadIdx.x < kPreTile / 32) s_unstaged[threadIdx.x] = 0;
   __syncthreads();
   const unsigned bid = s_bid;
   const long long base_i = static_cast<long long>(bid) * kPreTile;
-  const int lane = threadIdx.x & 31, wslot = threadIdx.x & ~31;
-  uint32_t bal[kPreItems], cum[kPreItems + 1];
-  cum[0] = 0;
+  const int lane = threadIdx.x & 31;
+  {
+    Geo G[kPreItems];
+    bool ok[kPreItems];
 #pragma unroll
-  for (int j = 0; j < kPreItems; ++j) {
-    const long long i = base_i + j * kPreThreads + threadIdx.x;
-    uint32_t maybe = 0;
-    if (i < A.n_render) {
-      Geo G;
-      load_mean_scale<AT>(A, seg_map(A.segs, i), G);
-      for (int c = 0; c < cams.C; ++c)
-        if (!surely_culled(G, cams.cam[c], eps)) maybe |= 1u << c;
+    for (int j = 0; j < kPreItems; ++j) {  // every load first
+      const long long i = base_i + j * kPreThreads + threadIdx.x;
+      ok[j] = i < A.n_render;
+      if (ok[j]) load_mean_scale<AT>(A, seg_map(A.segs, i), G[j]);
     }
-    s_aux[j * kPreThreads + threadIdx.x] = maybe;
-    s_mask[j * kPreThreads + threadIdx.x] = 0;
-    bal[j] = __ballot_sync(0xffffffffu, maybe != 0);
-    cum[j + 1] = cum[j] + __popc(bal[j]);
+#pragma unroll
+    for (int j = 0; j < kPreItems; ++j) {
+      const uint32_t slot = j * kPreThreads + threadIdx.x;
+      uint32_t maybe = 0;
+      if (ok[j])
+        for (int c = 0; c < cams.C; ++c)
+          if (!surely_culled(G[j], cams.cam[c], eps)) maybe |= 1u << c;
+      s_aux[slot] = maybe;
+      s_mask[slot] = 0;
+      list_append(maybe != 0, slot, s_list, &s_count[0], lane);
+    }
   }
-  __syncwarp();
-  for (uint32_t r = 0; r < cum[kPreItems]; r += 32) {
-    const uint32_t k = r + lane;
-    if (k < cum[kPreItems]) {
-      const int j = (k >= cum[1]) + (k >= cum[2]) + (k >= cum[3]);
-      const int slot = j * kPreThreads + wslot + nth_set_bit(bal[j], static_cast<int>(k - cum[j]));
-      const uint32_t maybe = s_aux[slot];
-      Geo G;
-      uint32_t vis = 0;
-      if (load_geo<AT>(A, seg_map(A.segs, base_i + slot), G)) {
-        for (int c = 0; c < cams.C; ++c) {
-          if (!(maybe & (1u << c))) continue;
-          Proj P;
-          if (project(G, cams.cam[c], eps, aa, P)) vis |= 1u << c;
+  __syncthreads();
+  const uint32_t n_maybe = s_count[0];
+  for (uint32_t k = threadIdx.x; k < n_maybe; k += kPreThreads) {
+    const uint32_t slot = s_list[k];
+    const uint32_t maybe = s_aux[slot];
+    Geo G;
+    uint32_t vis = 0;
+    if (load_geo<AT>(A, seg_map(A.segs, base_i + slot), G)) {
+      for (int c = 0; c < cams.C; ++c) {
+        if (!(maybe & (1u << c))) continue;
+        Proj P;
+        if (!project(G, cams.cam[c], eps, aa, P)) continue;
+        vis |= 1u << c;
+        const uint32_t e = atomicAdd(&s_count[1], 1u);
+        if (e < kPreStage) {
+          const Rec rr = record_geometry(P, c, eps);
+          s_rec[e][0] = rr.a;
+          s_rec[e][1] = rr.b;
+          s_rec[e][2] = rr.c;
+          s_rec[e][3] = rr.d;
+          s_meta[e] = slot | (static_cast<uint32_t>(c) << 16);
+        } else {
+          atomicOr(&s_unstaged[slot >> 5], 1u << (slot & 31));
         }
       }
-      s_mask[slot] = vis;
     }
+    s_mask[slot] = vis;
   }
-  __syncwarp();
+  __syncthreads();
   uint32_t mask[kPreItems];
   unsigned long long packed = 0;
 #pragma unroll
@@ -418,42 +472,61 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
   }
   unsigned long long tot_packed;
   const unsigned long long excl_packed = block_excl_scan64(packed, &tot_packed);
-  uint32_t lane_base[kPreItems];
   uint32_t total = 0;
 #pragma unroll
   for (int j = 0; j < kPreItems; ++j) {
-    lane_base[j] = total;
+    s_aux[j * kPreThreads + threadIdx.x] = total + static_cast<uint32_t>((excl_packed >> (16 * j)) & 0xffffu);
     total += static_cast<uint32_t>((tot_packed >> (16 * j)) & 0xffffu);
   }
+  if (threadIdx.x == 0) publish_aggregate(out.status, bid, total, out.epoch);
+  __syncthreads();
+  // colour of the staged records, while the predecessors finish
+  const uint32_t n_rec = s_count[1];
+  const uint32_t n_staged = n_rec < kPreStage ? n_rec : kPreStage;
+  for (uint32_t e = threadIdx.x; e < n_staged; e += kPreThreads) {
+    const uint32_t meta = s_meta[e];
+    const long long g = seg_map(A.segs, base_i + (meta & 0xffffu));
+    Geo G;
+    G.m[0] = __ldg(A.means + 3 * g + 0);
+    G.m[1] = __ldg(A.means + 3 * g + 1);
+    G.m[2] = __ldg(A.means + 3 * g + 2);
+    float rgb[3], dir[3], dn, Y[16];
+    bool cl[3];
+    eval_color<ST>(A, g, G, cams.cam[meta >> 16], rgb, dir, dn, Y, cl);
+    s_rec[e][1].w = rgb[0];
+    s_rec[e][2].x = rgb[1];
+    s_rec[e][2].y = rgb[2];
+  }
   if (threadIdx.x < 32) {
-    const unsigned long long ex = warp_chained_prefix(out.status, bid, total, out.epoch, out.err);
+    const unsigned long long ex = warp_lookback(out.status, bid, total, out.epoch, out.err);
     if (threadIdx.x == 0) s_excl = ex;
   }
   __syncthreads();
   const unsigned long long block_base = s_excl;
   if (threadIdx.x == 0 && base_i <= A.n_render - 1 && A.n_render - 1 < base_i + kPreTile)
     *out.v_total = static_cast<uint32_t>(block_base + total);
-  // phase 2: the first record index of every visible slot, then the records, spread over lanes
-  cum[0] = 0;
-#pragma unroll
-  for (int j = 0; j < kPreItems; ++j) {
-    s_aux[j * kPreThreads + threadIdx.x] =
-        static_cast<uint32_t>(block_base + lane_base[j] + ((excl_packed >> (16 * j)) & 0xffffu));
-    bal[j] = __ballot_sync(0xffffffffu, mask[j] != 0);
-    cum[j + 1] = cum[j] + __popc(bal[j]);
+  for (uint32_t e = threadIdx.x; e < n_staged; e += kPreThreads) {
+    const uint32_t meta = s_meta[e];
+    const uint32_t slot = meta & 0xffffu, c = meta >> 16;
+    const long long v = block_base + s_aux[slot] + __popc(s_mask[slot] & ((1u << c) - 1u));
+    Rec rr;
+    rr.a = s_rec[e][0];
+    rr.b = s_rec[e][1];
+    rr.c = s_rec[e][2];
+    rr.d = s_rec[e][3];
+    write_record(out, v, rr, base_i + slot);
   }
-  __syncwarp();
-  for (uint32_t r = 0; r < cum[kPreItems]; r += 32) {
-    const uint32_t k = r + lane;
-    if (k >= cum[kPreItems]) continue;
-    const int j = (k >= cum[1]) + (k >= cum[2]) + (k >= cum[3]);
-    const int slot = j * kPreThreads + wslot + nth_set_bit(bal[j], static_cast<int>(k - cum[j]));
+  if (n_rec <= kPreStage) return;  // block-uniform
+  // records that did not fit the stage: every record of those Gaussians is computed again
+  for (uint32_t k = threadIdx.x; k < n_maybe; k += kPreThreads) {
+    const uint32_t slot = s_list[k];
+    if (!((s_unstaged[slot >> 5] >> (slot & 31)) & 1u)) continue;
     const uint32_t vis = s_mask[slot];
     const long long i = base_i + slot;
     const long long g = seg_map(A.segs, i);
     Geo G;
     load_geo<AT>(A, g, G);
-    unsigned long long v = s_aux[slot];
+    long long v = block_base + s_aux[slot];
     for (int c = 0; c < cams.C; ++c) {
       if (!(vis & (1u << c))) continue;
       const DevCam& cam = cams.cam[c];
@@ -462,29 +535,11 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
       float rgb[3], dir[3], dn, Y[16];
       bool cl[3];
       eval_color<ST>(A, g, G, cam, rgb, dir, dn, Y, cl);
-      Rec rr;
-      rr.a = make_float4(P.mx, P.my, P.op, P.t[2]);
-      rr.b = make_float4(P.ca, P.cb, P.cc, rgb[0]);
-      const uint32_t lo = static_cast<uint32_t>(P.x0) | (static_cast<uint32_t>(P.x1) << 16);
-      const uint32_t hi = static_cast<uint32_t>(P.y0) | (static_cast<uint32_t>(P.y1) << 16) |
-                          (static_cast<uint32_t>(c) << 27);
-      rr.c = make_float4(rgb[1], rgb[2], __uint_as_float(lo), __uint_as_float(hi));
-      // Where op' exp(-d^T Q d / 2) >= 1/255, i.e. d^T Q d <= 2 ln(255 op'): an ellipse whose
-      // half-extents are sqrt(2 ln(255 op') Sigma_xx) and sqrt(2 ln(255 op') Sigma_yy), Sigma the
-      // dilated covariance. Widened by 0.1% + 0.01 px so FP32 evaluation never falls outside.
-      const float L = logf(255.f * P.op);
-      if (L > 0.f) {
-        const float ex = sqrtf(2.f * L * (P.ar + eps)) * 1.001f + 0.01f;
-        const float ey = sqrtf(2.f * L * (P.cr + eps)) * 1.001f + 0.01f;
-        rr.d = make_float4(P.mx - ex, P.mx + ex, P.my - ey, P.my + ey);
-      } else {
-        rr.d = make_float4(1.f, -1.f, 1.f, -1.f);  // empty: no pixel reaches 1/255
-      }
-      out.rec[v] = rr;
-      out.depth_keys[v] = __float_as_uint(P.t[2]);
-      out.depth_vals[v] = static_cast<uint32_t>(v);
-      out.touched[v] = static_cast<uint32_t>((P.x1 - P.x0) * (P.y1 - P.y0));
-      out.owner[v] = static_cast<uint32_t>(i);
+      Rec rr = record_geometry(P, c, eps);
+      rr.b.w = rgb[0];
+      rr.c.x = rgb[1];
+      rr.c.y = rgb[2];
+      write_record(out, v, rr, i);
       ++v;
     }
   }

@@ -31,9 +31,11 @@ __device__ __forceinline__ uint32_t status_flag(unsigned long long s, uint32_t e
   return (static_cast<uint32_t>(s >> 34) == epoch) ? static_cast<uint32_t>((s >> 32) & 3u) : 0u;
 }
 
-// 256-thread exclusive scan of one value per thread; returns the block total through *total.
+// Exclusive scan of one value per thread over the whole block (any multiple of 32 threads up
+// to 1024; every thread must call it); returns the block total through *total.
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* total) {
   __shared__ uint32_t warp_sums[32];
+  __shared__ uint32_t block_total;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t inc = x;
 #pragma unroll
@@ -53,19 +55,21 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* total)
       if (lane >= o) si += y;
     }
     if (lane < nw) warp_sums[lane] = si - s;
-    if (lane == nw - 1) warp_sums[31] = si;
+    if (lane == nw - 1) block_total = si;
   }
   __syncthreads();
   const uint32_t r = warp_sums[wid] + inc - x;
-  *total = warp_sums[31];
+  *total = block_total;
   __syncthreads();
   return r;
 }
 
-// 256-thread exclusive scan of one 64-bit value per thread (used with four independent 16-bit
-// lanes packed in one word: no lane's total may exceed 65535). Returns the block total too.
+// Exclusive scan of one 64-bit value per thread over the whole block (used with four
+// independent 16-bit lanes packed in one word: no lane's total may exceed 65535). Returns the
+// block total too.
 __device__ __forceinline__ unsigned long long block_excl_scan64(unsigned long long x, unsigned long long* total) {
   __shared__ unsigned long long warp_sums64[32];
+  __shared__ unsigned long long block_total64;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned long long inc = x;
 #pragma unroll
@@ -85,28 +89,31 @@ __device__ __forceinline__ unsigned long long block_excl_scan64(unsigned long lo
       if (lane >= o) si += y;
     }
     if (lane < nw) warp_sums64[lane] = si - s;
-    if (lane == nw - 1) warp_sums64[31] = si;
+    if (lane == nw - 1) block_total64 = si;
   }
   __syncthreads();
   const unsigned long long r = warp_sums64[wid] + inc - x;
-  *total = warp_sums64[31];
+  *total = block_total64;
   __syncthreads();
   return r;
 }
 
-// Decoupled look-back for tile `bid`, run by all 32 lanes of one warp: publishes the tile's
-// aggregate, then reads 32 predecessors at a time, waiting (bounded) until every one of them
+// Publishes tile `bid`'s aggregate (tile 0: its inclusive prefix) for the decoupled look-back.
+// One thread calls it.
+__device__ __forceinline__ void publish_aggregate(unsigned long long* status, uint32_t bid, uint32_t agg,
+                                                  uint32_t epoch) {
+  store_status(status + bid, pack_status(epoch, bid == 0 ? kStatusPrefix : kStatusAgg, agg));
+}
+
+// Decoupled look-back for tile `bid` whose aggregate `agg` is already published, run by all 32
+// lanes of one warp: reads 32 predecessors at a time, waiting (bounded) until every one of them
 // up to the nearest inclusive prefix is ready, and sums them. Returns this tile's exclusive
-// prefix in every lane and publishes its inclusive prefix. Values are 32-bit; the running
-// total is 64-bit and the caller checks it for overflow.
-__device__ __forceinline__ unsigned long long warp_chained_prefix(unsigned long long* status, uint32_t bid,
-                                                                  uint32_t agg, uint32_t epoch, int* err) {
+// prefix in every lane and publishes its inclusive prefix. Values are 32-bit; the running total
+// is 64-bit and the caller checks it for overflow.
+__device__ __forceinline__ unsigned long long warp_lookback(unsigned long long* status, uint32_t bid, uint32_t agg,
+                                                            uint32_t epoch, int* err) {
   const int lane = threadIdx.x & 31;
-  if (bid == 0) {
-    if (lane == 0) store_status(status, pack_status(epoch, kStatusPrefix, agg));
-    return 0;
-  }
-  if (lane == 0) store_status(status + bid, pack_status(epoch, kStatusAgg, agg));
+  if (bid == 0) return 0;
   unsigned long long excl = 0;
   long long end = static_cast<long long>(bid) - 1;
   unsigned spins = 0, ns = 32;
@@ -127,7 +134,7 @@ __device__ __forceinline__ unsigned long long warp_chained_prefix(unsigned long 
         break;
       }
       __nanosleep(ns);
-      if (ns < 1024) ns <<= 1;
+      if (ns < 256) ns <<= 1;
       continue;
     }
     unsigned long long v = ((upto >> lane) & 1u) ? val : 0u;
@@ -140,6 +147,14 @@ __device__ __forceinline__ unsigned long long warp_chained_prefix(unsigned long 
   if (lane == 0)
     store_status(status + bid, pack_status(epoch, kStatusPrefix, static_cast<uint32_t>(excl + agg)));
   return excl;
+}
+
+// Publish and look back in one call (all 32 lanes of one warp).
+__device__ __forceinline__ unsigned long long warp_chained_prefix(unsigned long long* status, uint32_t bid,
+                                                                  uint32_t agg, uint32_t epoch, int* err) {
+  if ((threadIdx.x & 31) == 0) publish_aggregate(status, bid, agg, epoch);
+  __syncwarp();
+  return warp_lookback(status, bid, agg, epoch, err);
 }
 
 }  // namespace gsr

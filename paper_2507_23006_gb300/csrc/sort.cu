@@ -47,20 +47,43 @@ __global__ void __launch_bounds__(256) hist_kernel(const uint32_t* __restrict__ 
 }
 
 // Sums the per-block histograms of pass blockIdx.x, writes the exclusive digit offsets to
-// hist[pass][256] and clears the pass's block counter.
-__global__ void __launch_bounds__(256) hist_scan_kernel(const uint32_t* __restrict__ hist_blocks, int nblocks,
-                                                        uint32_t* __restrict__ hist, uint32_t* counters) {
+// hist[pass][256] and clears the pass's block counter. 1024 threads: four groups of 256 sum
+// every fourth block histogram each (eight loads in flight per thread), then one scan.
+constexpr int kHistScanThreads = 1024;
+__global__ void __launch_bounds__(kHistScanThreads) hist_scan_kernel(const uint32_t* __restrict__ hist_blocks,
+                                                                     int nblocks, uint32_t* __restrict__ hist,
+                                                                     uint32_t* counters) {
+  __shared__ uint32_t s_part[4][256];
   const int p = blockIdx.x;
+  const int d = threadIdx.x & 255, part = threadIdx.x >> 8;
+  const uint32_t* src = hist_blocks + p * 256 + d;
   uint32_t x = 0;
-  for (int b = 0; b < nblocks; ++b) x += hist_blocks[static_cast<size_t>(b) * 4 * 256 + p * 256 + threadIdx.x];
+  int b = part;
+  for (; b + 28 < nblocks; b += 32) {
+    uint32_t v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __ldg(src + static_cast<size_t>(b + 4 * k) * 4 * 256);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x += v[k];
+  }
+  for (; b < nblocks; b += 4) x += __ldg(src + static_cast<size_t>(b) * 4 * 256);
+  s_part[part][d] = x;
+  __syncthreads();
+  // the whole block scans; threads past the first 256 add nothing
+  const uint32_t t = threadIdx.x < 256 ? s_part[0][d] + s_part[1][d] + s_part[2][d] + s_part[3][d] : 0u;
   uint32_t total;
-  const uint32_t e = block_excl_scan(x, &total);
-  hist[p * 256 + threadIdx.x] = e;
+  const uint32_t e = block_excl_scan(t, &total);
+  if (threadIdx.x < 256) hist[p * 256 + d] = e;
   if (threadIdx.x == 0) counters[p] = 0;
 }
 
+// Per-digit decoupled look-back of tile `bid` (one thread per digit): publishes the tile's
+// count, then sums predecessors' counts back to the nearest inclusive prefix, reading eight
+// predecessors per round (the loads are independent; the walk is latency-bound otherwise).
+// Waits are bounded: past kSpinLimit rounds the error flag is set and the partial sum is used.
 __device__ __forceinline__ uint32_t lookback_digit(unsigned long long* status, uint32_t bid, int d, uint32_t agg,
                                                    uint32_t epoch, int* err) {
+  constexpr int kAhead = 8;
   unsigned long long* me = status + static_cast<size_t>(bid) * 256 + d;
   if (bid == 0) {
     store_status(me, pack_status(epoch, kStatusPrefix, agg));
@@ -70,21 +93,34 @@ __device__ __forceinline__ uint32_t lookback_digit(unsigned long long* status, u
   uint32_t excl = 0;
   long long j = static_cast<long long>(bid) - 1;
   unsigned spins = 0, ns = 32;
-  while (j >= 0) {
-    const unsigned long long s = load_status(status + static_cast<size_t>(j) * 256 + d);
-    const uint32_t f = status_flag(s, epoch);
-    if (f == 0) {
+  bool done = false;
+  while (!done) {
+    unsigned long long w[kAhead];
+#pragma unroll
+    for (int k = 0; k < kAhead; ++k)
+      w[k] = (j - k >= 0) ? load_status(status + static_cast<size_t>(j - k) * 256 + d)
+                          : pack_status(epoch, kStatusPrefix, 0u);  // before tile 0: a prefix of 0
+    bool stalled = false;
+#pragma unroll
+    for (int k = 0; k < kAhead; ++k) {
+      if (done || stalled) continue;
+      const uint32_t f = status_flag(w[k], epoch);
+      if (f == 0) {
+        stalled = true;
+      } else {
+        excl += static_cast<uint32_t>(w[k]);
+        --j;
+        done = f == kStatusPrefix;
+      }
+    }
+    if (stalled && !done) {
       if (++spins > kSpinLimit) {
         atomicOr(err, kErrTimeout);
         break;
       }
       __nanosleep(ns);
       if (ns < 1024) ns <<= 1;
-      continue;
     }
-    excl += static_cast<uint32_t>(s);
-    if (f == kStatusPrefix) break;
-    --j;
   }
   store_status(me, pack_status(epoch, kStatusPrefix, excl + agg));
   return excl;
@@ -224,7 +260,7 @@ void radix_sort_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
   const int hblocks = std::max(1, static_cast<int>(std::min<long long>(std::min(sc.grid_cap, kMaxHistBlocks),
                                                                        (max_n + 4095) / 4096)));
   hist_kernel<<<hblocks, 256, 0, s>>>(keys_in, d_n, max_n, begin_bit, end_bit, passes, sc.hist_blocks);
-  hist_scan_kernel<<<passes, 256, 0, s>>>(sc.hist_blocks, hblocks, sc.hist, sc.counters);
+  hist_scan_kernel<<<passes, kHistScanThreads, 0, s>>>(sc.hist_blocks, hblocks, sc.hist, sc.counters);
   // ping-pong so that the last pass lands in keys_out; the inputs are never written
   const uint32_t* ksrc = keys_in;
   const uint32_t* vsrc = vals_in;

@@ -1,0 +1,74 @@
+"""Runs a fixed number of training steps (forward + backward through the C ABI) on one
+synthetic workload and nothing else: the command to put under a kernel profiler.
+
+    python -m paper_2507_23006_gb300.run_step --n 6000000 --width 1920 --height 1080 --steps 3
+
+Workloads: `city` (a synthetic city grid seen from 150 m up at 45 degrees, the training-step
+benchmark), `street` (a street block, one camera 30 m up looking 45 degrees down) and `box`
+(uniform Gaussians in a box in front of the camera). `--fwd-only` runs forward renders without
+saved state; `--fp16` stores attributes and SH in FP16; `--time` prints the mean device time
+of each stage over the steps after the first (CUDA events around every stage).
+"""
+from __future__ import annotations
+
+import argparse
+
+import torch
+
+from . import native, scenes
+
+
+def workload(kind: str, n: int, width: int, height: int):
+    if kind == "city":
+        return scenes.city(2, n), scenes.aerial_camera(width, height, altitude=150.0, pitch_deg=45.0,
+                                                       azimuth_deg=90.0)
+    if kind == "street":
+        return scenes.street_block(0, n), scenes.street_block_camera(width, height)
+    if kind == "box":
+        scene = scenes.box_scene(0, n)
+        return scene, scenes.box_camera(width, height)
+    raise ValueError(kind)
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--workload", default="city", choices=["city", "street", "box"])
+    p.add_argument("--n", type=int, default=6_000_000)
+    p.add_argument("--width", type=int, default=1920)
+    p.add_argument("--height", type=int, default=1080)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--fwd-only", action="store_true")
+    p.add_argument("--fp16", action="store_true")
+    p.add_argument("--tile-cull", type=int, default=1)
+    p.add_argument("--time", action="store_true")
+    a = p.parse_args()
+    scene, cam = workload(a.workload, a.n, a.width, a.height)
+    dt = torch.float16 if a.fp16 else torch.float32
+    ctx = native.Context(0)
+    g = native.Gaussians.from_scene(scene, attr_dtype=dt, sh_dtype=dt)
+    opts = native.Options(tile_cull=bool(a.tile_cull), save_state=not a.fwd_only)
+    npix = cam.width * cam.height
+    gen = torch.Generator(device="cuda").manual_seed(1234)
+    d_out = dict(rgb=torch.randn((npix, 3), device="cuda", generator=gen),
+                 depth_acc=torch.randn(npix, device="cuda", generator=gen) * 1e-2,
+                 alpha=torch.randn(npix, device="cuda", generator=gen))
+    for step in range(a.steps):
+        if a.time and step == 1:
+            torch.cuda.synchronize()
+            ctx.profile(True)
+            ctx.profile_collect()
+        out, st = native.render_forward(ctx, g, [cam], opts, want_state=not a.fwd_only)
+        if st is not None:
+            native.render_backward(ctx, g, [cam], st, d_out, opts)
+            st.release()
+    torch.cuda.synchronize()
+    if a.time and a.steps > 1:
+        ms = ctx.profile_collect()["ms"]
+        print(" ".join(f"{k}={v / (a.steps - 1) * 1e3:.1f}us" for k, v in ms.items() if v > 0))
+        ctx.profile(False)
+    ctx.close()
+    print(f"ran {a.steps} steps of {a.workload} n={g.n} {cam.width}x{cam.height}")
+
+
+if __name__ == "__main__":
+    main()
