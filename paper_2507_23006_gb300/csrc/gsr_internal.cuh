@@ -164,8 +164,8 @@ struct SortScratch {
   uint32_t* counters;            // [4]
   int grid_cap;                  // blocks per onesweep launch (resident blocks loop over tiles)
 };
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+constexpr int kSortThreads = 512;
+constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 size_t sort_status_words(long long max_n);  // 64-bit words per pass
 // epoch: tag for this call's status words (nonzero, below 2^30); clear_status: zero the status

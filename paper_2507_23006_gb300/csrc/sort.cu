@@ -128,14 +128,25 @@ __device__ __forceinline__ uint32_t lookback_digit(unsigned long long* status, u
 
 // One LSD pass. Resident blocks loop: each takes the next 4096-key tile from `counter` (so a
 // tile only ever waits on tiles already taken by running blocks) until the keys run out.
+//   rank: each of the 16 warps ranks its 256 keys item by item; lanes with equal digits are
+//         found with one ballot per digit bit, and the lowest such lane adds the group to the
+//         warp's counter of that digit (shared atomics, ordered by __syncwarp so that earlier
+//         items rank first);
+//   offsets: per digit, the warps' counts are scanned, the tile's count is published and the
+//         digit's offset taken from the predecessors (look-back);
+//   scatter: keys, then values, are placed in shared memory in tile-local digit order and
+//         written out in runs of equal digits (consecutive threads, consecutive addresses).
 __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* d_n, long long max_n, int shift, int width,
     const uint32_t* __restrict__ offsets, unsigned long long* status, uint32_t* counter, uint32_t epoch,
     int* err) {
   constexpr int kWarps = kSortThreads / 32;
+  constexpr int kOut = kSortTile / kSortThreads;  // tile positions each thread writes out
   __shared__ uint32_t s_hist[kWarps][256];
-  __shared__ uint32_t s_base[256];
+  __shared__ uint32_t s_local[256];  // first tile-local position of each digit
+  __shared__ uint32_t s_base[256];   // output position of tile-local position 0 of each digit
+  __shared__ uint32_t s_buf[kSortTile];
   __shared__ uint32_t s_bid;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const long long n = device_n(d_n, max_n);
@@ -148,6 +159,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
     const uint32_t bid = s_bid;
     const long long start = static_cast<long long>(bid) * kSortTile;
     if (start >= n) break;
+    const int tile_n = static_cast<int>(n - start < kSortTile ? n - start : kSortTile);
     const long long wbase = start + static_cast<long long>(w) * (32 * kSortItems);
     uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
 #pragma unroll
@@ -159,38 +171,73 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
     }
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
-      const long long idx = wbase + j * 32 + lane;
-      const uint32_t d = idx < n ? ((key[j] >> shift) & dmask) : 256u;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      const uint32_t pre = d < 256u ? s_hist[w][d] : 0u;
+      const bool ok = wbase + j * 32 + lane < n;
+      const uint32_t d = (key[j] >> shift) & dmask;
+      uint32_t peers = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+      for (int bit = 0; bit < 8; ++bit) {
+        if (bit < width) {
+          const uint32_t ones = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+          peers &= ((d >> bit) & 1u) ? ones : ~ones;
+        }
+      }
+      const int leader = ok ? __ffs(peers) - 1 : lane;
+      uint32_t old = 0;
+      if (ok && lane == leader) old = atomicAdd(&s_hist[w][d], static_cast<uint32_t>(__popc(peers)));
+      old = __shfl_sync(0xffffffffu, old, leader);
+      rank[j] = old + __popc(peers & lt);
       __syncwarp();
-      if (d < 256u && lane == __ffs(peers) - 1) s_hist[w][d] = pre + __popc(peers);
-      __syncwarp();
-      rank[j] = pre + __popc(peers & lt);
     }
     __syncthreads();
-    {
-      const int d = tid;  // one thread per digit (kSortThreads == 256)
-      uint32_t sum = 0;
+    uint32_t sum = 0;
+    if (tid < 256) {  // one thread per digit
+      const int d = tid;
 #pragma unroll
       for (int k = 0; k < kWarps; ++k) {
         const uint32_t c = s_hist[k][d];
         s_hist[k][d] = sum;
         sum += c;
       }
-      const uint32_t excl = lookback_digit(status, bid, d, sum, epoch, err);
-      s_base[d] = offsets[d] + excl;
+    }
+    uint32_t excl = 0;
+    if (tid < 256) excl = lookback_digit(status, bid, tid, sum, epoch, err);
+    uint32_t tile_total;
+    const uint32_t local = block_excl_scan(sum, &tile_total);  // every thread; digits are the first 256
+    if (tid < 256) {
+      s_local[tid] = local;
+      s_base[tid] = offsets[tid] + excl - local;
+    }
+    __syncthreads();
+    uint32_t lp[kSortItems];
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      lp[j] = 0xffffffffu;
+      if (wbase + j * 32 + lane < n) {
+        const uint32_t d = (key[j] >> shift) & dmask;
+        lp[j] = s_local[d] + s_hist[w][d] + rank[j];
+        s_buf[lp[j]] = key[j];
+      }
+    }
+    __syncthreads();
+    uint32_t pos[kOut];
+#pragma unroll
+    for (int k = 0; k < kOut; ++k) {
+      const int t = tid + k * kSortThreads;
+      if (t < tile_n) {
+        const uint32_t kk = s_buf[t];
+        pos[k] = s_base[(kk >> shift) & dmask] + static_cast<uint32_t>(t);
+        kout[pos[k]] = kk;
+      }
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-      const long long idx = wbase + j * 32 + lane;
-      if (idx < n) {
-        const uint32_t d = (key[j] >> shift) & dmask;
-        const uint32_t pos = s_base[d] + s_hist[w][d] + rank[j];
-        kout[pos] = key[j];
-        vout[pos] = val[j];
-      }
+    for (int j = 0; j < kSortItems; ++j)
+      if (lp[j] != 0xffffffffu) s_buf[lp[j]] = val[j];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kOut; ++k) {
+      const int t = tid + k * kSortThreads;
+      if (t < tile_n) vout[pos[k]] = s_buf[t];
     }
     __syncthreads();
   }
