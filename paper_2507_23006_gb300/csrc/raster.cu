@@ -49,16 +49,17 @@ constexpr int kBlendThreads = 128;
 constexpr int kBlendWarps = kBlendThreads / 32;
 constexpr int kBatch = 256;
 
-// Bit w set when the Gaussian's alpha >= 1/255 box (record field d) meets the pixel centres
-// of warp w (x in [x_lo, x_hi], rows y_base + 4w .. y_base + 4w + 3).
-__device__ __forceinline__ uint32_t warp_rows_mask(const float4 d, float x_lo, float x_hi, float y_base) {
+// Each warp of a blend block covers one 8x8 quarter of the 16x16 tile (warp w: columns
+// 8 (w & 1) .. +7, rows 8 (w >> 1) .. +7; lane l: column l & 7, rows 2 (l >> 3) and +1).
+// Bit w is set when the Gaussian's alpha >= 1/255 box (record field d) meets the pixel centres
+// of warp w; (x0, y0) is the tile's first pixel centre, (x_max, y_max) the image's last.
+__device__ __forceinline__ uint32_t warp_block_mask(const float4 d, float x0, float y0, float x_max, float y_max) {
   uint32_t m = 0;
-  if (d.y >= x_lo && d.x <= x_hi) {
 #pragma unroll
-    for (int w = 0; w < kBlendWarps; ++w) {
-      const float yc = y_base + 4.f * w;
-      if (d.w >= yc && d.z <= yc + 3.f) m |= 1u << w;
-    }
+  for (int w = 0; w < kBlendWarps; ++w) {
+    const float xl = x0 + 8.f * (w & 1), yl = y0 + 8.f * (w >> 1);
+    const float xh = fminf(xl + 7.f, x_max), yh = fminf(yl + 7.f, y_max);
+    if (d.y >= xl && d.x <= xh && d.w >= yl && d.z <= yh) m |= 1u << w;
   }
   return m;
 }
@@ -194,13 +195,13 @@ __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(const Rec* __r
   const int lt = t - cam.tile_off;
   const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
   const int tid = threadIdx.x, wid = tid >> 5;
-  const int px = tx * kTile + (tid & (kTile - 1));
-  const int py0 = ty * kTile + 2 * (tid >> 4);
+  const int px = tx * kTile + 8 * (wid & 1) + (tid & 7);
+  const int py0 = ty * kTile + 8 * (wid >> 1) + 2 * ((tid & 31) >> 3);
   const float fx = px + 0.5f;
   const float fy[2] = {py0 + 0.5f, py0 + 1.5f};
   const bool inside[2] = {px < cam.W && py0 < cam.H, px < cam.W && py0 + 1 < cam.H};
-  const float x_lo = tx * kTile + 0.5f, x_hi = fminf(static_cast<float>((tx + 1) * kTile), cam.W) - 0.5f;
-  const float y_base = ty * kTile + 0.5f;
+  const float x0 = tx * kTile + 0.5f, y0 = ty * kTile + 0.5f;
+  const float x_max = cam.W - 0.5f, y_max = cam.H - 0.5f;
   const uint2 range = ranges[t];
   const int n = static_cast<int>(range.y - range.x);
   float T[2] = {1.f, 1.f}, C0[2] = {0.f, 0.f}, C1[2] = {0.f, 0.f}, C2[2] = {0.f, 0.f}, D[2] = {0.f, 0.f};
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(const Rec* __r
         sA[k] = r.a;
         sB[k] = r.b;
         sC[k] = make_float2(r.c.x, r.c.y);
-        sM[k] = warp_rows_mask(r.d, x_lo, x_hi, y_base);
+        sM[k] = warp_block_mask(r.d, x0, y0, x_max, y_max);
         sL[k] = sigma_cutoff(r.a.z);
       }
     }
@@ -354,13 +355,13 @@ __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __r
   const int lt = t - cam.tile_off;
   const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int px = tx * kTile + (tid & (kTile - 1));
-  const int py0 = ty * kTile + 2 * (tid >> 4);
+  const int px = tx * kTile + 8 * (wid & 1) + (tid & 7);
+  const int py0 = ty * kTile + 8 * (wid >> 1) + 2 * ((tid & 31) >> 3);
   const float fx = px + 0.5f;
   const float fy[2] = {py0 + 0.5f, py0 + 1.5f};
   const bool inside[2] = {px < cam.W && py0 < cam.H, px < cam.W && py0 + 1 < cam.H};
-  const float x_lo = tx * kTile + 0.5f, x_hi = fminf(static_cast<float>((tx + 1) * kTile), cam.W) - 0.5f;
-  const float y_base = ty * kTile + 0.5f;
+  const float x0 = tx * kTile + 0.5f, y0 = ty * kTile + 0.5f;
+  const float x_max = cam.W - 0.5f, y_max = cam.H - 0.5f;
   const uint2 range = ranges[t];
   if (tid == 0) s_max = 0;
   __syncthreads();
@@ -419,7 +420,7 @@ __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __r
         sB[k] = r.b;
         sC[k] = make_float2(r.c.x, r.c.y);
         sV[k] = v;
-        sM[k] = warp_rows_mask(r.d, x_lo, x_hi, y_base);
+        sM[k] = warp_block_mask(r.d, x0, y0, x_max, y_max);
         sL[k] = sigma_cutoff(r.a.z);
       }
 #pragma unroll
@@ -452,12 +453,12 @@ __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __r
         if (alpha < kAlphaMin) continue;
         contrib = true;
         if (kCount) ++n_contrib;
-        const float om = 1.f - alpha;
-        const float Ti = T[q] / om;
+        const float rom = __frcp_rn(1.f - alpha);  // 1 / (1 - alpha), correctly rounded
+        const float Ti = T[q] * rom;
         const float wgt = alpha * Ti;
         const float dz = a.w - zr[q];
         const float dal = Ti * (GC0[q] * b.w + GC1[q] * cc.x + GC2[q] * cc.y + GD[q] * dz) +
-                          (GTz[q] * Tf[q] - (GC0[q] * S0[q] + GC1[q] * S1[q] + GC2[q] * S2[q] + GD[q] * SD[q])) / om;
+                          (GTz[q] * Tf[q] - (GC0[q] * S0[q] + GC1[q] * S1[q] + GC2[q] * S2[q] + GD[q] * SD[q])) * rom;
         S0[q] = fmaf(b.w, wgt, S0[q]);
         S1[q] = fmaf(cc.x, wgt, S1[q]);
         S2[q] = fmaf(cc.y, wgt, S2[q]);
