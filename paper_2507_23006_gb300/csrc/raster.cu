@@ -301,45 +301,64 @@ __device__ __forceinline__ float warp_sum(float x) {
 
 constexpr int kGradVals = 12;
 
-// Sums 16 per-lane values over the warp with 16 shuffles instead of 16 x 5: at each halving
-// step a lane sends the half it gives up to its partner and keeps the sum of the other half.
-// Afterwards lanes 2k and 2k+1 both hold the warp total of value k (k < 16).
-__device__ __forceinline__ float warp_transpose_sum16(float v[16], int lane) {
-  float w8[8], w4[4], w2[2];
+// Sums N (<= 16) per-lane values over the warp with about N + 2 shuffles instead of 5 N. Each
+// round halves the vector: a lane sends the half it gives up to its partner across `kBit` and
+// keeps the sum of the other half (an odd length is padded with a zero). Once one value is
+// left, the remaining lane bits are summed directly. index() gives the value each lane ends up
+// holding (-1: padding).
+template <int N, int kBit>
+struct TransposeSum {
+  static __device__ __forceinline__ float run(const float* v, int lane) {
+    constexpr int H = (N + 1) / 2;
+    const bool up = lane & kBit;
+    float w[H];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const bool up = lane & 16;
-    const float send = up ? v[k] : v[k + 8];
-    const float keep = up ? v[k + 8] : v[k];
-    w8[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    for (int k = 0; k < H; ++k) {
+      const float lo = v[k];
+      const float hi = (k + H < N) ? v[k + H] : 0.f;
+      const float send = up ? lo : hi;
+      const float keep = up ? hi : lo;
+      w[k] = keep + __shfl_xor_sync(0xffffffffu, send, kBit);
+    }
+    return TransposeSum<H, kBit / 2>::run(w, lane);
   }
+  static __device__ __forceinline__ int index(int lane) {
+    constexpr int H = (N + 1) / 2;
+    const int r = TransposeSum<H, kBit / 2>::index(lane);
+    if (r < 0) return -1;
+    if (lane & kBit) return r < N - H ? H + r : -1;  // the upper half holds N - H values
+    return r;
+  }
+};
+template <int kBit>
+struct TransposeSum<1, kBit> {
+  static __device__ __forceinline__ float run(const float* v, int) {
+    float x = v[0];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const bool up = lane & 8;
-    const float send = up ? w8[k] : w8[k + 4];
-    const float keep = up ? w8[k + 4] : w8[k];
-    w4[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    for (int b = kBit; b > 0; b >>= 1) x += __shfl_xor_sync(0xffffffffu, x, b);
+    return x;
   }
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const bool up = lane & 4;
-    const float send = up ? w4[k] : w4[k + 2];
-    const float keep = up ? w4[k + 2] : w4[k];
-    w2[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  }
-  const bool up = lane & 2;
-  float x = (up ? w2[1] : w2[0]) + __shfl_xor_sync(0xffffffffu, up ? w2[0] : w2[1], 2);
-  x += __shfl_xor_sync(0xffffffffu, x, 1);
-  return x;
+  static __device__ __forceinline__ int index(int) { return 0; }
+};
+
+// Lane bits still summed directly after the halving rounds of an N-value transpose sum: lanes
+// that differ only in these bits hold the same total.
+template <int N>
+__host__ __device__ constexpr int transpose_shared_bits() {
+  int n = N, bit = 16;
+  while (n > 1 && bit > 0) { n = (n + 1) / 2; bit >>= 1; }
+  return 2 * bit - 1;
 }
 
-template <bool kCount>
+// kAbs: also accumulate |dL/dmean2D| per pixel (AbsGS densification statistics).
+template <bool kCount, bool kAbs>
 __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __restrict__ rec,
                                                                   const uint32_t* __restrict__ pvals,
                                                                   const uint2* __restrict__ ranges, CamBatch cams,
                                                                   float3 bg, BlendBwdIn in, Grad2D* __restrict__ g2d,
-                                                                  float* __restrict__ g_aff, int absgrad,
+                                                                  float* __restrict__ g_aff,
                                                                   unsigned long long* counters) {
+  constexpr int kVals = kAbs ? kGradVals : kGradVals - 2;  // gradient values summed per Gaussian
   __shared__ float4 sA[kBatch];
   __shared__ float4 sB[kBatch];
   __shared__ float2 sC[kBatch];
@@ -355,6 +374,8 @@ __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __r
   const int lt = t - cam.tile_off;
   const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int t_idx = TransposeSum<kVals, 16>::index(lane);  // the gradient value this lane sums
+  const bool t_keep = t_idx >= 0 && (lane & transpose_shared_bits<kVals>()) == 0;
   const int px = tx * kTile + 8 * (wid & 1) + (tid & 7);
   const int py0 = ty * kTile + 8 * (wid >> 1) + 2 * ((tid & 31) >> 3);
   const float fx = px + 0.5f;
@@ -431,9 +452,9 @@ __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __r
     for (int j = 0; j < cnt; ++j) {
       if (!((sM[j] >> wid) & 1u)) continue;  // warp-uniform: no pixel of this warp is touched
       const uint32_t pos = static_cast<uint32_t>(n - 1 - base - j);
-      float gv[16];
+      float gv[kGradVals];
 #pragma unroll
-      for (int m = 0; m < 16; ++m) gv[m] = 0.f;
+      for (int m = 0; m < kGradVals; ++m) gv[m] = 0.f;
       bool contrib = false;
       const float4 a = sA[j];
       const float4 b = sB[j];
@@ -478,21 +499,21 @@ __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __r
         gv[7] += GC0[q] * wgt;
         gv[8] += GC1[q] * wgt;
         gv[9] += GC2[q] * wgt;
-        gv[10] += fabsf(dmx);
-        gv[11] += fabsf(dmy);
+        if (kAbs) {
+          gv[10] += fabsf(dmx);
+          gv[11] += fabsf(dmy);
+        }
       }
       if (__any_sync(0xffffffffu, contrib)) {
-        const float tot = warp_transpose_sum16(gv, lane);
-        const int m = lane >> 1;
-        if (!(lane & 1) && m < kGradVals && (m < kGradVals - 2 || absgrad)) atomicAdd(&sAcc[j][m], tot);
+        const float tot = TransposeSum<kVals, 16>::run(gv, lane);
+        if (t_keep) atomicAdd(&sAcc[j][t_idx], tot);
       }
     }
     __syncthreads();
     for (int k = tid; k < cnt; k += kBlendThreads) {
       float* f = reinterpret_cast<float*>(g2d + sV[k]);
 #pragma unroll
-      for (int m = 0; m < kGradVals; ++m) {
-        if (m >= kGradVals - 2 && !absgrad) continue;
+      for (int m = 0; m < kVals; ++m) {
         const float val = sAcc[k][m];
         if (val != 0.f) atomicAdd(f + m, val);
       }
@@ -575,12 +596,15 @@ void launch_blend_bwd(const Rec* rec, const uint32_t* pair_vals, const uint2* ra
                       unsigned long long* counters, cudaStream_t s) {
   if (cams.total_tiles <= 0) return;
   const float3 b3 = make_float3(bg[0], bg[1], bg[2]);
-  if (counters)
-    blend_bwd_kernel<true><<<cams.total_tiles, kBlendThreads, 0, s>>>(rec, pair_vals, ranges, cams, b3, in, g2d, g_aff,
-                                                                      absgrad, counters);
-  else
-    blend_bwd_kernel<false><<<cams.total_tiles, kBlendThreads, 0, s>>>(rec, pair_vals, ranges, cams, b3, in, g2d, g_aff,
-                                                                       absgrad, nullptr);
+#define GSR_BWD(C, A)                                                                                  \
+  blend_bwd_kernel<C, A><<<cams.total_tiles, kBlendThreads, 0, s>>>(rec, pair_vals, ranges, cams, b3, in, g2d, \
+                                                                    g_aff, counters)
+  if (counters) {
+    if (absgrad) GSR_BWD(true, true); else GSR_BWD(true, false);
+  } else {
+    if (absgrad) GSR_BWD(false, true); else GSR_BWD(false, false);
+  }
+#undef GSR_BWD
 }
 
 }  // namespace gsr
