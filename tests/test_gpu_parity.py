@@ -278,6 +278,41 @@ def test_box_scene_backward(ctx, aa, cull, deg):
     pu.grad_close(gg["appearance"], ref["affine"], "appearance")
 
 
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_gradient_rows_unaligned_and_prefilled(ctx, shift):
+    """Gradient arrays that start 4, 8 or 12 bytes past a 16-byte boundary and hold NaN before
+    the call: every row is written (rows of Gaussians without a record exactly 0) and the values
+    equal those written into fresh aligned arrays (up to the order of the FP32 atomic sums)."""
+    scene, cam = pu.scene_box(20000, seed=21)
+    m = np.array(scene.means, np.float64)
+    m[::3, 2] = -5.0  # a third of the Gaussians behind the camera: no record
+    scene = scenes.Scene(m, scene.scales, scene.quats, scene.opacities, scene.sh, 3)
+    nopts, oopts = pu.opts_pair(tile_cull=True, absgrad=True)
+    g, out, st = pu.gpu_render(ctx, scene, [cam], nopts)
+    res = oracle.render(scene, [cam], oopts, want_pairs=False)
+    up = _upstream(res, cam.width * cam.height, seed=3)
+    ref = _gpu_backward(ctx, g, [cam], st, up, nopts)
+    n = g.n
+    shapes = dict(means=(n, 3), scales=(n, 3), quats=(n, 4), opacities=(n,), sh=(n, 16, 3), absgrad=(n, 2))
+    grads = {}
+    for k, shp in shapes.items():
+        size = int(np.prod(shp))
+        buf = torch.full((size + 8,), float("nan"), device="cuda")
+        grads[k] = buf[shift:shift + size].view(shp)
+    grads["appearance"] = torch.full((1, 3, 4), float("nan"), device="cuda")
+    d = dict(rgb=torch.tensor(up[:, 0:3], dtype=torch.float32, device="cuda").contiguous(),
+             depth_acc=torch.tensor(up[:, 3], dtype=torch.float32, device="cuda").contiguous(),
+             depth_exp=torch.tensor(up[:, 4], dtype=torch.float32, device="cuda").contiguous(),
+             alpha=torch.tensor(up[:, 5], dtype=torch.float32, device="cuda").contiguous())
+    native.render_backward(ctx, g, [cam], st, d, nopts, grads=grads)
+    hidden = m[:, 2] < 0
+    for k in shapes:
+        got = grads[k].cpu().numpy().reshape(n, -1)
+        assert np.isfinite(got).all(), k
+        assert (got[hidden] == 0).all(), k
+        pu.grad_close(got, ref[k].reshape(n, -1), k, rel=1e-5, group_rel=1e-6)
+
+
 def test_backward_batched_with_appearance_and_recompute(ctx):
     scene, cam = pu.scene_box(3000, seed=4)
     cam2 = scenes.box_camera(160, 96, f=200.0)
