@@ -174,9 +174,6 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, uint32_t P, int
                          lower_bound_u32(keys, P, static_cast<uint32_t>(t) + 1u));
 }
 
-// sigma beyond which alpha = o' exp(-sigma) is certainly below 1/255: ln(255 o'), plus a margin
-// far above FP32 rounding, so that the cheap test never rejects what the exact test keeps.
-__device__ __forceinline__ float sigma_cutoff(float op) { return logf(255.f * op) * 1.001f + 1e-3f; }
 
 template <bool kCount>
 __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(const Rec* __restrict__ rec,
@@ -188,7 +185,6 @@ __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(const Rec* __r
   __shared__ float4 sB[kBatch];
   __shared__ float2 sC[kBatch];
   __shared__ uint32_t sM[kBatch];
-  __shared__ float sL[kBatch];
   const int t = blockIdx.x;
   const int c = find_cam(cams, t);
   const DevCam& cam = cams.cam[c];
@@ -218,40 +214,38 @@ __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(const Rec* __r
         sB[k] = r.b;
         sC[k] = make_float2(r.c.x, r.c.y);
         sM[k] = warp_block_mask(r.d, x0, y0, x_max, y_max);
-        sL[k] = sigma_cutoff(r.a.z);
       }
     }
     __syncthreads();
     const int cnt = min(kBatch, n - base);
-    for (int j = 0; j < cnt && !(done[0] && done[1]); ++j) {
+    // Branch-free over the two pixels of a lane: every test is a predicate, so the warp runs
+    // one instruction stream per Gaussian; it leaves once all of its pixels are done.
+    for (int j = 0; j < cnt; ++j) {
       if (!((sM[j] >> wid) & 1u)) continue;  // no pixel of this warp can reach alpha 1/255
+      if (__all_sync(0xffffffffu, done[0] && done[1])) break;
       const float4 a = sA[j];
       const float4 b = sB[j];
-      const float cut = sL[j];
+      const float2 cc = sC[j];
       const float dx = a.x - fx;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        if (done[q]) continue;
-        if (kCount) ++n_eval;
+        if (kCount) n_eval += !done[q];
         const float dy = a.y - fy[q];
         const float sigma = 0.5f * (b.x * dx * dx + b.z * dy * dy) + b.y * dx * dy;
-        if (sigma < 0.f || sigma > cut) continue;
         const float alpha = fminf(kAlphaMax, a.z * __expf(-sigma));
-        if (alpha < kAlphaMin) continue;
+        const bool ok = !done[q] && sigma >= 0.f && alpha >= kAlphaMin;
         const float Tn = T[q] * (1.f - alpha);
-        if (Tn < kTMin) {
-          done[q] = true;
-          continue;
-        }
-        const float wgt = alpha * T[q];
-        const float2 cc = sC[j];
+        const bool term = ok && Tn < kTMin;  // stop before T drops below 1e-4
+        const bool use = ok && !term;
+        const float wgt = use ? alpha * T[q] : 0.f;
         C0[q] = fmaf(b.w, wgt, C0[q]);
         C1[q] = fmaf(cc.x, wgt, C1[q]);
         C2[q] = fmaf(cc.y, wgt, C2[q]);
         D[q] = fmaf(a.w, wgt, D[q]);
-        T[q] = Tn;
-        last[q] = static_cast<uint32_t>(base + j + 1);
-        if (kCount) ++n_blend;
+        T[q] = use ? Tn : T[q];
+        last[q] = use ? static_cast<uint32_t>(base + j + 1) : last[q];
+        done[q] = done[q] || term;
+        if (kCount) n_blend += use;
       }
     }
   }
@@ -364,7 +358,6 @@ __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __r
   __shared__ float2 sC[kBatch];
   __shared__ uint32_t sV[kBatch];
   __shared__ uint32_t sM[kBatch];
-  __shared__ float sL[kBatch];
   __shared__ float sAcc[kBatch][kGradVals + 1];
   __shared__ uint32_t s_max;
   __shared__ float s_aff[kBlendWarps][12];
@@ -442,7 +435,6 @@ __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __r
         sC[k] = make_float2(r.c.x, r.c.y);
         sV[k] = v;
         sM[k] = warp_block_mask(r.d, x0, y0, x_max, y_max);
-        sL[k] = sigma_cutoff(r.a.z);
       }
 #pragma unroll
       for (int m = 0; m < kGradVals; ++m) sAcc[k][m] = 0.f;
@@ -459,24 +451,22 @@ __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __r
       const float4 a = sA[j];
       const float4 b = sB[j];
       const float2 cc = sC[j];
-      const float cut = sL[j];
       const float dx = a.x - fx;
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (!(inside[q] && pos < last[q])) continue;
-        if (kCount) ++n_visit;
+      for (int q = 0; q < 2; ++q) {  // branch-free: contributions are masked, not branched around
+        const bool vis = inside[q] && pos < last[q];
+        if (kCount) n_visit += vis;
         const float dy = a.y - fy[q];
         const float sigma = 0.5f * (b.x * dx * dx + b.z * dy * dy) + b.y * dx * dy;
-        if (sigma < 0.f || sigma > cut) continue;
         const float G = __expf(-sigma);
         const float araw = a.z * G;
         const float alpha = fminf(kAlphaMax, araw);
-        if (alpha < kAlphaMin) continue;
-        contrib = true;
-        if (kCount) ++n_contrib;
+        const bool c = vis && sigma >= 0.f && alpha >= kAlphaMin;
+        if (kCount) n_contrib += c;
+        contrib = contrib || c;
         const float rom = __frcp_rn(1.f - alpha);  // 1 / (1 - alpha), correctly rounded
         const float Ti = T[q] * rom;
-        const float wgt = alpha * Ti;
+        const float wgt = c ? alpha * Ti : 0.f;
         const float dz = a.w - zr[q];
         const float dal = Ti * (GC0[q] * b.w + GC1[q] * cc.x + GC2[q] * cc.y + GD[q] * dz) +
                           (GTz[q] * Tf[q] - (GC0[q] * S0[q] + GC1[q] * S1[q] + GC2[q] * S2[q] + GD[q] * SD[q])) * rom;
@@ -484,8 +474,8 @@ __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __r
         S1[q] = fmaf(cc.x, wgt, S1[q]);
         S2[q] = fmaf(cc.y, wgt, S2[q]);
         SD[q] = fmaf(dz, wgt, SD[q]);
-        T[q] = Ti;
-        const float draw = araw > kAlphaMax ? 0.f : dal;
+        T[q] = c ? Ti : T[q];
+        const float draw = (c && araw <= kAlphaMax) ? dal : 0.f;  // the clamp at 0.99 passes no gradient
         const float dsig = -draw * araw;
         const float dmx = (b.x * dx + b.y * dy) * dsig;
         const float dmy = (b.y * dx + b.z * dy) * dsig;

@@ -282,7 +282,7 @@ def test_box_scene_backward(ctx, aa, cull, deg):
 def test_gradient_rows_unaligned_and_prefilled(ctx, shift):
     """Gradient arrays that start 4, 8 or 12 bytes past a 16-byte boundary and hold NaN before
     the call: every row is written (rows of Gaussians without a record exactly 0) and the values
-    equal those written into fresh aligned arrays (up to the order of the FP32 atomic sums)."""
+    match the oracle's gradient at the usual bar."""
     scene, cam = pu.scene_box(20000, seed=21)
     m = np.array(scene.means, np.float64)
     m[::3, 2] = -5.0  # a third of the Gaussians behind the camera: no record
@@ -291,7 +291,7 @@ def test_gradient_rows_unaligned_and_prefilled(ctx, shift):
     g, out, st = pu.gpu_render(ctx, scene, [cam], nopts)
     res = oracle.render(scene, [cam], oopts, want_pairs=False)
     up = _upstream(res, cam.width * cam.height, seed=3)
-    ref = _gpu_backward(ctx, g, [cam], st, up, nopts)
+    ref = oracle.backward(scene, [cam], up, oopts)
     n = g.n
     shapes = dict(means=(n, 3), scales=(n, 3), quats=(n, 4), opacities=(n,), sh=(n, 16, 3), absgrad=(n, 2))
     grads = {}
@@ -310,7 +310,7 @@ def test_gradient_rows_unaligned_and_prefilled(ctx, shift):
         got = grads[k].cpu().numpy().reshape(n, -1)
         assert np.isfinite(got).all(), k
         assert (got[hidden] == 0).all(), k
-        pu.grad_close(got, ref[k].reshape(n, -1), k, rel=1e-5, group_rel=1e-6)
+        pu.grad_close(got, np.asarray(ref[k]).reshape(n, -1), k)
 
 
 def test_backward_batched_with_appearance_and_recompute(ctx):
