@@ -45,7 +45,7 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--n", type=int, default=6_000_000)
+    p.add_argument("--gaussians", type=int, default=6_000_000)
     p.add_argument("--width", type=int, default=1920)
     p.add_argument("--height", type=int, default=1080)
     p.add_argument("--tile-cull", type=int, default=1)
@@ -123,10 +123,42 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def rank_env():
+    """(rank, world size, local rank) from the launcher's environment (1 process without one)."""
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def view_azimuth(rank):
+    """The work is sharded by camera: rank r renders the city from its own heading (no data is
+    exchanged between ranks)."""
+    return 90.0 + 45.0 * rank
+
+
+def max_over_ranks(x, world, device="cpu"):
+    """The largest of every rank's x (all ranks call it; a no-op for one process)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_ms_per_step(ms_max, world):
+    """`world` ranks each finish one step within ms_max: the whole job's time per step."""
+    return ms_max / world
+
+
+def workload_name(n, height):
+    return f"city{n / 1e6:g}m_{height}p"
+
+
 def make_workload(n, width, height, rank=0):
     from paper_2507_23006_gb300 import scenes
     scene = scenes.city(2, n)
-    cam = scenes.aerial_camera(width, height, altitude=150.0, pitch_deg=45.0, azimuth_deg=90.0 + 45.0 * rank)
+    cam = scenes.aerial_camera(width, height, altitude=150.0, pitch_deg=45.0, azimuth_deg=view_azimuth(rank))
     return scene, cam
 
 
@@ -172,7 +204,7 @@ def cpu_reference(scene, cam, tile_cull, n_tiles_sample, seed=0):
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    scene, cam = make_workload(args.n, args.width, args.height)
+    scene, cam = make_workload(args.gaussians, args.width, args.height)
     steps = []
     cores = None
     sample = ""
@@ -185,7 +217,7 @@ def run_reference(args, rank, world):
     line = dict(metric=METRIC, value=ms, unit="ms/step", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms, higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64",
                 data="synthetic", impl="reference",
-                config=dict(workload="city6m_1080p", n_gaussians=args.n, width=args.width, height=args.height,
+                config=dict(workload=workload_name(args.gaussians, args.height), n_gaussians=args.gaussians, width=args.width, height=args.height,
                             tile_cull=bool(args.tile_cull), l2="inputs larger than L2"),
                 cpu_baseline=dict(value=ms, unit="ms/step", cores=cores, kind="oracle", sample=sample),
                 e2e=dict(value=ms, unit="ms/step", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
@@ -200,7 +232,7 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = f"cuda:{local_rank}"
-    scene, cam = make_workload(args.n, args.width, args.height, rank)
+    scene, cam = make_workload(args.gaussians, args.width, args.height, rank)
     ctx = native.Context(local_rank)
     g = native.Gaussians.from_scene(scene, device=dev)
     opts = native.Options(tile_cull=bool(args.tile_cull), save_state=True)
@@ -264,10 +296,7 @@ def run_ours(args, rank, world, local_rank):
     timed = ctx.profile_collect()
     ctx.profile(False, False)
     dom_ms = timed["ms"][dom] / max(timed["launches"][dom], 1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     # forward-only frames per second (render path without state)
     for _ in range(2):
         native.render_forward(ctx, g, [cam], opts, outputs=outs, want_state=False)
@@ -279,7 +308,7 @@ def run_ours(args, rank, world, local_rank):
         native.render_forward(ctx, g, [cam], opts, outputs=outs, want_state=False)
     f1.record(stream)
     torch.cuda.synchronize()
-    fwd_ms = f0.elapsed_time(f1) / args.steps
+    fwd_ms = max_over_ranks(f0.elapsed_time(f1) / args.steps, world, dev)
     # blend evaluation counts (deterministic; one counting pass outside the timed region)
     ctx.profile(True, True)
     st = step()
@@ -348,11 +377,8 @@ def run_ours(args, rank, world, local_rank):
         x1.record(stream)
         torch.cuda.synchronize()
         e2e_ms = x0.elapsed_time(x1) / args.steps
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = dict(value=e2e_ms / world, unit="ms/step", h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
+        e2e_ms = max_over_ranks(e2e_ms, world, dev)
+        e2e = dict(value=job_ms_per_step(e2e_ms, world), unit="ms/step", h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
 
     serve_stats = None
     if not args.no_serve:
@@ -390,11 +416,11 @@ def run_ours(args, rank, world, local_rank):
         r = cpu_reference(scene, cam, args.tile_cull, args.cpu_tiles)
         cpu = dict(value=r["ms_per_step"], unit="ms/step", cores=r["cores"], kind="oracle", sample=r["sample"],
                    sample_seconds=round(r["sample_s"], 1))
-    value = ms / world
+    value = job_ms_per_step(ms, world)
     line = dict(metric=METRIC, value=value, unit="ms/step", n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms, higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f32",
                 data="synthetic",
-                config=dict(workload="city6m_1080p", n_gaussians=n, width=cam.width, height=cam.height,
+                config=dict(workload=workload_name(n, cam.height), n_gaussians=n, width=cam.width, height=cam.height,
                             tile_cull=bool(args.tile_cull), sh_degree=3, attributes="f32",
                             l2="inputs larger than L2 (1.4 GB), no flush", parallelism=f"replicas{world}"),
                 render_fps=1000.0 / fwd_ms * world, fwd_ms=fwd_ms,
@@ -468,9 +494,7 @@ def kernels_per_step(tile_cull, info):
 
 def main():
     args = parse()
-    rank = int(os.environ.get("RANK", 0))
-    world = int(os.environ.get("WORLD_SIZE", 1))
-    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    rank, world, local_rank = rank_env()
     if world > 1:
         import torch.distributed as dist
         if args.impl == "ours":
