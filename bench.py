@@ -251,6 +251,8 @@ def run_ours(args, rank, world, local_rank):
                  absgrad=None)
 
     def step():
+        # the gradient arrays are zeroed beside the forward pass (gsr_param_grads_zero)
+        native.zero_param_grads(ctx, g, grads)
         _, st = native.render_forward(ctx, g, [cam], opts, outputs=outs)
         native.render_backward(ctx, g, [cam], st, d_out, opts, grads=grads)
         return st
@@ -325,6 +327,7 @@ def run_ours(args, rank, world, local_rank):
         out16 = {k: _t.empty_like(v) for k, v in outs.items()}
 
         def step16():
+            native.zero_param_grads(ctx, g16, grads)
             _, st16 = native.render_forward(ctx, g16, [cam], opts, outputs=out16)
             native.render_backward(ctx, g16, [cam], st16, d_out, opts, grads=grads)
 

@@ -194,6 +194,22 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
                                const gsr_opts* opts, const gsr_fwd_state* state, const gsr_out_grads* dout,
                                const gsr_param_grads* grads, gsr_stream stream);
 
+/* Zeroes the parameter-gradient arrays of `grads` (means, scales, quats, opacities, sh and, when
+ * not NULL, absgrad; sized for g->n Gaussians and g->sh_coeffs as in gsr_render_backward) ahead
+ * of the backward pass. No counterpart in the paper: it moves the gradient initialisation that
+ * gsr_render_backward otherwise does itself to an earlier point, so that this memory-bound fill
+ * (236 bytes per Gaussian in FP32) runs beside a forward pass, whose stages leave most of the
+ * memory bandwidth unused, instead of beside the blend backward. The call only records the
+ * request (`stream` is not used): the next gsr_render_forward on this context queues the fill
+ * on the context's internal stream right after its preprocess stage (which itself moves much
+ * memory), ordered after everything queued on that forward's stream. The next
+ * gsr_render_backward on this context that is given exactly these arrays skips its own fill and
+ * waits for this one before writing (queuing it itself if no forward did); a backward given other
+ * arrays fills those itself and drops the request. The caller must not use the arrays between
+ * this call and that backward. Errors: GSR_ERR_INVALID_ARG (null struct or gradient array). */
+gsr_status gsr_param_grads_zero(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_param_grads* grads,
+                                gsr_stream stream);
+
 void gsr_state_release(gsr_ctx* ctx, gsr_fwd_state* state);
 gsr_status gsr_state_get_info(const gsr_fwd_state* state, gsr_state_info* info);
 /* Copies `bytes` of a state buffer into device memory `dst` (stream-ordered). */
@@ -219,8 +235,8 @@ typedef enum gsr_stage {
   GSR_STAGE_BLEND_FWD = 8,      /* forward compositing */
   GSR_STAGE_BLEND_BWD = 9,      /* backward compositing */
   GSR_STAGE_PREPROCESS_BWD = 10,/* projection and colour backward */
-  GSR_STAGE_BETWEEN = 11,       /* idle time between consecutive stages (memsets, host waits,
-                                   launch latency), gaps of 1 ms or more excluded */
+  GSR_STAGE_BETWEEN = 11,       /* idle time between consecutive stages of one call (memsets,
+                                   waits on the host or the side stream, launch latency) */
   GSR_NUM_STAGES = 12
 } gsr_stage;
 

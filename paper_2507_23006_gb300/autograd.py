@@ -25,7 +25,13 @@ class _Rasterize(torch.autograd.Function):
         if appearance is not None:
             appearance = appearance.contiguous()
             apps = [appearance[c] for c in range(len(cams))]
+        grads = None
+        if any(fctx.needs_input_grad[:6]):
+            # gradient arrays zeroed now, beside the forward pass, rather than inside the backward
+            grads = native.param_grads(lib_ctx, g, len(cams), opts.absgrad)
+            native.zero_param_grads(lib_ctx, g, grads)
         outs, state = native.render_forward(lib_ctx, g, cams, opts, appearances=apps)
+        fctx.grads = grads
         fctx.state = state
         fctx.lib_ctx = lib_ctx
         fctx.cams = cams
@@ -43,9 +49,10 @@ class _Rasterize(torch.autograd.Function):
             return None if t is None else t.contiguous().float()
         grads = native.render_backward(fctx.lib_ctx, fctx.g, fctx.cams, fctx.state,
                                        dict(rgb=c(d_rgb), depth_acc=c(d_dacc), depth_exp=c(d_dexp),
-                                            alpha=c(d_alpha)), fctx.opts, appearances=fctx.apps)
+                                            alpha=c(d_alpha)), fctx.opts, appearances=fctx.apps, grads=fctx.grads)
         fctx.state.release()
         fctx.state = None
+        fctx.grads = None
         app = grads["appearance"] if fctx.has_app else None
         return (grads["means"], grads["scales"].to(fctx.attr_dtype), grads["quats"].to(fctx.attr_dtype),
                 grads["opacities"].to(fctx.attr_dtype), grads["sh"].to(fctx.sh_dtype), app,

@@ -53,7 +53,9 @@ struct gsr_ctx {
   struct Rec3 {
     int stage;
     cudaEvent_t a, b;
+    uint64_t call;  // the API call that recorded it
   };
+  uint64_t call_seq = 0;
   std::vector<Rec3> prof_recs;
   uint32_t prof_mask = 0xffffffffu;  // stages whose events are recorded (bit k = stage k)
   std::vector<cudaEvent_t> ev_pool;
@@ -62,8 +64,12 @@ struct gsr_ctx {
   uint32_t epoch = 0;  // tag of the chained-scan status words of the latest launch
   // a second stream for work that overlaps the caller's (joined back before returning)
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_prezero = nullptr;
+  FillSpans prezero{};           // gradient arrays to zero ahead (gsr_param_grads_zero)
+  bool prezero_requested = false;  // recorded, the fill not queued yet
+  bool prezero_pending = false;    // fill queued (ev_prezero marks its end), not used yet
   int grid_cap = 304;  // resident blocks of the looping scan / sort kernels (2 per SM)
+  int fill_blocks = 76;  // blocks of the gradient zero fill (one per two SMs)
   // default allocator: a context-owned stream-ordered pool (growth and release never
   // synchronise the device, which matters when several contexts serve concurrently)
   cudaMemPool_t pool = nullptr;
@@ -220,7 +226,7 @@ struct StageTimer {
       return;
     }
     cudaEventRecord(b, s);
-    ctx->prof_recs.push_back({stage, a, b});
+    ctx->prof_recs.push_back({stage, a, b, ctx->call_seq});
   }
 };
 
@@ -327,6 +333,29 @@ struct BinOut {
 };
 
 // Preprocess + sort + bin into `bo`. Returns V and P through the pointers.
+// Zeroes the spans on the side stream after the work queued on `s`; `done` marks the end.
+// The fill is one small kernel (launch_zero_fill: a block per ctx->fill_blocks) rather than the
+// runtime's memset, which occupies every SM and stalls the latency-bound stages it runs beside.
+cudaError_t enqueue_fill(gsr_ctx* ctx, const FillSpans& f, cudaStream_t s, cudaEvent_t done) {
+  cudaError_t e = cudaEventRecord(ctx->ev_fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+  if (e == cudaSuccess) {
+    launch_zero_fill(f, ctx->fill_blocks, ctx->side);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(done, ctx->side);
+  return e;
+}
+
+// Queues a requested gradient fill (gsr_param_grads_zero) after the work queued on `s`.
+cudaError_t start_prezero(gsr_ctx* ctx, cudaStream_t s) {
+  if (!ctx->prezero_requested) return cudaSuccess;
+  ctx->prezero_requested = false;
+  const cudaError_t e = enqueue_fill(ctx, ctx->prezero, s, ctx->ev_prezero);
+  ctx->prezero_pending = e == cudaSuccess;
+  return e;
+}
+
 gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb, const gsr_opts* o, BinOut bo,
                        long long* V_out, long long* P_out, cudaStream_t s) {
   const long long N = render_count(g);
@@ -414,6 +443,10 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
     StageTimer tm(ctx, GSR_STAGE_PREPROCESS, s);
     launch_preprocess_fwd(ga, cb, o->eps2d, o->antialiased, po, pre_blocks, s);
   }
+  // A requested gradient fill starts here: the stages up to the end of the forward blend move
+  // little memory, the preprocess before them much.
+  e = start_prezero(ctx, s);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
 
   // depth sort of the visible records (V read on the device)
   if (!ensure_sort(ctx, capv, s)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
@@ -536,6 +569,7 @@ gsr_status gsr_create(gsr_ctx** out, int device, const gsr_allocator* alloc) {
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
     ctx->grid_cap = 2 * sms;
+    ctx->fill_blocks = std::max(1, sms / 2);
   cudaGetLastError();
   if (!alloc) {
     cudaMemPoolProps props{};
@@ -556,7 +590,8 @@ gsr_status gsr_create(gsr_ctx** out, int device, const gsr_allocator* alloc) {
   cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
   if (cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_prezero, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     gsr_destroy(ctx);
     return GSR_ERR_CUDA;
@@ -589,6 +624,7 @@ void gsr_destroy(gsr_ctx* ctx) {
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->ev_prezero) cudaEventDestroy(ctx->ev_prezero);
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->d_err) cudaFree(ctx->d_err);
@@ -624,6 +660,7 @@ gsr_status gsr_render_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_ca
   if (st != GSR_OK) return st;
   if (!out || !out->rgb) return set_err(ctx, GSR_ERR_INVALID_ARG, "rgb output is required");
   if (state_out) *state_out = nullptr;
+  ++ctx->call_seq;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
@@ -697,6 +734,48 @@ gsr_status gsr_render_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_ca
   return GSR_OK;
 }
 
+namespace {
+
+FillSpans grad_spans(const gsr_gaussians* g, const gsr_param_grads* grads) {
+  FillSpans f{};
+  const size_t n = static_cast<size_t>(g->n);
+  const auto add = [&f](float* p, size_t len) { f.ptr[f.count] = p; f.len[f.count] = len; ++f.count; };
+  add(grads->means, 3 * n);
+  add(grads->scales, 3 * n);
+  add(grads->quats, 4 * n);
+  add(grads->opacities, n);
+  add(grads->sh, 3 * static_cast<size_t>(g->sh_coeffs) * n);
+  if (grads->absgrad) add(grads->absgrad, 2 * n);
+  return f;
+}
+
+bool same_spans(const FillSpans& a, const FillSpans& b) {
+  if (a.count != b.count) return false;
+  for (int k = 0; k < a.count; ++k)
+    if (a.ptr[k] != b.ptr[k] || a.len[k] != b.len[k]) return false;
+  return true;
+}
+
+}  // namespace
+
+gsr_status gsr_param_grads_zero(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_param_grads* grads,
+                                gsr_stream stream) {
+  if (!ctx) return GSR_ERR_INVALID_ARG;
+  if (!g || !grads) return set_err(ctx, GSR_ERR_INVALID_ARG, "null gaussians or gradient struct");
+  if (g->n < 0 || (g->n > 0 && g->sh_coeffs < 1)) return set_err(ctx, GSR_ERR_INVALID_ARG, "bad Gaussian count");
+  if (g->n > 0 && (!grads->means || !grads->scales || !grads->quats || !grads->opacities || !grads->sh))
+    return set_err(ctx, GSR_ERR_INVALID_ARG, "null parameter gradient array");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  (void)stream;
+  ctx->prezero_pending = false;
+  ctx->prezero_requested = false;
+  if (g->n == 0) return GSR_OK;
+  ctx->prezero = grad_spans(g, grads);
+  ctx->prezero_requested = true;
+  return GSR_OK;
+}
+
 gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_camera* cams, int32_t n_cams,
                                const gsr_opts* opts, const gsr_fwd_state* state, const gsr_out_grads* dout,
                                const gsr_param_grads* grads, gsr_stream stream) {
@@ -709,6 +788,7 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
   const long long N = render_count(g);
   if (N != state->info.n_render || n_cams != state->info.n_cams)
     return set_err(ctx, GSR_ERR_INVALID_ARG, "inputs differ from the forward that made the state");
+  ++ctx->call_seq;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
@@ -734,26 +814,23 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
     e = cudaMemsetAsync(grads->appearance, 0, sizeof(float) * 12 * n_cams, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
   // Every parameter-gradient row starts at zero; only rows of Gaussians with a record are then
-  // written. The fill runs on the side stream, overlapping the (ALU-bound) blend backward.
+  // written. The fill runs on the side stream (overlapping the blend backward), unless
+  // gsr_param_grads_zero already queued it for these arrays.
+  cudaEvent_t join = nullptr;
   if (g->n > 0) {
-    const size_t n = static_cast<size_t>(g->n);
-    e = cudaEventRecord(ctx->ev_fork, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
-    if (e == cudaSuccess) {
-      FillSpans f{};
-      const auto add = [&f](float* p, size_t len) { f.ptr[f.count] = p; f.len[f.count] = len; ++f.count; };
-      add(grads->means, 3 * n);
-      add(grads->scales, 3 * n);
-      add(grads->quats, 4 * n);
-      add(grads->opacities, n);
-      add(grads->sh, 3 * static_cast<size_t>(g->sh_coeffs) * n);
-      if (grads->absgrad) add(grads->absgrad, 2 * n);
-      launch_zero_fill(f, ctx->grid_cap / 2, ctx->side);
-      e = cudaGetLastError();
+    const FillSpans f = grad_spans(g, grads);
+    if ((ctx->prezero_requested || ctx->prezero_pending) && same_spans(f, ctx->prezero)) {
+      e = start_prezero(ctx, s);  // not queued by a forward yet: now
+      if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
+      join = ctx->ev_prezero;
+    } else {
+      e = enqueue_fill(ctx, f, s, ctx->ev_join);
+      if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
+      join = ctx->ev_join;
     }
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
-    if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
   }
+  ctx->prezero_pending = false;  // a request this backward did not use is dropped
+  ctx->prezero_requested = false;
   BlendBwdIn bi;
   bi.d_rgb = dout->rgb;
   bi.d_depth_acc = dout->depth_acc;
@@ -767,8 +844,8 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
     launch_blend_bwd(as<Rec>(*bo.rec), as<uint32_t>(*bo.pvals_s), as<uint2>(*bo.ranges), cb, opts->bg, bi,
                      as<Grad2D>(ctx->g2d), grads->appearance, opts->absgrad && grads->absgrad, counters_of(ctx), s);
   }
-  if (g->n > 0) {
-    e = cudaStreamWaitEvent(s, ctx->ev_join, 0);
+  if (join) {
+    e = cudaStreamWaitEvent(s, join, 0);
     if (e != cudaSuccess) return cuda_err(ctx, e, "join");
   }
   GaussArgs ga;
@@ -904,21 +981,22 @@ gsr_status gsr_profile_collect(gsr_ctx* ctx, double* ms, int64_t* launches, int6
   if (!ctx) return GSR_ERR_INVALID_ARG;
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
-  cudaEvent_t prev_end = nullptr;
+  const gsr_ctx::Rec3* prev = nullptr;
   for (auto& r : ctx->prof_recs) {
     float t = 0.f, gap = 0.f;
+    const bool same_call = prev && prev->call == r.call;
     e = cudaEventSynchronize(r.b);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
-    if (e == cudaSuccess && prev_end) e = cudaEventElapsedTime(&gap, prev_end, r.a);
+    if (e == cudaSuccess && same_call) e = cudaEventElapsedTime(&gap, prev->b, r.a);
     if (e != cudaSuccess) return cuda_err(ctx, e, "profile events");
     if (ms) {
       ms[r.stage] += t;
-      // time between the end of one stage and the start of the next: memsets, host round
-      // trips, launch latency (gaps of 1 ms or more, between separate calls, are left out)
-      if (prev_end && gap > 0.f && gap < 1.0f) ms[GSR_STAGE_BETWEEN] += gap;
+      // time between the end of one stage and the start of the next within one call: memsets,
+      // waits on the side stream or the host, launch latency
+      if (same_call && gap > 0.f) ms[GSR_STAGE_BETWEEN] += gap;
     }
     if (launches) launches[r.stage] += 1;
-    prev_end = r.b;
+    prev = &r;
   }
   for (auto& r : ctx->prof_recs) {
     ctx->ev_pool.push_back(r.a);

@@ -141,7 +141,7 @@ struct FillSpans {
   size_t len[kFillSpans];  // floats
   int count;
 };
-// Sets `count` float arrays to zero with `blocks` blocks of one warp (bulk copies).
+// Sets `count` float arrays to zero with `blocks` blocks of 128 threads.
 void launch_zero_fill(const FillSpans& f, int blocks, cudaStream_t s);
 // Runs over the V visible records; the first record of each Gaussian writes its gradient rows
 // (the rows of Gaussians with no record must already be zero).

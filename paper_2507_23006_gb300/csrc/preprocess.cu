@@ -745,54 +745,29 @@ void launch_preprocess_fwd(const GaussArgs& g, const CamBatch& cams, float eps2d
 #undef GSR_PRE
 }
 
-// Zero fill of up to kFillSpans float arrays in one launch, done by the bulk-copy (TMA) engine
-// so that it takes almost no issue slots from the kernel it runs beside: one warp per block
-// zeroes a 16 KB shared buffer and one thread copies it over the arrays' 16-byte aligned bodies
-// (chunk c of the concatenated bodies goes to block c mod gridDim.x); the unaligned ends of each
-// array (under 16 bytes) are stored by block 0. The thread waits for its copies to complete
-// before the block exits.
-constexpr int kFillChunk = 16384;
-__global__ void __launch_bounds__(32) zero_fill_kernel(FillSpans f) {
-  __shared__ __align__(128) float4 s_zero[kFillChunk / 16];
-  for (int k = threadIdx.x; k < kFillChunk / 16; k += 32) s_zero[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // zeros visible to the copy engine
-  __syncwarp();
-  const uint32_t src = static_cast<uint32_t>(__cvta_generic_to_shared(s_zero));
-  const long long G = gridDim.x;
-  long long chunk_base = 0;
+// Zero fill of up to kFillSpans float arrays in one launch: a grid-stride loop of 16-byte
+// stores over each array's aligned body, scalar stores for the (under 16-byte) ends.
+__global__ void __launch_bounds__(128) zero_fill_kernel(FillSpans f) {
+  const size_t tid = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const size_t nthr = static_cast<size_t>(gridDim.x) * blockDim.x;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int k = 0; k < f.count; ++k) {
     float* p = f.ptr[k];
     const size_t n = f.len[k];
     const size_t mis = (reinterpret_cast<uintptr_t>(p) >> 2) & 3u;
     const size_t head = mis ? (4u - mis < n ? 4u - mis : n) : 0u;
-    const size_t body_bytes = ((n - head) * sizeof(float)) & ~static_cast<size_t>(15);
-    const size_t tail = head + body_bytes / sizeof(float);
-    if (blockIdx.x == 0) {
-      for (size_t i = threadIdx.x; i < head; i += 32) p[i] = 0.f;
-      for (size_t i = tail + threadIdx.x; i < n; i += 32) p[i] = 0.f;
-    }
-    const long long nch = static_cast<long long>((body_bytes + kFillChunk - 1) / kFillChunk);
-    if (threadIdx.x == 0) {
-      char* body = reinterpret_cast<char*>(p + head);
-      for (long long c = ((blockIdx.x - chunk_base) % G + G) % G; c < nch; c += G) {
-        const size_t off = static_cast<size_t>(c) * kFillChunk;
-        const uint32_t sz = static_cast<uint32_t>(body_bytes - off < kFillChunk ? body_bytes - off : kFillChunk);
-        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
-                     :: "l"(body + off), "r"(src), "r"(sz) : "memory");
-      }
-    }
-    chunk_base += nch;
+    const size_t n4 = (n - head) >> 2;
+    float4* body = reinterpret_cast<float4*>(p + head);
+    for (size_t i = tid; i < n4; i += nthr) body[i] = z;
+    const size_t done = head + 4 * n4;
+    if (tid < head) p[tid] = 0.f;
+    if (tid < n - done) p[done + tid] = 0.f;
   }
-  if (threadIdx.x == 0) {
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-  }
-  __syncwarp();
 }
 
 void launch_zero_fill(const FillSpans& f, int blocks, cudaStream_t s) {
-  if (f.count <= 0) return;
-  zero_fill_kernel<<<blocks, 32, 0, s>>>(f);
+  if (f.count <= 0 || blocks <= 0) return;
+  zero_fill_kernel<<<blocks, 128, 0, s>>>(f);
 }
 
 void launch_preprocess_bwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased, long long V,

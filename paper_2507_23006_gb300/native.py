@@ -37,6 +37,7 @@ EXPORTED = [
     "gsr_workspace_bytes", "gsr_render_forward", "gsr_render_backward", "gsr_state_release",
     "gsr_state_get_info", "gsr_state_copy", "gsr_sync_check", "gsr_sort_pairs_u32", "gsr_select_lod",
     "gsr_profile_enable", "gsr_profile_collect", "gsr_sort_pairs_u32_noalloc", "gsr_profile_select",
+    "gsr_param_grads_zero",
 ]
 
 STAGES = ["preprocess", "depth_sort", "tile_count", "pair_scan", "readback", "duplicate", "tile_sort", "ranges",
@@ -141,12 +142,13 @@ def load(build_if_missing: bool = True):
         L.gsr_profile_enable.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
         L.gsr_profile_collect.argtypes = [vp, vp, vp, vp]
         L.gsr_profile_select.argtypes = [vp, ctypes.c_uint32]
+        L.gsr_param_grads_zero.argtypes = [vp, vp, vp, vp]
         for name in EXPORTED:
             getattr(L, name)
         for name in ("gsr_create", "gsr_workspace_query", "gsr_render_forward", "gsr_render_backward",
                      "gsr_state_get_info", "gsr_state_copy", "gsr_sync_check", "gsr_sort_pairs_u32",
                      "gsr_select_lod", "gsr_profile_enable", "gsr_profile_collect",
-                     "gsr_sort_pairs_u32_noalloc", "gsr_profile_select"):
+                     "gsr_sort_pairs_u32_noalloc", "gsr_profile_select", "gsr_param_grads_zero"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -383,26 +385,43 @@ def render_forward(ctx: Context, g: Gaussians, cams, opts: Options = None, appea
     return outputs, (State(ctx, sh.value) if want_state else None)
 
 
+def param_grads(ctx: Context, g: Gaussians, n_cams: int, absgrad: bool = False) -> dict:
+    """Uninitialised gradient arrays for render_backward."""
+    dev = f"cuda:{ctx.device}"
+    n = g.n
+    K = int(g.sh.shape[1])
+    return dict(means=torch.empty((n, 3), device=dev), scales=torch.empty((n, 3), device=dev),
+                quats=torch.empty((n, 4), device=dev), opacities=torch.empty(n, device=dev),
+                sh=torch.empty((n, K, 3), device=dev), appearance=torch.empty((n_cams, 3, 4), device=dev),
+                absgrad=torch.empty((n, 2), device=dev) if absgrad else None)
+
+
+def _c_param_grads(grads: dict):
+    return CParamGrads(_ptr(grads["means"]), _ptr(grads["scales"]), _ptr(grads["quats"]), _ptr(grads["opacities"]),
+                       _ptr(grads["sh"]), _ptr(grads.get("appearance")), _ptr(grads.get("absgrad")))
+
+
+def zero_param_grads(ctx: Context, g: Gaussians, grads: dict, stream=None):
+    """Requests the zero fill of the gradient arrays ahead of the backward (see
+    gsr_param_grads_zero): called before render_forward, the fill runs beside that forward."""
+    cg, seg_keep = g.c_struct()
+    pg = _c_param_grads(grads)
+    _check(ctx, load().gsr_param_grads_zero(ctx.handle, ctypes.byref(cg), ctypes.byref(pg), _stream(stream)))
+    del seg_keep
+
+
 def render_backward(ctx: Context, g: Gaussians, cams, state: State, d_out: dict, opts: Options = None,
                     appearances=None, grads: Optional[dict] = None, stream=None) -> dict:
     """Gradients of L given dL/d(outputs) (keys rgb, depth_acc, depth_exp, alpha; missing = 0)."""
     opts = opts or Options()
-    dev = f"cuda:{ctx.device}"
-    n = g.n
-    K = int(g.sh.shape[1])
     if grads is None:
-        grads = dict(means=torch.empty((n, 3), device=dev), scales=torch.empty((n, 3), device=dev),
-                     quats=torch.empty((n, 4), device=dev), opacities=torch.empty(n, device=dev),
-                     sh=torch.empty((n, K, 3), device=dev),
-                     appearance=torch.empty((len(cams), 3, 4), device=dev),
-                     absgrad=torch.empty((n, 2), device=dev) if opts.absgrad else None)
+        grads = param_grads(ctx, g, len(cams), opts.absgrad)
     cg, seg_keep = g.c_struct()
     carr = c_cameras(cams, appearances)
     co = opts.c_struct()
     dg = COutGrads(_ptr(d_out.get("rgb")), _ptr(d_out.get("depth_acc")), _ptr(d_out.get("depth_exp")),
                    _ptr(d_out.get("alpha")))
-    pg = CParamGrads(_ptr(grads["means"]), _ptr(grads["scales"]), _ptr(grads["quats"]), _ptr(grads["opacities"]),
-                     _ptr(grads["sh"]), _ptr(grads.get("appearance")), _ptr(grads.get("absgrad")))
+    pg = _c_param_grads(grads)
     st = load().gsr_render_backward(ctx.handle, ctypes.byref(cg), carr, len(cams), ctypes.byref(co), state.handle,
                                     ctypes.byref(dg), ctypes.byref(pg), _stream(stream))
     _check(ctx, st)

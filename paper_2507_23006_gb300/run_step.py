@@ -1,13 +1,14 @@
 """Runs a fixed number of training steps (forward + backward through the C ABI) on one
 synthetic workload and nothing else: the command to put under a kernel profiler.
 
-    python -m paper_2507_23006_gb300.run_step --n 6000000 --width 1920 --height 1080 --steps 3
+    python -m paper_2507_23006_gb300.run_step --gaussians 6000000 --width 1920 --height 1080 --steps 3
 
 Workloads: `city` (a synthetic city grid seen from 150 m up at 45 degrees, the training-step
 benchmark), `street` (a street block, one camera 30 m up looking 45 degrees down) and `box`
 (uniform Gaussians in a box in front of the camera). `--fwd-only` runs forward renders without
-saved state; `--fp16` stores attributes and SH in FP16; `--time` prints the mean device time
-of each stage over the steps after the first (CUDA events around every stage).
+saved state; `--fp16` stores attributes and SH in FP16; `--time` prints the device time per
+step after the first, and then the mean time of each stage over as many more steps (CUDA events
+around every stage).
 """
 from __future__ import annotations
 
@@ -33,7 +34,7 @@ def workload(kind: str, n: int, width: int, height: int):
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--workload", default="city", choices=["city", "street", "box"])
-    p.add_argument("--n", type=int, default=6_000_000)
+    p.add_argument("--gaussians", type=int, default=6_000_000)
     p.add_argument("--width", type=int, default=1920)
     p.add_argument("--height", type=int, default=1080)
     p.add_argument("--steps", type=int, default=3)
@@ -42,7 +43,7 @@ def main():
     p.add_argument("--tile-cull", type=int, default=1)
     p.add_argument("--time", action="store_true")
     a = p.parse_args()
-    scene, cam = workload(a.workload, a.n, a.width, a.height)
+    scene, cam = workload(a.workload, a.gaussians, a.width, a.height)
     dt = torch.float16 if a.fp16 else torch.float32
     ctx = native.Context(0)
     g = native.Gaussians.from_scene(scene, attr_dtype=dt, sh_dtype=dt)
@@ -52,20 +53,38 @@ def main():
     d_out = dict(rgb=torch.randn((npix, 3), device="cuda", generator=gen),
                  depth_acc=torch.randn(npix, device="cuda", generator=gen) * 1e-2,
                  alpha=torch.randn(npix, device="cuda", generator=gen))
-    for step in range(a.steps):
-        if a.time and step == 1:
-            torch.cuda.synchronize()
-            ctx.profile(True)
-            ctx.profile_collect()
+    grads = native.param_grads(ctx, g, 1)
+
+    def step():
+        if not a.fwd_only:
+            native.zero_param_grads(ctx, g, grads)  # beside the forward pass
         out, st = native.render_forward(ctx, g, [cam], opts, want_state=not a.fwd_only)
         if st is not None:
-            native.render_backward(ctx, g, [cam], st, d_out, opts)
+            native.render_backward(ctx, g, [cam], st, d_out, opts, grads=grads)
             st.release()
+
+    step()
     torch.cuda.synchronize()
     if a.time and a.steps > 1:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.steps - 1):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.profile_collect()
+        for _ in range(a.steps - 1):
+            step()
+        torch.cuda.synchronize()
         ms = ctx.profile_collect()["ms"]
-        print(" ".join(f"{k}={v / (a.steps - 1) * 1e3:.1f}us" for k, v in ms.items() if v > 0))
         ctx.profile(False)
+        print(f"step={e0.elapsed_time(e1) / (a.steps - 1) * 1e3:.1f}us (without stage events); stages:",
+              " ".join(f"{k}={v / (a.steps - 1) * 1e3:.1f}us" for k, v in ms.items() if v > 0))
+    else:
+        for _ in range(a.steps - 1):
+            step()
+    torch.cuda.synchronize()
     ctx.close()
     print(f"ran {a.steps} steps of {a.workload} n={g.n} {cam.width}x{cam.height}")
 

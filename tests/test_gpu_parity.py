@@ -313,6 +313,47 @@ def test_gradient_rows_unaligned_and_prefilled(ctx, shift):
         pu.grad_close(got, np.asarray(ref[k]).reshape(n, -1), k)
 
 
+def test_param_grads_zeroed_ahead_of_the_forward(ctx):
+    """gsr_param_grads_zero before the forward: the backward with the same arrays skips its own
+    fill; a backward given other arrays fills them itself. Both are checked on NaN-prefilled
+    arrays against the oracle."""
+    scene, cam = pu.scene_box(8000, seed=22)
+    m = np.array(scene.means, np.float64)
+    m[::4, 2] = -5.0
+    scene = scenes.Scene(m, scene.scales, scene.quats, scene.opacities, scene.sh, 3)
+    hidden = m[:, 2] < 0
+    nopts, oopts = pu.opts_pair(tile_cull=True)
+    g = native.Gaussians.from_scene(scene)
+    res = oracle.render(scene, [cam], oopts, want_pairs=False)
+    up = _upstream(res, cam.width * cam.height, seed=4)
+    ref = oracle.backward(scene, [cam], up, oopts)
+    d = dict(rgb=torch.tensor(up[:, 0:3], dtype=torch.float32, device="cuda").contiguous(),
+             depth_acc=torch.tensor(up[:, 3], dtype=torch.float32, device="cuda").contiguous(),
+             depth_exp=torch.tensor(up[:, 4], dtype=torch.float32, device="cuda").contiguous(),
+             alpha=torch.tensor(up[:, 5], dtype=torch.float32, device="cuda").contiguous())
+
+    def nan_grads():
+        gr = native.param_grads(ctx, g, 1)
+        for v in gr.values():
+            if v is not None:
+                v.fill_(float("nan"))
+        return gr
+
+    for same in (True, False):
+        a, b = nan_grads(), nan_grads()
+        native.zero_param_grads(ctx, g, a)
+        out, st = native.render_forward(ctx, g, [cam], nopts)
+        got = native.render_backward(ctx, g, [cam], st, d, nopts, grads=a if same else b)
+        ctx.sync_check()
+        for k in ("means", "scales", "quats", "opacities", "sh"):
+            arr = got[k].cpu().numpy().reshape(g.n, -1)
+            assert np.isfinite(arr).all(), (k, same)
+            assert (arr[hidden] == 0).all(), (k, same)
+            pu.grad_close(arr, np.asarray(ref[k]).reshape(g.n, -1), f"{k} (same arrays: {same})")
+        if not same:  # the arrays zeroed ahead were not used by the backward, but are zero
+            assert all((a[k] == 0).all() for k in ("means", "scales", "quats", "opacities", "sh"))
+
+
 def test_backward_batched_with_appearance_and_recompute(ctx):
     scene, cam = pu.scene_box(3000, seed=4)
     cam2 = scenes.box_camera(160, 96, f=200.0)
