@@ -58,7 +58,7 @@ def lib():
             L.oracle_backward.restype = ctypes.c_int
             L.oracle_backward.argtypes = [ctypes.c_int64, _D, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D,
-                                          _I64, ctypes.c_int64]
+                                          _I64, ctypes.c_int64, _D]
             L.oracle_sh_basis.restype = ctypes.c_int
             L.oracle_sh_basis.argtypes = [ctypes.c_int64, _D, ctypes.c_int, _D]
             L.oracle_select_lod.restype = ctypes.c_int
@@ -187,9 +187,12 @@ def render(scene, cams, opts: Opts | None = None, affines=None, tile_subset=None
     return RenderResult(img, mark, sig, pairs, gmark, list(cams))
 
 
-def backward(scene, cams, up_grads, opts: Opts | None = None, affines=None, want_g2d=False, tile_subset=None):
+def backward(scene, cams, up_grads, opts: Opts | None = None, affines=None, want_g2d=False, tile_subset=None,
+             want_mag=False):
     """Analytic gradients of L = <up_grads, outputs>; up_grads is [sum HW, 6]
-    (d rgb 3, d depth_acc, d depth_exp, d alpha). Returns a dict of float64 arrays."""
+    (d rgb 3, d depth_acc, d depth_exp, d alpha). Returns a dict of float64 arrays. With
+    want_mag, out["mag"] holds, per gradient array, the magnitude of each element's sum (the
+    pixels' contributions in absolute value through the absolute Jacobian): |gradient| <= mag."""
     opts = opts or Opts()
     if not isinstance(cams, (list, tuple)):
         cams = [cams]
@@ -203,17 +206,21 @@ def backward(scene, cams, up_grads, opts: Opts | None = None, affines=None, want
                opacities=np.zeros(n), sh=np.zeros((n, K, 3)), affine=np.zeros((C, 12)),
                absgrad=np.zeros((n, 2)))
     g2d = np.zeros((C * n, 12)) if want_g2d else None
+    mag = np.zeros((n, 11 + 3 * K)) if want_mag else None
     sub = None if tile_subset is None else np.ascontiguousarray(np.asarray(tile_subset, np.int64))
     nsub = 0 if sub is None else sub.size
     rc = lib().oracle_backward(n, _p(means, _D), _p(scales, _D), _p(quats, _D), _p(opac, _D), _p(sh, _D), K, deg,
                                C, _p(rows, _D), _p(aff, _D), _p(opts.row(), _D), _p(up, _D),
                                _p(out["means"], _D), _p(out["scales"], _D), _p(out["quats"], _D),
                                _p(out["opacities"], _D), _p(out["sh"], _D), _p(out["affine"], _D),
-                               _p(out["absgrad"], _D), _p(g2d, _D), _p(sub, _I64), nsub)
+                               _p(out["absgrad"], _D), _p(g2d, _D), _p(sub, _I64), nsub, _p(mag, _D))
     if rc != 0:
         raise ValueError("oracle_backward: invalid arguments")
     if want_g2d:
         out["g2d"] = g2d
+    if want_mag:
+        out["mag"] = dict(means=mag[:, 0:3], scales=mag[:, 3:6], quats=mag[:, 6:10], opacities=mag[:, 10],
+                          sh=mag[:, 11:].reshape(n, K, 3))
     return out
 
 

@@ -243,6 +243,7 @@ struct Proj {
   unsigned flags = 0;    // discrete decisions: bit0-2 rgb clamp, bit3/4 Jacobian clamp x/y, bit5 comp=0
   // values of intermediate decisions, for knife-edge marks
   double z_val = 0.0, det_val = 0.0, ac_val = 0.0;
+  double mx_err = 0.0, my_err = 0.0;  // bound on the FP32 rounding error of mean2d (px)
 };
 
 template <typename T>
@@ -318,6 +319,7 @@ Proj<T> project(const T mean[3], const T scale[3], const T quat[4], const T& opa
       P.flags |= 32u;
     }
   }
+  P.op = op;
   P.ca = c / det;
   P.cb = -b / det;
   P.cc = a / det;
@@ -327,6 +329,23 @@ Proj<T> project(const T mean[3], const T scale[3], const T quat[4], const T& opa
   P.r = static_cast<int>(std::ceil(P.rad_src));
   P.mx = cam.fx * t[0] / t[2] + cam.cx;
   P.my = cam.fy * t[1] / t[2] + cam.cy;
+  {
+    // How far an FP32 evaluation of mean2d = f t/z + c can land from the exact value: a few
+    // units of rounding (2^-24) of the magnitudes summed at each step, i.e. of the terms of
+    // t = W mu + t_cam and of f t/z and c, which can be far larger than the result when they
+    // cancel (near the image's top-left edge, for instance).
+    const double u32 = 1.0 / 16777216.0;
+    double et[3];
+    for (int i = 0; i < 3; ++i)
+      et[i] = 4.0 * u32 * (std::fabs(cam.R[i * 3 + 0] * val(mean[0])) + std::fabs(cam.R[i * 3 + 1] * val(mean[1])) +
+                           std::fabs(cam.R[i * 3 + 2] * val(mean[2])) + std::fabs(cam.t[i]));
+    const double z = std::fabs(val(t[2]));
+    const double u = val(t[0]) / val(t[2]), w = val(t[1]) / val(t[2]);
+    const double eu = (et[0] + std::fabs(u) * et[2]) / z + 2.0 * u32 * std::fabs(u);
+    const double ew = (et[1] + std::fabs(w) * et[2]) / z + 2.0 * u32 * std::fabs(w);
+    P.mx_err = std::fabs(cam.fx) * eu + 4.0 * u32 * (std::fabs(cam.fx * u) + std::fabs(cam.cx));
+    P.my_err = std::fabs(cam.fy) * ew + 4.0 * u32 * (std::fabs(cam.fy * w) + std::fabs(cam.cy));
+  }
   P.rect = rect_of(val(P.mx), val(P.my), P.r, cam);
   if ((P.rect.x1 - P.rect.x0) * (P.rect.y1 - P.rect.y0) <= 0) return P;
   // view-dependent colour
@@ -401,12 +420,14 @@ double tile_cull_margin(const Proj<double>& p, const CamD& cam, int tx, int ty) 
 }
 
 // Knife-edge check of the rectangle: do FP32-sized perturbations of the decision's inputs
-// change it?  Returns the union of the perturbed rectangles and whether they differ.
-bool rect_knife_edge(const Proj<double>& p, const CamD& cam, Rect* uni) {
-  const double dm_x = 1e-6 * (std::fabs(p.mx) + 1.0);
-  const double dm_y = 1e-6 * (std::fabs(p.my) + 1.0);
+// change it?  Returns the union and the intersection of the nominal and perturbed rectangles
+// (the Gaussian is in every tile of the intersection whatever the precision; only the tiles of
+// the union outside it are uncertain) and whether they differ.
+bool rect_knife_edge(const Proj<double>& p, const CamD& cam, Rect* uni, Rect* inter) {
+  const double dm_x = std::max(1e-6 * (std::fabs(p.mx) + 1.0), 4.0 * p.mx_err);
+  const double dm_y = std::max(1e-6 * (std::fabs(p.my) + 1.0), 4.0 * p.my_err);
   const double dr = 1e-5 * p.rad_src;
-  Rect U = p.rect;
+  Rect U = p.rect, I = p.rect;
   bool differs = false;
   for (int sx = -1; sx <= 1; sx += 2)
     for (int sy = -1; sy <= 1; sy += 2)
@@ -416,8 +437,11 @@ bool rect_knife_edge(const Proj<double>& p, const CamD& cam, Rect* uni) {
         if (q.x0 != p.rect.x0 || q.x1 != p.rect.x1 || q.y0 != p.rect.y0 || q.y1 != p.rect.y1) differs = true;
         U.x0 = std::min(U.x0, q.x0); U.x1 = std::max(U.x1, q.x1);
         U.y0 = std::min(U.y0, q.y0); U.y1 = std::max(U.y1, q.y1);
+        I.x0 = std::max(I.x0, q.x0); I.x1 = std::min(I.x1, q.x1);
+        I.y0 = std::max(I.y0, q.y0); I.y1 = std::min(I.y1, q.y1);
       }
   *uni = U;
+  *inter = I;
   return differs;
 }
 
@@ -451,6 +475,7 @@ void bin_all(const SceneD& s, const std::vector<CamD>& cams, const OptsD& o, Bin
   // make uncertain are marked afterwards
   const int64_t CN = static_cast<int64_t>(C) * n;
   std::vector<Rect> mark_rect(CN, Rect{0, 0, 0, 0});
+  std::vector<Rect> sure_rect(CN, Rect{0, 0, 0, 0});  // tiles not made uncertain inside mark_rect
 #pragma omp parallel for schedule(dynamic, 1024)
   for (int64_t id = 0; id < CN; ++id) {
     const int c = static_cast<int>(id / n);
@@ -470,19 +495,41 @@ void bin_all(const SceneD& s, const std::vector<CamD>& cams, const OptsD& o, Bin
       Proj<double> q = project_d(s, g, wide, o);
       if (q.r > 0) mark_rect[id] = q.rect;
     }
-    if (!p.vis) continue;
-    Rect U;
-    if (rect_knife_edge(p, cam, &U)) {
+    // visible, or culled only because its rectangle came out empty (at an image edge)
+    if (!p.vis && !(p.rad_src > 0.0)) continue;
+    Rect U, I;
+    if (rect_knife_edge(p, cam, &U, &I)) {
+      if (near_plane || near_det) {  // existence uncertain: every tile of both rectangles
+        Rect& M = mark_rect[id];
+        if (M.x1 > M.x0 && M.y1 > M.y0) {
+          M.x0 = std::min(M.x0, U.x0); M.x1 = std::max(M.x1, U.x1);
+          M.y0 = std::min(M.y0, U.y0); M.y1 = std::max(M.y1, U.y1);
+        } else {
+          M = U;
+        }
+      } else {
+        mark_rect[id] = U;
+        sure_rect[id] = I;
+      }
       B->gmark[id] = 1;
-      mark_rect[id] = U;
     }
   }
   for (int64_t id = 0; id < CN; ++id) {
     const Rect& U = mark_rect[id];
+    const Rect& I = sure_rect[id];
     if (!B->gmark[id]) continue;
     const int c = static_cast<int>(id / n);
+    // a tile whose membership (or the Gaussian's existence) is uncertain matters only where the
+    // Gaussian can reach alpha 1/255 at one of its pixel centres (checked with the nominal
+    // projection when it has a conic; the margin is far above FP32 rounding)
+    const Proj<double>& p = B->proj[id];
+    const bool conic_ok = p.rad_src > 0.0 && p.det_val > 0.0;
     for (int ty = U.y0; ty < U.y1; ++ty)
-      for (int tx = U.x0; tx < U.x1; ++tx) B->tile_mark[B->tile_off[c] + ty * cams[c].tiles_x + tx] = 1;
+      for (int tx = U.x0; tx < U.x1; ++tx) {
+        if (tx >= I.x0 && tx < I.x1 && ty >= I.y0 && ty < I.y1) continue;
+        if (conic_ok && tile_cull_margin(p, cams[c], tx, ty) < -1e-3) continue;
+        B->tile_mark[B->tile_off[c] + ty * cams[c].tiles_x + tx] = 1;
+      }
   }
   // binning: count kept tiles per (camera, Gaussian), then fill, both in parallel
   std::vector<int64_t> cnt(CN + 1, 0);
@@ -753,12 +800,17 @@ int64_t oracle_render(int64_t n, const double* means, const double* scales, cons
 //                         opacity', rgb, depth, |mean2d| x/y
 //   tile_subset[n_subset] or NULL: only the pixels of these global tiles enter L (the result
 //                         equals the full gradient when up_grads is zero on every other pixel)
+//   g_mag[n][11 + 3K] or NULL: per parameter (mean 3, scale 3, quaternion 4, opacity, SH), the
+//                         magnitude of the sum that gives its gradient: every pixel's contribution
+//                         to the 2D quantities in absolute value, through the absolute Jacobian of
+//                         the projection. It bounds |gradient| and sets the scale of the rounding
+//                         error of any implementation that sums those contributions.
 int oracle_backward(int64_t n, const double* means, const double* scales, const double* quats,
                     const double* opac, const double* sh, int K, int deg, int C, const double* cams,
                     const double* affines, const double* opts, const double* up_grads,
                     double* g_means, double* g_scales, double* g_quats, double* g_opac, double* g_sh,
                     double* g_affine, double* g_absgrad, double* g2d_out, const int64_t* tile_subset,
-                    int64_t n_subset) {
+                    int64_t n_subset, double* g_mag) {
   if (!valid_inputs(n, means, scales, quats, opac, sh, K, deg, C, cams)) return -1;
   SceneD s{n, means, scales, quats, opac, sh, K, deg};
   std::vector<CamD> cv = load_cams(C, cams, affines);
@@ -772,6 +824,9 @@ int oracle_backward(int64_t n, const double* means, const double* scales, const 
   // per (tile, Gaussian) gradient contributions, reduced serially afterwards (deterministic)
   constexpr int G2 = 12;
   std::vector<double> pairbuf(static_cast<size_t>(P) * G2, 0.0);
+  // with g_mag: the same per-pixel contributions in absolute value (10 per pair)
+  constexpr int GM = 10;
+  std::vector<double> pairabs(g_mag ? static_cast<size_t>(P) * GM : 0, 0.0);
   std::vector<double> tile_aff(static_cast<size_t>(ntiles) * 12, 0.0);
   std::vector<uint8_t> use_tile(ntiles, tile_subset ? 0 : 1);
   if (tile_subset)
@@ -846,15 +901,26 @@ int oracle_backward(int64_t n, const double* means, const double* scales, const 
           pb[0] += mx_bar; pb[1] += my_bar; pb[2] += ca_bar; pb[3] += cb_bar; pb[4] += cc_bar;
           pb[5] += op_bar; pb[6] += rgb_bar[0]; pb[7] += rgb_bar[1]; pb[8] += rgb_bar[2];
           pb[9] += z_bar; pb[10] += std::fabs(mx_bar); pb[11] += std::fabs(my_bar);
+          if (g_mag) {
+            double* pa = pairabs.data() + (list_off[t] + pos) * GM;
+            const double v[GM] = {mx_bar, my_bar, ca_bar, cb_bar, cc_bar, op_bar, rgb_bar[0], rgb_bar[1],
+                                  rgb_bar[2], z_bar};
+            for (int j = 0; j < GM; ++j) pa[j] += std::fabs(v[j]);
+          }
         }
       }
   }
   std::vector<double> g2d(static_cast<size_t>(C) * n * G2, 0.0);
+  std::vector<double> g2abs(g_mag ? static_cast<size_t>(C) * n * GM : 0, 0.0);
   for (int64_t t = 0; t < ntiles; ++t)
     for (int64_t k = 0; k < static_cast<int64_t>(B.lists[t].size()); ++k) {
       const int64_t id = B.lists[t][k];
       const double* pb = pairbuf.data() + (list_off[t] + k) * G2;
       for (int j = 0; j < G2; ++j) g2d[id * G2 + j] += pb[j];
+      if (g_mag) {
+        const double* pa = pairabs.data() + (list_off[t] + k) * GM;
+        for (int j = 0; j < GM; ++j) g2abs[id * GM + j] += pa[j];
+      }
     }
   if (g_affine) {
     std::fill(g_affine, g_affine + 12 * C, 0.0);
@@ -874,6 +940,8 @@ int oracle_backward(int64_t n, const double* means, const double* scales, const 
     double gsh[48];
     std::fill(gsh, gsh + 48, 0.0);
     double gabs[2] = {0, 0};
+    double mag[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, mag_sh[48];
+    std::fill(mag_sh, mag_sh + 48, 0.0);
     D11 m[3], sc[3], q[4], op;
     for (int i = 0; i < 3; ++i) m[i] = D11::var(means[3 * g + i], i);
     for (int i = 0; i < 3; ++i) sc[i] = D11::var(scales[3 * g + i], 3 + i);
@@ -900,6 +968,16 @@ int oracle_backward(int64_t n, const double* means, const double* scales, const 
       }
       gabs[0] += gg[10];
       gabs[1] += gg[11];
+      if (g_mag) {
+        // magnitude: the absolute per-pixel contributions through the absolute Jacobian
+        const double* ga = g2abs.data() + (c * n + g) * GM;
+        for (int j = 0; j < 10; ++j)
+          for (int k = 0; k < 11; ++k) mag[k] += ga[j] * std::fabs(outs[j]->d[k]);
+        for (int ch = 0; ch < 3; ++ch) {
+          if (p.flags & (1u << ch)) continue;
+          for (int k = 0; k < nb && k < K; ++k) mag_sh[k * 3 + ch] += std::fabs(p.Y[k]) * ga[6 + ch];
+        }
+      }
     }
     for (int i = 0; i < 3; ++i) g_means[3 * g + i] = gm[i];
     for (int i = 0; i < 3; ++i) g_scales[3 * g + i] = gs[i];
@@ -907,6 +985,11 @@ int oracle_backward(int64_t n, const double* means, const double* scales, const 
     g_opac[g] = go;
     for (int k = 0; k < K * 3; ++k) g_sh[g * K * 3 + k] = (k < 48) ? gsh[k] : 0.0;
     if (g_absgrad) { g_absgrad[2 * g] = gabs[0]; g_absgrad[2 * g + 1] = gabs[1]; }
+    if (g_mag) {
+      double* out = g_mag + static_cast<size_t>(g) * (11 + 3 * K);
+      for (int k = 0; k < 11; ++k) out[k] = mag[k];
+      for (int k = 0; k < K * 3; ++k) out[11 + k] = (k < 48) ? mag_sh[k] : 0.0;
+    }
   }
   return 0;
 }

@@ -65,16 +65,22 @@ def oracle_tile_lists(pairs):
     return lists
 
 
-def grad_close(g, ref, name, rel=1e-3, group_rel=1e-3):
+def grad_close(g, ref, name, rel=1e-3, group_rel=1e-3, mag=None):
     """|g - ref| <= rel * ||ref row|| + group_rel * rms(ref) elementwise, where a row is one
     Gaussian's block of the parameter (its mean, scale, quaternion, opacity or SH block): a
     single component of a row can be a near-cancelling sum of large per-pixel terms, so its
-    FP32 error scales with the row, not with the component."""
+    FP32 error scales with the row, not with the component.
+
+    mag (the oracle's magnitude of each element's sum, oracle.backward(want_mag=True)) widens the
+    first term to rel * max(||ref row||, mag): where the per-pixel contributions cancel to a
+    result far below their own size, FP32 summation is accurate relative to that size only."""
     ref = np.asarray(ref, np.float64)
     g = np.asarray(g, np.float64).reshape(ref.shape)
     rows = ref.reshape(ref.shape[0], -1) if ref.ndim > 1 else ref.reshape(-1, 1)
     row_norm = np.sqrt((rows ** 2).sum(axis=1, keepdims=True))
     row_norm = np.broadcast_to(row_norm, rows.shape).reshape(-1)
+    if mag is not None:
+        row_norm = np.maximum(row_norm, np.asarray(mag, np.float64).reshape(-1))
     g = g.reshape(-1)
     ref = ref.reshape(-1)
     rms = np.sqrt(np.mean(ref ** 2)) if ref.size else 0.0

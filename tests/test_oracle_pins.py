@@ -446,3 +446,44 @@ def test_select_lod_culls_behind_and_budget_demotes_farthest():
     # impossible budget: everything visible goes to level 0, warning
     st, lev, _, nsel = oracle.select_lod(aabb, lo, cam, [100.0, 200.0], budget=3)
     assert lev.tolist() == [-1, 0, 0, 0] and nsel == 15 and st == 1
+
+
+@pytest.mark.parametrize("delta,marked", [(5e-6, True), (-5e-6, True), (0.2, False), (-0.2, False)])
+def test_rectangle_knife_edge_where_mean2d_cancels(delta, marked):
+    """my = fy y/z + cy with the two terms near -535.5 and 533.5: a rectangle bound 5e-6 px from
+    an integer is within reach of FP32 rounding (about 1e-4 px here), so the item is marked,
+    whichever side of the edge the FP64 value falls; 0.2 px away it is not."""
+    fy, cy, z = 1385.640646055102, 533.5, 427.466
+    cam = scenes.pinhole(np.hstack([np.eye(3), np.zeros((3, 1))]), 1600, 1067, fx=fy, fy=fy, cx=800.0, cy=cy)
+    # radius 3: 3 sqrt(lambda) in (2, 3); the top bound y1 = floor((my + 3 + 15) / 16) sits at 1
+    my = -2.0 + delta
+    y = (my - cy) * z / fy
+    scene = make_scene([[0.0, y, z]], [0.1], opac=[0.9], dc=[0.5])
+    rec, flags = oracle.project(scene, cam, oracle.Opts())
+    assert rec[0, 10] == 3.0 or not flags[0] & 1  # radius 3 (with the max(0.1, .) floor)
+    assert abs(fy * y / z) > 500 and abs(cy) > 500  # the cancelling terms
+    assert bool(flags[0] & 2) == marked
+    assert bool(flags[0] & 1) == (delta > 0)  # visible only when the FP64 bound reaches row 0
+
+
+def test_gradient_magnitude_bounds_and_single_pixel_equality():
+    """The magnitude returned with the gradient (the per-pixel contributions in absolute value
+    through the absolute Jacobian) bounds |gradient| elementwise (triangle inequality), and
+    equals it where one pixel of one Gaussian carries the loss and the Jacobian has one term
+    per entry (an isotropic Gaussian at the image centre, loss on its centre pixel's alpha)."""
+    scene, cam = scenes.box_scene(7, 300), scenes.box_camera(64, 64, f=80.0)
+    opts = oracle.Opts(bg=(0.1, 0.2, 0.3))
+    res = oracle.render(scene, [cam], opts, want_pairs=False)
+    up = np.random.default_rng(1).normal(size=(64 * 64, 6))
+    ref = oracle.backward(scene, [cam], up, opts, want_mag=True)
+    for k in ("means", "scales", "quats", "opacities", "sh"):
+        assert np.all(ref["mag"][k] >= np.abs(ref[k]) * (1 - 1e-12) - 1e-15), k
+        assert ref["mag"][k].max() > 0, k
+    # one Gaussian, one pixel: the opacity gradient has a single term
+    one = make_scene([[0.0, 0.0, 5.0]], [0.3], opac=[0.6], dc=[0.5])
+    cam1 = scenes.pinhole(np.hstack([np.eye(3), np.zeros((3, 1))]), 16, 16, fx=40.0, fy=40.0, cx=8.0, cy=8.0)
+    up1 = np.zeros((256, 6))
+    up1[8 * 16 + 8, 5] = 1.0
+    r1 = oracle.backward(one, [cam1], up1, oracle.Opts(), want_mag=True)
+    np.testing.assert_allclose(r1["mag"]["opacities"], np.abs(r1["opacities"]), rtol=1e-12)
+    assert res.img.shape[0] == 64 * 64
