@@ -55,6 +55,9 @@ def parse():
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--serve-rate", type=float, default=200.0)
     p.add_argument("--serve-seconds", type=float, default=2.0)
+    p.add_argument("--serve-full", action="store_true",
+                   help="also run the serving configuration at its own sizes (20M/6M/1.5M levels, 30 s trace)")
+    p.add_argument("--serve-full-seconds", type=float, default=30.0)
     p.add_argument("--cpu-tiles", type=int, default=24)
     return p.parse_args()
 
@@ -414,6 +417,7 @@ def run_ours(args, rank, world, local_rank):
     serve_stats = None
     if not args.no_serve:
         serve_stats = run_serve(scene, args)
+    serve_full = run_serve_full(args) if args.serve_full and rank == 0 else None
 
     if rank != 0:
         return 0
@@ -458,24 +462,15 @@ def run_ours(args, rank, world, local_rank):
                 render_fps=1000.0 / fwd_ms * world, fwd_ms=fwd_ms,
                 stages_ms=stage_ms, visible=V, pairs=P, counters=counts,
                 roofline=roof, cpu_baseline=cpu, e2e=e2e, clocks=clocks, fp16_storage=fp16, serve=serve_stats)
+    if serve_full is not None:
+        line["serve_full"] = serve_full
     line["gpu_launches"] = int(args.steps * kernels_per_step(args.tile_cull, info))
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serve(scene, args):
-    """Serving on the same city: detail levels (the 6M scene and two merged coarser levels,
-    0.3x the 20M / 6M / 1.5M of the reference configuration, budget scaled alike), Poisson
-    arrivals, resolutions drawn from 720p / 1080p / 4K, half walk-through and half aerial poses.
-    The FP16 LOD server and the plain FP32 full-detail renderer serve the same trace."""
-    import torch
-    from paper_2507_23006_gb300 import lod, scenes, serve
-    t0 = time.perf_counter()
-    mid = lod.merge_to_count(scene, int(0.3 * scene.n))
-    coarse = lod.merge_to_count(mid, int(0.075 * scene.n))
-    levels = lod.build_lod([coarse, mid, scene])
-    full = lod.build_lod([scene])
-    build_s = time.perf_counter() - t0
+def _serve_cameras():
+    from paper_2507_23006_gb300 import scenes
     res_choices = [(1280, 720), (1920, 1080), (3840, 2160)]
 
     def make_cam(rng):
@@ -485,28 +480,109 @@ def run_serve(scene, args):
         return scenes.aerial_camera(w, h, altitude=rng.uniform(80, 300), pitch_deg=rng.uniform(30, 89),
                                     target=(rng.uniform(-500, 500), rng.uniform(-500, 500), 0.0),
                                     azimuth_deg=rng.uniform(0, 360))
+    return make_cam
 
+
+def _serve_pair(levels, full, budget, rate, seconds, warm_s):
+    """The FP16 LOD server and the plain FP32 full-detail renderer on the same Poisson trace
+    (after a warm-up trace), then a burst of 200 simultaneous requests (saturated frames/s)."""
+    import torch
+    from paper_2507_23006_gb300 import serve
+    make_cam = _serve_cameras()
     out = {}
-    budget = int(4_000_000 * scene.n / 20_000_000)
-    for name, lodscene, dt, gb in (("lod_fp16", levels, torch.float16, budget),
-                                   ("full_fp32", full, torch.float32, 0)):
-        srv = serve.RenderServer(slots=4, gaussian_budget=gb)
+    for name, lodscene, dt, gb in (("lod_fp16", levels, torch.float16, budget), ("full_fp32", full, torch.float32, 0)):
+        srv = serve.RenderServer(slots=4, gaussian_budget=gb, keep_results=False)
         srv.add_scene("city", lodscene, attr_dtype=dt, sh_dtype=dt)
-        srv.run_trace(serve.poisson_trace(np.random.default_rng(7), args.serve_rate, 0.5, "city", make_cam))
-        st = srv.run_trace(serve.poisson_trace(np.random.default_rng(8), args.serve_rate, args.serve_seconds, "city",
-                                               make_cam))
-        # capacity: 200 requests that all arrive at once
+        srv.run_trace(serve.poisson_trace(np.random.default_rng(7), rate, warm_s, "city", make_cam))
+        st = srv.run_trace(serve.poisson_trace(np.random.default_rng(8), rate, seconds, "city", make_cam))
         rng = np.random.default_rng(9)
         burst = srv.run_trace([(0.0, "city", make_cam(rng)) for _ in range(200)])
         srv.close()
         out[name] = {k: st[k] for k in ("p50_ms", "p99_ms", "mean_ms", "fps", "served", "failed", "max_in_flight",
                                         "mean_batch", "mean_selected")}
         out[name]["saturated_fps"] = burst["fps"]
+        errs = sorted({r.error for r in st["requests"] + burst["requests"] if r.error})
+        if errs:
+            out[name]["errors"] = errs[:3]
         del srv
         torch.cuda.empty_cache()
+    return out
+
+
+def _serve_psnr(levels, full, budget, views=12):
+    """PSNR of the FP16-attribute render of each view's selected LOD set against the FP32 render
+    of the same set (the bar), and against the full-detail FP32 render (for information)."""
+    import torch
+    from paper_2507_23006_gb300 import native, serve
+    make_cam = _serve_cameras()
+    ctx = native.Context(0)
+    g32 = native.Gaussians.from_scene(levels.gaussians)
+    g16 = native.Gaussians.from_scene(levels.gaussians, attr_dtype=torch.float16, sh_dtype=torch.float16)
+    gf = native.Gaussians.from_scene(full.gaussians)
+    sel = serve.RenderServer(slots=1, gaussian_budget=budget)
+    sel.add_scene("city", levels)
+    opts = native.Options(tile_cull=True)
+    rng = np.random.default_rng(11)
+    same, vs_full = [], []
+
+    def psnr(a, b):
+        mse = float(((a.clamp(0, 1) - b.clamp(0, 1)) ** 2).mean())
+        return 10.0 * math.log10(1.0 / max(mse, 1e-20))
+    for _ in range(views):
+        cam = make_cam(rng)
+        segs, _, _ = sel.select("city", cam)
+        r32, _ = native.render_forward(ctx, native.Gaussians(g32.means, g32.scales, g32.quats, g32.opacities, g32.sh, 3,
+                                                             segs), [cam], opts, want_state=False)
+        r16, _ = native.render_forward(ctx, native.Gaussians(g16.means, g16.scales, g16.quats, g16.opacities, g16.sh, 3,
+                                                             segs), [cam], opts, want_state=False)
+        rf, _ = native.render_forward(ctx, gf, [cam], opts, want_state=False)
+        same.append(psnr(r16["rgb"], r32["rgb"]))
+        vs_full.append(psnr(r16["rgb"], rf["rgb"]))
+    sel.close()
+    ctx.close()
+    return dict(min_psnr_fp16_vs_fp32_same_set_db=round(min(same), 2),
+                mean_psnr_lod_fp16_vs_full_fp32_db=round(float(np.mean(vs_full)), 2), views=views)
+
+
+def run_serve(scene, args):
+    """Serving on the bench's city: detail levels (the 6M scene and two merged coarser levels,
+    0.3x the 20M / 6M / 1.5M of the reference configuration, budget scaled alike), Poisson
+    arrivals, resolutions drawn from 720p / 1080p / 4K, half walk-through and half aerial poses.
+    The FP16 LOD server and the plain FP32 full-detail renderer serve the same trace."""
+    from paper_2507_23006_gb300 import lod
+    t0 = time.perf_counter()
+    mid = lod.merge_to_count(scene, int(0.3 * scene.n))
+    coarse = lod.merge_to_count(mid, int(0.075 * scene.n))
+    levels = lod.build_lod([coarse, mid, scene])
+    full = lod.build_lod([scene])
+    build_s = time.perf_counter() - t0
+    budget = int(4_000_000 * scene.n / 20_000_000)
+    out = _serve_pair(levels, full, budget, args.serve_rate, args.serve_seconds, 0.5)
     out["config"] = dict(levels=levels.level_sizes, partitions=int(levels.aabb.shape[0]), gaussian_budget=budget,
                          thresholds_m=[100.0, 200.0], rate_hz=args.serve_rate, seconds=args.serve_seconds,
                          resolutions=["1280x720", "1920x1080", "3840x2160"], slots=4, lod_build_s=round(build_s, 1))
+    return out
+
+
+def run_serve_full(args):
+    """The serving configuration at its own sizes: a 20M-Gaussian city (seed 3) merged to 6M
+    and 1.5M levels over 100 m partitions, a 4M-Gaussian budget, Poisson arrivals at 200 req/s
+    for 30 s after a 2 s warm-up, 720p / 1080p / 4K, half walk-through and half aerial poses."""
+    from paper_2507_23006_gb300 import lod, scenes
+    t0 = time.perf_counter()
+    fine = scenes.city(3, 20_000_000)
+    mid = lod.merge_to_count(fine, 6_000_000)
+    coarse = lod.merge_to_count(mid, 1_500_000)
+    levels = lod.build_lod([coarse, mid, fine])
+    full = lod.build_lod([fine])
+    build_s = time.perf_counter() - t0
+    budget = 4_000_000
+    out = _serve_pair(levels, full, budget, args.serve_rate, args.serve_full_seconds, 2.0)
+    out["psnr"] = _serve_psnr(levels, full, budget)
+    out["config"] = dict(levels=levels.level_sizes, partitions=int(levels.aabb.shape[0]), gaussian_budget=budget,
+                         thresholds_m=[100.0, 200.0], rate_hz=args.serve_rate, seconds=args.serve_full_seconds,
+                         warmup_s=2.0, resolutions=["1280x720", "1920x1080", "3840x2160"], slots=4,
+                         lod_build_s=round(build_s, 1))
     return out
 
 

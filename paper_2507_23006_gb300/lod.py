@@ -9,6 +9,7 @@ partition, with per-partition boxes and per-level offsets.
 from __future__ import annotations
 
 import dataclasses
+import math
 
 import numpy as np
 
@@ -56,51 +57,74 @@ def _rot_to_quat(R):
     return q / np.linalg.norm(q, axis=1, keepdims=True)
 
 
-def merge_to_count(scene: Scene, target: int, extent: float = 1000.0, iters: int = 14) -> Scene:
-    """Opacity-weighted merging over a voxel grid, voxel size searched so that about `target`
-    voxels are occupied. Per voxel with weights w_i = o_i: mean = sum w mu / sum w; covariance =
-    sum w (Sigma_i + (mu_i - mean)(mu_i - mean)^T) / sum w (eigendecomposed into rotation and
-    scales); SH = sum w sh / sum w; opacity = 1 - prod(1 - o_i), at most 0.99."""
-    mu = np.asarray(scene.means, np.float64)
-    lo = mu.min(axis=0)
+def merge_to_count(scene: Scene, target: int, extent: float = 1000.0, iters: int = 40, rel_tol: float = 0.02,
+                   device=None) -> Scene:
+    """Opacity-weighted merging over a voxel grid, voxel size searched (geometric bisection,
+    stopping within rel_tol of the target) so that about `target` voxels are occupied. Per voxel
+    with weights w_i = o_i: mean = sum w mu / sum w; covariance = sum w (Sigma_i + (mu_i - mean)
+    (mu_i - mean)^T) / sum w (eigendecomposed into rotation and scales); SH = sum w sh / sum w;
+    opacity = 1 - prod(1 - o_i), at most 0.99. Runs with torch on `device` (the GPU when there
+    is one: a 20M-Gaussian level takes seconds there)."""
+    import torch
+    dev = torch.device(device or ("cuda" if torch.cuda.is_available() else "cpu"))
+    f64 = torch.float64
+    mu = torch.as_tensor(np.asarray(scene.means, np.float64), device=dev)
+    lo = mu.min(dim=0).values
 
     def keys(size):
-        v = np.floor((mu - lo) / size).astype(np.int64)
+        v = torch.floor((mu - lo) / size).long()
         return (v[:, 0] * 1_000_003 + v[:, 1]) * 1_000_033 + v[:, 2]
 
     a, b = 1e-3, extent
+    size = b
     for _ in range(iters):
-        mid = np.sqrt(a * b)
-        cnt = np.unique(keys(mid)).size
+        mid = math.sqrt(a * b)
+        cnt = int(torch.unique(keys(mid)).numel())
+        if abs(cnt - target) <= rel_tol * target:
+            size = mid
+            break
         if cnt > target:
             a = mid
         else:
             b = mid
-    _, inv = np.unique(keys(b), return_inverse=True)
-    m = int(inv.max()) + 1
-    w = np.asarray(scene.opacities, np.float64)
-    sw = np.bincount(inv, weights=w, minlength=m)
-    sw = np.maximum(sw, 1e-12)
-    mean = np.stack([np.bincount(inv, weights=w * mu[:, k], minlength=m) for k in range(3)], 1) / sw[:, None]
-    R = _quat_to_rot(np.asarray(scene.quats, np.float64))
-    s2 = np.asarray(scene.scales, np.float64) ** 2
-    cov = np.einsum("nij,nj,nkj->nik", R, s2, R)
+        size = b
+    _, inv = torch.unique(keys(size), return_inverse=True)
+    m = int(inv.max().item()) + 1
+    w = torch.as_tensor(np.asarray(scene.opacities, np.float64), device=dev).reshape(-1)
+    sw = torch.zeros(m, dtype=f64, device=dev).index_add_(0, inv, w).clamp_min(1e-12)
+    mean = torch.zeros(m, 3, dtype=f64, device=dev).index_add_(0, inv, w[:, None] * mu) / sw[:, None]
+    q = torch.as_tensor(np.asarray(scene.quats, np.float64), device=dev)
+    R = torch.as_tensor(_quat_to_rot(q.cpu().numpy()), device=dev) if dev.type == "cpu" else _quat_to_rot_t(q)
+    s2 = torch.as_tensor(np.asarray(scene.scales, np.float64), device=dev) ** 2
+    cov = torch.einsum("nij,nj,nkj->nik", R, s2, R)
+    del R
     d = mu - mean[inv]
-    cov = cov + d[:, :, None] * d[:, None, :]
-    C = np.zeros((m, 3, 3))
-    for i in range(3):
-        for j in range(3):
-            C[:, i, j] = np.bincount(inv, weights=w * cov[:, i, j], minlength=m) / sw
-    evals, evecs = np.linalg.eigh(C)
+    cov += d[:, :, None] * d[:, None, :]
+    C = torch.zeros(m, 9, dtype=f64, device=dev).index_add_(0, inv, w[:, None] * cov.reshape(-1, 9))
+    del cov, d
+    C = (C / sw[:, None]).reshape(m, 3, 3).cpu().numpy()
+    evals, evecs = np.linalg.eigh(C)  # on the host (LAPACK): seconds for millions of 3x3 matrices
     evecs[np.linalg.det(evecs) < 0, :, 0] *= -1.0
-    scales = np.sqrt(np.maximum(evals, 1e-10))
+    scales = torch.as_tensor(np.sqrt(np.maximum(evals, 1e-10)))
     quats = _rot_to_quat(evecs)
-    sh = np.asarray(scene.sh, np.float64).reshape(scene.n, -1)
-    shm = np.stack([np.bincount(inv, weights=w * sh[:, k], minlength=m) for k in range(sh.shape[1])], 1) / sw[:, None]
-    logt = np.bincount(inv, weights=np.log1p(-np.minimum(w, 0.999999)), minlength=m)
-    opac = np.minimum(1.0 - np.exp(logt), 0.99)
-    return Scene(mean.astype(np.float32), scales.astype(np.float32), quats.astype(np.float32),
-                 opac.astype(np.float32), shm.reshape(m, -1, 3).astype(np.float32), scene.sh_degree)
+    K = np.asarray(scene.sh).shape[1]
+    sh = torch.as_tensor(np.asarray(scene.sh, np.float32).reshape(scene.n, -1), device=dev)
+    shm = torch.zeros(m, sh.shape[1], dtype=torch.float32, device=dev).index_add_(0, inv, w[:, None].float() * sh)
+    shm = shm / sw[:, None].float()
+    logt = torch.zeros(m, dtype=f64, device=dev).index_add_(0, inv, torch.log1p(-w.clamp_max(0.999999)))
+    opac = torch.clamp(1.0 - torch.exp(logt), max=0.99)
+    return Scene(mean.float().cpu().numpy(), scales.float().cpu().numpy(), quats.astype(np.float32),
+                 opac.float().cpu().numpy(), shm.reshape(m, K, 3).cpu().numpy(), scene.sh_degree)
+
+
+def _quat_to_rot_t(q):
+    """_quat_to_rot on a torch tensor (same formula, on the tensor's device)."""
+    import torch
+    q = q / q.norm(dim=1, keepdim=True)
+    w, x, y, z = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    return torch.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                        2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                        2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], dim=1).reshape(-1, 3, 3)
 
 
 @dataclasses.dataclass

@@ -58,7 +58,7 @@ class _Resident:
 class RenderServer:
     def __init__(self, device: int = 0, slots: int = 4, memory_budget: Optional[int] = None,
                  gaussian_budget: int = 4_000_000, thresholds=(100.0, 200.0), max_batch: int = 8,
-                 opts: Optional[native.Options] = None):
+                 opts: Optional[native.Options] = None, keep_results: bool = True):
         self.device = int(device)
         self.dev = f"cuda:{self.device}"
         torch.cuda.set_device(self.device)
@@ -69,6 +69,9 @@ class RenderServer:
         self.gaussian_budget = int(gaussian_budget)
         self.thresholds = tuple(float(t) for t in thresholds)
         self.max_batch = int(max_batch)
+        # keep_results=False drops each image once it is ready (a server hands it to its
+        # client); kept, every image of a long trace stays in device memory
+        self.keep_results = bool(keep_results)
         self.opts = opts or native.Options(tile_cull=True, save_state=False)
         self.scenes: dict[str, _Resident] = {}
         self.queue: collections.deque = collections.deque()
@@ -170,9 +173,11 @@ class RenderServer:
                 off = 0
                 for r in batch:
                     hw = r.camera.width * r.camera.height
-                    r.rgb = out["rgb"][off:off + hw].view(r.camera.height, r.camera.width, 3)
+                    if self.keep_results:
+                        r.rgb = out["rgb"][off:off + hw].view(r.camera.height, r.camera.width, 3)
                     off += hw
                     r.t_start, r.t_done, r.batch_size = t0, t1, len(batch)
+                del out
             except Exception as e:  # reported on the request, the slot keeps serving
                 for r in batch:
                     r.error = str(e)
