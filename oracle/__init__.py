@@ -50,15 +50,15 @@ def lib():
             L = ctypes.CDLL(path)
             L.oracle_project.restype = ctypes.c_int
             L.oracle_project.argtypes = [ctypes.c_int64, _D, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int,
-                                         _D, _D, _D, _I32]
+                                         _D, _D, _D, _I32, _D, _D, _D]
             L.oracle_render.restype = ctypes.c_int64
             L.oracle_render.argtypes = [ctypes.c_int64, _D, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, _D, _D, _D, _I64, ctypes.c_int64, _D, _U8, _U64,
-                                        _I64, ctypes.c_int64, _U8]
+                                        _I64, ctypes.c_int64, _U8, _D, _D, _D]
             L.oracle_backward.restype = ctypes.c_int
             L.oracle_backward.argtypes = [ctypes.c_int64, _D, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D,
-                                          _I64, ctypes.c_int64, _D]
+                                          _I64, ctypes.c_int64, _D, _D, _D, _D, _D, _D, _D]
             L.oracle_sh_basis.restype = ctypes.c_int
             L.oracle_sh_basis.argtypes = [ctypes.c_int64, _D, ctypes.c_int, _D]
             L.oracle_select_lod.restype = ctypes.c_int
@@ -105,6 +105,22 @@ def _cam_rows(cams):
     return np.ascontiguousarray(np.stack([c.as_row() for c in cams]))
 
 
+MLP_SIZES = dict(gauss_embed=16, image_embed=32, hidden=32, out=4)
+
+
+def _mlp_args(mlp, n, C):
+    """Appearance transform (Sec. 3.5.1) inputs -> (gemb [n,16], iemb [C,32], params [1700]) or
+    Nones. mlp: dict(gemb [n,16], iemb [C,32], w1 [32,48], b1 [32], w2 [4,32], b2 [4])."""
+    if mlp is None:
+        return None, None, None
+    gemb = _f64(mlp["gemb"]).reshape(n, 16)
+    iemb = _f64(mlp["iemb"]).reshape(C, 32)
+    params = np.ascontiguousarray(np.concatenate([_f64(mlp["w1"]).reshape(-1), _f64(mlp["b1"]).reshape(-1),
+                                                  _f64(mlp["w2"]).reshape(-1), _f64(mlp["b2"]).reshape(-1)]))
+    assert params.size == 32 * 48 + 32 + 4 * 32 + 4
+    return gemb, iemb, params
+
+
 def num_threads() -> int:
     return int(lib().oracle_num_threads())
 
@@ -113,16 +129,18 @@ def set_num_threads(k: int) -> None:
     lib().oracle_set_num_threads(int(k))
 
 
-def project(scene, cam, opts: Opts | None = None):
-    """Per-Gaussian projection for one camera -> (rec [n,16], flags [n])."""
+def project(scene, cam, opts: Opts | None = None, mlp=None):
+    """Per-Gaussian projection for one camera -> (rec [n,16], flags [n]). With mlp (see
+    _mlp_args; its image embedding is the camera's), colour and opacity are transformed."""
     opts = opts or Opts()
     means, scales, quats, opac, sh, K, deg = _scene_args(scene)
     n = means.shape[0]
     rec = np.zeros((n, 16), np.float64)
     flags = np.zeros(n, np.int32)
+    gemb, iemb, params = _mlp_args(mlp, n, 1)
     rc = lib().oracle_project(n, _p(means, _D), _p(scales, _D), _p(quats, _D), _p(opac, _D), _p(sh, _D),
                               K, deg, _p(_cam_rows([cam]), _D), _p(opts.row(), _D), _p(rec, _D),
-                              _p(flags, _I32))
+                              _p(flags, _I32), _p(gemb, _D), _p(iemb, _D), _p(params, _D))
     if rc != 0:
         raise ValueError("oracle_project: invalid arguments")
     return rec, flags
@@ -152,8 +170,9 @@ class RenderResult:
 
 
 def render(scene, cams, opts: Opts | None = None, affines=None, tile_subset=None, want_pairs=True,
-           want_sig=False) -> RenderResult:
-    """Forward render of a list of cameras, packed one after another."""
+           want_sig=False, mlp=None) -> RenderResult:
+    """Forward render of a list of cameras, packed one after another (mlp: the appearance
+    transform's inputs, see _mlp_args)."""
     opts = opts or Opts()
     if not isinstance(cams, (list, tuple)):
         cams = [cams]
@@ -169,10 +188,12 @@ def render(scene, cams, opts: Opts | None = None, affines=None, tile_subset=None
     gmark = np.zeros(C * n, np.uint8)
     sub = None if tile_subset is None else np.ascontiguousarray(np.asarray(tile_subset, np.int64))
     nsub = 0 if sub is None else sub.size
+    gemb, iemb, params = _mlp_args(mlp, n, C)
+    margs = (_p(gemb, _D), _p(iemb, _D), _p(params, _D))
     args = (n, _p(means, _D), _p(scales, _D), _p(quats, _D), _p(opac, _D), _p(sh, _D), K, deg, C,
             _p(rows, _D), _p(aff, _D), _p(opts.row(), _D), _p(sub, _I64), nsub)
     # first call sizes the pair list
-    P = lib().oracle_render(*args, _p(img, _D), _p(mark, _U8), _p(sig, _U64), None, 0, _p(gmark, _U8))
+    P = lib().oracle_render(*args, _p(img, _D), _p(mark, _U8), _p(sig, _U64), None, 0, _p(gmark, _U8), *margs)
     if P < 0:
         raise ValueError("oracle_render: invalid arguments")
     pairs = None
@@ -181,14 +202,14 @@ def render(scene, cams, opts: Opts | None = None, affines=None, tile_subset=None
         P2 = lib().oracle_render(n, _p(means, _D), _p(scales, _D), _p(quats, _D), _p(opac, _D), _p(sh, _D),
                                  K, deg, C, _p(rows, _D), _p(aff, _D), _p(opts.row(), _D),
                                  _p(np.zeros(1, np.int64), _I64), 0, _p(np.zeros((1, 8)), _D), None, None,
-                                 _p(pairs, _I64), pairs.shape[0], None)
+                                 _p(pairs, _I64), pairs.shape[0], None, *margs)
         assert P2 == P
         pairs = pairs[:P]
     return RenderResult(img, mark, sig, pairs, gmark, list(cams))
 
 
 def backward(scene, cams, up_grads, opts: Opts | None = None, affines=None, want_g2d=False, tile_subset=None,
-             want_mag=False):
+             want_mag=False, mlp=None):
     """Analytic gradients of L = <up_grads, outputs>; up_grads is [sum HW, 6]
     (d rgb 3, d depth_acc, d depth_exp, d alpha). Returns a dict of float64 arrays. With
     want_mag, out["mag"] holds, per gradient array, the magnitude of each element's sum (the
@@ -207,17 +228,27 @@ def backward(scene, cams, up_grads, opts: Opts | None = None, affines=None, want
                absgrad=np.zeros((n, 2)))
     g2d = np.zeros((C * n, 12)) if want_g2d else None
     mag = np.zeros((n, 11 + 3 * K)) if want_mag else None
+    gemb, iemb, params = _mlp_args(mlp, n, C)
+    g_gemb = np.zeros((n, 16)) if mlp is not None else None
+    g_iemb = np.zeros((C, 32)) if mlp is not None else None
+    g_mlp = np.zeros(params.size) if mlp is not None else None
     sub = None if tile_subset is None else np.ascontiguousarray(np.asarray(tile_subset, np.int64))
     nsub = 0 if sub is None else sub.size
     rc = lib().oracle_backward(n, _p(means, _D), _p(scales, _D), _p(quats, _D), _p(opac, _D), _p(sh, _D), K, deg,
                                C, _p(rows, _D), _p(aff, _D), _p(opts.row(), _D), _p(up, _D),
                                _p(out["means"], _D), _p(out["scales"], _D), _p(out["quats"], _D),
                                _p(out["opacities"], _D), _p(out["sh"], _D), _p(out["affine"], _D),
-                               _p(out["absgrad"], _D), _p(g2d, _D), _p(sub, _I64), nsub, _p(mag, _D))
+                               _p(out["absgrad"], _D), _p(g2d, _D), _p(sub, _I64), nsub, _p(mag, _D),
+                               _p(gemb, _D), _p(iemb, _D), _p(params, _D), _p(g_gemb, _D), _p(g_iemb, _D),
+                               _p(g_mlp, _D))
     if rc != 0:
         raise ValueError("oracle_backward: invalid arguments")
     if want_g2d:
         out["g2d"] = g2d
+    if mlp is not None:
+        w1n, b1n, w2n = 32 * 48, 32, 4 * 32
+        out["mlp"] = dict(gemb=g_gemb, iemb=g_iemb, w1=g_mlp[:w1n].reshape(32, 48), b1=g_mlp[w1n:w1n + b1n],
+                          w2=g_mlp[w1n + b1n:w1n + b1n + w2n].reshape(4, 32), b2=g_mlp[w1n + b1n + w2n:])
     if want_mag:
         out["mag"] = dict(means=mag[:, 0:3], scales=mag[:, 3:6], quats=mag[:, 6:10], opacities=mag[:, 10],
                           sh=mag[:, 11:].reshape(n, K, 3))

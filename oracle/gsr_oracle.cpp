@@ -103,7 +103,39 @@ struct CamD {
   bool has_aff;
   double A[12];  // [A | b] row-major 3x4
   double center[3];
+  const double* iemb = nullptr;  // image embedding [32] of the appearance transform, or NULL
 };
+
+// ---------------------------------------------------------------------------------------------
+// Appearance transform (Sec. 3.5.1): a per-Gaussian embedding l_G (16) and a per-image embedding
+// l_I (32) go through one hidden layer of 32 with ReLU and an output layer of 4 with a sigmoid
+// (the sizes of the paper's supplementary notes). Reading of how the outputs adjust the Gaussian
+// (the paper says only that they adjust colour and opacity, and pulls the opacity output toward
+// zero): colour gain 2 out[0..2] on the SH colour (identity at 1/2) and opacity factor
+// 1 - out[3] (identity at 0). params = w1 [32][48] | b1 [32] | w2 [4][32] | b2 [4].
+constexpr int kEmbG = 16, kEmbI = 32, kHid = 32, kMlpOut = 4;
+constexpr int kMlpIn = kEmbG + kEmbI;
+constexpr int kMlpParams = kHid * kMlpIn + kHid + kMlpOut * kHid + kMlpOut;
+
+void mlp_forward(const double* params, const double* lg, const double* li, double pre[kHid], double hid[kHid],
+                 double out[kMlpOut]) {
+  const double* w1 = params;
+  const double* b1 = w1 + kHid * kMlpIn;
+  const double* w2 = b1 + kHid;
+  const double* b2 = w2 + kMlpOut * kHid;
+  for (int k = 0; k < kHid; ++k) {
+    double a = b1[k];
+    for (int j = 0; j < kEmbG; ++j) a += w1[k * kMlpIn + j] * lg[j];
+    for (int j = 0; j < kEmbI; ++j) a += w1[k * kMlpIn + kEmbG + j] * li[j];
+    pre[k] = a;
+    hid[k] = a > 0.0 ? a : 0.0;
+  }
+  for (int o = 0; o < kMlpOut; ++o) {
+    double z = b2[o];
+    for (int k = 0; k < kHid; ++k) z += w2[o * kHid + k] * hid[k];
+    out[o] = 1.0 / (1.0 + std::exp(-z));
+  }
+}
 
 struct OptsD {
   double eps2d;
@@ -244,11 +276,13 @@ struct Proj {
   // values of intermediate decisions, for knife-edge marks
   double z_val = 0.0, det_val = 0.0, ac_val = 0.0;
   double mx_err = 0.0, my_err = 0.0;  // bound on the FP32 rounding error of mean2d (px)
+  double rgb_pre[3] = {0, 0, 0}, op_pre = 0.0;  // colour and opacity before the appearance transform
 };
 
 template <typename T>
 Proj<T> project(const T mean[3], const T scale[3], const T quat[4], const T& opac,
-                const double* sh, int K, int deg, const CamD& cam, const OptsD& o) {
+                const double* sh, int K, int deg, const CamD& cam, const OptsD& o,
+                const double* mlp_out = nullptr) {
   Proj<T> P;
   // camera-space position t = W mu + t_cam
   T t[3];
@@ -361,8 +395,12 @@ Proj<T> project(const T mean[3], const T scale[3], const T quat[4], const T& opa
     T v = T(0.5);
     for (int k = 0; k < nb && k < K; ++k) v = v + sh[k * 3 + ch] * Yt[k];
     if (val(v) < 0.0) { v = T(0.0); P.flags |= (1u << ch); }
+    P.rgb_pre[ch] = val(v);
+    if (mlp_out) v = v * (2.0 * mlp_out[ch]);
     P.rgb[ch] = v;
   }
+  P.op_pre = val(op);
+  if (mlp_out) op = op * (1.0 - mlp_out[3]);
   P.op = op;
   P.z = t[2];
   const double outs[] = {val(P.mx), val(P.my), val(P.ca), val(P.cb), val(P.cc), val(P.op),
@@ -384,11 +422,23 @@ struct SceneD {
   const double* sh;
   int K;
   int deg;
+  const double* gemb = nullptr;  // [n][16] Gaussian embeddings, or NULL (no appearance transform)
+  const double* mlp = nullptr;   // [kMlpParams]
 };
 
+// The appearance transform's outputs for Gaussian g seen by `cam`; false when it is off.
+bool mlp_of(const SceneD& s, int64_t g, const CamD& cam, double out[kMlpOut]) {
+  if (!s.mlp || !s.gemb || !cam.iemb) return false;
+  double pre[kHid], hid[kHid];
+  mlp_forward(s.mlp, s.gemb + kEmbG * g, cam.iemb, pre, hid, out);
+  return true;
+}
+
 Proj<double> project_d(const SceneD& s, int64_t g, const CamD& cam, const OptsD& o) {
+  double m[kMlpOut];
+  const bool on = mlp_of(s, g, cam, m);
   return project<double>(s.means + 3 * g, s.scales + 3 * g, s.quats + 4 * g, s.opac[g],
-                         s.sh + g * s.K * 3, s.K, s.deg, cam, o);
+                         s.sh + g * s.K * 3, s.K, s.deg, cam, o, on ? m : nullptr);
 }
 
 // Minimum over the tile's in-image pixel centres of the Mahalanobis distance (p-mu)^T conic (p-mu).
@@ -681,9 +731,12 @@ bool valid_inputs(int64_t n, const double* means, const double* scales, const do
   return true;
 }
 
-std::vector<CamD> load_cams(int C, const double* cams, const double* affines) {
+std::vector<CamD> load_cams(int C, const double* cams, const double* affines, const double* iemb = nullptr) {
   std::vector<CamD> v;
-  for (int c = 0; c < C; ++c) v.push_back(load_cam(cams + 20 * c, affines ? affines + 12 * c : nullptr));
+  for (int c = 0; c < C; ++c) {
+    v.push_back(load_cam(cams + 20 * c, affines ? affines + 12 * c : nullptr));
+    v.back().iemb = iemb ? iemb + kEmbI * c : nullptr;
+  }
   return v;
 }
 
@@ -698,10 +751,11 @@ extern "C" {
 //               (rgb clamp r/g/b, Jacobian clamp x/y, zero compensation).
 int oracle_project(int64_t n, const double* means, const double* scales, const double* quats,
                    const double* opac, const double* sh, int K, int deg, const double* cam_row,
-                   const double* opts, double* out_rec, int32_t* out_flags) {
+                   const double* opts, double* out_rec, int32_t* out_flags, const double* gemb,
+                   const double* iemb, const double* mlp) {
   if (!valid_inputs(n, means, scales, quats, opac, sh, K, deg, 1, cam_row)) return -1;
-  SceneD s{n, means, scales, quats, opac, sh, K, deg};
-  std::vector<CamD> cams = load_cams(1, cam_row, nullptr);
+  SceneD s{n, means, scales, quats, opac, sh, K, deg, gemb, mlp};
+  std::vector<CamD> cams = load_cams(1, cam_row, nullptr, iemb);
   OptsD o = load_opts(opts);
   Binned B;
   bin_all(s, cams, o, &B);
@@ -742,10 +796,11 @@ int64_t oracle_render(int64_t n, const double* means, const double* scales, cons
                       const double* opac, const double* sh, int K, int deg, int C, const double* cams,
                       const double* affines, const double* opts, const int64_t* tile_subset,
                       int64_t n_subset, double* out_img, uint8_t* out_mark, uint64_t* out_sig,
-                      int64_t* out_pairs, int64_t pair_cap, uint8_t* out_gmark) {
+                      int64_t* out_pairs, int64_t pair_cap, uint8_t* out_gmark, const double* gemb,
+                      const double* iemb, const double* mlp) {
   if (!valid_inputs(n, means, scales, quats, opac, sh, K, deg, C, cams)) return -1;
-  SceneD s{n, means, scales, quats, opac, sh, K, deg};
-  std::vector<CamD> cv = load_cams(C, cams, affines);
+  SceneD s{n, means, scales, quats, opac, sh, K, deg, gemb, mlp};
+  std::vector<CamD> cv = load_cams(C, cams, affines, iemb);
   OptsD o = load_opts(opts);
   Binned B;
   bin_all(s, cv, o, &B);
@@ -810,10 +865,14 @@ int oracle_backward(int64_t n, const double* means, const double* scales, const 
                     const double* affines, const double* opts, const double* up_grads,
                     double* g_means, double* g_scales, double* g_quats, double* g_opac, double* g_sh,
                     double* g_affine, double* g_absgrad, double* g2d_out, const int64_t* tile_subset,
-                    int64_t n_subset, double* g_mag) {
+                    int64_t n_subset, double* g_mag, const double* gemb, const double* iemb, const double* mlp,
+                    double* g_gemb, double* g_iemb, double* g_mlp) {
   if (!valid_inputs(n, means, scales, quats, opac, sh, K, deg, C, cams)) return -1;
-  SceneD s{n, means, scales, quats, opac, sh, K, deg};
-  std::vector<CamD> cv = load_cams(C, cams, affines);
+  SceneD s{n, means, scales, quats, opac, sh, K, deg, gemb, mlp};
+  std::vector<CamD> cv = load_cams(C, cams, affines, iemb);
+  const bool mlp_on = gemb && iemb && mlp;
+  // per visible (camera, Gaussian): d(MLP output logits), for the serial weight reduction below
+  std::vector<double> mlp_dz(mlp_on ? static_cast<size_t>(C) * n * kMlpOut : 0, 0.0);
   OptsD o = load_opts(opts);
   Binned B;
   bin_all(s, cv, o, &B);
@@ -940,6 +999,8 @@ int oracle_backward(int64_t n, const double* means, const double* scales, const 
     double gsh[48];
     std::fill(gsh, gsh + 48, 0.0);
     double gabs[2] = {0, 0};
+    double gemb_acc[kEmbG];
+    std::fill(gemb_acc, gemb_acc + kEmbG, 0.0);
     double mag[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, mag_sh[48];
     std::fill(mag_sh, mag_sh + 48, 0.0);
     D11 m[3], sc[3], q[4], op;
@@ -950,7 +1011,9 @@ int oracle_backward(int64_t n, const double* means, const double* scales, const 
     for (int c = 0; c < C; ++c) {
       if (!B.proj[c * n + g].vis) continue;
       const double* gg = g2d.data() + (c * n + g) * G2;
-      Proj<D11> p = project<D11>(m, sc, q, op, sh + g * K * 3, K, deg, cv[c], o);
+      double mo[kMlpOut];
+      const bool on = mlp_of(s, g, cv[c], mo);
+      Proj<D11> p = project<D11>(m, sc, q, op, sh + g * K * 3, K, deg, cv[c], o, on ? mo : nullptr);
       if (!p.vis) continue;
       const D11* outs[10] = {&p.mx, &p.my, &p.ca, &p.cb, &p.cc, &p.op, &p.rgb[0], &p.rgb[1], &p.rgb[2], &p.z};
       double acc[11];
@@ -964,7 +1027,28 @@ int oracle_backward(int64_t n, const double* means, const double* scales, const 
       const int nb = (deg + 1) * (deg + 1);
       for (int ch = 0; ch < 3; ++ch) {
         if (p.flags & (1u << ch)) continue;  // rgb clamped at 0
-        for (int k = 0; k < nb && k < K; ++k) gsh[k * 3 + ch] += p.Y[k] * gg[6 + ch];
+        const double gain = on ? 2.0 * mo[ch] : 1.0;
+        for (int k = 0; k < nb && k < K; ++k) gsh[k * 3 + ch] += p.Y[k] * gain * gg[6 + ch];
+      }
+      if (on) {
+        // appearance transform: rgb = 2 out[0..2] rgb_pre, op' = (1 - out[3]) op_pre
+        double dz[kMlpOut];
+        for (int ch = 0; ch < 3; ++ch) dz[ch] = 2.0 * p.rgb_pre[ch] * gg[6 + ch];
+        dz[3] = -p.op_pre * gg[5];
+        for (int oo = 0; oo < kMlpOut; ++oo) dz[oo] *= mo[oo] * (1.0 - mo[oo]);  // through the sigmoid
+        for (int oo = 0; oo < kMlpOut; ++oo) mlp_dz[(static_cast<size_t>(c) * n + g) * kMlpOut + oo] = dz[oo];
+        if (g_gemb) {
+          double pre[kHid], hid[kHid], out4[kMlpOut];
+          mlp_forward(mlp, gemb + kEmbG * g, cv[c].iemb, pre, hid, out4);
+          const double* w1 = mlp;
+          const double* w2 = mlp + kHid * kMlpIn + kHid;
+          for (int k = 0; k < kHid; ++k) {
+            if (!(pre[k] > 0.0)) continue;
+            double dh = 0.0;
+            for (int oo = 0; oo < kMlpOut; ++oo) dh += w2[oo * kHid + k] * dz[oo];
+            for (int j = 0; j < kEmbG; ++j) gemb_acc[j] += w1[k * kMlpIn + j] * dh;
+          }
+        }
       }
       gabs[0] += gg[10];
       gabs[1] += gg[11];
@@ -985,11 +1069,47 @@ int oracle_backward(int64_t n, const double* means, const double* scales, const 
     g_opac[g] = go;
     for (int k = 0; k < K * 3; ++k) g_sh[g * K * 3 + k] = (k < 48) ? gsh[k] : 0.0;
     if (g_absgrad) { g_absgrad[2 * g] = gabs[0]; g_absgrad[2 * g + 1] = gabs[1]; }
+    if (g_gemb && mlp_on)
+      for (int j = 0; j < kEmbG; ++j) g_gemb[kEmbG * g + j] = gemb_acc[j];
     if (g_mag) {
       double* out = g_mag + static_cast<size_t>(g) * (11 + 3 * K);
       for (int k = 0; k < 11; ++k) out[k] = mag[k];
       for (int k = 0; k < K * 3; ++k) out[11 + k] = (k < 48) ? mag_sh[k] : 0.0;
     }
+  }
+  if (mlp_on && (g_mlp || g_iemb)) {
+    // weights and image embeddings: sums over every visible (camera, Gaussian)
+    std::vector<double> gw(kMlpParams, 0.0), gi(static_cast<size_t>(C) * kEmbI, 0.0);
+    const double* w1 = mlp;
+    const double* w2 = mlp + kHid * kMlpIn + kHid;
+    for (int c = 0; c < C; ++c)
+      for (int64_t g = 0; g < n; ++g) {
+        const double* dz = mlp_dz.data() + (static_cast<size_t>(c) * n + g) * kMlpOut;
+        if (dz[0] == 0.0 && dz[1] == 0.0 && dz[2] == 0.0 && dz[3] == 0.0) continue;
+        double pre[kHid], hid[kHid], out4[kMlpOut];
+        mlp_forward(mlp, gemb + kEmbG * g, cv[c].iemb, pre, hid, out4);
+        double* gw1 = gw.data();
+        double* gb1 = gw1 + kHid * kMlpIn;
+        double* gw2 = gb1 + kHid;
+        double* gb2 = gw2 + kMlpOut * kHid;
+        for (int oo = 0; oo < kMlpOut; ++oo) {
+          gb2[oo] += dz[oo];
+          for (int k = 0; k < kHid; ++k) gw2[oo * kHid + k] += dz[oo] * hid[k];
+        }
+        for (int k = 0; k < kHid; ++k) {
+          if (!(pre[k] > 0.0)) continue;
+          double dh = 0.0;
+          for (int oo = 0; oo < kMlpOut; ++oo) dh += w2[oo * kHid + k] * dz[oo];
+          gb1[k] += dh;
+          for (int j = 0; j < kEmbG; ++j) gw1[k * kMlpIn + j] += dh * gemb[kEmbG * g + j];
+          for (int j = 0; j < kEmbI; ++j) {
+            gw1[k * kMlpIn + kEmbG + j] += dh * cv[c].iemb[j];
+            gi[static_cast<size_t>(c) * kEmbI + j] += dh * w1[k * kMlpIn + kEmbG + j];
+          }
+        }
+      }
+    if (g_mlp) std::copy(gw.begin(), gw.end(), g_mlp);
+    if (g_iemb) std::copy(gi.begin(), gi.end(), g_iemb);
   }
   return 0;
 }

@@ -487,3 +487,92 @@ def test_gradient_magnitude_bounds_and_single_pixel_equality():
     r1 = oracle.backward(one, [cam1], up1, oracle.Opts(), want_mag=True)
     np.testing.assert_allclose(r1["mag"]["opacities"], np.abs(r1["opacities"]), rtol=1e-12)
     assert res.img.shape[0] == 64 * 64
+
+
+# --- appearance transform (Sec. 3.5.1) ---------------------------------------------------------------
+
+def random_mlp(rng, n, C, scale=0.3):
+    return dict(gemb=rng.normal(0, 1, (n, 16)), iemb=rng.normal(0, 1, (C, 32)),
+                w1=rng.normal(0, scale, (32, 48)), b1=rng.normal(0, scale, 32),
+                w2=rng.normal(0, scale, (4, 32)), b2=rng.normal(0, scale, 4))
+
+
+def test_appearance_transform_limits():
+    """A zero output layer gives sigmoid(0) = 1/2: colour gain 1 and opacity halved, i.e. the
+    plain render of the scene with halved opacities; a very negative opacity bias with zero
+    colour logits leaves the Gaussian unchanged."""
+    sc, cam = scenes.tiny_scene(3, 30, 32, 32, log_scale_mean=-1.8)
+    rng = np.random.default_rng(0)
+    mlp = random_mlp(rng, sc.n, 1)
+    mlp["w2"][:] = 0.0
+    mlp["b2"][:] = 0.0
+    opts = oracle.Opts(bg=(0.1, 0.2, 0.3))
+    half = scenes.Scene(sc.means, sc.scales, sc.quats, np.asarray(sc.opacities, np.float64) * 0.5, sc.sh, 3)
+    a = oracle.render(sc, [cam], opts, mlp=mlp, want_pairs=False).img
+    b = oracle.render(half, [cam], opts, want_pairs=False).img
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-12)
+    mlp["b2"][3] = -60.0  # opacity factor 1 - sigmoid(-60)
+    a = oracle.render(sc, [cam], opts, mlp=mlp, want_pairs=False).img
+    b = oracle.render(sc, [cam], opts, want_pairs=False).img
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-12)
+    assert b[:, 5].max() > 0.3
+
+
+@pytest.mark.parametrize("aa,cams", [(True, 1), (False, 2)])
+def test_appearance_transform_gradients_match_finite_differences(aa, cams):
+    """FP64 central differences of L = <w, outputs> over the whole render, for every kind of
+    appearance-transform input (Gaussian and image embeddings, both layers' weights and biases)
+    and for the geometric and SH parameters of a few Gaussians."""
+    sc, cam = scenes.tiny_scene(11, 20, 32, 32, log_scale_mean=-1.8)
+    cam_list = [cam] if cams == 1 else [cam, scenes.box_camera(24, 24, f=25.0)]
+    rng = np.random.default_rng(1)
+    mlp = random_mlp(rng, sc.n, cams)
+    opts = oracle.Opts(antialiased=aa, bg=(0.1, 0.2, 0.3))
+    npix = sum(c.width * c.height for c in cam_list)
+    w = rng.normal(size=(npix, 6))
+    g = oracle.backward(sc, cam_list, w, opts, mlp=mlp)
+
+    def loss(m, scene=sc):
+        r = oracle.render(scene, cam_list, opts, mlp=m, want_pairs=False, want_sig=True)
+        return float(np.sum(w * r.img[:, :6])), r.sig.copy()
+
+    L0, sig0 = loss(mlp)
+    checked = 0
+    for key, count in (("gemb", 10), ("iemb", 10), ("w1", 16), ("b1", 6), ("w2", 10), ("b2", 4)):
+        arr = mlp[key]
+        flat_idx = rng.choice(arr.size, size=min(count, arr.size), replace=False)
+        an_all = g["mlp"][key].reshape(-1)
+        for j in flat_idx:
+            h = 1e-6
+            vals = []
+            for sgn in (1, -1):
+                m2 = {k: v.copy() for k, v in mlp.items()}
+                m2[key].reshape(-1)[j] += sgn * h
+                L, sig = loss(m2)
+                assert np.array_equal(sig, sig0)
+                vals.append(L)
+            fd = (vals[0] - vals[1]) / (2 * h)
+            an = an_all[j]
+            scale = np.sqrt(np.mean(an_all ** 2)) + 1e-12
+            assert abs(fd - an) <= 2e-6 * (abs(an) + scale) + 1e-8, (key, j, fd, an)
+            checked += 1
+    assert checked >= 50
+    # the geometric and SH gradients through the transformed colour and opacity
+    params = {k: np.asarray(v, np.float64).copy() for k, v in
+              dict(means=sc.means, scales=sc.scales, quats=sc.quats, opacities=sc.opacities, sh=sc.sh).items()}
+    for gi in rng.choice(sc.n, size=4, replace=False):
+        for name in ("means", "opacities", "sh"):
+            flat = params[name].reshape(sc.n, -1)
+            for j in range(min(flat.shape[1], 3)):
+                vals = []
+                h = 1e-6
+                for sgn in (1, -1):
+                    p2 = {k: v.copy() for k, v in params.items()}
+                    p2[name].reshape(sc.n, -1)[gi, j] += sgn * h
+                    s2 = scenes.Scene(p2["means"], p2["scales"], p2["quats"], p2["opacities"], p2["sh"], 3)
+                    L, sig = loss(mlp, s2)
+                    vals.append(L)
+                fd = (vals[0] - vals[1]) / (2 * h)
+                an = g[name].reshape(sc.n, -1)[gi, j]
+                scale = np.sqrt(np.mean(g[name] ** 2)) + 1e-12
+                assert abs(fd - an) <= 1e-5 * (abs(an) + scale) + 1e-8, (name, gi, j, fd, an)
