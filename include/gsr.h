@@ -65,6 +65,20 @@ typedef struct gsr_segment {
   int64_t count; /* number of Gaussians */
 } gsr_segment;
 
+/* Per-Gaussian appearance transform (Sec. 3.5.1): each Gaussian has an embedding l_G (16) and
+ * each image an embedding l_I (32); one hidden layer of 32 with ReLU and an output layer of 4
+ * with a sigmoid (the sizes the paper gives) map [l_G ; l_I] to out. The paper says only that
+ * out adjusts the Gaussian's colour and opacity (and pulls the opacity part toward zero); read
+ * here as rgb' = 2 out[0..2] * rgb (the SH colour after its clamp; identity at 1/2) and
+ * opacity' = (1 - out[3]) * opacity (after the anti-aliasing compensation; identity at 0).
+ * All device memory, FP32, read-only; evaluated in FP32 per visible (Gaussian, camera). */
+typedef struct gsr_appearance_mlp {
+  const float* gauss_embed;  /* [n,16], indexed like the Gaussian arrays */
+  const float* image_embed;  /* [n_cams,32]: one per camera of the launch, in camera order */
+  const float* params;       /* [1700]: w1 [32][48] | b1 [32] | w2 [4][32] | b2 [4], row-major;
+                                hidden = ReLU(w1 [l_G ; l_I] + b1), out = sigmoid(w2 hidden + b2) */
+} gsr_appearance_mlp;
+
 /* Gaussians (Sec. 3.1, Eq. 1), structure of arrays, all device memory.
  * If segs != NULL only the listed segments are rendered, in list order (the order decides the
  * index used for depth ties); segs is HOST memory with nsegs entries. */
@@ -81,6 +95,7 @@ typedef struct gsr_gaussians {
   int32_t sh_dtype;       /* gsr_dtype of sh */
   const gsr_segment* segs;
   int32_t nsegs;
+  const gsr_appearance_mlp* mlp;  /* appearance transform (HOST struct, device arrays), or NULL */
 } gsr_gaussians;
 
 /* One pinhole camera (host memory). */
@@ -129,6 +144,10 @@ typedef struct gsr_param_grads {
   float* sh;          /* [n, sh_coeffs, 3] */
   float* appearance;  /* [C,3,4] (cameras without appearance get the gradient of the identity) */
   float* absgrad;     /* [n,2] sum over pixels and cameras of |dL/dmean2d_x|, |dL/dmean2d_y| */
+  /* appearance transform (required when g->mlp != NULL, ignored otherwise): */
+  float* gauss_embed; /* [n,16] */
+  float* image_embed; /* [C,32] */
+  float* mlp_params;  /* [1700], laid out like gsr_appearance_mlp.params */
 } gsr_param_grads;
 
 /* Optional device allocator (e.g. a framework's caching allocator). NULL: cudaMalloc/cudaFree. */

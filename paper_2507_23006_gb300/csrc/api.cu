@@ -249,6 +249,8 @@ gsr_status validate(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_camera* cams
   if (g->attr_dtype < 0 || g->attr_dtype > 2 || g->sh_dtype < 0 || g->sh_dtype > 2)
     return set_err(ctx, GSR_ERR_INVALID_ARG, "unknown dtype");
   if (g->nsegs < 0 || (g->nsegs > 0 && !g->segs)) return set_err(ctx, GSR_ERR_INVALID_ARG, "bad segment list");
+  if (g->mlp && (!g->mlp->image_embed || !g->mlp->params || (g->n > 0 && !g->mlp->gauss_embed)))
+    return set_err(ctx, GSR_ERR_INVALID_ARG, "null appearance-transform array");
   for (int s = 0; s < g->nsegs; ++s) {
     const gsr_segment& sg = g->segs[s];
     if (sg.begin < 0 || sg.count < 0 || sg.begin + sg.count > g->n)
@@ -356,6 +358,24 @@ cudaError_t start_prezero(gsr_ctx* ctx, cudaStream_t s) {
   return e;
 }
 
+// The per-Gaussian fields of GaussArgs (everything but the count and the segment map).
+void set_gauss_fields(const gsr_gaussians* g, GaussArgs& ga) {
+  ga.means = g->means;
+  ga.scales = g->scales;
+  ga.quats = g->quats;
+  ga.opac = g->opacities;
+  ga.sh = g->sh;
+  ga.K = g->sh_coeffs;
+  ga.deg = g->sh_degree;
+  ga.attr_dtype = g->attr_dtype;
+  ga.sh_dtype = g->sh_dtype;
+  ga.quat_vec4 = g->attr_dtype == GSR_F32 && (reinterpret_cast<uintptr_t>(g->quats) % 16 == 0);
+  ga.sh_vec4 = g->sh_dtype == GSR_F32 && (reinterpret_cast<uintptr_t>(g->sh) % 16 == 0) && ((3 * g->sh_coeffs) % 4 == 0);
+  ga.gemb = g->mlp ? g->mlp->gauss_embed : nullptr;
+  ga.iemb = g->mlp ? g->mlp->image_embed : nullptr;
+  ga.mlp = g->mlp ? g->mlp->params : nullptr;
+}
+
 gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb, const gsr_opts* o, BinOut bo,
                        long long* V_out, long long* P_out, cudaStream_t s) {
   const long long N = render_count(g);
@@ -390,17 +410,7 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
     ga.segs.begin = as<long long>(ctx->seg_begin);
     ga.segs.start = as<long long>(ctx->seg_start);
   }
-  ga.means = g->means;
-  ga.scales = g->scales;
-  ga.quats = g->quats;
-  ga.opac = g->opacities;
-  ga.sh = g->sh;
-  ga.K = g->sh_coeffs;
-  ga.deg = g->sh_degree;
-  ga.attr_dtype = g->attr_dtype;
-  ga.sh_dtype = g->sh_dtype;
-  ga.quat_vec4 = g->attr_dtype == GSR_F32 && (reinterpret_cast<uintptr_t>(g->quats) % 16 == 0);
-  ga.sh_vec4 = g->sh_dtype == GSR_F32 && (reinterpret_cast<uintptr_t>(g->sh) % 16 == 0) && ((3 * g->sh_coeffs) % 4 == 0);
+  set_gauss_fields(g, ga);
 
   const int pre_blocks = static_cast<int>((N + kPreTile - 1) / kPreTile);
   GSR_TRY_ALLOC(*bo.rec, sizeof(Rec) * capv);
@@ -746,6 +756,7 @@ FillSpans grad_spans(const gsr_gaussians* g, const gsr_param_grads* grads) {
   add(grads->opacities, n);
   add(grads->sh, 3 * static_cast<size_t>(g->sh_coeffs) * n);
   if (grads->absgrad) add(grads->absgrad, 2 * n);
+  if (g->mlp && grads->gauss_embed) add(grads->gauss_embed, static_cast<size_t>(kEmbG) * n);
   return f;
 }
 
@@ -785,6 +796,8 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
     return set_err(ctx, GSR_ERR_INVALID_ARG, "null state, upstream or gradient struct");
   if (g->n > 0 && (!grads->means || !grads->scales || !grads->quats || !grads->opacities || !grads->sh))
     return set_err(ctx, GSR_ERR_INVALID_ARG, "null parameter gradient array");
+  if (g->mlp && (!grads->image_embed || !grads->mlp_params || (g->n > 0 && !grads->gauss_embed)))
+    return set_err(ctx, GSR_ERR_INVALID_ARG, "null appearance-transform gradient array");
   const long long N = render_count(g);
   if (N != state->info.n_render || n_cams != state->info.n_cams)
     return set_err(ctx, GSR_ERR_INVALID_ARG, "inputs differ from the forward that made the state");
@@ -812,6 +825,8 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
   e = cudaMemsetAsync(ctx->g2d.p, 0, sizeof(Grad2D) * Vc, s);
   if (e == cudaSuccess && grads->appearance)
     e = cudaMemsetAsync(grads->appearance, 0, sizeof(float) * 12 * n_cams, s);
+  if (e == cudaSuccess && g->mlp) e = cudaMemsetAsync(grads->image_embed, 0, sizeof(float) * kEmbI * n_cams, s);
+  if (e == cudaSuccess && g->mlp) e = cudaMemsetAsync(grads->mlp_params, 0, sizeof(float) * kMlpParams, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
   // Every parameter-gradient row starts at zero; only rows of Gaussians with a record are then
   // written. The fill runs on the side stream (overlapping the blend backward), unless
@@ -869,17 +884,7 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
     ga.segs.begin = as<long long>(ctx->seg_begin);
     ga.segs.start = as<long long>(ctx->seg_start);
   }
-  ga.means = g->means;
-  ga.scales = g->scales;
-  ga.quats = g->quats;
-  ga.opac = g->opacities;
-  ga.sh = g->sh;
-  ga.K = g->sh_coeffs;
-  ga.deg = g->sh_degree;
-  ga.attr_dtype = g->attr_dtype;
-  ga.sh_dtype = g->sh_dtype;
-  ga.quat_vec4 = g->attr_dtype == GSR_F32 && (reinterpret_cast<uintptr_t>(g->quats) % 16 == 0);
-  ga.sh_vec4 = g->sh_dtype == GSR_F32 && (reinterpret_cast<uintptr_t>(g->sh) % 16 == 0) && ((3 * g->sh_coeffs) % 4 == 0);
+  set_gauss_fields(g, ga);
   ParamGrads pg;
   pg.means = grads->means;
   pg.scales = grads->scales;
@@ -891,6 +896,11 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
             ((3 * g->sh_coeffs) % 4 == 0);
   {
     StageTimer tm(ctx, GSR_STAGE_PREPROCESS_BWD, s);
+    // the appearance transform's backward turns the records' gradients into those of the
+    // transform's inputs before the projection backward reads them
+    if (g->mlp)
+      launch_mlp_bwd(ga, cb, V, as<Rec>(*bo.rec), as<uint32_t>(*bo.owner), as<Grad2D>(ctx->g2d),
+                     grads->gauss_embed, grads->image_embed, grads->mlp_params, 3 * (ctx->grid_cap / 2), s);
     launch_preprocess_bwd(ga, cb, opts->eps2d, opts->antialiased, V, as<Rec>(*bo.rec), as<uint32_t>(*bo.owner),
                           as<Grad2D>(ctx->g2d), pg, s);
   }

@@ -100,7 +100,19 @@ struct GaussArgs {
   int sh_dtype;
   int quat_vec4;       // float32 quaternions on a 16-byte boundary: load each as one float4
   int sh_vec4;         // float32 SH rows on 16-byte boundaries (3K % 4 == 0): load as float4
+  // appearance transform (gsr_appearance_mlp), all NULL when off
+  const float* gemb;   // [n][16]
+  const float* iemb;   // [C][32]
+  const float* mlp;    // [kMlpParams]
 };
+
+// Appearance transform sizes (the paper's): l_G 16, l_I 32, hidden 32, outputs 4.
+constexpr int kEmbG = 16, kEmbI = 32, kHid = 32, kMlpOut = 4;
+constexpr int kMlpIn = kEmbG + kEmbI;
+constexpr int kMlpB1 = kHid * kMlpIn;           // offset of b1 in the packed parameters
+constexpr int kMlpW2 = kMlpB1 + kHid;           // offset of w2
+constexpr int kMlpB2 = kMlpW2 + kMlpOut * kHid; // offset of b2
+constexpr int kMlpParams = kMlpB2 + kMlpOut;    // 1700
 
 struct PreOut {
   Rec* rec;                    // [cap_v]
@@ -135,7 +147,7 @@ struct ParamGrads {
 
 void launch_preprocess_fwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased,
                            const PreOut& out, int blocks, cudaStream_t s);
-constexpr int kFillSpans = 6;
+constexpr int kFillSpans = 8;
 struct FillSpans {
   float* ptr[kFillSpans];
   size_t len[kFillSpans];  // floats
@@ -143,6 +155,13 @@ struct FillSpans {
 };
 // Sets `count` float arrays to zero with `blocks` blocks of 128 threads.
 void launch_zero_fill(const FillSpans& f, int blocks, cudaStream_t s);
+// Backward of the appearance transform, one thread per visible record (before
+// launch_preprocess_bwd): turns the record's gradients of the transformed opacity and colour into
+// those of the untransformed ones (in place in g2d), adds l_G's gradient to g_gemb (atomics; rows
+// zeroed before) and sums the gradients of the weights and image embeddings into g_params and
+// g_iemb (atomics; zeroed before).
+void launch_mlp_bwd(const GaussArgs& g, const CamBatch& cams, long long V, const Rec* rec, const uint32_t* owner,
+                    Grad2D* g2d, float* g_gemb, float* g_iemb, float* g_params, int blocks, cudaStream_t s);
 // Runs over the V visible records; the first record of each Gaussian writes its gradient rows
 // (the rows of Gaussians with no record must already be zero).
 void launch_preprocess_bwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased, long long V,

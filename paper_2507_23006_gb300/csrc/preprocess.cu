@@ -366,6 +366,54 @@ __device__ __forceinline__ void write_record(const PreOut& out, long long v, con
   out.owner[v] = static_cast<uint32_t>(i);
 }
 
+// Appearance transform (Sec. 3.5.1) weights in shared memory: the Gaussian-embedding part of w1,
+// w2 and b2, and per camera of the launch u_c = w1[:, 16:48] l_I(c) + b1 (the image part of the
+// hidden layer is the same for every Gaussian seen by that camera).
+struct MlpSmem {
+  float w1g[kHid][kEmbG];
+  float w2[kMlpOut][kHid];
+  float b2[kMlpOut];
+  float u[kMaxCams][kHid];
+};
+
+// Fills M from the packed parameters and image embeddings (whole block; the caller syncs).
+__device__ void mlp_load_smem(const GaussArgs& A, int C, MlpSmem& M) {
+  for (int e = threadIdx.x; e < kHid * kEmbG; e += blockDim.x)
+    M.w1g[e / kEmbG][e % kEmbG] = __ldg(A.mlp + (e / kEmbG) * kMlpIn + e % kEmbG);
+  for (int e = threadIdx.x; e < kMlpOut * kHid; e += blockDim.x) M.w2[e / kHid][e % kHid] = __ldg(A.mlp + kMlpW2 + e);
+  for (int e = threadIdx.x; e < kMlpOut; e += blockDim.x) M.b2[e] = __ldg(A.mlp + kMlpB2 + e);
+  for (int e = threadIdx.x; e < C * kHid; e += blockDim.x) {
+    const int c = e / kHid, k = e % kHid;
+    float a = __ldg(A.mlp + kMlpB1 + k);
+    for (int j = 0; j < kEmbI; ++j) a = fmaf(__ldg(A.mlp + k * kMlpIn + kEmbG + j), __ldg(A.iemb + c * kEmbI + j), a);
+    M.u[c][k] = a;
+  }
+}
+
+__device__ __forceinline__ void load_gemb(const GaussArgs& A, long long g, float lg[kEmbG]) {
+#pragma unroll
+  for (int j = 0; j < kEmbG; ++j) lg[j] = __ldg(A.gemb + g * kEmbG + j);
+}
+
+// The transform's outputs for a Gaussian embedding seen by camera c: out = sigmoid(w2 ReLU(u_c +
+// w1_G l_G) + b2); 2 out[0..2] is the colour gain, 1 - out[3] the opacity factor.
+__device__ __forceinline__ void mlp_eval(const MlpSmem& M, const float lg[kEmbG], int c, float out[kMlpOut]) {
+  float z[kMlpOut];
+#pragma unroll
+  for (int o = 0; o < kMlpOut; ++o) z[o] = M.b2[o];
+#pragma unroll 4
+  for (int k = 0; k < kHid; ++k) {
+    float a = M.u[c][k];
+#pragma unroll
+    for (int j = 0; j < kEmbG; ++j) a = fmaf(M.w1g[k][j], lg[j], a);
+    const float h = fmaxf(a, 0.f);
+#pragma unroll
+    for (int o = 0; o < kMlpOut; ++o) z[o] = fmaf(M.w2[o][k], h, z[o]);
+  }
+#pragma unroll
+  for (int o = 0; o < kMlpOut; ++o) out[o] = 1.f / (1.f + __expf(-z[o]));
+}
+
 // Appends the slots of the lanes with `pred` to the block's list (order within the list is
 // arbitrary); one shared atomic per warp.
 __device__ __forceinline__ void list_append(bool pred, uint32_t slot, uint32_t* list, uint32_t* count, int lane) {
@@ -391,7 +439,8 @@ constexpr int kPreStage = 256;  // records a block keeps in shared memory betwee
 //   predecessors finish; then one warp takes the block's offset (decoupled look-back) and the
 //   staged records are written at their places, so the records are in (i, camera) order.
 //   Records beyond the stage's capacity are computed again in full after the offset is known.
-template <typename AT, typename ST>
+// kMlp: with the appearance transform (A.mlp and the embeddings are set).
+template <typename AT, typename ST, bool kMlp>
 __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArgs A, CamBatch cams, float eps, int aa,
                                                                        PreOut out) {
   __shared__ unsigned s_bid;
@@ -403,11 +452,13 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
   __shared__ uint32_t s_unstaged[kPreTile / 32];
   __shared__ float4 s_rec[kPreStage][4];
   __shared__ uint32_t s_meta[kPreStage];  // slot | camera << 16
+  __shared__ MlpSmem s_mlp;                // appearance transform, when on
   if (threadIdx.x == 0) {
     s_bid = atomicAdd(out.counter, 1u);
     s_count[0] = 0;
     s_count[1] = 0;
   }
+  if (kMlp) mlp_load_smem(A, cams.C, s_mlp);  // read after the barrier that ends phase 1a
   if (threadIdx.x < kPreTile / 32) s_unstaged[threadIdx.x] = 0;
   __syncthreads();
   const unsigned bid = s_bid;
@@ -441,15 +492,26 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
     const uint32_t maybe = s_aux[slot];
     Geo G;
     uint32_t vis = 0;
-    if (load_geo<AT>(A, seg_map(A.segs, base_i + slot), G)) {
+    const long long gi = seg_map(A.segs, base_i + slot);
+    if (load_geo<AT>(A, gi, G)) {
+      float lg[kEmbG];
+      if (kMlp) load_gemb(A, gi, lg);
       for (int c = 0; c < cams.C; ++c) {
         if (!(maybe & (1u << c))) continue;
         Proj P;
         if (!project(G, cams.cam[c], eps, aa, P)) continue;
         vis |= 1u << c;
+        float mo[kMlpOut] = {0.5f, 0.5f, 0.5f, 0.f};
+        if (kMlp) {
+          mlp_eval(s_mlp, lg, c, mo);
+          P.op *= 1.f - mo[3];  // before the record's alpha >= 1/255 box is taken from it
+        }
         const uint32_t e = atomicAdd(&s_count[1], 1u);
         if (e < kPreStage) {
-          const Rec rr = record_geometry(P, c, eps);
+          Rec rr = record_geometry(P, c, eps);
+          rr.b.w = 2.f * mo[0];  // colour gains until the colour is evaluated
+          rr.c.x = 2.f * mo[1];
+          rr.c.y = 2.f * mo[2];
           s_rec[e][0] = rr.a;
           s_rec[e][1] = rr.b;
           s_rec[e][2] = rr.c;
@@ -493,9 +555,9 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
     float rgb[3], dir[3], dn, Y[16];
     bool cl[3];
     eval_color<ST>(A, g, G, cams.cam[meta >> 16], rgb, dir, dn, Y, cl);
-    s_rec[e][1].w = rgb[0];
-    s_rec[e][2].x = rgb[1];
-    s_rec[e][2].y = rgb[2];
+    s_rec[e][1].w *= rgb[0];  // times the colour gain (1 without the appearance transform)
+    s_rec[e][2].x *= rgb[1];
+    s_rec[e][2].y *= rgb[2];
   }
   if (threadIdx.x < 32) {
     const unsigned long long ex = warp_lookback(out.status, bid, total, out.epoch, out.err);
@@ -526,19 +588,26 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
     const long long g = seg_map(A.segs, i);
     Geo G;
     load_geo<AT>(A, g, G);
+    float lg[kEmbG];
+    if (kMlp) load_gemb(A, g, lg);
     long long v = block_base + s_aux[slot];
     for (int c = 0; c < cams.C; ++c) {
       if (!(vis & (1u << c))) continue;
       const DevCam& cam = cams.cam[c];
       Proj P;
       project(G, cam, eps, aa, P);
+      float mo[kMlpOut] = {0.5f, 0.5f, 0.5f, 0.f};
+      if (kMlp) {
+        mlp_eval(s_mlp, lg, c, mo);
+        P.op *= 1.f - mo[3];
+      }
       float rgb[3], dir[3], dn, Y[16];
       bool cl[3];
       eval_color<ST>(A, g, G, cam, rgb, dir, dn, Y, cl);
       Rec rr = record_geometry(P, c, eps);
-      rr.b.w = rgb[0];
-      rr.c.x = rgb[1];
-      rr.c.y = rgb[2];
+      rr.b.w = 2.f * mo[0] * rgb[0];
+      rr.c.x = 2.f * mo[1] * rgb[1];
+      rr.c.y = 2.f * mo[2] * rgb[2];
       write_record(out, v, rr, i);
       ++v;
     }
@@ -713,10 +782,181 @@ __global__ void __launch_bounds__(kBwdThreads) preprocess_bwd_kernel(
   }
 }
 
+// Backward of the appearance transform, one thread per visible record, blocks looping over
+// chunks of kBwdThreads records. With out = sigmoid(z): rgb' = 2 out[0..2] rgb and
+// op' = (1 - out[3]) op, so dz_c = rgb'_c d rgb'_c (1 - out_c) and dz_3 = -op' d op' out_3 (no
+// division by the outputs); the record's gradients are replaced by those of rgb and op
+// (d rgb = 2 out d rgb', d op = (1 - out[3]) d op'), which the projection backward then uses.
+// The weight gradients are sums of outer products over the records: each chunk's embeddings,
+// hidden activations and pre-activation gradients are staged in shared memory and summed there
+// by register tiles; the image part of w1, b1 and the image embeddings depend on a record only
+// through its camera, so they are formed once per block from per-camera sums of the
+// pre-activation gradients. Each block adds its totals with one atomic per parameter.
+struct MlpBwdSmem {
+  MlpSmem M;
+  float lg[kBwdThreads][20];           // l_G per record (rows padded to 80 B: conflict-free float4)
+  float hid[kBwdThreads][kHid + 1];    // ReLU outputs
+  float dpre[kBwdThreads][kHid + 1];   // gradients of the hidden pre-activations
+  float4 dz[kBwdThreads];              // gradients of the output pre-activations
+  int cam[kBwdThreads];
+  float sum[kMaxCams][kHid];           // per camera: sum of dpre over the block's records
+};
+
+__global__ void __launch_bounds__(kBwdThreads) mlp_bwd_kernel(GaussArgs A, CamBatch cams, long long V,
+                                                              const Rec* __restrict__ rec,
+                                                              const uint32_t* __restrict__ owner, Grad2D* g2d,
+                                                              float* __restrict__ g_gemb, float* __restrict__ g_iemb,
+                                                              float* __restrict__ g_params) {
+  constexpr int R = kBwdThreads;
+  static_assert(R == 128 && kHid == 32 && kEmbG == 16 && kMlpOut == 4, "register tiles assume these sizes");
+  extern __shared__ __align__(16) unsigned char mlp_bwd_raw[];
+  MlpBwdSmem& S = *reinterpret_cast<MlpBwdSmem*>(mlp_bwd_raw);
+  const int t = threadIdx.x;
+  mlp_load_smem(A, cams.C, S.M);
+  for (int e = t; e < kMaxCams * kHid; e += R) (&S.sum[0][0])[e] = 0.f;
+  // register tiles: w1_G[k1][j1..j1+3]; w2[0..3][k2] and b2 over the records of quarter q2;
+  // the per-camera sums of dpre[k2] over the same quarter
+  const int k1 = t >> 2, j1 = (t & 3) * 4;
+  const int k2 = t & 31, q2 = t >> 5;
+  float a1[4] = {0.f, 0.f, 0.f, 0.f}, a2[4] = {0.f, 0.f, 0.f, 0.f}, ab2[4] = {0.f, 0.f, 0.f, 0.f};
+  float cam_acc = 0.f;
+  int cam_cur = -1;
+  __syncthreads();
+  for (long long base = static_cast<long long>(blockIdx.x) * R; base < V; base += static_cast<long long>(gridDim.x) * R) {
+    const long long v = base + t;
+    int c = -1;
+    float lg[kEmbG];
+#pragma unroll
+    for (int j = 0; j < kEmbG; ++j) lg[j] = 0.f;
+    float dz[kMlpOut] = {0.f, 0.f, 0.f, 0.f};
+    if (v < V) {
+      const Rec r = rec[v];
+      c = rec_cam(r);
+      const long long g = seg_map(A.segs, owner[v]);
+      load_gemb(A, g, lg);
+      float z[kMlpOut];
+#pragma unroll
+      for (int o = 0; o < kMlpOut; ++o) z[o] = S.M.b2[o];
+      uint32_t on = 0;  // ReLU active
+#pragma unroll 4
+      for (int k = 0; k < kHid; ++k) {
+        float a = S.M.u[c][k];
+#pragma unroll
+        for (int j = 0; j < kEmbG; ++j) a = fmaf(S.M.w1g[k][j], lg[j], a);
+        const float h = fmaxf(a, 0.f);
+        on |= (a > 0.f ? 1u : 0u) << k;
+        S.hid[t][k] = h;
+#pragma unroll
+        for (int o = 0; o < kMlpOut; ++o) z[o] = fmaf(S.M.w2[o][k], h, z[o]);
+      }
+      float out[kMlpOut];
+#pragma unroll
+      for (int o = 0; o < kMlpOut; ++o) out[o] = 1.f / (1.f + __expf(-z[o]));
+      Grad2D gd = g2d[v];
+      const float rgbp[3] = {r.b.w, r.c.x, r.c.y};
+      const float drgbp[3] = {gd.b.w, gd.c.x, gd.c.y};
+      const float dopp = gd.a.z;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) dz[ch] = rgbp[ch] * drgbp[ch] * (1.f - out[ch]);
+      dz[3] = -r.a.z * dopp * out[3];
+      gd.a.z = dopp * (1.f - out[3]);
+      gd.b.w = 2.f * out[0] * drgbp[0];
+      gd.c.x = 2.f * out[1] * drgbp[1];
+      gd.c.y = 2.f * out[2] * drgbp[2];
+      g2d[v] = gd;
+      float dlg[kEmbG];
+#pragma unroll
+      for (int j = 0; j < kEmbG; ++j) dlg[j] = 0.f;
+#pragma unroll 4
+      for (int k = 0; k < kHid; ++k) {
+        float dh = 0.f;
+#pragma unroll
+        for (int o = 0; o < kMlpOut; ++o) dh = fmaf(S.M.w2[o][k], dz[o], dh);
+        const float dp = (on >> k) & 1u ? dh : 0.f;
+        S.dpre[t][k] = dp;
+#pragma unroll
+        for (int j = 0; j < kEmbG; ++j) dlg[j] = fmaf(S.M.w1g[k][j], dp, dlg[j]);
+      }
+      float* dst = g_gemb + g * kEmbG;
+#pragma unroll
+      for (int j = 0; j < kEmbG; ++j) atomicAdd(dst + j, dlg[j]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kHid; ++k) S.hid[t][k] = S.dpre[t][k] = 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < kEmbG; j += 4)
+      *reinterpret_cast<float4*>(&S.lg[t][j]) = make_float4(lg[j], lg[j + 1], lg[j + 2], lg[j + 3]);
+    S.dz[t] = make_float4(dz[0], dz[1], dz[2], dz[3]);
+    S.cam[t] = c;
+    __syncthreads();
+    for (int u = 0; u < R; ++u) {
+      const float dp = S.dpre[u][k1];
+      const float4 l = *reinterpret_cast<const float4*>(&S.lg[u][j1]);
+      a1[0] = fmaf(dp, l.x, a1[0]);
+      a1[1] = fmaf(dp, l.y, a1[1]);
+      a1[2] = fmaf(dp, l.z, a1[2]);
+      a1[3] = fmaf(dp, l.w, a1[3]);
+    }
+    for (int u = q2 * 32; u < q2 * 32 + 32; ++u) {
+      const float h = S.hid[u][k2];
+      const float4 d = S.dz[u];
+      a2[0] = fmaf(d.x, h, a2[0]);
+      a2[1] = fmaf(d.y, h, a2[1]);
+      a2[2] = fmaf(d.z, h, a2[2]);
+      a2[3] = fmaf(d.w, h, a2[3]);
+      ab2[0] += d.x;
+      ab2[1] += d.y;
+      ab2[2] += d.z;
+      ab2[3] += d.w;
+      const int cu = S.cam[u];  // the same for the whole warp
+      if (cu != cam_cur) {
+        if (cam_cur >= 0) atomicAdd(&S.sum[cam_cur][k2], cam_acc);
+        cam_cur = cu;
+        cam_acc = 0.f;
+      }
+      cam_acc += S.dpre[u][k2];
+    }
+    __syncthreads();
+  }
+  if (cam_cur >= 0) atomicAdd(&S.sum[cam_cur][k2], cam_acc);
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (a1[q] != 0.f) atomicAdd(g_params + k1 * kMlpIn + j1 + q, a1[q]);
+#pragma unroll
+  for (int o = 0; o < kMlpOut; ++o) {
+    if (a2[o] != 0.f) atomicAdd(g_params + kMlpW2 + o * kHid + k2, a2[o]);
+    if (k2 == 0 && ab2[o] != 0.f) atomicAdd(g_params + kMlpB2 + o, ab2[o]);
+  }
+  __syncthreads();
+  // image part of w1 and b1: sums over the cameras of sum[c][k] l_I(c)[j] and sum[c][k]
+  for (int e = t; e < kHid * (kEmbI + 1); e += R) {
+    const int k = e / (kEmbI + 1), j = e % (kEmbI + 1);
+    float a = 0.f;
+    if (j < kEmbI) {
+      for (int c = 0; c < cams.C; ++c) a = fmaf(S.sum[c][k], __ldg(A.iemb + c * kEmbI + j), a);
+      if (a != 0.f) atomicAdd(g_params + k * kMlpIn + kEmbG + j, a);
+    } else {
+      for (int c = 0; c < cams.C; ++c) a += S.sum[c][k];
+      if (a != 0.f) atomicAdd(g_params + kMlpB1 + k, a);
+    }
+  }
+  // image embeddings: d l_I(c) = w1_I^T sum[c]
+  for (int e = t; e < cams.C * kEmbI; e += R) {
+    const int c = e / kEmbI, j = e % kEmbI;
+    float a = 0.f;
+    for (int k = 0; k < kHid; ++k) a = fmaf(__ldg(A.mlp + k * kMlpIn + kEmbG + j), S.sum[c][k], a);
+    if (a != 0.f) atomicAdd(g_iemb + e, a);
+  }
+}
+
 template <typename AT, typename ST>
 void launch_fwd_t(const GaussArgs& g, const CamBatch& cams, float eps, int aa, const PreOut& out, int blocks,
                   cudaStream_t s) {
-  preprocess_fwd_kernel<AT, ST><<<blocks, kPreThreads, 0, s>>>(g, cams, eps, aa, out);
+  if (g.mlp)
+    preprocess_fwd_kernel<AT, ST, true><<<blocks, kPreThreads, 0, s>>>(g, cams, eps, aa, out);
+  else
+    preprocess_fwd_kernel<AT, ST, false><<<blocks, kPreThreads, 0, s>>>(g, cams, eps, aa, out);
 }
 
 template <typename AT, typename ST>
@@ -768,6 +1008,23 @@ __global__ void __launch_bounds__(128) zero_fill_kernel(FillSpans f) {
 void launch_zero_fill(const FillSpans& f, int blocks, cudaStream_t s) {
   if (f.count <= 0 || blocks <= 0) return;
   zero_fill_kernel<<<blocks, 128, 0, s>>>(f);
+}
+
+void launch_mlp_bwd(const GaussArgs& g, const CamBatch& cams, long long V, const Rec* rec, const uint32_t* owner,
+                    Grad2D* g2d, float* g_gemb, float* g_iemb, float* g_params, int blocks, cudaStream_t s) {
+  if (V <= 0 || !g.mlp) return;
+  static uint64_t attr_set = 0;  // one bit per device: the attribute is set in each device's context
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 64 || !((attr_set >> dev) & 1u)) {
+    cudaFuncSetAttribute(mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(sizeof(MlpBwdSmem)));
+    if (dev < 64) attr_set |= 1ull << dev;
+  }
+  const long long need = (V + kBwdThreads - 1) / kBwdThreads;
+  const int grid = static_cast<int>(need < blocks ? need : blocks);
+  mlp_bwd_kernel<<<grid, kBwdThreads, sizeof(MlpBwdSmem), s>>>(g, cams, V, rec, owner, g2d, g_gemb, g_iemb,
+                                                               g_params);
 }
 
 void launch_preprocess_bwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased, long long V,

@@ -55,11 +55,16 @@ class Segment(ctypes.Structure):
     _fields_ = [("begin", ctypes.c_int64), ("count", ctypes.c_int64)]
 
 
+class CAppearanceMLP(ctypes.Structure):
+    _fields_ = [("gauss_embed", ctypes.c_void_p), ("image_embed", ctypes.c_void_p), ("params", ctypes.c_void_p)]
+
+
 class CGaussians(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("means", ctypes.c_void_p), ("scales", ctypes.c_void_p),
                 ("quats", ctypes.c_void_p), ("opacities", ctypes.c_void_p), ("sh", ctypes.c_void_p),
                 ("sh_coeffs", ctypes.c_int32), ("sh_degree", ctypes.c_int32), ("attr_dtype", ctypes.c_int32),
-                ("sh_dtype", ctypes.c_int32), ("segs", ctypes.POINTER(Segment)), ("nsegs", ctypes.c_int32)]
+                ("sh_dtype", ctypes.c_int32), ("segs", ctypes.POINTER(Segment)), ("nsegs", ctypes.c_int32),
+                ("mlp", ctypes.POINTER(CAppearanceMLP))]
 
 
 class CCamera(ctypes.Structure):
@@ -87,7 +92,8 @@ class COutGrads(ctypes.Structure):
 class CParamGrads(ctypes.Structure):
     _fields_ = [("means", ctypes.c_void_p), ("scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
                 ("opacities", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("appearance", ctypes.c_void_p),
-                ("absgrad", ctypes.c_void_p)]
+                ("absgrad", ctypes.c_void_p), ("gauss_embed", ctypes.c_void_p), ("image_embed", ctypes.c_void_p),
+                ("mlp_params", ctypes.c_void_p)]
 
 
 class CStateInfo(ctypes.Structure):
@@ -170,6 +176,38 @@ def _ptr(t: Optional[torch.Tensor]):
     return t.data_ptr()
 
 
+MLP_PARAMS = 32 * 48 + 32 + 4 * 32 + 4
+
+
+@dataclasses.dataclass
+class AppearanceMLP:
+    """Per-Gaussian appearance transform (Sec. 3.5.1), FP32 device tensors: Gaussian embeddings,
+    one image embedding per camera of a launch (in camera order) and the packed weights
+    w1 [32,48] | b1 [32] | w2 [4,32] | b2 [4]."""
+    gauss_embed: torch.Tensor  # [n,16]
+    image_embed: torch.Tensor  # [n_cams,32]
+    params: torch.Tensor       # [1700]
+
+    @staticmethod
+    def from_arrays(d: dict, device="cuda") -> "AppearanceMLP":
+        """From dict(gemb, iemb, w1, b1, w2, b2) of arrays (the layout scenes.appearance_mlp draws)."""
+        def t(a):
+            return torch.as_tensor(np.ascontiguousarray(a, np.float32)).to(device).contiguous()
+        params = np.concatenate([np.asarray(d[k], np.float32).reshape(-1) for k in ("w1", "b1", "w2", "b2")])
+        return AppearanceMLP(t(d["gemb"]), t(d["iemb"]), t(params))
+
+    def c_struct(self, n: int) -> CAppearanceMLP:
+        for name, a, shape in (("gauss_embed", self.gauss_embed, (n, 16)), ("params", self.params, (MLP_PARAMS,))):
+            if tuple(a.shape) != shape:
+                raise ValueError(f"{name} must have shape {shape}")
+        if self.image_embed.dim() != 2 or self.image_embed.shape[1] != 32:
+            raise ValueError("image_embed must have shape [n_cams, 32]")
+        for a in (self.gauss_embed, self.image_embed, self.params):
+            if a.dtype != torch.float32 or not a.is_contiguous():
+                raise ValueError("appearance-transform tensors must be contiguous float32")
+        return CAppearanceMLP(_ptr(self.gauss_embed), _ptr(self.image_embed), _ptr(self.params))
+
+
 @dataclasses.dataclass
 class Gaussians:
     """Device-resident Gaussians (structure of arrays)."""
@@ -180,6 +218,7 @@ class Gaussians:
     sh: torch.Tensor          # [n,K,3] sh dtype
     sh_degree: int = 3
     segments: Optional[Sequence[tuple]] = None
+    mlp: Optional[AppearanceMLP] = None
 
     @property
     def n(self) -> int:
@@ -200,16 +239,22 @@ class Gaussians:
                 seg_arr[k].begin = int(b)
                 seg_arr[k].count = int(c)
         n = self.n
+        cmlp = self.mlp.c_struct(n) if self.mlp is not None else None
         g = CGaussians(n, _ptr(self.means), _ptr(self.scales), _ptr(self.quats), _ptr(self.opacities),
                        _ptr(self.sh), int(self.sh.shape[1]) if self.sh.dim() == 3 else 1, int(self.sh_degree),
                        DTYPES[self.scales.dtype], DTYPES[self.sh.dtype],
                        ctypes.cast(seg_arr, ctypes.POINTER(Segment)) if seg_arr is not None else None,
-                       len(self.segments) if self.segments is not None else 0)
+                       len(self.segments) if self.segments is not None else 0,
+                       ctypes.pointer(cmlp) if cmlp is not None else None)
         if self.means.dtype != torch.float32:
             raise ValueError("means must be float32")
         if not (self.scales.dtype == self.quats.dtype == self.opacities.dtype):
             raise ValueError("scales, quats and opacities must share one dtype")
-        return g, seg_arr
+        return g, (seg_arr, cmlp)
+
+    def check_cameras(self, n_cams: int):
+        if self.mlp is not None and self.mlp.image_embed.shape[0] != n_cams:
+            raise ValueError(f"image_embed has {self.mlp.image_embed.shape[0]} rows for {n_cams} cameras")
 
     def render_count(self) -> int:
         if self.segments is None:
@@ -372,6 +417,7 @@ def render_forward(ctx: Context, g: Gaussians, cams, opts: Options = None, appea
     if outputs is None:
         outputs = dict(rgb=torch.empty((npix, 3), device=dev), depth_acc=torch.empty(npix, device=dev),
                        depth_exp=torch.empty(npix, device=dev), alpha=torch.empty(npix, device=dev))
+    g.check_cameras(len(cams))
     cg, seg_keep = g.c_struct()
     carr = c_cameras(cams, appearances)
     co = opts.c_struct()
@@ -390,15 +436,20 @@ def param_grads(ctx: Context, g: Gaussians, n_cams: int, absgrad: bool = False) 
     dev = f"cuda:{ctx.device}"
     n = g.n
     K = int(g.sh.shape[1])
-    return dict(means=torch.empty((n, 3), device=dev), scales=torch.empty((n, 3), device=dev),
-                quats=torch.empty((n, 4), device=dev), opacities=torch.empty(n, device=dev),
-                sh=torch.empty((n, K, 3), device=dev), appearance=torch.empty((n_cams, 3, 4), device=dev),
-                absgrad=torch.empty((n, 2), device=dev) if absgrad else None)
+    out = dict(means=torch.empty((n, 3), device=dev), scales=torch.empty((n, 3), device=dev),
+               quats=torch.empty((n, 4), device=dev), opacities=torch.empty(n, device=dev),
+               sh=torch.empty((n, K, 3), device=dev), appearance=torch.empty((n_cams, 3, 4), device=dev),
+               absgrad=torch.empty((n, 2), device=dev) if absgrad else None)
+    if g.mlp is not None:
+        out.update(gauss_embed=torch.empty((n, 16), device=dev), image_embed=torch.empty((n_cams, 32), device=dev),
+                   mlp_params=torch.empty(MLP_PARAMS, device=dev))
+    return out
 
 
 def _c_param_grads(grads: dict):
     return CParamGrads(_ptr(grads["means"]), _ptr(grads["scales"]), _ptr(grads["quats"]), _ptr(grads["opacities"]),
-                       _ptr(grads["sh"]), _ptr(grads.get("appearance")), _ptr(grads.get("absgrad")))
+                       _ptr(grads["sh"]), _ptr(grads.get("appearance")), _ptr(grads.get("absgrad")),
+                       _ptr(grads.get("gauss_embed")), _ptr(grads.get("image_embed")), _ptr(grads.get("mlp_params")))
 
 
 def zero_param_grads(ctx: Context, g: Gaussians, grads: dict, stream=None):
@@ -416,6 +467,7 @@ def render_backward(ctx: Context, g: Gaussians, cams, state: State, d_out: dict,
     opts = opts or Options()
     if grads is None:
         grads = param_grads(ctx, g, len(cams), opts.absgrad)
+    g.check_cameras(len(cams))
     cg, seg_keep = g.c_struct()
     carr = c_cameras(cams, appearances)
     co = opts.c_struct()

@@ -118,6 +118,15 @@ def random_attributes(rng: np.random.Generator, n: int, log_scale_mean=-2.5, log
     return scales, quats, opac, sh
 
 
+def appearance_mlp(rng: np.random.Generator, n: int, n_cams: int, scale: float = 0.3) -> dict:
+    """Random inputs of the per-Gaussian appearance transform (Sec. 3.5.1): Gaussian embeddings
+    [n,16] and image embeddings [n_cams,32] ~ N(0,1); w1 [32,48], b1 [32], w2 [4,32], b2 [4] ~
+    N(0, scale). The draws only, in that order."""
+    return dict(gemb=rng.normal(0, 1, (n, 16)), iemb=rng.normal(0, 1, (n_cams, 32)),
+                w1=rng.normal(0, scale, (32, 48)), b1=rng.normal(0, scale, 32),
+                w2=rng.normal(0, scale, (4, 32)), b2=rng.normal(0, scale, 4))
+
+
 def box_scene(seed: int = 0, n: int = 10_000) -> Scene:
     """Means uniform in x,y in [-5,5], z in [5,15] in front of an identity camera."""
     rng = np.random.default_rng(seed)

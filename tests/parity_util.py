@@ -98,5 +98,12 @@ def camera_list(cams):
     return list(cams) if isinstance(cams, (list, tuple)) else [cams]
 
 
+def mlp_for_camera(mlp, c):
+    """The appearance-transform inputs as one camera sees them (its own image embedding)."""
+    if mlp is None:
+        return None
+    return dict(mlp, iemb=np.asarray(mlp["iemb"])[c:c + 1])
+
+
 def scene_box(n=10_000, seed=0):
     return scenes.box_scene(seed, n), scenes.box_camera()

@@ -49,12 +49,12 @@ def test_sort_matches_stable_numpy(ctx, n, bits):
 
 # ---- forward ------------------------------------------------------------------------------------
 
-def _check_records(sa, scene, cams, oopts, gmark):
+def _check_records(sa, scene, cams, oopts, gmark, mlp=None):
     n = scene.n
     rec = sa["rec"]
     x0, x1, y0, y1, cam_bits = pu.unpack_rect(rec)
     for c, cam in enumerate(cams):
-        ref, flags = oracle.project(scene, cam, oopts)
+        ref, flags = oracle.project(scene, cam, oopts, mlp=pu.mlp_for_camera(mlp, c))
         sel = sa["cam_of"] == c
         g = sa["g_of"][sel]
         vis_gpu = np.zeros(n, bool)
@@ -253,6 +253,7 @@ def _upstream(res, npix, seed, alpha_min=0.05):
 
 
 def _gpu_backward(ctx, g, cams, st, up, nopts, appearances=None):
+    """Parameter gradients of L = <up, outputs> through render_backward, on the host."""
     dev = "cuda"
     d = dict(rgb=torch.tensor(up[:, 0:3], dtype=torch.float32, device=dev).contiguous(),
              depth_acc=torch.tensor(up[:, 3], dtype=torch.float32, device=dev).contiguous(),

@@ -491,19 +491,13 @@ def test_gradient_magnitude_bounds_and_single_pixel_equality():
 
 # --- appearance transform (Sec. 3.5.1) ---------------------------------------------------------------
 
-def random_mlp(rng, n, C, scale=0.3):
-    return dict(gemb=rng.normal(0, 1, (n, 16)), iemb=rng.normal(0, 1, (C, 32)),
-                w1=rng.normal(0, scale, (32, 48)), b1=rng.normal(0, scale, 32),
-                w2=rng.normal(0, scale, (4, 32)), b2=rng.normal(0, scale, 4))
-
-
 def test_appearance_transform_limits():
     """A zero output layer gives sigmoid(0) = 1/2: colour gain 1 and opacity halved, i.e. the
     plain render of the scene with halved opacities; a very negative opacity bias with zero
     colour logits leaves the Gaussian unchanged."""
     sc, cam = scenes.tiny_scene(3, 30, 32, 32, log_scale_mean=-1.8)
     rng = np.random.default_rng(0)
-    mlp = random_mlp(rng, sc.n, 1)
+    mlp = scenes.appearance_mlp(rng, sc.n, 1)
     mlp["w2"][:] = 0.0
     mlp["b2"][:] = 0.0
     opts = oracle.Opts(bg=(0.1, 0.2, 0.3))
@@ -526,7 +520,7 @@ def test_appearance_transform_gradients_match_finite_differences(aa, cams):
     sc, cam = scenes.tiny_scene(11, 20, 32, 32, log_scale_mean=-1.8)
     cam_list = [cam] if cams == 1 else [cam, scenes.box_camera(24, 24, f=25.0)]
     rng = np.random.default_rng(1)
-    mlp = random_mlp(rng, sc.n, cams)
+    mlp = scenes.appearance_mlp(rng, sc.n, cams)
     opts = oracle.Opts(antialiased=aa, bg=(0.1, 0.2, 0.3))
     npix = sum(c.width * c.height for c in cam_list)
     w = rng.normal(size=(npix, 6))
