@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp16", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-mlp", action="store_true")
     p.add_argument("--serve-rate", type=float, default=200.0)
     p.add_argument("--serve-seconds", type=float, default=2.0)
     p.add_argument("--serve-full", action="store_true",
@@ -256,6 +257,68 @@ def run_reference(args, rank, world):
     return 0
 
 
+# FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# algorithmic flops per visible record of the appearance-transform backward (an FMA is 2):
+# recompute 2 (16*32 + 32*4), back through both layers to l_G 2 (4*32 + 32*16), weight-gradient
+# outer products of w1's Gaussian part and w2 2 (32*16 + 4*32), bias sums 32 + 4
+MLP_BWD_FLOPS_PER_RECORD = 2 * (16 * 32 + 32 * 4) * 3 + 36
+
+
+def run_mlp_leg(args, ctx, g, cam, opts, d_out, outs, stream, dev, rank):
+    """The training step with the per-Gaussian appearance transform (Sec. 3.5.1) on: random
+    embeddings and weights, the same Gaussians and camera. Reports the step time, the stages the
+    transform touches and the roofline of its backward kernel (ALU-bound, FP32)."""
+    import torch
+    from paper_2507_23006_gb300 import native
+
+    gen = torch.Generator(device=dev).manual_seed(4321 + rank)
+    mlp = native.AppearanceMLP(torch.randn((g.n, 16), device=dev, generator=gen),
+                               torch.randn((1, 32), device=dev, generator=gen),
+                               0.3 * torch.randn(native.MLP_PARAMS, device=dev, generator=gen))
+    gm = native.Gaussians(g.means, g.scales, g.quats, g.opacities, g.sh, 3, None, mlp)
+    grads = native.param_grads(ctx, gm, 1)
+    out_m = {k: torch.empty_like(v) for k, v in outs.items()}
+
+    def step():
+        native.zero_param_grads(ctx, gm, grads)
+        _, st = native.render_forward(ctx, gm, [cam], opts, outputs=out_m)
+        native.render_backward(ctx, gm, [cam], st, d_out, opts, grads=grads)
+        return st
+
+    for _ in range(3):
+        st = step()
+    torch.cuda.synchronize()
+    V = st.info()["n_visible"]
+    del st
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st = step()
+        del st
+    e1.record(stream)
+    torch.cuda.synchronize()
+    # stage times from a second, profiled pass (events around the three stages only)
+    stages = ["preprocess", "appearance_bwd", "preprocess_bwd"]
+    ctx.profile(True, False, stages=stages)
+    ctx.profile_collect()
+    for _ in range(args.steps):
+        st = step()
+        del st
+    torch.cuda.synchronize()
+    prof = ctx.profile_collect()
+    ctx.profile(False, False)
+    stage_ms = {k: prof["ms"][k] / max(prof["launches"][k], 1) for k in stages}
+    achieved = MLP_BWD_FLOPS_PER_RECORD * V / (stage_ms["appearance_bwd"] * 1e-3) / 1e12
+    return dict(ms_per_step=e0.elapsed_time(e1) / args.steps, n_visible=V,
+                stage_ms={k: round(v, 4) for k, v in stage_ms.items()},
+                appearance_bwd_roofline=dict(bound="alu", achieved=round(achieved, 2), peak=round(FP32_PEAK_TFLOPS, 1),
+                                             unit="TFLOP/s", frac=round(achieved / FP32_PEAK_TFLOPS, 3),
+                                             flops_per_record=MLP_BWD_FLOPS_PER_RECORD,
+                                             peak_source="152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"))
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -380,6 +443,8 @@ def run_ours(args, rank, world, local_rank):
                     rgb_mean_abs_vs_fp32=float((out16["rgb"] - outs["rgb"]).abs().mean()),
                     bytes_per_gaussian=int(12 + 2 * (3 + 4 + 1) + 2 * 48))
 
+    mlp_leg = None if args.no_mlp else run_mlp_leg(args, ctx, g, cam, opts, d_out, outs, stream, dev, rank)
+
     # end to end through the same API: Gaussians from pinned host memory in, gradients out
     e2e = None
     if not args.no_e2e:
@@ -461,7 +526,7 @@ def run_ours(args, rank, world, local_rank):
                             l2="inputs larger than L2 (1.4 GB), no flush", parallelism=f"replicas{world}"),
                 render_fps=1000.0 / fwd_ms * world, fwd_ms=fwd_ms,
                 stages_ms=stage_ms, visible=V, pairs=P, counters=counts,
-                roofline=roof, cpu_baseline=cpu, e2e=e2e, clocks=clocks, fp16_storage=fp16, serve=serve_stats)
+                roofline=roof, cpu_baseline=cpu, e2e=e2e, clocks=clocks, fp16_storage=fp16, appearance_mlp=mlp_leg, serve=serve_stats)
     if serve_full is not None:
         line["serve_full"] = serve_full
     line["gpu_launches"] = int(args.steps * kernels_per_step(args.tile_cull, info))

@@ -256,7 +256,8 @@ typedef enum gsr_stage {
   GSR_STAGE_PREPROCESS_BWD = 10,/* projection and colour backward */
   GSR_STAGE_BETWEEN = 11,       /* idle time between consecutive stages of one call (memsets,
                                    waits on the host or the side stream, launch latency) */
-  GSR_NUM_STAGES = 12
+  GSR_STAGE_APPEARANCE_BWD = 12,/* appearance-transform backward (only with gsr_gaussians.mlp) */
+  GSR_NUM_STAGES = 13
 } gsr_stage;
 
 /* Counters gathered while profiling with count_evals = 1. */

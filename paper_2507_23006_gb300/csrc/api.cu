@@ -894,13 +894,15 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
   pg.absgrad = opts->absgrad ? grads->absgrad : nullptr;
   pg.vec4 = (reinterpret_cast<uintptr_t>(grads->quats) % 16 == 0) && (reinterpret_cast<uintptr_t>(grads->sh) % 16 == 0) &&
             ((3 * g->sh_coeffs) % 4 == 0);
-  {
-    StageTimer tm(ctx, GSR_STAGE_PREPROCESS_BWD, s);
+  if (g->mlp) {
     // the appearance transform's backward turns the records' gradients into those of the
     // transform's inputs before the projection backward reads them
-    if (g->mlp)
-      launch_mlp_bwd(ga, cb, V, as<Rec>(*bo.rec), as<uint32_t>(*bo.owner), as<Grad2D>(ctx->g2d),
-                     grads->gauss_embed, grads->image_embed, grads->mlp_params, 3 * (ctx->grid_cap / 2), s);
+    StageTimer tm(ctx, GSR_STAGE_APPEARANCE_BWD, s);
+    launch_mlp_bwd(ga, cb, V, as<Rec>(*bo.rec), as<uint32_t>(*bo.owner), as<Grad2D>(ctx->g2d), grads->gauss_embed,
+                   grads->image_embed, grads->mlp_params, 3 * (ctx->grid_cap / 2), s);
+  }
+  {
+    StageTimer tm(ctx, GSR_STAGE_PREPROCESS_BWD, s);
     launch_preprocess_bwd(ga, cb, opts->eps2d, opts->antialiased, V, as<Rec>(*bo.rec), as<uint32_t>(*bo.owner),
                           as<Grad2D>(ctx->g2d), pg, s);
   }

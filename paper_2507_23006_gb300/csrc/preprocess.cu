@@ -382,11 +382,18 @@ __device__ void mlp_load_smem(const GaussArgs& A, int C, MlpSmem& M) {
     M.w1g[e / kEmbG][e % kEmbG] = __ldg(A.mlp + (e / kEmbG) * kMlpIn + e % kEmbG);
   for (int e = threadIdx.x; e < kMlpOut * kHid; e += blockDim.x) M.w2[e / kHid][e % kHid] = __ldg(A.mlp + kMlpW2 + e);
   for (int e = threadIdx.x; e < kMlpOut; e += blockDim.x) M.b2[e] = __ldg(A.mlp + kMlpB2 + e);
-  for (int e = threadIdx.x; e < C * kHid; e += blockDim.x) {
-    const int c = e / kHid, k = e % kHid;
-    float a = __ldg(A.mlp + kMlpB1 + k);
-    for (int j = 0; j < kEmbI; ++j) a = fmaf(__ldg(A.mlp + k * kMlpIn + kEmbG + j), __ldg(A.iemb + c * kEmbI + j), a);
-    M.u[c][k] = a;
+  // u: four threads per (camera, hidden unit), eight terms each with every load issued at once,
+  // summed over the four lanes (C * kHid * 4 is a multiple of 32: whole warps take part)
+  for (int e = threadIdx.x; e < C * kHid * 4; e += blockDim.x) {
+    const int c = e / (kHid * 4), k = (e >> 2) % kHid, q = e & 3;
+    const float* w = A.mlp + k * kMlpIn + kEmbG + q * 8;
+    const float* l = A.iemb + c * kEmbI + q * 8;
+    float a = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a = fmaf(__ldg(w + j), __ldg(l + j), a);
+    a += __shfl_xor_sync(0xffffffffu, a, 1);
+    a += __shfl_xor_sync(0xffffffffu, a, 2);
+    if (q == 0) M.u[c][k] = a + __ldg(A.mlp + kMlpB1 + k);
   }
 }
 
@@ -493,9 +500,9 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
     Geo G;
     uint32_t vis = 0;
     const long long gi = seg_map(A.segs, base_i + slot);
+    float lg[kEmbG];
+    if (kMlp) load_gemb(A, gi, lg);  // issued with the geometry's loads
     if (load_geo<AT>(A, gi, G)) {
-      float lg[kEmbG];
-      if (kMlp) load_gemb(A, gi, lg);
       for (int c = 0; c < cams.C; ++c) {
         if (!(maybe & (1u << c))) continue;
         Proj P;
@@ -794,7 +801,7 @@ __global__ void __launch_bounds__(kBwdThreads) preprocess_bwd_kernel(
 // pre-activation gradients. Each block adds its totals with one atomic per parameter.
 struct MlpBwdSmem {
   MlpSmem M;
-  float lg[kBwdThreads][20];           // l_G per record (rows padded to 80 B: conflict-free float4)
+  float4 lg[kBwdThreads][kEmbG / 4];   // l_G per record; float4 q of row t at q ^ ((t >> 1) & 3)
   float hid[kBwdThreads][kHid + 1];    // ReLU outputs
   float dpre[kBwdThreads][kHid + 1];   // gradients of the hidden pre-activations
   float4 dz[kBwdThreads];              // gradients of the output pre-activations
@@ -822,18 +829,45 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_bwd_kernel(GaussArgs A, CamBa
   float cam_acc = 0.f;
   int cam_cur = -1;
   __syncthreads();
-  for (long long base = static_cast<long long>(blockIdx.x) * R; base < V; base += static_cast<long long>(gridDim.x) * R) {
+  // The thread's record of the next chunk is loaded one chunk ahead (its loads are in flight
+  // during the current chunk's parameter sums): camera, opacity', rgb', the four upstream
+  // gradients the transform changes, the Gaussian and its embedding.
+  const long long stride = static_cast<long long>(gridDim.x) * R;
+  bool f_ok = false;
+  int f_cam = -1;
+  long long f_g = 0;
+  float f_op = 0.f, f_rgb[3] = {0.f, 0.f, 0.f}, f_d[4] = {0.f, 0.f, 0.f, 0.f}, f_lg[kEmbG];
+  auto fetch = [&](long long v) {
+    f_ok = v < V;
+    f_cam = -1;
+#pragma unroll
+    for (int j = 0; j < kEmbG; ++j) f_lg[j] = 0.f;
+    if (!f_ok) return;
+    const float4* rp = reinterpret_cast<const float4*>(rec + v);
+    const float4 ra = rp[0], rb = rp[1], rc = rp[2];
+    f_op = ra.z;
+    f_rgb[0] = rb.w;
+    f_rgb[1] = rc.x;
+    f_rgb[2] = rc.y;
+    f_cam = static_cast<int>(__float_as_uint(rc.w) >> 27);
+    const float* gp = reinterpret_cast<const float*>(g2d + v);
+    f_d[0] = gp[2];  // opacity'
+    f_d[1] = gp[7];  // red
+    f_d[2] = gp[8];  // green
+    f_d[3] = gp[9];  // blue
+    f_g = seg_map(A.segs, owner[v]);
+    load_gemb(A, f_g, f_lg);
+  };
+  fetch(static_cast<long long>(blockIdx.x) * R + t);
+  for (long long base = static_cast<long long>(blockIdx.x) * R; base < V; base += stride) {
     const long long v = base + t;
-    int c = -1;
+    const int c = f_cam;
+    const long long g = f_g;
     float lg[kEmbG];
 #pragma unroll
-    for (int j = 0; j < kEmbG; ++j) lg[j] = 0.f;
+    for (int j = 0; j < kEmbG; ++j) lg[j] = f_lg[j];
     float dz[kMlpOut] = {0.f, 0.f, 0.f, 0.f};
-    if (v < V) {
-      const Rec r = rec[v];
-      c = rec_cam(r);
-      const long long g = seg_map(A.segs, owner[v]);
-      load_gemb(A, g, lg);
+    if (f_ok) {
       float z[kMlpOut];
 #pragma unroll
       for (int o = 0; o < kMlpOut; ++o) z[o] = S.M.b2[o];
@@ -852,18 +886,14 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_bwd_kernel(GaussArgs A, CamBa
       float out[kMlpOut];
 #pragma unroll
       for (int o = 0; o < kMlpOut; ++o) out[o] = 1.f / (1.f + __expf(-z[o]));
-      Grad2D gd = g2d[v];
-      const float rgbp[3] = {r.b.w, r.c.x, r.c.y};
-      const float drgbp[3] = {gd.b.w, gd.c.x, gd.c.y};
-      const float dopp = gd.a.z;
 #pragma unroll
-      for (int ch = 0; ch < 3; ++ch) dz[ch] = rgbp[ch] * drgbp[ch] * (1.f - out[ch]);
-      dz[3] = -r.a.z * dopp * out[3];
-      gd.a.z = dopp * (1.f - out[3]);
-      gd.b.w = 2.f * out[0] * drgbp[0];
-      gd.c.x = 2.f * out[1] * drgbp[1];
-      gd.c.y = 2.f * out[2] * drgbp[2];
-      g2d[v] = gd;
+      for (int ch = 0; ch < 3; ++ch) dz[ch] = f_rgb[ch] * f_d[1 + ch] * (1.f - out[ch]);
+      dz[3] = -f_op * f_d[0] * out[3];
+      float* gw = reinterpret_cast<float*>(g2d + v);
+      gw[2] = f_d[0] * (1.f - out[3]);
+      gw[7] = 2.f * out[0] * f_d[1];
+      gw[8] = 2.f * out[1] * f_d[2];
+      gw[9] = 2.f * out[2] * f_d[3];
       float dlg[kEmbG];
 #pragma unroll
       for (int j = 0; j < kEmbG; ++j) dlg[j] = 0.f;
@@ -885,14 +915,15 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_bwd_kernel(GaussArgs A, CamBa
       for (int k = 0; k < kHid; ++k) S.hid[t][k] = S.dpre[t][k] = 0.f;
     }
 #pragma unroll
-    for (int j = 0; j < kEmbG; j += 4)
-      *reinterpret_cast<float4*>(&S.lg[t][j]) = make_float4(lg[j], lg[j + 1], lg[j + 2], lg[j + 3]);
+    for (int j = 0; j < kEmbG; j += 4)  // swizzled: the eight lanes of one store phase hit distinct banks
+      S.lg[t][(j >> 2) ^ ((t >> 1) & 3)] = make_float4(lg[j], lg[j + 1], lg[j + 2], lg[j + 3]);
     S.dz[t] = make_float4(dz[0], dz[1], dz[2], dz[3]);
     S.cam[t] = c;
     __syncthreads();
+    fetch(base + stride + t);
     for (int u = 0; u < R; ++u) {
       const float dp = S.dpre[u][k1];
-      const float4 l = *reinterpret_cast<const float4*>(&S.lg[u][j1]);
+      const float4 l = S.lg[u][(j1 >> 2) ^ ((u >> 1) & 3)];
       a1[0] = fmaf(dp, l.x, a1[0]);
       a1[1] = fmaf(dp, l.y, a1[1]);
       a1[2] = fmaf(dp, l.z, a1[2]);
@@ -928,13 +959,17 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_bwd_kernel(GaussArgs A, CamBa
     if (a2[o] != 0.f) atomicAdd(g_params + kMlpW2 + o * kHid + k2, a2[o]);
     if (k2 == 0 && ab2[o] != 0.f) atomicAdd(g_params + kMlpB2 + o, ab2[o]);
   }
+  // the chunk arrays are free now: stage the image part of w1 (in hid) and the image
+  // embeddings (in dpre) for the per-camera terms
+  for (int e = t; e < kHid * kEmbI; e += R) S.hid[e / kEmbI][e % kEmbI] = __ldg(A.mlp + (e / kEmbI) * kMlpIn + kEmbG + e % kEmbI);
+  for (int e = t; e < cams.C * kEmbI; e += R) S.dpre[e / kEmbI][e % kEmbI] = __ldg(A.iemb + e);
   __syncthreads();
   // image part of w1 and b1: sums over the cameras of sum[c][k] l_I(c)[j] and sum[c][k]
   for (int e = t; e < kHid * (kEmbI + 1); e += R) {
     const int k = e / (kEmbI + 1), j = e % (kEmbI + 1);
     float a = 0.f;
     if (j < kEmbI) {
-      for (int c = 0; c < cams.C; ++c) a = fmaf(S.sum[c][k], __ldg(A.iemb + c * kEmbI + j), a);
+      for (int c = 0; c < cams.C; ++c) a = fmaf(S.sum[c][k], S.dpre[c][j], a);
       if (a != 0.f) atomicAdd(g_params + k * kMlpIn + kEmbG + j, a);
     } else {
       for (int c = 0; c < cams.C; ++c) a += S.sum[c][k];
@@ -945,7 +980,8 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_bwd_kernel(GaussArgs A, CamBa
   for (int e = t; e < cams.C * kEmbI; e += R) {
     const int c = e / kEmbI, j = e % kEmbI;
     float a = 0.f;
-    for (int k = 0; k < kHid; ++k) a = fmaf(__ldg(A.mlp + k * kMlpIn + kEmbG + j), S.sum[c][k], a);
+#pragma unroll 8
+    for (int k = 0; k < kHid; ++k) a = fmaf(S.hid[k][j], S.sum[c][k], a);
     if (a != 0.f) atomicAdd(g_iemb + e, a);
   }
 }

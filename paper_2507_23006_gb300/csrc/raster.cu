@@ -346,7 +346,7 @@ __host__ __device__ constexpr int transpose_shared_bits() {
 
 // kAbs: also accumulate |dL/dmean2D| per pixel (AbsGS densification statistics).
 template <bool kCount, bool kAbs>
-__global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __restrict__ rec,
+__global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* __restrict__ rec,
                                                                   const uint32_t* __restrict__ pvals,
                                                                   const uint2* __restrict__ ranges, CamBatch cams,
                                                                   float3 bg, BlendBwdIn in, Grad2D* __restrict__ g2d,
@@ -444,26 +444,36 @@ __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __r
     for (int j = 0; j < cnt; ++j) {
       if (!((sM[j] >> wid) & 1u)) continue;  // warp-uniform: no pixel of this warp is touched
       const uint32_t pos = static_cast<uint32_t>(n - 1 - base - j);
-      float gv[kGradVals];
-#pragma unroll
-      for (int m = 0; m < kGradVals; ++m) gv[m] = 0.f;
-      bool contrib = false;
       const float4 a = sA[j];
       const float4 b = sB[j];
       const float2 cc = sC[j];
       const float dx = a.x - fx;
+      float dyq[2], Gq[2], arawq[2], alphaq[2];
+      bool cq[2];
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {  // branch-free: contributions are masked, not branched around
+      for (int q = 0; q < 2; ++q) {
         const bool vis = inside[q] && pos < last[q];
         if (kCount) n_visit += vis;
-        const float dy = a.y - fy[q];
-        const float sigma = 0.5f * (b.x * dx * dx + b.z * dy * dy) + b.y * dx * dy;
-        const float G = __expf(-sigma);
-        const float araw = a.z * G;
-        const float alpha = fminf(kAlphaMax, araw);
-        const bool c = vis && sigma >= 0.f && alpha >= kAlphaMin;
-        if (kCount) n_contrib += c;
-        contrib = contrib || c;
+        dyq[q] = a.y - fy[q];
+        const float sigma = 0.5f * (b.x * dx * dx + b.z * dyq[q] * dyq[q]) + b.y * dx * dyq[q];
+        Gq[q] = __expf(-sigma);
+        arawq[q] = a.z * Gq[q];
+        alphaq[q] = fminf(kAlphaMax, arawq[q]);
+        cq[q] = vis && sigma >= 0.f && alphaq[q] >= kAlphaMin;
+        if (kCount) n_contrib += cq[q];
+      }
+      // warp-uniform: where no pixel of the warp takes the Gaussian, nothing below changes
+      if (!__any_sync(0xffffffffu, cq[0] || cq[1])) continue;
+      float gv[kGradVals];
+#pragma unroll
+      for (int m = 0; m < kGradVals; ++m) gv[m] = 0.f;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {  // branch-free: contributions are masked, not branched around
+        const float dy = dyq[q];
+        const float G = Gq[q];
+        const float araw = arawq[q];
+        const float alpha = alphaq[q];
+        const bool c = cq[q];
         const float rom = __frcp_rn(1.f - alpha);  // 1 / (1 - alpha), correctly rounded
         const float Ti = T[q] * rom;
         const float wgt = c ? alpha * Ti : 0.f;
@@ -494,10 +504,8 @@ __global__ void __launch_bounds__(kBlendThreads) blend_bwd_kernel(const Rec* __r
           gv[11] += fabsf(dmy);
         }
       }
-      if (__any_sync(0xffffffffu, contrib)) {
-        const float tot = TransposeSum<kVals, 16>::run(gv, lane);
-        if (t_keep) atomicAdd(&sAcc[j][t_idx], tot);
-      }
+      const float tot = TransposeSum<kVals, 16>::run(gv, lane);
+      if (t_keep) atomicAdd(&sAcc[j][t_idx], tot);
     }
     __syncthreads();
     for (int k = tid; k < cnt; k += kBlendThreads) {

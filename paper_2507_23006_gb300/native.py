@@ -41,7 +41,7 @@ EXPORTED = [
 ]
 
 STAGES = ["preprocess", "depth_sort", "tile_count", "pair_scan", "readback", "duplicate", "tile_sort", "ranges",
-          "blend_fwd", "blend_bwd", "preprocess_bwd", "between_stages"]
+          "blend_fwd", "blend_bwd", "preprocess_bwd", "between_stages", "appearance_bwd"]
 COUNTERS = ["fwd_evals", "fwd_contribs", "bwd_evals", "bwd_contribs"]
 
 

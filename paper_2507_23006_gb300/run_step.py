@@ -6,7 +6,8 @@ synthetic workload and nothing else: the command to put under a kernel profiler.
 Workloads: `city` (a synthetic city grid seen from 150 m up at 45 degrees, the training-step
 benchmark), `street` (a street block, one camera 30 m up looking 45 degrees down) and `box`
 (uniform Gaussians in a box in front of the camera). `--fwd-only` runs forward renders without
-saved state; `--fp16` stores attributes and SH in FP16; `--time` prints the device time per
+saved state; `--fp16` stores attributes and SH in FP16; `--mlp` turns on the per-Gaussian
+appearance transform (random embeddings and weights); `--time` prints the device time per
 step after the first, and then the mean time of each stage over as many more steps (CUDA events
 around every stage).
 """
@@ -40,6 +41,7 @@ def main():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--fwd-only", action="store_true")
     p.add_argument("--fp16", action="store_true")
+    p.add_argument("--mlp", action="store_true")
     p.add_argument("--tile-cull", type=int, default=1)
     p.add_argument("--time", action="store_true")
     a = p.parse_args()
@@ -47,6 +49,11 @@ def main():
     dt = torch.float16 if a.fp16 else torch.float32
     ctx = native.Context(0)
     g = native.Gaussians.from_scene(scene, attr_dtype=dt, sh_dtype=dt)
+    if a.mlp:
+        gm = torch.Generator(device="cuda").manual_seed(4321)
+        g.mlp = native.AppearanceMLP(torch.randn((g.n, 16), device="cuda", generator=gm),
+                                     torch.randn((1, 32), device="cuda", generator=gm),
+                                     0.3 * torch.randn(native.MLP_PARAMS, device="cuda", generator=gm))
     opts = native.Options(tile_cull=bool(a.tile_cull), save_state=not a.fwd_only)
     npix = cam.width * cam.height
     gen = torch.Generator(device="cuda").manual_seed(1234)
