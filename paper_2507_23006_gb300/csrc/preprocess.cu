@@ -334,6 +334,18 @@ __device__ __forceinline__ void eval_color_regs(int deg, const Geo& G, const Dev
 }
 
 // The 64-byte record of a visible (Gaussian, camera c) projection, colour left at zero.
+// Where op' exp(-d^T Q d / 2) >= 1/255, i.e. d^T Q d <= 2 ln(255 op'): an ellipse whose
+// half-extents are sqrt(2 ln(255 op') Sigma_xx) and sqrt(2 ln(255 op') Sigma_yy), Sigma the
+// dilated covariance (sxx, syy its diagonal). Widened by 0.1% + 0.01 px so FP32 evaluation never
+// falls outside.
+__device__ __forceinline__ float4 alpha_box(float mx, float my, float op, float sxx, float syy) {
+  const float L = logf(255.f * op);
+  if (!(L > 0.f)) return make_float4(1.f, -1.f, 1.f, -1.f);  // empty: no pixel reaches 1/255
+  const float ex = sqrtf(2.f * L * sxx) * 1.001f + 0.01f;
+  const float ey = sqrtf(2.f * L * syy) * 1.001f + 0.01f;
+  return make_float4(mx - ex, mx + ex, my - ey, my + ey);
+}
+
 __device__ __forceinline__ Rec record_geometry(const Proj& P, int c, float eps) {
   Rec rr;
   rr.a = make_float4(P.mx, P.my, P.op, P.t[2]);
@@ -341,17 +353,7 @@ __device__ __forceinline__ Rec record_geometry(const Proj& P, int c, float eps) 
   const uint32_t lo = static_cast<uint32_t>(P.x0) | (static_cast<uint32_t>(P.x1) << 16);
   const uint32_t hi = static_cast<uint32_t>(P.y0) | (static_cast<uint32_t>(P.y1) << 16) | (static_cast<uint32_t>(c) << 27);
   rr.c = make_float4(0.f, 0.f, __uint_as_float(lo), __uint_as_float(hi));
-  // Where op' exp(-d^T Q d / 2) >= 1/255, i.e. d^T Q d <= 2 ln(255 op'): an ellipse whose
-  // half-extents are sqrt(2 ln(255 op') Sigma_xx) and sqrt(2 ln(255 op') Sigma_yy), Sigma the
-  // dilated covariance. Widened by 0.1% + 0.01 px so FP32 evaluation never falls outside.
-  const float L = logf(255.f * P.op);
-  if (L > 0.f) {
-    const float ex = sqrtf(2.f * L * (P.ar + eps)) * 1.001f + 0.01f;
-    const float ey = sqrtf(2.f * L * (P.cr + eps)) * 1.001f + 0.01f;
-    rr.d = make_float4(P.mx - ex, P.mx + ex, P.my - ey, P.my + ey);
-  } else {
-    rr.d = make_float4(1.f, -1.f, 1.f, -1.f);  // empty: no pixel reaches 1/255
-  }
+  rr.d = alpha_box(P.mx, P.my, P.op, P.ar + eps, P.cr + eps);
   return rr;
 }
 
@@ -402,23 +404,62 @@ __device__ __forceinline__ void load_gemb(const GaussArgs& A, long long g, float
   for (int j = 0; j < kEmbG; ++j) lg[j] = __ldg(A.gemb + g * kEmbG + j);
 }
 
-// The transform's outputs for a Gaussian embedding seen by camera c: out = sigmoid(w2 ReLU(u_c +
-// w1_G l_G) + b2); 2 out[0..2] is the colour gain, 1 - out[3] the opacity factor.
-__device__ __forceinline__ void mlp_eval(const MlpSmem& M, const float lg[kEmbG], int c, float out[kMlpOut]) {
-  float z[kMlpOut];
+// Pre-activation of hidden unit k, in two chains of eight terms; the forward and the backward's
+// recomputation share it, so both see the same bits.
+__device__ __forceinline__ float mlp_pre(const MlpSmem& M, const float lg[kEmbG], int c, int k) {
+  float a = M.u[c][k], a2 = 0.f;
 #pragma unroll
-  for (int o = 0; o < kMlpOut; ++o) z[o] = M.b2[o];
-#pragma unroll 4
-  for (int k = 0; k < kHid; ++k) {
-    float a = M.u[c][k];
-#pragma unroll
-    for (int j = 0; j < kEmbG; ++j) a = fmaf(M.w1g[k][j], lg[j], a);
-    const float h = fmaxf(a, 0.f);
-#pragma unroll
-    for (int o = 0; o < kMlpOut; ++o) z[o] = fmaf(M.w2[o][k], h, z[o]);
+  for (int j = 0; j < kEmbG; j += 2) {
+    a = fmaf(M.w1g[k][j], lg[j], a);
+    a2 = fmaf(M.w1g[k][j + 1], lg[j + 1], a2);
   }
+  return a + a2;
+}
+
+// Partial output pre-activations over the hidden units of quarter q (8q .. 8q+7, in order).
+// f(k, a, h) sees each unit's pre-activation a and output h.
+template <typename F>
+__device__ __forceinline__ void mlp_zpart(const MlpSmem& M, const float lg[kEmbG], int c, int q, float zq[kMlpOut],
+                                          F&& f) {
 #pragma unroll
-  for (int o = 0; o < kMlpOut; ++o) out[o] = 1.f / (1.f + __expf(-z[o]));
+  for (int o = 0; o < kMlpOut; ++o) zq[o] = 0.f;
+#pragma unroll 2
+  for (int k = 8 * q; k < 8 * q + 8; ++k) {
+    const float a = mlp_pre(M, lg, c, k);
+    const float h = fmaxf(a, 0.f);
+    f(k, a, h);
+#pragma unroll
+    for (int o = 0; o < kMlpOut; ++o) zq[o] = fmaf(M.w2[o][k], h, zq[o]);
+  }
+}
+
+// The transform's outputs from the four quarters' partial sums: out = sigmoid(b2 + ((z0 + z1) +
+// (z2 + z3))). Every evaluation (one thread, four cooperating lanes, the backward's
+// recomputation) sums in this order, so all of them see the same bits.
+__device__ __forceinline__ void mlp_out(const MlpSmem& M, const float z01[kMlpOut], const float z23[kMlpOut],
+                                        float out[kMlpOut]) {
+#pragma unroll
+  for (int o = 0; o < kMlpOut; ++o) out[o] = 1.f / (1.f + __expf(-(M.b2[o] + (z01[o] + z23[o]))));
+}
+
+// The transform's outputs for a Gaussian embedding seen by camera c: out = sigmoid(w2 ReLU(u_c +
+// w1_G l_G) + b2); 2 out[0..2] is the colour gain, 1 - out[3] the opacity factor. f as in mlp_zpart.
+template <typename F>
+__device__ __forceinline__ void mlp_eval_f(const MlpSmem& M, const float lg[kEmbG], int c, float out[kMlpOut], F&& f) {
+  float z01[kMlpOut], z23[kMlpOut], zq[kMlpOut];
+  mlp_zpart(M, lg, c, 0, z01, f);
+  mlp_zpart(M, lg, c, 1, zq, f);
+#pragma unroll
+  for (int o = 0; o < kMlpOut; ++o) z01[o] += zq[o];
+  mlp_zpart(M, lg, c, 2, z23, f);
+  mlp_zpart(M, lg, c, 3, zq, f);
+#pragma unroll
+  for (int o = 0; o < kMlpOut; ++o) z23[o] += zq[o];
+  mlp_out(M, z01, z23, out);
+}
+
+__device__ __forceinline__ void mlp_eval(const MlpSmem& M, const float lg[kEmbG], int c, float out[kMlpOut]) {
+  mlp_eval_f(M, lg, c, out, [](int, float, float) {});
 }
 
 // Appends the slots of the lanes with `pred` to the block's list (order within the list is
@@ -500,25 +541,19 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
     Geo G;
     uint32_t vis = 0;
     const long long gi = seg_map(A.segs, base_i + slot);
-    float lg[kEmbG];
-    if (kMlp) load_gemb(A, gi, lg);  // issued with the geometry's loads
     if (load_geo<AT>(A, gi, G)) {
       for (int c = 0; c < cams.C; ++c) {
         if (!(maybe & (1u << c))) continue;
         Proj P;
         if (!project(G, cams.cam[c], eps, aa, P)) continue;
         vis |= 1u << c;
-        float mo[kMlpOut] = {0.5f, 0.5f, 0.5f, 0.f};
-        if (kMlp) {
-          mlp_eval(s_mlp, lg, c, mo);
-          P.op *= 1.f - mo[3];  // before the record's alpha >= 1/255 box is taken from it
-        }
         const uint32_t e = atomicAdd(&s_count[1], 1u);
         if (e < kPreStage) {
           Rec rr = record_geometry(P, c, eps);
-          rr.b.w = 2.f * mo[0];  // colour gains until the colour is evaluated
-          rr.c.x = 2.f * mo[1];
-          rr.c.y = 2.f * mo[2];
+          rr.b.w = rr.c.x = rr.c.y = 1.f;  // colour gains until the colour is evaluated
+          // with the appearance transform the opacity (and so the alpha box) is final only
+          // after the colour phase: keep the dilated variances the box is made from
+          if (kMlp) rr.d = make_float4(P.ar + eps, P.cr + eps, 0.f, 0.f);
           s_rec[e][0] = rr.a;
           s_rec[e][1] = rr.b;
           s_rec[e][2] = rr.c;
@@ -559,12 +594,27 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
     G.m[0] = __ldg(A.means + 3 * g + 0);
     G.m[1] = __ldg(A.means + 3 * g + 1);
     G.m[2] = __ldg(A.means + 3 * g + 2);
+    float mo[kMlpOut];
+    if (kMlp) {  // before the colour: only the four outputs stay live through it
+      float lg[kEmbG];
+      load_gemb(A, g, lg);
+      mlp_eval(s_mlp, lg, static_cast<int>(meta >> 16), mo);
+    }
     float rgb[3], dir[3], dn, Y[16];
     bool cl[3];
     eval_color<ST>(A, g, G, cams.cam[meta >> 16], rgb, dir, dn, Y, cl);
-    s_rec[e][1].w *= rgb[0];  // times the colour gain (1 without the appearance transform)
-    s_rec[e][2].x *= rgb[1];
-    s_rec[e][2].y *= rgb[2];
+    if (kMlp) {
+      const float4 a = s_rec[e][0], d = s_rec[e][3];
+      const float op = a.z * (1.f - mo[3]);
+      s_rec[e][0].z = op;
+      s_rec[e][3] = alpha_box(a.x, a.y, op, d.x, d.y);
+      rgb[0] *= 2.f * mo[0];
+      rgb[1] *= 2.f * mo[1];
+      rgb[2] *= 2.f * mo[2];
+    }
+    s_rec[e][1].w = rgb[0];
+    s_rec[e][2].x = rgb[1];
+    s_rec[e][2].y = rgb[2];
   }
   if (threadIdx.x < 32) {
     const unsigned long long ex = warp_lookback(out.status, bid, total, out.epoch, out.err);
@@ -595,8 +645,6 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
     const long long g = seg_map(A.segs, i);
     Geo G;
     load_geo<AT>(A, g, G);
-    float lg[kEmbG];
-    if (kMlp) load_gemb(A, g, lg);
     long long v = block_base + s_aux[slot];
     for (int c = 0; c < cams.C; ++c) {
       if (!(vis & (1u << c))) continue;
@@ -605,6 +653,8 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
       project(G, cam, eps, aa, P);
       float mo[kMlpOut] = {0.5f, 0.5f, 0.5f, 0.f};
       if (kMlp) {
+        float lg[kEmbG];
+        load_gemb(A, g, lg);
         mlp_eval(s_mlp, lg, c, mo);
         P.op *= 1.f - mo[3];
       }
@@ -868,24 +918,12 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_bwd_kernel(GaussArgs A, CamBa
     for (int j = 0; j < kEmbG; ++j) lg[j] = f_lg[j];
     float dz[kMlpOut] = {0.f, 0.f, 0.f, 0.f};
     if (f_ok) {
-      float z[kMlpOut];
-#pragma unroll
-      for (int o = 0; o < kMlpOut; ++o) z[o] = S.M.b2[o];
       uint32_t on = 0;  // ReLU active
-#pragma unroll 4
-      for (int k = 0; k < kHid; ++k) {
-        float a = S.M.u[c][k];
-#pragma unroll
-        for (int j = 0; j < kEmbG; ++j) a = fmaf(S.M.w1g[k][j], lg[j], a);
-        const float h = fmaxf(a, 0.f);
+      float out[kMlpOut];
+      mlp_eval_f(S.M, lg, c, out, [&](int k, float a, float h) {
         on |= (a > 0.f ? 1u : 0u) << k;
         S.hid[t][k] = h;
-#pragma unroll
-        for (int o = 0; o < kMlpOut; ++o) z[o] = fmaf(S.M.w2[o][k], h, z[o]);
-      }
-      float out[kMlpOut];
-#pragma unroll
-      for (int o = 0; o < kMlpOut; ++o) out[o] = 1.f / (1.f + __expf(-z[o]));
+      });
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) dz[ch] = f_rgb[ch] * f_d[1 + ch] * (1.f - out[ch]);
       dz[3] = -f_op * f_d[0] * out[3];
