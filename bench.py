@@ -320,6 +320,52 @@ def run_mlp_leg(args, ctx, g, cam, opts, d_out, outs, stream, dev, rank):
                                              peak_source="152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"))
 
 
+# Algorithmic work of each stage of one step (the design notes derive each figure): bytes that
+# must cross HBM, FP32 operations and MUFU operations (ex2, reciprocal) of the blends.
+def stage_work(n, V, P, tiles, npix, counts, sort_passes_tile):
+    fe, be = counts["fwd_evals"], counts["bwd_evals"]
+    return {
+        "preprocess": dict(bytes=52.0 * n + 252.0 * V),
+        "depth_sort": dict(bytes=68.0 * V),
+        "tile_count": dict(bytes=56.0 * V),
+        "pair_scan": dict(bytes=12.0 * V),
+        "duplicate": dict(bytes=56.0 * V + 8.0 * P),
+        "tile_sort": dict(bytes=(4.0 + 16.0 * sort_passes_tile) * P),
+        "ranges": dict(bytes=4.0 * P + 8.0 * tiles),
+        "blend_fwd": dict(bytes=48.0 * P + 28.0 * npix, flops=FLOPS_PER_FWD_EVAL * fe, mufu=1.0 * fe),
+        "blend_bwd": dict(bytes=48.0 * P + 28.0 * npix + 48.0 * V, flops=FLOPS_PER_BWD_EVAL * be, mufu=2.0 * be),
+        # single camera: one record per visible Gaussian; its attribute and SH rows read and its
+        # gradient rows written (236 B each way) plus the record, its 2D gradients and owner
+        "preprocess_bwd": dict(bytes=472.0 * V + 116.0 * V),
+        # the gradient rows of every Gaussian zeroed (side stream, beside the binning)
+        "gradient_fill": dict(bytes=236.0 * n),
+    }
+
+
+def stage_rooflines(stage_ms, n, V, P, tiles, npix, counts, fp32_tflops, mufu_per_s, hbm_gbs, step_ms):
+    """Per stage: the algorithmic time (the largest of bytes / HBM peak, FP32 ops / FP32 peak and
+    MUFU ops / MUFU peak) against the measured time; for the step, the sum of the stages'
+    algorithmic times (the gradient fill's included) against the step time."""
+    passes = (max(1, math.ceil(math.log2(max(tiles, 2)))) + 7) // 8
+    out = {}
+    total = 0.0
+    for k, w in stage_work(n, V, P, tiles, npix, counts, passes).items():
+        t = {"hbm": w.get("bytes", 0.0) / (hbm_gbs * 1e9), "alu": w.get("flops", 0.0) / (fp32_tflops * 1e12),
+             "mufu": w.get("mufu", 0.0) / mufu_per_s}
+        bound = max(t, key=t.get)
+        algo_us = t[bound] * 1e6
+        total += algo_us
+        meas = stage_ms.get(k)
+        row = dict(bound=bound, algorithmic_us=round(algo_us, 2))
+        if meas:
+            row.update(measured_us=round(meas * 1e3, 2), frac=round(algo_us / (meas * 1e3), 3))
+        else:
+            row.update(measured_us=None, frac=None, note="runs beside the other stages")
+        out[k] = row
+    return out, dict(algorithmic_us=round(total, 1), step_us=round(step_ms * 1e3, 1),
+                     frac=round(total / (step_ms * 1e3), 3))
+
+
 def run_e2e(args, ctx, g, cam, opts, d_out, grads, outs, stream, world, dev, barrier):
     """The step through the same API with the Gaussians and upstream gradients copied in from
     pinned host memory and the parameter gradients copied out, every step. Pipelined the way a
@@ -573,6 +619,8 @@ def run_ours(args, rank, world, local_rank):
         roof = dict(kernel=dom, launch_ms=dom_ms, bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm,
                     traffic=stored_traffic(dom, workload_name(n, cam.height)),
                     peak_source=f"{hbm_kind} HBM copy bandwidth")
+    stage_roof, step_roof = stage_rooflines(stage_ms, n, V, P, info["n_tiles"], cam.width * cam.height, counts,
+                                            fp32_peak, sms * 16 * sm_mhz * 1e6, hbm, ms)
     cpu = None
     if not args.no_cpu_baseline:
         r = cpu_reference(scene, cam, args.tile_cull, args.cpu_tiles)
@@ -587,7 +635,8 @@ def run_ours(args, rank, world, local_rank):
                             l2="inputs larger than L2 (1.4 GB), no flush", parallelism=f"replicas{world}"),
                 render_fps=1000.0 / fwd_ms * world, fwd_ms=fwd_ms,
                 stages_ms=stage_ms, visible=V, pairs=P, counters=counts,
-                roofline=roof, cpu_baseline=cpu, e2e=e2e, clocks=clocks, fp16_storage=fp16, appearance_mlp=mlp_leg, serve=serve_stats)
+                roofline=roof, stage_roofline=stage_roof, step_roofline=step_roof,
+                cpu_baseline=cpu, e2e=e2e, clocks=clocks, fp16_storage=fp16, appearance_mlp=mlp_leg, serve=serve_stats)
     if serve_full is not None:
         line["serve_full"] = serve_full
     line["gpu_launches"] = int(args.steps * kernels_per_step(args.tile_cull, info))

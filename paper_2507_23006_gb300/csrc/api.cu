@@ -472,7 +472,7 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
     GSR_TRY_ALLOC(ctx->cnt_sorted, sizeof(uint32_t) * capv);
     StageTimer tm(ctx, GSR_STAGE_TILE_COUNT, s);
     launch_duplicate(as<Rec>(*bo.rec), as<uint32_t>(ctx->dvals_s), nullptr, d_V, capv, cb, 1,
-                     as<uint32_t>(ctx->cnt_sorted), nullptr, nullptr, s);
+                     as<uint32_t>(ctx->cnt_sorted), nullptr, nullptr, 4 * ctx->grid_cap, s);
     cnt_sorted = as<uint32_t>(ctx->cnt_sorted);
   }
   {
@@ -515,8 +515,8 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
     sc = sort_scratch(ctx);
     {
       StageTimer tm(ctx, GSR_STAGE_DUPLICATE, s);
-      launch_duplicate(as<Rec>(*bo.rec), as<uint32_t>(ctx->dvals_s), as<uint32_t>(ctx->offsets), d_V, capv, cb,
-                       o->tile_cull, nullptr, as<uint32_t>(ctx->pkeys), as<uint32_t>(ctx->pvals), s);
+      launch_duplicate(as<Rec>(*bo.rec), as<uint32_t>(ctx->dvals_s), as<uint32_t>(ctx->offsets), d_V, V, cb,
+                       o->tile_cull, nullptr, as<uint32_t>(ctx->pkeys), as<uint32_t>(ctx->pvals), 4 * ctx->grid_cap, s);
     }
     const int tb = bits_for(cb.total_tiles);
     {

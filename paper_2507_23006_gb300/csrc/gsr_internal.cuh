@@ -205,7 +205,7 @@ void pair_offsets_scan(const uint32_t* touched, const uint32_t* order, const uin
 // Duplicate-with-keys (warp-cooperative). count_only: writes cnt_sorted[i] (tile-culled counts).
 void launch_duplicate(const Rec* rec, const uint32_t* order, const uint32_t* offsets, const uint32_t* d_n,
                       long long max_n, const CamBatch& cams, int tile_cull, uint32_t* cnt_sorted,
-                      uint32_t* pair_keys, uint32_t* pair_vals, cudaStream_t s);
+                      uint32_t* pair_keys, uint32_t* pair_vals, int max_blocks, cudaStream_t s);
 void launch_ranges(const uint32_t* sorted_keys, long long P, int n_tiles, uint2* ranges, cudaStream_t s);
 
 struct BlendFwdOut {

@@ -11,6 +11,8 @@
 //   blend bwd:  same tiling, contributors walked back to front recovering T_i = T_{i+1}/(1-a_i);
 //               per-Gaussian gradients are summed over the warp with shuffles, over the CTA in
 //               shared memory, and added to global memory once per (tile, Gaussian).
+#include <algorithm>
+
 #include "gsr_internal.cuh"
 
 namespace gsr {
@@ -73,8 +75,11 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const Rec* __restrict__ 
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   long long n = static_cast<long long>(*d_n);
   if (n > max_n) n = max_n;
-  const long long base_i = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) & ~31ll;
-  if (base_i >= n) return;  // warp-uniform
+  // warps stride over the records 32 at a time (the grid is sized for the resident blocks, not
+  // for the capacity, so no block starts only to find nothing to do)
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long base_i = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) & ~31ll; base_i < n;
+       base_i += stride) {
   const long long i = base_i + lane;
   const bool valid = i < n;
   uint32_t v = 0, off = 0, area = 0, lo = 0, hi = 0;
@@ -154,6 +159,8 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const Rec* __restrict__ 
     }
   }
   if (kCount && valid) cnt_sorted[i] = s_cnt[w][lane];
+  __syncwarp();  // the next round clears s_cnt
+  }
 }
 
 __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__ a, uint32_t n, uint32_t key) {
@@ -559,9 +566,9 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
 
 void launch_duplicate(const Rec* rec, const uint32_t* order, const uint32_t* offsets, const uint32_t* d_n,
                       long long max_n, const CamBatch& cams, int tile_cull, uint32_t* cnt_sorted,
-                      uint32_t* pair_keys, uint32_t* pair_vals, cudaStream_t s) {
+                      uint32_t* pair_keys, uint32_t* pair_vals, int max_blocks, cudaStream_t s) {
   if (max_n <= 0) return;
-  const int blocks = static_cast<int>((max_n + 255) / 256);
+  const int blocks = static_cast<int>(std::min<long long>((max_n + 255) / 256, std::max(max_blocks, 1)));
   if (cnt_sorted) {
     duplicate_kernel<true, true><<<blocks, 256, 0, s>>>(rec, order, offsets, d_n, max_n, cams, cnt_sorted, nullptr,
                                                         nullptr);
