@@ -39,7 +39,7 @@ struct gsr_ctx {
   // scratch
   Buf seg_begin, seg_start;
   Buf rec, dkeys, dvals, touched, owner;  // binning (recompute / no-state mode)
-  Buf dkeys_s, dvals_s, sort_ktmp, sort_vtmp, sort_hist, sort_hist_blocks, sort_status, sort_counters;
+  Buf dkeys_s, dvals_s, sort_ktmp, sort_vtmp, sort_hist, sort_status;
   Buf cnt_sorted, offsets, pre_status, scan_status, misc;
   Buf pkeys, pvals, pkeys_s, pvals_s, ranges;  // pairs (no-state mode)
   Buf pix_T, pix_n, pix_D;                     // per-pixel state (no-state mode)
@@ -175,9 +175,7 @@ SortScratch sort_scratch(gsr_ctx* ctx) {
   sc.keys_tmp = as<uint32_t>(ctx->sort_ktmp);
   sc.vals_tmp = as<uint32_t>(ctx->sort_vtmp);
   sc.hist = as<uint32_t>(ctx->sort_hist);
-  sc.hist_blocks = as<uint32_t>(ctx->sort_hist_blocks);
   sc.status = as<unsigned long long>(ctx->sort_status);
-  sc.counters = as<uint32_t>(ctx->sort_counters);
   sc.grid_cap = ctx->grid_cap;
   return sc;
 }
@@ -185,10 +183,8 @@ SortScratch sort_scratch(gsr_ctx* ctx) {
 bool ensure_sort(gsr_ctx* ctx, long long n, cudaStream_t s) {
   const size_t words = sort_status_words(n) * 4;  // four passes at most
   return ensure(ctx, ctx->sort_ktmp, sizeof(uint32_t) * n, s) && ensure(ctx, ctx->sort_vtmp, sizeof(uint32_t) * n, s) &&
-         ensure(ctx, ctx->sort_hist, sizeof(uint32_t) * 4 * 256, s) &&
-         ensure(ctx, ctx->sort_hist_blocks, sizeof(uint32_t) * 4 * 256 * kMaxHistBlocks, s) &&
-         ensure_zeroed(ctx, ctx->sort_status, sizeof(unsigned long long) * words, s) &&
-         ensure(ctx, ctx->sort_counters, sizeof(uint32_t) * 4, s);
+         ensure(ctx, ctx->sort_hist, sizeof(uint32_t) * kSortCountWords, s) &&
+         ensure_zeroed(ctx, ctx->sort_status, sizeof(unsigned long long) * words, s);
 }
 
 unsigned long long* counters_of(gsr_ctx* ctx) {
@@ -438,7 +434,13 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
 
+  // sort scratch first: the preprocess counts the depth keys' digits for the sort
+  if (!ensure_sort(ctx, capv, s)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
+  SortScratch sc = sort_scratch(ctx);
+  sort_clear_counts(sc, s);
+
   PreOut po;
+  po.key_counts = sc.hist;
   po.rec = as<Rec>(*bo.rec);
   po.depth_keys = as<uint32_t>(ctx->dkeys);
   po.depth_vals = as<uint32_t>(ctx->dvals);
@@ -458,13 +460,11 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   e = start_prezero(ctx, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
 
-  // depth sort of the visible records (V read on the device)
-  if (!ensure_sort(ctx, capv, s)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
-  SortScratch sc = sort_scratch(ctx);
+  // depth sort of the visible records (V read on the device; digits counted by the preprocess)
   if (N * C > 0) {
     StageTimer tm(ctx, GSR_STAGE_DEPTH_SORT, s);
     radix_sort_u32(as<uint32_t>(ctx->dkeys), as<uint32_t>(ctx->dvals), as<uint32_t>(ctx->dkeys_s),
-                   as<uint32_t>(ctx->dvals_s), d_V, capv, 0, 32, sc, next_epoch(ctx, s), false, ctx->d_err, s);
+                   as<uint32_t>(ctx->dvals_s), d_V, capv, 0, 32, sc, next_epoch(ctx, s), false, true, ctx->d_err, s);
   }
 
   const uint32_t* cnt_sorted = nullptr;
@@ -472,7 +472,7 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
     GSR_TRY_ALLOC(ctx->cnt_sorted, sizeof(uint32_t) * capv);
     StageTimer tm(ctx, GSR_STAGE_TILE_COUNT, s);
     launch_duplicate(as<Rec>(*bo.rec), as<uint32_t>(ctx->dvals_s), nullptr, d_V, capv, cb, 1,
-                     as<uint32_t>(ctx->cnt_sorted), nullptr, nullptr, 4 * ctx->grid_cap, s);
+                     as<uint32_t>(ctx->cnt_sorted), nullptr, nullptr, nullptr, 0, 4 * ctx->grid_cap, s);
     cnt_sorted = as<uint32_t>(ctx->cnt_sorted);
   }
   {
@@ -513,16 +513,18 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   if (P > 0) {
     if (!ensure_sort(ctx, Pc, s)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
     sc = sort_scratch(ctx);
+    const int tb = bits_for(cb.total_tiles);
+    sort_clear_counts(sc, s);  // the pair emitter counts the tile keys' digits
     {
       StageTimer tm(ctx, GSR_STAGE_DUPLICATE, s);
       launch_duplicate(as<Rec>(*bo.rec), as<uint32_t>(ctx->dvals_s), as<uint32_t>(ctx->offsets), d_V, V, cb,
-                       o->tile_cull, nullptr, as<uint32_t>(ctx->pkeys), as<uint32_t>(ctx->pvals), 4 * ctx->grid_cap, s);
+                       o->tile_cull, nullptr, as<uint32_t>(ctx->pkeys), as<uint32_t>(ctx->pvals), sc.hist, tb,
+                       4 * ctx->grid_cap, s);
     }
-    const int tb = bits_for(cb.total_tiles);
     {
       StageTimer tm(ctx, GSR_STAGE_TILE_SORT, s);
       radix_sort_u32(as<uint32_t>(ctx->pkeys), as<uint32_t>(ctx->pvals), as<uint32_t>(ctx->pkeys_s),
-                     as<uint32_t>(*bo.pvals_s), nullptr, P, 0, tb, sc, next_epoch(ctx, s), false, ctx->d_err, s);
+                     as<uint32_t>(*bo.pvals_s), nullptr, P, 0, tb, sc, next_epoch(ctx, s), false, true, ctx->d_err, s);
     }
   }
   {
@@ -621,7 +623,7 @@ void gsr_destroy(gsr_ctx* ctx) {
   ctx->state_pool.clear();
   Buf* all[] = {&ctx->seg_begin, &ctx->seg_start, &ctx->rec, &ctx->dkeys, &ctx->dvals, &ctx->touched,
                 &ctx->owner, &ctx->dkeys_s, &ctx->dvals_s, &ctx->sort_ktmp, &ctx->sort_vtmp,
-                &ctx->sort_hist, &ctx->sort_hist_blocks, &ctx->sort_status, &ctx->sort_counters, &ctx->cnt_sorted, &ctx->offsets,
+                &ctx->sort_hist, &ctx->sort_status, &ctx->cnt_sorted, &ctx->offsets,
                 &ctx->pre_status, &ctx->scan_status, &ctx->misc, &ctx->pkeys, &ctx->pvals, &ctx->pkeys_s, &ctx->pvals_s,
                 &ctx->ranges, &ctx->pix_T, &ctx->pix_n, &ctx->pix_D, &ctx->g2d, &ctx->gaff};
   for (Buf* b : all) release(ctx, *b, nullptr);
@@ -1046,7 +1048,7 @@ gsr_status gsr_sort_pairs_u32(gsr_ctx* ctx, const uint32_t* keys_in, const uint3
   if (!ensure_sort(ctx, n, s)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
   SortScratch sc = sort_scratch(ctx);
   radix_sort_u32(keys_in, vals_in, keys_out, vals_out, nullptr, n, begin_bit, end_bit, sc, next_epoch(ctx, s), false,
-                 ctx->d_err, s);
+                 false, ctx->d_err, s);
   e = cudaGetLastError();
   return e == cudaSuccess ? GSR_OK : cuda_err(ctx, e, "sort launch");
 }

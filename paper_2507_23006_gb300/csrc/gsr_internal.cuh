@@ -125,6 +125,7 @@ struct PreOut {
   uint32_t* v_total;           // out: V
   int* err;
   uint32_t epoch;              // tag of this launch's status words
+  uint32_t* key_counts;        // [4][256] digit counts of the depth keys (for their sort), added to
 };
 
 struct Grad2D {  // per visible record: 12 floats, three float4
@@ -173,25 +174,42 @@ constexpr int kPreTile = kPreThreads * kPreItems;
 
 // Stable radix sort by key bits [begin_bit, end_bit); n taken from *d_n when d_n != nullptr
 // (then max_n bounds it and sizes the launch), else n = max_n.
-constexpr int kMaxHistBlocks = 512;  // blocks of the histogram pass (per-block rows, no atomics)
+// Digit counts [4][256] followed by the four passes' block counters: zeroed together before
+// the keys' digits are counted.
+constexpr int kSortCountWords = 4 * 256 + 4;
 struct SortScratch {
   uint32_t* keys_tmp;
   uint32_t* vals_tmp;
-  uint32_t* hist;                // [4][256] exclusive digit offsets
-  uint32_t* hist_blocks;         // [kMaxHistBlocks][4][256] per-block histograms
+  uint32_t* hist;                // [kSortCountWords]: digit counts per pass, then block counters
   unsigned long long* status;    // [4][tiles][256] epoch-tagged look-back words
-  uint32_t* counters;            // [4]
   int grid_cap;                  // blocks per onesweep launch (resident blocks loop over tiles)
 };
+// Adds key's digits of passes [0, passes) (8 bits each from begin_bit, the last one up to
+// end_bit) to a block's shared counts sh[4][256].
+__device__ __forceinline__ void count_digits(uint32_t key, int begin_bit, int end_bit, int passes, uint32_t* sh) {
+  for (int p = 0; p < passes; ++p) {
+    const int shift = begin_bit + 8 * p;
+    const int width = end_bit - shift < 8 ? end_bit - shift : 8;
+    atomicAdd(&sh[p * 256 + ((key >> shift) & ((1u << width) - 1))], 1u);
+  }
+}
+// Adds a block's nonzero shared counts to the global counts (whole block; the caller syncs
+// before).
+__device__ __forceinline__ void flush_digit_counts(const uint32_t* sh, int passes, uint32_t* hist) {
+  for (int k = threadIdx.x; k < passes * 256; k += blockDim.x)
+    if (sh[k]) atomicAdd(hist + k, sh[k]);
+}
+void sort_clear_counts(const SortScratch& sc, cudaStream_t s);
 constexpr int kSortThreads = 512;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 size_t sort_status_words(long long max_n);  // 64-bit words per pass
 // epoch: tag for this call's status words (nonzero, below 2^30); clear_status: zero the status
-// words first instead of relying on the tag.
+// words first instead of relying on the tag; counts_ready: sc.hist already holds the keys' digit
+// counts (sort_clear_counts, then count_digits / flush_digit_counts in the producing kernel).
 void radix_sort_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
                     const uint32_t* d_n, long long max_n, int begin_bit, int end_bit, const SortScratch& sc,
-                    uint32_t epoch, bool clear_status, int* err, cudaStream_t s);
+                    uint32_t epoch, bool clear_status, bool counts_ready, int* err, cudaStream_t s);
 
 // Exclusive scan of per-record tile counts in depth order: counts[i] = touched[order[i]]
 // (or cnt_sorted[i] when given), offsets[i] out, *p_total = sum. n from *d_n.
@@ -205,7 +223,8 @@ void pair_offsets_scan(const uint32_t* touched, const uint32_t* order, const uin
 // Duplicate-with-keys (warp-cooperative). count_only: writes cnt_sorted[i] (tile-culled counts).
 void launch_duplicate(const Rec* rec, const uint32_t* order, const uint32_t* offsets, const uint32_t* d_n,
                       long long max_n, const CamBatch& cams, int tile_cull, uint32_t* cnt_sorted,
-                      uint32_t* pair_keys, uint32_t* pair_vals, int max_blocks, cudaStream_t s);
+                      uint32_t* pair_keys, uint32_t* pair_vals, uint32_t* key_counts, int key_bits, int max_blocks,
+                      cudaStream_t s);
 void launch_ranges(const uint32_t* sorted_keys, long long P, int n_tiles, uint2* ranges, cudaStream_t s);
 
 struct BlendFwdOut {

@@ -501,6 +501,7 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
   __shared__ float4 s_rec[kPreStage][4];
   __shared__ uint32_t s_meta[kPreStage];  // slot | camera << 16
   __shared__ MlpSmem s_mlp;                // appearance transform, when on
+  __shared__ uint32_t s_digits[4 * 256];   // digit counts of the block's depth keys
   if (threadIdx.x == 0) {
     s_bid = atomicAdd(out.counter, 1u);
     s_count[0] = 0;
@@ -508,6 +509,7 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
   }
   if (kMlp) mlp_load_smem(A, cams.C, s_mlp);  // read after the barrier that ends phase 1a
   if (threadIdx.x < kPreTile / 32) s_unstaged[threadIdx.x] = 0;
+  for (int k = threadIdx.x; k < 4 * 256; k += kPreThreads) s_digits[k] = 0;
   __syncthreads();
   const unsigned bid = s_bid;
   const long long base_i = static_cast<long long>(bid) * kPreTile;
@@ -627,6 +629,8 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
   for (uint32_t e = threadIdx.x; e < n_staged; e += kPreThreads) {
     const uint32_t meta = s_meta[e];
     const uint32_t slot = meta & 0xffffu, c = meta >> 16;
+    // a Gaussian with a record that did not fit the stage has all of its records written below
+    if ((s_unstaged[slot >> 5] >> (slot & 31)) & 1u) continue;
     const long long v = block_base + s_aux[slot] + __popc(s_mask[slot] & ((1u << c) - 1u));
     Rec rr;
     rr.a = s_rec[e][0];
@@ -634,8 +638,13 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
     rr.c = s_rec[e][2];
     rr.d = s_rec[e][3];
     write_record(out, v, rr, base_i + slot);
+    count_digits(__float_as_uint(rr.a.w), 0, 32, 4, s_digits);
   }
-  if (n_rec <= kPreStage) return;  // block-uniform
+  if (n_rec <= kPreStage) {  // block-uniform
+    __syncthreads();
+    flush_digit_counts(s_digits, 4, out.key_counts);
+    return;
+  }
   // records that did not fit the stage: every record of those Gaussians is computed again
   for (uint32_t k = threadIdx.x; k < n_maybe; k += kPreThreads) {
     const uint32_t slot = s_list[k];
@@ -666,9 +675,12 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(GaussArg
       rr.c.x = 2.f * mo[1] * rgb[1];
       rr.c.y = 2.f * mo[2] * rgb[2];
       write_record(out, v, rr, i);
+      count_digits(__float_as_uint(rr.a.w), 0, 32, 4, s_digits);
       ++v;
     }
   }
+  __syncthreads();
+  flush_digit_counts(s_digits, 4, out.key_counts);
 }
 
 // Backward of the projection and colour. One thread per visible record; the thread holding a

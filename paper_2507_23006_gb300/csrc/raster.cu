@@ -70,9 +70,16 @@ template <bool kCull, bool kCount>
 __global__ void __launch_bounds__(256) duplicate_kernel(const Rec* __restrict__ rec, const uint32_t* __restrict__ order,
                                                         const uint32_t* __restrict__ offsets, const uint32_t* d_n,
                                                         long long max_n, CamBatch cams, uint32_t* __restrict__ cnt_sorted,
-                                                        uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals) {
+                                                        uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals,
+                                                        uint32_t* __restrict__ key_counts, int key_bits) {
   __shared__ uint32_t s_cnt[8][32];
+  __shared__ uint32_t s_digits[4 * 256];  // digit counts of the emitted tile keys (for their sort)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int passes = (key_bits + 7) / 8;
+  if (key_counts) {
+    for (int k = threadIdx.x; k < 4 * 256; k += blockDim.x) s_digits[k] = 0;
+    __syncthreads();
+  }
   long long n = static_cast<long long>(*d_n);
   if (n > max_n) n = max_n;
   // warps stride over the records 32 at a time (the grid is sized for the resident blocks, not
@@ -146,20 +153,28 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const Rec* __restrict__ 
       if (!kCount && keep) {
         const uint32_t pos = o_off + base_cnt + before;
         const DevCam& cam = cams.cam[c];
-        pkeys[pos] = static_cast<uint32_t>(cam.tile_off) + ty * cam.tiles_x + tx;
+        const uint32_t key = static_cast<uint32_t>(cam.tile_off) + ty * cam.tiles_x + tx;
+        pkeys[pos] = key;
         pvals[pos] = o_v;
+        if (key_counts) count_digits(key, 0, key_bits, passes, s_digits);
       }
       if (active && lane == 31 - __clz(group)) s_cnt[w][owner] = base_cnt + __popc(kb & group);
       __syncwarp();
     } else if (active) {
       const DevCam& cam = cams.cam[c];
       const uint32_t pos = o_off + q;
-      pkeys[pos] = static_cast<uint32_t>(cam.tile_off) + ty * cam.tiles_x + tx;
+      const uint32_t key = static_cast<uint32_t>(cam.tile_off) + ty * cam.tiles_x + tx;
+      pkeys[pos] = key;
       pvals[pos] = o_v;
+      if (key_counts) count_digits(key, 0, key_bits, passes, s_digits);
     }
   }
   if (kCount && valid) cnt_sorted[i] = s_cnt[w][lane];
   __syncwarp();  // the next round clears s_cnt
+  }
+  if (key_counts) {
+    __syncthreads();
+    flush_digit_counts(s_digits, passes, key_counts);
   }
 }
 
@@ -566,18 +581,19 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
 
 void launch_duplicate(const Rec* rec, const uint32_t* order, const uint32_t* offsets, const uint32_t* d_n,
                       long long max_n, const CamBatch& cams, int tile_cull, uint32_t* cnt_sorted,
-                      uint32_t* pair_keys, uint32_t* pair_vals, int max_blocks, cudaStream_t s) {
+                      uint32_t* pair_keys, uint32_t* pair_vals, uint32_t* key_counts, int key_bits, int max_blocks,
+                      cudaStream_t s) {
   if (max_n <= 0) return;
   const int blocks = static_cast<int>(std::min<long long>((max_n + 255) / 256, std::max(max_blocks, 1)));
   if (cnt_sorted) {
     duplicate_kernel<true, true><<<blocks, 256, 0, s>>>(rec, order, offsets, d_n, max_n, cams, cnt_sorted, nullptr,
-                                                        nullptr);
+                                                        nullptr, nullptr, 0);
   } else if (tile_cull) {
     duplicate_kernel<true, false><<<blocks, 256, 0, s>>>(rec, order, offsets, d_n, max_n, cams, nullptr, pair_keys,
-                                                         pair_vals);
+                                                         pair_vals, key_counts, key_bits);
   } else {
     duplicate_kernel<false, false><<<blocks, 256, 0, s>>>(rec, order, offsets, d_n, max_n, cams, nullptr, pair_keys,
-                                                          pair_vals);
+                                                          pair_vals, key_counts, key_bits);
   }
 }
 

@@ -8,7 +8,9 @@
 // per-digit counts, and takes its global digit offsets from its predecessors by a decoupled
 // look-back whose waits are bounded (a wait that runs out sets an error bit and the block
 // carries on, so the kernel always finishes). Blocks take their tile index from an atomic
-// counter at start, so a block only ever waits for blocks that are already running.
+// counter at start, so a block only ever waits for blocks that are already running. The digit
+// counts of all passes come from one histogram kernel, or from the kernel that produced the
+// keys (count_digits / flush_digit_counts), before the first pass.
 #include <algorithm>
 
 #include "gsr_internal.cuh"
@@ -23,58 +25,20 @@ __device__ __forceinline__ long long device_n(const uint32_t* d_n, long long max
   return n < max_n ? n : max_n;
 }
 
-// Per-block digit histograms of every pass (no atomics on global memory, nothing to clear):
-// block b writes hist_blocks[b][pass][256].
+// Digit counts of every pass: each block counts its keys in shared memory, then adds its
+// nonzero bins to hist[pass][256] (zeroed beforehand) with one atomic each.
 __global__ void __launch_bounds__(256) hist_kernel(const uint32_t* __restrict__ keys, const uint32_t* d_n,
                                                    long long max_n, int begin_bit, int end_bit, int passes,
-                                                   uint32_t* __restrict__ hist_blocks) {
+                                                   uint32_t* __restrict__ hist) {
   __shared__ uint32_t sh[4 * 256];
   for (int k = threadIdx.x; k < 4 * 256; k += blockDim.x) sh[k] = 0;
   __syncthreads();
   const long long n = device_n(d_n, max_n);
   for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-       i += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const uint32_t k = keys[i];
-    for (int p = 0; p < passes; ++p) {
-      const int shift = begin_bit + 8 * p;
-      const int width = min(8, end_bit - shift);
-      atomicAdd(&sh[p * 256 + ((k >> shift) & ((1u << width) - 1))], 1u);
-    }
-  }
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    count_digits(keys[i], begin_bit, end_bit, passes, sh);
   __syncthreads();
-  uint32_t* dst = hist_blocks + static_cast<size_t>(blockIdx.x) * 4 * 256;
-  for (int k = threadIdx.x; k < passes * 256; k += blockDim.x) dst[k] = sh[k];
-}
-
-// Sums the per-block histograms of pass blockIdx.x, writes the exclusive digit offsets to
-// hist[pass][256] and clears the pass's block counter. 1024 threads: four groups of 256 sum
-// every fourth block histogram each (eight loads in flight per thread), then one scan.
-constexpr int kHistScanThreads = 1024;
-__global__ void __launch_bounds__(kHistScanThreads) hist_scan_kernel(const uint32_t* __restrict__ hist_blocks,
-                                                                     int nblocks, uint32_t* __restrict__ hist,
-                                                                     uint32_t* counters) {
-  __shared__ uint32_t s_part[4][256];
-  const int p = blockIdx.x;
-  const int d = threadIdx.x & 255, part = threadIdx.x >> 8;
-  const uint32_t* src = hist_blocks + p * 256 + d;
-  uint32_t x = 0;
-  int b = part;
-  for (; b + 28 < nblocks; b += 32) {
-    uint32_t v[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = __ldg(src + static_cast<size_t>(b + 4 * k) * 4 * 256);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) x += v[k];
-  }
-  for (; b < nblocks; b += 4) x += __ldg(src + static_cast<size_t>(b) * 4 * 256);
-  s_part[part][d] = x;
-  __syncthreads();
-  // the whole block scans; threads past the first 256 add nothing
-  const uint32_t t = threadIdx.x < 256 ? s_part[0][d] + s_part[1][d] + s_part[2][d] + s_part[3][d] : 0u;
-  uint32_t total;
-  const uint32_t e = block_excl_scan(t, &total);
-  if (threadIdx.x < 256) hist[p * 256 + d] = e;
-  if (threadIdx.x == 0) counters[p] = 0;
+  flush_digit_counts(sh, passes, hist);
 }
 
 // Per-digit decoupled look-back of tile `bid` (one thread per digit): publishes the tile's
@@ -139,19 +103,25 @@ __device__ __forceinline__ uint32_t lookback_digit(unsigned long long* status, u
 __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* d_n, long long max_n, int shift, int width,
-    const uint32_t* __restrict__ offsets, unsigned long long* status, uint32_t* counter, uint32_t epoch,
+    const uint32_t* __restrict__ counts, unsigned long long* status, uint32_t* counter, uint32_t epoch,
     int* err) {
   constexpr int kWarps = kSortThreads / 32;
   constexpr int kOut = kSortTile / kSortThreads;  // tile positions each thread writes out
   __shared__ uint32_t s_hist[kWarps][256];
   __shared__ uint32_t s_local[256];  // first tile-local position of each digit
   __shared__ uint32_t s_base[256];   // output position of tile-local position 0 of each digit
+  __shared__ uint32_t s_digit[256];  // first output position of each digit (all keys)
   __shared__ uint32_t s_buf[kSortTile];
   __shared__ uint32_t s_bid;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const long long n = device_n(d_n, max_n);
   const uint32_t dmask = (1u << width) - 1;
   const uint32_t lt = (1u << lane) - 1;
+  {  // the pass's digit counts, scanned by every block for itself
+    uint32_t all;
+    const uint32_t first = block_excl_scan(tid < 256 ? counts[tid] : 0u, &all);
+    if (tid < 256) s_digit[tid] = first;
+  }
   for (;;) {
     for (int k = tid; k < kWarps * 256; k += kSortThreads) (&s_hist[0][0])[k] = 0;
     if (tid == 0) s_bid = atomicAdd(counter, 1u);
@@ -205,7 +175,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
     const uint32_t local = block_excl_scan(sum, &tile_total);  // every thread; digits are the first 256
     if (tid < 256) {
       s_local[tid] = local;
-      s_base[tid] = offsets[tid] + excl - local;
+      s_base[tid] = s_digit[tid] + excl - local;
     }
     __syncthreads();
     uint32_t lp[kSortItems];
@@ -290,6 +260,10 @@ __global__ void __launch_bounds__(kScanThreads) pair_scan_kernel(
 
 }  // namespace
 
+void sort_clear_counts(const SortScratch& sc, cudaStream_t s) {
+  cudaMemsetAsync(sc.hist, 0, sizeof(uint32_t) * kSortCountWords, s);
+}
+
 size_t sort_status_words(long long max_n) {
   const long long tiles = (max_n + kSortTile - 1) / kSortTile;
   return static_cast<size_t>(std::max<long long>(tiles, 1)) * 256;
@@ -297,17 +271,18 @@ size_t sort_status_words(long long max_n) {
 
 void radix_sort_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
                     const uint32_t* d_n, long long max_n, int begin_bit, int end_bit, const SortScratch& sc,
-                    uint32_t epoch, bool clear_status, int* err, cudaStream_t s) {
+                    uint32_t epoch, bool clear_status, bool counts_ready, int* err, cudaStream_t s) {
   if (max_n <= 0 || end_bit <= begin_bit) return;
   const int passes = (end_bit - begin_bit + 7) / 8;
   const long long tiles = (max_n + kSortTile - 1) / kSortTile;
   const size_t words = sort_status_words(max_n);
   const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>(tiles, sc.grid_cap)));
   if (clear_status) cudaMemsetAsync(sc.status, 0, sizeof(unsigned long long) * words * passes, s);
-  const int hblocks = std::max(1, static_cast<int>(std::min<long long>(std::min(sc.grid_cap, kMaxHistBlocks),
-                                                                       (max_n + 4095) / 4096)));
-  hist_kernel<<<hblocks, 256, 0, s>>>(keys_in, d_n, max_n, begin_bit, end_bit, passes, sc.hist_blocks);
-  hist_scan_kernel<<<passes, kHistScanThreads, 0, s>>>(sc.hist_blocks, hblocks, sc.hist, sc.counters);
+  if (!counts_ready) {  // else the producer of the keys has counted their digits
+    sort_clear_counts(sc, s);
+    const int hblocks = std::max(1, static_cast<int>(std::min<long long>(sc.grid_cap, (max_n + 4095) / 4096)));
+    hist_kernel<<<hblocks, 256, 0, s>>>(keys_in, d_n, max_n, begin_bit, end_bit, passes, sc.hist);
+  }
   // ping-pong so that the last pass lands in keys_out; the inputs are never written
   const uint32_t* ksrc = keys_in;
   const uint32_t* vsrc = vals_in;
@@ -318,7 +293,7 @@ void radix_sort_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
     const int shift = begin_bit + 8 * p;
     const int width = std::min(8, end_bit - shift);
     onesweep_kernel<<<grid, kSortThreads, 0, s>>>(ksrc, vsrc, kdst, vdst, d_n, max_n, shift, width, sc.hist + 256 * p,
-                                                  sc.status + words * p, sc.counters + p, epoch, err);
+                                                  sc.status + words * p, sc.hist + 4 * 256 + p, epoch, err);
     ksrc = kdst;
     vsrc = vdst;
   }

@@ -23,15 +23,13 @@ namespace {
 constexpr long long kMaxN = 1ll << 18;
 constexpr long long kMaxTiles = (kMaxN + kSortTile - 1) / kSortTile;
 // Layout in 32-bit words; the look-back status words are 64-bit, so their offset is even.
-constexpr int kNoAllocHistBlocks = 64;  // histogram blocks: ceil(n / 4096) <= 64 for n <= 2^18
+constexpr int kNoAllocBlocks = 64;  // resident blocks per launch: ceil(n / 4096) <= 64 for n <= 2^18
 constexpr size_t kKeysTmp = 0;
 constexpr size_t kValsTmp = kKeysTmp + kMaxN;
-constexpr size_t kHist = kValsTmp + kMaxN;
-constexpr size_t kHistBlocks = kHist + 4 * 256;
-constexpr size_t kStatus = kHistBlocks + 4 * 256 * kNoAllocHistBlocks;
-constexpr size_t kCounters = kStatus + 2 * 4 * kMaxTiles * 256;
-constexpr size_t kErrWord = kCounters + 4;
-constexpr size_t kWords = kErrWord + 4;  // about 2.9 MB in all
+constexpr size_t kHist = kValsTmp + kMaxN;  // digit counts and block counters
+constexpr size_t kStatus = (kHist + kSortCountWords + 1) & ~static_cast<size_t>(1);
+constexpr size_t kErrWord = kStatus + 2 * 4 * kMaxTiles * 256;
+constexpr size_t kWords = kErrWord + 4;  // about 2.6 MB in all
 static_assert(kStatus % 2 == 0, "64-bit status words need an even word offset");
 
 static __device__ __align__(256) uint32_t g_sort_scratch[kWords];
@@ -93,15 +91,13 @@ extern "C" gsr_status gsr_sort_pairs_u32_noalloc(const uint32_t* keys_in, const 
   sc.keys_tmp = base + kKeysTmp;
   sc.vals_tmp = base + kValsTmp;
   sc.hist = base + kHist;
-  sc.hist_blocks = base + kHistBlocks;
   sc.status = reinterpret_cast<unsigned long long*>(base + kStatus);
-  sc.counters = base + kCounters;
-  sc.grid_cap = std::min(2 * sms, kNoAllocHistBlocks);
+  sc.grid_cap = std::min(2 * sms, kNoAllocBlocks);
   int* err = device_err ? reinterpret_cast<int*>(device_err) : reinterpret_cast<int*>(base + kErrWord);
-  // Every call clears the look-back status words before its first kernel (a stream-ordered
-  // memset, no allocation); its histogram kernels overwrite the histograms and reset the block
-  // counters; the ping-pong buffers need no clearing.
-  radix_sort_u32(keys_in, vals_in, keys_out, vals_out, nullptr, n, begin_bit, end_bit, sc, 1u, true, err, s);
+  // Every call clears the look-back status words, the digit counts and the block counters
+  // before its first kernel (stream-ordered memsets, no allocation); the ping-pong buffers need
+  // no clearing.
+  radix_sort_u32(keys_in, vals_in, keys_out, vals_out, nullptr, n, begin_bit, end_bit, sc, 1u, true, false, err, s);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GSR_OK : GSR_ERR_CUDA;
 }
