@@ -763,14 +763,15 @@ def run_serve_full(args):
 
 def kernels_per_step(tile_cull, info):
     """Kernels of ours launched per fwd+bwd step (memsets excluded)."""
-    k = 1                      # preprocess
-    k += 2 + 4                 # depth sort: histogram, histogram scan, 4 onesweep passes
+    k = 1                      # preprocess (also counts the depth keys' digits)
+    k += 4                     # depth sort: 4 onesweep passes
     k += 1 if tile_cull else 0  # tile-culled counts
     k += 1                     # pair scan
     tiles = int(info["n_tiles"])
     bits = max(1, math.ceil(math.log2(max(tiles, 2))))
-    k += 1 + 2 + (bits + 7) // 8 + 1  # duplicate, tile sort (hist, scan, passes), ranges
+    k += 1 + (bits + 7) // 8 + 1  # duplicate (counts the tile keys' digits), tile sort passes, ranges
     k += 1                     # blend forward
+    k += 1                     # gradient zero fill (side stream)
     k += 1 + 1                 # blend backward, preprocess backward
     return k
 

@@ -44,9 +44,8 @@ __device__ __forceinline__ float tile_min_maha(float mx, float my, float a, floa
   return best;
 }
 
-// The blend kernels run 128 threads per 16x16 tile; thread t owns column t % 16 and rows
-// 2 (t / 16) and 2 (t / 16) + 1, so warp w covers rows 4w .. 4w+3. Records are staged 256 at a
-// time.
+// The blend kernels run 128 threads per 16x16 tile (four warps of 8x8 pixels, below). Records
+// are staged 256 at a time.
 constexpr int kBlendThreads = 128;
 constexpr int kBlendWarps = kBlendThreads / 32;
 constexpr int kBatch = 256;

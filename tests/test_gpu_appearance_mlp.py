@@ -141,3 +141,52 @@ def test_empty_and_invisible(ctx):
     assert st.info()["n_visible"] == 0
     for k in ("gauss_embed", "image_embed", "mlp_params", "means"):
         assert torch.count_nonzero(gr[k]) == 0, k
+
+
+def test_fp16_storage_with_the_transform(ctx):
+    """FP16 attributes and SH with the transform on: records and images against the oracle on
+    the dequantised inputs (what the kernels compute with)."""
+    cams = _cams()[:2]
+    scene, mlp, g32 = _setup(6000, 17, len(cams))
+    g = native.Gaussians.from_scene(scene, attr_dtype=torch.float16, sh_dtype=torch.float16)
+    g.mlp = g32.mlp
+    deq = scenes.Scene(scene.means, g.scales.float().cpu().numpy(), g.quats.float().cpu().numpy(),
+                       g.opacities.float().cpu().numpy(), g.sh.float().cpu().numpy(), 3)
+    nopts, oopts = pu.opts_pair(bg=(0.1, 0.2, 0.3))
+    out, st = native.render_forward(ctx, g, cams, nopts)
+    ctx.sync_check()
+    sa = pu.state_arrays(st)
+    res = oracle.render(deq, cams, oopts, mlp=mlp)
+    _check_records(sa, deq, cams, oopts, res.gmark, mlp=mlp)
+    _check_images(out, res, cams, 15.0)
+
+
+def test_segments_with_the_transform(ctx):
+    """A segment list renders the listed Gaussians in list order: the same images as the
+    concatenated arrays (embeddings sliced with them), bit for bit, and the same gradients
+    (scattered back to the rows of the full arrays; zero elsewhere)."""
+    cams = _cams()[:2]
+    scene, mlp, g = _setup(5000, 19, len(cams))
+    segs = [(3000, 1200), (0, 1700)]
+    g.segments = segs
+    idx = torch.cat([torch.arange(b, b + c) for b, c in segs]).cuda()
+    flat = native.Gaussians(*(getattr(g, k)[idx].contiguous() for k in ("means", "scales", "quats", "opacities", "sh")),
+                            3, None, native.AppearanceMLP(g.mlp.gauss_embed[idx].contiguous(), g.mlp.image_embed,
+                                                          g.mlp.params))
+    nopts, _ = pu.opts_pair(bg=(0.1, 0.2, 0.3))
+    out_s, st_s = native.render_forward(ctx, g, cams, nopts)
+    out_f, st_f = native.render_forward(ctx, flat, cams, nopts)
+    ctx.sync_check()
+    for k in ("rgb", "alpha", "depth_acc"):
+        assert torch.equal(out_s[k], out_f[k]), k
+    w = torch.randn(out_s["rgb"].shape, generator=torch.Generator(device="cuda").manual_seed(5), device="cuda")
+    gs = native.render_backward(ctx, g, cams, st_s, dict(rgb=w), nopts)
+    gf = native.render_backward(ctx, flat, cams, st_f, dict(rgb=w), nopts)
+    ctx.sync_check()
+    for k in ("gauss_embed", "means", "sh"):
+        full = gs[k]
+        assert torch.count_nonzero(full[torch.tensor(sorted(set(range(g.n)) - set(idx.tolist())), device="cuda")]) == 0
+        a, b = full[idx], gf[k]
+        assert float(torch.linalg.norm(a - b)) <= 1e-5 * float(torch.linalg.norm(b)), k
+    for k in ("image_embed", "mlp_params"):
+        assert float(torch.linalg.norm(gs[k] - gf[k])) <= 1e-5 * float(torch.linalg.norm(gf[k])), k
