@@ -70,6 +70,7 @@ struct gsr_ctx {
   bool prezero_pending = false;    // fill queued (ev_prezero marks its end), not used yet
   int grid_cap = 304;  // resident blocks of the looping scan / sort kernels (2 per SM)
   int fill_blocks = 76;  // blocks of the gradient zero fill (one per two SMs)
+  bool pre_dense = false;  // the last binning kept over a quarter of its (camera, Gaussian) pairs
   // default allocator: a context-owned stream-ordered pool (growth and release never
   // synchronise the device, which matters when several contexts serve concurrently)
   cudaMemPool_t pool = nullptr;
@@ -453,7 +454,7 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   po.epoch = next_epoch(ctx, s);
   {
     StageTimer tm(ctx, GSR_STAGE_PREPROCESS, s);
-    launch_preprocess_fwd(ga, cb, o->eps2d, o->antialiased, po, pre_blocks, s);
+    launch_preprocess_fwd(ga, cb, o->eps2d, o->antialiased, po, pre_blocks, ctx->pre_dense, s);
   }
   // A requested gradient fill starts here: the stages up to the end of the forward blend move
   // little memory, the preprocess before them much.
@@ -502,6 +503,8 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   if (P >= (1ll << 30)) return set_err(ctx, GSR_ERR_UNSUPPORTED, "more than 2^30 (tile, Gaussian) pairs");
   *V_out = V;
   *P_out = P;
+  // the next preprocess picks its variant from this launch's survivor ratio
+  ctx->pre_dense = 4 * V > N * C;
 
   // duplicate, sort by tile, ranges
   const long long Pc = std::max<long long>(P, 1);

@@ -146,8 +146,12 @@ struct ParamGrads {
 
 // ---- host-side launchers (one per translation unit) -------------------------------------
 
+// dense: many Gaussians expected to survive the culls (picks the variant budgeted for the
+// per-record work over the one budgeted for the scan over all Gaussians; results are the same).
 void launch_preprocess_fwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased,
-                           const PreOut& out, int blocks, cudaStream_t s);
+                           const PreOut& out, int blocks, bool dense, cudaStream_t s);
+void launch_preprocess_fwd_dense(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased,
+                                 const PreOut& out, int blocks, cudaStream_t s);
 constexpr int kFillSpans = 8;
 struct FillSpans {
   float* ptr[kFillSpans];

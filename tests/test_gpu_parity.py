@@ -466,3 +466,26 @@ def test_street_block_full_size_sampled(ctx, street):
     ref = oracle.backward(scene, [cam], up, oopts, tile_subset=tiles)
     for k in ("means", "scales", "quats", "opacities", "sh"):
         pu.grad_close(gg[k], ref[k], k)
+
+
+def test_preprocess_variants_agree():
+    """The preprocess has two register budgets (for launches where few Gaussians survive the
+    culls, and for dense ones), picked from the previous launch's survivor ratio: a fresh context
+    renders a dense scene first with the sparse variant, then with the dense one; the records
+    and images are the same bits."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c2 = native.Context(0)
+    scene, cam = pu.scene_box(6000, seed=23)
+    nopts, _ = pu.opts_pair(bg=(0.1, 0.2, 0.3))
+    g = native.Gaussians.from_scene(scene)
+    out1, st1 = native.render_forward(c2, g, [cam], nopts)
+    rec1 = pu.state_arrays(st1)["rec"]
+    out2, st2 = native.render_forward(c2, g, [cam], nopts)
+    rec2 = pu.state_arrays(st2)["rec"]
+    c2.sync_check()
+    assert st1.info()["n_visible"] > 0.25 * scene.n  # dense: the second launch took the other variant
+    np.testing.assert_array_equal(rec1.view(np.uint32), rec2.view(np.uint32))
+    for k in ("rgb", "alpha", "depth_acc"):
+        assert torch.equal(out1[k], out2[k]), k
+    c2.close()
