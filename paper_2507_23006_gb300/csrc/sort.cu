@@ -4,8 +4,8 @@
 // The sort orders the binned (tile, Gaussian) pairs (the "tile-based" rasterizer of Sec. 3.4.2
 // and 3.1): first the visible records by depth, then the pairs stably by tile, which together
 // give the (tile, depth, index) order of the blend. Each pass reads every key once: a block
-// ranks its 4096 keys by the pass's 8-bit digit with warp match-any (stable), publishes its
-// per-digit counts, and takes its global digit offsets from its predecessors by a decoupled
+// ranks its 4096 keys by the pass's 8-bit digit (stable: one warp ballot per digit bit finds
+// the lanes with equal digits), publishes its per-digit counts, and takes its global digit offsets from its predecessors by a decoupled
 // look-back whose waits are bounded (a wait that runs out sets an error bit and the block
 // carries on, so the kernel always finishes). Blocks take their tile index from an atomic
 // counter at start, so a block only ever waits for blocks that are already running. The digit
