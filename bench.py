@@ -118,12 +118,28 @@ class ClockSampler:
         return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons), samples=len(sm))
 
 
-def sources_sha256():
-    """Hash of the CUDA sources and the public header: a stored counter is only valid for it."""
+# CUDA sources each stage's kernels are built from (besides the shared headers): a stored DRAM
+# counter stays valid while these files are unchanged.
+KERNEL_SOURCES = {
+    "blend_fwd": ["raster.cu"],
+    "blend_bwd": ["raster.cu"],
+    "preprocess": ["preprocess_fwd.cuh", "preprocess.cu", "preprocess_dense.cu"],
+    "preprocess_bwd": ["preprocess_fwd.cuh", "preprocess.cu"],
+}
+COMMON_SOURCES = ["gsr_internal.cuh", "scan_util.cuh"]
+
+
+def sources_sha256(kernel=None):
+    """Hash of the CUDA sources of `kernel` (all of them when None) and the public header: a
+    stored counter is only valid for it."""
     import glob
     import hashlib
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_2507_23006_gb300", "csrc", "*.cu*")))
+    csrc = os.path.join(ROOT, "paper_2507_23006_gb300", "csrc")
+    if kernel is None:
+        files = sorted(glob.glob(os.path.join(csrc, "*.cu*")))
+    else:
+        files = [os.path.join(csrc, f) for f in sorted(COMMON_SOURCES + KERNEL_SOURCES[kernel])]
     for f in files + [os.path.join(ROOT, "include", "gsr.h")]:
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
@@ -133,17 +149,19 @@ def sources_sha256():
 
 def stored_traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` on `workload` from the committed ncu capture
-    (profiles/traffic.json), or None when there is none for the current sources."""
+    (profiles/traffic.json), or None when there is none for the kernel's current sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    if rec.get("sources_sha256") != sources_sha256() or rec.get("workload") != workload:
-        return None
     k = rec.get("kernels", {}).get(kernel)
-    return None if k is None else float(k["dram_bytes_per_launch"])
+    if rec.get("workload") != workload or k is None or kernel not in KERNEL_SOURCES:
+        return None
+    if k.get("sources_sha256") != sources_sha256(kernel):
+        return None
+    return float(k["dram_bytes_per_launch"])
 
 
 def peaks():
