@@ -1,6 +1,6 @@
 // Per-Gaussian preprocessing (projection, colour, culling) and its backward pass.
 //
-// Forward (Sec. 3.1: "the 3D Gaussians are first projected onto the image plane"):
+// Forward (Sec. 3.1, the projection of each 3D Gaussian to a 2D one before blending):
 //   Sigma = R S S^T R^T (Eq. 1) from the quaternion and scale, then for every camera of the
 //   launch t = W mu + t_cam, T = J W with J the perspective Jacobian at the clamped direction,
 //   Sigma2D = T Sigma T^T + eps I, the Mip-Splatting opacity compensation (Sec. 3.5.4), the
