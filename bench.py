@@ -130,17 +130,17 @@ COMMON_SOURCES = ["gsr_internal.cuh", "scan_util.cuh"]
 
 
 def sources_sha256(kernel=None):
-    """Hash of the CUDA sources of `kernel` (all of them when None) and the public header: a
-    stored counter is only valid for it."""
+    """Hash of the CUDA sources of `kernel` (its files and the internal headers; when None, every
+    CUDA source and the public header): a stored counter is only valid for it."""
     import glob
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2507_23006_gb300", "csrc")
     if kernel is None:
-        files = sorted(glob.glob(os.path.join(csrc, "*.cu*")))
+        files = sorted(glob.glob(os.path.join(csrc, "*.cu*"))) + [os.path.join(ROOT, "include", "gsr.h")]
     else:
         files = [os.path.join(csrc, f) for f in sorted(COMMON_SOURCES + KERNEL_SOURCES[kernel])]
-    for f in files + [os.path.join(ROOT, "include", "gsr.h")]:
+    for f in files:
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())

@@ -208,13 +208,20 @@ gsr_status gsr_render_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_ca
                               gsr_stream stream);
 
 /* Backward pass: gradients of L given dL/d(outputs). g, cams, n_cams and opts must be those of
- * the forward that produced `state`, with the same array contents. Asynchronous. */
+ * the forward that produced `state`, with the same array contents. Every gradient array of
+ * `grads` is overwritten (not accumulated into); rows of Gaussians without a record are zero.
+ * With g->mlp set, grads->gauss_embed, image_embed and mlp_params are required and receive the
+ * appearance transform's gradients (Sec. 3.5.1); the records' opacity and colour gradients are
+ * carried through the transform before the projection backward. Asynchronous. Errors:
+ * GSR_ERR_INVALID_ARG (null or mismatched inputs, a null gradient array), GSR_ERR_OOM,
+ * GSR_ERR_CUDA, GSR_ERR_DEVICE_TIMEOUT (recompute mode: a bounded wait of the re-run binning). */
 gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_camera* cams, int32_t n_cams,
                                const gsr_opts* opts, const gsr_fwd_state* state, const gsr_out_grads* dout,
                                const gsr_param_grads* grads, gsr_stream stream);
 
 /* Zeroes the parameter-gradient arrays of `grads` (means, scales, quats, opacities, sh and, when
- * not NULL, absgrad; sized for g->n Gaussians and g->sh_coeffs as in gsr_render_backward) ahead
+ * not NULL, absgrad and, with g->mlp set, gauss_embed; sized for g->n Gaussians and g->sh_coeffs
+ * as in gsr_render_backward; the backward zeroes the small image_embed and mlp_params itself) ahead
  * of the backward pass. No counterpart in the paper: it moves the gradient initialisation that
  * gsr_render_backward otherwise does itself to an earlier point, so that this memory-bound fill
  * (236 bytes per Gaussian in FP32) runs beside a forward pass, whose stages leave most of the
