@@ -60,7 +60,6 @@ def parse():
     p.add_argument("--serve-full", action="store_true",
                    help="also run the serving configuration at its own sizes (20M/6M/1.5M levels, 30 s trace)")
     p.add_argument("--serve-full-seconds", type=float, default=30.0)
-    p.add_argument("--cpu-tiles", type=int, default=24)
     return p.parse_args()
 
 
@@ -213,43 +212,23 @@ def make_workload(n, width, height, rank=0):
     return scene, cam
 
 
-def cpu_reference(scene, cam, tile_cull, n_tiles_sample, seed=0):
-    """FP64 oracle fwd+bwd on a bounded sample: the full preprocess/binning of the frame plus
-    n_tiles_sample random tiles composited forward and backward, extrapolated by tile count."""
+def cpu_reference(scene, cam, tile_cull, seed=0):
+    """The FP64 oracle's fwd+bwd of the whole frame (preprocess, binning and compositing of every
+    tile, then the backward with random upstream gradients on every pixel), timed as it stands
+    on the host's cores."""
     import oracle
     opts = oracle.Opts(tile_cull=bool(tile_cull))
-    tiles_x = (cam.width + 15) // 16
-    tiles_y = (cam.height + 15) // 16
-    T = tiles_x * tiles_y
-    rng = np.random.default_rng(seed)
-    tiles = rng.choice(T, size=min(n_tiles_sample, T), replace=False)
-    npix = cam.width * cam.height
-    up = np.zeros((npix, 6))
-    pix = []
-    for t in tiles:
-        ty, tx = divmod(int(t), tiles_x)
-        for y in range(ty * 16, min(ty * 16 + 16, cam.height)):
-            pix.extend(range(y * cam.width + tx * 16, y * cam.width + min(tx * 16 + 16, cam.width)))
-    up[np.array(pix)] = rng.normal(size=(len(pix), 6))
+    T = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
+    up = np.random.default_rng(seed).normal(size=(cam.width * cam.height, 6))
     t0 = time.perf_counter()
-    oracle.render(scene, [cam], opts, tile_subset=np.zeros(0, np.int64), want_pairs=False)
-    t_bin = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.render(scene, [cam], opts, tile_subset=tiles, want_pairs=False)
+    oracle.render(scene, [cam], opts, want_pairs=False)
     t_fwd = time.perf_counter() - t0
     t0 = time.perf_counter()
-    oracle.backward(scene, [cam], up, opts, tile_subset=np.zeros(0, np.int64))
-    t_bwd0 = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.backward(scene, [cam], up, opts, tile_subset=tiles)
+    oracle.backward(scene, [cam], up, opts)
     t_bwd = time.perf_counter() - t0
-    per_tile_f = max(t_fwd - t_bin, 0.0) / len(tiles)
-    per_tile_b = max(t_bwd - t_bwd0, 0.0) / len(tiles)
-    step_s = t_bin + per_tile_f * T + t_bwd0 + per_tile_b * T
-    return dict(ms_per_step=step_s * 1e3, sample_s=t_bin + t_fwd + t_bwd0 + t_bwd, cores=oracle.num_threads(),
-                sample=(f"full FP64 preprocess+binning of all {scene.n} Gaussians, forward and backward, plus "
-                        f"{len(tiles)} of {T} tiles composited forward and backward; extrapolated to the "
-                        f"frame by tile count"))
+    return dict(ms_per_step=(t_fwd + t_bwd) * 1e3, sample_s=t_fwd + t_bwd, cores=oracle.num_threads(),
+                sample=(f"the whole frame: FP64 preprocess and binning of all {scene.n} Gaussians and "
+                        f"compositing of all {T} tiles, forward and backward"))
 
 
 def run_reference(args, rank, world):
@@ -260,7 +239,7 @@ def run_reference(args, rank, world):
     cores = None
     sample = ""
     for k in range(args.warmup + args.steps):
-        r = cpu_reference(scene, cam, args.tile_cull, max(4, args.cpu_tiles // 3), seed=k)
+        r = cpu_reference(scene, cam, args.tile_cull, seed=k)
         cores, sample = r["cores"], r["sample"]
         if k >= args.warmup:
             steps.append(r["ms_per_step"])
@@ -641,7 +620,7 @@ def run_ours(args, rank, world, local_rank):
                                             fp32_peak, sms * 16 * sm_mhz * 1e6, hbm, ms)
     cpu = None
     if not args.no_cpu_baseline:
-        r = cpu_reference(scene, cam, args.tile_cull, args.cpu_tiles)
+        r = cpu_reference(scene, cam, args.tile_cull)
         cpu = dict(value=r["ms_per_step"], unit="ms/step", cores=r["cores"], kind="oracle", sample=r["sample"],
                    sample_seconds=round(r["sample_s"], 1))
     value = job_ms_per_step(ms, world)
