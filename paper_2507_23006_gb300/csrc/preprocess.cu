@@ -22,7 +22,9 @@ namespace {
 // Gaussian's first record walks all of that Gaussian's cameras (its records are consecutive),
 // accumulates the parameter gradients in registers and writes the Gaussian's rows once.
 template <typename AT, typename ST>
-__global__ void __launch_bounds__(kBwdThreads) preprocess_bwd_kernel(
+// Budgeted for three resident blocks per SM (168 registers, some spills): more warps in flight
+// hide more of its scattered loads and stores than the spills cost.
+__global__ void __launch_bounds__(kBwdThreads, 3) preprocess_bwd_kernel(
     GaussArgs A, CamBatch cams, float eps, int aa, long long V, const Rec* __restrict__ rec,
     const uint32_t* __restrict__ owner, const Grad2D* __restrict__ g2d, ParamGrads out) {
   const long long v0 = static_cast<long long>(blockIdx.x) * kBwdThreads + threadIdx.x;
