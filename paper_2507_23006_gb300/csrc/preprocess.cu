@@ -13,6 +13,8 @@
 // camera) order, with the block offsets from a single-pass chained scan (Merrill & Garland
 // decoupled look-back) whose waits are bounded; within one camera the compacted index grows
 // with the Gaussian index, which gives the depth sort its tie-break.
+#include <atomic>
+
 #include "preprocess_fwd.cuh"
 
 namespace gsr {
@@ -443,13 +445,16 @@ void launch_zero_fill(const FillSpans& f, int blocks, cudaStream_t s) {
 void launch_mlp_bwd(const GaussArgs& g, const CamBatch& cams, long long V, const Rec* rec, const uint32_t* owner,
                     Grad2D* g2d, float* g_gemb, float* g_iemb, float* g_params, int blocks, cudaStream_t s) {
   if (V <= 0 || !g.mlp) return;
-  static uint64_t attr_set = 0;  // one bit per device: the attribute is set in each device's context
+  // one bit per device: the attribute is set in each device's context (contexts on several host
+  // threads may get here at once; setting it twice is harmless)
+  static std::atomic<uint64_t> attr_set{0};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 64 || !((attr_set >> dev) & 1u)) {
-    cudaFuncSetAttribute(mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(sizeof(MlpBwdSmem)));
-    if (dev < 64) attr_set |= 1ull << dev;
+  if (dev >= 64 || !((attr_set.load(std::memory_order_relaxed) >> dev) & 1u)) {
+    if (cudaFuncSetAttribute(mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(sizeof(MlpBwdSmem))) == cudaSuccess &&
+        dev < 64)
+      attr_set.fetch_or(1ull << dev, std::memory_order_relaxed);
   }
   const long long need = (V + kBwdThreads - 1) / kBwdThreads;
   const int grid = static_cast<int>(need < blocks ? need : blocks);
