@@ -12,6 +12,9 @@
 //     filter) the opacity is scaled by sqrt(det(Sigma2D) / det(Sigma2D + eps I)).
 //   * Colour from real spherical harmonics of degree <= 3, built here from the definition
 //     (associated Legendre functions via Bonnet's recurrence and Re/Im of (x + i y)^m).
+//   * Sec. 3.5.1 (optional): the per-Gaussian appearance transform, an MLP of the Gaussian's
+//     and the image's embeddings that scales each Gaussian's colour and opacity (section
+//     "Appearance transform" below).
 //   * Tile binning: a Gaussian lands in every 16x16 tile of its 3-sigma rectangle; with
 //     tile culling on (Sec. 3.4.2, StopThePop) a tile is dropped when the largest opacity the
 //     Gaussian can reach at any pixel centre of that tile is below 1/255.
