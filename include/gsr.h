@@ -77,6 +77,10 @@ typedef struct gsr_appearance_mlp {
   const float* image_embed;  /* [n_cams,32]: one per camera of the launch, in camera order */
   const float* params;       /* [1700]: w1 [32][48] | b1 [32] | w2 [4][32] | b2 [4], row-major;
                                 hidden = ReLU(w1 [l_G ; l_I] + b1), out = sigmoid(w2 hidden + b2) */
+  /* Or, for rendering only: the outputs [n,4] of every Gaussian for one image embedding, from
+   * gsr_appearance_cache (16-byte aligned). When set, the three arrays above are not read, every
+   * camera of the launch uses these outputs, and gsr_render_backward refuses the struct. */
+  const float* cached;
 } gsr_appearance_mlp;
 
 /* Gaussians (Sec. 3.1, Eq. 1), structure of arrays, all device memory.
@@ -245,6 +249,15 @@ gsr_status gsr_state_copy(const gsr_fwd_state* state, int32_t which, void* dst, 
 /* Waits for `stream` and reports any error recorded by a bounded device wait since the last
  * forward began (GSR_ERR_DEVICE_TIMEOUT), then clears it. */
 gsr_status gsr_sync_check(gsr_ctx* ctx, gsr_stream stream);
+
+/* Evaluates the appearance transform (Sec. 3.5.1) of every Gaussian of g (array order, segments
+ * ignored) for the image embedding in row `image` of g->mlp->image_embed, into out [g->n,4]
+ * (device memory, 16-byte aligned). The paper notes that these offsets can be kept while the
+ * image embedding is unchanged; passing them as g->mlp->cached renders without evaluating the
+ * transform, with the same bits as evaluating it for a camera with that embedding. Needs
+ * g->mlp's gauss_embed, image_embed and params; `image` must be a row of image_embed.
+ * Asynchronous. Errors: GSR_ERR_INVALID_ARG (null or misaligned arrays, image < 0). */
+gsr_status gsr_appearance_cache(gsr_ctx* ctx, const gsr_gaussians* g, int32_t image, float* out, gsr_stream stream);
 
 /* ---- profiling ------------------------------------------------------------------------- */
 

@@ -246,8 +246,10 @@ gsr_status validate(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_camera* cams
   if (g->attr_dtype < 0 || g->attr_dtype > 2 || g->sh_dtype < 0 || g->sh_dtype > 2)
     return set_err(ctx, GSR_ERR_INVALID_ARG, "unknown dtype");
   if (g->nsegs < 0 || (g->nsegs > 0 && !g->segs)) return set_err(ctx, GSR_ERR_INVALID_ARG, "bad segment list");
-  if (g->mlp && (!g->mlp->image_embed || !g->mlp->params || (g->n > 0 && !g->mlp->gauss_embed)))
+  if (g->mlp && !g->mlp->cached && (!g->mlp->image_embed || !g->mlp->params || (g->n > 0 && !g->mlp->gauss_embed)))
     return set_err(ctx, GSR_ERR_INVALID_ARG, "null appearance-transform array");
+  if (g->mlp && g->mlp->cached && reinterpret_cast<uintptr_t>(g->mlp->cached) % 16 != 0)
+    return set_err(ctx, GSR_ERR_INVALID_ARG, "cached appearance outputs must be 16-byte aligned");
   for (int s = 0; s < g->nsegs; ++s) {
     const gsr_segment& sg = g->segs[s];
     if (sg.begin < 0 || sg.count < 0 || sg.begin + sg.count > g->n)
@@ -368,9 +370,11 @@ void set_gauss_fields(const gsr_gaussians* g, GaussArgs& ga) {
   ga.sh_dtype = g->sh_dtype;
   ga.quat_vec4 = g->attr_dtype == GSR_F32 && (reinterpret_cast<uintptr_t>(g->quats) % 16 == 0);
   ga.sh_vec4 = g->sh_dtype == GSR_F32 && (reinterpret_cast<uintptr_t>(g->sh) % 16 == 0) && ((3 * g->sh_coeffs) % 4 == 0);
-  ga.gemb = g->mlp ? g->mlp->gauss_embed : nullptr;
-  ga.iemb = g->mlp ? g->mlp->image_embed : nullptr;
-  ga.mlp = g->mlp ? g->mlp->params : nullptr;
+  const bool eval = g->mlp && !g->mlp->cached;
+  ga.gemb = eval ? g->mlp->gauss_embed : nullptr;
+  ga.iemb = eval ? g->mlp->image_embed : nullptr;
+  ga.mlp = eval ? g->mlp->params : nullptr;
+  ga.mlp_cached = g->mlp ? g->mlp->cached : nullptr;
 }
 
 gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb, const gsr_opts* o, BinOut bo,
@@ -774,6 +778,26 @@ bool same_spans(const FillSpans& a, const FillSpans& b) {
 
 }  // namespace
 
+gsr_status gsr_appearance_cache(gsr_ctx* ctx, const gsr_gaussians* g, int32_t image, float* out, gsr_stream stream) {
+  if (!ctx) return GSR_ERR_INVALID_ARG;
+  if (!g || !g->mlp || !out || image < 0 || g->n < 0)
+    return set_err(ctx, GSR_ERR_INVALID_ARG, "null gaussians, transform or output, or a negative image row");
+  const gsr_appearance_mlp* m = g->mlp;
+  if (!m->image_embed || !m->params || (g->n > 0 && !m->gauss_embed))
+    return set_err(ctx, GSR_ERR_INVALID_ARG, "null appearance-transform array");
+  if (reinterpret_cast<uintptr_t>(out) % 16 != 0)
+    return set_err(ctx, GSR_ERR_INVALID_ARG, "output must be 16-byte aligned");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  GaussArgs ga{};
+  ga.gemb = m->gauss_embed;
+  ga.iemb = m->image_embed + static_cast<size_t>(kEmbI) * image;
+  ga.mlp = m->params;
+  launch_mlp_cache(ga, g->n, out, 4 * ctx->grid_cap, reinterpret_cast<cudaStream_t>(stream));
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GSR_OK : cuda_err(ctx, e, "appearance cache launch");
+}
+
 gsr_status gsr_param_grads_zero(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_param_grads* grads,
                                 gsr_stream stream) {
   if (!ctx) return GSR_ERR_INVALID_ARG;
@@ -801,6 +825,8 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
     return set_err(ctx, GSR_ERR_INVALID_ARG, "null state, upstream or gradient struct");
   if (g->n > 0 && (!grads->means || !grads->scales || !grads->quats || !grads->opacities || !grads->sh))
     return set_err(ctx, GSR_ERR_INVALID_ARG, "null parameter gradient array");
+  if (g->mlp && g->mlp->cached)
+    return set_err(ctx, GSR_ERR_UNSUPPORTED, "cached appearance outputs are for rendering only");
   if (g->mlp && (!grads->image_embed || !grads->mlp_params || (g->n > 0 && !grads->gauss_embed)))
     return set_err(ctx, GSR_ERR_INVALID_ARG, "null appearance-transform gradient array");
   const long long N = render_count(g);

@@ -104,6 +104,7 @@ struct GaussArgs {
   const float* gemb;   // [n][16]
   const float* iemb;   // [C][32]
   const float* mlp;    // [kMlpParams]
+  const float* mlp_cached;  // [n][4] outputs for one image embedding (rendering), or NULL
 };
 
 // Appearance transform sizes (the paper's): l_G 16, l_I 32, hidden 32, outputs 4.
@@ -165,6 +166,8 @@ void launch_zero_fill(const FillSpans& f, int blocks, cudaStream_t s);
 // those of the untransformed ones (in place in g2d), adds l_G's gradient to g_gemb (atomics; rows
 // zeroed before) and sums the gradients of the weights and image embeddings into g_params and
 // g_iemb (atomics; zeroed before).
+// The appearance transform of Gaussians [0, n) for the image embedding at A.iemb into out.
+void launch_mlp_cache(const GaussArgs& A, long long n, float* out, int blocks, cudaStream_t s);
 void launch_mlp_bwd(const GaussArgs& g, const CamBatch& cams, long long V, const Rec* rec, const uint32_t* owner,
                     Grad2D* g2d, float* g_gemb, float* g_iemb, float* g_params, int blocks, cudaStream_t s);
 // Runs over the V visible records; the first record of each Gaussian writes its gradient rows

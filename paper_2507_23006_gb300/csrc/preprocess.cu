@@ -378,10 +378,24 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_bwd_kernel(GaussArgs A, CamBa
 // The variant for launches where few Gaussians survive the culls (an aerial view of a large
 // scene): more resident blocks for the scan over all Gaussians. The one for dense launches is
 // in preprocess_dense.cu.
+// The transform of Gaussians [0, n) for one image embedding (A.iemb points at its row).
+__global__ void __launch_bounds__(256) mlp_cache_kernel(GaussArgs A, long long n, float4* __restrict__ out) {
+  __shared__ MlpSmem M;
+  mlp_load_smem(A, 1, M);
+  __syncthreads();
+  for (long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; g < n;
+       g += static_cast<long long>(gridDim.x) * blockDim.x) {
+    float lg[kEmbG], mo[kMlpOut];
+    load_gemb(A, g, lg);
+    mlp_eval(M, lg, 0, mo);
+    out[g] = make_float4(mo[0], mo[1], mo[2], mo[3]);
+  }
+}
+
 template <typename AT, typename ST>
 void launch_fwd_t(const GaussArgs& g, const CamBatch& cams, float eps, int aa, const PreOut& out, int blocks,
                   cudaStream_t s) {
-  if (g.mlp)
+  if (g.mlp || g.mlp_cached)
     preprocess_fwd_kernel<AT, ST, true, 4><<<blocks, kPreThreads, 0, s>>>(g, cams, eps, aa, out);
   else
     preprocess_fwd_kernel<AT, ST, false, 5><<<blocks, kPreThreads, 0, s>>>(g, cams, eps, aa, out);
@@ -440,6 +454,12 @@ __global__ void __launch_bounds__(128) zero_fill_kernel(FillSpans f) {
 void launch_zero_fill(const FillSpans& f, int blocks, cudaStream_t s) {
   if (f.count <= 0 || blocks <= 0) return;
   zero_fill_kernel<<<blocks, 128, 0, s>>>(f);
+}
+
+void launch_mlp_cache(const GaussArgs& A, long long n, float* out, int blocks, cudaStream_t s) {
+  if (n <= 0) return;
+  const long long need = (n + 255) / 256;
+  mlp_cache_kernel<<<static_cast<int>(need < blocks ? need : blocks), 256, 0, s>>>(A, n, reinterpret_cast<float4*>(out));
 }
 
 void launch_mlp_bwd(const GaussArgs& g, const CamBatch& cams, long long V, const Rec* rec, const uint32_t* owner,

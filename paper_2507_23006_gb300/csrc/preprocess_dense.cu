@@ -9,7 +9,7 @@ namespace {
 template <typename AT, typename ST>
 void launch_dense_t(const GaussArgs& g, const CamBatch& cams, float eps, int aa, const PreOut& out, int blocks,
                     cudaStream_t s) {
-  if (g.mlp)
+  if (g.mlp || g.mlp_cached)
     preprocess_fwd_kernel<AT, ST, true, 3><<<blocks, kPreThreads, 0, s>>>(g, cams, eps, aa, out);
   else
     preprocess_fwd_kernel<AT, ST, false, 3><<<blocks, kPreThreads, 0, s>>>(g, cams, eps, aa, out);

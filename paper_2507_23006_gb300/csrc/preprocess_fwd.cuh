@@ -452,6 +452,23 @@ __device__ __forceinline__ void mlp_eval(const MlpSmem& M, const float lg[kEmbG]
   mlp_eval_f(M, lg, c, out, [](int, float, float) {});
 }
 
+// The transform's outputs for Gaussian g seen by camera c: the launch's cached outputs (one image
+// embedding for every camera) when it has them, else evaluated.
+__device__ __forceinline__ void mlp_outputs(const GaussArgs& A, const MlpSmem& M, long long g, int c,
+                                            float out[kMlpOut]) {
+  if (A.mlp_cached) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(A.mlp_cached) + g);
+    out[0] = v.x;
+    out[1] = v.y;
+    out[2] = v.z;
+    out[3] = v.w;
+    return;
+  }
+  float lg[kEmbG];
+  load_gemb(A, g, lg);
+  mlp_eval(M, lg, c, out);
+}
+
 // Appends the slots of the lanes with `pred` to the block's list (order within the list is
 // arbitrary); one shared atomic per warp.
 __device__ __forceinline__ void list_append(bool pred, uint32_t slot, uint32_t* list, uint32_t* count, int lane) {
@@ -499,7 +516,7 @@ __global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_fwd_kernel
     s_count[0] = 0;
     s_count[1] = 0;
   }
-  if (kMlp) mlp_load_smem(A, cams.C, s_mlp);  // read after the barrier that ends phase 1a
+  if (kMlp && !A.mlp_cached) mlp_load_smem(A, cams.C, s_mlp);  // read after the barrier that ends phase 1a
   if (threadIdx.x < kPreTile / 32) s_unstaged[threadIdx.x] = 0;
   for (int k = threadIdx.x; k < 4 * 256; k += kPreThreads) s_digits[k] = 0;
   __syncthreads();
@@ -589,11 +606,7 @@ __global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_fwd_kernel
     G.m[1] = __ldg(A.means + 3 * g + 1);
     G.m[2] = __ldg(A.means + 3 * g + 2);
     float mo[kMlpOut];
-    if (kMlp) {  // before the colour: only the four outputs stay live through it
-      float lg[kEmbG];
-      load_gemb(A, g, lg);
-      mlp_eval(s_mlp, lg, static_cast<int>(meta >> 16), mo);
-    }
+    if (kMlp) mlp_outputs(A, s_mlp, g, static_cast<int>(meta >> 16), mo);  // only the four outputs stay live
     float rgb[3], dir[3], dn, Y[16];
     bool cl[3];
     eval_color<ST>(A, g, G, cams.cam[meta >> 16], rgb, dir, dn, Y, cl);
@@ -654,9 +667,7 @@ __global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_fwd_kernel
       project(G, cam, eps, aa, P);
       float mo[kMlpOut] = {0.5f, 0.5f, 0.5f, 0.f};
       if (kMlp) {
-        float lg[kEmbG];
-        load_gemb(A, g, lg);
-        mlp_eval(s_mlp, lg, c, mo);
+        mlp_outputs(A, s_mlp, g, c, mo);
         P.op *= 1.f - mo[3];
       }
       float rgb[3], dir[3], dn, Y[16];

@@ -36,6 +36,7 @@ EXPORTED = [
     "gsr_create", "gsr_destroy", "gsr_status_string", "gsr_last_error", "gsr_workspace_query",
     "gsr_workspace_bytes", "gsr_render_forward", "gsr_render_backward", "gsr_state_release",
     "gsr_state_get_info", "gsr_state_copy", "gsr_sync_check", "gsr_sort_pairs_u32", "gsr_select_lod",
+    "gsr_appearance_cache",
     "gsr_profile_enable", "gsr_profile_collect", "gsr_sort_pairs_u32_noalloc", "gsr_profile_select",
     "gsr_param_grads_zero",
 ]
@@ -56,7 +57,8 @@ class Segment(ctypes.Structure):
 
 
 class CAppearanceMLP(ctypes.Structure):
-    _fields_ = [("gauss_embed", ctypes.c_void_p), ("image_embed", ctypes.c_void_p), ("params", ctypes.c_void_p)]
+    _fields_ = [("gauss_embed", ctypes.c_void_p), ("image_embed", ctypes.c_void_p), ("params", ctypes.c_void_p),
+                ("cached", ctypes.c_void_p)]
 
 
 class CGaussians(ctypes.Structure):
@@ -149,12 +151,14 @@ def load(build_if_missing: bool = True):
         L.gsr_profile_collect.argtypes = [vp, vp, vp, vp]
         L.gsr_profile_select.argtypes = [vp, ctypes.c_uint32]
         L.gsr_param_grads_zero.argtypes = [vp, vp, vp, vp]
+        L.gsr_appearance_cache.argtypes = [vp, ctypes.POINTER(CGaussians), ctypes.c_int32, vp, vp]
         for name in EXPORTED:
             getattr(L, name)
         for name in ("gsr_create", "gsr_workspace_query", "gsr_render_forward", "gsr_render_backward",
                      "gsr_state_get_info", "gsr_state_copy", "gsr_sync_check", "gsr_sort_pairs_u32",
                      "gsr_select_lod", "gsr_profile_enable", "gsr_profile_collect",
-                     "gsr_sort_pairs_u32_noalloc", "gsr_profile_select", "gsr_param_grads_zero"):
+                     "gsr_sort_pairs_u32_noalloc", "gsr_profile_select", "gsr_param_grads_zero",
+                     "gsr_appearance_cache"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -183,10 +187,12 @@ MLP_PARAMS = 32 * 48 + 32 + 4 * 32 + 4
 class AppearanceMLP:
     """Per-Gaussian appearance transform (Sec. 3.5.1), FP32 device tensors: Gaussian embeddings,
     one image embedding per camera of a launch (in camera order) and the packed weights
-    w1 [32,48] | b1 [32] | w2 [4,32] | b2 [4]."""
-    gauss_embed: torch.Tensor  # [n,16]
-    image_embed: torch.Tensor  # [n_cams,32]
-    params: torch.Tensor       # [1700]
+    w1 [32,48] | b1 [32] | w2 [4,32] | b2 [4]. Or, for rendering only, `cached`: the outputs of
+    every Gaussian for one image embedding (appearance_cache); the other three are then unused."""
+    gauss_embed: Optional[torch.Tensor]  # [n,16]
+    image_embed: Optional[torch.Tensor]  # [n_cams,32]
+    params: Optional[torch.Tensor]       # [1700]
+    cached: Optional[torch.Tensor] = None  # [n,4]
 
     @staticmethod
     def from_arrays(d: dict, device="cuda") -> "AppearanceMLP":
@@ -197,6 +203,10 @@ class AppearanceMLP:
         return AppearanceMLP(t(d["gemb"]), t(d["iemb"]), t(params))
 
     def c_struct(self, n: int) -> CAppearanceMLP:
+        if self.cached is not None:
+            if tuple(self.cached.shape) != (n, 4) or self.cached.dtype != torch.float32 or not self.cached.is_contiguous():
+                raise ValueError("cached must be a contiguous float32 [n, 4] tensor")
+            return CAppearanceMLP(None, None, None, _ptr(self.cached))
         for name, a, shape in (("gauss_embed", self.gauss_embed, (n, 16)), ("params", self.params, (MLP_PARAMS,))):
             if tuple(a.shape) != shape:
                 raise ValueError(f"{name} must have shape {shape}")
@@ -205,7 +215,7 @@ class AppearanceMLP:
         for a in (self.gauss_embed, self.image_embed, self.params):
             if a.dtype != torch.float32 or not a.is_contiguous():
                 raise ValueError("appearance-transform tensors must be contiguous float32")
-        return CAppearanceMLP(_ptr(self.gauss_embed), _ptr(self.image_embed), _ptr(self.params))
+        return CAppearanceMLP(_ptr(self.gauss_embed), _ptr(self.image_embed), _ptr(self.params), None)
 
 
 @dataclasses.dataclass
@@ -253,7 +263,7 @@ class Gaussians:
         return g, (seg_arr, cmlp)
 
     def check_cameras(self, n_cams: int):
-        if self.mlp is not None and self.mlp.image_embed.shape[0] != n_cams:
+        if self.mlp is not None and self.mlp.cached is None and self.mlp.image_embed.shape[0] != n_cams:
             raise ValueError(f"image_embed has {self.mlp.image_embed.shape[0]} rows for {n_cams} cameras")
 
     def render_count(self) -> int:
@@ -450,6 +460,23 @@ def _c_param_grads(grads: dict):
     return CParamGrads(_ptr(grads["means"]), _ptr(grads["scales"]), _ptr(grads["quats"]), _ptr(grads["opacities"]),
                        _ptr(grads["sh"]), _ptr(grads.get("appearance")), _ptr(grads.get("absgrad")),
                        _ptr(grads.get("gauss_embed")), _ptr(grads.get("image_embed")), _ptr(grads.get("mlp_params")))
+
+
+def appearance_cache(ctx: Context, g: Gaussians, image: int = 0, out: Optional[torch.Tensor] = None,
+                     stream=None) -> torch.Tensor:
+    """The appearance transform's outputs [n,4] of every Gaussian for row `image` of
+    g.mlp.image_embed (gsr_appearance_cache); AppearanceMLP(None, None, None, cached=...) renders
+    with them without evaluating the transform."""
+    if g.mlp is None or g.mlp.cached is not None:
+        raise ValueError("needs Gaussians with an evaluated appearance transform")
+    if not 0 <= image < g.mlp.image_embed.shape[0]:
+        raise ValueError("image is not a row of image_embed")
+    if out is None:
+        out = torch.empty((g.n, 4), device=g.means.device)
+    cg, keep = g.c_struct()
+    _check(ctx, load().gsr_appearance_cache(ctx.handle, ctypes.byref(cg), int(image), _ptr(out), _stream(stream)))
+    del keep
+    return out
 
 
 def zero_param_grads(ctx: Context, g: Gaussians, grads: dict, stream=None):

@@ -190,3 +190,26 @@ def test_segments_with_the_transform(ctx):
         assert float(torch.linalg.norm(a - b)) <= 1e-5 * float(torch.linalg.norm(b)), k
     for k in ("image_embed", "mlp_params"):
         assert float(torch.linalg.norm(gs[k] - gf[k])) <= 1e-5 * float(torch.linalg.norm(gf[k])), k
+
+
+def test_cached_outputs_render_the_same_bits(ctx):
+    """The transform's outputs cached for one image embedding (gsr_appearance_cache) render the
+    same bits as evaluating it, for every camera given that embedding; the cache is for
+    rendering only (the backward refuses it)."""
+    cams = _cams()
+    scene, mlp, g = _setup(6000, 29, len(cams))
+    same = g.mlp.image_embed[:1].expand(len(cams), 32).contiguous()
+    g.mlp = native.AppearanceMLP(g.mlp.gauss_embed, same, g.mlp.params)
+    nopts, _ = pu.opts_pair(bg=(0.1, 0.2, 0.3))
+    out_e, _ = native.render_forward(ctx, g, cams, nopts, want_state=False)
+    cache = native.appearance_cache(ctx, g, 0)
+    gc = native.Gaussians(g.means, g.scales, g.quats, g.opacities, g.sh, 3, None,
+                          native.AppearanceMLP(None, None, None, cached=cache))
+    out_c, st = native.render_forward(ctx, gc, cams, nopts)
+    ctx.sync_check()
+    for k in ("rgb", "alpha", "depth_acc"):
+        assert torch.equal(out_e[k], out_c[k]), k
+    # the cache holds the transform's outputs: sigmoids in (0, 1)
+    assert float(cache.min()) > 0.0 and float(cache.max()) < 1.0
+    with pytest.raises(native.GsrError):
+        native.render_backward(ctx, gc, cams, st, dict(rgb=torch.ones_like(out_c["rgb"])), nopts)
