@@ -250,6 +250,17 @@ gsr_status gsr_state_copy(const gsr_fwd_state* state, int32_t which, void* dst, 
  * forward began (GSR_ERR_DEVICE_TIMEOUT), then clears it. */
 gsr_status gsr_sync_check(gsr_ctx* ctx, gsr_stream stream);
 
+/* Failure detection (no counterpart in the paper). Every device wait of this context's kernels
+ * (the decoupled look-backs of the chained scans and of the sort) gives up after `polls` polls
+ * (0: the default, 2^20, well under a second), sets the context's error word and lets the kernel
+ * finish; the call that checks the word (gsr_render_forward, a recompute-mode
+ * gsr_render_backward, gsr_sync_check) returns GSR_ERR_DEVICE_TIMEOUT and the results of that
+ * call are invalid, while every write stays inside its buffers. never_ready = 1 is a test switch:
+ * every look-back then treats its predecessors' status words as unpublished, so each wait runs to
+ * its limit (a wait on a flag nothing sets). The context stays usable: setting (0, 0) restores
+ * normal operation. Host-side only; takes effect from the next call. */
+gsr_status gsr_set_wait_limit(gsr_ctx* ctx, uint32_t polls, int32_t never_ready);
+
 /* Evaluates the appearance transform (Sec. 3.5.1) of every Gaussian of g (array order, segments
  * ignored) for the image embedding in row `image` of g->mlp->image_embed, into out [g->n,4]
  * (device memory, 16-byte aligned). The paper notes that these offsets can be kept while the
@@ -317,15 +328,19 @@ gsr_status gsr_sort_pairs_u32(gsr_ctx* ctx, const uint32_t* keys_in, const uint3
  * runs inside another framework's allocator. It calls no cudaMalloc, cudaFree or allocating
  * library routine. The paper has no counterpart: this is a deployment variant of the sort.
  *   Limit: n <= 262144 (2^18); a larger n returns GSR_ERR_UNSUPPORTED without doing anything.
- *   Scratch: one static device array of about 2.9 MB inside libgsr, reserved on every GPU that
+ *   Scratch: one static device array of about 2.6 MB inside libgsr, reserved on every GPU that
  *     loads the library until the process exits and shared by every call. Calls that overlap
  *     on the GPU (two streams, or two host threads) race on it and give wrong results:
- *     serialise them on one stream. Each call resets what must start at zero (histograms and
- *     block counters by its own kernels, look-back status words by a stream-ordered memset).
- *   The first call on a device looks up the array's device address with that device current;
- *     make that first call before any stream capture.
- *   device_err: device int32, or NULL; a bounded wait that runs out ORs 1 into it (the output
- *     is then invalid); the call never clears it.
+ *     serialise them on one stream. Each call clears what must start at zero (the look-back
+ *     status words, the digit counts and the block counters) with stream-ordered memsets.
+ *   The first call on a device looks up the array's device address with that device current
+ *     and keeps it for the life of the process; make that first call before any stream
+ *     capture. A process that calls cudaDeviceReset must not call this entry point again on
+ *     that device (the kept address would be stale).
+ *   device_err: required, device int32; a bounded wait that runs out ORs 1 into it (the output
+ *     is then invalid); the call never clears it. NULL returns GSR_ERR_INVALID_ARG: a timeout
+ *     must have somewhere to be reported.
+ *   begin_bit == end_bit copies the inputs to the outputs.
  * Asynchronous on `stream`; inputs are not modified; outputs must not alias the inputs. */
 gsr_status gsr_sort_pairs_u32_noalloc(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                                       uint32_t* vals_out, int64_t n, int32_t begin_bit, int32_t end_bit,

@@ -65,6 +65,8 @@ def lib():
             L.oracle_select_lod.argtypes = [ctypes.c_int, _D, ctypes.c_int, _I64, _D, _D, ctypes.c_int64,
                                             _I32, _I64, _I32, _I64]
             L.oracle_num_threads.restype = ctypes.c_int
+            L.oracle_set_mutation.restype = ctypes.c_int
+            L.oracle_set_mutation.argtypes = [ctypes.c_int]
             L.oracle_set_num_threads.argtypes = [ctypes.c_int]
             _lib = L
     return _lib
@@ -119,6 +121,26 @@ def _mlp_args(mlp, n, C):
                                                   _f64(mlp["w2"]).reshape(-1), _f64(mlp["b2"]).reshape(-1)]))
     assert params.size == 32 * 48 + 32 + 4 * 32 + 4
     return gemb, iemb, params
+
+
+MUTATIONS = {1: "alpha clamp mask dropped", 2: "degree-2 SH band sign flipped",
+             3: "depth term of dL/dalpha left out", 4: "conic a and c gradients swapped"}
+
+
+class mutation:
+    """Context manager for tests: the oracle's gradients carry one known mistake (MUTATIONS)
+    inside the block, so a test can show that a parity bar would catch it."""
+
+    def __init__(self, k: int):
+        self.k = int(k)
+
+    def __enter__(self):
+        self.prev = lib().oracle_set_mutation(self.k)
+        return self
+
+    def __exit__(self, *exc):
+        lib().oracle_set_mutation(self.prev)
+        return False
 
 
 def num_threads() -> int:

@@ -649,6 +649,14 @@ void bin_all(const SceneD& s, const std::vector<CamD>& cams, const OptsD& o, Bin
   }
 }
 
+// Test switch (oracle_set_mutation): plants one known mistake in the gradients, so that the tests
+// can show that their parity bars catch it. 0, the default, computes the correct gradients.
+//   1: the 0.99 clamp of alpha passes gradient (its mask is dropped)
+//   2: the gradient of the degree-2 SH band has the wrong sign
+//   3: the depth term of dL/dalpha is left out (the depth output's dependence on alpha and T)
+//   4: the gradients of conic a and conic c are swapped (a transposed operand)
+int g_mutation = 0;
+
 // One contributor of a pixel (for the backward re-walk).
 struct Contrib {
   int64_t id;
@@ -934,14 +942,16 @@ int oracle_backward(int64_t n, const double* means, const double* scales, const 
           double cdot = Cbar[0] * cp[0] + Cbar[1] * cp[1] + Cbar[2] * cp[2];
           a_bar += cdot * q.T;
           Ti_bar += cdot * q.alpha;
-          a_bar += D_bar * p.z * q.T;
-          Ti_bar += D_bar * p.z * q.alpha;
+          if (g_mutation != 3) {
+            a_bar += D_bar * p.z * q.T;
+            Ti_bar += D_bar * p.z * q.alpha;
+          }
           double cp_bar[3];
           for (int ch = 0; ch < 3; ++ch) cp_bar[ch] = Cbar[ch] * q.alpha * q.T;
           double z_bar = D_bar * q.alpha * q.T;
           T_bar = Ti_bar;
           // a = min(0.99, araw); araw = o' exp(-sigma)
-          double araw_bar = q.clamped ? 0.0 : a_bar;
+          double araw_bar = (q.clamped && g_mutation != 1) ? 0.0 : a_bar;
           double op_bar = araw_bar * std::exp(-q.sigma);
           double sig_bar = -araw_bar * q.araw;
           double ca_bar = 0.5 * q.dx * q.dx * sig_bar;
@@ -960,6 +970,7 @@ int oracle_backward(int64_t n, const double* means, const double* scales, const 
           }
           const int64_t pos = q.pos;
           double* pb = pairbuf.data() + (list_off[t] + pos) * G2;
+          if (g_mutation == 4) std::swap(ca_bar, cc_bar);
           pb[0] += mx_bar; pb[1] += my_bar; pb[2] += ca_bar; pb[3] += cb_bar; pb[4] += cc_bar;
           pb[5] += op_bar; pb[6] += rgb_bar[0]; pb[7] += rgb_bar[1]; pb[8] += rgb_bar[2];
           pb[9] += z_bar; pb[10] += std::fabs(mx_bar); pb[11] += std::fabs(my_bar);
@@ -1031,7 +1042,10 @@ int oracle_backward(int64_t n, const double* means, const double* scales, const 
       for (int ch = 0; ch < 3; ++ch) {
         if (p.flags & (1u << ch)) continue;  // rgb clamped at 0
         const double gain = on ? 2.0 * mo[ch] : 1.0;
-        for (int k = 0; k < nb && k < K; ++k) gsh[k * 3 + ch] += p.Y[k] * gain * gg[6 + ch];
+        for (int k = 0; k < nb && k < K; ++k) {
+          const double sign = (g_mutation == 2 && k >= 4 && k < 9) ? -1.0 : 1.0;
+          gsh[k * 3 + ch] += sign * p.Y[k] * gain * gg[6 + ch];
+        }
       }
       if (on) {
         // appearance transform: rgb = 2 out[0..2] rgb_pre, op' = (1 - out[3]) op_pre
@@ -1216,6 +1230,13 @@ int oracle_select_lod(int P, const double* aabb, int L, const int64_t* level_off
   *nsegs = ns;
   *n_sel = total;
   return status;
+}
+
+// Sets the test switch above (0 restores the correct gradients); returns the previous value.
+int oracle_set_mutation(int k) {
+  const int prev = g_mutation;
+  g_mutation = k;
+  return prev;
 }
 
 int oracle_num_threads() {

@@ -71,6 +71,7 @@ struct gsr_ctx {
   int grid_cap = 304;  // resident blocks of the looping scan / sort kernels (2 per SM)
   int fill_blocks = 76;  // blocks of the gradient zero fill (one per two SMs)
   bool pre_dense = false;  // the last binning kept over a quarter of its (camera, Gaussian) pairs
+  WaitCfg wait;  // how the look-backs of this context's kernels wait (gsr_set_wait_limit)
   // default allocator: a context-owned stream-ordered pool (growth and release never
   // synchronise the device, which matters when several contexts serve concurrently)
   cudaMemPool_t pool = nullptr;
@@ -178,6 +179,7 @@ SortScratch sort_scratch(gsr_ctx* ctx) {
   sc.hist = as<uint32_t>(ctx->sort_hist);
   sc.status = as<unsigned long long>(ctx->sort_status);
   sc.grid_cap = ctx->grid_cap;
+  sc.wait = ctx->wait;
   return sc;
 }
 
@@ -456,6 +458,7 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   po.v_total = d_V;
   po.err = ctx->d_err;
   po.epoch = next_epoch(ctx, s);
+  po.wait = ctx->wait;
   {
     StageTimer tm(ctx, GSR_STAGE_PREPROCESS, s);
     launch_preprocess_fwd(ga, cb, o->eps2d, o->antialiased, po, pre_blocks, ctx->pre_dense, s);
@@ -483,7 +486,8 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   {
     StageTimer tm(ctx, GSR_STAGE_PAIR_SCAN, s);
     pair_offsets_scan(as<uint32_t>(ctx->touched), as<uint32_t>(ctx->dvals_s), cnt_sorted, as<uint32_t>(ctx->offsets),
-                      d_V, capv, d_scan_status, d_scan_counter, d_P, ctx->d_err, next_epoch(ctx, s), ctx->grid_cap, s);
+                      d_V, capv, d_scan_status, d_scan_counter, d_P, ctx->d_err, next_epoch(ctx, s), ctx->grid_cap,
+                      ctx->wait, s);
   }
   // read V, P and the error word
   uint32_t* h = static_cast<uint32_t*>(ctx->pinned);
@@ -1004,6 +1008,13 @@ gsr_status gsr_sync_check(gsr_ctx* ctx, gsr_stream stream) {
     if (h & kErrTimeout) return set_err(ctx, GSR_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out");
     return set_err(ctx, GSR_ERR_UNSUPPORTED, "a device count overflowed");
   }
+  return GSR_OK;
+}
+
+gsr_status gsr_set_wait_limit(gsr_ctx* ctx, uint32_t polls, int32_t never_ready) {
+  if (!ctx) return GSR_ERR_INVALID_ARG;
+  ctx->wait.limit = polls ? polls : kSpinLimit;
+  ctx->wait.never_ready = never_ready ? 1u : 0u;
   return GSR_OK;
 }
 

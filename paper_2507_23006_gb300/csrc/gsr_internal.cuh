@@ -25,6 +25,15 @@ constexpr int kErrOverflow = 2;     // a count did not fit the buffer it was siz
 // up to 1 us between polls this is well under a second).
 constexpr unsigned kSpinLimit = 1u << 20;
 
+// How the chained-scan look-backs wait: `limit` polls per step before giving up (kErrTimeout),
+// and `never_ready` (a test switch) makes every look-back treat its predecessors' status words as
+// unpublished, so that each wait runs to the limit. A wait that gives up uses the partial prefix
+// it has summed, which is never larger than the true one, so every write stays in bounds.
+struct WaitCfg {
+  unsigned limit = kSpinLimit;
+  unsigned never_ready = 0;
+};
+
 struct DevCam {
   float R[9];
   float t[3];
@@ -127,6 +136,7 @@ struct PreOut {
   int* err;
   uint32_t epoch;              // tag of this launch's status words
   uint32_t* key_counts;        // [4][256] digit counts of the depth keys (for their sort), added to
+  WaitCfg wait;
 };
 
 struct Grad2D {  // per visible record: 12 floats, three float4
@@ -190,6 +200,7 @@ struct SortScratch {
   uint32_t* hist;                // [kSortCountWords]: digit counts per pass, then block counters
   unsigned long long* status;    // [4][tiles][256] epoch-tagged look-back words
   int grid_cap;                  // blocks per onesweep launch (resident blocks loop over tiles)
+  WaitCfg wait;
 };
 // Adds key's digits of passes [0, passes) (8 bits each from begin_bit, the last one up to
 // end_bit) to a block's shared counts sh[4][256].
@@ -225,7 +236,7 @@ constexpr int kScanItems = 8;
 void pair_offsets_scan(const uint32_t* touched, const uint32_t* order, const uint32_t* cnt_sorted,
                        uint32_t* offsets, const uint32_t* d_n, long long max_n,
                        unsigned long long* status, uint32_t* counter, unsigned long long* p_total, int* err,
-                       uint32_t epoch, int grid_cap, cudaStream_t s);
+                       uint32_t epoch, int grid_cap, WaitCfg wait, cudaStream_t s);
 
 // Duplicate-with-keys (warp-cooperative). count_only: writes cnt_sorted[i] (tile-culled counts).
 void launch_duplicate(const Rec* rec, const uint32_t* order, const uint32_t* offsets, const uint32_t* d_n,

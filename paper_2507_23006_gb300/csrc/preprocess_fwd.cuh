@@ -624,7 +624,7 @@ __global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_fwd_kernel
     s_rec[e][2].y = rgb[2];
   }
   if (threadIdx.x < 32) {
-    const unsigned long long ex = warp_lookback(out.status, bid, total, out.epoch, out.err);
+    const unsigned long long ex = warp_lookback(out.status, bid, total, out.epoch, out.err, out.wait);
     if (threadIdx.x == 0) s_excl = ex;
   }
   __syncthreads();

@@ -111,7 +111,7 @@ __device__ __forceinline__ void publish_aggregate(unsigned long long* status, ui
 // prefix in every lane and publishes its inclusive prefix. Values are 32-bit; the running total
 // is 64-bit and the caller checks it for overflow.
 __device__ __forceinline__ unsigned long long warp_lookback(unsigned long long* status, uint32_t bid, uint32_t agg,
-                                                            uint32_t epoch, int* err) {
+                                                            uint32_t epoch, int* err, WaitCfg wait) {
   const int lane = threadIdx.x & 31;
   if (bid == 0) return 0;
   unsigned long long excl = 0;
@@ -122,14 +122,14 @@ __device__ __forceinline__ unsigned long long warp_lookback(unsigned long long* 
     uint32_t flag = kStatusPrefix, val = 0;  // before tile 0: an inclusive prefix of 0
     if (j >= 0) {
       const unsigned long long s = load_status(status + j);
-      flag = status_flag(s, epoch);
+      flag = wait.never_ready ? 0u : status_flag(s, epoch);
       val = static_cast<uint32_t>(s);
     }
     const uint32_t pm = __ballot_sync(0xffffffffu, flag == kStatusPrefix);
     const uint32_t xm = __ballot_sync(0xffffffffu, flag == 0u);
     const uint32_t upto = pm ? (((pm & (0u - pm)) << 1) - 1u) : 0xffffffffu;
     if (xm & upto) {
-      if (++spins > kSpinLimit) {
+      if (++spins > wait.limit) {
         if (lane == 0) atomicOr(err, kErrTimeout);
         break;
       }
@@ -151,10 +151,11 @@ __device__ __forceinline__ unsigned long long warp_lookback(unsigned long long* 
 
 // Publish and look back in one call (all 32 lanes of one warp).
 __device__ __forceinline__ unsigned long long warp_chained_prefix(unsigned long long* status, uint32_t bid,
-                                                                  uint32_t agg, uint32_t epoch, int* err) {
+                                                                  uint32_t agg, uint32_t epoch, int* err,
+                                                                  WaitCfg wait) {
   if ((threadIdx.x & 31) == 0) publish_aggregate(status, bid, agg, epoch);
   __syncwarp();
-  return warp_lookback(status, bid, agg, epoch, err);
+  return warp_lookback(status, bid, agg, epoch, err, wait);
 }
 
 }  // namespace gsr

@@ -44,9 +44,9 @@ __global__ void __launch_bounds__(256) hist_kernel(const uint32_t* __restrict__ 
 // Per-digit decoupled look-back of tile `bid` (one thread per digit): publishes the tile's
 // count, then sums predecessors' counts back to the nearest inclusive prefix, reading eight
 // predecessors per round (the loads are independent; the walk is latency-bound otherwise).
-// Waits are bounded: past kSpinLimit rounds the error flag is set and the partial sum is used.
+// Waits are bounded: past wait.limit rounds the error flag is set and the partial sum is used.
 __device__ __forceinline__ uint32_t lookback_digit(unsigned long long* status, uint32_t bid, int d, uint32_t agg,
-                                                   uint32_t epoch, int* err) {
+                                                   uint32_t epoch, int* err, WaitCfg wait) {
   constexpr int kAhead = 8;
   unsigned long long* me = status + static_cast<size_t>(bid) * 256 + d;
   if (bid == 0) {
@@ -68,7 +68,7 @@ __device__ __forceinline__ uint32_t lookback_digit(unsigned long long* status, u
 #pragma unroll
     for (int k = 0; k < kAhead; ++k) {
       if (done || stalled) continue;
-      const uint32_t f = status_flag(w[k], epoch);
+      const uint32_t f = (wait.never_ready && j - k >= 0) ? 0u : status_flag(w[k], epoch);
       if (f == 0) {
         stalled = true;
       } else {
@@ -78,7 +78,7 @@ __device__ __forceinline__ uint32_t lookback_digit(unsigned long long* status, u
       }
     }
     if (stalled && !done) {
-      if (++spins > kSpinLimit) {
+      if (++spins > wait.limit) {
         atomicOr(err, kErrTimeout);
         break;
       }
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* d_n, long long max_n, int shift, int width,
     const uint32_t* __restrict__ counts, unsigned long long* status, uint32_t* counter, uint32_t epoch,
-    int* err) {
+    int* err, WaitCfg wait) {
   constexpr int kWarps = kSortThreads / 32;
   constexpr int kOut = kSortTile / kSortThreads;  // tile positions each thread writes out
   __shared__ uint32_t s_hist[kWarps][256];
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
       }
     }
     uint32_t excl = 0;
-    if (tid < 256) excl = lookback_digit(status, bid, tid, sum, epoch, err);
+    if (tid < 256) excl = lookback_digit(status, bid, tid, sum, epoch, err, wait);
     uint32_t tile_total;
     const uint32_t local = block_excl_scan(sum, &tile_total);  // every thread; digits are the first 256
     if (tid < 256) {
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
 __global__ void __launch_bounds__(kScanThreads) pair_scan_kernel(
     const uint32_t* __restrict__ touched, const uint32_t* __restrict__ order, const uint32_t* __restrict__ cnt_sorted,
     uint32_t* __restrict__ offsets, const uint32_t* d_n, long long max_n, unsigned long long* status,
-    uint32_t* counter, unsigned long long* p_total, uint32_t epoch, int* err) {
+    uint32_t* counter, unsigned long long* p_total, uint32_t epoch, int* err, WaitCfg wait) {
   __shared__ uint32_t s_bid;
   __shared__ unsigned long long s_base;
   const long long n = device_n(d_n, max_n);
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kScanThreads) pair_scan_kernel(
     uint32_t total;
     const uint32_t excl = block_excl_scan(sum, &total);
     if (threadIdx.x < 32) {
-      const unsigned long long ex = warp_chained_prefix(status, bid, total, epoch, err);
+      const unsigned long long ex = warp_chained_prefix(status, bid, total, epoch, err, wait);
       if (threadIdx.x == 0) s_base = ex;
     }
     __syncthreads();
@@ -293,7 +293,8 @@ void radix_sort_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
     const int shift = begin_bit + 8 * p;
     const int width = std::min(8, end_bit - shift);
     onesweep_kernel<<<grid, kSortThreads, 0, s>>>(ksrc, vsrc, kdst, vdst, d_n, max_n, shift, width, sc.hist + 256 * p,
-                                                  sc.status + words * p, sc.hist + 4 * 256 + p, epoch, err);
+                                                  sc.status + words * p, sc.hist + 4 * 256 + p, epoch, err,
+                                                  sc.wait);
     ksrc = kdst;
     vsrc = vdst;
   }
@@ -302,13 +303,13 @@ void radix_sort_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
 void pair_offsets_scan(const uint32_t* touched, const uint32_t* order, const uint32_t* cnt_sorted,
                        uint32_t* offsets, const uint32_t* d_n, long long max_n, unsigned long long* status,
                        uint32_t* counter, unsigned long long* p_total, int* err, uint32_t epoch, int grid_cap,
-                       cudaStream_t s) {
+                       WaitCfg wait, cudaStream_t s) {
   const long long per = kScanThreads * kScanItems;
   const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>((max_n + per - 1) / per, grid_cap)));
   cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
   cudaMemsetAsync(p_total, 0, sizeof(unsigned long long), s);
   pair_scan_kernel<<<grid, kScanThreads, 0, s>>>(touched, order, cnt_sorted, offsets, d_n, max_n, status, counter,
-                                                 p_total, epoch, err);
+                                                 p_total, epoch, err, wait);
 }
 
 }  // namespace gsr

@@ -28,8 +28,7 @@ constexpr size_t kKeysTmp = 0;
 constexpr size_t kValsTmp = kKeysTmp + kMaxN;
 constexpr size_t kHist = kValsTmp + kMaxN;  // digit counts and block counters
 constexpr size_t kStatus = (kHist + kSortCountWords + 1) & ~static_cast<size_t>(1);
-constexpr size_t kErrWord = kStatus + 2 * 4 * kMaxTiles * 256;
-constexpr size_t kWords = kErrWord + 4;  // about 2.6 MB in all
+constexpr size_t kWords = kStatus + 2 * 4 * kMaxTiles * 256;  // 656,388 words, about 2.6 MB
 static_assert(kStatus % 2 == 0, "64-bit status words need an even word offset");
 
 static __device__ __align__(256) uint32_t g_sort_scratch[kWords];
@@ -40,7 +39,9 @@ uint32_t* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of g_sort_scratch on the current device, looked up once per device. In host
 // code the symbol's name is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress with that device current.
+// cudaGetSymbolAddress with that device current. The address is kept for the life of the
+// process: after a cudaDeviceReset the module is loaded again and the kept address is stale, so
+// a process that resets a device must not call this entry point again on it.
 gsr_status scratch_address(uint32_t** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -69,6 +70,7 @@ extern "C" gsr_status gsr_sort_pairs_u32_noalloc(const uint32_t* keys_in, const 
                                                  int32_t begin_bit, int32_t end_bit, int32_t* device_err,
                                                  gsr_stream stream) {
   if (n < 0 || begin_bit < 0 || end_bit > 32 || end_bit < begin_bit) return GSR_ERR_INVALID_ARG;
+  if (!device_err) return GSR_ERR_INVALID_ARG;  // a timeout must have somewhere to be reported
   if (n > kMaxN) return GSR_ERR_UNSUPPORTED;
   if (n == 0) return GSR_OK;
   if (!keys_in || !vals_in || !keys_out || !vals_out) return GSR_ERR_INVALID_ARG;
@@ -93,9 +95,9 @@ extern "C" gsr_status gsr_sort_pairs_u32_noalloc(const uint32_t* keys_in, const 
   sc.hist = base + kHist;
   sc.status = reinterpret_cast<unsigned long long*>(base + kStatus);
   sc.grid_cap = std::min(2 * sms, kNoAllocBlocks);
-  int* err = device_err ? reinterpret_cast<int*>(device_err) : reinterpret_cast<int*>(base + kErrWord);
-  // Every call clears the look-back status words, the digit counts and the block counters
-  // before its first kernel (stream-ordered memsets, no allocation); the ping-pong buffers need
+  int* err = reinterpret_cast<int*>(device_err);
+  // Every call clears the look-back status words, the digit counts and the block counters with
+  // stream-ordered memsets before its first kernel (no allocation); the ping-pong buffers need
   // no clearing.
   radix_sort_u32(keys_in, vals_in, keys_out, vals_out, nullptr, n, begin_bit, end_bit, sc, 1u, true, false, err, s);
   const cudaError_t e = cudaGetLastError();

@@ -38,7 +38,7 @@ EXPORTED = [
     "gsr_state_get_info", "gsr_state_copy", "gsr_sync_check", "gsr_sort_pairs_u32", "gsr_select_lod",
     "gsr_appearance_cache",
     "gsr_profile_enable", "gsr_profile_collect", "gsr_sort_pairs_u32_noalloc", "gsr_profile_select",
-    "gsr_param_grads_zero",
+    "gsr_param_grads_zero", "gsr_set_wait_limit",
 ]
 
 STAGES = ["preprocess", "depth_sort", "tile_count", "pair_scan", "readback", "duplicate", "tile_sort", "ranges",
@@ -98,6 +98,32 @@ class CParamGrads(ctypes.Structure):
                 ("mlp_params", ctypes.c_void_p)]
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class CAllocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", ctypes.c_void_p)]
+
+
+class TorchAllocator:
+    """Backs a context's workspace with PyTorch's caching allocator (gsr_allocator callbacks):
+    the library's scratch then shares torch's memory pool and shows in its statistics.
+    alloc(bytes, stream) returns a device address or 0 (the library reports GSR_ERR_OOM)."""
+
+    def __init__(self, device: int = 0):
+        self.device = int(device)
+
+    def alloc(self, nbytes: int, stream: int) -> int:
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0)))
+        except RuntimeError:  # torch's out-of-memory error
+            return 0
+
+    def free(self, ptr: int, nbytes: int, stream: int) -> None:
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+
 class CStateInfo(ctypes.Structure):
     _fields_ = [("n_render", ctypes.c_int64), ("n_cams", ctypes.c_int32), ("n_visible", ctypes.c_int64),
                 ("n_pairs", ctypes.c_int64), ("n_tiles", ctypes.c_int64), ("n_pixels", ctypes.c_int64)]
@@ -151,6 +177,7 @@ def load(build_if_missing: bool = True):
         L.gsr_profile_collect.argtypes = [vp, vp, vp, vp]
         L.gsr_profile_select.argtypes = [vp, ctypes.c_uint32]
         L.gsr_param_grads_zero.argtypes = [vp, vp, vp, vp]
+        L.gsr_set_wait_limit.argtypes = [vp, ctypes.c_uint32, ctypes.c_int32]
         L.gsr_appearance_cache.argtypes = [vp, ctypes.POINTER(CGaussians), ctypes.c_int32, vp, vp]
         for name in EXPORTED:
             getattr(L, name)
@@ -158,7 +185,7 @@ def load(build_if_missing: bool = True):
                      "gsr_state_get_info", "gsr_state_copy", "gsr_sync_check", "gsr_sort_pairs_u32",
                      "gsr_select_lod", "gsr_profile_enable", "gsr_profile_collect",
                      "gsr_sort_pairs_u32_noalloc", "gsr_profile_select", "gsr_param_grads_zero",
-                     "gsr_appearance_cache"):
+                     "gsr_appearance_cache", "gsr_set_wait_limit"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -350,15 +377,26 @@ class State:
 
 
 class Context:
-    """One library context (workspace) bound to one device; use one per stream."""
+    """One library context (workspace) bound to one device; use one per stream.
 
-    def __init__(self, device: int = 0):
+    allocator: None (the library's own stream-ordered pool) or an object with
+    alloc(nbytes, stream) -> address (0 on failure) and free(address, nbytes, stream), e.g.
+    TorchAllocator; its callbacks are kept alive as long as the context."""
+
+    def __init__(self, device: int = 0, allocator=None):
         L = load()
         self.device = int(device)
         self.handle = None
         self._states = weakref.WeakSet()
+        self._alloc_keep = None
+        calloc = None
+        if allocator is not None:
+            a_fn = ALLOC_FN(lambda nbytes, stream, user: allocator.alloc(nbytes, stream or 0) or None)
+            f_fn = FREE_FN(lambda ptr, nbytes, stream, user: allocator.free(ptr, nbytes, stream or 0))
+            calloc = CAllocator(a_fn, f_fn, None)
+            self._alloc_keep = (allocator, a_fn, f_fn, calloc)
         h = ctypes.c_void_p()
-        st = L.gsr_create(ctypes.byref(h), self.device, None)
+        st = L.gsr_create(ctypes.byref(h), self.device, ctypes.byref(calloc) if calloc is not None else None)
         if st != GSR_OK:
             raise GsrError(st, "gsr_create")
         self.handle = h.value
@@ -388,6 +426,11 @@ class Context:
         _check(self, load().gsr_workspace_query(self.handle, int(n_render), arr, len(cams), int(expected_pairs),
                                                 ctypes.byref(out)))
         return int(out.value)
+
+    def set_wait_limit(self, polls: int = 0, never_ready: bool = False):
+        """Bound on the polls of every device wait (0: the default); never_ready makes every wait
+        run to it (a test of failure detection). See gsr_set_wait_limit."""
+        _check(self, load().gsr_set_wait_limit(self.handle, int(polls), int(bool(never_ready))))
 
     def sync_check(self, stream=None):
         _check(self, load().gsr_sync_check(self.handle, _stream(stream)))

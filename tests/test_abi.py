@@ -35,6 +35,8 @@ def test_status_strings_and_null_arguments():
     assert L.gsr_status_string(-4) == b"device wait timed out"
     # null context / out pointers are rejected before any CUDA call
     assert L.gsr_sort_pairs_u32(None, None, None, None, None, 10, 0, 32, None) == -1
+    # the allocation-free sort needs a device error word; without one it refuses
+    assert L.gsr_sort_pairs_u32_noalloc(None, None, None, None, 10, 0, 32, None, None) == -1
     assert L.gsr_create(None, 0, None) == -1
     assert L.gsr_render_forward(None, None, None, 1, None, None, None, None) == -1
     assert L.gsr_state_get_info(None, None) == -1

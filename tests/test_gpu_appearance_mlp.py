@@ -94,9 +94,9 @@ def test_backward_all_gradients(ctx, save):
     res = oracle.render(scene, cams, oopts, mlp=mlp, want_pairs=False)
     up = _upstream(res, res.img.shape[0], seed=9)
     gg = _gpu_backward(ctx, g, cams, st, up, nopts)
-    ref = oracle.backward(scene, cams, up, oopts, mlp=mlp)
+    ref = oracle.backward(scene, cams, up, oopts, mlp=mlp, want_mag=True)
     for k in ("means", "scales", "quats", "opacities", "sh"):
-        pu.grad_close(gg[k], ref[k], f"{k} (save_state={save})")
+        pu.grad_close(gg[k], ref[k], f"{k} (save_state={save})", mag=ref["mag"][k])
     _check_mlp_grads(gg, ref)
 
 

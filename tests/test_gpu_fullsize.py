@@ -101,14 +101,6 @@ def _check_images(out, res, pix, depth_scale, min_unmarked=0.8):
     return um
 
 
-def _upstream_on(um, npix, seed):
-    up = np.zeros((npix, 6))
-    w = np.random.default_rng(seed).normal(size=(um.size, 6))
-    w[:, 4] = 0.0
-    up[um] = w
-    return up
-
-
 def test_city_8_cameras_mixed_resolution_fp16_sh(ctx):
     scene = scenes.city(2, 6_000_000)
     cams = scenes.city_batch_cameras(2)
@@ -130,7 +122,7 @@ def test_city_8_cameras_mixed_resolution_fp16_sh(ctx):
         a = gl.get(int(t), np.zeros(0, np.int64))
         b = ol.get(int(t), np.zeros(0, np.int64))
         np.testing.assert_array_equal(np.sort(a[res.gmark[a] == 0]), np.sort(b[res.gmark[b] == 0]))
-    up = _upstream_on(um, sum(c.width * c.height for c in cams), seed=6)
+    up = pu.upstream_on(um, sum(c.width * c.height for c in cams), seed=6, alpha=res.img[:, 5])
     gg = _gpu_backward(ctx, g, cams, st, up, nopts)
     ref = oracle.backward(deq, cams, up, oopts, tile_subset=tiles, want_mag=True)
     for k in ("means", "scales", "quats", "opacities", "sh"):
@@ -166,7 +158,7 @@ def test_large_street_level_4k_fp16_sh_recompute(ctx):
     um = _check_images(out, res, pix, depth_scale=100.0, min_unmarked=0.5)
     # no pair lists are kept in recompute mode: n_contrib may differ by near-tie positions
     assert np.abs(nc[um] - res.img[um, 7].astype(np.int64)).max() <= 2
-    up = _upstream_on(um, npix, seed=8)
+    up = pu.upstream_on(um, npix, seed=8, alpha=res.img[:, 5])
     gg = _gpu_backward(ctx, g, [cam], st, up, nopts)
     peak = torch.cuda.max_memory_allocated() + ctx.workspace_bytes()
     print(f"\n30M / 4K recompute: compared {um.size} of {pix.size} sampled pixels; "

@@ -244,12 +244,7 @@ def test_stacked_termination_closed_form(ctx, o):
 
 # ---- backward -----------------------------------------------------------------------------------
 
-def _upstream(res, npix, seed, alpha_min=0.05):
-    rng = np.random.default_rng(seed)
-    up = rng.normal(size=(npix, 6))
-    up[res.mark.astype(bool)] = 0.0
-    up[res.img[:, 5] < alpha_min, 4] = 0.0   # expected depth is ill-conditioned where alpha ~ 0
-    return up
+_upstream = pu.upstream
 
 
 def _gpu_backward(ctx, g, cams, st, up, nopts, appearances=None):
@@ -266,16 +261,17 @@ def _gpu_backward(ctx, g, cams, st, up, nopts, appearances=None):
 
 @pytest.mark.parametrize("aa,cull,deg", [(True, False, 3), (False, True, 3), (True, True, 1)])
 def test_box_scene_backward(ctx, aa, cull, deg):
-    scene, cam = pu.scene_box(4000, seed=3)
+    scene, cam = pu.scene_box_backward(4000, seed=3)
     scene.sh_degree = deg
     nopts, oopts = pu.opts_pair(antialiased=aa, tile_cull=cull, bg=(0.2, 0.1, 0.0), absgrad=True)
     g, out, st = pu.gpu_render(ctx, scene, [cam], nopts)
     res = oracle.render(scene, [cam], oopts, want_pairs=False)
     up = _upstream(res, cam.width * cam.height, seed=11)
     gg = _gpu_backward(ctx, g, [cam], st, up, nopts)
-    ref = oracle.backward(scene, [cam], up, oopts)
-    for k in ("means", "scales", "quats", "opacities", "sh", "absgrad"):
-        pu.grad_close(gg[k], ref[k], k)
+    ref = oracle.backward(scene, [cam], up, oopts, want_mag=True)
+    for k in ("means", "scales", "quats", "opacities", "sh"):
+        pu.grad_close(gg[k], ref[k], k, mag=ref["mag"][k])
+    pu.grad_close(gg["absgrad"], ref["absgrad"], "absgrad")  # sums of magnitudes: no cancellation
     pu.grad_close(gg["appearance"], ref["affine"], "appearance")
 
 
@@ -292,7 +288,7 @@ def test_gradient_rows_unaligned_and_prefilled(ctx, shift):
     g, out, st = pu.gpu_render(ctx, scene, [cam], nopts)
     res = oracle.render(scene, [cam], oopts, want_pairs=False)
     up = _upstream(res, cam.width * cam.height, seed=3)
-    ref = oracle.backward(scene, [cam], up, oopts)
+    ref = oracle.backward(scene, [cam], up, oopts, want_mag=True)
     n = g.n
     shapes = dict(means=(n, 3), scales=(n, 3), quats=(n, 4), opacities=(n,), sh=(n, 16, 3), absgrad=(n, 2))
     grads = {}
@@ -311,7 +307,8 @@ def test_gradient_rows_unaligned_and_prefilled(ctx, shift):
         got = grads[k].cpu().numpy().reshape(n, -1)
         assert np.isfinite(got).all(), k
         assert (got[hidden] == 0).all(), k
-        pu.grad_close(got, np.asarray(ref[k]).reshape(n, -1), k)
+        pu.grad_close(got, np.asarray(ref[k]).reshape(n, -1), k,
+                      mag=None if k == "absgrad" else np.asarray(ref["mag"][k]).reshape(n, -1))
 
 
 def test_param_grads_zeroed_ahead_of_the_forward(ctx):
@@ -327,7 +324,7 @@ def test_param_grads_zeroed_ahead_of_the_forward(ctx):
     g = native.Gaussians.from_scene(scene)
     res = oracle.render(scene, [cam], oopts, want_pairs=False)
     up = _upstream(res, cam.width * cam.height, seed=4)
-    ref = oracle.backward(scene, [cam], up, oopts)
+    ref = oracle.backward(scene, [cam], up, oopts, want_mag=True)
     d = dict(rgb=torch.tensor(up[:, 0:3], dtype=torch.float32, device="cuda").contiguous(),
              depth_acc=torch.tensor(up[:, 3], dtype=torch.float32, device="cuda").contiguous(),
              depth_exp=torch.tensor(up[:, 4], dtype=torch.float32, device="cuda").contiguous(),
@@ -350,7 +347,8 @@ def test_param_grads_zeroed_ahead_of_the_forward(ctx):
             arr = got[k].cpu().numpy().reshape(g.n, -1)
             assert np.isfinite(arr).all(), (k, same)
             assert (arr[hidden] == 0).all(), (k, same)
-            pu.grad_close(arr, np.asarray(ref[k]).reshape(g.n, -1), f"{k} (same arrays: {same})")
+            pu.grad_close(arr, np.asarray(ref[k]).reshape(g.n, -1), f"{k} (same arrays: {same})",
+                          mag=np.asarray(ref["mag"][k]).reshape(g.n, -1))
         if not same:  # the arrays zeroed ahead were not used by the backward, but are zero
             assert all((a[k] == 0).all() for k in ("means", "scales", "quats", "opacities", "sh"))
 
@@ -369,9 +367,9 @@ def test_backward_batched_with_appearance_and_recompute(ctx):
         res = oracle.render(scene, cams, oopts, affines=np.stack([aff, np.eye(3, 4)]), want_pairs=False)
         up = _upstream(res, res.img.shape[0], seed=5)
         gg = _gpu_backward(ctx, g, cams, st, up, nopts, appearances=[aff_t, None])
-        ref = oracle.backward(scene, cams, up, oopts, affines=np.stack([aff, np.eye(3, 4)]))
+        ref = oracle.backward(scene, cams, up, oopts, affines=np.stack([aff, np.eye(3, 4)]), want_mag=True)
         for k in ("means", "scales", "quats", "opacities", "sh"):
-            pu.grad_close(gg[k], ref[k], f"{k} (save_state={save})")
+            pu.grad_close(gg[k], ref[k], f"{k} (save_state={save})", mag=ref["mag"][k])
         pu.grad_close(gg["appearance"].reshape(2, 12), ref["affine"], "appearance")
 
 
@@ -457,15 +455,12 @@ def test_street_block_full_size_sampled(ctx, street):
         a = gl.get(int(t), np.zeros(0, np.int64))
         b = ol.get(int(t), np.zeros(0, np.int64))
         np.testing.assert_array_equal(np.sort(a[res.gmark[a] == 0]), np.sort(b[res.gmark[b] == 0]))
-    # gradients with upstream only on the sampled, unmarked pixels
-    up = np.zeros((cam.width * cam.height, 6))
-    w = np.random.default_rng(9).normal(size=(um.size, 6))
-    w[:, 4] = 0.0
-    up[um] = w
+    # gradients with upstream only on the sampled, unmarked pixels (depth_exp where alpha > 0.05)
+    up = pu.upstream_on(um, cam.width * cam.height, seed=9, alpha=res.img[:, 5])
     gg = _gpu_backward(ctx, g, [cam], st, up, nopts)
-    ref = oracle.backward(scene, [cam], up, oopts, tile_subset=tiles)
+    ref = oracle.backward(scene, [cam], up, oopts, tile_subset=tiles, want_mag=True)
     for k in ("means", "scales", "quats", "opacities", "sh"):
-        pu.grad_close(gg[k], ref[k], k)
+        pu.grad_close(gg[k], ref[k], k, mag=ref["mag"][k])
 
 
 def test_preprocess_variants_agree():

@@ -65,14 +65,16 @@ def test_autograd_matches_oracle_chain(ctx, recompute):
     wt = torch.tensor(w, dtype=torch.float32, device="cuda")
     loss = (rgb * wt[:, :3]).sum() + (dacc * wt[:, 3]).sum() + (alpha * wt[:, 5]).sum()
     loss.backward()
-    ref = oracle.backward(scene, cams, w, oopts, affines=aff)
+    ref = oracle.backward(scene, cams, w, oopts, affines=aff, want_mag=True)
     s = np.asarray(scene.scales, np.float64)
     o = np.asarray(scene.opacities, np.float64)
-    pu.grad_close(p["means"].grad.cpu().numpy(), ref["means"], "means")
-    pu.grad_close(p["log_scales"].grad.cpu().numpy(), ref["scales"] * s, "log_scales")
-    pu.grad_close(p["quats"].grad.cpu().numpy(), ref["quats"], "quats")
-    pu.grad_close(p["logits"].grad.cpu().numpy(), ref["opacities"] * o * (1 - o), "logits")
-    pu.grad_close(p["sh"].grad.cpu().numpy(), ref["sh"], "sh")
+    mag = ref["mag"]
+    pu.grad_close(p["means"].grad.cpu().numpy(), ref["means"], "means", mag=mag["means"])
+    pu.grad_close(p["log_scales"].grad.cpu().numpy(), ref["scales"] * s, "log_scales", mag=mag["scales"] * s)
+    pu.grad_close(p["quats"].grad.cpu().numpy(), ref["quats"], "quats", mag=mag["quats"])
+    pu.grad_close(p["logits"].grad.cpu().numpy(), ref["opacities"] * o * (1 - o), "logits",
+                  mag=mag["opacities"] * o * (1 - o))
+    pu.grad_close(p["sh"].grad.cpu().numpy(), ref["sh"], "sh", mag=mag["sh"])
     pu.grad_close(app.grad.cpu().numpy().reshape(2, 12), ref["affine"], "appearance")
 
 
@@ -115,9 +117,9 @@ def test_reduced_precision_storage(ctx, attr, sh):
              depth_acc=torch.tensor(up[:, 3], dtype=torch.float32, device="cuda"),
              alpha=torch.tensor(up[:, 5], dtype=torch.float32, device="cuda"))
     gr = native.render_backward(ctx, g, [cam], st, d, opts)
-    ref = oracle.backward(deq, [cam], up, oopts)
+    ref = oracle.backward(deq, [cam], up, oopts, want_mag=True)
     for k in ("means", "scales", "quats", "opacities", "sh"):
-        pu.grad_close(gr[k].cpu().numpy(), ref[k], f"{k} ({attr}, {sh})")
+        pu.grad_close(gr[k].cpu().numpy(), ref[k], f"{k} ({attr}, {sh})", mag=ref["mag"][k])
     # reported, not pinned: error of the reduced-precision render against the FP32 inputs
     full = oracle.render(scene, [cam], oopts, want_pairs=False)
     err = np.abs(out["rgb"].cpu().numpy() - full.img[:, :3])
