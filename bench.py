@@ -319,18 +319,22 @@ def run_mlp_leg(args, ctx, g, cam, opts, d_out, outs, stream, dev, rank):
 
 # Algorithmic work of each stage of one step (the design notes derive each figure): bytes that
 # must cross HBM, FP32 operations and MUFU operations (ex2, reciprocal) of the blends.
-def stage_work(n, V, P, tiles, npix, counts, sort_passes_tile):
+def stage_work(n, V, P, tiles, npix, counts):
     fe, be = counts["fwd_evals"], counts["bwd_evals"]
     return {
-        "preprocess": dict(bytes=52.0 * n + 252.0 * V),
-        "depth_sort": dict(bytes=68.0 * V),
-        "tile_count": dict(bytes=56.0 * V),
-        "pair_scan": dict(bytes=12.0 * V),
-        "duplicate": dict(bytes=56.0 * V + 8.0 * P),
-        "tile_sort": dict(bytes=(4.0 + 16.0 * sort_passes_tile) * P),
-        "ranges": dict(bytes=4.0 * P + 8.0 * tiles),
+        # the per-unit figures of the hot-path scope table: 44 B read per Gaussian, 192 B of SH
+        # read and a 48 B record written per visible one
+        "preprocess": dict(bytes=44.0 * n + 240.0 * V),
+        # binning: the counting and the placing pass read the 48 bytes of each record that locate
+        # it (position, opacity, depth, conic, rectangle); the scan reads each tile's count and
+        # writes its range and cursor; placing writes an 8-byte key per pair; sorting reads the
+        # keys and writes the 4-byte record index per pair
+        "tile_count": dict(bytes=48.0 * V + 4.0 * tiles),
+        "tile_scan": dict(bytes=16.0 * tiles),
+        "place": dict(bytes=48.0 * V + 8.0 * P),
+        "tile_sort": dict(bytes=12.0 * P),
         "blend_fwd": dict(bytes=48.0 * P + 28.0 * npix, flops=FLOPS_PER_FWD_EVAL * fe, mufu=1.0 * fe),
-        "blend_bwd": dict(bytes=48.0 * P + 28.0 * npix + 48.0 * V, flops=FLOPS_PER_BWD_EVAL * be, mufu=2.0 * be),
+        "blend_bwd": dict(bytes=48.0 * P + 28.0 * npix + 40.0 * V, flops=FLOPS_PER_BWD_EVAL * be, mufu=2.0 * be),
         # single camera: one record per visible Gaussian; its attribute and SH rows read and its
         # gradient rows written (236 B each way) plus the record, its 2D gradients and owner
         "preprocess_bwd": dict(bytes=472.0 * V + 116.0 * V),
@@ -343,10 +347,9 @@ def stage_rooflines(stage_ms, n, V, P, tiles, npix, counts, fp32_tflops, mufu_pe
     """Per stage: the algorithmic time (the largest of bytes / HBM peak, FP32 ops / FP32 peak and
     MUFU ops / MUFU peak) against the measured time; for the step, the sum of the stages'
     algorithmic times (the gradient fill's included) against the step time."""
-    passes = (max(1, math.ceil(math.log2(max(tiles, 2)))) + 7) // 8
     out = {}
     total = 0.0
-    for k, w in stage_work(n, V, P, tiles, npix, counts, passes).items():
+    for k, w in stage_work(n, V, P, tiles, npix, counts).items():
         t = {"hbm": w.get("bytes", 0.0) / (hbm_gbs * 1e9), "alu": w.get("flops", 0.0) / (fp32_tflops * 1e12),
              "mufu": w.get("mufu", 0.0) / mufu_per_s}
         bound = max(t, key=t.get)
@@ -607,10 +610,8 @@ def run_ours(args, rank, world, local_rank):
                     frac=achieved / fp32_peak, traffic=stored_traffic(dom, workload_name(n, cam.height)),
                     peak_source=f"{sms} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sampled)")
     else:
-        passes = (max(1, math.ceil(math.log2(max(info["n_tiles"], 2)))) + 7) // 8
-        per_unit = dict(preprocess=52.0 * n + 252.0 * V, depth_sort=68.0 * V, pair_scan=12.0 * V,
-                        tile_count=56.0 * V, duplicate=56.0 * V + 8.0 * P, tile_sort=(4.0 + 16.0 * passes) * P,
-                        ranges=4.0 * P + 8.0 * info["n_tiles"], preprocess_bwd=288.0 * n + 240.0 * V, readback=0.0)
+        work = stage_work(n, V, P, info["n_tiles"], cam.width * cam.height, counts)
+        per_unit = {k: w.get("bytes", 0.0) for k, w in work.items()}
         bytes_ = per_unit.get(dom, 0.0)
         achieved = bytes_ / (dom_ms * 1e-3) / 1e9
         roof = dict(kernel=dom, launch_ms=dom_ms, bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm,
@@ -760,13 +761,10 @@ def run_serve_full(args):
 
 def kernels_per_step(tile_cull, info):
     """Kernels of ours launched per fwd+bwd step (memsets excluded)."""
-    k = 1                      # preprocess (also counts the depth keys' digits)
-    k += 4                     # depth sort: 4 onesweep passes
-    k += 1 if tile_cull else 0  # tile-culled counts
-    k += 1                     # pair scan
-    tiles = int(info["n_tiles"])
-    bits = max(1, math.ceil(math.log2(max(tiles, 2))))
-    k += 1 + (bits + 7) // 8 + 1  # duplicate (counts the tile keys' digits), tile sort passes, ranges
+    k = 1                      # preprocess
+    k += 1 if int(info["n_visible"]) > 0 else 0  # pair counts per tile
+    k += 1                     # tile scan
+    k += 2 if int(info["n_pairs"]) > 0 else 0    # pair placement, per-tile sort
     k += 1                     # blend forward
     k += 1                     # gradient zero fill (side stream)
     k += 1 + 1                 # blend backward, preprocess backward

@@ -85,7 +85,12 @@ typedef struct gsr_appearance_mlp {
 
 /* Gaussians (Sec. 3.1, Eq. 1), structure of arrays, all device memory.
  * If segs != NULL only the listed segments are rendered, in list order (the order decides the
- * index used for depth ties); segs is HOST memory with nsegs entries. */
+ * index used for depth ties); segs is HOST memory with nsegs entries.
+ * seg_cams (HOST, nsegs entries, or NULL = every camera renders every segment): bit c set means
+ * camera c of the launch renders segment k. A launch can so render several views whose detail
+ * levels differ (Sec. 3.4.2: a level per partition and per view): the segments are the union
+ * of the views' selections, each marked with the views that selected it. A camera's images are
+ * then those of rendering its own segments alone, in the same relative order. */
 typedef struct gsr_gaussians {
   int64_t n;              /* number of Gaussians in the arrays */
   const float* means;     /* [n,3] float32, world coordinates */
@@ -100,6 +105,7 @@ typedef struct gsr_gaussians {
   const gsr_segment* segs;
   int32_t nsegs;
   const gsr_appearance_mlp* mlp;  /* appearance transform (HOST struct, device arrays), or NULL */
+  const uint32_t* seg_cams;       /* [nsegs] camera masks of the segments (HOST), or NULL */
 } gsr_gaussians;
 
 /* One pinhole camera (host memory). */
@@ -184,7 +190,8 @@ typedef enum gsr_state_buffer {
   GSR_BUF_RANGES = 3,     /* [n_tiles] uint32 x2: [start, end) into the pair list */
   GSR_BUF_T_FINAL = 4,    /* [n_pixels] float32 final transmittance */
   GSR_BUF_N_CONTRIB = 5,  /* [n_pixels] uint32 list positions walked up to the last contributor */
-  GSR_BUF_DEPTH_ACC = 6   /* [n_pixels] float32 accumulated depth */
+  GSR_BUF_DEPTH_STATE = 6 /* [n_pixels] float32 x2: depth of the pixel's first contributor z_f, and
+                             sum over contributors of (z - z_f) alpha T (depth_acc = z_f (1 - T) + it) */
 } gsr_state_buffer;
 
 /* ---- context --------------------------------------------------------------------------- */
@@ -275,20 +282,18 @@ gsr_status gsr_appearance_cache(gsr_ctx* ctx, const gsr_gaussians* g, int32_t im
 /* Stages timed with CUDA events on the call's stream while profiling is on. */
 typedef enum gsr_stage {
   GSR_STAGE_PREPROCESS = 0,     /* projection, colour, cull, compaction */
-  GSR_STAGE_DEPTH_SORT = 1,     /* radix sort of visible records by depth */
-  GSR_STAGE_TILE_COUNT = 2,     /* tile-culled pair counts (tile_cull only) */
-  GSR_STAGE_PAIR_SCAN = 3,      /* exclusive scan of pair counts */
-  GSR_STAGE_READBACK = 4,       /* the forward's one device-to-host read of V and P */
-  GSR_STAGE_DUPLICATE = 5,      /* (tile, record) pair emission */
-  GSR_STAGE_TILE_SORT = 6,      /* stable radix sort of pairs by tile */
-  GSR_STAGE_RANGES = 7,         /* per-tile ranges */
-  GSR_STAGE_BLEND_FWD = 8,      /* forward compositing */
-  GSR_STAGE_BLEND_BWD = 9,      /* backward compositing */
-  GSR_STAGE_PREPROCESS_BWD = 10,/* projection and colour backward */
-  GSR_STAGE_BETWEEN = 11,       /* idle time between consecutive stages of one call (memsets,
+  GSR_STAGE_TILE_COUNT = 1,     /* (tile, record) pairs counted per tile (with tile culling) */
+  GSR_STAGE_TILE_SCAN = 2,      /* scan of the tile counts: each tile's range of pairs, P */
+  GSR_STAGE_READBACK = 3,       /* the forward's one device-to-host read of V and P */
+  GSR_STAGE_PLACE = 4,          /* pairs written into their tiles' ranges */
+  GSR_STAGE_TILE_SORT = 5,      /* every tile's pairs sorted by (depth, index) */
+  GSR_STAGE_BLEND_FWD = 6,      /* forward compositing */
+  GSR_STAGE_BLEND_BWD = 7,      /* backward compositing */
+  GSR_STAGE_PREPROCESS_BWD = 8, /* projection and colour backward */
+  GSR_STAGE_BETWEEN = 9,        /* idle time between consecutive stages of one call (memsets,
                                    waits on the host or the side stream, launch latency) */
-  GSR_STAGE_APPEARANCE_BWD = 12,/* appearance-transform backward (only with gsr_gaussians.mlp) */
-  GSR_NUM_STAGES = 13
+  GSR_STAGE_APPEARANCE_BWD = 10,/* appearance-transform backward (only with gsr_gaussians.mlp) */
+  GSR_NUM_STAGES = 11
 } gsr_stage;
 
 /* Counters gathered while profiling with count_evals = 1. */

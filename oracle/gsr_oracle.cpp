@@ -96,6 +96,48 @@ inline double dsqrt(double a) { return std::sqrt(a); }
 inline double val(double x) { return x; }
 template <int N> double val(const Dual<N>& x) { return x.v; }
 
+// Forward-mode magnitudes: a value and N nonnegative partials, where every operation adds up the
+// absolute values of the elementary terms of its derivative (|d(ab)| <= |b| |da| + |a| |db|, and so
+// on). Each partial so obtained is the sum of the magnitudes of all the products the chain rule adds
+// up for it: it bounds the exact partial, and the rounding error of any evaluation of the partial
+// in finite precision, in any order, scales with it rather than with the (possibly cancelling)
+// exact value.
+template <int N>
+struct Mag {
+  double v;
+  double d[N];
+  Mag() : v(0.0) { for (int i = 0; i < N; ++i) d[i] = 0.0; }
+  Mag(double x) : v(x) { for (int i = 0; i < N; ++i) d[i] = 0.0; }  // NOLINT: implicit
+  static Mag var(double x, int i) { Mag r(x); r.d[i] = 1.0; return r; }
+};
+template <int N> Mag<N> operator+(const Mag<N>& a, const Mag<N>& b) {
+  Mag<N> r; r.v = a.v + b.v; for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i]; return r; }
+template <int N> Mag<N> operator-(const Mag<N>& a, const Mag<N>& b) {
+  Mag<N> r; r.v = a.v - b.v; for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i]; return r; }
+template <int N> Mag<N> operator-(const Mag<N>& a) {
+  Mag<N> r; r.v = -a.v; for (int i = 0; i < N; ++i) r.d[i] = a.d[i]; return r; }
+template <int N> Mag<N> operator*(const Mag<N>& a, const Mag<N>& b) {
+  Mag<N> r; r.v = a.v * b.v;
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * std::fabs(b.v) + std::fabs(a.v) * b.d[i];
+  return r; }
+template <int N> Mag<N> operator/(const Mag<N>& a, const Mag<N>& b) {
+  Mag<N> r; r.v = a.v / b.v;
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] / std::fabs(b.v) + std::fabs(a.v) * b.d[i] / (b.v * b.v);
+  return r; }
+template <int N> Mag<N> operator+(const Mag<N>& a, double b) { return a + Mag<N>(b); }
+template <int N> Mag<N> operator+(double a, const Mag<N>& b) { return Mag<N>(a) + b; }
+template <int N> Mag<N> operator-(const Mag<N>& a, double b) { return a - Mag<N>(b); }
+template <int N> Mag<N> operator-(double a, const Mag<N>& b) { return Mag<N>(a) - b; }
+template <int N> Mag<N> operator*(const Mag<N>& a, double b) { return a * Mag<N>(b); }
+template <int N> Mag<N> operator*(double a, const Mag<N>& b) { return Mag<N>(a) * b; }
+template <int N> Mag<N> operator/(const Mag<N>& a, double b) { return a / Mag<N>(b); }
+template <int N> Mag<N> operator/(double a, const Mag<N>& b) { return Mag<N>(a) / b; }
+template <int N> Mag<N> dsqrt(const Mag<N>& a) {
+  Mag<N> r; r.v = std::sqrt(a.v);
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] / (2.0 * r.v);
+  return r; }
+template <int N> double val(const Mag<N>& x) { return x.v; }
+
 // ---------------------------------------------------------------------------------------------
 struct CamD {
   double R[9], t[3];
@@ -867,10 +909,10 @@ int64_t oracle_render(int64_t n, const double* means, const double* scales, cons
 //   tile_subset[n_subset] or NULL: only the pixels of these global tiles enter L (the result
 //                         equals the full gradient when up_grads is zero on every other pixel)
 //   g_mag[n][11 + 3K] or NULL: per parameter (mean 3, scale 3, quaternion 4, opacity, SH), the
-//                         magnitude of the sum that gives its gradient: every pixel's contribution
-//                         to the 2D quantities in absolute value, through the absolute Jacobian of
-//                         the projection. It bounds |gradient| and sets the scale of the rounding
-//                         error of any implementation that sums those contributions.
+//                         magnitude of the sum that gives its gradient: the same chain rule with
+//                         every sum replaced by the sum of its terms' magnitudes, through the
+//                         blend walk and the projection (Mag). It bounds |gradient| and sets the
+//                         scale of the rounding error of any finite-precision evaluation of it.
 int oracle_backward(int64_t n, const double* means, const double* scales, const double* quats,
                     const double* opac, const double* sh, int K, int deg, int C, const double* cams,
                     const double* affines, const double* opts, const double* up_grads,
@@ -926,6 +968,10 @@ int oracle_backward(int64_t n, const double* means, const double* scales, const 
         double aout_bar = up[5] + ((alpha_out > 1e-10) ? -up[4] * R.D / (alpha_out * alpha_out) : 0.0);
         double T_bar = -aout_bar;
         for (int ch = 0; ch < 3; ++ch) T_bar += up[ch] * o.bg[ch];
+        // with g_mag, the same quantities as sums of their terms' magnitudes (see Mag above)
+        const double D_bar_abs = std::fabs(up[3]) + std::fabs(up[4]) / std::max(alpha_out, 1e-10);
+        double T_bar_abs = std::fabs(up[5]) + ((alpha_out > 1e-10) ? std::fabs(up[4] * R.D) / (alpha_out * alpha_out) : 0.0);
+        for (int ch = 0; ch < 3; ++ch) T_bar_abs += std::fabs(up[ch] * o.bg[ch]);
         const double* Cbar = up;  // dL/dC' per channel
         // reverse over contributors:  C += c' a T ; D += z a T ; T <- T (1 - a)
         for (int64_t i = static_cast<int64_t>(tr.size()) - 1; i >= 0; --i) {
@@ -975,10 +1021,26 @@ int oracle_backward(int64_t n, const double* means, const double* scales, const 
           pb[5] += op_bar; pb[6] += rgb_bar[0]; pb[7] += rgb_bar[1]; pb[8] += rgb_bar[2];
           pb[9] += z_bar; pb[10] += std::fabs(mx_bar); pb[11] += std::fabs(my_bar);
           if (g_mag) {
+            // the same chain with every sum replaced by the sum of its terms' magnitudes
+            double cdot_abs = 0.0;
+            for (int ch = 0; ch < 3; ++ch) cdot_abs += std::fabs(Cbar[ch] * cp[ch]);
+            const double dz_abs = std::fabs(D_bar_abs * p.z);
+            const double a_abs = q.T * T_bar_abs + (cdot_abs + dz_abs) * q.T;
+            T_bar_abs = (1.0 - q.alpha) * T_bar_abs + (cdot_abs + dz_abs) * q.alpha;
+            const double raw_abs = q.clamped ? 0.0 : a_abs;
+            const double sig_abs = raw_abs * q.araw;
+            double rgb_abs[3];
+            for (int k2 = 0; k2 < 3; ++k2) {
+              rgb_abs[k2] = 0.0;
+              for (int ch = 0; ch < 3; ++ch) rgb_abs[k2] += std::fabs(cam.A[ch * 4 + k2] * Cbar[ch]) * q.alpha * q.T;
+            }
             double* pa = pairabs.data() + (list_off[t] + pos) * GM;
-            const double v[GM] = {mx_bar, my_bar, ca_bar, cb_bar, cc_bar, op_bar, rgb_bar[0], rgb_bar[1],
-                                  rgb_bar[2], z_bar};
-            for (int j = 0; j < GM; ++j) pa[j] += std::fabs(v[j]);
+            const double v[GM] = {(std::fabs(p.ca * q.dx) + std::fabs(p.cb * q.dy)) * sig_abs,
+                                  (std::fabs(p.cc * q.dy) + std::fabs(p.cb * q.dx)) * sig_abs,
+                                  0.5 * q.dx * q.dx * sig_abs, std::fabs(q.dx * q.dy) * sig_abs,
+                                  0.5 * q.dy * q.dy * sig_abs, raw_abs * std::exp(-q.sigma),
+                                  rgb_abs[0], rgb_abs[1], rgb_abs[2], D_bar_abs * q.alpha * q.T};
+            for (int j = 0; j < GM; ++j) pa[j] += v[j];
           }
         }
       }
@@ -1070,10 +1132,20 @@ int oracle_backward(int64_t n, const double* means, const double* scales, const 
       gabs[0] += gg[10];
       gabs[1] += gg[11];
       if (g_mag) {
-        // magnitude: the absolute per-pixel contributions through the absolute Jacobian
+        // magnitude: the per-pixel contributions' magnitudes through the projection's partials
+        // taken as sums of magnitudes (Mag)
+        using M11 = Mag<11>;
+        M11 mm[3], ms[3], mq[4], mop;
+        for (int i = 0; i < 3; ++i) mm[i] = M11::var(means[3 * g + i], i);
+        for (int i = 0; i < 3; ++i) ms[i] = M11::var(scales[3 * g + i], 3 + i);
+        for (int i = 0; i < 4; ++i) mq[i] = M11::var(quats[4 * g + i], 6 + i);
+        mop = M11::var(opac[g], 10);
+        Proj<M11> pm = project<M11>(mm, ms, mq, mop, sh + g * K * 3, K, deg, cv[c], o, on ? mo : nullptr);
+        const M11* mouts[10] = {&pm.mx, &pm.my, &pm.ca, &pm.cb, &pm.cc, &pm.op, &pm.rgb[0], &pm.rgb[1], &pm.rgb[2],
+                                &pm.z};
         const double* ga = g2abs.data() + (c * n + g) * GM;
         for (int j = 0; j < 10; ++j)
-          for (int k = 0; k < 11; ++k) mag[k] += ga[j] * std::fabs(outs[j]->d[k]);
+          for (int k = 0; k < 11; ++k) mag[k] += ga[j] * mouts[j]->d[k];
         for (int ch = 0; ch < 3; ++ch) {
           if (p.flags & (1u << ch)) continue;
           for (int k = 0; k < nb && k < K; ++k) mag_sh[k * 3 + ch] += std::fabs(p.Y[k]) * ga[6 + ch];

@@ -5,7 +5,7 @@ quaternions, SH coefficients, optional per-image 3x4 appearance transforms, opti
 appearance transform of Sec. 3.5.1: Gaussian and image embeddings and its packed weights), applies the
 activations in torch (exp, sigmoid), and renders through the CUDA library; backward calls the
 library's backward and lets torch chain the activations. With ``recompute=True`` the forward
-keeps only 12 bytes per pixel and the backward re-runs the binning (Sec. 3.1 rendering of
+keeps only 16 bytes per pixel and the backward re-runs the binning (Sec. 3.1 rendering of
 tens of millions of Gaussians at 4K without storing the pair lists).
 """
 from __future__ import annotations

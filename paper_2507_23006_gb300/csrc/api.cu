@@ -2,13 +2,10 @@
 //
 // Forward launch sequence on the caller's stream (Sec. 3.1, Eq. 2 and the tile-based binning):
 //   preprocess (projection + colour + cull, compacted by a chained scan)
-//   -> radix sort of the visible records by depth (4 onesweep passes)
-//   -> [tile-cull counts] -> chained scan of per-record tile counts (pair offsets)
+//   -> pair counts per tile -> chained scan over the tiles (each tile's range, P)
 //   -> one stream synchronisation to read V and P and size the pair buffers
-//   -> duplicate-with-keys -> radix sort of the pairs by tile (stable; 1-3 passes)
-//   -> tile ranges -> blend.
-// Sorting by depth first and then stably by tile yields the (tile, depth, index) order with
-// 32-bit keys only.
+//   -> pairs placed in their tiles' ranges -> each tile's list sorted by (depth, index)
+//   -> blend.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -37,14 +34,14 @@ struct gsr_ctx {
   std::string last_error;
   size_t held = 0;
   // scratch
-  Buf seg_begin, seg_start;
-  Buf rec, dkeys, dvals, touched, owner;  // binning (recompute / no-state mode)
-  Buf dkeys_s, dvals_s, sort_ktmp, sort_vtmp, sort_hist, sort_status;
-  Buf cnt_sorted, offsets, pre_status, scan_status, misc;
-  Buf pkeys, pvals, pkeys_s, pvals_s, ranges;  // pairs (no-state mode)
+  Buf seg_begin, seg_start, seg_cams;
+  Buf rec, owner;                              // records (recompute / no-state mode)
+  Buf sort_ktmp, sort_vtmp, sort_hist, sort_status;  // gsr_sort_pairs_u32
+  Buf pre_status, scan_status, misc, tile_ctr;
+  Buf pair_keys, key_scratch, pvals_s, ranges;  // pairs (pvals_s, ranges: no-state mode)
   Buf pix_T, pix_n, pix_D;                     // per-pixel state (no-state mode)
   Buf g2d, gaff;
-  // host pinned staging: [0] V (u32), [1] err (int), [2..3] P (u64)
+  // host pinned staging of the binning counters (misc, 32 bytes) and the error word
   void* pinned = nullptr;
   int* d_err = nullptr;  // 64 bytes: error word at 0, blend counters (4 x u64) at byte 8
   // profiling
@@ -82,7 +79,6 @@ struct gsr_fwd_state {
   gsr_ctx* ctx = nullptr;
   gsr_state_info info{};
   bool has_bins = false;
-  int tile_bits = 1;
   Buf rec, owner, pvals_s, ranges;
   Buf T_final, n_contrib, D;
 };
@@ -164,7 +160,7 @@ bool ensure_zeroed(gsr_ctx* ctx, Buf& b, size_t bytes, cudaStream_t s) {
 // arrays are cleared and the count restarts.
 uint32_t next_epoch(gsr_ctx* ctx, cudaStream_t s) {
   if (++ctx->epoch >= (1u << 30)) {
-    Buf* st[] = {&ctx->pre_status, &ctx->scan_status, &ctx->sort_status};
+    Buf* st[] = {&ctx->pre_status, &ctx->scan_status, &ctx->sort_status};  // every chained scan's words
     for (Buf* b : st)
       if (b->p) cudaMemsetAsync(b->p, 0, b->cap, s);
     ctx->epoch = 1;
@@ -248,6 +244,7 @@ gsr_status validate(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_camera* cams
   if (g->attr_dtype < 0 || g->attr_dtype > 2 || g->sh_dtype < 0 || g->sh_dtype > 2)
     return set_err(ctx, GSR_ERR_INVALID_ARG, "unknown dtype");
   if (g->nsegs < 0 || (g->nsegs > 0 && !g->segs)) return set_err(ctx, GSR_ERR_INVALID_ARG, "bad segment list");
+  if (g->seg_cams && !g->segs) return set_err(ctx, GSR_ERR_INVALID_ARG, "segment camera masks without segments");
   if (g->mlp && !g->mlp->cached && (!g->mlp->image_embed || !g->mlp->params || (g->n > 0 && !g->mlp->gauss_embed)))
     return set_err(ctx, GSR_ERR_INVALID_ARG, "null appearance-transform array");
   if (g->mlp && g->mlp->cached && reinterpret_cast<uintptr_t>(g->mlp->cached) % 16 != 0)
@@ -317,11 +314,6 @@ CamBatch make_cams(const gsr_camera* cams, int C, long long* npix) {
   return cb;
 }
 
-int bits_for(long long v) {
-  int b = 1;
-  while ((1ll << b) < v) ++b;
-  return b;
-}
 
 #define GSR_TRY_ALLOC(buf, bytes)                                          \
   do {                                                                     \
@@ -379,6 +371,42 @@ void set_gauss_fields(const gsr_gaussians* g, GaussArgs& ga) {
   ga.mlp_cached = g->mlp ? g->mlp->cached : nullptr;
 }
 
+// Uploads the segment list (array index and selected index of each segment's first Gaussian, and
+// the cameras that render it) and fills the kernels' segment map; an identity map without
+// segments. Copies from pageable host memory return once the data is staged, so the host
+// vectors may go when this returns and the stream is not synchronised.
+gsr_status upload_segments(gsr_ctx* ctx, const gsr_gaussians* g, SegMap* m, cudaStream_t s) {
+  m->nsegs = 0;
+  m->begin = nullptr;
+  m->start = nullptr;
+  m->cams = nullptr;
+  if (!g->segs) return GSR_OK;
+  const int ns = std::max(g->nsegs, 1);
+  GSR_TRY_ALLOC(ctx->seg_begin, sizeof(long long) * ns);
+  GSR_TRY_ALLOC(ctx->seg_start, sizeof(long long) * ns);
+  if (g->seg_cams) GSR_TRY_ALLOC(ctx->seg_cams, sizeof(uint32_t) * ns);
+  std::vector<long long> hb(ns, 0), hs(ns, 0);
+  std::vector<uint32_t> hc(ns, 0);
+  long long acc = 0;
+  for (int k = 0; k < g->nsegs; ++k) {
+    hb[k] = g->segs[k].begin;
+    hs[k] = acc;  // an empty segment starts where the next one does: the search takes the last
+    acc += g->segs[k].count;
+    if (g->seg_cams) hc[k] = g->seg_cams[k];
+  }
+  cudaError_t e = cudaMemcpyAsync(ctx->seg_begin.p, hb.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->seg_start.p, hs.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && g->seg_cams)
+    e = cudaMemcpyAsync(ctx->seg_cams.p, hc.data(), sizeof(uint32_t) * ns, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "segment upload");
+  m->nsegs = g->nsegs;
+  m->begin = as<long long>(ctx->seg_begin);
+  m->start = as<long long>(ctx->seg_start);
+  m->cams = g->seg_cams ? as<uint32_t>(ctx->seg_cams) : nullptr;
+  return GSR_OK;
+}
+
 gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb, const gsr_opts* o, BinOut bo,
                        long long* V_out, long long* P_out, cudaStream_t s) {
   const long long N = render_count(g);
@@ -387,74 +415,39 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   // segment map
   GaussArgs ga;
   ga.n_render = N;
-  ga.segs.nsegs = 0;
-  ga.segs.begin = nullptr;
-  ga.segs.start = nullptr;
-  if (g->segs) {
-    const int ns = std::max(g->nsegs, 1);
-    GSR_TRY_ALLOC(ctx->seg_begin, sizeof(long long) * ns);
-    GSR_TRY_ALLOC(ctx->seg_start, sizeof(long long) * ns);
-    std::vector<long long> hb(ns, 0), hs(ns, 0);
-    long long acc = 0;
-    for (int k = 0; k < g->nsegs; ++k) {
-      hb[k] = g->segs[k].begin;
-      hs[k] = acc;
-      acc += g->segs[k].count;
-    }
-    // skip empty segments by giving them the start of the next one (search takes the last)
-    cudaError_t e = cudaMemcpyAsync(ctx->seg_begin.p, hb.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(ctx->seg_start.p, hs.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_err(ctx, e, "segment upload");
-    // the host vectors must outlive the copies
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_err(ctx, e, "segment upload sync");
-    ga.segs.nsegs = g->nsegs;
-    ga.segs.begin = as<long long>(ctx->seg_begin);
-    ga.segs.start = as<long long>(ctx->seg_start);
-  }
+  const gsr_status sst = upload_segments(ctx, g, &ga.segs, s);
+  if (sst != GSR_OK) return sst;
   set_gauss_fields(g, ga);
 
   const int pre_blocks = static_cast<int>((N + kPreTile - 1) / kPreTile);
+  const int tiles = cb.total_tiles;
   GSR_TRY_ALLOC(*bo.rec, sizeof(Rec) * capv);
   GSR_TRY_ALLOC(*bo.owner, sizeof(uint32_t) * capv);
-  GSR_TRY_ALLOC(ctx->dkeys, sizeof(uint32_t) * capv);
-  GSR_TRY_ALLOC(ctx->dvals, sizeof(uint32_t) * capv);
-  GSR_TRY_ALLOC(ctx->touched, sizeof(uint32_t) * capv);
-  GSR_TRY_ALLOC(ctx->dkeys_s, sizeof(uint32_t) * capv);
-  GSR_TRY_ALLOC(ctx->dvals_s, sizeof(uint32_t) * capv);
-  GSR_TRY_ALLOC(ctx->offsets, sizeof(uint32_t) * capv);
+  GSR_TRY_ALLOC(*bo.ranges, sizeof(uint2) * std::max(tiles, 1));
+  GSR_TRY_ALLOC(ctx->tile_ctr, sizeof(uint32_t) * std::max(tiles, 1));
   if (!ensure_zeroed(ctx, ctx->pre_status, sizeof(unsigned long long) * std::max(pre_blocks, 1), s))
     return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
-  const long long scan_blocks = (capv + kScanThreads * kScanItems - 1) / (kScanThreads * kScanItems);
+  const long long scan_blocks = (tiles + kScanThreads * kScanItems - 1) / (kScanThreads * kScanItems);
   if (!ensure_zeroed(ctx, ctx->scan_status, sizeof(unsigned long long) * (scan_blocks + 1), s))
     return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
-  // misc: [0] preprocess block counter, [1] V, [2] scan block counter, [3] pad, [4..5] P (u64)
+  // misc (32-bit words): [0] preprocess block counter, [1] V, [2] tile-scan block counter,
+  // [3] largest tile's pair count, [4..5] P (64-bit)
   GSR_TRY_ALLOC(ctx->misc, 64);
   uint32_t* misc = as<uint32_t>(ctx->misc);
-  uint32_t* d_counter = misc + 0;
   uint32_t* d_V = misc + 1;
-  uint32_t* d_scan_counter = misc + 2;
   unsigned long long* d_P = reinterpret_cast<unsigned long long*>(misc + 4);
-  unsigned long long* d_scan_status = as<unsigned long long>(ctx->scan_status);
+  uint32_t* tile_ctr = as<uint32_t>(ctx->tile_ctr);
+  // The error word is not cleared here: a pair-placement overflow of the previous launch (which
+  // runs after that launch's read-back) is reported by this one's, then the word is cleared.
   cudaError_t e = cudaMemsetAsync(ctx->misc.p, 0, 64, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tile_ctr, 0, sizeof(uint32_t) * tiles, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
 
-  // sort scratch first: the preprocess counts the depth keys' digits for the sort
-  if (!ensure_sort(ctx, capv, s)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
-  SortScratch sc = sort_scratch(ctx);
-  sort_clear_counts(sc, s);
-
   PreOut po;
-  po.key_counts = sc.hist;
   po.rec = as<Rec>(*bo.rec);
-  po.depth_keys = as<uint32_t>(ctx->dkeys);
-  po.depth_vals = as<uint32_t>(ctx->dvals);
-  po.touched = as<uint32_t>(ctx->touched);
   po.owner = as<uint32_t>(*bo.owner);
   po.status = as<unsigned long long>(ctx->pre_status);
-  po.counter = d_counter;
+  po.counter = misc + 0;
   po.v_total = d_V;
   po.err = ctx->d_err;
   po.epoch = next_epoch(ctx, s);
@@ -468,28 +461,18 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   e = start_prezero(ctx, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
 
-  // depth sort of the visible records (V read on the device; digits counted by the preprocess)
+  // pairs per tile, then each tile's range and the total P
   if (N * C > 0) {
-    StageTimer tm(ctx, GSR_STAGE_DEPTH_SORT, s);
-    radix_sort_u32(as<uint32_t>(ctx->dkeys), as<uint32_t>(ctx->dvals), as<uint32_t>(ctx->dkeys_s),
-                   as<uint32_t>(ctx->dvals_s), d_V, capv, 0, 32, sc, next_epoch(ctx, s), false, true, ctx->d_err, s);
-  }
-
-  const uint32_t* cnt_sorted = nullptr;
-  if (o->tile_cull && N * C > 0) {
-    GSR_TRY_ALLOC(ctx->cnt_sorted, sizeof(uint32_t) * capv);
     StageTimer tm(ctx, GSR_STAGE_TILE_COUNT, s);
-    launch_duplicate(as<Rec>(*bo.rec), as<uint32_t>(ctx->dvals_s), nullptr, d_V, capv, cb, 1,
-                     as<uint32_t>(ctx->cnt_sorted), nullptr, nullptr, nullptr, 0, 4 * ctx->grid_cap, s);
-    cnt_sorted = as<uint32_t>(ctx->cnt_sorted);
+    launch_bin_pairs(as<Rec>(*bo.rec), d_V, capv, cb, o->tile_cull, tile_ctr, nullptr, nullptr, ctx->d_err,
+                     4 * ctx->grid_cap, s);
   }
   {
-    StageTimer tm(ctx, GSR_STAGE_PAIR_SCAN, s);
-    pair_offsets_scan(as<uint32_t>(ctx->touched), as<uint32_t>(ctx->dvals_s), cnt_sorted, as<uint32_t>(ctx->offsets),
-                      d_V, capv, d_scan_status, d_scan_counter, d_P, ctx->d_err, next_epoch(ctx, s), ctx->grid_cap,
-                      ctx->wait, s);
+    StageTimer tm(ctx, GSR_STAGE_TILE_SCAN, s);
+    launch_tile_scan(tile_ctr, as<uint2>(*bo.ranges), tiles, as<unsigned long long>(ctx->scan_status), misc + 2, d_P,
+                     misc + 3, next_epoch(ctx, s), ctx->d_err, ctx->wait, ctx->grid_cap, s);
   }
-  // read V, P and the error word
+  // read V, P, the largest tile and the error word
   uint32_t* h = static_cast<uint32_t*>(ctx->pinned);
   {
     StageTimer tm(ctx, GSR_STAGE_READBACK, s);
@@ -501,11 +484,17 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(ctx, e, "binning launch");
   const long long V = N > 0 ? h[1] : 0;
+  const uint32_t max_count = h[3];
   unsigned long long Pu;
   std::memcpy(&Pu, h + 4, sizeof(Pu));
   const int derr = static_cast<int>(h[8]);
+  if (derr) {
+    e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
+  }
   if (derr & kErrTimeout) return set_err(ctx, GSR_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out in binning");
-  if (derr & kErrOverflow) return set_err(ctx, GSR_ERR_UNSUPPORTED, "more than 2^32 (tile, Gaussian) pairs");
+  if (derr & kErrOverflow)
+    return set_err(ctx, GSR_ERR_UNSUPPORTED, "pair count overflow (more than 2^32 pairs, or a placement past its tile)");
   if (V > capv) return set_err(ctx, GSR_ERR_CUDA, "inconsistent visible count");
   const long long P = V > 0 ? static_cast<long long>(Pu) : 0;
   if (P >= (1ll << 30)) return set_err(ctx, GSR_ERR_UNSUPPORTED, "more than 2^30 (tile, Gaussian) pairs");
@@ -514,37 +503,27 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   // the next preprocess picks its variant from this launch's survivor ratio
   ctx->pre_dense = 4 * V > N * C;
 
-  // duplicate, sort by tile, ranges
+  // place the pairs in their tiles' ranges, then order every tile's list by (depth, index)
   const long long Pc = std::max<long long>(P, 1);
-  GSR_TRY_ALLOC(ctx->pkeys, sizeof(uint32_t) * Pc);
-  GSR_TRY_ALLOC(ctx->pvals, sizeof(uint32_t) * Pc);
-  GSR_TRY_ALLOC(ctx->pkeys_s, sizeof(uint32_t) * Pc);
+  GSR_TRY_ALLOC(ctx->pair_keys, sizeof(unsigned long long) * Pc);
   GSR_TRY_ALLOC(*bo.pvals_s, sizeof(uint32_t) * Pc);
-  GSR_TRY_ALLOC(*bo.ranges, sizeof(uint2) * std::max(cb.total_tiles, 1));
+  int cap = 1;
+  while (cap < static_cast<long long>(max_count) && cap < kTileSortCap) cap <<= 1;
+  unsigned long long* scratch = nullptr;
+  if (max_count > static_cast<uint32_t>(kTileSortCap)) {
+    GSR_TRY_ALLOC(ctx->key_scratch, sizeof(unsigned long long) * Pc);
+    scratch = as<unsigned long long>(ctx->key_scratch);
+  }
   if (P > 0) {
-    if (!ensure_sort(ctx, Pc, s)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
-    sc = sort_scratch(ctx);
-    const int tb = bits_for(cb.total_tiles);
-    sort_clear_counts(sc, s);  // the pair emitter counts the tile keys' digits
     {
-      StageTimer tm(ctx, GSR_STAGE_DUPLICATE, s);
-      launch_duplicate(as<Rec>(*bo.rec), as<uint32_t>(ctx->dvals_s), as<uint32_t>(ctx->offsets), d_V, V, cb,
-                       o->tile_cull, nullptr, as<uint32_t>(ctx->pkeys), as<uint32_t>(ctx->pvals), sc.hist, tb,
-                       4 * ctx->grid_cap, s);
+      StageTimer tm(ctx, GSR_STAGE_PLACE, s);
+      launch_bin_pairs(as<Rec>(*bo.rec), d_V, V, cb, o->tile_cull, tile_ctr, as<uint2>(*bo.ranges),
+                       as<unsigned long long>(ctx->pair_keys), ctx->d_err, 4 * ctx->grid_cap, s);
     }
     {
       StageTimer tm(ctx, GSR_STAGE_TILE_SORT, s);
-      radix_sort_u32(as<uint32_t>(ctx->pkeys), as<uint32_t>(ctx->pvals), as<uint32_t>(ctx->pkeys_s),
-                     as<uint32_t>(*bo.pvals_s), nullptr, P, 0, tb, sc, next_epoch(ctx, s), false, true, ctx->d_err, s);
-    }
-  }
-  {
-    StageTimer tm(ctx, GSR_STAGE_RANGES, s);
-    if (P > 0) {
-      launch_ranges(as<uint32_t>(ctx->pkeys_s), P, cb.total_tiles, as<uint2>(*bo.ranges), s);
-    } else {
-      e = cudaMemsetAsync(bo.ranges->p, 0, sizeof(uint2) * std::max(cb.total_tiles, 1), s);
-      if (e != cudaSuccess) return cuda_err(ctx, e, "memset ranges");
+      launch_tile_sort(as<unsigned long long>(ctx->pair_keys), as<uint2>(*bo.ranges), tiles, as<uint32_t>(*bo.pvals_s),
+                       scratch, cap, s);
     }
   }
   e = cudaGetLastError();
@@ -632,11 +611,10 @@ void gsr_destroy(gsr_ctx* ctx) {
     delete st;
   }
   ctx->state_pool.clear();
-  Buf* all[] = {&ctx->seg_begin, &ctx->seg_start, &ctx->rec, &ctx->dkeys, &ctx->dvals, &ctx->touched,
-                &ctx->owner, &ctx->dkeys_s, &ctx->dvals_s, &ctx->sort_ktmp, &ctx->sort_vtmp,
-                &ctx->sort_hist, &ctx->sort_status, &ctx->cnt_sorted, &ctx->offsets,
-                &ctx->pre_status, &ctx->scan_status, &ctx->misc, &ctx->pkeys, &ctx->pvals, &ctx->pkeys_s, &ctx->pvals_s,
-                &ctx->ranges, &ctx->pix_T, &ctx->pix_n, &ctx->pix_D, &ctx->g2d, &ctx->gaff};
+  Buf* all[] = {&ctx->seg_begin, &ctx->seg_start, &ctx->seg_cams, &ctx->rec, &ctx->owner, &ctx->sort_ktmp,
+                &ctx->sort_vtmp, &ctx->sort_hist, &ctx->sort_status, &ctx->pre_status, &ctx->scan_status, &ctx->misc,
+                &ctx->tile_ctr, &ctx->pair_keys, &ctx->key_scratch, &ctx->pvals_s, &ctx->ranges, &ctx->pix_T,
+                &ctx->pix_n, &ctx->pix_D, &ctx->g2d, &ctx->gaff};
   for (Buf* b : all) release(ctx, *b, nullptr);
   for (auto& r : ctx->prof_recs) {
     cudaEventDestroy(r.a);
@@ -667,11 +645,10 @@ gsr_status gsr_workspace_query(gsr_ctx* ctx, int64_t n_render, const gsr_camera*
   const size_t capv = static_cast<size_t>(std::max<int64_t>(1, n_render * n_cams));
   const size_t P = static_cast<size_t>(std::max<int64_t>(1, expected_pairs));
   size_t b = 0;
-  b += capv * (sizeof(Rec) + 8 * sizeof(uint32_t));  // records, owners, keys, values, counts, offsets
-  b += std::max(capv, P) * 2 * sizeof(uint32_t) + sort_status_words(std::max(capv, P)) * 4 * sizeof(unsigned long long);
-  b += P * 4 * sizeof(uint32_t);                              // pairs
-  b += static_cast<size_t>(cb.total_tiles) * sizeof(uint2);
-  b += static_cast<size_t>(npix) * 3 * sizeof(float);         // per-pixel state
+  b += capv * (sizeof(Rec) + sizeof(uint32_t));                  // records, owners
+  b += P * (2 * sizeof(unsigned long long) + sizeof(uint32_t));  // pair keys, merge scratch, sorted records
+  b += static_cast<size_t>(cb.total_tiles) * (sizeof(uint2) + sizeof(uint32_t));  // ranges, counters
+  b += static_cast<size_t>(npix) * 4 * sizeof(float);            // per-pixel state
   *bytes_out = b;
   return GSR_OK;
 }
@@ -722,7 +699,7 @@ gsr_status gsr_render_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_ca
   Buf* pn = stt ? &stt->n_contrib : &ctx->pix_n;
   Buf* pD = stt ? &stt->D : &ctx->pix_D;
   if (!ensure(ctx, *pT, sizeof(float) * npix, s) || !ensure(ctx, *pn, sizeof(uint32_t) * npix, s) ||
-      !ensure(ctx, *pD, sizeof(float) * npix, s)) {
+      !ensure(ctx, *pD, sizeof(float2) * npix, s)) {
     if (stt) gsr_state_release(ctx, stt);
     return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
   }
@@ -733,7 +710,7 @@ gsr_status gsr_render_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_ca
   bf.alpha = out->alpha;
   bf.T_final = as<float>(*pT);
   bf.n_contrib = as<uint32_t>(*pn);
-  bf.D_state = as<float>(*pD);
+  bf.D_state = as<float2>(*pD);
   {
     StageTimer tm(ctx, GSR_STAGE_BLEND_FWD, s);
     launch_blend_fwd(as<Rec>(*bo.rec), as<uint32_t>(*bo.pvals_s), as<uint2>(*bo.ranges), cb, opts->bg, bf,
@@ -751,7 +728,6 @@ gsr_status gsr_render_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_ca
     stt->info.n_pairs = P;
     stt->info.n_tiles = cb.total_tiles;
     stt->info.n_pixels = npix;
-    stt->tile_bits = bits_for(cb.total_tiles);
     *state_out = stt;
   }
   return GSR_OK;
@@ -888,7 +864,7 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
   bi.d_alpha = dout->alpha;
   bi.T_final = static_cast<const float*>(state->T_final.p);
   bi.n_contrib = static_cast<const uint32_t*>(state->n_contrib.p);
-  bi.D_state = static_cast<const float*>(state->D.p);
+  bi.D_state = static_cast<const float2*>(state->D.p);
   {
     StageTimer tm(ctx, GSR_STAGE_BLEND_BWD, s);
     launch_blend_bwd(as<Rec>(*bo.rec), as<uint32_t>(*bo.pvals_s), as<uint2>(*bo.ranges), cb, opts->bg, bi,
@@ -900,24 +876,16 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
   }
   GaussArgs ga;
   ga.n_render = N;
-  ga.segs.nsegs = g->segs ? g->nsegs : 0;
-  ga.segs.begin = g->segs ? as<long long>(ctx->seg_begin) : nullptr;
-  ga.segs.start = g->segs ? as<long long>(ctx->seg_start) : nullptr;
-  if (g->segs && state->has_bins) {
-    // the segment table may have been overwritten by another forward: upload it again
-    std::vector<long long> hb(std::max(g->nsegs, 1), 0), hs(std::max(g->nsegs, 1), 0);
-    long long acc = 0;
-    for (int k = 0; k < g->nsegs; ++k) { hb[k] = g->segs[k].begin; hs[k] = acc; acc += g->segs[k].count; }
-    if (!ensure(ctx, ctx->seg_begin, sizeof(long long) * hb.size(), s) ||
-        !ensure(ctx, ctx->seg_start, sizeof(long long) * hs.size(), s))
-      return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
-    e = cudaMemcpyAsync(ctx->seg_begin.p, hb.data(), sizeof(long long) * hb.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(ctx->seg_start.p, hs.data(), sizeof(long long) * hs.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_err(ctx, e, "segment upload");
+  // the segment table may have been overwritten by another call since the forward: upload it
+  // again (the recompute path above has just done so)
+  if (state->has_bins || !g->segs) {
+    st = upload_segments(ctx, g, &ga.segs, s);
+    if (st != GSR_OK) return st;
+  } else {
+    ga.segs.nsegs = g->nsegs;
     ga.segs.begin = as<long long>(ctx->seg_begin);
     ga.segs.start = as<long long>(ctx->seg_start);
+    ga.segs.cams = g->seg_cams ? as<uint32_t>(ctx->seg_cams) : nullptr;
   }
   set_gauss_fields(g, ga);
   ParamGrads pg;
@@ -987,7 +955,7 @@ gsr_status gsr_state_copy(const gsr_fwd_state* state, int32_t which, void* dst, 
     case GSR_BUF_RANGES: pick(state->ranges, ctx->ranges, 8 * I.n_tiles); break;
     case GSR_BUF_T_FINAL: src = state->T_final.p; have = std::min<size_t>(4 * I.n_pixels, state->T_final.cap); break;
     case GSR_BUF_N_CONTRIB: src = state->n_contrib.p; have = std::min<size_t>(4 * I.n_pixels, state->n_contrib.cap); break;
-    case GSR_BUF_DEPTH_ACC: src = state->D.p; have = std::min<size_t>(4 * I.n_pixels, state->D.cap); break;
+    case GSR_BUF_DEPTH_STATE: src = state->D.p; have = std::min<size_t>(8 * I.n_pixels, state->D.cap); break;
     default: return GSR_ERR_INVALID_ARG;
   }
   if (!src || bytes > have) return GSR_ERR_INVALID_ARG;

@@ -58,6 +58,7 @@ struct SegMap {
   int nsegs;                   // 0: identity
   const long long* begin;      // [nsegs] array index of the segment's first Gaussian
   const long long* start;      // [nsegs] selected index of the segment's first Gaussian
+  const uint32_t* cams;        // [nsegs] cameras of the launch that render the segment, or NULL (all)
 };
 
 // Splat record: 64 bytes (two 32-byte sectors), read by the blend kernels through the sorted
@@ -83,14 +84,30 @@ __device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16* p, long
   return __bfloat162float(p[i]);
 }
 
-__device__ __forceinline__ long long seg_map(const SegMap& m, long long i) {
-  if (m.nsegs == 0) return i;
+__device__ __forceinline__ int seg_of(const SegMap& m, long long i) {
   int lo = 0, hi = m.nsegs - 1;
   while (lo < hi) {  // last segment with start <= i
     int mid = (lo + hi + 1) >> 1;
     if (m.start[mid] <= i) lo = mid; else hi = mid - 1;
   }
-  return m.begin[lo] + (i - m.start[lo]);
+  return lo;
+}
+
+__device__ __forceinline__ long long seg_map(const SegMap& m, long long i) {
+  if (m.nsegs == 0) return i;
+  const int k = seg_of(m, i);
+  return m.begin[k] + (i - m.start[k]);
+}
+
+// seg_map, and the cameras of the launch that render selected Gaussian i (bit c = camera c).
+__device__ __forceinline__ long long seg_map_cams(const SegMap& m, long long i, uint32_t* cams) {
+  if (m.nsegs == 0) {
+    *cams = 0xffffffffu;
+    return i;
+  }
+  const int k = seg_of(m, i);
+  *cams = m.cams ? m.cams[k] : 0xffffffffu;
+  return m.begin[k] + (i - m.start[k]);
 }
 
 // ---- arguments of the kernels ---------------------------------------------------------------
@@ -126,16 +143,12 @@ constexpr int kMlpParams = kMlpB2 + kMlpOut;    // 1700
 
 struct PreOut {
   Rec* rec;                    // [cap_v]
-  uint32_t* depth_keys;        // [cap_v]
-  uint32_t* depth_vals;        // [cap_v]
-  uint32_t* touched;           // [cap_v] tiles in the rectangle
   uint32_t* owner;             // [cap_v] rendered index of the Gaussian of each record
   unsigned long long* status;  // [blocks] chained-scan status words (epoch-tagged)
   uint32_t* counter;           // dynamic block index
   uint32_t* v_total;           // out: V
   int* err;
   uint32_t epoch;              // tag of this launch's status words
-  uint32_t* key_counts;        // [4][256] digit counts of the depth keys (for their sort), added to
   WaitCfg wait;
 };
 
@@ -229,21 +242,26 @@ void radix_sort_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
                     const uint32_t* d_n, long long max_n, int begin_bit, int end_bit, const SortScratch& sc,
                     uint32_t epoch, bool clear_status, bool counts_ready, int* err, cudaStream_t s);
 
-// Exclusive scan of per-record tile counts in depth order: counts[i] = touched[order[i]]
-// (or cnt_sorted[i] when given), offsets[i] out, *p_total = sum. n from *d_n.
+// Binning of the V visible records (V read from *d_n, at most max_n) into (tile, record) pairs:
+// launch_bin_pairs with keys == nullptr adds each tile's pair count to tile_ctr (zeroed before;
+// ranges unused);
+// launch_tile_scan turns the counts into ranges [start, end), P (*p_total), the largest count
+// (*max_count, zeroed before) and per-tile cursors (in tile_ctr); launch_bin_pairs with keys
+// places each pair's key (depth bits << 32 | record) in its tile's range (a pair past the range end
+// sets kErrOverflow in *err and is not written); launch_tile_sort sorts
+// every tile's keys and writes the records in that order into vals. Tiles with more than `cap`
+// pairs (a power of two) are sorted in runs merged through `scratch` ([P], may be null if none is).
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
-void pair_offsets_scan(const uint32_t* touched, const uint32_t* order, const uint32_t* cnt_sorted,
-                       uint32_t* offsets, const uint32_t* d_n, long long max_n,
-                       unsigned long long* status, uint32_t* counter, unsigned long long* p_total, int* err,
-                       uint32_t epoch, int grid_cap, WaitCfg wait, cudaStream_t s);
-
-// Duplicate-with-keys (warp-cooperative). count_only: writes cnt_sorted[i] (tile-culled counts).
-void launch_duplicate(const Rec* rec, const uint32_t* order, const uint32_t* offsets, const uint32_t* d_n,
-                      long long max_n, const CamBatch& cams, int tile_cull, uint32_t* cnt_sorted,
-                      uint32_t* pair_keys, uint32_t* pair_vals, uint32_t* key_counts, int key_bits, int max_blocks,
+constexpr int kTileSortCap = 4096;
+void launch_bin_pairs(const Rec* rec, const uint32_t* d_n, long long max_n, const CamBatch& cams, int tile_cull,
+                      uint32_t* tile_ctr, const uint2* ranges, unsigned long long* keys, int* err, int max_blocks,
                       cudaStream_t s);
-void launch_ranges(const uint32_t* sorted_keys, long long P, int n_tiles, uint2* ranges, cudaStream_t s);
+void launch_tile_scan(uint32_t* tile_ctr, uint2* ranges, int n_tiles, unsigned long long* status, uint32_t* counter,
+                      unsigned long long* p_total, uint32_t* max_count, uint32_t epoch, int* err, WaitCfg wait,
+                      int grid_cap, cudaStream_t s);
+void launch_tile_sort(unsigned long long* keys, const uint2* ranges, int n_tiles, uint32_t* vals,
+                      unsigned long long* scratch, int cap, cudaStream_t s);
 
 struct BlendFwdOut {
   float* rgb;
@@ -252,7 +270,7 @@ struct BlendFwdOut {
   float* alpha;
   float* T_final;
   uint32_t* n_contrib;
-  float* D_state;
+  float2* D_state;  // per pixel: depth of the first contributor, sum of (z - that depth) w
 };
 // counters (nullable): [0] evaluations, [1] contributions (forward), [2], [3] (backward)
 void launch_blend_fwd(const Rec* rec, const uint32_t* pair_vals, const uint2* ranges, const CamBatch& cams,
@@ -265,7 +283,7 @@ struct BlendBwdIn {
   const float* d_alpha;
   const float* T_final;
   const uint32_t* n_contrib;
-  const float* D_state;
+  const float2* D_state;
 };
 void launch_blend_bwd(const Rec* rec, const uint32_t* pair_vals, const uint2* ranges, const CamBatch& cams,
                       const float* bg, const BlendBwdIn& in, Grad2D* g2d, float* g_aff, int absgrad,

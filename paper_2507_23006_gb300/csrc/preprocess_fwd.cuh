@@ -348,13 +348,7 @@ __device__ __forceinline__ Rec record_geometry(const Proj& P, int c, float eps) 
 }
 
 __device__ __forceinline__ void write_record(const PreOut& out, long long v, const Rec& rr, long long i) {
-  const uint32_t lo = __float_as_uint(rr.c.z), hi = __float_as_uint(rr.c.w);
-  const uint32_t w = ((lo >> 16) & 0xffffu) - (lo & 0xffffu);
-  const uint32_t h = ((hi >> 16) & 0x7ffu) - (hi & 0xffffu);
   out.rec[v] = rr;
-  out.depth_keys[v] = __float_as_uint(rr.a.w);
-  out.depth_vals[v] = static_cast<uint32_t>(v);
-  out.touched[v] = w * h;
   out.owner[v] = static_cast<uint32_t>(i);
 }
 
@@ -510,7 +504,6 @@ __global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_fwd_kernel
   __shared__ float4 s_rec[kPreStage][4];
   __shared__ uint32_t s_meta[kPreStage];  // slot | camera << 16
   __shared__ MlpSmem s_mlp;                // appearance transform, when on
-  __shared__ uint32_t s_digits[4 * 256];   // digit counts of the block's depth keys
   if (threadIdx.x == 0) {
     s_bid = atomicAdd(out.counter, 1u);
     s_count[0] = 0;
@@ -518,7 +511,6 @@ __global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_fwd_kernel
   }
   if (kMlp && !A.mlp_cached) mlp_load_smem(A, cams.C, s_mlp);  // read after the barrier that ends phase 1a
   if (threadIdx.x < kPreTile / 32) s_unstaged[threadIdx.x] = 0;
-  for (int k = threadIdx.x; k < 4 * 256; k += kPreThreads) s_digits[k] = 0;
   __syncthreads();
   const unsigned bid = s_bid;
   const long long base_i = static_cast<long long>(bid) * kPreTile;
@@ -526,11 +518,13 @@ __global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_fwd_kernel
   {
     Geo G[kPreItems];
     bool ok[kPreItems];
+    uint32_t seg_cams[kPreItems];  // cameras that render the Gaussian's segment
 #pragma unroll
     for (int j = 0; j < kPreItems; ++j) {  // every load first
       const long long i = base_i + j * kPreThreads + threadIdx.x;
       ok[j] = i < A.n_render;
-      if (ok[j]) load_mean_scale<AT>(A, seg_map(A.segs, i), G[j]);
+      seg_cams[j] = 0;
+      if (ok[j]) load_mean_scale<AT>(A, seg_map_cams(A.segs, i, &seg_cams[j]), G[j]);
     }
 #pragma unroll
     for (int j = 0; j < kPreItems; ++j) {
@@ -538,7 +532,7 @@ __global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_fwd_kernel
       uint32_t maybe = 0;
       if (ok[j])
         for (int c = 0; c < cams.C; ++c)
-          if (!surely_culled(G[j], cams.cam[c], eps)) maybe |= 1u << c;
+          if (((seg_cams[j] >> c) & 1u) && !surely_culled(G[j], cams.cam[c], eps)) maybe |= 1u << c;
       s_aux[slot] = maybe;
       s_mask[slot] = 0;
       list_append(maybe != 0, slot, s_list, &s_count[0], lane);
@@ -643,13 +637,8 @@ __global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_fwd_kernel
     rr.c = s_rec[e][2];
     rr.d = s_rec[e][3];
     write_record(out, v, rr, base_i + slot);
-    count_digits(__float_as_uint(rr.a.w), 0, 32, 4, s_digits);
   }
-  if (n_rec <= kPreStage) {  // block-uniform
-    __syncthreads();
-    flush_digit_counts(s_digits, 4, out.key_counts);
-    return;
-  }
+  if (n_rec <= kPreStage) return;  // block-uniform
   // records that did not fit the stage: every record of those Gaussians is computed again
   for (uint32_t k = threadIdx.x; k < n_maybe; k += kPreThreads) {
     const uint32_t slot = s_list[k];
@@ -678,12 +667,9 @@ __global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_fwd_kernel
       rr.c.x = 2.f * mo[1] * rgb[1];
       rr.c.y = 2.f * mo[2] * rgb[2];
       write_record(out, v, rr, i);
-      count_digits(__float_as_uint(rr.a.w), 0, 32, 4, s_digits);
       ++v;
     }
   }
-  __syncthreads();
-  flush_digit_counts(s_digits, 4, out.key_counts);
 }
 
 }  // namespace

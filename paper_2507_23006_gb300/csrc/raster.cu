@@ -1,10 +1,9 @@
 // Tile binning and the per-tile alpha blending of Sec. 3.1, Eq. 2, forward and backward.
 //
-//   duplicate:  every visible record, in depth order, emits one (tile, record) pair per tile of
-//               its 3-sigma rectangle, minus the tiles StopThePop culling drops (Sec. 3.4.2);
-//               a warp expands 32 records together, so one huge ground splat does not stall
-//               its neighbours.
-//   ranges:     [start, end) of each tile in the tile-sorted pair list.
+//   binning:    every visible record has one (tile, record) pair per tile of its 3-sigma
+//               rectangle, minus the tiles StopThePop culling drops (Sec. 3.4.2): the pairs are
+//               counted per tile, the counts scanned into each tile's [start, end), the pairs
+//               placed in their tile's range, and each tile's list sorted by (depth, index).
 //   blend fwd:  one 16x16 CTA per tile; records are staged in shared memory 256 at a time;
 //               each pixel blends front to back and stops at T < 1e-4; the CTA stops loading
 //               once every pixel is done.
@@ -14,6 +13,7 @@
 #include <algorithm>
 
 #include "gsr_internal.cuh"
+#include "scan_util.cuh"
 
 namespace gsr {
 namespace {
@@ -25,21 +25,27 @@ __device__ __forceinline__ int find_cam(const CamBatch& cams, int t) {
 }
 
 // Smallest Mahalanobis distance (p - m)^T Q (p - m) over the rectangle of pixel centres of a tile.
+// Every operation is explicitly rounded (no contraction left to the compiler), so the counting and
+// the placing pass of the binning, two separately compiled kernels, take the same decisions.
+__device__ __forceinline__ float quad_form(float a, float b, float c, float dx, float dy) {
+  return __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(a, dx), dx), __fmul_rn(__fmul_rn(2.f, b), __fmul_rn(dx, dy))),
+                   __fmul_rn(__fmul_rn(c, dy), dy));
+}
 __device__ __forceinline__ float tile_min_maha(float mx, float my, float a, float b, float c, float xlo,
                                                float xhi, float ylo, float yhi) {
   if (mx >= xlo && mx <= xhi && my >= ylo && my <= yhi) return 0.f;
   float best = INFINITY;
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
-    const float dx = (e ? xhi : xlo) - mx;
-    const float dy = fminf(fmaxf(-b * dx / c, ylo - my), yhi - my);
-    best = fminf(best, a * dx * dx + 2.f * b * dx * dy + c * dy * dy);
+    const float dx = __fsub_rn(e ? xhi : xlo, mx);
+    const float dy = fminf(fmaxf(__fdiv_rn(__fmul_rn(-b, dx), c), __fsub_rn(ylo, my)), __fsub_rn(yhi, my));
+    best = fminf(best, quad_form(a, b, c, dx, dy));
   }
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
-    const float dy = (e ? yhi : ylo) - my;
-    const float dx = fminf(fmaxf(-b * dy / a, xlo - mx), xhi - mx);
-    best = fminf(best, a * dx * dx + 2.f * b * dx * dy + c * dy * dy);
+    const float dy = __fsub_rn(e ? yhi : ylo, my);
+    const float dx = fminf(fmaxf(__fdiv_rn(__fmul_rn(-b, dy), a), __fsub_rn(xlo, mx)), __fsub_rn(xhi, mx));
+    best = fminf(best, quad_form(a, b, c, dx, dy));
   }
   return best;
 }
@@ -65,136 +71,235 @@ __device__ __forceinline__ uint32_t warp_block_mask(const float4 d, float x0, fl
   return m;
 }
 
-template <bool kCull, bool kCount>
-__global__ void __launch_bounds__(256) duplicate_kernel(const Rec* __restrict__ rec, const uint32_t* __restrict__ order,
-                                                        const uint32_t* __restrict__ offsets, const uint32_t* d_n,
-                                                        long long max_n, CamBatch cams, uint32_t* __restrict__ cnt_sorted,
-                                                        uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals,
-                                                        uint32_t* __restrict__ key_counts, int key_bits) {
-  __shared__ uint32_t s_cnt[8][32];
-  __shared__ uint32_t s_digits[4 * 256];  // digit counts of the emitted tile keys (for their sort)
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int passes = (key_bits + 7) / 8;
-  if (key_counts) {
-    for (int k = threadIdx.x; k < 4 * 256; k += blockDim.x) s_digits[k] = 0;
-    __syncthreads();
-  }
+// Counts (kPlace = false) or places (kPlace = true) the (tile, record) pairs of the visible
+// records: one per tile of a record's rectangle, minus the tiles StopThePop culling drops (kCull;
+// the same FP32 test in both passes, so they agree pair for pair). A warp takes 32 records and
+// shares their tiles out over its lanes, so one huge ground splat does not stall its neighbours.
+// Counting adds one to the tile's counter per kept pair; placing takes the pair's slot from the
+// tile's cursor (set to the tile's first slot by the scan) and writes the key (depth bits << 32 |
+// record index) there. The order inside a tile is then fixed by sorting those keys.
+template <bool kCull, bool kPlace>
+__global__ void __launch_bounds__(256) bin_pairs_kernel(const Rec* __restrict__ rec, const uint32_t* d_n, long long max_n,
+                                                        CamBatch cams, uint32_t* __restrict__ tile_ctr,
+                                                        const uint2* __restrict__ ranges,
+                                                        unsigned long long* __restrict__ keys, int* err) {
+  const int lane = threadIdx.x & 31;
   long long n = static_cast<long long>(*d_n);
   if (n > max_n) n = max_n;
-  // warps stride over the records 32 at a time (the grid is sized for the resident blocks, not
-  // for the capacity, so no block starts only to find nothing to do)
+  // warps stride over the records 32 at a time (the grid is sized for the resident blocks)
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
   for (long long base_i = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) & ~31ll; base_i < n;
        base_i += stride) {
-  const long long i = base_i + lane;
-  const bool valid = i < n;
-  uint32_t v = 0, off = 0, area = 0, lo = 0, hi = 0;
-  float4 ra = make_float4(0, 0, 0, 0), rb = ra;
-  if (valid) {
-    v = order[i];
-    const Rec r = rec[v];
-    ra = r.a;
-    rb = r.b;
-    lo = __float_as_uint(r.c.z);
-    hi = __float_as_uint(r.c.w);
-    area = ((lo >> 16) - (lo & 0xffffu)) * (((hi >> 16) & 0x7ffu) - (hi & 0xffffu));
-    if (!kCount) off = offsets[i];
-  }
-  uint32_t incl = area;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-  s_cnt[w][lane] = 0;
-  __syncwarp();
-  for (uint32_t r0 = 0; r0 < total; r0 += 32) {
-    const uint32_t k = r0 + lane;
-    const bool active = k < total;
-    int owner = 0;
-#pragma unroll
-    for (int b = 16; b > 0; b >>= 1) {
-      const uint32_t probe = __shfl_sync(0xffffffffu, incl, owner + b - 1);
-      if (probe <= k) owner += b;
+    const long long i = base_i + lane;
+    uint32_t area = 0, lo = 0, hi = 0;
+    float4 ra = make_float4(0, 0, 0, 0), rb = ra;
+    if (i < n) {
+      const Rec r = rec[i];
+      ra = r.a;
+      rb = r.b;
+      lo = __float_as_uint(r.c.z);
+      hi = __float_as_uint(r.c.w);
+      area = ((lo >> 16) - (lo & 0xffffu)) * (((hi >> 16) & 0x7ffu) - (hi & 0xffffu));
     }
-    owner = min(owner, 31);
-    const uint32_t o_incl = __shfl_sync(0xffffffffu, incl, owner);
-    const uint32_t o_area = __shfl_sync(0xffffffffu, area, owner);
-    const uint32_t o_lo = __shfl_sync(0xffffffffu, lo, owner);
-    const uint32_t o_hi = __shfl_sync(0xffffffffu, hi, owner);
-    const uint32_t o_v = __shfl_sync(0xffffffffu, v, owner);
-    const uint32_t o_off = __shfl_sync(0xffffffffu, off, owner);
-    const uint32_t q = k - (o_incl - o_area);
-    const uint32_t x0 = o_lo & 0xffffu, wdt = (o_lo >> 16) - x0;
-    const uint32_t y0 = o_hi & 0xffffu;
-    const int c = static_cast<int>(o_hi >> 27);
-    const uint32_t tx = active ? x0 + q % max(wdt, 1u) : 0;
-    const uint32_t ty = active ? y0 + q / max(wdt, 1u) : 0;
-    bool keep = active;
-    if (kCull) {
+    uint32_t incl = area;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    for (uint32_t r0 = 0; r0 < total; r0 += 32) {
+      const uint32_t k = r0 + lane;
+      const bool active = k < total;
+      int owner = 0;  // the record of pair slot k: the first lane whose inclusive count exceeds k
+#pragma unroll
+      for (int b = 16; b > 0; b >>= 1) {
+        const uint32_t probe = __shfl_sync(0xffffffffu, incl, owner + b - 1);
+        if (probe <= k) owner += b;
+      }
+      owner = min(owner, 31);
+      const uint32_t o_incl = __shfl_sync(0xffffffffu, incl, owner);
+      const uint32_t o_area = __shfl_sync(0xffffffffu, area, owner);
+      const uint32_t o_lo = __shfl_sync(0xffffffffu, lo, owner);
+      const uint32_t o_hi = __shfl_sync(0xffffffffu, hi, owner);
       const float mx = __shfl_sync(0xffffffffu, ra.x, owner), my = __shfl_sync(0xffffffffu, ra.y, owner);
-      const float op = __shfl_sync(0xffffffffu, ra.z, owner);
+      const float op = __shfl_sync(0xffffffffu, ra.z, owner), oz = __shfl_sync(0xffffffffu, ra.w, owner);
       const float ca = __shfl_sync(0xffffffffu, rb.x, owner), cb = __shfl_sync(0xffffffffu, rb.y, owner);
       const float cc = __shfl_sync(0xffffffffu, rb.z, owner);
-      if (active) {
-        const DevCam& cam = cams.cam[c];
+      if (!active) continue;
+      const uint32_t q = k - (o_incl - o_area);
+      const uint32_t x0 = o_lo & 0xffffu, wdt = (o_lo >> 16) - x0;
+      const uint32_t y0 = o_hi & 0xffffu;
+      const int c = static_cast<int>(o_hi >> 27);
+      const uint32_t tx = x0 + q % max(wdt, 1u);
+      const uint32_t ty = y0 + q / max(wdt, 1u);
+      const DevCam& cam = cams.cam[c];
+      if (kCull) {
         const float xlo = tx * kTile + 0.5f, xhi = fminf(static_cast<float>((tx + 1) * kTile), cam.W) - 0.5f;
         const float ylo = ty * kTile + 0.5f, yhi = fminf(static_cast<float>((ty + 1) * kTile), cam.H) - 0.5f;
         const float d2 = tile_min_maha(mx, my, ca, cb, cc, xlo, xhi, ylo, yhi);
-        keep = op > 0.f && 0.5f * d2 <= logf(op * 255.f);
+        if (!(op > 0.f && __fmul_rn(0.5f, d2) <= logf(__fmul_rn(op, 255.f)))) continue;
       }
-      const uint32_t kb = __ballot_sync(0xffffffffu, keep);
-      const uint32_t group = __match_any_sync(0xffffffffu, active ? static_cast<uint32_t>(owner) : 64u);
-      const uint32_t before = __popc(kb & group & ((1u << lane) - 1));
-      const uint32_t base_cnt = s_cnt[w][owner];
-      __syncwarp();
-      if (!kCount && keep) {
-        const uint32_t pos = o_off + base_cnt + before;
-        const DevCam& cam = cams.cam[c];
-        const uint32_t key = static_cast<uint32_t>(cam.tile_off) + ty * cam.tiles_x + tx;
-        pkeys[pos] = key;
-        pvals[pos] = o_v;
-        if (key_counts) count_digits(key, 0, key_bits, passes, s_digits);
+      const uint32_t t = static_cast<uint32_t>(cam.tile_off) + ty * cam.tiles_x + tx;
+      const uint32_t slot = atomicAdd(tile_ctr + t, 1u);
+      if (kPlace) {
+        // the counting pass made room for exactly this many pairs; a pair beyond the tile's range
+        // (which identical decisions rule out) is reported, never written
+        if (slot < ranges[t].y) {
+          const uint32_t v = static_cast<uint32_t>(base_i) + static_cast<uint32_t>(owner);
+          keys[slot] = (static_cast<unsigned long long>(__float_as_uint(oz)) << 32) | v;
+        } else {
+          atomicOr(err, kErrOverflow);
+        }
       }
-      if (active && lane == 31 - __clz(group)) s_cnt[w][owner] = base_cnt + __popc(kb & group);
-      __syncwarp();
-    } else if (active) {
-      const DevCam& cam = cams.cam[c];
-      const uint32_t pos = o_off + q;
-      const uint32_t key = static_cast<uint32_t>(cam.tile_off) + ty * cam.tiles_x + tx;
-      pkeys[pos] = key;
-      pvals[pos] = o_v;
-      if (key_counts) count_digits(key, 0, key_bits, passes, s_digits);
     }
   }
-  if (kCount && valid) cnt_sorted[i] = s_cnt[w][lane];
-  __syncwarp();  // the next round clears s_cnt
-  }
-  if (key_counts) {
+}
+
+// Exclusive scan of the per-tile pair counts (chained scan, decoupled look-back): ranges[t] =
+// [start, start + count); the counter becomes the tile's cursor (start) for the placing pass;
+// *p_total = P; *max_count = the largest tile's count.
+__global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(uint32_t* __restrict__ ctr, uint2* __restrict__ ranges,
+                                                                 int n_tiles, unsigned long long* status,
+                                                                 uint32_t* counter, unsigned long long* p_total,
+                                                                 uint32_t* max_count, uint32_t epoch, int* err,
+                                                                 WaitCfg wait) {
+  __shared__ uint32_t s_bid;
+  __shared__ unsigned long long s_base;
+  __shared__ uint32_t s_max[kScanThreads / 32];
+  for (;;) {
+    if (threadIdx.x == 0) s_bid = atomicAdd(counter, 1u);
     __syncthreads();
-    flush_digit_counts(s_digits, passes, key_counts);
+    const uint32_t bid = s_bid;
+    const long long start = static_cast<long long>(bid) * (kScanThreads * kScanItems);
+    if (start >= n_tiles) break;
+    uint32_t x[kScanItems];
+    uint32_t sum = 0, mx = 0;
+    const long long first = start + static_cast<long long>(threadIdx.x) * kScanItems;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const long long idx = first + k;
+      x[k] = idx < n_tiles ? ctr[idx] : 0u;
+      sum += x[k];
+      mx = max(mx, x[k]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+    uint32_t tot;
+    const uint32_t excl = block_excl_scan(sum, &tot);
+    if (threadIdx.x < 32) {
+      const unsigned long long ex = warp_chained_prefix(status, bid, tot, epoch, err, wait);
+      if (threadIdx.x == 0) {
+        s_base = ex;
+        uint32_t m = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) m = max(m, s_max[w]);
+        atomicMax(max_count, m);
+      }
+    }
+    __syncthreads();
+    unsigned long long run = s_base + excl;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const long long idx = first + k;
+      if (idx < n_tiles) {
+        if (run + x[k] > 0xffffffffull) atomicOr(err, kErrOverflow);
+        ranges[idx] = make_uint2(static_cast<uint32_t>(run), static_cast<uint32_t>(run + x[k]));
+        ctr[idx] = static_cast<uint32_t>(run);
+        if (idx == n_tiles - 1) *p_total = run + x[k];
+      }
+      run += x[k];
+    }
+    __syncthreads();
   }
 }
 
-__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__ a, uint32_t n, uint32_t key) {
-  uint32_t lo = 0, hi = n;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (__ldg(a + mid) < key) lo = mid + 1; else hi = mid;
+// Sorts m keys (a power of two, at most 2 blockDim.x per round of the loop) in shared memory,
+// ascending: Batcher's bitonic network, one comparator per thread and stage.
+__device__ __forceinline__ void block_bitonic_sort(unsigned long long* s, int m) {
+  for (int k = 2; k <= m; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int c = threadIdx.x; c < (m >> 1); c += blockDim.x) {
+        const int i = 2 * c - (c & (j - 1));  // bit j of i is clear; its partner is i + j
+        const unsigned long long a = s[i], b = s[i + j];
+        if ((a > b) == ((i & k) == 0)) {
+          s[i] = b;
+          s[i + j] = a;
+        }
+      }
+      __syncthreads();
+    }
   }
-  return lo;
 }
 
-// One thread per tile: [first pair with key >= t, first pair with key >= t + 1) of the sorted
-// keys; every tile is written, so nothing needs clearing first.
-__global__ void ranges_kernel(const uint32_t* __restrict__ keys, uint32_t P, int n_tiles, uint2* __restrict__ ranges) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_tiles) return;
-  ranges[t] = make_uint2(lower_bound_u32(keys, P, static_cast<uint32_t>(t)),
-                         lower_bound_u32(keys, P, static_cast<uint32_t>(t) + 1u));
+// Merges the sorted runs a[0, na) and b[0, nb) (distinct keys) into out[0, na + nb) with the
+// whole block: each thread finds where its share of the output starts on the merge path (a
+// binary search along a diagonal) and merges that share sequentially.
+__device__ void block_merge(const unsigned long long* a, int na, const unsigned long long* b, int nb,
+                            unsigned long long* out) {
+  const int total = na + nb;
+  const int per = (total + blockDim.x - 1) / blockDim.x;
+  const int d0 = min(static_cast<int>(threadIdx.x) * per, total);
+  const int d1 = min(d0 + per, total);
+  int lo = max(0, d0 - nb), hi = min(d0, na);
+  while (lo < hi) {  // i = number of a's among the first d0 outputs
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < b[d0 - mid - 1]) lo = mid + 1; else hi = mid;
+  }
+  int i = lo, j = d0 - lo;
+  for (int d = d0; d < d1; ++d) {
+    const bool take_a = j >= nb || (i < na && a[i] < b[j]);
+    out[d] = take_a ? a[i++] : b[j++];
+  }
 }
 
+// One block per tile: sorts the tile's keys (depth bits << 32 | record index), i.e. its pairs by
+// depth with ties to the lower record (so the lower Gaussian index, C7), and writes the records in
+// that order. A list of at most `cap` keys (a power of two; the dynamic shared memory holds cap
+// keys) is sorted in shared memory; a longer one in runs of cap, merged pairwise in global memory
+// through `scratch` (same offsets as the keys).
+__global__ void __launch_bounds__(256) tile_sort_kernel(unsigned long long* __restrict__ keys, const uint2* __restrict__ ranges,
+                                                        uint32_t* __restrict__ vals, unsigned long long* __restrict__ scratch,
+                                                        int cap) {
+  extern __shared__ unsigned long long s_keys[];
+  const uint2 r = ranges[blockIdx.x];
+  const int n = static_cast<int>(r.y - r.x);
+  if (n == 0) return;
+  unsigned long long* k = keys + r.x;
+  if (n <= cap) {
+    int m = 1;
+    while (m < n) m <<= 1;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s_keys[i] = i < n ? k[i] : ~0ull;
+    __syncthreads();
+    block_bitonic_sort(s_keys, m);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) vals[r.x + i] = static_cast<uint32_t>(s_keys[i]);
+    return;
+  }
+  // runs of cap keys sorted in place
+  for (int base = 0; base < n; base += cap) {
+    const int len = min(cap, n - base);
+    for (int i = threadIdx.x; i < cap; i += blockDim.x) s_keys[i] = i < len ? k[base + i] : ~0ull;
+    __syncthreads();
+    block_bitonic_sort(s_keys, cap);
+    for (int i = threadIdx.x; i < len; i += blockDim.x) k[base + i] = s_keys[i];
+    __syncthreads();
+  }
+  // pairwise merges, ping-ponging between the keys and the scratch
+  unsigned long long* src = k;
+  unsigned long long* dst = scratch + r.x;
+  for (int width = cap; width < n; width <<= 1) {
+    for (int lo = 0; lo < n; lo += 2 * width) {
+      const int na = min(width, n - lo);
+      const int nb = max(0, min(width, n - lo - width));
+      block_merge(src + lo, na, src + lo + na, nb, dst + lo);
+    }
+    __syncthreads();
+    unsigned long long* t = src;
+    src = dst;
+    dst = t;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) vals[r.x + i] = static_cast<uint32_t>(src[i]);
+}
 
 template <bool kCount>
 __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(const Rec* __restrict__ rec,
@@ -221,7 +326,11 @@ __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(const Rec* __r
   const float x_max = cam.W - 0.5f, y_max = cam.H - 0.5f;
   const uint2 range = ranges[t];
   const int n = static_cast<int>(range.y - range.x);
+  // Depth is accumulated relative to the pixel's first contributor (Zf): D = sum (z - Zf) w stays
+  // small, so the expected depth Zf + D / (1 - T), and the backward's z_i - (expected depth), keep
+  // their absolute precision at any distance (a plain sum of z w at z ~ 1000 carries 1e-4 of rounding).
   float T[2] = {1.f, 1.f}, C0[2] = {0.f, 0.f}, C1[2] = {0.f, 0.f}, C2[2] = {0.f, 0.f}, D[2] = {0.f, 0.f};
+  float Zf[2] = {0.f, 0.f};
   uint32_t last[2] = {0, 0};
   bool done[2] = {!inside[0], !inside[1]};
   uint32_t n_eval = 0, n_blend = 0;
@@ -262,7 +371,8 @@ __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(const Rec* __r
         C0[q] = fmaf(b.w, wgt, C0[q]);
         C1[q] = fmaf(cc.x, wgt, C1[q]);
         C2[q] = fmaf(cc.y, wgt, C2[q]);
-        D[q] = fmaf(a.w, wgt, D[q]);
+        Zf[q] = (use && T[q] == 1.f) ? a.w : Zf[q];  // T < 1 after the first contributor
+        D[q] = fmaf(a.w - Zf[q], wgt, D[q]);
         T[q] = use ? Tn : T[q];
         last[q] = use ? static_cast<uint32_t>(base + j + 1) : last[q];
         done[q] = done[q] || term;
@@ -299,12 +409,13 @@ __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(const Rec* __r
     out.rgb[3 * pix + 0] = r0 + T[q] * bg.x;
     out.rgb[3 * pix + 1] = r1 + T[q] * bg.y;
     out.rgb[3 * pix + 2] = r2 + T[q] * bg.z;
-    if (out.depth_acc) out.depth_acc[pix] = D[q];
-    if (out.depth_exp) out.depth_exp[pix] = D[q] / fmaxf(o, 1e-10f);
+    // o is 0 (no contributor) or at least 1/255
+    if (out.depth_acc) out.depth_acc[pix] = fmaf(Zf[q], o, D[q]);
+    if (out.depth_exp) out.depth_exp[pix] = o > 0.f ? Zf[q] + D[q] / o : 0.f;
     if (out.alpha) out.alpha[pix] = o;
     if (out.T_final) out.T_final[pix] = T[q];
     if (out.n_contrib) out.n_contrib[pix] = last[q];
-    if (out.D_state) out.D_state[pix] = D[q];
+    if (out.D_state) out.D_state[pix] = make_float2(Zf[q], D[q]);
   }
 }
 
@@ -403,12 +514,12 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
   const float* A = cam.aff;
   const float bb0 = A ? A[3] : 0.f, bb1 = A ? A[7] : 0.f, bb2 = A ? A[11] : 0.f;
   // per pixel: upstream gradients of C = sum c a T, of the depth part and of T_final
-  float Tf[2], T[2], g0[2], g1[2], g2[2], aout[2], GC0[2], GC1[2], GC2[2], GD[2], GTz[2], zr[2];
+  float Tf[2], T[2], g0[2], g1[2], g2[2], aout[2], GC0[2], GC1[2], GC2[2], GD[2], GTz[2], zr[2], zrl[2];
   float S0[2] = {0.f, 0.f}, S1[2] = {0.f, 0.f}, S2[2] = {0.f, 0.f}, SD[2] = {0.f, 0.f};
   uint32_t last[2];
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
-    float D = 0.f, gda = 0.f, gde = 0.f, gal = 0.f;
+    float zf = 0.f, D = 0.f, gda = 0.f, gde = 0.f, gal = 0.f;
     Tf[q] = 1.f;
     last[q] = 0;
     g0[q] = g1[q] = g2[q] = 0.f;
@@ -416,7 +527,9 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
       const long long pix = cam.pix_off + static_cast<long long>(py0 + q) * cam.W + px;
       Tf[q] = in.T_final[pix];
       last[q] = in.n_contrib[pix];
-      D = in.D_state[pix];
+      const float2 ds = in.D_state[pix];  // first contributor's depth, sum of (z - it) w
+      zf = ds.x;
+      D = ds.y;
       if (in.d_rgb) { g0[q] = in.d_rgb[3 * pix]; g1[q] = in.d_rgb[3 * pix + 1]; g2[q] = in.d_rgb[3 * pix + 2]; }
       if (in.d_depth_acc) gda = in.d_depth_acc[pix];
       if (in.d_depth_exp) gde = in.d_depth_exp[pix];
@@ -431,14 +544,17 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
     }
     aout[q] = 1.f - Tf[q];
     GD[q] = gda + gde / fmaxf(aout[q], 1e-10f);
-    const float ga_eff = gal + (aout[q] > 1e-10f ? -gde * D / (aout[q] * aout[q]) : 0.f);
-    const float GT = g0[q] * (bg.x - bb0) + g1[q] * (bg.y - bb1) + g2[q] * (bg.z - bb2) - ga_eff;
     // Depths are carried relative to the pixel's expected depth zr: with z_i = zr + d_i the depth
     // part of dL/dalpha_i, T_i z_i - S_D / (1 - a_i), equals T_i d_i - S_d / (1 - a_i)
     // + zr T_final / (1 - a_i) (the weights behind i sum to T_{i+1} - T_final); this avoids the
     // FP32 cancellation of two large, nearly equal terms when the contributors lie at similar depth.
-    zr[q] = aout[q] > 1e-10f ? D / aout[q] : 0.f;
-    GTz[q] = GD[q] * zr[q] - GT;
+    // d_i = (z_i - zf) - D / aout is formed from differences of nearby depths only. The T_final
+    // term, (dL/dD) zr - dL/dT_final, loses its expected-depth parts, which cancel exactly:
+    // it is (dL/ddepth_acc) zr + dL/dalpha - dL/drgb . (bg - b).
+    const float zrel = aout[q] > 0.f ? D / aout[q] : 0.f;
+    zr[q] = zf;     // d_i = (z_i - zf) - zrel
+    zrl[q] = zrel;
+    GTz[q] = gda * (zf + zrel) + gal - (g0[q] * (bg.x - bb0) + g1[q] * (bg.y - bb1) + g2[q] * (bg.z - bb2));
     T[q] = Tf[q];
   }
   __syncthreads();
@@ -498,7 +614,7 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
         const float rom = __frcp_rn(1.f - alpha);  // 1 / (1 - alpha), correctly rounded
         const float Ti = T[q] * rom;
         const float wgt = c ? alpha * Ti : 0.f;
-        const float dz = a.w - zr[q];
+        const float dz = (a.w - zr[q]) - zrl[q];
         const float dal = Ti * (GC0[q] * b.w + GC1[q] * cc.x + GC2[q] * cc.y + GD[q] * dz) +
                           (GTz[q] * Tf[q] - (GC0[q] * S0[q] + GC1[q] * S1[q] + GC2[q] * S2[q] + GD[q] * SD[q])) * rom;
         S0[q] = fmaf(b.w, wgt, S0[q]);
@@ -578,27 +694,34 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
 
 }  // namespace
 
-void launch_duplicate(const Rec* rec, const uint32_t* order, const uint32_t* offsets, const uint32_t* d_n,
-                      long long max_n, const CamBatch& cams, int tile_cull, uint32_t* cnt_sorted,
-                      uint32_t* pair_keys, uint32_t* pair_vals, uint32_t* key_counts, int key_bits, int max_blocks,
+void launch_bin_pairs(const Rec* rec, const uint32_t* d_n, long long max_n, const CamBatch& cams, int tile_cull,
+                      uint32_t* tile_ctr, const uint2* ranges, unsigned long long* keys, int* err, int max_blocks,
                       cudaStream_t s) {
   if (max_n <= 0) return;
   const int blocks = static_cast<int>(std::min<long long>((max_n + 255) / 256, std::max(max_blocks, 1)));
-  if (cnt_sorted) {
-    duplicate_kernel<true, true><<<blocks, 256, 0, s>>>(rec, order, offsets, d_n, max_n, cams, cnt_sorted, nullptr,
-                                                        nullptr, nullptr, 0);
-  } else if (tile_cull) {
-    duplicate_kernel<true, false><<<blocks, 256, 0, s>>>(rec, order, offsets, d_n, max_n, cams, nullptr, pair_keys,
-                                                         pair_vals, key_counts, key_bits);
+#define GSR_BIN(C, P) bin_pairs_kernel<C, P><<<blocks, 256, 0, s>>>(rec, d_n, max_n, cams, tile_ctr, ranges, keys, err)
+  if (keys) {
+    if (tile_cull) GSR_BIN(true, true); else GSR_BIN(false, true);
   } else {
-    duplicate_kernel<false, false><<<blocks, 256, 0, s>>>(rec, order, offsets, d_n, max_n, cams, nullptr, pair_keys,
-                                                          pair_vals, key_counts, key_bits);
+    if (tile_cull) GSR_BIN(true, false); else GSR_BIN(false, false);
   }
+#undef GSR_BIN
 }
 
-void launch_ranges(const uint32_t* sorted_keys, long long P, int n_tiles, uint2* ranges, cudaStream_t s) {
+void launch_tile_scan(uint32_t* tile_ctr, uint2* ranges, int n_tiles, unsigned long long* status, uint32_t* counter,
+                      unsigned long long* p_total, uint32_t* max_count, uint32_t epoch, int* err, WaitCfg wait,
+                      int grid_cap, cudaStream_t s) {
   if (n_tiles <= 0) return;
-  ranges_kernel<<<(n_tiles + 255) / 256, 256, 0, s>>>(sorted_keys, static_cast<uint32_t>(P), n_tiles, ranges);
+  const long long per = kScanThreads * kScanItems;
+  const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>((n_tiles + per - 1) / per, grid_cap)));
+  tile_scan_kernel<<<grid, kScanThreads, 0, s>>>(tile_ctr, ranges, n_tiles, status, counter, p_total, max_count,
+                                                 epoch, err, wait);
+}
+
+void launch_tile_sort(unsigned long long* keys, const uint2* ranges, int n_tiles, uint32_t* vals,
+                      unsigned long long* scratch, int cap, cudaStream_t s) {
+  if (n_tiles <= 0) return;
+  tile_sort_kernel<<<n_tiles, 256, sizeof(unsigned long long) * cap, s>>>(keys, ranges, vals, scratch, cap);
 }
 
 void launch_blend_fwd(const Rec* rec, const uint32_t* pair_vals, const uint2* ranges, const CamBatch& cams,

@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "ok", 1: "over budget", -1: "invalid argument", -2: "out of d
 
 DTYPES = {torch.float32: 0, torch.float16: 1, torch.bfloat16: 2}
 
-BUF_RECORDS, BUF_OWNER, BUF_PAIR_VALS, BUF_RANGES, BUF_T_FINAL, BUF_N_CONTRIB, BUF_DEPTH_ACC = range(7)
+BUF_RECORDS, BUF_OWNER, BUF_PAIR_VALS, BUF_RANGES, BUF_T_FINAL, BUF_N_CONTRIB, BUF_DEPTH_STATE = range(7)
 REC_FLOATS = 16  # one splat record: four float4
 
 EXPORTED = [
@@ -41,8 +41,8 @@ EXPORTED = [
     "gsr_param_grads_zero", "gsr_set_wait_limit",
 ]
 
-STAGES = ["preprocess", "depth_sort", "tile_count", "pair_scan", "readback", "duplicate", "tile_sort", "ranges",
-          "blend_fwd", "blend_bwd", "preprocess_bwd", "between_stages", "appearance_bwd"]
+STAGES = ["preprocess", "tile_count", "tile_scan", "readback", "place", "tile_sort", "blend_fwd", "blend_bwd",
+          "preprocess_bwd", "between_stages", "appearance_bwd"]
 COUNTERS = ["fwd_evals", "fwd_contribs", "bwd_evals", "bwd_contribs"]
 
 
@@ -66,7 +66,7 @@ class CGaussians(ctypes.Structure):
                 ("quats", ctypes.c_void_p), ("opacities", ctypes.c_void_p), ("sh", ctypes.c_void_p),
                 ("sh_coeffs", ctypes.c_int32), ("sh_degree", ctypes.c_int32), ("attr_dtype", ctypes.c_int32),
                 ("sh_dtype", ctypes.c_int32), ("segs", ctypes.POINTER(Segment)), ("nsegs", ctypes.c_int32),
-                ("mlp", ctypes.POINTER(CAppearanceMLP))]
+                ("mlp", ctypes.POINTER(CAppearanceMLP)), ("seg_cams", ctypes.POINTER(ctypes.c_uint32))]
 
 
 class CCamera(ctypes.Structure):
@@ -256,6 +256,8 @@ class Gaussians:
     sh_degree: int = 3
     segments: Optional[Sequence[tuple]] = None
     mlp: Optional[AppearanceMLP] = None
+    # per segment, the cameras of a launch that render it (bit c = camera c); None: all of them
+    segment_cams: Optional[Sequence[int]] = None
 
     @property
     def n(self) -> int:
@@ -275,6 +277,11 @@ class Gaussians:
             for k, (b, c) in enumerate(self.segments):
                 seg_arr[k].begin = int(b)
                 seg_arr[k].count = int(c)
+        cam_arr = None
+        if self.segment_cams is not None:
+            if self.segments is None or len(self.segment_cams) != len(self.segments):
+                raise ValueError("segment_cams needs one camera mask per segment")
+            cam_arr = (ctypes.c_uint32 * max(len(self.segment_cams), 1))(*[int(m) for m in self.segment_cams])
         n = self.n
         cmlp = self.mlp.c_struct(n) if self.mlp is not None else None
         g = CGaussians(n, _ptr(self.means), _ptr(self.scales), _ptr(self.quats), _ptr(self.opacities),
@@ -282,12 +289,13 @@ class Gaussians:
                        DTYPES[self.scales.dtype], DTYPES[self.sh.dtype],
                        ctypes.cast(seg_arr, ctypes.POINTER(Segment)) if seg_arr is not None else None,
                        len(self.segments) if self.segments is not None else 0,
-                       ctypes.pointer(cmlp) if cmlp is not None else None)
+                       ctypes.pointer(cmlp) if cmlp is not None else None,
+                       ctypes.cast(cam_arr, ctypes.POINTER(ctypes.c_uint32)) if cam_arr is not None else None)
         if self.means.dtype != torch.float32:
             raise ValueError("means must be float32")
         if not (self.scales.dtype == self.quats.dtype == self.opacities.dtype):
             raise ValueError("scales, quats and opacities must share one dtype")
-        return g, (seg_arr, cmlp)
+        return g, (seg_arr, cmlp, cam_arr)
 
     def check_cameras(self, n_cams: int):
         if self.mlp is not None and self.mlp.cached is None and self.mlp.image_embed.shape[0] != n_cams:
@@ -559,6 +567,28 @@ def sort_pairs_u32(ctx: Context, keys: torch.Tensor, vals: torch.Tensor, begin_b
     _check(ctx, load().gsr_sort_pairs_u32(ctx.handle, _ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo), keys.numel(),
                                           int(begin_bit), int(end_bit), _stream(stream)))
     return ko, vo
+
+
+def union_segments(selections):
+    """Segments and camera masks for one launch of several views with their own detail levels:
+    selections[c] lists view c's (partition, level, begin, count) in partition order (one level
+    per partition). Returns (segments, masks) for Gaussians.segments / segment_cams: the union,
+    ordered by (partition, level), so every view keeps its own relative order (and so the same
+    depth-tie order and the same image as rendered alone)."""
+    if len(selections) > 32:
+        raise ValueError("at most 32 views per launch")
+    table = {}
+    for c, sel in enumerate(selections):
+        for p, lev, begin, count in sel:
+            key = (int(p), int(lev))
+            if key in table:
+                if (table[key][0], table[key][1]) != (int(begin), int(count)):
+                    raise ValueError(f"views disagree on the segment of partition {key[0]} level {key[1]}")
+                table[key][2] |= 1 << c
+            else:
+                table[key] = [int(begin), int(count), 1 << c]
+    keys = sorted(table)
+    return [(table[k][0], table[k][1]) for k in keys], [table[k][2] for k in keys]
 
 
 def select_lod(aabb: np.ndarray, level_offsets: np.ndarray, cam, thresholds, budget: int = 0):

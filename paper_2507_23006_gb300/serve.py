@@ -7,9 +7,11 @@ view (gsr_select_lod: invisible partitions culled, nearer partitions finer, fart
 first while over the budget) and estimates the device memory the render needs
 (gsr_workspace_query plus the output images). Each slot owns a library context and a CUDA
 stream and is driven by its own host thread; a free slot takes the oldest waiting request as
-soon as the memory it needs is free, together with later waiting requests of the same scene
-whose level selection is identical (one launch renders up to `max_batch` such views of
-mixed resolutions). Slots run concurrently, so requests that arrive while others render are
+soon as the memory it needs is free, together with later waiting requests of the same scene, up
+to `max_batch` views of any resolutions and detail selections in one launch: the launch renders
+the union of their selected segments, each segment marked with the views that selected it
+(gsr_gaussians.seg_cams), and each view's image is the one it gets alone. The batch's memory is
+that of the union. Slots run concurrently, so requests that arrive while others render are
 admitted as slots and memory free up. Latency is arrival to image ready.
 """
 from __future__ import annotations
@@ -34,6 +36,7 @@ class Request:
     camera: object
     t_arrival: float
     segments: list = None
+    selection: list = None  # (partition, level, begin, count) of each selected partition
     n_selected: int = 0
     over_budget: bool = False
     mem_bytes: int = 0
@@ -92,18 +95,35 @@ class RenderServer:
         self.scenes[name] = _Resident(lod, self.dev, attr_dtype, sh_dtype)
 
     def select(self, scene: str, cam):
+        segs, nsel, over, _ = self.select_levels(scene, cam)
+        return segs, nsel, over
+
+    def select_levels(self, scene: str, cam):
+        """Level selection of one view -> (segments, n_selected, over budget, selection), the
+        selection listing (partition, level, begin, count) in partition order."""
         r = self.scenes[scene]
         st, levels, segs, nsel = native.select_lod(r.lod.aabb, r.lod.level_offsets, cam, self.thresholds,
                                                    self.gaussian_budget)
-        return segs, nsel, st == native.GSR_WARN_OVER_BUDGET
+        lo = r.lod.level_offsets
+        sel = []
+        for p, lev in enumerate(levels):
+            if lev >= 0 and lo[lev, p + 1] > lo[lev, p]:
+                sel.append((p, int(lev), int(lo[lev, p]), int(lo[lev, p + 1] - lo[lev, p])))
+        assert [(b, c) for _, _, b, c in sel] == [tuple(x) for x in segs]
+        return segs, nsel, st == native.GSR_WARN_OVER_BUDGET, sel
+
+    def _memory(self, n_render: int, cams) -> int:
+        """Device memory of one launch: the library's workspace and the output images."""
+        ctx0 = self._slots[0][0]
+        n = max(int(n_render), 1)
+        return ctx0.workspace_query(n, list(cams), 3 * n) + sum(c.width * c.height for c in cams) * 6 * 4
 
     def submit(self, scene: str, cam, t_arrival: Optional[float] = None) -> Request:
-        segs, nsel, over = self.select(scene, cam)
-        ctx0 = self._slots[0][0]
-        mem = ctx0.workspace_query(max(nsel, 1), [cam], 3 * max(nsel, 1)) + cam.width * cam.height * 6 * 4
+        segs, nsel, over, sel = self.select_levels(scene, cam)
+        mem = self._memory(nsel, [cam])
         with self.cv:
             req = Request(self._next_id, scene, cam, time.perf_counter() if t_arrival is None else t_arrival,
-                          segs, nsel, over, mem)
+                          segs, sel, nsel, over, mem)
             self._next_id += 1
             if mem > self.memory_budget:
                 req.error = "request needs more memory than the server's budget"
@@ -127,7 +147,8 @@ class RenderServer:
 
     def _take(self):
         """Under the lock: the oldest waiting request if its memory fits, plus later waiting
-        requests of the same scene with the same level selection (batched into one launch)."""
+        requests of the same scene (any resolution, any level selection) while the memory of
+        the batch (the union of their selections, all their cameras) fits: one launch."""
         if not self.queue:
             return None
         head = self.queue[0]
@@ -135,13 +156,19 @@ class RenderServer:
             return None
         batch = [self.queue.popleft()]
         mem = head.mem_bytes
+        union = {(p, lev): cnt for p, lev, _, cnt in head.selection}
         keep = collections.deque()
         while self.queue and len(batch) < self.max_batch:
             r = self.queue.popleft()
-            if (r.scene == head.scene and r.segments == head.segments
-                    and self.mem_in_use + mem + r.mem_bytes <= self.memory_budget):
+            if r.scene != head.scene:
+                keep.append(r)
+                continue
+            grown = dict(union)
+            grown.update({(p, lev): cnt for p, lev, _, cnt in r.selection})
+            need = self._memory(sum(grown.values()), [q.camera for q in batch] + [r.camera])
+            if self.mem_in_use + need <= self.memory_budget:
                 batch.append(r)
-                mem += r.mem_bytes
+                union, mem = grown, need
             else:
                 keep.append(r)
         self.queue.extendleft(reversed(keep))
@@ -164,7 +191,11 @@ class RenderServer:
             t0 = time.perf_counter()
             try:
                 res = self.scenes[batch[0].scene]
-                g = dataclasses.replace(res.g, segments=batch[0].segments)
+                if len(batch) == 1:
+                    g = dataclasses.replace(res.g, segments=batch[0].segments)
+                else:
+                    segs, masks = native.union_segments([r.selection for r in batch])
+                    g = dataclasses.replace(res.g, segments=segs, segment_cams=masks)
                 cams = [r.camera for r in batch]
                 with torch.cuda.stream(stream):
                     out, _ = native.render_forward(ctx, g, cams, self.opts, want_state=False, stream=stream)

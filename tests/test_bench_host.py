@@ -22,7 +22,7 @@ def test_stage_rooflines_pick_the_binding_resource():
     rows, step = bench.stage_rooflines(stage_ms, n, V, P, tiles, npix, counts, 1.0, 1e15, 1000.0, 8.0)
     pre = rows["preprocess"]
     assert pre["bound"] == "hbm"
-    assert pre["algorithmic_us"] == pytest.approx(52.0 * n / 1e12 * 1e6, rel=1e-6)
+    assert pre["algorithmic_us"] == pytest.approx(44.0 * n / 1e12 * 1e6, rel=1e-6)
     assert pre["frac"] == pytest.approx(pre["algorithmic_us"] / 2000.0, rel=1e-3)
     bwd = rows["blend_bwd"]
     assert bwd["bound"] == "alu" and bwd["algorithmic_us"] == pytest.approx(2000.0, rel=1e-3)
@@ -35,9 +35,11 @@ def test_stage_rooflines_pick_the_binding_resource():
 
 
 def test_kernels_per_step():
-    # 8160 tiles: 13 key bits, two tile-sort passes
-    assert bench.kernels_per_step(True, {"n_tiles": 8160}) == 1 + 4 + 1 + 1 + 1 + 2 + 1 + 1 + 1 + 2
-    assert bench.kernels_per_step(False, {"n_tiles": 256}) == 1 + 4 + 0 + 1 + 1 + 1 + 1 + 1 + 1 + 2
+    # preprocess, per-tile counts, tile scan, placing, per-tile sort, forward blend, gradient fill,
+    # backward blend, projection backward
+    assert bench.kernels_per_step(True, {"n_tiles": 8160, "n_visible": 10, "n_pairs": 20}) == 9
+    # nothing visible: no counting, placing or sorting
+    assert bench.kernels_per_step(False, {"n_tiles": 256, "n_visible": 0, "n_pairs": 0}) == 6
 
 
 def test_stored_counters_are_keyed_to_their_kernel_sources():

@@ -31,17 +31,54 @@ def _camera(rng):
                                 azimuth_deg=rng.uniform(0, 360))
 
 
+def test_distinct_views_in_one_launch_equal_alone(city_lod):
+    """Views of different resolutions whose detail selections differ, rendered in one launch
+    (the union of their segments, each marked with the views that selected it), give each view
+    the image it gets alone: bit for bit (the same records, depth order and blend)."""
+    ctx = native.Context(0)
+    srv = serve.RenderServer(slots=1, gaussian_budget=150_000)
+    srv.add_scene("city", city_lod)
+    g = srv.scenes["city"].g
+    rng = np.random.default_rng(5)
+    cams = [_camera(rng) for _ in range(6)]
+    sels = [srv.select_levels("city", c) for c in cams]
+    assert len({tuple(map(tuple, s[0])) for s in sels}) >= 3  # the views select differently
+    segs, masks = native.union_segments([s[3] for s in sels])
+    assert any(m & (m - 1) for m in masks) and any(not m & (m - 1) for m in masks)  # shared and own segments
+    opts = native.Options(tile_cull=True)
+    gb = native.Gaussians(g.means, g.scales, g.quats, g.opacities, g.sh, 3, segs, segment_cams=masks)
+    out, st = native.render_forward(ctx, gb, cams, opts)
+    ctx.sync_check()
+    off = 0
+    for cam, sel in zip(cams, sels):
+        ga = native.Gaussians(g.means, g.scales, g.quats, g.opacities, g.sh, 3, sel[0])
+        alone, _ = native.render_forward(ctx, ga, [cam], opts, want_state=False)
+        hw = cam.width * cam.height
+        for k in ("rgb", "depth_acc", "alpha"):
+            assert torch.equal(alone[k], out[k][off:off + hw]), k
+        off += hw
+    # the launch read each Gaussian of the union once and made a record only for the views
+    # that selected it
+    assert st.info()["n_render"] == sum(c for _, c in segs)
+    srv.close()
+    ctx.close()
+
+
 def test_results_in_the_mix_equal_results_alone(city_lod):
     rng = np.random.default_rng(0)
     trace = serve.poisson_trace(rng, 150.0, 0.25, "city", _camera)
-    # a few repeated views so that some launches batch several cameras
-    trace += [(0.26 + 0.001 * k, "city", trace[k][2]) for k in range(4)]
+    # a burst of distinct views arriving together: launches batch views whose resolutions and
+    # detail selections differ
+    trace += [(0.26, "city", _camera(rng)) for _ in range(12)]
     mixed = serve.RenderServer(slots=3, gaussian_budget=150_000)
     mixed.add_scene("city", city_lod)
     stats = mixed.run_trace(trace)
     mixed.close()
     assert stats["failed"] == 0 and stats["served"] == len(trace)
     assert stats["max_in_flight"] >= 2
+    batched = [r for r in stats["requests"] if r.batch_size > 1]
+    assert len(batched) >= 4 and stats["mean_batch"] > 1.0
+    assert len({tuple(map(tuple, r.segments)) for r in batched}) >= 2
     alone = serve.RenderServer(slots=1, gaussian_budget=150_000)
     alone.add_scene("city", city_lod)
     for r in stats["requests"]:
