@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--no-fp16", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-mlp", action="store_true")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the other configurations (street block, 8-camera city, 30M at 4K) and oracle timings")
     p.add_argument("--serve-rate", type=float, default=200.0)
     p.add_argument("--serve-seconds", type=float, default=2.0)
     p.add_argument("--serve-full", action="store_true",
@@ -455,6 +457,149 @@ def run_e2e(args, ctx, g, cam, opts, d_out, grads, outs, stream, world, dev, bar
                 link_gbs=round((h2d + d2h) / (pipe_ms * 1e-3) / 1e9, 1))
 
 
+def _events_ms(fn, k, stream):
+    """Mean device milliseconds of fn() over k calls (CUDA events on `stream`, after 2 untimed)."""
+    import torch
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / k
+
+
+def _upstream_t(npix, dev, seed):
+    import torch
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    return dict(rgb=torch.randn((npix, 3), device=dev, generator=gen),
+                depth_acc=torch.randn(npix, device=dev, generator=gen) * 1e-2,
+                alpha=torch.randn(npix, device=dev, generator=gen))
+
+
+def run_configs(args, ctx, dev, stream):
+    """The other configurations of the hot path, on the device with inputs resident (CUDA events,
+    2 untimed calls first): the 500k street block at 1080p with a per-image 3x4 transform (forward
+    and backward timed apart); the 6M city seen by 8 cameras of mixed resolution in one launch,
+    FP32 and FP16 SH side by side, with the image error of each against the FP64 oracle on the
+    original FP32 inputs (camera 0, every pixel); the 30M street-level scene at 3840x2160 with FP16
+    SH in recompute mode (step time and peak device memory)."""
+    import torch
+    import oracle
+    from paper_2507_23006_gb300 import native, scenes
+    k = max(3, min(args.steps, 10))
+    out = {}
+    # street block (500k, 1080p)
+    sc, cam = scenes.street_block(1, 500_000), scenes.street_block_camera()
+    rng = np.random.default_rng(1)
+    aff = np.concatenate([np.eye(3), np.zeros((3, 1))], 1) + rng.normal(0, 0.01, (3, 4))
+    aff_t = torch.tensor(aff, dtype=torch.float32, device=dev)
+    g = native.Gaussians.from_scene(sc, device=dev)
+    opts = native.Options(tile_cull=True)
+    npix = cam.width * cam.height
+    up = _upstream_t(npix, dev, 5)
+    grads = native.param_grads(ctx, g, 1)
+    holder = {}
+
+    def fwd():
+        holder["st"] = native.render_forward(ctx, g, [cam], opts, appearances=[aff_t])[1]
+
+    def bwd():
+        native.render_backward(ctx, g, [cam], holder["st"], up, opts, appearances=[aff_t], grads=grads)
+
+    fms = _events_ms(fwd, k, stream)
+    bms = _events_ms(bwd, k, stream)
+    info = holder["st"].info()
+    out["street_block_500k_1080p"] = dict(fwd_ms=round(fms, 4), bwd_ms=round(bms, 4), visible=info["n_visible"],
+                                          pairs=info["n_pairs"], appearance_affine=True)
+    del holder["st"], g, grads
+    # city, 8 cameras of mixed resolution in one launch
+    sc = scenes.city(2, 6_000_000)
+    cams = scenes.city_batch_cameras(2)
+    npix = sum(c.width * c.height for c in cams)
+    up = _upstream_t(npix, dev, 6)
+    city = {}
+    renders = {}
+    for name, shd in (("fp32", torch.float32), ("fp16_sh", torch.float16)):
+        g = native.Gaussians.from_scene(sc, device=dev, sh_dtype=shd)
+        grads = native.param_grads(ctx, g, len(cams))
+
+        def step():
+            native.zero_param_grads(ctx, g, grads)
+            _, st = native.render_forward(ctx, g, cams, opts)
+            native.render_backward(ctx, g, cams, st, up, opts, grads=grads)
+
+        ms = _events_ms(step, k, stream)
+        o, st = native.render_forward(ctx, g, cams, opts)
+        torch.cuda.synchronize()
+        renders[name] = {kk: v[: cams[0].width * cams[0].height].double().cpu().numpy() for kk, v in o.items()}
+        city[name] = dict(ms_per_launch=round(ms, 4), visible=st.info()["n_visible"], pairs=st.info()["n_pairs"],
+                          sh_bytes_per_gaussian=48 * (4 if shd == torch.float32 else 2))
+        del g, grads, st, o
+    ref = oracle.render(sc, [cams[0]], oracle.Opts(tile_cull=True), want_pairs=False)
+    um = ref.mark == 0
+    for name, r in renders.items():
+        city[name]["vs_oracle_cam0"] = dict(
+            rgb_max_abs=float(np.abs(r["rgb"][um] - ref.img[um, 0:3]).max()),
+            alpha_max_abs=float(np.abs(r["alpha"][um] - ref.img[um, 5]).max()),
+            depth_acc_max_rel=float((np.abs(r["depth_acc"][um] - ref.img[um, 3]) /
+                                     np.maximum(ref.img[um, 3], 1e-9)).max()),
+            pixels=int(um.sum()), marked=int((~um).sum()))
+    out["city6m_8cam_mixed"] = dict(cameras=[f"{c.width}x{c.height}" for c in cams], **city)
+    # 30M street-level at 4K, FP16 SH, recompute mode
+    sc = scenes.large_scene(4, 30_000_000)
+    cam = scenes.street_level_camera(3840, 2160)
+    g = native.Gaussians.from_scene(sc, device=dev, sh_dtype=torch.float16)
+    del sc
+    ropts = native.Options(tile_cull=True, save_state=False)
+    up = _upstream_t(cam.width * cam.height, dev, 7)
+    grads = native.param_grads(ctx, g, 1)
+
+    def step4():
+        native.zero_param_grads(ctx, g, grads)
+        _, st = native.render_forward(ctx, g, [cam], ropts)
+        native.render_backward(ctx, g, [cam], st, up, ropts, grads=grads)
+
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    ms = _events_ms(step4, max(3, k // 2), stream)
+    peak = torch.cuda.max_memory_allocated() + ctx.workspace_bytes()
+    _, st = native.render_forward(ctx, g, [cam], ropts)
+    out["large30m_4k_recompute_fp16sh"] = dict(ms_per_step=round(ms, 3), peak_device_gib=round(peak / 2 ** 30, 2),
+                                                visible=st.info()["n_visible"], pairs=st.info()["n_pairs"])
+    del g, grads, st
+    torch.cuda.empty_cache()
+    return out
+
+
+def oracle_timings():
+    """The FP64 oracle as it stands, forward and backward of the whole frame: the 10k box scene
+    (256x256) and the 500k street block (1080p) with every host core and with one, the 6M city's
+    first 8-camera-launch camera (1600x1067) with every core. (The headline frame is cpu_baseline.)"""
+    import oracle
+    from paper_2507_23006_gb300 import scenes
+    full = oracle.num_threads()
+    out = {"cores": full}
+    cases = [("box10k_256", scenes.box_scene(0, 10_000), scenes.box_camera(), (full, 1)),
+             ("street_block500k_1080p", scenes.street_block(1, 500_000), scenes.street_block_camera(), (full, 1)),
+             ("city6m_1600x1067_cam0", scenes.city(2, 6_000_000), scenes.city_batch_cameras(2)[0], (full,))]
+    try:
+        for name, sc, cam, threads in cases:
+            row = {}
+            for t in threads:
+                oracle.set_num_threads(t)
+                r = cpu_reference(sc, cam, True)
+                row[f"{t}_cores_ms"] = round(r["ms_per_step"], 1)
+            out[name] = row
+    finally:
+        oracle.set_num_threads(full)
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -586,6 +731,8 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_e2e:
         e2e = run_e2e(args, ctx, g, cam, opts, d_out, grads, outs, stream, world, dev, barrier)
 
+    configs = None if args.no_configs or rank != 0 else run_configs(args, ctx, dev, stream)
+
     serve_stats = None
     if not args.no_serve:
         serve_stats = run_serve(scene, args)
@@ -624,6 +771,8 @@ def run_ours(args, rank, world, local_rank):
         r = cpu_reference(scene, cam, args.tile_cull)
         cpu = dict(value=r["ms_per_step"], unit="ms/step", cores=r["cores"], kind="oracle", sample=r["sample"],
                    sample_seconds=round(r["sample_s"], 1))
+        if not args.no_configs:
+            cpu["other_configs"] = oracle_timings()
     value = job_ms_per_step(ms, world)
     line = dict(metric=METRIC, value=value, unit="ms/step", n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms, higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f32",
@@ -632,9 +781,13 @@ def run_ours(args, rank, world, local_rank):
                             tile_cull=bool(args.tile_cull), sh_degree=3, attributes="f32",
                             l2="inputs larger than L2 (1.4 GB), no flush", parallelism=f"replicas{world}"),
                 render_fps=1000.0 / fwd_ms * world, fwd_ms=fwd_ms,
-                stages_ms=stage_ms, visible=V, pairs=P, counters=counts,
+                # weak scaling: every rank renders its own view; the rank step time (max over ranks)
+                # and the views the whole job trains per second, apart from `value`
+                per_rank_ms_per_step=ms, views_per_s=world * 1000.0 / ms,
+                stages_ms=stage_ms, visible=V, pairs=P, max_tile_pairs=info.get("max_tile_pairs"), counters=counts,
                 roofline=roof, stage_roofline=stage_roof, step_roofline=step_roof,
-                cpu_baseline=cpu, e2e=e2e, clocks=clocks, fp16_storage=fp16, appearance_mlp=mlp_leg, serve=serve_stats)
+                cpu_baseline=cpu, e2e=e2e, clocks=clocks, fp16_storage=fp16, appearance_mlp=mlp_leg, serve=serve_stats,
+                configs=configs)
     if serve_full is not None:
         line["serve_full"] = serve_full
     line["gpu_launches"] = int(args.steps * kernels_per_step(args.tile_cull, info))

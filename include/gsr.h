@@ -178,6 +178,7 @@ typedef struct gsr_state_info {
   int64_t n_pairs;    /* P: (tile, Gaussian) pairs after culling */
   int64_t n_tiles;    /* sum over cameras of tiles_x * tiles_y */
   int64_t n_pixels;   /* sum over cameras of W * H */
+  int64_t max_tile_pairs;  /* pairs of the fullest tile */
 } gsr_state_info;
 
 /* Buffers of a forward state that gsr_state_copy can export (for tests and tools). */

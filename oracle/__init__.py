@@ -54,7 +54,7 @@ def lib():
             L.oracle_render.restype = ctypes.c_int64
             L.oracle_render.argtypes = [ctypes.c_int64, _D, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, _D, _D, _D, _I64, ctypes.c_int64, _D, _U8, _U64,
-                                        _I64, ctypes.c_int64, _U8, _D, _D, _D]
+                                        _I64, ctypes.c_int64, _U8, _D, _D, _D, _D]
             L.oracle_backward.restype = ctypes.c_int
             L.oracle_backward.argtypes = [ctypes.c_int64, _D, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D,
@@ -168,10 +168,18 @@ def project(scene, cam, opts: Opts | None = None, mlp=None):
     return rec, flags
 
 
+# Reasons of a pixel's knife-edge mark (bits of RenderResult.mark). MARK_SOFT: only a near-tie
+# in depth order whose swap cannot move the pixel's outputs by 1e-5 (the gradients and the list
+# positions of the swapped contributors still depend on it).
+MARK_EDGE, MARK_ALPHA_MIN, MARK_ALPHA_MAX, MARK_STOP, MARK_TIE, MARK_TILE, MARK_SOFT = 1, 2, 4, 8, 16, 32, 64
+
+
 class RenderResult:
-    def __init__(self, img, mark, sig, pairs, gmark, cams):
+    def __init__(self, img, mark, sig, pairs, gmark, cams, bound=None):
         self.img = img          # [sum HW, 8]
-        self.mark = mark        # [sum HW] uint8
+        self.bound = bound      # [sum HW, 3] or None: largest change of rgb / depth_acc / alpha the
+                                # marked decisions could make (MARK_TILE excepted)
+        self.mark = mark        # [sum HW] uint8: reasons (MARK_*) a decision is within FP32 reach, 0 if none
         self.sig = sig          # [sum HW] uint64
         self.pairs = pairs      # [P, 2] int64 (global tile, c*n+g)
         self.gmark = gmark      # [C*n] uint8
@@ -192,7 +200,7 @@ class RenderResult:
 
 
 def render(scene, cams, opts: Opts | None = None, affines=None, tile_subset=None, want_pairs=True,
-           want_sig=False, mlp=None) -> RenderResult:
+           want_sig=False, mlp=None, want_bound=False) -> RenderResult:
     """Forward render of a list of cameras, packed one after another (mlp: the appearance
     transform's inputs, see _mlp_args)."""
     opts = opts or Opts()
@@ -208,6 +216,7 @@ def render(scene, cams, opts: Opts | None = None, affines=None, tile_subset=None
     mark = np.zeros(npix, np.uint8)
     sig = np.zeros(npix, np.uint64) if want_sig else None
     gmark = np.zeros(C * n, np.uint8)
+    bound = np.zeros((npix, 3), np.float64) if want_bound else None
     sub = None if tile_subset is None else np.ascontiguousarray(np.asarray(tile_subset, np.int64))
     nsub = 0 if sub is None else sub.size
     gemb, iemb, params = _mlp_args(mlp, n, C)
@@ -215,7 +224,8 @@ def render(scene, cams, opts: Opts | None = None, affines=None, tile_subset=None
     args = (n, _p(means, _D), _p(scales, _D), _p(quats, _D), _p(opac, _D), _p(sh, _D), K, deg, C,
             _p(rows, _D), _p(aff, _D), _p(opts.row(), _D), _p(sub, _I64), nsub)
     # first call sizes the pair list
-    P = lib().oracle_render(*args, _p(img, _D), _p(mark, _U8), _p(sig, _U64), None, 0, _p(gmark, _U8), *margs)
+    P = lib().oracle_render(*args, _p(img, _D), _p(mark, _U8), _p(sig, _U64), None, 0, _p(gmark, _U8), *margs,
+                            _p(bound, _D))
     if P < 0:
         raise ValueError("oracle_render: invalid arguments")
     pairs = None
@@ -224,10 +234,10 @@ def render(scene, cams, opts: Opts | None = None, affines=None, tile_subset=None
         P2 = lib().oracle_render(n, _p(means, _D), _p(scales, _D), _p(quats, _D), _p(opac, _D), _p(sh, _D),
                                  K, deg, C, _p(rows, _D), _p(aff, _D), _p(opts.row(), _D),
                                  _p(np.zeros(1, np.int64), _I64), 0, _p(np.zeros((1, 8)), _D), None, None,
-                                 _p(pairs, _I64), pairs.shape[0], None, *margs)
+                                 _p(pairs, _I64), pairs.shape[0], None, *margs, None)
         assert P2 == P
         pairs = pairs[:P]
-    return RenderResult(img, mark, sig, pairs, gmark, list(cams))
+    return RenderResult(img, mark, sig, pairs, gmark, list(cams), bound)
 
 
 def backward(scene, cams, up_grads, opts: Opts | None = None, affines=None, want_g2d=False, tile_subset=None,

@@ -699,6 +699,19 @@ void bin_all(const SceneD& s, const std::vector<CamD>& cams, const OptsD& o, Bin
 //   4: the gradients of conic a and conic c are swapped (a transposed operand)
 int g_mutation = 0;
 
+// Reasons for a knife-edge mark at a pixel (bits of PixelResult::mark and of out_mark).
+constexpr unsigned kMarkEdge = 1;      // the Gaussian's quadratic form is within reach of 0
+constexpr unsigned kMarkAlphaMin = 2;  // alpha within reach of 1/255
+constexpr unsigned kMarkAlphaMax = 4;  // alpha within reach of the 0.99 clamp
+constexpr unsigned kMarkStop = 8;      // T (1 - alpha) within reach of 1e-4
+constexpr unsigned kMarkTie = 16;      // two consecutive contributors at nearly equal depth
+constexpr unsigned kMarkTile = 32;     // the tile's list itself is uncertain (a rectangle, a cull)
+// Two consecutive contributors at nearly equal depth whose order cannot move the pixel's outputs by
+// 1e-5: swapping adjacent layers i, j changes the colour by T_i alpha_i alpha_j (c_i - c_j), the
+// depth by T_i alpha_i alpha_j (z_i - z_j) and leaves T unchanged, so below that bound only the
+// gradients (each layer's transmittance) and the list positions depend on the order.
+constexpr unsigned kMarkTieSoft = 64;
+
 // One contributor of a pixel (for the backward re-walk).
 struct Contrib {
   int64_t id;
@@ -712,8 +725,13 @@ struct PixelResult {
   double D;      // sum of z alpha T
   double T;      // final transmittance
   int64_t last;  // list positions walked up to and including the last contributor
-  bool mark;
+  unsigned mark;  // why a decision at this pixel is within FP32 reach (kMark* bits), 0 if none
   uint64_t sig;
+  // The largest change the decisions within FP32 reach could make to this pixel's colour (any
+  // channel), accumulated depth and alpha, if taken the other way (ties: in any order within each
+  // group of near-tied consecutive contributors). Zero where nothing is marked. The tile-level
+  // marks (kMarkTile: whether a Gaussian is in the tile's list at all) are not bounded.
+  double bound[3];
 };
 
 inline void fnv(uint64_t* h, uint64_t v) {
@@ -726,11 +744,27 @@ inline void fnv(uint64_t* h, uint64_t v) {
 // Eq. 2, front to back, for pixel (x, y) of camera `cam` over `list`.
 PixelResult composite(const Binned& B, const std::vector<int64_t>& list, const CamD& cam, int x, int y,
                       std::vector<Contrib>* trace) {
-  PixelResult R{{0, 0, 0}, 0.0, 1.0, 0, false, 1469598103934665603ull};
+  PixelResult R{{0, 0, 0}, 0.0, 1.0, 0, 0u, 1469598103934665603ull, {0.0, 0.0, 0.0}};
+  // bound bookkeeping: weights of uncertain inclusions and stops (times the largest colour and
+  // depth seen, at the end), and the current group of near-tied consecutive contributors
+  double incl_w = 0.0, stop_w = 0.0, cmax = 0.0, zmax = 0.0;
+  double g_T = 0.0, g_keep = 1.0, g_cmin[3] = {0, 0, 0}, g_cmax[3] = {0, 0, 0}, g_zmin = 0.0, g_zmax = 0.0;
+  int g_n = 0;
+  auto close_group = [&]() {
+    if (g_n > 1) {
+      double dc = 0.0;
+      for (int ch = 0; ch < 3; ++ch) dc = std::max(dc, g_cmax[ch] - g_cmin[ch]);
+      const double w = g_T * (1.0 - g_keep);  // the group's total weight, the same in any order
+      R.bound[0] += w * dc;
+      R.bound[1] += w * (g_zmax - g_zmin);
+    }
+    g_n = 0;
+  };
   const double px = x + 0.5, py = y + 0.5;
   double T = 1.0;
   double Terr = 0.0;  // running estimate of the FP32 relative error of T
   double prev_z = -1.0;
+  double prev_T = 0.0, prev_alpha = 0.0, prev_c[3] = {0.0, 0.0, 0.0};  // the previous contributor
   for (size_t k = 0; k < list.size(); ++k) {
     const int64_t id = list[k];
     const Proj<double>& p = B.proj[id];
@@ -740,32 +774,94 @@ PixelResult composite(const Binned& B, const std::vector<int64_t>& list, const C
     const double errs = 1e-6 * terms +
                         4e-7 * (std::fabs(p.ca * dx + p.cb * dy) + std::fabs(p.cb * dx + p.cc * dy)) *
                             (std::fabs(p.mx) + std::fabs(p.my) + 1.0) + 1e-5;
-    if (sigma < errs && p.op * std::exp(-sigma) >= kAlphaMin * 0.9) R.mark = true;
+    const double araw_e = p.op * std::exp(-sigma);
+    if (sigma < errs && araw_e >= kAlphaMin * 0.9) {
+      R.mark |= kMarkEdge;
+      const double a_e = std::min(kAlphaMax, araw_e);
+      incl_w += T * a_e / (1.0 - a_e);
+    }
     if (sigma < 0.0) { fnv(&R.sig, static_cast<uint64_t>(id) * 8 + 1); continue; }
     const double araw = p.op * std::exp(-sigma);
-    if (std::fabs(std::log(araw / kAlphaMin)) < errs) R.mark = true;
-    if (std::fabs(std::log(araw / kAlphaMax)) < errs) R.mark = true;
+    if (std::fabs(std::log(araw / kAlphaMin)) < errs) {
+      R.mark |= kMarkAlphaMin;
+      incl_w += T * kAlphaMin * std::exp(errs) / (1.0 - kAlphaMin);
+    }
+    if (std::fabs(std::log(araw / kAlphaMax)) < errs) {
+      R.mark |= kMarkAlphaMax;
+      incl_w += T * kAlphaMax * errs / (1.0 - kAlphaMax);  // alpha itself moves by at most that
+    }
     const double alpha = std::min(kAlphaMax, araw);
     if (alpha < kAlphaMin) { fnv(&R.sig, static_cast<uint64_t>(id) * 8 + 2); continue; }
     const double Tn = T * (1.0 - alpha);
     const double terr_n = Terr + (alpha / (1.0 - alpha)) * errs + 1.2e-7;
-    if (std::fabs(std::log(Tn / kTMin)) < 2.0 * terr_n + 1e-6) R.mark = true;
+    if (std::fabs(std::log(Tn / kTMin)) < 2.0 * terr_n + 1e-6) {
+      R.mark |= kMarkStop;
+      stop_w += T;  // stopping here or not moves at most the weight left, T
+    }
     if (Tn < kTMin) { fnv(&R.sig, static_cast<uint64_t>(id) * 8 + 3); break; }
-    if (prev_z >= 0.0 && std::fabs(p.z - prev_z) <= 2e-6 * std::max(p.z, prev_z)) R.mark = true;
+    double cp[3];
+    for (int ch = 0; ch < 3; ++ch) {
+      cp[ch] = cam.A[ch * 4 + 3];
+      for (int k2 = 0; k2 < 3; ++k2) cp[ch] += cam.A[ch * 4 + k2] * p.rgb[k2];
+    }
+    const bool tied = prev_z >= 0.0 && std::fabs(p.z - prev_z) <= 2e-6 * std::max(p.z, prev_z);
+    if (tied) {
+      double dc = 0.0;
+      for (int ch = 0; ch < 3; ++ch) dc = std::max(dc, std::fabs(cp[ch] - prev_c[ch]));
+      const double swap = prev_T * prev_alpha * alpha * std::max(dc, std::fabs(p.z - prev_z));
+      R.mark |= swap >= 1e-5 ? kMarkTie : kMarkTieSoft;
+      if (g_n == 0) {  // the group starts with the previous contributor
+        g_n = 1;
+        g_T = prev_T;
+        g_keep = 1.0 - prev_alpha;
+        for (int ch = 0; ch < 3; ++ch) g_cmin[ch] = g_cmax[ch] = prev_c[ch];
+        g_zmin = g_zmax = prev_z;
+      }
+      g_n += 1;
+      g_keep *= 1.0 - alpha;
+      for (int ch = 0; ch < 3; ++ch) {
+        g_cmin[ch] = std::min(g_cmin[ch], cp[ch]);
+        g_cmax[ch] = std::max(g_cmax[ch], cp[ch]);
+      }
+      g_zmin = std::min(g_zmin, p.z);
+      g_zmax = std::max(g_zmax, p.z);
+    } else {
+      close_group();
+    }
+    for (int ch = 0; ch < 3; ++ch) cmax = std::max(cmax, std::fabs(cp[ch]));
+    zmax = std::max(zmax, std::fabs(p.z));
     prev_z = p.z;
+    prev_T = T;
+    prev_alpha = alpha;
+    for (int ch = 0; ch < 3; ++ch) prev_c[ch] = cp[ch];
     const bool clamped = araw > kAlphaMax;
     fnv(&R.sig, static_cast<uint64_t>(id) * 8 + (clamped ? 4 : 5));
     const double w = alpha * T;
-    for (int ch = 0; ch < 3; ++ch) {
-      double cp = cam.A[ch * 4 + 3];
-      for (int k2 = 0; k2 < 3; ++k2) cp += cam.A[ch * 4 + k2] * p.rgb[k2];
-      R.C[ch] += cp * w;
-    }
+    for (int ch = 0; ch < 3; ++ch) R.C[ch] += cp[ch] * w;
     R.D += p.z * w;
     if (trace) trace->push_back(Contrib{id, static_cast<int64_t>(k), dx, dy, sigma, araw, alpha, T, clamped});
     T = Tn;
     Terr = terr_n;
     R.last = static_cast<int64_t>(k) + 1;
+  }
+  close_group();
+  if (incl_w > 0.0 || stop_w > 0.0) {
+    // an uncertain inclusion moves the colour by at most its weight times (its colour + the
+    // colour behind it), alpha by its weight; an uncertain stop moves them by at most the weight
+    // left. The colour and depth bounds are those of the whole list (after the transform).
+    double craw = 0.0;
+    for (int64_t id : list) {
+      const Proj<double>& p = B.proj[id];
+      for (int ch = 0; ch < 3; ++ch) craw = std::max(craw, std::fabs(p.rgb[ch]));
+      zmax = std::max(zmax, std::fabs(p.z));
+    }
+    for (int ch = 0; ch < 3; ++ch) {
+      const double a = std::fabs(cam.A[ch * 4]) + std::fabs(cam.A[ch * 4 + 1]) + std::fabs(cam.A[ch * 4 + 2]);
+      cmax = std::max(cmax, a * craw + std::fabs(cam.A[ch * 4 + 3]));
+    }
+    R.bound[0] += (2.0 * incl_w + stop_w) * cmax;
+    R.bound[1] += (2.0 * incl_w + stop_w) * zmax;
+    R.bound[2] += incl_w + stop_w;
   }
   R.T = T;
   return R;
@@ -840,17 +936,20 @@ int oracle_project(int64_t n, const double* means, const double* scales, const d
 //   opts[6]: eps2d, antialiased, tile_cull, bg r, g, b
 //   tile_subset: global tile ids to composite (NULL: all tiles); other pixels are left untouched
 //   out_img[sum HW][8]: r, g, b, depth_acc, depth_exp, alpha, T_final, n_contrib
-//   out_mark[sum HW]: 1 where a discrete decision at this pixel is within FP32 reach
+//   out_mark[sum HW]: nonzero where a discrete decision at this pixel is within FP32 reach: the
+//                     reasons as kMark* bits
 //   out_sig[sum HW] or NULL: hash of every per-Gaussian decision at the pixel
 //   out_pairs[pair_cap][2] or NULL: (global tile, c*n+g) in blend order, tile-major
 //   out_gmark[C*n] or NULL: Gaussian-level knife edges
+//   out_bound[sum HW][3] or NULL: per pixel, the largest change of its colour (any channel),
+//                     depth_acc and alpha that the marked decisions could make (PixelResult::bound)
 // Returns the total number of (tile, Gaussian) pairs, or -1 on invalid arguments.
 int64_t oracle_render(int64_t n, const double* means, const double* scales, const double* quats,
                       const double* opac, const double* sh, int K, int deg, int C, const double* cams,
                       const double* affines, const double* opts, const int64_t* tile_subset,
                       int64_t n_subset, double* out_img, uint8_t* out_mark, uint64_t* out_sig,
                       int64_t* out_pairs, int64_t pair_cap, uint8_t* out_gmark, const double* gemb,
-                      const double* iemb, const double* mlp) {
+                      const double* iemb, const double* mlp, double* out_bound) {
   if (!valid_inputs(n, means, scales, quats, opac, sh, K, deg, C, cams)) return -1;
   SceneD s{n, means, scales, quats, opac, sh, K, deg, gemb, mlp};
   std::vector<CamD> cv = load_cams(C, cams, affines, iemb);
@@ -893,8 +992,10 @@ int64_t oracle_render(int64_t n, const double* means, const double* scales, cons
         out[5] = alpha;
         out[6] = R.T;
         out[7] = static_cast<double>(R.last);
-        if (out_mark) out_mark[pix] = (R.mark || B.tile_mark[t]) ? 1 : 0;
+        if (out_mark) out_mark[pix] = static_cast<uint8_t>(R.mark | (B.tile_mark[t] ? kMarkTile : 0u));
         if (out_sig) out_sig[pix] = R.sig;
+        if (out_bound)
+          for (int k = 0; k < 3; ++k) out_bound[3 * pix + k] = R.bound[k];
       }
   }
   return P;

@@ -37,7 +37,7 @@ struct gsr_ctx {
   Buf seg_begin, seg_start, seg_cams;
   Buf rec, owner;                              // records (recompute / no-state mode)
   Buf sort_ktmp, sort_vtmp, sort_hist, sort_status;  // gsr_sort_pairs_u32
-  Buf pre_status, scan_status, misc, tile_ctr;
+  Buf pre_status, scan_status, misc, tile_ctr, big_tiles;
   Buf pair_keys, key_scratch, pvals_s, ranges;  // pairs (pvals_s, ranges: no-state mode)
   Buf pix_T, pix_n, pix_D;                     // per-pixel state (no-state mode)
   Buf g2d, gaff;
@@ -408,7 +408,7 @@ gsr_status upload_segments(gsr_ctx* ctx, const gsr_gaussians* g, SegMap* m, cuda
 }
 
 gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb, const gsr_opts* o, BinOut bo,
-                       long long* V_out, long long* P_out, cudaStream_t s) {
+                       long long* V_out, long long* P_out, cudaStream_t s, long long* max_tile_out = nullptr) {
   const long long N = render_count(g);
   const int C = cb.C;
   const long long capv = std::max<long long>(1, N * C);
@@ -425,13 +425,14 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   GSR_TRY_ALLOC(*bo.owner, sizeof(uint32_t) * capv);
   GSR_TRY_ALLOC(*bo.ranges, sizeof(uint2) * std::max(tiles, 1));
   GSR_TRY_ALLOC(ctx->tile_ctr, sizeof(uint32_t) * std::max(tiles, 1));
+  GSR_TRY_ALLOC(ctx->big_tiles, sizeof(uint32_t) * std::max(tiles, 1));
   if (!ensure_zeroed(ctx, ctx->pre_status, sizeof(unsigned long long) * std::max(pre_blocks, 1), s))
     return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
   const long long scan_blocks = (tiles + kScanThreads * kScanItems - 1) / (kScanThreads * kScanItems);
   if (!ensure_zeroed(ctx, ctx->scan_status, sizeof(unsigned long long) * (scan_blocks + 1), s))
     return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
   // misc (32-bit words): [0] preprocess block counter, [1] V, [2] tile-scan block counter,
-  // [3] largest tile's pair count, [4..5] P (64-bit)
+  // [3] largest tile's pair count, [4..5] P (64-bit), [6] tiles listed for the large-list sort
   GSR_TRY_ALLOC(ctx->misc, 64);
   uint32_t* misc = as<uint32_t>(ctx->misc);
   uint32_t* d_V = misc + 1;
@@ -470,7 +471,8 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   {
     StageTimer tm(ctx, GSR_STAGE_TILE_SCAN, s);
     launch_tile_scan(tile_ctr, as<uint2>(*bo.ranges), tiles, as<unsigned long long>(ctx->scan_status), misc + 2, d_P,
-                     misc + 3, next_epoch(ctx, s), ctx->d_err, ctx->wait, ctx->grid_cap, s);
+                     misc + 3, as<uint32_t>(ctx->big_tiles), misc + 6, next_epoch(ctx, s), ctx->d_err, ctx->wait,
+                     ctx->grid_cap, s);
   }
   // read V, P, the largest tile and the error word
   uint32_t* h = static_cast<uint32_t*>(ctx->pinned);
@@ -500,6 +502,7 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   if (P >= (1ll << 30)) return set_err(ctx, GSR_ERR_UNSUPPORTED, "more than 2^30 (tile, Gaussian) pairs");
   *V_out = V;
   *P_out = P;
+  if (max_tile_out) *max_tile_out = P > 0 ? static_cast<long long>(max_count) : 0;
   // the next preprocess picks its variant from this launch's survivor ratio
   ctx->pre_dense = 4 * V > N * C;
 
@@ -507,8 +510,6 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   const long long Pc = std::max<long long>(P, 1);
   GSR_TRY_ALLOC(ctx->pair_keys, sizeof(unsigned long long) * Pc);
   GSR_TRY_ALLOC(*bo.pvals_s, sizeof(uint32_t) * Pc);
-  int cap = 1;
-  while (cap < static_cast<long long>(max_count) && cap < kTileSortCap) cap <<= 1;
   unsigned long long* scratch = nullptr;
   if (max_count > static_cast<uint32_t>(kTileSortCap)) {
     GSR_TRY_ALLOC(ctx->key_scratch, sizeof(unsigned long long) * Pc);
@@ -523,7 +524,7 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
     {
       StageTimer tm(ctx, GSR_STAGE_TILE_SORT, s);
       launch_tile_sort(as<unsigned long long>(ctx->pair_keys), as<uint2>(*bo.ranges), tiles, as<uint32_t>(*bo.pvals_s),
-                       scratch, cap, s);
+                       scratch, max_count, as<uint32_t>(ctx->big_tiles), misc + 6, ctx->grid_cap, s);
     }
   }
   e = cudaGetLastError();
@@ -613,7 +614,7 @@ void gsr_destroy(gsr_ctx* ctx) {
   ctx->state_pool.clear();
   Buf* all[] = {&ctx->seg_begin, &ctx->seg_start, &ctx->seg_cams, &ctx->rec, &ctx->owner, &ctx->sort_ktmp,
                 &ctx->sort_vtmp, &ctx->sort_hist, &ctx->sort_status, &ctx->pre_status, &ctx->scan_status, &ctx->misc,
-                &ctx->tile_ctr, &ctx->pair_keys, &ctx->key_scratch, &ctx->pvals_s, &ctx->ranges, &ctx->pix_T,
+                &ctx->tile_ctr, &ctx->big_tiles, &ctx->pair_keys, &ctx->key_scratch, &ctx->pvals_s, &ctx->ranges, &ctx->pix_T,
                 &ctx->pix_n, &ctx->pix_D, &ctx->g2d, &ctx->gaff};
   for (Buf* b : all) release(ctx, *b, nullptr);
   for (auto& r : ctx->prof_recs) {
@@ -689,8 +690,8 @@ gsr_status gsr_render_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_ca
   } else {
     bo = BinOut{&ctx->rec, &ctx->owner, &ctx->pvals_s, &ctx->ranges};
   }
-  long long V = 0, P = 0;
-  st = run_binning(ctx, g, cb, opts, bo, &V, &P, s);
+  long long V = 0, P = 0, max_tile = 0;
+  st = run_binning(ctx, g, cb, opts, bo, &V, &P, s, &max_tile);
   if (st != GSR_OK) {
     if (stt) gsr_state_release(ctx, stt);
     return st;
@@ -728,6 +729,7 @@ gsr_status gsr_render_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_ca
     stt->info.n_pairs = P;
     stt->info.n_tiles = cb.total_tiles;
     stt->info.n_pixels = npix;
+    stt->info.max_tile_pairs = max_tile;
     *state_out = stt;
   }
   return GSR_OK;

@@ -246,22 +246,26 @@ void radix_sort_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
 // launch_bin_pairs with keys == nullptr adds each tile's pair count to tile_ctr (zeroed before;
 // ranges unused);
 // launch_tile_scan turns the counts into ranges [start, end), P (*p_total), the largest count
-// (*max_count, zeroed before) and per-tile cursors (in tile_ctr); launch_bin_pairs with keys
+// (*max_count, zeroed before), the list of tiles with more than kTileSortSmall pairs (big,
+// *n_big zeroed before) and per-tile cursors (in tile_ctr); launch_bin_pairs with keys
 // places each pair's key (depth bits << 32 | record) in its tile's range (a pair past the range end
 // sets kErrOverflow in *err and is not written); launch_tile_sort sorts
-// every tile's keys and writes the records in that order into vals. Tiles with more than `cap`
-// pairs (a power of two) are sorted in runs merged through `scratch` ([P], may be null if none is).
+// every tile's keys and writes the records in that order into vals. Tiles with more than
+// kTileSortCap pairs are sorted in runs merged through `scratch` ([P], null when max_count is
+// at most kTileSortCap).
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
-constexpr int kTileSortCap = 4096;
+constexpr int kTileSortSmall = 1024;  // tiles up to this many pairs: one small block each
+constexpr int kTileSortCap = 16384;   // keys a large block sorts in shared memory (128 KB)
 void launch_bin_pairs(const Rec* rec, const uint32_t* d_n, long long max_n, const CamBatch& cams, int tile_cull,
                       uint32_t* tile_ctr, const uint2* ranges, unsigned long long* keys, int* err, int max_blocks,
                       cudaStream_t s);
 void launch_tile_scan(uint32_t* tile_ctr, uint2* ranges, int n_tiles, unsigned long long* status, uint32_t* counter,
-                      unsigned long long* p_total, uint32_t* max_count, uint32_t epoch, int* err, WaitCfg wait,
-                      int grid_cap, cudaStream_t s);
+                      unsigned long long* p_total, uint32_t* max_count, uint32_t* big, uint32_t* n_big, uint32_t epoch,
+                      int* err, WaitCfg wait, int grid_cap, cudaStream_t s);
 void launch_tile_sort(unsigned long long* keys, const uint2* ranges, int n_tiles, uint32_t* vals,
-                      unsigned long long* scratch, int cap, cudaStream_t s);
+                      unsigned long long* scratch, uint32_t max_count, const uint32_t* big, const uint32_t* n_big,
+                      int grid_cap, cudaStream_t s);
 
 struct BlendFwdOut {
   float* rgb;

@@ -8,8 +8,11 @@
 //               each pixel blends front to back and stops at T < 1e-4; the CTA stops loading
 //               once every pixel is done.
 //   blend bwd:  same tiling, contributors walked back to front recovering T_i = T_{i+1}/(1-a_i);
-//               per-Gaussian gradients are summed over the warp with shuffles, over the CTA in
-//               shared memory, and added to global memory once per (tile, Gaussian).
+//               the walk queues each contribution (Gaussian, pixel, dL/dalpha, weight) per warp,
+//               and every 32 queued contributions are turned into gradients by the 32 lanes at
+//               once (a Gaussian takes only a few of a warp's 64 pixels), summed per Gaussian with
+//               a segmented shuffle sum, over the CTA in shared memory, and added to global memory
+//               once per (tile, Gaussian).
 #include <algorithm>
 
 #include "gsr_internal.cuh"
@@ -158,12 +161,13 @@ __global__ void __launch_bounds__(256) bin_pairs_kernel(const Rec* __restrict__ 
 
 // Exclusive scan of the per-tile pair counts (chained scan, decoupled look-back): ranges[t] =
 // [start, start + count); the counter becomes the tile's cursor (start) for the placing pass;
-// *p_total = P; *max_count = the largest tile's count.
+// *p_total = P; *max_count = the largest tile's count; the tiles with more than kTileSortSmall
+// pairs are listed in big[0, *n_big) (any order) for the large-list sort.
 __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(uint32_t* __restrict__ ctr, uint2* __restrict__ ranges,
                                                                  int n_tiles, unsigned long long* status,
                                                                  uint32_t* counter, unsigned long long* p_total,
-                                                                 uint32_t* max_count, uint32_t epoch, int* err,
-                                                                 WaitCfg wait) {
+                                                                 uint32_t* max_count, uint32_t* big, uint32_t* n_big,
+                                                                 uint32_t epoch, int* err, WaitCfg wait) {
   __shared__ uint32_t s_bid;
   __shared__ unsigned long long s_base;
   __shared__ uint32_t s_max[kScanThreads / 32];
@@ -206,6 +210,7 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(uint32_t* __res
         if (run + x[k] > 0xffffffffull) atomicOr(err, kErrOverflow);
         ranges[idx] = make_uint2(static_cast<uint32_t>(run), static_cast<uint32_t>(run + x[k]));
         ctr[idx] = static_cast<uint32_t>(run);
+        if (x[k] > static_cast<uint32_t>(kTileSortSmall)) big[atomicAdd(n_big, 1u)] = static_cast<uint32_t>(idx);
         if (idx == n_tiles - 1) *p_total = run + x[k];
       }
       run += x[k];
@@ -253,18 +258,19 @@ __device__ void block_merge(const unsigned long long* a, int na, const unsigned 
   }
 }
 
-// One block per tile: sorts the tile's keys (depth bits << 32 | record index), i.e. its pairs by
-// depth with ties to the lower record (so the lower Gaussian index, C7), and writes the records in
-// that order. A list of at most `cap` keys (a power of two; the dynamic shared memory holds cap
-// keys) is sorted in shared memory; a longer one in runs of cap, merged pairwise in global memory
-// through `scratch` (same offsets as the keys).
-__global__ void __launch_bounds__(256) tile_sort_kernel(unsigned long long* __restrict__ keys, const uint2* __restrict__ ranges,
-                                                        uint32_t* __restrict__ vals, unsigned long long* __restrict__ scratch,
-                                                        int cap) {
-  extern __shared__ unsigned long long s_keys[];
-  const uint2 r = ranges[blockIdx.x];
+// Per-tile sort: tiles of at most kTileSortSmall pairs get a block of kSortSmallThreads each; the
+// larger ones blocks of kSortBigThreads that sort up to kTileSortCap keys in shared memory.
+constexpr int kSortSmallThreads = 128;
+constexpr int kSortBigThreads = 1024;
+
+// Sorts one tile's keys (depth bits << 32 | record index), i.e. its pairs by depth with ties to
+// the lower record (so the lower Gaussian index, C7), and writes the records in that order (whole
+// block). A list of at most `cap` keys (a power of two; s_keys holds cap keys) is sorted in shared
+// memory; a longer one in runs of cap, merged pairwise in global memory through `scratch` (same
+// offsets as the keys).
+__device__ void sort_tile(unsigned long long* __restrict__ keys, uint2 r, uint32_t* __restrict__ vals,
+                          unsigned long long* __restrict__ scratch, int cap, unsigned long long* s_keys) {
   const int n = static_cast<int>(r.y - r.x);
-  if (n == 0) return;
   unsigned long long* k = keys + r.x;
   if (n <= cap) {
     int m = 1;
@@ -273,6 +279,7 @@ __global__ void __launch_bounds__(256) tile_sort_kernel(unsigned long long* __re
     __syncthreads();
     block_bitonic_sort(s_keys, m);
     for (int i = threadIdx.x; i < n; i += blockDim.x) vals[r.x + i] = static_cast<uint32_t>(s_keys[i]);
+    __syncthreads();
     return;
   }
   // runs of cap keys sorted in place
@@ -299,6 +306,30 @@ __global__ void __launch_bounds__(256) tile_sort_kernel(unsigned long long* __re
     dst = t;
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) vals[r.x + i] = static_cast<uint32_t>(src[i]);
+  __syncthreads();
+}
+
+// One small block per tile of at most kTileSortSmall pairs (larger tiles are left to the list sort).
+__global__ void __launch_bounds__(kSortSmallThreads) tile_sort_kernel(unsigned long long* __restrict__ keys,
+                                                                      const uint2* __restrict__ ranges,
+                                                                      uint32_t* __restrict__ vals, int cap) {
+  extern __shared__ unsigned long long s_keys[];
+  const uint2 r = ranges[blockIdx.x];
+  const uint32_t n = r.y - r.x;
+  if (n == 0 || n > static_cast<uint32_t>(kTileSortSmall)) return;
+  sort_tile(keys, r, vals, nullptr, cap, s_keys);
+}
+
+// Large blocks over the listed tiles with more than kTileSortSmall pairs.
+__global__ void __launch_bounds__(kSortBigThreads) tile_sort_big_kernel(unsigned long long* __restrict__ keys,
+                                                                        const uint2* __restrict__ ranges,
+                                                                        uint32_t* __restrict__ vals,
+                                                                        unsigned long long* __restrict__ scratch,
+                                                                        const uint32_t* __restrict__ big,
+                                                                        const uint32_t* __restrict__ n_big, int cap) {
+  extern __shared__ unsigned long long s_keys[];
+  const uint32_t nb = *n_big;
+  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) sort_tile(keys, ranges[big[b]], vals, scratch, cap, s_keys);
 }
 
 template <bool kCount>
@@ -427,54 +458,9 @@ __device__ __forceinline__ float warp_sum(float x) {
 
 constexpr int kGradVals = 12;
 
-// Sums N (<= 16) per-lane values over the warp with about N + 2 shuffles instead of 5 N. Each
-// round halves the vector: a lane sends the half it gives up to its partner across `kBit` and
-// keeps the sum of the other half (an odd length is padded with a zero). Once one value is
-// left, the remaining lane bits are summed directly. index() gives the value each lane ends up
-// holding (-1: padding).
-template <int N, int kBit>
-struct TransposeSum {
-  static __device__ __forceinline__ float run(const float* v, int lane) {
-    constexpr int H = (N + 1) / 2;
-    const bool up = lane & kBit;
-    float w[H];
-#pragma unroll
-    for (int k = 0; k < H; ++k) {
-      const float lo = v[k];
-      const float hi = (k + H < N) ? v[k + H] : 0.f;
-      const float send = up ? lo : hi;
-      const float keep = up ? hi : lo;
-      w[k] = keep + __shfl_xor_sync(0xffffffffu, send, kBit);
-    }
-    return TransposeSum<H, kBit / 2>::run(w, lane);
-  }
-  static __device__ __forceinline__ int index(int lane) {
-    constexpr int H = (N + 1) / 2;
-    const int r = TransposeSum<H, kBit / 2>::index(lane);
-    if (r < 0) return -1;
-    if (lane & kBit) return r < N - H ? H + r : -1;  // the upper half holds N - H values
-    return r;
-  }
-};
-template <int kBit>
-struct TransposeSum<1, kBit> {
-  static __device__ __forceinline__ float run(const float* v, int) {
-    float x = v[0];
-#pragma unroll
-    for (int b = kBit; b > 0; b >>= 1) x += __shfl_xor_sync(0xffffffffu, x, b);
-    return x;
-  }
-  static __device__ __forceinline__ int index(int) { return 0; }
-};
-
-// Lane bits still summed directly after the halving rounds of an N-value transpose sum: lanes
-// that differ only in these bits hold the same total.
-template <int N>
-__host__ __device__ constexpr int transpose_shared_bits() {
-  int n = N, bit = 16;
-  while (n > 1 && bit > 0) { n = (n + 1) / 2; bit >>= 1; }
-  return 2 * bit - 1;
-}
+// Contributions queued per warp between the reverse walk and the gradient pass (a power of two,
+// at least 32 pending plus the 64 one Gaussian can add).
+constexpr int kQueue = 128;
 
 // kAbs: also accumulate |dL/dmean2D| per pixel (AbsGS densification statistics).
 template <bool kCount, bool kAbs>
@@ -491,6 +477,9 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
   __shared__ uint32_t sV[kBatch];
   __shared__ uint32_t sM[kBatch];
   __shared__ float sAcc[kBatch][kGradVals + 1];
+  __shared__ uint32_t sQk[kBlendWarps][kQueue];  // queued: batch slot | pixel << 16 | clamped << 31
+  __shared__ float2 sQv[kBlendWarps][kQueue];    // their dL/dalpha and weight alpha T
+  __shared__ float4 sPix[kBlendWarps][64];       // per pixel: dL/dC (3) after the transform, dL/dD
   __shared__ uint32_t s_max;
   __shared__ float s_aff[kBlendWarps][12];
   const int t = blockIdx.x;
@@ -499,8 +488,6 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
   const int lt = t - cam.tile_off;
   const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int t_idx = TransposeSum<kVals, 16>::index(lane);  // the gradient value this lane sums
-  const bool t_keep = t_idx >= 0 && (lane & transpose_shared_bits<kVals>()) == 0;
   const int px = tx * kTile + 8 * (wid & 1) + (tid & 7);
   const int py0 = ty * kTile + 8 * (wid >> 1) + 2 * ((tid & 31) >> 3);
   const float fx = px + 0.5f;
@@ -557,9 +544,80 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
     GTz[q] = gda * (zf + zrel) + gal - (g0[q] * (bg.x - bb0) + g1[q] * (bg.y - bb1) + g2[q] * (bg.z - bb2));
     T[q] = Tf[q];
   }
+  // the pixel constants the gradient pass reads (pixel p of a warp: lane p >> 1, row p & 1)
+#pragma unroll
+  for (int q = 0; q < 2; ++q) sPix[wid][2 * lane + q] = make_float4(GC0[q], GC1[q], GC2[q], GD[q]);
   __syncthreads();
   const int n = static_cast<int>(s_max);
+  const float tile_x = tx * kTile + 8 * (wid & 1) + 0.5f, tile_y = ty * kTile + 8 * (wid >> 1) + 0.5f;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  uint32_t q_head = 0, q_tail = 0;  // this warp's contribution queue (warp-uniform counters)
   uint32_t n_visit = 0, n_contrib = 0;
+
+  // Gradient pass over `k` queued contributions from q_head: lane l takes contribution l, forms the
+  // per-Gaussian values of that (pixel, Gaussian) pair, the values of equal Gaussians (adjacent in
+  // the queue) are summed with a segmented shuffle sum, and the first lane of each run adds its
+  // sums to the batch's shared accumulators.
+  auto flush = [&](int k) {
+    __syncwarp();
+    const bool act = lane < k;
+    const uint32_t slot = (q_head + lane) & (kQueue - 1);
+    const uint32_t key = act ? sQk[wid][slot] : 0u;
+    const uint32_t j = key & 0xffffu;
+    const uint32_t run = act ? j : 0xffffffffu;  // run id: the batch slot, none for idle lanes
+    float gv[kGradVals];
+#pragma unroll
+    for (int m = 0; m < kGradVals; ++m) gv[m] = 0.f;
+    if (act) {
+      const float2 dv = sQv[wid][slot];  // dL/dalpha, alpha T
+      const uint32_t p = (key >> 16) & 0x3fu;
+      const float4 a = sA[j];
+      const float4 b = sB[j];
+      const float dx = a.x - (tile_x + static_cast<float>((p >> 1) & 7));
+      const float dy = a.y - (tile_y + static_cast<float>(2 * (p >> 4) + (p & 1)));
+      const float sigma = 0.5f * (b.x * dx * dx + b.z * dy * dy) + b.y * dx * dy;
+      const float G = __expf(-sigma);
+      const float araw = a.z * G;
+      const float draw = (key >> 31) ? 0.f : dv.x;  // the clamp at 0.99 (as the walk decided) passes no gradient
+      const float dsig = -draw * araw;
+      const float dmx = (b.x * dx + b.y * dy) * dsig;
+      const float dmy = (b.y * dx + b.z * dy) * dsig;
+      const float4 pc = sPix[wid][p];
+      gv[0] = dmx;
+      gv[1] = dmy;
+      gv[2] = draw * G;
+      gv[3] = pc.w * dv.y;
+      gv[4] = 0.5f * dx * dx * dsig;
+      gv[5] = dx * dy * dsig;
+      gv[6] = 0.5f * dy * dy * dsig;
+      gv[7] = pc.x * dv.y;
+      gv[8] = pc.y * dv.y;
+      gv[9] = pc.z * dv.y;
+      if (kAbs) {
+        gv[10] = fabsf(dmx);
+        gv[11] = fabsf(dmy);
+      }
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t other = __shfl_down_sync(0xffffffffu, run, off);
+      const bool same = lane + off < 32 && other == run;
+#pragma unroll
+      for (int m = 0; m < kVals; ++m) {
+        const float y = __shfl_down_sync(0xffffffffu, gv[m], off);
+        if (same) gv[m] += y;
+      }
+    }
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, run, 1);
+    if (act && (lane == 0 || prev != run)) {
+#pragma unroll
+      for (int m = 0; m < kVals; ++m)
+        if (gv[m] != 0.f) atomicAdd(&sAcc[j][m], gv[m]);
+    }
+    q_head += static_cast<uint32_t>(k);
+    __syncwarp();
+  };
+
   for (int base = 0; base < n; base += kBatch) {
     __syncthreads();
     for (int k = tid; k < kBatch; k += kBlendThreads) {
@@ -585,30 +643,26 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
       const float4 b = sB[j];
       const float2 cc = sC[j];
       const float dx = a.x - fx;
-      float dyq[2], Gq[2], arawq[2], alphaq[2];
+      float Gq[2], arawq[2], alphaq[2];
       bool cq[2];
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const bool vis = inside[q] && pos < last[q];
         if (kCount) n_visit += vis;
-        dyq[q] = a.y - fy[q];
-        const float sigma = 0.5f * (b.x * dx * dx + b.z * dyq[q] * dyq[q]) + b.y * dx * dyq[q];
+        const float dy = a.y - fy[q];
+        const float sigma = 0.5f * (b.x * dx * dx + b.z * dy * dy) + b.y * dx * dy;
         Gq[q] = __expf(-sigma);
         arawq[q] = a.z * Gq[q];
         alphaq[q] = fminf(kAlphaMax, arawq[q]);
         cq[q] = vis && sigma >= 0.f && alphaq[q] >= kAlphaMin;
         if (kCount) n_contrib += cq[q];
       }
-      // warp-uniform: where no pixel of the warp takes the Gaussian, nothing below changes
-      if (!__any_sync(0xffffffffu, cq[0] || cq[1])) continue;
-      float gv[kGradVals];
+      const uint32_t m0 = __ballot_sync(0xffffffffu, cq[0]);
+      const uint32_t m1 = __ballot_sync(0xffffffffu, cq[1]);
+      if (!(m0 | m1)) continue;  // warp-uniform: no pixel of the warp takes the Gaussian
+      // the reverse walk: this contributor's transmittance and dL/dalpha, then the suffix sums
 #pragma unroll
-      for (int m = 0; m < kGradVals; ++m) gv[m] = 0.f;
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {  // branch-free: contributions are masked, not branched around
-        const float dy = dyq[q];
-        const float G = Gq[q];
-        const float araw = arawq[q];
+      for (int q = 0; q < 2; ++q) {  // branch-free: non-contributors change nothing
         const float alpha = alphaq[q];
         const bool c = cq[q];
         const float rom = __frcp_rn(1.f - alpha);  // 1 / (1 - alpha), correctly rounded
@@ -622,28 +676,17 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
         S2[q] = fmaf(cc.y, wgt, S2[q]);
         SD[q] = fmaf(dz, wgt, SD[q]);
         T[q] = c ? Ti : T[q];
-        const float draw = (c && araw <= kAlphaMax) ? dal : 0.f;  // the clamp at 0.99 passes no gradient
-        const float dsig = -draw * araw;
-        const float dmx = (b.x * dx + b.y * dy) * dsig;
-        const float dmy = (b.y * dx + b.z * dy) * dsig;
-        gv[0] += dmx;
-        gv[1] += dmy;
-        gv[2] += draw * G;
-        gv[3] += GD[q] * wgt;
-        gv[4] += 0.5f * dx * dx * dsig;
-        gv[5] += dx * dy * dsig;
-        gv[6] += 0.5f * dy * dy * dsig;
-        gv[7] += GC0[q] * wgt;
-        gv[8] += GC1[q] * wgt;
-        gv[9] += GC2[q] * wgt;
-        if (kAbs) {
-          gv[10] += fabsf(dmx);
-          gv[11] += fabsf(dmy);
+        if (c) {
+          const uint32_t slot = q_tail + (q ? __popc(m0) : 0u) + __popc((q ? m1 : m0) & lt_mask);
+          sQk[wid][slot & (kQueue - 1)] = static_cast<uint32_t>(j) | (static_cast<uint32_t>(2 * lane + q) << 16) |
+                                           (arawq[q] > kAlphaMax ? 0x80000000u : 0u);
+          sQv[wid][slot & (kQueue - 1)] = make_float2(dal, wgt);
         }
       }
-      const float tot = TransposeSum<kVals, 16>::run(gv, lane);
-      if (t_keep) atomicAdd(&sAcc[j][t_idx], tot);
+      q_tail += __popc(m0) + __popc(m1);
+      while (q_tail - q_head >= 32) flush(32);
     }
+    if (q_tail != q_head) flush(static_cast<int>(q_tail - q_head));  // the batch's slots are reused next
     __syncthreads();
     for (int k = tid; k < cnt; k += kBlendThreads) {
       float* f = reinterpret_cast<float*>(g2d + sV[k]);
@@ -709,19 +752,33 @@ void launch_bin_pairs(const Rec* rec, const uint32_t* d_n, long long max_n, cons
 }
 
 void launch_tile_scan(uint32_t* tile_ctr, uint2* ranges, int n_tiles, unsigned long long* status, uint32_t* counter,
-                      unsigned long long* p_total, uint32_t* max_count, uint32_t epoch, int* err, WaitCfg wait,
-                      int grid_cap, cudaStream_t s) {
+                      unsigned long long* p_total, uint32_t* max_count, uint32_t* big, uint32_t* n_big, uint32_t epoch,
+                      int* err, WaitCfg wait, int grid_cap, cudaStream_t s) {
   if (n_tiles <= 0) return;
   const long long per = kScanThreads * kScanItems;
   const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>((n_tiles + per - 1) / per, grid_cap)));
-  tile_scan_kernel<<<grid, kScanThreads, 0, s>>>(tile_ctr, ranges, n_tiles, status, counter, p_total, max_count,
-                                                 epoch, err, wait);
+  tile_scan_kernel<<<grid, kScanThreads, 0, s>>>(tile_ctr, ranges, n_tiles, status, counter, p_total, max_count, big,
+                                                 n_big, epoch, err, wait);
 }
 
 void launch_tile_sort(unsigned long long* keys, const uint2* ranges, int n_tiles, uint32_t* vals,
-                      unsigned long long* scratch, int cap, cudaStream_t s) {
-  if (n_tiles <= 0) return;
-  tile_sort_kernel<<<n_tiles, 256, sizeof(unsigned long long) * cap, s>>>(keys, ranges, vals, scratch, cap);
+                      unsigned long long* scratch, uint32_t max_count, const uint32_t* big, const uint32_t* n_big,
+                      int grid_cap, cudaStream_t s) {
+  if (n_tiles <= 0 || max_count == 0) return;
+  int cap = 1;
+  while (cap < static_cast<long long>(max_count) && cap < kTileSortSmall) cap <<= 1;
+  tile_sort_kernel<<<n_tiles, kSortSmallThreads, sizeof(unsigned long long) * cap, s>>>(keys, ranges, vals, cap);
+  if (max_count > static_cast<uint32_t>(kTileSortSmall)) {
+    int big_cap = 1;
+    while (big_cap < static_cast<long long>(max_count) && big_cap < kTileSortCap) big_cap <<= 1;
+    // the large dynamic shared memory needs an opt-in (per process, once; repeating it is harmless)
+    static const cudaError_t attr = cudaFuncSetAttribute(tile_sort_big_kernel,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         static_cast<int>(sizeof(unsigned long long) * kTileSortCap));
+    (void)attr;
+    tile_sort_big_kernel<<<std::max(1, grid_cap / 2), kSortBigThreads, sizeof(unsigned long long) * big_cap, s>>>(
+        keys, ranges, vals, scratch, big, n_big, big_cap);
+  }
 }
 
 void launch_blend_fwd(const Rec* rec, const uint32_t* pair_vals, const uint2* ranges, const CamBatch& cams,

@@ -126,7 +126,8 @@ class TorchAllocator:
 
 class CStateInfo(ctypes.Structure):
     _fields_ = [("n_render", ctypes.c_int64), ("n_cams", ctypes.c_int32), ("n_visible", ctypes.c_int64),
-                ("n_pairs", ctypes.c_int64), ("n_tiles", ctypes.c_int64), ("n_pixels", ctypes.c_int64)]
+                ("n_pairs", ctypes.c_int64), ("n_tiles", ctypes.c_int64), ("n_pixels", ctypes.c_int64),
+                ("max_tile_pairs", ctypes.c_int64)]
 
 
 def lib_path() -> str:
@@ -360,7 +361,7 @@ class State:
         i = CStateInfo()
         _check(self.ctx, load().gsr_state_get_info(self.handle, ctypes.byref(i)))
         return dict(n_render=i.n_render, n_cams=i.n_cams, n_visible=i.n_visible, n_pairs=i.n_pairs,
-                    n_tiles=i.n_tiles, n_pixels=i.n_pixels)
+                    n_tiles=i.n_tiles, n_pixels=i.n_pixels, max_tile_pairs=i.max_tile_pairs)
 
     def copy(self, which: int, count: int, dtype=torch.int32, width: int = 1) -> torch.Tensor:
         out = torch.empty((count, width) if width > 1 else (count,), dtype=dtype, device=f"cuda:{self.ctx.device}")

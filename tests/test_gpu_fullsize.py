@@ -92,12 +92,29 @@ def _dequantised(scene, g):
                         scene.sh_degree)
 
 
-def _check_images(out, res, pix, depth_scale, min_unmarked=0.8):
-    um = pix[res.mark[pix] == 0]
-    assert um.size > min_unmarked * pix.size, f"{um.size} of {pix.size} pixels unmarked"
-    np.testing.assert_allclose(out["rgb"].cpu().numpy()[um], res.img[um, 0:3], atol=1e-4)
-    np.testing.assert_allclose(out["alpha"].cpu().numpy()[um], res.img[um, 5], atol=1e-4)
-    np.testing.assert_allclose(out["depth_acc"].cpu().numpy()[um], res.img[um, 3], atol=1e-4 * depth_scale)
+def _check_images(out, res, pix, depth_scale, min_compared=0.9):
+    """Unmarked pixels within 1e-4 (depth within 1e-4 of the depth scale). Marked pixels, except
+    those whose tile list is itself uncertain, within 1e-4 plus the oracle's bound on what their
+    uncertain decisions can change (res.bound). At least min_compared of the pixels are compared.
+    Returns the unmarked pixels (the only ones that carry upstream gradients)."""
+    mark = res.mark[pix]
+    um = pix[mark == 0]
+    mk = pix[(mark != 0) & ((mark & oracle.MARK_TILE) == 0)]
+    compared = (um.size + mk.size) / pix.size
+    print(f"\nimages: {um.size} unmarked, {mk.size} marked and compared within their bound, "
+          f"{pix.size - um.size - mk.size} in uncertain tile lists, of {pix.size} ({compared:.3f} compared)")
+    assert compared >= min_compared, f"{compared:.3f} of the sampled pixels compared"
+    rgb = out["rgb"].cpu().numpy().astype(np.float64)
+    alpha = out["alpha"].cpu().numpy().astype(np.float64)
+    dacc = out["depth_acc"].cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(rgb[um], res.img[um, 0:3], atol=1e-4)
+    np.testing.assert_allclose(alpha[um], res.img[um, 5], atol=1e-4)
+    np.testing.assert_allclose(dacc[um], res.img[um, 3], atol=1e-4 * depth_scale)
+    if mk.size:
+        b = res.bound[mk]
+        assert np.all(np.abs(rgb[mk] - res.img[mk, 0:3]).max(axis=1) <= 1e-4 + b[:, 0])
+        assert np.all(np.abs(alpha[mk] - res.img[mk, 5]) <= 1e-4 + b[:, 2])
+        assert np.all(np.abs(dacc[mk] - res.img[mk, 3]) <= 1e-4 * depth_scale + b[:, 1])
     return um
 
 
@@ -111,7 +128,7 @@ def test_city_8_cameras_mixed_resolution_fp16_sh(ctx):
     ctx.sync_check()
     sa = pu.state_arrays(st)
     tiles = _sample_tiles(sa, cams, 6, 2, seed=5)
-    res = oracle.render(deq, cams, oopts, tile_subset=tiles)
+    res = oracle.render(deq, cams, oopts, tile_subset=tiles, want_bound=True)
     _check_records(sa, deq, cams, oopts, res.gmark)
     pix, tile_of = _tile_pixels(tiles, cams, with_tile=True)
     um = _check_images(out, res, pix, depth_scale=400.0)
@@ -150,12 +167,13 @@ def test_large_street_level_4k_fp16_sh_recompute(ctx):
                      + (np.nonzero(nc > 0)[0] % cam.width) // 16)
     tiles = np.unique(np.concatenate([rng.choice(busy, 32, replace=False),
                                       rng.choice(tiles_x * ((cam.height + 15) // 16), 8, replace=False)]))
-    res = oracle.render(deq, [cam], oopts, tile_subset=tiles, want_pairs=False)
+    res = oracle.render(deq, [cam], oopts, tile_subset=tiles, want_pairs=False, want_bound=True)
     pix = _tile_pixels(tiles, [cam])
-    # Looking down a street, more decisions sit within FP32 reach: facades that face the camera
-    # put many contributors at nearly equal depth (order near-ties) and saturated pixels end with
-    # T close to 1e-4 after hundreds of contributors; those pixels are marked and not compared.
-    um = _check_images(out, res, pix, depth_scale=100.0, min_unmarked=0.5)
+    # Looking down a street, many decisions sit within FP32 reach: facades that face the camera put
+    # contributors at nearly equal depth (about 200 contributors per pixel), so the depth order of
+    # a pixel's front layers is often not fixed by FP32; those pixels are compared within the
+    # oracle's bound on what the order can change.
+    um = _check_images(out, res, pix, depth_scale=100.0)
     # no pair lists are kept in recompute mode: n_contrib may differ by near-tie positions
     assert np.abs(nc[um] - res.img[um, 7].astype(np.int64)).max() <= 2
     up = pu.upstream_on(um, npix, seed=8, alpha=res.img[:, 5])

@@ -570,3 +570,25 @@ def test_appearance_transform_gradients_match_finite_differences(aa, cams):
                 an = g[name].reshape(sc.n, -1)[gi, j]
                 scale = np.sqrt(np.mean(g[name] ** 2)) + 1e-12
                 assert abs(fd - an) <= 1e-5 * (abs(an) + scale) + 1e-8, (name, gi, j, fd, an)
+
+
+def test_flip_bound_covers_the_other_order_of_a_depth_tie():
+    """Two overlapping Gaussians at the same depth (a tie, broken by index) with different
+    colours: the render with their indices swapped takes the other order. The image difference
+    is nonzero, every pixel where it is nonzero is marked, and it stays within the oracle's
+    per-pixel bound (the bound the GPU comparison of marked pixels uses); unmarked pixels have a
+    zero bound."""
+    sc = make_scene([[0.0, 0.0, 5.0], [0.02, 0.01, 5.0]], [0.3, 0.25], opac=[0.7, 0.6],
+                    dc=[[0.9, 0.1, 0.4], [0.1, 0.8, 0.2]])
+    r1 = oracle.render(sc, [CAM64], want_bound=True)
+    r2 = oracle.render(sc.subset(np.array([1, 0])), [CAM64], want_bound=True)
+    d_rgb = np.abs(r1.img[:, 0:3] - r2.img[:, 0:3]).max(axis=1)
+    d_dep = np.abs(r1.img[:, 3] - r2.img[:, 3])
+    d_alp = np.abs(r1.img[:, 5] - r2.img[:, 5])
+    assert d_rgb.max() > 1e-3
+    changed = d_rgb > 1e-12
+    assert np.all(r1.mark[changed] & (oracle.MARK_TIE | oracle.MARK_SOFT))
+    assert np.all(d_rgb <= r1.bound[:, 0] * (1 + 1e-9) + 1e-12)
+    assert np.all(d_dep <= r1.bound[:, 1] * (1 + 1e-9) + 1e-12)
+    assert np.all(d_alp <= r1.bound[:, 2] + 1e-12)
+    assert np.all(r1.bound[r1.mark == 0] == 0.0)
