@@ -724,6 +724,31 @@ def run_ours(args, rank, world, local_rank):
                     rgb_mean_abs_vs_fp32=float((out16["rgb"] - outs["rgb"]).abs().mean()),
                     bytes_per_gaussian=int(12 + 2 * (3 + 4 + 1) + 2 * 48))
 
+    # the same step with the pairs ordered by global onesweep radix sorts instead of per-tile sorts
+    # (same results): step time and binning stage times of both
+    binning = None
+    if not args.no_configs:
+        binning = {}
+        bstages = ["tile_count", "tile_scan", "readback", "place", "tile_sort", "depth_sort", "ranges"]
+        for name, glob in (("per_tile_sort", False), ("global_onesweep", True)):
+            o2 = native.Options(tile_cull=bool(args.tile_cull), save_state=True, global_sort=glob)
+
+            def step_b():
+                native.zero_param_grads(ctx, g, grads)
+                _, stb = native.render_forward(ctx, g, [cam], o2, outputs=outs)
+                native.render_backward(ctx, g, [cam], stb, d_out, o2, grads=grads)
+
+            ms_b = _events_ms(step_b, max(3, min(args.steps, 10)), stream)
+            ctx.profile(True, False)
+            ctx.profile_collect()
+            for _ in range(5):
+                step_b()
+            torch.cuda.synchronize()
+            pr = ctx.profile_collect()
+            ctx.profile(False, False)
+            binning[name] = dict(ms_per_step=round(ms_b, 4),
+                                 stage_us={k: round(pr["ms"][k] / 5 * 1e3, 1) for k in bstages if pr["ms"][k] > 0})
+
     mlp_leg = None if args.no_mlp else run_mlp_leg(args, ctx, g, cam, opts, d_out, outs, stream, dev, rank)
 
     # end to end through the same API: Gaussians from pinned host memory in, gradients out
@@ -787,7 +812,7 @@ def run_ours(args, rank, world, local_rank):
                 stages_ms=stage_ms, visible=V, pairs=P, max_tile_pairs=info.get("max_tile_pairs"), counters=counts,
                 roofline=roof, stage_roofline=stage_roof, step_roofline=step_roof,
                 cpu_baseline=cpu, e2e=e2e, clocks=clocks, fp16_storage=fp16, appearance_mlp=mlp_leg, serve=serve_stats,
-                configs=configs)
+                configs=configs, binning=binning)
     if serve_full is not None:
         line["serve_full"] = serve_full
     line["gpu_launches"] = int(args.steps * kernels_per_step(args.tile_cull, info))

@@ -125,6 +125,11 @@ typedef struct gsr_opts {
   float bg[3];          /* background colour blended with the final transmittance */
   int32_t save_state;   /* 1: keep sorted pairs for backward; 0: backward recomputes them */
   int32_t absgrad;      /* 1: backward also accumulates sum |dL/dmean2d| per axis (AbsGS) */
+  int32_t global_sort;  /* how the (tile, Gaussian) pairs are put in (tile, depth, index) order:
+                           0 (default): counted per tile, placed in each tile's range and sorted per
+                           tile in shared memory; 1: the visible records sorted by depth and the
+                           pairs sorted stably by tile with the onesweep radix sort. Same order,
+                           same results; only the timing differs. */
 } gsr_opts;
 
 /* Forward outputs, device float32, cameras packed one after another (camera c starts at pixel
@@ -258,6 +263,15 @@ gsr_status gsr_state_copy(const gsr_fwd_state* state, int32_t which, void* dst, 
  * forward began (GSR_ERR_DEVICE_TIMEOUT), then clears it. */
 gsr_status gsr_sync_check(gsr_ctx* ctx, gsr_stream stream);
 
+/* Pace of the gradient zero fill (no counterpart in the paper). The fill of the parameter-gradient
+ * arrays (gsr_param_grads_zero, or the backward's own) runs on the context's side stream beside the
+ * forward's binning and blends and the backward's blend; at full speed it takes most of the memory
+ * bandwidth from the latency-bound stages it overlaps. gb_per_s > 0 spreads it out at about that
+ * rate (each fill block starts a 16 KB chunk only when it is due on the GPU's nanosecond timer);
+ * 0 writes as fast as possible. blocks > 0 sets how many blocks fill (0 keeps the current number).
+ * Results are the same either way; only the timing changes. Errors: GSR_ERR_INVALID_ARG. */
+gsr_status gsr_set_fill_rate(gsr_ctx* ctx, float gb_per_s, int32_t blocks);
+
 /* Failure detection (no counterpart in the paper). Every device wait of this context's kernels
  * (the decoupled look-backs of the chained scans and of the sort) gives up after `polls` polls
  * (0: the default, 2^20, well under a second), sets the context's error word and lets the kernel
@@ -283,18 +297,24 @@ gsr_status gsr_appearance_cache(gsr_ctx* ctx, const gsr_gaussians* g, int32_t im
 /* Stages timed with CUDA events on the call's stream while profiling is on. */
 typedef enum gsr_stage {
   GSR_STAGE_PREPROCESS = 0,     /* projection, colour, cull, compaction */
-  GSR_STAGE_TILE_COUNT = 1,     /* (tile, record) pairs counted per tile (with tile culling) */
-  GSR_STAGE_TILE_SCAN = 2,      /* scan of the tile counts: each tile's range of pairs, P */
+  GSR_STAGE_TILE_COUNT = 1,     /* (tile, record) pairs counted per tile (global_sort: per record,
+                                   with tile culling only) */
+  GSR_STAGE_TILE_SCAN = 2,      /* scan of the tile counts: each tile's range of pairs, P (global_sort:
+                                   of the records' counts in depth order: their pair offsets, P) */
   GSR_STAGE_READBACK = 3,       /* the forward's one device-to-host read of V and P */
-  GSR_STAGE_PLACE = 4,          /* pairs written into their tiles' ranges */
-  GSR_STAGE_TILE_SORT = 5,      /* every tile's pairs sorted by (depth, index) */
+  GSR_STAGE_PLACE = 4,          /* pairs written into their tiles' ranges (global_sort: at their
+                                   records' offsets, keyed by tile) */
+  GSR_STAGE_TILE_SORT = 5,      /* every tile's pairs sorted by (depth, index) (global_sort: the
+                                   pairs sorted stably by tile) */
   GSR_STAGE_BLEND_FWD = 6,      /* forward compositing */
   GSR_STAGE_BLEND_BWD = 7,      /* backward compositing */
   GSR_STAGE_PREPROCESS_BWD = 8, /* projection and colour backward */
   GSR_STAGE_BETWEEN = 9,        /* idle time between consecutive stages of one call (memsets,
                                    waits on the host or the side stream, launch latency) */
   GSR_STAGE_APPEARANCE_BWD = 10,/* appearance-transform backward (only with gsr_gaussians.mlp) */
-  GSR_NUM_STAGES = 11
+  GSR_STAGE_DEPTH_SORT = 11,    /* global_sort: radix sort of the visible records by depth */
+  GSR_STAGE_RANGES = 12,        /* global_sort: each tile's range in the sorted pairs */
+  GSR_NUM_STAGES = 13
 } gsr_stage;
 
 /* Counters gathered while profiling with count_evals = 1. */
@@ -303,7 +323,9 @@ typedef enum gsr_counter {
   GSR_CNT_FWD_CONTRIBS = 1,  /* of which blended (alpha >= 1/255, before termination) */
   GSR_CNT_BWD_EVALS = 2,     /* (pixel, Gaussian) positions visited by the backward blend */
   GSR_CNT_BWD_CONTRIBS = 3,  /* of which contributors */
-  GSR_NUM_COUNTERS = 4
+  GSR_CNT_BWD_WARP_ITERS = 4,          /* (warp, Gaussian) iterations the backward blend evaluates */
+  GSR_CNT_BWD_WARP_ITERS_CONTRIB = 5,  /* of which at least one pixel of the warp takes the Gaussian */
+  GSR_NUM_COUNTERS = 6
 } gsr_counter;
 
 /* on = 1 records CUDA events around every stage of later calls; count_evals = 1 also counts

@@ -39,11 +39,12 @@ struct gsr_ctx {
   Buf sort_ktmp, sort_vtmp, sort_hist, sort_status;  // gsr_sort_pairs_u32
   Buf pre_status, scan_status, misc, tile_ctr, big_tiles;
   Buf pair_keys, key_scratch, pvals_s, ranges;  // pairs (pvals_s, ranges: no-state mode)
+  Buf dkeys, dvals, touched, dkeys_s, dvals_s, offsets, cnt_sorted, pkeys, pvals, pkeys_s;  // global sort
   Buf pix_T, pix_n, pix_D;                     // per-pixel state (no-state mode)
   Buf g2d, gaff;
   // host pinned staging of the binning counters (misc, 32 bytes) and the error word
   void* pinned = nullptr;
-  int* d_err = nullptr;  // 64 bytes: error word at 0, blend counters (4 x u64) at byte 8
+  int* d_err = nullptr;  // 64 bytes: error word at 0, blend counters (GSR_NUM_COUNTERS x u64) at byte 8
   // profiling
   bool prof = false;
   bool count_evals = false;
@@ -66,7 +67,8 @@ struct gsr_ctx {
   bool prezero_requested = false;  // recorded, the fill not queued yet
   bool prezero_pending = false;    // fill queued (ev_prezero marks its end), not used yet
   int grid_cap = 304;  // resident blocks of the looping scan / sort kernels (2 per SM)
-  int fill_blocks = 76;  // blocks of the gradient zero fill (one per two SMs)
+  int fill_blocks = 76;  // blocks of the gradient zero fill
+  float fill_gbs = 0.f;  // pace of the gradient zero fill in GB/s (0: unpaced); gsr_set_fill_rate
   bool pre_dense = false;  // the last binning kept over a quarter of its (camera, Gaussian) pairs
   WaitCfg wait;  // how the look-backs of this context's kernels wait (gsr_set_wait_limit)
   // default allocator: a context-owned stream-ordered pool (growth and release never
@@ -335,7 +337,7 @@ cudaError_t enqueue_fill(gsr_ctx* ctx, const FillSpans& f, cudaStream_t s, cudaE
   cudaError_t e = cudaEventRecord(ctx->ev_fork, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
   if (e == cudaSuccess) {
-    launch_zero_fill(f, ctx->fill_blocks, ctx->side);
+    launch_zero_fill(f, ctx->fill_blocks, ctx->fill_gbs, ctx->side);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaEventRecord(done, ctx->side);
@@ -421,30 +423,28 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
 
   const int pre_blocks = static_cast<int>((N + kPreTile - 1) / kPreTile);
   const int tiles = cb.total_tiles;
+  const bool global = o->global_sort != 0;
   GSR_TRY_ALLOC(*bo.rec, sizeof(Rec) * capv);
   GSR_TRY_ALLOC(*bo.owner, sizeof(uint32_t) * capv);
   GSR_TRY_ALLOC(*bo.ranges, sizeof(uint2) * std::max(tiles, 1));
-  GSR_TRY_ALLOC(ctx->tile_ctr, sizeof(uint32_t) * std::max(tiles, 1));
-  GSR_TRY_ALLOC(ctx->big_tiles, sizeof(uint32_t) * std::max(tiles, 1));
   if (!ensure_zeroed(ctx, ctx->pre_status, sizeof(unsigned long long) * std::max(pre_blocks, 1), s))
     return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
-  const long long scan_blocks = (tiles + kScanThreads * kScanItems - 1) / (kScanThreads * kScanItems);
+  const long long scan_items = global ? capv : tiles;
+  const long long scan_blocks = (scan_items + kScanThreads * kScanItems - 1) / (kScanThreads * kScanItems);
   if (!ensure_zeroed(ctx, ctx->scan_status, sizeof(unsigned long long) * (scan_blocks + 1), s))
     return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
-  // misc (32-bit words): [0] preprocess block counter, [1] V, [2] tile-scan block counter,
+  // misc (32-bit words): [0] preprocess block counter, [1] V, [2] scan block counter,
   // [3] largest tile's pair count, [4..5] P (64-bit), [6] tiles listed for the large-list sort
   GSR_TRY_ALLOC(ctx->misc, 64);
   uint32_t* misc = as<uint32_t>(ctx->misc);
   uint32_t* d_V = misc + 1;
   unsigned long long* d_P = reinterpret_cast<unsigned long long*>(misc + 4);
-  uint32_t* tile_ctr = as<uint32_t>(ctx->tile_ctr);
   // The error word is not cleared here: a pair-placement overflow of the previous launch (which
   // runs after that launch's read-back) is reported by this one's, then the word is cleared.
   cudaError_t e = cudaMemsetAsync(ctx->misc.p, 0, 64, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(tile_ctr, 0, sizeof(uint32_t) * tiles, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
 
-  PreOut po;
+  PreOut po{};
   po.rec = as<Rec>(*bo.rec);
   po.owner = as<uint32_t>(*bo.owner);
   po.status = as<unsigned long long>(ctx->pre_status);
@@ -453,6 +453,30 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   po.err = ctx->d_err;
   po.epoch = next_epoch(ctx, s);
   po.wait = ctx->wait;
+  uint32_t* tile_ctr = nullptr;
+  SortScratch sc{};
+  if (global) {
+    // depth keys of the records, sorted by the onesweep radix sort (the preprocess counts their digits)
+    GSR_TRY_ALLOC(ctx->dkeys, sizeof(uint32_t) * capv);
+    GSR_TRY_ALLOC(ctx->dvals, sizeof(uint32_t) * capv);
+    GSR_TRY_ALLOC(ctx->touched, sizeof(uint32_t) * capv);
+    GSR_TRY_ALLOC(ctx->dkeys_s, sizeof(uint32_t) * capv);
+    GSR_TRY_ALLOC(ctx->dvals_s, sizeof(uint32_t) * capv);
+    GSR_TRY_ALLOC(ctx->offsets, sizeof(uint32_t) * capv);
+    if (!ensure_sort(ctx, capv, s)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
+    sc = sort_scratch(ctx);
+    sort_clear_counts(sc, s);
+    po.depth_keys = as<uint32_t>(ctx->dkeys);
+    po.depth_vals = as<uint32_t>(ctx->dvals);
+    po.touched = as<uint32_t>(ctx->touched);
+    po.key_counts = sc.hist;
+  } else {
+    GSR_TRY_ALLOC(ctx->tile_ctr, sizeof(uint32_t) * std::max(tiles, 1));
+    GSR_TRY_ALLOC(ctx->big_tiles, sizeof(uint32_t) * std::max(tiles, 1));
+    tile_ctr = as<uint32_t>(ctx->tile_ctr);
+    e = cudaMemsetAsync(tile_ctr, 0, sizeof(uint32_t) * tiles, s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
+  }
   {
     StageTimer tm(ctx, GSR_STAGE_PREPROCESS, s);
     launch_preprocess_fwd(ga, cb, o->eps2d, o->antialiased, po, pre_blocks, ctx->pre_dense, s);
@@ -462,13 +486,32 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   e = start_prezero(ctx, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
 
-  // pairs per tile, then each tile's range and the total P
-  if (N * C > 0) {
-    StageTimer tm(ctx, GSR_STAGE_TILE_COUNT, s);
-    launch_bin_pairs(as<Rec>(*bo.rec), d_V, capv, cb, o->tile_cull, tile_ctr, nullptr, nullptr, ctx->d_err,
-                     4 * ctx->grid_cap, s);
-  }
-  {
+  if (global) {
+    // records by depth, then (tile-culled) counts and pair offsets in depth order
+    if (N * C > 0) {
+      StageTimer tm(ctx, GSR_STAGE_DEPTH_SORT, s);
+      radix_sort_u32(as<uint32_t>(ctx->dkeys), as<uint32_t>(ctx->dvals), as<uint32_t>(ctx->dkeys_s),
+                     as<uint32_t>(ctx->dvals_s), d_V, capv, 0, 32, sc, next_epoch(ctx, s), false, true, ctx->d_err, s);
+    }
+    const uint32_t* cnt_sorted = nullptr;
+    if (o->tile_cull && N * C > 0) {
+      GSR_TRY_ALLOC(ctx->cnt_sorted, sizeof(uint32_t) * capv);
+      StageTimer tm(ctx, GSR_STAGE_TILE_COUNT, s);
+      launch_duplicate(as<Rec>(*bo.rec), as<uint32_t>(ctx->dvals_s), nullptr, d_V, capv, cb, 1,
+                       as<uint32_t>(ctx->cnt_sorted), nullptr, nullptr, nullptr, 0, 4 * ctx->grid_cap, s);
+      cnt_sorted = as<uint32_t>(ctx->cnt_sorted);
+    }
+    StageTimer tm(ctx, GSR_STAGE_TILE_SCAN, s);
+    pair_offsets_scan(as<uint32_t>(ctx->touched), as<uint32_t>(ctx->dvals_s), cnt_sorted, as<uint32_t>(ctx->offsets),
+                      d_V, capv, as<unsigned long long>(ctx->scan_status), misc + 2, d_P, ctx->d_err,
+                      next_epoch(ctx, s), ctx->grid_cap, ctx->wait, s);
+  } else {
+    // pairs per tile, then each tile's range and the total P
+    if (N * C > 0) {
+      StageTimer tm(ctx, GSR_STAGE_TILE_COUNT, s);
+      launch_bin_pairs(as<Rec>(*bo.rec), d_V, capv, cb, o->tile_cull, tile_ctr, nullptr, nullptr, ctx->d_err,
+                       4 * ctx->grid_cap, s);
+    }
     StageTimer tm(ctx, GSR_STAGE_TILE_SCAN, s);
     launch_tile_scan(tile_ctr, as<uint2>(*bo.ranges), tiles, as<unsigned long long>(ctx->scan_status), misc + 2, d_P,
                      misc + 3, as<uint32_t>(ctx->big_tiles), misc + 6, next_epoch(ctx, s), ctx->d_err, ctx->wait,
@@ -506,16 +549,46 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   // the next preprocess picks its variant from this launch's survivor ratio
   ctx->pre_dense = 4 * V > N * C;
 
-  // place the pairs in their tiles' ranges, then order every tile's list by (depth, index)
   const long long Pc = std::max<long long>(P, 1);
-  GSR_TRY_ALLOC(ctx->pair_keys, sizeof(unsigned long long) * Pc);
   GSR_TRY_ALLOC(*bo.pvals_s, sizeof(uint32_t) * Pc);
-  unsigned long long* scratch = nullptr;
-  if (max_count > static_cast<uint32_t>(kTileSortCap)) {
-    GSR_TRY_ALLOC(ctx->key_scratch, sizeof(unsigned long long) * Pc);
-    scratch = as<unsigned long long>(ctx->key_scratch);
-  }
-  if (P > 0) {
+  if (global) {
+    // pairs keyed by tile in depth order, sorted stably by tile, ranges by binary search
+    GSR_TRY_ALLOC(ctx->pkeys, sizeof(uint32_t) * Pc);
+    GSR_TRY_ALLOC(ctx->pvals, sizeof(uint32_t) * Pc);
+    GSR_TRY_ALLOC(ctx->pkeys_s, sizeof(uint32_t) * Pc);
+    if (P > 0) {
+      if (!ensure_sort(ctx, Pc, s)) return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
+      sc = sort_scratch(ctx);
+      int tb = 1;
+      while ((1ll << tb) < tiles) ++tb;
+      sort_clear_counts(sc, s);  // the pair emitter counts the tile keys' digits
+      {
+        StageTimer tm(ctx, GSR_STAGE_PLACE, s);
+        launch_duplicate(as<Rec>(*bo.rec), as<uint32_t>(ctx->dvals_s), as<uint32_t>(ctx->offsets), d_V, V, cb,
+                         o->tile_cull, nullptr, as<uint32_t>(ctx->pkeys), as<uint32_t>(ctx->pvals), sc.hist, tb,
+                         4 * ctx->grid_cap, s);
+      }
+      {
+        StageTimer tm(ctx, GSR_STAGE_TILE_SORT, s);
+        radix_sort_u32(as<uint32_t>(ctx->pkeys), as<uint32_t>(ctx->pvals), as<uint32_t>(ctx->pkeys_s),
+                       as<uint32_t>(*bo.pvals_s), nullptr, P, 0, tb, sc, next_epoch(ctx, s), false, true, ctx->d_err, s);
+      }
+    }
+    StageTimer tm(ctx, GSR_STAGE_RANGES, s);
+    if (P > 0) {
+      launch_ranges(as<uint32_t>(ctx->pkeys_s), P, tiles, as<uint2>(*bo.ranges), s);
+    } else {
+      e = cudaMemsetAsync(bo.ranges->p, 0, sizeof(uint2) * std::max(tiles, 1), s);
+      if (e != cudaSuccess) return cuda_err(ctx, e, "memset ranges");
+    }
+  } else if (P > 0) {
+    // place the pairs in their tiles' ranges, then order every tile's list by (depth, index)
+    GSR_TRY_ALLOC(ctx->pair_keys, sizeof(unsigned long long) * Pc);
+    unsigned long long* scratch = nullptr;
+    if (max_count > static_cast<uint32_t>(kTileSortCap)) {
+      GSR_TRY_ALLOC(ctx->key_scratch, sizeof(unsigned long long) * Pc);
+      scratch = as<unsigned long long>(ctx->key_scratch);
+    }
     {
       StageTimer tm(ctx, GSR_STAGE_PLACE, s);
       launch_bin_pairs(as<Rec>(*bo.rec), d_V, V, cb, o->tile_cull, tile_ctr, as<uint2>(*bo.ranges),
@@ -615,7 +688,8 @@ void gsr_destroy(gsr_ctx* ctx) {
   Buf* all[] = {&ctx->seg_begin, &ctx->seg_start, &ctx->seg_cams, &ctx->rec, &ctx->owner, &ctx->sort_ktmp,
                 &ctx->sort_vtmp, &ctx->sort_hist, &ctx->sort_status, &ctx->pre_status, &ctx->scan_status, &ctx->misc,
                 &ctx->tile_ctr, &ctx->big_tiles, &ctx->pair_keys, &ctx->key_scratch, &ctx->pvals_s, &ctx->ranges, &ctx->pix_T,
-                &ctx->pix_n, &ctx->pix_D, &ctx->g2d, &ctx->gaff};
+                &ctx->pix_n, &ctx->pix_D, &ctx->g2d, &ctx->gaff, &ctx->dkeys, &ctx->dvals, &ctx->touched,
+                &ctx->dkeys_s, &ctx->dvals_s, &ctx->offsets, &ctx->cnt_sorted, &ctx->pkeys, &ctx->pvals, &ctx->pkeys_s};
   for (Buf* b : all) release(ctx, *b, nullptr);
   for (auto& r : ctx->prof_recs) {
     cudaEventDestroy(r.a);
@@ -981,6 +1055,13 @@ gsr_status gsr_sync_check(gsr_ctx* ctx, gsr_stream stream) {
   return GSR_OK;
 }
 
+gsr_status gsr_set_fill_rate(gsr_ctx* ctx, float gb_per_s, int32_t blocks) {
+  if (!ctx || !(gb_per_s >= 0.f) || blocks < 0) return GSR_ERR_INVALID_ARG;
+  ctx->fill_gbs = gb_per_s;
+  if (blocks > 0) ctx->fill_blocks = blocks;
+  return GSR_OK;
+}
+
 gsr_status gsr_set_wait_limit(gsr_ctx* ctx, uint32_t polls, int32_t never_ready) {
   if (!ctx) return GSR_ERR_INVALID_ARG;
   ctx->wait.limit = polls ? polls : kSpinLimit;
@@ -1027,7 +1108,7 @@ gsr_status gsr_profile_collect(gsr_ctx* ctx, double* ms, int64_t* launches, int6
     ctx->ev_pool.push_back(r.b);
   }
   ctx->prof_recs.clear();
-  unsigned long long h[4] = {0, 0, 0, 0};
+  unsigned long long h[GSR_NUM_COUNTERS] = {};
   e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(h, reinterpret_cast<char*>(ctx->d_err) + 8, sizeof(h), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemset(reinterpret_cast<char*>(ctx->d_err) + 8, 0, sizeof(h));

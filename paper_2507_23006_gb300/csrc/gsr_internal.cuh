@@ -144,6 +144,12 @@ constexpr int kMlpParams = kMlpB2 + kMlpOut;    // 1700
 struct PreOut {
   Rec* rec;                    // [cap_v]
   uint32_t* owner;             // [cap_v] rendered index of the Gaussian of each record
+  // the global-sort binning only (null otherwise): depth keys and record indices for the depth
+  // sort, tiles in each record's rectangle, and the keys' digit counts [4][256] (added to)
+  uint32_t* depth_keys;
+  uint32_t* depth_vals;
+  uint32_t* touched;
+  uint32_t* key_counts;
   unsigned long long* status;  // [blocks] chained-scan status words (epoch-tagged)
   uint32_t* counter;           // dynamic block index
   uint32_t* v_total;           // out: V
@@ -182,8 +188,8 @@ struct FillSpans {
   size_t len[kFillSpans];  // floats
   int count;
 };
-// Sets `count` float arrays to zero with `blocks` blocks of 128 threads.
-void launch_zero_fill(const FillSpans& f, int blocks, cudaStream_t s);
+// Sets `count` float arrays to zero with `blocks` blocks, at about gb_per_s (0: unpaced).
+void launch_zero_fill(const FillSpans& f, int blocks, float gb_per_s, cudaStream_t s);
 // Backward of the appearance transform, one thread per visible record (before
 // launch_preprocess_bwd): turns the record's gradients of the transformed opacity and colour into
 // those of the untransformed ones (in place in g2d), adds l_G's gradient to g_gemb (atomics; rows
@@ -266,6 +272,21 @@ void launch_tile_scan(uint32_t* tile_ctr, uint2* ranges, int n_tiles, unsigned l
 void launch_tile_sort(unsigned long long* keys, const uint2* ranges, int n_tiles, uint32_t* vals,
                       unsigned long long* scratch, uint32_t max_count, const uint32_t* big, const uint32_t* n_big,
                       int grid_cap, cudaStream_t s);
+
+// The global-sort binning (gsr_opts.global_sort). pair_offsets_scan: exclusive scan of per-record
+// tile counts in depth order (counts[i] = touched[order[i]], or cnt_sorted[i] when given) into
+// offsets, *p_total = P, n from *d_n. launch_duplicate: with cnt_sorted, the tile-culled count of
+// each record in depth order; else the (tile id, record) pairs at the records' offsets (counting
+// the tile keys' digits for their sort). launch_ranges: each tile's [start, end) in the sorted keys.
+void pair_offsets_scan(const uint32_t* touched, const uint32_t* order, const uint32_t* cnt_sorted,
+                       uint32_t* offsets, const uint32_t* d_n, long long max_n, unsigned long long* status,
+                       uint32_t* counter, unsigned long long* p_total, int* err, uint32_t epoch, int grid_cap,
+                       WaitCfg wait, cudaStream_t s);
+void launch_duplicate(const Rec* rec, const uint32_t* order, const uint32_t* offsets, const uint32_t* d_n,
+                      long long max_n, const CamBatch& cams, int tile_cull, uint32_t* cnt_sorted,
+                      uint32_t* pair_keys, uint32_t* pair_vals, uint32_t* key_counts, int key_bits, int max_blocks,
+                      cudaStream_t s);
+void launch_ranges(const uint32_t* sorted_keys, long long P, int n_tiles, uint2* ranges, cudaStream_t s);
 
 struct BlendFwdOut {
   float* rgb;

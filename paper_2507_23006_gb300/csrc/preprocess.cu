@@ -13,6 +13,7 @@
 // camera) order, with the block offsets from a single-pass chained scan (Merrill & Garland
 // decoupled look-back) whose waits are bounded; within one camera the compacted index grows
 // with the Gaussian index, which gives the depth sort its tie-break.
+#include <algorithm>
 #include <atomic>
 
 #include "preprocess_fwd.cuh"
@@ -431,12 +432,27 @@ void launch_preprocess_fwd(const GaussArgs& g, const CamBatch& cams, float eps2d
 #undef GSR_PRE
 }
 
-// Zero fill of up to kFillSpans float arrays in one launch: a grid-stride loop of 16-byte
-// stores over each array's aligned body, scalar stores for the (under 16-byte) ends.
-__global__ void __launch_bounds__(128) zero_fill_kernel(FillSpans f) {
-  const size_t tid = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const size_t nthr = static_cast<size_t>(gridDim.x) * blockDim.x;
+// Zero fill of up to kFillSpans float arrays in one launch: each block writes 16 KB chunks (16-byte
+// stores over each array's aligned body, scalar stores for the under-16-byte ends), the chunks
+// dealt out to the blocks in turn. With ns_per_chunk > 0 a block starts its k-th chunk no earlier
+// than k ns_per_chunk after it started (read on the GPU's nanosecond timer): the fill then runs at
+// a set rate beside the kernels of the main stream instead of taking the memory bandwidth from
+// them in one burst. Every wait is bounded, so a timer that stalls only speeds the fill up.
+constexpr int kFillThreads = 256;
+constexpr int kFillChunk = kFillThreads * 4;  // float4 per chunk (16 KB)
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__global__ void __launch_bounds__(kFillThreads) zero_fill_kernel(FillSpans f, unsigned ns_per_chunk) {
   const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  __shared__ unsigned long long s_t0;
+  if (threadIdx.x == 0) s_t0 = global_ns();
+  __syncthreads();
+  unsigned long long k_done = 0;  // chunks this block has written
   for (int k = 0; k < f.count; ++k) {
     float* p = f.ptr[k];
     const size_t n = f.len[k];
@@ -444,16 +460,39 @@ __global__ void __launch_bounds__(128) zero_fill_kernel(FillSpans f) {
     const size_t head = mis ? (4u - mis < n ? 4u - mis : n) : 0u;
     const size_t n4 = (n - head) >> 2;
     float4* body = reinterpret_cast<float4*>(p + head);
-    for (size_t i = tid; i < n4; i += nthr) body[i] = z;
-    const size_t done = head + 4 * n4;
-    if (tid < head) p[tid] = 0.f;
-    if (tid < n - done) p[done + tid] = 0.f;
+    const size_t chunks = (n4 + kFillChunk - 1) / kFillChunk;
+    for (size_t c = blockIdx.x; c < chunks; c += gridDim.x, ++k_done) {
+      if (ns_per_chunk) {
+        if (threadIdx.x == 0) {
+          const unsigned long long due = s_t0 + k_done * ns_per_chunk;
+          for (int w = 0; w < 100000; ++w) {  // bounded: at most 100000 short sleeps
+            const unsigned long long now = global_ns();
+            if (now >= due) break;
+            __nanosleep(static_cast<unsigned>(min(due - now, 4096ull)));
+          }
+        }
+        __syncthreads();
+      }
+      const size_t i0 = c * kFillChunk;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const size_t i = i0 + e * kFillThreads + threadIdx.x;
+        if (i < n4) body[i] = z;
+      }
+    }
+    if (blockIdx.x == 0) {
+      const size_t done = head + 4 * n4;
+      if (threadIdx.x < head) p[threadIdx.x] = 0.f;
+      if (threadIdx.x < n - done) p[done + threadIdx.x] = 0.f;
+    }
   }
 }
 
-void launch_zero_fill(const FillSpans& f, int blocks, cudaStream_t s) {
+void launch_zero_fill(const FillSpans& f, int blocks, float gb_per_s, cudaStream_t s) {
   if (f.count <= 0 || blocks <= 0) return;
-  zero_fill_kernel<<<blocks, 128, 0, s>>>(f);
+  // a block's chunk every (chunk bytes x blocks / rate) ns
+  const double ns = gb_per_s > 0.f ? (16.0 * kFillChunk) * blocks / gb_per_s : 0.0;
+  zero_fill_kernel<<<blocks, kFillThreads, 0, s>>>(f, static_cast<unsigned>(std::min(ns, 1e9)));
 }
 
 void launch_mlp_cache(const GaussArgs& A, long long n, float* out, int blocks, cudaStream_t s) {

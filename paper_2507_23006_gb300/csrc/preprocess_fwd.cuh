@@ -350,6 +350,12 @@ __device__ __forceinline__ Rec record_geometry(const Proj& P, int c, float eps) 
 __device__ __forceinline__ void write_record(const PreOut& out, long long v, const Rec& rr, long long i) {
   out.rec[v] = rr;
   out.owner[v] = static_cast<uint32_t>(i);
+  if (out.depth_keys) {  // the global-sort binning's inputs
+    const uint32_t lo = __float_as_uint(rr.c.z), hi = __float_as_uint(rr.c.w);
+    out.depth_keys[v] = __float_as_uint(rr.a.w);
+    out.depth_vals[v] = static_cast<uint32_t>(v);
+    out.touched[v] = (((lo >> 16) & 0xffffu) - (lo & 0xffffu)) * (((hi >> 16) & 0x7ffu) - (hi & 0xffffu));
+  }
 }
 
 // Appearance transform (Sec. 3.5.1) weights in shared memory: the Gaussian-embedding part of w1,
@@ -504,6 +510,7 @@ __global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_fwd_kernel
   __shared__ float4 s_rec[kPreStage][4];
   __shared__ uint32_t s_meta[kPreStage];  // slot | camera << 16
   __shared__ MlpSmem s_mlp;                // appearance transform, when on
+  __shared__ uint32_t s_digits[4 * 256];   // digit counts of the block's depth keys (global sort)
   if (threadIdx.x == 0) {
     s_bid = atomicAdd(out.counter, 1u);
     s_count[0] = 0;
@@ -511,6 +518,8 @@ __global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_fwd_kernel
   }
   if (kMlp && !A.mlp_cached) mlp_load_smem(A, cams.C, s_mlp);  // read after the barrier that ends phase 1a
   if (threadIdx.x < kPreTile / 32) s_unstaged[threadIdx.x] = 0;
+  if (out.key_counts)
+    for (int k = threadIdx.x; k < 4 * 256; k += kPreThreads) s_digits[k] = 0;
   __syncthreads();
   const unsigned bid = s_bid;
   const long long base_i = static_cast<long long>(bid) * kPreTile;
@@ -637,8 +646,15 @@ __global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_fwd_kernel
     rr.c = s_rec[e][2];
     rr.d = s_rec[e][3];
     write_record(out, v, rr, base_i + slot);
+    if (out.key_counts) count_digits(__float_as_uint(rr.a.w), 0, 32, 4, s_digits);
   }
-  if (n_rec <= kPreStage) return;  // block-uniform
+  if (n_rec <= kPreStage) {  // block-uniform
+    if (out.key_counts) {
+      __syncthreads();
+      flush_digit_counts(s_digits, 4, out.key_counts);
+    }
+    return;
+  }
   // records that did not fit the stage: every record of those Gaussians is computed again
   for (uint32_t k = threadIdx.x; k < n_maybe; k += kPreThreads) {
     const uint32_t slot = s_list[k];
@@ -667,8 +683,13 @@ __global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_fwd_kernel
       rr.c.x = 2.f * mo[1] * rgb[1];
       rr.c.y = 2.f * mo[2] * rgb[2];
       write_record(out, v, rr, i);
+      if (out.key_counts) count_digits(__float_as_uint(rr.a.w), 0, 32, 4, s_digits);
       ++v;
     }
+  }
+  if (out.key_counts) {
+    __syncthreads();
+    flush_digit_counts(s_digits, 4, out.key_counts);
   }
 }
 

@@ -8,12 +8,10 @@
 //               each pixel blends front to back and stops at T < 1e-4; the CTA stops loading
 //               once every pixel is done.
 //   blend bwd:  same tiling, contributors walked back to front recovering T_i = T_{i+1}/(1-a_i);
-//               the walk queues each contribution (Gaussian, pixel, dL/dalpha, weight) per warp,
-//               and every 32 queued contributions are turned into gradients by the 32 lanes at
-//               once (a Gaussian takes only a few of a warp's 64 pixels), summed per Gaussian with
-//               a segmented shuffle sum, over the CTA in shared memory, and added to global memory
-//               once per (tile, Gaussian).
+//               per-Gaussian gradients are summed over the warp with shuffles, over the CTA in
+//               shared memory, and added to global memory once per (tile, Gaussian).
 #include <algorithm>
+#include <atomic>
 
 #include "gsr_internal.cuh"
 #include "scan_util.cuh"
@@ -332,6 +330,140 @@ __global__ void __launch_bounds__(kSortBigThreads) tile_sort_big_kernel(unsigned
   for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) sort_tile(keys, ranges[big[b]], vals, scratch, cap, s_keys);
 }
 
+// The global-sort binning (gsr_opts.global_sort): every visible record, in depth order, emits
+// its (tile, record) pairs at its offset from the pair scan, with the tile id as the key (and, in
+// count_only mode, only counts the pairs StopThePop keeps); the pairs are then sorted stably by
+// tile with the onesweep radix sort, and each tile's range found by binary search.
+template <bool kCull, bool kCount>
+__global__ void __launch_bounds__(256) duplicate_kernel(const Rec* __restrict__ rec, const uint32_t* __restrict__ order,
+                                                        const uint32_t* __restrict__ offsets, const uint32_t* d_n,
+                                                        long long max_n, CamBatch cams, uint32_t* __restrict__ cnt_sorted,
+                                                        uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals,
+                                                        uint32_t* __restrict__ key_counts, int key_bits) {
+  __shared__ uint32_t s_cnt[8][32];
+  __shared__ uint32_t s_digits[4 * 256];  // digit counts of the emitted tile keys (for their sort)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int passes = (key_bits + 7) / 8;
+  if (key_counts) {
+    for (int k = threadIdx.x; k < 4 * 256; k += blockDim.x) s_digits[k] = 0;
+    __syncthreads();
+  }
+  long long n = static_cast<long long>(*d_n);
+  if (n > max_n) n = max_n;
+  // warps stride over the records 32 at a time (the grid is sized for the resident blocks, not
+  // for the capacity, so no block starts only to find nothing to do)
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long base_i = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) & ~31ll; base_i < n;
+       base_i += stride) {
+  const long long i = base_i + lane;
+  const bool valid = i < n;
+  uint32_t v = 0, off = 0, area = 0, lo = 0, hi = 0;
+  float4 ra = make_float4(0, 0, 0, 0), rb = ra;
+  if (valid) {
+    v = order[i];
+    const Rec r = rec[v];
+    ra = r.a;
+    rb = r.b;
+    lo = __float_as_uint(r.c.z);
+    hi = __float_as_uint(r.c.w);
+    area = ((lo >> 16) - (lo & 0xffffu)) * (((hi >> 16) & 0x7ffu) - (hi & 0xffffu));
+    if (!kCount) off = offsets[i];
+  }
+  uint32_t incl = area;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  s_cnt[w][lane] = 0;
+  __syncwarp();
+  for (uint32_t r0 = 0; r0 < total; r0 += 32) {
+    const uint32_t k = r0 + lane;
+    const bool active = k < total;
+    int owner = 0;
+#pragma unroll
+    for (int b = 16; b > 0; b >>= 1) {
+      const uint32_t probe = __shfl_sync(0xffffffffu, incl, owner + b - 1);
+      if (probe <= k) owner += b;
+    }
+    owner = min(owner, 31);
+    const uint32_t o_incl = __shfl_sync(0xffffffffu, incl, owner);
+    const uint32_t o_area = __shfl_sync(0xffffffffu, area, owner);
+    const uint32_t o_lo = __shfl_sync(0xffffffffu, lo, owner);
+    const uint32_t o_hi = __shfl_sync(0xffffffffu, hi, owner);
+    const uint32_t o_v = __shfl_sync(0xffffffffu, v, owner);
+    const uint32_t o_off = __shfl_sync(0xffffffffu, off, owner);
+    const uint32_t q = k - (o_incl - o_area);
+    const uint32_t x0 = o_lo & 0xffffu, wdt = (o_lo >> 16) - x0;
+    const uint32_t y0 = o_hi & 0xffffu;
+    const int c = static_cast<int>(o_hi >> 27);
+    const uint32_t tx = active ? x0 + q % max(wdt, 1u) : 0;
+    const uint32_t ty = active ? y0 + q / max(wdt, 1u) : 0;
+    bool keep = active;
+    if (kCull) {
+      const float mx = __shfl_sync(0xffffffffu, ra.x, owner), my = __shfl_sync(0xffffffffu, ra.y, owner);
+      const float op = __shfl_sync(0xffffffffu, ra.z, owner);
+      const float ca = __shfl_sync(0xffffffffu, rb.x, owner), cb = __shfl_sync(0xffffffffu, rb.y, owner);
+      const float cc = __shfl_sync(0xffffffffu, rb.z, owner);
+      if (active) {
+        const DevCam& cam = cams.cam[c];
+        const float xlo = tx * kTile + 0.5f, xhi = fminf(static_cast<float>((tx + 1) * kTile), cam.W) - 0.5f;
+        const float ylo = ty * kTile + 0.5f, yhi = fminf(static_cast<float>((ty + 1) * kTile), cam.H) - 0.5f;
+        const float d2 = tile_min_maha(mx, my, ca, cb, cc, xlo, xhi, ylo, yhi);
+        keep = op > 0.f && __fmul_rn(0.5f, d2) <= logf(__fmul_rn(op, 255.f));
+      }
+      const uint32_t kb = __ballot_sync(0xffffffffu, keep);
+      const uint32_t group = __match_any_sync(0xffffffffu, active ? static_cast<uint32_t>(owner) : 64u);
+      const uint32_t before = __popc(kb & group & ((1u << lane) - 1));
+      const uint32_t base_cnt = s_cnt[w][owner];
+      __syncwarp();
+      if (!kCount && keep) {
+        const uint32_t pos = o_off + base_cnt + before;
+        const DevCam& cam = cams.cam[c];
+        const uint32_t key = static_cast<uint32_t>(cam.tile_off) + ty * cam.tiles_x + tx;
+        pkeys[pos] = key;
+        pvals[pos] = o_v;
+        if (key_counts) count_digits(key, 0, key_bits, passes, s_digits);
+      }
+      if (active && lane == 31 - __clz(group)) s_cnt[w][owner] = base_cnt + __popc(kb & group);
+      __syncwarp();
+    } else if (active) {
+      const DevCam& cam = cams.cam[c];
+      const uint32_t pos = o_off + q;
+      const uint32_t key = static_cast<uint32_t>(cam.tile_off) + ty * cam.tiles_x + tx;
+      pkeys[pos] = key;
+      pvals[pos] = o_v;
+      if (key_counts) count_digits(key, 0, key_bits, passes, s_digits);
+    }
+  }
+  if (kCount && valid) cnt_sorted[i] = s_cnt[w][lane];
+  __syncwarp();  // the next round clears s_cnt
+  }
+  if (key_counts) {
+    __syncthreads();
+    flush_digit_counts(s_digits, passes, key_counts);
+  }
+}
+
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__ a, uint32_t n, uint32_t key) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// One thread per tile: [first pair with key >= t, first pair with key >= t + 1) of the sorted
+// keys; every tile is written, so nothing needs clearing first.
+__global__ void ranges_kernel(const uint32_t* __restrict__ keys, uint32_t P, int n_tiles, uint2* __restrict__ ranges) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tiles) return;
+  ranges[t] = make_uint2(lower_bound_u32(keys, P, static_cast<uint32_t>(t)),
+                         lower_bound_u32(keys, P, static_cast<uint32_t>(t) + 1u));
+}
+
 template <bool kCount>
 __global__ void __launch_bounds__(kBlendThreads) blend_fwd_kernel(const Rec* __restrict__ rec,
                                                                   const uint32_t* __restrict__ pvals,
@@ -458,9 +590,54 @@ __device__ __forceinline__ float warp_sum(float x) {
 
 constexpr int kGradVals = 12;
 
-// Contributions queued per warp between the reverse walk and the gradient pass (a power of two,
-// at least 32 pending plus the 64 one Gaussian can add).
-constexpr int kQueue = 128;
+// Sums N (<= 16) per-lane values over the warp with about N + 2 shuffles instead of 5 N. Each
+// round halves the vector: a lane sends the half it gives up to its partner across `kBit` and
+// keeps the sum of the other half (an odd length is padded with a zero). Once one value is
+// left, the remaining lane bits are summed directly. index() gives the value each lane ends up
+// holding (-1: padding).
+template <int N, int kBit>
+struct TransposeSum {
+  static __device__ __forceinline__ float run(const float* v, int lane) {
+    constexpr int H = (N + 1) / 2;
+    const bool up = lane & kBit;
+    float w[H];
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const float lo = v[k];
+      const float hi = (k + H < N) ? v[k + H] : 0.f;
+      const float send = up ? lo : hi;
+      const float keep = up ? hi : lo;
+      w[k] = keep + __shfl_xor_sync(0xffffffffu, send, kBit);
+    }
+    return TransposeSum<H, kBit / 2>::run(w, lane);
+  }
+  static __device__ __forceinline__ int index(int lane) {
+    constexpr int H = (N + 1) / 2;
+    const int r = TransposeSum<H, kBit / 2>::index(lane);
+    if (r < 0) return -1;
+    if (lane & kBit) return r < N - H ? H + r : -1;  // the upper half holds N - H values
+    return r;
+  }
+};
+template <int kBit>
+struct TransposeSum<1, kBit> {
+  static __device__ __forceinline__ float run(const float* v, int) {
+    float x = v[0];
+#pragma unroll
+    for (int b = kBit; b > 0; b >>= 1) x += __shfl_xor_sync(0xffffffffu, x, b);
+    return x;
+  }
+  static __device__ __forceinline__ int index(int) { return 0; }
+};
+
+// Lane bits still summed directly after the halving rounds of an N-value transpose sum: lanes
+// that differ only in these bits hold the same total.
+template <int N>
+__host__ __device__ constexpr int transpose_shared_bits() {
+  int n = N, bit = 16;
+  while (n > 1 && bit > 0) { n = (n + 1) / 2; bit >>= 1; }
+  return 2 * bit - 1;
+}
 
 // kAbs: also accumulate |dL/dmean2D| per pixel (AbsGS densification statistics).
 template <bool kCount, bool kAbs>
@@ -477,9 +654,6 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
   __shared__ uint32_t sV[kBatch];
   __shared__ uint32_t sM[kBatch];
   __shared__ float sAcc[kBatch][kGradVals + 1];
-  __shared__ uint32_t sQk[kBlendWarps][kQueue];  // queued: batch slot | pixel << 16 | clamped << 31
-  __shared__ float2 sQv[kBlendWarps][kQueue];    // their dL/dalpha and weight alpha T
-  __shared__ float4 sPix[kBlendWarps][64];       // per pixel: dL/dC (3) after the transform, dL/dD
   __shared__ uint32_t s_max;
   __shared__ float s_aff[kBlendWarps][12];
   const int t = blockIdx.x;
@@ -488,6 +662,8 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
   const int lt = t - cam.tile_off;
   const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int t_idx = TransposeSum<kVals, 16>::index(lane);  // the gradient value this lane sums
+  const bool t_keep = t_idx >= 0 && (lane & transpose_shared_bits<kVals>()) == 0;
   const int px = tx * kTile + 8 * (wid & 1) + (tid & 7);
   const int py0 = ty * kTile + 8 * (wid >> 1) + 2 * ((tid & 31) >> 3);
   const float fx = px + 0.5f;
@@ -544,80 +720,12 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
     GTz[q] = gda * (zf + zrel) + gal - (g0[q] * (bg.x - bb0) + g1[q] * (bg.y - bb1) + g2[q] * (bg.z - bb2));
     T[q] = Tf[q];
   }
-  // the pixel constants the gradient pass reads (pixel p of a warp: lane p >> 1, row p & 1)
-#pragma unroll
-  for (int q = 0; q < 2; ++q) sPix[wid][2 * lane + q] = make_float4(GC0[q], GC1[q], GC2[q], GD[q]);
   __syncthreads();
   const int n = static_cast<int>(s_max);
-  const float tile_x = tx * kTile + 8 * (wid & 1) + 0.5f, tile_y = ty * kTile + 8 * (wid >> 1) + 0.5f;
-  const uint32_t lt_mask = (1u << lane) - 1u;
-  uint32_t q_head = 0, q_tail = 0;  // this warp's contribution queue (warp-uniform counters)
-  uint32_t n_visit = 0, n_contrib = 0;
-
-  // Gradient pass over `k` queued contributions from q_head: lane l takes contribution l, forms the
-  // per-Gaussian values of that (pixel, Gaussian) pair, the values of equal Gaussians (adjacent in
-  // the queue) are summed with a segmented shuffle sum, and the first lane of each run adds its
-  // sums to the batch's shared accumulators.
-  auto flush = [&](int k) {
-    __syncwarp();
-    const bool act = lane < k;
-    const uint32_t slot = (q_head + lane) & (kQueue - 1);
-    const uint32_t key = act ? sQk[wid][slot] : 0u;
-    const uint32_t j = key & 0xffffu;
-    const uint32_t run = act ? j : 0xffffffffu;  // run id: the batch slot, none for idle lanes
-    float gv[kGradVals];
-#pragma unroll
-    for (int m = 0; m < kGradVals; ++m) gv[m] = 0.f;
-    if (act) {
-      const float2 dv = sQv[wid][slot];  // dL/dalpha, alpha T
-      const uint32_t p = (key >> 16) & 0x3fu;
-      const float4 a = sA[j];
-      const float4 b = sB[j];
-      const float dx = a.x - (tile_x + static_cast<float>((p >> 1) & 7));
-      const float dy = a.y - (tile_y + static_cast<float>(2 * (p >> 4) + (p & 1)));
-      const float sigma = 0.5f * (b.x * dx * dx + b.z * dy * dy) + b.y * dx * dy;
-      const float G = __expf(-sigma);
-      const float araw = a.z * G;
-      const float draw = (key >> 31) ? 0.f : dv.x;  // the clamp at 0.99 (as the walk decided) passes no gradient
-      const float dsig = -draw * araw;
-      const float dmx = (b.x * dx + b.y * dy) * dsig;
-      const float dmy = (b.y * dx + b.z * dy) * dsig;
-      const float4 pc = sPix[wid][p];
-      gv[0] = dmx;
-      gv[1] = dmy;
-      gv[2] = draw * G;
-      gv[3] = pc.w * dv.y;
-      gv[4] = 0.5f * dx * dx * dsig;
-      gv[5] = dx * dy * dsig;
-      gv[6] = 0.5f * dy * dy * dsig;
-      gv[7] = pc.x * dv.y;
-      gv[8] = pc.y * dv.y;
-      gv[9] = pc.z * dv.y;
-      if (kAbs) {
-        gv[10] = fabsf(dmx);
-        gv[11] = fabsf(dmy);
-      }
-    }
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t other = __shfl_down_sync(0xffffffffu, run, off);
-      const bool same = lane + off < 32 && other == run;
-#pragma unroll
-      for (int m = 0; m < kVals; ++m) {
-        const float y = __shfl_down_sync(0xffffffffu, gv[m], off);
-        if (same) gv[m] += y;
-      }
-    }
-    const uint32_t prev = __shfl_up_sync(0xffffffffu, run, 1);
-    if (act && (lane == 0 || prev != run)) {
-#pragma unroll
-      for (int m = 0; m < kVals; ++m)
-        if (gv[m] != 0.f) atomicAdd(&sAcc[j][m], gv[m]);
-    }
-    q_head += static_cast<uint32_t>(k);
-    __syncwarp();
-  };
-
+  // the deepest list position any pixel of this warp walks back from: positions past it are
+  // skipped without evaluating them
+  const uint32_t warp_last = __reduce_max_sync(0xffffffffu, max(last[0], last[1]));
+  uint32_t n_visit = 0, n_contrib = 0, n_iter = 0, n_iter_c = 0;
   for (int base = 0; base < n; base += kBatch) {
     __syncthreads();
     for (int k = tid; k < kBatch; k += kBlendThreads) {
@@ -637,35 +745,47 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
     __syncthreads();
     const int cnt = min(kBatch, n - base);
     for (int j = 0; j < cnt; ++j) {
-      if (!((sM[j] >> wid) & 1u)) continue;  // warp-uniform: no pixel of this warp is touched
       const uint32_t pos = static_cast<uint32_t>(n - 1 - base - j);
+      if (pos >= warp_last || !((sM[j] >> wid) & 1u)) continue;  // warp-uniform: nothing of this warp
       const float4 a = sA[j];
       const float4 b = sB[j];
       const float2 cc = sC[j];
       const float dx = a.x - fx;
-      float Gq[2], arawq[2], alphaq[2];
+      float dyq[2], Gq[2], arawq[2], alphaq[2];
       bool cq[2];
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const bool vis = inside[q] && pos < last[q];
         if (kCount) n_visit += vis;
-        const float dy = a.y - fy[q];
-        const float sigma = 0.5f * (b.x * dx * dx + b.z * dy * dy) + b.y * dx * dy;
+        dyq[q] = a.y - fy[q];
+        const float sigma = 0.5f * (b.x * dx * dx + b.z * dyq[q] * dyq[q]) + b.y * dx * dyq[q];
         Gq[q] = __expf(-sigma);
         arawq[q] = a.z * Gq[q];
         alphaq[q] = fminf(kAlphaMax, arawq[q]);
         cq[q] = vis && sigma >= 0.f && alphaq[q] >= kAlphaMin;
         if (kCount) n_contrib += cq[q];
       }
-      const uint32_t m0 = __ballot_sync(0xffffffffu, cq[0]);
-      const uint32_t m1 = __ballot_sync(0xffffffffu, cq[1]);
-      if (!(m0 | m1)) continue;  // warp-uniform: no pixel of the warp takes the Gaussian
-      // the reverse walk: this contributor's transmittance and dL/dalpha, then the suffix sums
+      // warp-uniform: where no pixel of the warp takes the Gaussian, nothing below changes
+      // warp-uniform: which of the lanes' two pixel rows any pixel of the warp takes the Gaussian in
+      const bool any0 = __any_sync(0xffffffffu, cq[0]);
+      const bool any1 = __any_sync(0xffffffffu, cq[1]);
+      if (kCount) {
+        n_iter += 1;
+        n_iter_c += any0 || any1;
+      }
+      if (!(any0 || any1)) continue;  // nothing below changes
+      float gv[kGradVals];
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {  // branch-free: non-contributors change nothing
+      for (int m = 0; m < kGradVals; ++m) gv[m] = 0.f;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {  // branch-free within a row: contributions are masked
+        if (!(q ? any1 : any0)) continue;  // warp-uniform: no pixel of this row takes it
+        const float dy = dyq[q];
+        const float G = Gq[q];
+        const float araw = arawq[q];
         const float alpha = alphaq[q];
         const bool c = cq[q];
-        const float rom = __frcp_rn(1.f - alpha);  // 1 / (1 - alpha), correctly rounded
+        const float rom = __fdividef(1.f, 1.f - alpha);  // 1 / (1 - alpha) to 2 ulp (1 - alpha >= 0.01)
         const float Ti = T[q] * rom;
         const float wgt = c ? alpha * Ti : 0.f;
         const float dz = (a.w - zr[q]) - zrl[q];
@@ -676,17 +796,28 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
         S2[q] = fmaf(cc.y, wgt, S2[q]);
         SD[q] = fmaf(dz, wgt, SD[q]);
         T[q] = c ? Ti : T[q];
-        if (c) {
-          const uint32_t slot = q_tail + (q ? __popc(m0) : 0u) + __popc((q ? m1 : m0) & lt_mask);
-          sQk[wid][slot & (kQueue - 1)] = static_cast<uint32_t>(j) | (static_cast<uint32_t>(2 * lane + q) << 16) |
-                                           (arawq[q] > kAlphaMax ? 0x80000000u : 0u);
-          sQv[wid][slot & (kQueue - 1)] = make_float2(dal, wgt);
+        const float draw = (c && araw <= kAlphaMax) ? dal : 0.f;  // the clamp at 0.99 passes no gradient
+        const float dsig = -draw * araw;
+        const float dmx = (b.x * dx + b.y * dy) * dsig;
+        const float dmy = (b.y * dx + b.z * dy) * dsig;
+        gv[0] += dmx;
+        gv[1] += dmy;
+        gv[2] += draw * G;
+        gv[3] += GD[q] * wgt;
+        gv[4] += 0.5f * dx * dx * dsig;
+        gv[5] += dx * dy * dsig;
+        gv[6] += 0.5f * dy * dy * dsig;
+        gv[7] += GC0[q] * wgt;
+        gv[8] += GC1[q] * wgt;
+        gv[9] += GC2[q] * wgt;
+        if (kAbs) {
+          gv[10] += fabsf(dmx);
+          gv[11] += fabsf(dmy);
         }
       }
-      q_tail += __popc(m0) + __popc(m1);
-      while (q_tail - q_head >= 32) flush(32);
+      const float tot = TransposeSum<kVals, 16>::run(gv, lane);
+      if (t_keep) atomicAdd(&sAcc[j][t_idx], tot);
     }
-    if (q_tail != q_head) flush(static_cast<int>(q_tail - q_head));  // the batch's slots are reused next
     __syncthreads();
     for (int k = tid; k < cnt; k += kBlendThreads) {
       float* f = reinterpret_cast<float*>(g2d + sV[k]);
@@ -707,6 +838,8 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
     if (lane == 0) {
       atomicAdd(counters + 2, e);
       atomicAdd(counters + 3, b);
+      atomicAdd(counters + 4, static_cast<unsigned long long>(n_iter));  // warp-uniform counts
+      atomicAdd(counters + 5, static_cast<unsigned long long>(n_iter_c));
     }
   }
   if (g_aff) {
@@ -771,14 +904,43 @@ void launch_tile_sort(unsigned long long* keys, const uint2* ranges, int n_tiles
   if (max_count > static_cast<uint32_t>(kTileSortSmall)) {
     int big_cap = 1;
     while (big_cap < static_cast<long long>(max_count) && big_cap < kTileSortCap) big_cap <<= 1;
-    // the large dynamic shared memory needs an opt-in (per process, once; repeating it is harmless)
-    static const cudaError_t attr = cudaFuncSetAttribute(tile_sort_big_kernel,
-                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                         static_cast<int>(sizeof(unsigned long long) * kTileSortCap));
-    (void)attr;
+    // the large dynamic shared memory needs an opt-in in each device's context: one bit per
+    // device (contexts on several host threads may get here at once; setting it twice is harmless)
+    static std::atomic<uint64_t> attr_set{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 64 || !((attr_set.load(std::memory_order_relaxed) >> dev) & 1u)) {
+      if (cudaFuncSetAttribute(tile_sort_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(sizeof(unsigned long long) * kTileSortCap)) == cudaSuccess &&
+          dev < 64)
+        attr_set.fetch_or(1ull << dev, std::memory_order_relaxed);
+    }
     tile_sort_big_kernel<<<std::max(1, grid_cap / 2), kSortBigThreads, sizeof(unsigned long long) * big_cap, s>>>(
         keys, ranges, vals, scratch, big, n_big, big_cap);
   }
+}
+
+void launch_duplicate(const Rec* rec, const uint32_t* order, const uint32_t* offsets, const uint32_t* d_n,
+                      long long max_n, const CamBatch& cams, int tile_cull, uint32_t* cnt_sorted,
+                      uint32_t* pair_keys, uint32_t* pair_vals, uint32_t* key_counts, int key_bits, int max_blocks,
+                      cudaStream_t s) {
+  if (max_n <= 0) return;
+  const int blocks = static_cast<int>(std::min<long long>((max_n + 255) / 256, std::max(max_blocks, 1)));
+  if (cnt_sorted) {
+    duplicate_kernel<true, true><<<blocks, 256, 0, s>>>(rec, order, offsets, d_n, max_n, cams, cnt_sorted, nullptr,
+                                                        nullptr, nullptr, 0);
+  } else if (tile_cull) {
+    duplicate_kernel<true, false><<<blocks, 256, 0, s>>>(rec, order, offsets, d_n, max_n, cams, nullptr, pair_keys,
+                                                         pair_vals, key_counts, key_bits);
+  } else {
+    duplicate_kernel<false, false><<<blocks, 256, 0, s>>>(rec, order, offsets, d_n, max_n, cams, nullptr, pair_keys,
+                                                          pair_vals, key_counts, key_bits);
+  }
+}
+
+void launch_ranges(const uint32_t* sorted_keys, long long P, int n_tiles, uint2* ranges, cudaStream_t s) {
+  if (n_tiles <= 0) return;
+  ranges_kernel<<<(n_tiles + 255) / 256, 256, 0, s>>>(sorted_keys, static_cast<uint32_t>(P), n_tiles, ranges);
 }
 
 void launch_blend_fwd(const Rec* rec, const uint32_t* pair_vals, const uint2* ranges, const CamBatch& cams,

@@ -1,6 +1,8 @@
 // Onesweep LSD radix sort (Adinets & Merrill 2022) of uint32 (key, value) pairs: the library's
-// general sort building block (gsr_sort_pairs_u32 and its allocation-free variant). Each pass
-// reads every key once: a block
+// general sort building block (gsr_sort_pairs_u32 and its allocation-free variant) and the sort
+// of the global-sort binning (gsr_opts.global_sort: the visible records by depth, then the pairs
+// stably by tile), with the chained scan that turns per-record tile counts into pair offsets
+// there. Each pass reads every key once: a block
 // ranks its 4096 keys by the pass's 8-bit digit (stable: one warp ballot per digit bit finds
 // the lanes with equal digits), publishes its per-digit counts, and takes its global digit offsets from its predecessors by a decoupled
 // look-back whose waits are bounded (a wait that runs out sets an error bit and the block
@@ -210,6 +212,53 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
   }
 }
 
+// Exclusive scan of per-record tile counts in depth order (the global-sort binning):
+// counts[i] = touched[order[i]] (or cnt_sorted[i] when given), offsets[i] out, *p_total = sum.
+__global__ void __launch_bounds__(kScanThreads) pair_scan_kernel(
+    const uint32_t* __restrict__ touched, const uint32_t* __restrict__ order, const uint32_t* __restrict__ cnt_sorted,
+    uint32_t* __restrict__ offsets, const uint32_t* d_n, long long max_n, unsigned long long* status,
+    uint32_t* counter, unsigned long long* p_total, uint32_t epoch, int* err, WaitCfg wait) {
+  __shared__ uint32_t s_bid;
+  __shared__ unsigned long long s_base;
+  const long long n = device_n(d_n, max_n);
+  for (;;) {
+    if (threadIdx.x == 0) s_bid = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t bid = s_bid;
+    const long long start = static_cast<long long>(bid) * (kScanThreads * kScanItems);
+    if (start >= n) break;
+    uint32_t x[kScanItems];
+    uint32_t sum = 0;
+    const long long first = start + static_cast<long long>(threadIdx.x) * kScanItems;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const long long idx = first + k;
+      x[k] = 0;
+      if (idx < n) x[k] = cnt_sorted ? cnt_sorted[idx] : touched[order[idx]];
+      sum += x[k];
+    }
+    uint32_t total;
+    const uint32_t excl = block_excl_scan(sum, &total);
+    if (threadIdx.x < 32) {
+      const unsigned long long ex = warp_chained_prefix(status, bid, total, epoch, err, wait);
+      if (threadIdx.x == 0) s_base = ex;
+    }
+    __syncthreads();
+    unsigned long long run = s_base + excl;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const long long idx = first + k;
+      if (idx < n) {
+        if (run > 0xffffffffull) atomicOr(err, kErrOverflow);
+        offsets[idx] = static_cast<uint32_t>(run);
+        if (idx == n - 1) *p_total = run + x[k];
+      }
+      run += x[k];
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 void sort_clear_counts(const SortScratch& sc, cudaStream_t s) {
@@ -250,6 +299,18 @@ void radix_sort_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
     ksrc = kdst;
     vsrc = vdst;
   }
+}
+
+void pair_offsets_scan(const uint32_t* touched, const uint32_t* order, const uint32_t* cnt_sorted,
+                       uint32_t* offsets, const uint32_t* d_n, long long max_n, unsigned long long* status,
+                       uint32_t* counter, unsigned long long* p_total, int* err, uint32_t epoch, int grid_cap,
+                       WaitCfg wait, cudaStream_t s) {
+  const long long per = kScanThreads * kScanItems;
+  const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>((max_n + per - 1) / per, grid_cap)));
+  cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
+  cudaMemsetAsync(p_total, 0, sizeof(unsigned long long), s);
+  pair_scan_kernel<<<grid, kScanThreads, 0, s>>>(touched, order, cnt_sorted, offsets, d_n, max_n, status, counter,
+                                                 p_total, epoch, err, wait);
 }
 
 }  // namespace gsr

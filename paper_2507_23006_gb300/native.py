@@ -38,12 +38,12 @@ EXPORTED = [
     "gsr_state_get_info", "gsr_state_copy", "gsr_sync_check", "gsr_sort_pairs_u32", "gsr_select_lod",
     "gsr_appearance_cache",
     "gsr_profile_enable", "gsr_profile_collect", "gsr_sort_pairs_u32_noalloc", "gsr_profile_select",
-    "gsr_param_grads_zero", "gsr_set_wait_limit",
+    "gsr_param_grads_zero", "gsr_set_wait_limit", "gsr_set_fill_rate",
 ]
 
 STAGES = ["preprocess", "tile_count", "tile_scan", "readback", "place", "tile_sort", "blend_fwd", "blend_bwd",
-          "preprocess_bwd", "between_stages", "appearance_bwd"]
-COUNTERS = ["fwd_evals", "fwd_contribs", "bwd_evals", "bwd_contribs"]
+          "preprocess_bwd", "between_stages", "appearance_bwd", "depth_sort", "ranges"]
+COUNTERS = ["fwd_evals", "fwd_contribs", "bwd_evals", "bwd_contribs", "bwd_warp_iters", "bwd_warp_iters_contrib"]
 
 
 class GsrError(RuntimeError):
@@ -78,7 +78,8 @@ class CCamera(ctypes.Structure):
 
 class COpts(ctypes.Structure):
     _fields_ = [("eps2d", ctypes.c_float), ("antialiased", ctypes.c_int32), ("tile_cull", ctypes.c_int32),
-                ("bg", ctypes.c_float * 3), ("save_state", ctypes.c_int32), ("absgrad", ctypes.c_int32)]
+                ("bg", ctypes.c_float * 3), ("save_state", ctypes.c_int32), ("absgrad", ctypes.c_int32),
+                ("global_sort", ctypes.c_int32)]
 
 
 class COutputs(ctypes.Structure):
@@ -179,6 +180,7 @@ def load(build_if_missing: bool = True):
         L.gsr_profile_select.argtypes = [vp, ctypes.c_uint32]
         L.gsr_param_grads_zero.argtypes = [vp, vp, vp, vp]
         L.gsr_set_wait_limit.argtypes = [vp, ctypes.c_uint32, ctypes.c_int32]
+        L.gsr_set_fill_rate.argtypes = [vp, ctypes.c_float, ctypes.c_int32]
         L.gsr_appearance_cache.argtypes = [vp, ctypes.POINTER(CGaussians), ctypes.c_int32, vp, vp]
         for name in EXPORTED:
             getattr(L, name)
@@ -186,7 +188,7 @@ def load(build_if_missing: bool = True):
                      "gsr_state_get_info", "gsr_state_copy", "gsr_sync_check", "gsr_sort_pairs_u32",
                      "gsr_select_lod", "gsr_profile_enable", "gsr_profile_collect",
                      "gsr_sort_pairs_u32_noalloc", "gsr_profile_select", "gsr_param_grads_zero",
-                     "gsr_appearance_cache", "gsr_set_wait_limit"):
+                     "gsr_appearance_cache", "gsr_set_wait_limit", "gsr_set_fill_rate"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -335,6 +337,7 @@ class Options:
     bg: tuple = (0.0, 0.0, 0.0)
     save_state: bool = True
     absgrad: bool = False
+    global_sort: bool = False  # order the pairs with global radix sorts instead of per-tile sorts
 
     def c_struct(self) -> COpts:
         o = COpts()
@@ -345,6 +348,7 @@ class Options:
             o.bg[k] = float(self.bg[k])
         o.save_state = int(bool(self.save_state))
         o.absgrad = int(bool(self.absgrad))
+        o.global_sort = int(bool(self.global_sort))
         return o
 
 
@@ -440,6 +444,11 @@ class Context:
         """Bound on the polls of every device wait (0: the default); never_ready makes every wait
         run to it (a test of failure detection). See gsr_set_wait_limit."""
         _check(self, load().gsr_set_wait_limit(self.handle, int(polls), int(bool(never_ready))))
+
+    def set_fill_rate(self, gb_per_s: float = 0.0, blocks: int = 0):
+        """Pace of the gradient zero fill in GB/s (0: unpaced) and its block count (0: keep).
+        See gsr_set_fill_rate."""
+        _check(self, load().gsr_set_fill_rate(self.handle, float(gb_per_s), int(blocks)))
 
     def sync_check(self, stream=None):
         _check(self, load().gsr_sync_check(self.handle, _stream(stream)))

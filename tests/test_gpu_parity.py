@@ -128,11 +128,14 @@ def _check_images(out, res, cams, depth_scale):
     return int(mark.sum())
 
 
-@pytest.mark.parametrize("aa,cull", [(True, False), (False, True), (True, True)])
-def test_box_scene_forward(ctx, aa, cull):
-    """10,000 Gaussians in a 10x10x10 box 5-15 units in front of a 256x256 camera (fx = 300)."""
+@pytest.mark.parametrize("aa,cull,global_sort", [(True, False, False), (False, True, False), (True, True, False),
+                                                 (True, True, True)])
+def test_box_scene_forward(ctx, aa, cull, global_sort):
+    """10,000 Gaussians in a 10x10x10 box 5-15 units in front of a 256x256 camera (fx = 300);
+    both orderings of the pairs (per-tile sorts and global radix sorts)."""
     scene, cam = pu.scene_box()
     nopts, oopts = pu.opts_pair(antialiased=aa, tile_cull=cull, bg=(0.1, 0.2, 0.3))
+    nopts.global_sort = global_sort
     g, out, st = pu.gpu_render(ctx, scene, [cam], nopts)
     sa = pu.state_arrays(st)
     res = oracle.render(scene, [cam], oopts)
@@ -461,6 +464,41 @@ def test_street_block_full_size_sampled(ctx, street):
     ref = oracle.backward(scene, [cam], up, oopts, tile_subset=tiles, want_mag=True)
     for k in ("means", "scales", "quats", "opacities", "sh"):
         pu.grad_close(gg[k], ref[k], k, mag=ref["mag"][k])
+
+
+@pytest.mark.parametrize("which", ["box", "street"])
+def test_global_sort_gives_the_same_bits(ctx, which):
+    """The two orderings of the (tile, Gaussian) pairs, per-tile sorts in shared memory and global
+    onesweep radix sorts (depth, then stably by tile), put every tile's list in the same
+    (depth, index) order: records, pair lists, ranges, last contributors and images bit for bit;
+    gradients equal up to the order of the FP32 atomic sums."""
+    if which == "box":
+        scene, cam = pu.scene_box(10_000, seed=8)
+    else:
+        scene, cam = scenes.street_block(1, 500_000), scenes.street_block_camera()
+    g = native.Gaussians.from_scene(scene)
+    res = {}
+    for glob in (False, True):
+        opts = native.Options(tile_cull=True, global_sort=glob)
+        out, st = native.render_forward(ctx, g, [cam], opts)
+        ctx.sync_check()
+        sa = pu.state_arrays(st)
+        up = np.random.default_rng(3).normal(size=(cam.width * cam.height, 6))
+        up[:, 4] = 0.0
+        gr = _gpu_backward(ctx, g, [cam], st, up, opts)
+        res[glob] = (out, sa, gr)
+    (o0, s0, g0), (o1, s1, g1) = res[False], res[True]
+    assert s0["info"]["n_pairs"] == s1["info"]["n_pairs"] > 0
+    for k in ("rec", "g_of", "pair_vals", "ranges", "n_contrib", "T_final"):
+        np.testing.assert_array_equal(s0[k], s1[k], err_msg=k)
+    for k in ("rgb", "depth_acc", "depth_exp", "alpha"):
+        assert torch.equal(o0[k], o1[k]), k
+    up = np.random.default_rng(3).normal(size=(cam.width * cam.height, 6))
+    up[:, 4] = 0.0
+    mag = oracle.backward(scene, [cam], up, oracle.Opts(tile_cull=True), want_mag=True)["mag"]
+    for k in ("means", "scales", "quats", "opacities", "sh"):
+        pu.grad_close(g1[k], g0[k], f"{k} (global vs per-tile sort)", rel=1e-5, group_rel=1e-6, mag=mag[k],
+                      cancel_rel=1e-5)
 
 
 def test_preprocess_variants_agree():
