@@ -643,9 +643,10 @@ gsr_status gsr_create(gsr_ctx** out, int device, const gsr_allocator* alloc) {
   }
   cudaMemset(ctx->d_err, 0, 64);
   int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0) {
     ctx->grid_cap = 2 * sms;
     ctx->fill_blocks = std::max(1, sms / 2);
+  }
   cudaGetLastError();
   if (!alloc) {
     cudaMemPoolProps props{};

@@ -7,7 +7,8 @@ Workloads: `city` (a synthetic city grid seen from 150 m up at 45 degrees, the t
 benchmark), `street` (a street block, one camera 30 m up looking 45 degrees down) and `box`
 (uniform Gaussians in a box in front of the camera). `--fwd-only` runs forward renders without
 saved state; `--fp16` stores attributes and SH in FP16; `--mlp` turns on the per-Gaussian
-appearance transform (random embeddings and weights); `--time` prints the device time per
+appearance transform (random embeddings and weights); `--global-sort` bins through the global
+(tile, depth) radix sort instead of the per-tile sort; `--time` prints the device time per
 step after the first, and then the mean time of each stage over as many more steps (CUDA events
 around every stage).
 """
@@ -43,6 +44,7 @@ def main():
     p.add_argument("--fp16", action="store_true")
     p.add_argument("--mlp", action="store_true")
     p.add_argument("--tile-cull", type=int, default=1)
+    p.add_argument("--global-sort", action="store_true")
     p.add_argument("--time", action="store_true")
     a = p.parse_args()
     scene, cam = workload(a.workload, a.gaussians, a.width, a.height)
@@ -54,7 +56,8 @@ def main():
         g.mlp = native.AppearanceMLP(torch.randn((g.n, 16), device="cuda", generator=gm),
                                      torch.randn((1, 32), device="cuda", generator=gm),
                                      0.3 * torch.randn(native.MLP_PARAMS, device="cuda", generator=gm))
-    opts = native.Options(tile_cull=bool(a.tile_cull), save_state=not a.fwd_only)
+    opts = native.Options(tile_cull=bool(a.tile_cull), save_state=not a.fwd_only,
+                          global_sort=a.global_sort)
     npix = cam.width * cam.height
     gen = torch.Generator(device="cuda").manual_seed(1234)
     d_out = dict(rgb=torch.randn((npix, 3), device="cuda", generator=gen),
