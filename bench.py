@@ -122,9 +122,11 @@ class ClockSampler:
 # CUDA sources each stage's kernels are built from (besides the shared headers): a stored DRAM
 # counter stays valid while these files are unchanged.
 KERNEL_SOURCES = {
-    "blend_fwd": ["raster.cu"],
-    "blend_bwd": ["raster.cu"],
-    "preprocess": ["preprocess_fwd.cuh", "preprocess.cu", "preprocess_dense.cu"],
+    "blend_fwd": ["blend_fwd.cu", "tile_util.cuh"],
+    "blend_bwd": ["blend_bwd.cu", "tile_util.cuh"],
+    "tile_scan": ["binning.cu", "tile_util.cuh"],
+    "place": ["binning.cu", "tile_util.cuh"],
+    "preprocess": ["preprocess_fwd.cuh", "preprocess.cu", "preprocess_rec.cu"],
     "preprocess_bwd": ["preprocess_fwd.cuh", "preprocess.cu"],
 }
 COMMON_SOURCES = ["gsr_internal.cuh", "scan_util.cuh"]
@@ -327,20 +329,21 @@ def stage_work(n, V, P, tiles, npix, counts):
         # the per-unit figures of the hot-path scope table: 44 B read per Gaussian, 192 B of SH
         # read and a 48 B record written per visible one
         "preprocess": dict(bytes=44.0 * n + 240.0 * V),
-        # binning: the counting and the placing pass read the 48 bytes of each record that locate
-        # it (position, opacity, depth, conic, rectangle); the scan reads each tile's count and
-        # writes its range and cursor; placing writes an 8-byte key per pair; sorting reads the
-        # keys and writes the 4-byte record index per pair
-        "tile_count": dict(bytes=48.0 * V + 4.0 * tiles),
+        # binning: the record pass of the preprocess counts the pairs per tile from the records it
+        # holds (atomics on the per-tile counters, no extra bytes); the scan reads each tile's
+        # count and writes its range and cursor; placing reads the 48 bytes of each record that
+        # locate it (position, opacity, depth, conic, rectangle) and writes an 8-byte key per pair
         "tile_scan": dict(bytes=16.0 * tiles),
         "place": dict(bytes=48.0 * V + 8.0 * P),
-        "tile_sort": dict(bytes=12.0 * P),
-        "blend_fwd": dict(bytes=48.0 * P + 28.0 * npix, flops=FLOPS_PER_FWD_EVAL * fe, mufu=1.0 * fe),
+        # the forward blend sorts each tile's keys (lists of at most 1024 pairs; longer ones, none on
+        # these workloads, are sorted by a launch of their own): it reads the 8-byte key and writes
+        # the 4-byte record index per pair, then reads each pair's 48-byte record
+        "blend_fwd": dict(bytes=60.0 * P + 28.0 * npix, flops=FLOPS_PER_FWD_EVAL * fe, mufu=1.0 * fe),
         "blend_bwd": dict(bytes=48.0 * P + 28.0 * npix + 40.0 * V, flops=FLOPS_PER_BWD_EVAL * be, mufu=2.0 * be),
         # single camera: one record per visible Gaussian; its attribute and SH rows read and its
         # gradient rows written (236 B each way) plus the record, its 2D gradients and owner
         "preprocess_bwd": dict(bytes=472.0 * V + 116.0 * V),
-        # the gradient rows of every Gaussian zeroed (side stream, beside the binning)
+        # the gradient rows of every Gaussian zeroed (side stream, beside the backward blend)
         "gradient_fill": dict(bytes=236.0 * n),
     }
 
@@ -626,7 +629,7 @@ def run_ours(args, rank, world, local_rank):
                  absgrad=None)
 
     def step():
-        # the gradient arrays are zeroed beside the forward pass (gsr_param_grads_zero)
+        # the gradient arrays are zeroed beside the backward blend (gsr_param_grads_zero)
         native.zero_param_grads(ctx, g, grads)
         _, st = native.render_forward(ctx, g, [cam], opts, outputs=outs)
         native.render_backward(ctx, g, [cam], st, d_out, opts, grads=grads)
@@ -852,6 +855,8 @@ def _serve_pair(levels, full, budget, rate, seconds, warm_s):
         out[name] = {k: st[k] for k in ("p50_ms", "p99_ms", "mean_ms", "fps", "served", "failed", "max_in_flight",
                                         "mean_batch", "mean_selected")}
         out[name]["saturated_fps"] = burst["fps"]
+        out[name]["saturated_mean_batch"] = burst["mean_batch"]  # views per launch under the burst
+        out[name]["saturated_p99_ms"] = burst["p99_ms"]
         errs = sorted({r.error for r in st["requests"] + burst["requests"] if r.error})
         if errs:
             out[name]["errors"] = errs[:3]
@@ -939,11 +944,11 @@ def run_serve_full(args):
 
 def kernels_per_step(tile_cull, info):
     """Kernels of ours launched per fwd+bwd step (memsets excluded)."""
-    k = 1                      # preprocess
-    k += 1 if int(info["n_visible"]) > 0 else 0  # pair counts per tile
+    k = 2                      # preprocess: cull pass, record pass (which counts the pairs per tile)
     k += 1                     # tile scan
-    k += 2 if int(info["n_pairs"]) > 0 else 0    # pair placement, per-tile sort
-    k += 1                     # blend forward
+    k += 1 if int(info["n_pairs"]) > 0 else 0    # pair placement
+    k += 1 if int(info.get("max_tile_pairs", 0)) > 1024 else 0  # sort of the lists over 1024 pairs
+    k += 1                     # blend forward (sorts the other lists)
     k += 1                     # gradient zero fill (side stream)
     k += 1 + 1                 # blend backward, preprocess backward
     return k

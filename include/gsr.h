@@ -239,16 +239,16 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
 /* Zeroes the parameter-gradient arrays of `grads` (means, scales, quats, opacities, sh and, when
  * not NULL, absgrad and, with g->mlp set, gauss_embed; sized for g->n Gaussians and g->sh_coeffs
  * as in gsr_render_backward; the backward zeroes the small image_embed and mlp_params itself) ahead
- * of the backward pass. No counterpart in the paper: it moves the gradient initialisation that
- * gsr_render_backward otherwise does itself to an earlier point, so that this memory-bound fill
- * (236 bytes per Gaussian in FP32) runs beside a forward pass, whose stages leave most of the
- * memory bandwidth unused, instead of beside the blend backward. The call only records the
- * request (`stream` is not used): the next gsr_render_forward on this context queues the fill
- * on the context's internal stream right after its preprocess stage (which itself moves much
- * memory), ordered after everything queued on that forward's stream. The next
- * gsr_render_backward on this context that is given exactly these arrays skips its own fill and
- * waits for this one before writing (queuing it itself if no forward did); a backward given other
- * arrays fills those itself and drops the request. The caller must not use the arrays between
+ * of the backward pass. No counterpart in the paper. The call records the request (a fill still
+ * queued for an earlier request is ordered before later work on `stream`; nothing else is
+ * queued): the next gsr_render_backward on this context that is given exactly these arrays
+ * queues this memory-bound fill (236 bytes per Gaussian in FP32) on the context's internal
+ * stream right before its blend, which it runs beside, and waits for it before writing the
+ * rows; that is also what a backward does without a request, so the request only fixes the
+ * arrays ahead of time. (Queuing the fill earlier, at the end of the forward, was measured
+ * slower: started alone it then shared the GPU badly with the blend backward.) A backward given
+ * other arrays zeroes the requested ones too, ordered before everything it queues after, and
+ * fills its own. The caller must not use the arrays between
  * this call and that backward. Errors: GSR_ERR_INVALID_ARG (null struct or gradient array). */
 gsr_status gsr_param_grads_zero(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_param_grads* grads,
                                 gsr_stream stream);
@@ -265,10 +265,11 @@ gsr_status gsr_sync_check(gsr_ctx* ctx, gsr_stream stream);
 
 /* Pace of the gradient zero fill (no counterpart in the paper). The fill of the parameter-gradient
  * arrays (gsr_param_grads_zero, or the backward's own) runs on the context's side stream beside the
- * forward's binning and blends and the backward's blend; at full speed it takes most of the memory
- * bandwidth from the latency-bound stages it overlaps. gb_per_s > 0 spreads it out at about that
- * rate (each fill block starts a 16 KB chunk only when it is due on the GPU's nanosecond timer);
- * 0 writes as fast as possible. blocks > 0 sets how many blocks fill (0 keeps the current number).
+ * backward's blend; at full speed it takes most of the memory bandwidth from the stages it
+ * overlaps. gb_per_s > 0 spreads it out at about that rate (each fill block starts a 16 KB chunk
+ * only when it is due on the GPU's nanosecond timer); 0 (the default) writes as fast as possible.
+ * blocks > 0 sets how many blocks fill (0 keeps the current number; the default is 5/8 of the
+ * SM count).
  * Results are the same either way; only the timing changes. Errors: GSR_ERR_INVALID_ARG. */
 gsr_status gsr_set_fill_rate(gsr_ctx* ctx, float gb_per_s, int32_t blocks);
 

@@ -33,7 +33,7 @@ class _Rasterize(torch.autograd.Function):
             apps = [appearance[c] for c in range(len(cams))]
         grads = None
         if any(fctx.needs_input_grad[:9]):
-            # gradient arrays zeroed now, beside the forward pass, rather than inside the backward
+            # the gradient arrays to zero (the backward queues the fill beside its blend)
             grads = native.param_grads(lib_ctx, g, len(cams), opts.absgrad)
             native.zero_param_grads(lib_ctx, g, grads)
         outs, state = native.render_forward(lib_ctx, g, cams, opts, appearances=apps)

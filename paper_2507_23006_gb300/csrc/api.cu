@@ -36,8 +36,9 @@ struct gsr_ctx {
   // scratch
   Buf seg_begin, seg_start, seg_cams;
   Buf rec, owner;                              // records (recompute / no-state mode)
+  Buf rcam;                                    // camera of each record (preprocess passes)
   Buf sort_ktmp, sort_vtmp, sort_hist, sort_status;  // gsr_sort_pairs_u32
-  Buf pre_status, scan_status, misc, tile_ctr, big_tiles;
+  Buf pre_vis, pre_counts, scan_status, misc, tile_ctr, big_tiles;
   Buf pair_keys, key_scratch, pvals_s, ranges;  // pairs (pvals_s, ranges: no-state mode)
   Buf dkeys, dvals, touched, dkeys_s, dvals_s, offsets, cnt_sorted, pkeys, pvals, pkeys_s;  // global sort
   Buf pix_T, pix_n, pix_D;                     // per-pixel state (no-state mode)
@@ -67,9 +68,8 @@ struct gsr_ctx {
   bool prezero_requested = false;  // recorded, the fill not queued yet
   bool prezero_pending = false;    // fill queued (ev_prezero marks its end), not used yet
   int grid_cap = 304;  // resident blocks of the looping scan / sort kernels (2 per SM)
-  int fill_blocks = 76;  // blocks of the gradient zero fill
+  int fill_blocks = 95;  // blocks of the gradient zero fill (5/8 of the SMs)
   float fill_gbs = 0.f;  // pace of the gradient zero fill in GB/s (0: unpaced); gsr_set_fill_rate
-  bool pre_dense = false;  // the last binning kept over a quarter of its (camera, Gaussian) pairs
   WaitCfg wait;  // how the look-backs of this context's kernels wait (gsr_set_wait_limit)
   // default allocator: a context-owned stream-ordered pool (growth and release never
   // synchronise the device, which matters when several contexts serve concurrently)
@@ -162,7 +162,7 @@ bool ensure_zeroed(gsr_ctx* ctx, Buf& b, size_t bytes, cudaStream_t s) {
 // arrays are cleared and the count restarts.
 uint32_t next_epoch(gsr_ctx* ctx, cudaStream_t s) {
   if (++ctx->epoch >= (1u << 30)) {
-    Buf* st[] = {&ctx->pre_status, &ctx->scan_status, &ctx->sort_status};  // every chained scan's words
+    Buf* st[] = {&ctx->scan_status, &ctx->sort_status};  // every chained scan's words
     for (Buf* b : st)
       if (b->p) cudaMemsetAsync(b->p, 0, b->cap, s);
     ctx->epoch = 1;
@@ -409,8 +409,11 @@ gsr_status upload_segments(gsr_ctx* ctx, const gsr_gaussians* g, SegMap* m, cuda
   return GSR_OK;
 }
 
+// sort_in_blend: the per-tile lists of at most kTileSortSmall pairs are left unsorted in
+// ctx->pair_keys for the forward blend to sort (only the longer lists are sorted here).
 gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb, const gsr_opts* o, BinOut bo,
-                       long long* V_out, long long* P_out, cudaStream_t s, long long* max_tile_out = nullptr) {
+                       long long* V_out, long long* P_out, cudaStream_t s, long long* max_tile_out = nullptr,
+                       bool sort_in_blend = false) {
   const long long N = render_count(g);
   const int C = cb.C;
   const long long capv = std::max<long long>(1, N * C);
@@ -427,13 +430,13 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   GSR_TRY_ALLOC(*bo.rec, sizeof(Rec) * capv);
   GSR_TRY_ALLOC(*bo.owner, sizeof(uint32_t) * capv);
   GSR_TRY_ALLOC(*bo.ranges, sizeof(uint2) * std::max(tiles, 1));
-  if (!ensure_zeroed(ctx, ctx->pre_status, sizeof(unsigned long long) * std::max(pre_blocks, 1), s))
-    return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
+  GSR_TRY_ALLOC(ctx->pre_vis, sizeof(uint32_t) * std::max<long long>(N, 1));
+  GSR_TRY_ALLOC(ctx->pre_counts, sizeof(uint32_t) * std::max(pre_blocks, 1));
   const long long scan_items = global ? capv : tiles;
   const long long scan_blocks = (scan_items + kScanThreads * kScanItems - 1) / (kScanThreads * kScanItems);
   if (!ensure_zeroed(ctx, ctx->scan_status, sizeof(unsigned long long) * (scan_blocks + 1), s))
     return set_err(ctx, GSR_ERR_OOM, "device allocation failed");
-  // misc (32-bit words): [0] preprocess block counter, [1] V, [2] scan block counter,
+  // misc (32-bit words): [0] unused, [1] V, [2] scan block counter,
   // [3] largest tile's pair count, [4..5] P (64-bit), [6] tiles listed for the large-list sort
   GSR_TRY_ALLOC(ctx->misc, 64);
   uint32_t* misc = as<uint32_t>(ctx->misc);
@@ -447,12 +450,12 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   PreOut po{};
   po.rec = as<Rec>(*bo.rec);
   po.owner = as<uint32_t>(*bo.owner);
-  po.status = as<unsigned long long>(ctx->pre_status);
-  po.counter = misc + 0;
+  GSR_TRY_ALLOC(ctx->rcam, capv);
+  po.rcam = as<uint8_t>(ctx->rcam);
+  po.vis = as<uint32_t>(ctx->pre_vis);
+  po.counts = as<uint32_t>(ctx->pre_counts);
   po.v_total = d_V;
   po.err = ctx->d_err;
-  po.epoch = next_epoch(ctx, s);
-  po.wait = ctx->wait;
   uint32_t* tile_ctr = nullptr;
   SortScratch sc{};
   if (global) {
@@ -476,16 +479,13 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
     tile_ctr = as<uint32_t>(ctx->tile_ctr);
     e = cudaMemsetAsync(tile_ctr, 0, sizeof(uint32_t) * tiles, s);
     if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
+    po.tile_ctr = tile_ctr;  // the record pass counts the pairs per tile
+    po.tile_cull = o->tile_cull;
   }
   {
     StageTimer tm(ctx, GSR_STAGE_PREPROCESS, s);
-    launch_preprocess_fwd(ga, cb, o->eps2d, o->antialiased, po, pre_blocks, ctx->pre_dense, s);
+    launch_preprocess_fwd(ga, cb, o->eps2d, o->antialiased, po, pre_blocks, 4 * ctx->grid_cap, s);
   }
-  // A requested gradient fill starts here: the stages up to the end of the forward blend move
-  // little memory, the preprocess before them much.
-  e = start_prezero(ctx, s);
-  if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
-
   if (global) {
     // records by depth, then (tile-culled) counts and pair offsets in depth order
     if (N * C > 0) {
@@ -506,12 +506,7 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
                       d_V, capv, as<unsigned long long>(ctx->scan_status), misc + 2, d_P, ctx->d_err,
                       next_epoch(ctx, s), ctx->grid_cap, ctx->wait, s);
   } else {
-    // pairs per tile, then each tile's range and the total P
-    if (N * C > 0) {
-      StageTimer tm(ctx, GSR_STAGE_TILE_COUNT, s);
-      launch_bin_pairs(as<Rec>(*bo.rec), d_V, capv, cb, o->tile_cull, tile_ctr, nullptr, nullptr, ctx->d_err,
-                       4 * ctx->grid_cap, s);
-    }
+    // each tile's range and the total P from the pairs per tile (counted by the record pass)
     StageTimer tm(ctx, GSR_STAGE_TILE_SCAN, s);
     launch_tile_scan(tile_ctr, as<uint2>(*bo.ranges), tiles, as<unsigned long long>(ctx->scan_status), misc + 2, d_P,
                      misc + 3, as<uint32_t>(ctx->big_tiles), misc + 6, next_epoch(ctx, s), ctx->d_err, ctx->wait,
@@ -546,8 +541,6 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   *V_out = V;
   *P_out = P;
   if (max_tile_out) *max_tile_out = P > 0 ? static_cast<long long>(max_count) : 0;
-  // the next preprocess picks its variant from this launch's survivor ratio
-  ctx->pre_dense = 4 * V > N * C;
 
   const long long Pc = std::max<long long>(P, 1);
   GSR_TRY_ALLOC(*bo.pvals_s, sizeof(uint32_t) * Pc);
@@ -597,7 +590,7 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
     {
       StageTimer tm(ctx, GSR_STAGE_TILE_SORT, s);
       launch_tile_sort(as<unsigned long long>(ctx->pair_keys), as<uint2>(*bo.ranges), tiles, as<uint32_t>(*bo.pvals_s),
-                       scratch, max_count, as<uint32_t>(ctx->big_tiles), misc + 6, ctx->grid_cap, s);
+                       scratch, max_count, as<uint32_t>(ctx->big_tiles), misc + 6, !sort_in_blend, ctx->grid_cap, s);
     }
   }
   e = cudaGetLastError();
@@ -645,7 +638,7 @@ gsr_status gsr_create(gsr_ctx** out, int device, const gsr_allocator* alloc) {
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0) {
     ctx->grid_cap = 2 * sms;
-    ctx->fill_blocks = std::max(1, sms / 2);
+    ctx->fill_blocks = std::max(1, 5 * sms / 8);
   }
   cudaGetLastError();
   if (!alloc) {
@@ -686,8 +679,8 @@ void gsr_destroy(gsr_ctx* ctx) {
     delete st;
   }
   ctx->state_pool.clear();
-  Buf* all[] = {&ctx->seg_begin, &ctx->seg_start, &ctx->seg_cams, &ctx->rec, &ctx->owner, &ctx->sort_ktmp,
-                &ctx->sort_vtmp, &ctx->sort_hist, &ctx->sort_status, &ctx->pre_status, &ctx->scan_status, &ctx->misc,
+  Buf* all[] = {&ctx->seg_begin, &ctx->seg_start, &ctx->seg_cams, &ctx->rec, &ctx->owner, &ctx->rcam, &ctx->sort_ktmp,
+                &ctx->sort_vtmp, &ctx->sort_hist, &ctx->sort_status, &ctx->pre_vis, &ctx->pre_counts, &ctx->scan_status, &ctx->misc,
                 &ctx->tile_ctr, &ctx->big_tiles, &ctx->pair_keys, &ctx->key_scratch, &ctx->pvals_s, &ctx->ranges, &ctx->pix_T,
                 &ctx->pix_n, &ctx->pix_D, &ctx->g2d, &ctx->gaff, &ctx->dkeys, &ctx->dvals, &ctx->touched,
                 &ctx->dkeys_s, &ctx->dvals_s, &ctx->offsets, &ctx->cnt_sorted, &ctx->pkeys, &ctx->pvals, &ctx->pkeys_s};
@@ -766,7 +759,8 @@ gsr_status gsr_render_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_ca
     bo = BinOut{&ctx->rec, &ctx->owner, &ctx->pvals_s, &ctx->ranges};
   }
   long long V = 0, P = 0, max_tile = 0;
-  st = run_binning(ctx, g, cb, opts, bo, &V, &P, s, &max_tile);
+  const bool sort_in_blend = opts->global_sort == 0;
+  st = run_binning(ctx, g, cb, opts, bo, &V, &P, s, &max_tile, sort_in_blend);
   if (st != GSR_OK) {
     if (stt) gsr_state_release(ctx, stt);
     return st;
@@ -789,8 +783,9 @@ gsr_status gsr_render_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_ca
   bf.D_state = as<float2>(*pD);
   {
     StageTimer tm(ctx, GSR_STAGE_BLEND_FWD, s);
-    launch_blend_fwd(as<Rec>(*bo.rec), as<uint32_t>(*bo.pvals_s), as<uint2>(*bo.ranges), cb, opts->bg, bf,
-                     counters_of(ctx), s);
+    const unsigned long long* tile_keys = sort_in_blend && P > 0 ? as<unsigned long long>(ctx->pair_keys) : nullptr;
+    launch_blend_fwd(as<Rec>(*bo.rec), as<uint32_t>(*bo.pvals_s), tile_keys, static_cast<uint32_t>(max_tile),
+                     as<uint2>(*bo.ranges), cb, opts->bg, bf, counters_of(ctx), s);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -864,7 +859,11 @@ gsr_status gsr_param_grads_zero(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_
     return set_err(ctx, GSR_ERR_INVALID_ARG, "null parameter gradient array");
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
-  (void)stream;
+  // a fill queued for an earlier request still writes its arrays: order it before what follows
+  if (ctx->prezero_pending) {
+    e = cudaStreamWaitEvent(reinterpret_cast<cudaStream_t>(stream), ctx->ev_prezero, 0);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "join");
+  }
   ctx->prezero_pending = false;
   ctx->prezero_requested = false;
   if (g->n == 0) return GSR_OK;
@@ -917,22 +916,32 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
   if (e == cudaSuccess && g->mlp) e = cudaMemsetAsync(grads->mlp_params, 0, sizeof(float) * kMlpParams, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
   // Every parameter-gradient row starts at zero; only rows of Gaussians with a record are then
-  // written. The fill runs on the side stream (overlapping the blend backward), unless
-  // gsr_param_grads_zero already queued it for these arrays.
+  // written. The fill is queued on the side stream right before the blend backward, which it
+  // runs beside (an ALU-bound kernel that leaves the memory bandwidth to it). Queued earlier, at
+  // the end of the forward, it was measured four times slower: started alone, it then ran beside
+  // the blend backward at a fraction of its speed and kept the projection backward waiting.
   cudaEvent_t join = nullptr;
   if (g->n > 0) {
     const FillSpans f = grad_spans(g, grads);
     if ((ctx->prezero_requested || ctx->prezero_pending) && same_spans(f, ctx->prezero)) {
-      e = start_prezero(ctx, s);  // not queued by a forward yet: now
+      e = start_prezero(ctx, s);
       if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
       join = ctx->ev_prezero;
     } else {
-      e = enqueue_fill(ctx, f, s, ctx->ev_join);
+      // arrays requested for zeroing other than these: zero them too, ordered before what follows
+      e = start_prezero(ctx, s);
+      if (e == cudaSuccess && ctx->prezero_pending) e = cudaStreamWaitEvent(s, ctx->ev_prezero, 0);
+      if (e == cudaSuccess) e = enqueue_fill(ctx, f, s, ctx->ev_join);
       if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
       join = ctx->ev_join;
     }
   }
-  ctx->prezero_pending = false;  // a request this backward did not use is dropped
+  if (g->n == 0) {
+    e = start_prezero(ctx, s);
+    if (e == cudaSuccess && ctx->prezero_pending) e = cudaStreamWaitEvent(s, ctx->ev_prezero, 0);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "join");
+  }
+  ctx->prezero_pending = false;  // the request is done with
   ctx->prezero_requested = false;
   BlendBwdIn bi;
   bi.d_rgb = dout->rgb;

@@ -144,18 +144,21 @@ constexpr int kMlpParams = kMlpB2 + kMlpOut;    // 1700
 struct PreOut {
   Rec* rec;                    // [cap_v]
   uint32_t* owner;             // [cap_v] rendered index of the Gaussian of each record
+  uint8_t* rcam;               // [cap_v] camera of each record (between the passes)
+  uint32_t* vis;               // [n_render] camera bits of each Gaussian's visible records
+  uint32_t* counts;            // [blocks] records per cull block, then each block's first record
   // the global-sort binning only (null otherwise): depth keys and record indices for the depth
   // sort, tiles in each record's rectangle, and the keys' digit counts [4][256] (added to)
   uint32_t* depth_keys;
   uint32_t* depth_vals;
   uint32_t* touched;
   uint32_t* key_counts;
-  unsigned long long* status;  // [blocks] chained-scan status words (epoch-tagged)
-  uint32_t* counter;           // dynamic block index
+  // the per-tile binning only (null otherwise): per-tile pair counts, added to (zeroed before),
+  // with or without the StopThePop tile cull
+  uint32_t* tile_ctr;
+  int tile_cull;
   uint32_t* v_total;           // out: V
   int* err;
-  uint32_t epoch;              // tag of this launch's status words
-  WaitCfg wait;
 };
 
 struct Grad2D {  // per visible record: 12 floats, three float4
@@ -176,12 +179,13 @@ struct ParamGrads {
 
 // ---- host-side launchers (one per translation unit) -------------------------------------
 
-// dense: many Gaussians expected to survive the culls (picks the variant budgeted for the
-// per-record work over the one budgeted for the scan over all Gaussians; results are the same).
+// The forward preprocess: the cull pass over all Gaussians (`blocks` blocks of kPreTile), the
+// scan of its block counts, the compaction of the records' (Gaussian, camera), then the record
+// pass over the visible records (`rec_blocks` blocks, grid-stride).
 void launch_preprocess_fwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased,
-                           const PreOut& out, int blocks, bool dense, cudaStream_t s);
-void launch_preprocess_fwd_dense(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased,
-                                 const PreOut& out, int blocks, cudaStream_t s);
+                           const PreOut& out, int blocks, int rec_blocks, cudaStream_t s);
+void launch_preprocess_rec(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased,
+                           const PreOut& out, int rec_blocks, cudaStream_t s);
 constexpr int kFillSpans = 8;
 struct FillSpans {
   float* ptr[kFillSpans];
@@ -248,15 +252,15 @@ void radix_sort_u32(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
                     const uint32_t* d_n, long long max_n, int begin_bit, int end_bit, const SortScratch& sc,
                     uint32_t epoch, bool clear_status, bool counts_ready, int* err, cudaStream_t s);
 
-// Binning of the V visible records (V read from *d_n, at most max_n) into (tile, record) pairs:
-// launch_bin_pairs with keys == nullptr adds each tile's pair count to tile_ctr (zeroed before;
-// ranges unused);
+// Binning of the V visible records (V read from *d_n, at most max_n) into (tile, record) pairs,
+// once the preprocess's record pass has added each tile's pair count to tile_ctr (PreOut):
 // launch_tile_scan turns the counts into ranges [start, end), P (*p_total), the largest count
 // (*max_count, zeroed before), the list of tiles with more than kTileSortSmall pairs (big,
-// *n_big zeroed before) and per-tile cursors (in tile_ctr); launch_bin_pairs with keys
-// places each pair's key (depth bits << 32 | record) in its tile's range (a pair past the range end
-// sets kErrOverflow in *err and is not written); launch_tile_sort sorts
-// every tile's keys and writes the records in that order into vals. Tiles with more than
+// *n_big zeroed before) and per-tile cursors (in tile_ctr); launch_bin_pairs places each pair's
+// key (depth bits << 32 | record) in its tile's range (a pair past the range end sets
+// kErrOverflow in *err and is not written); launch_tile_sort sorts every tile's keys (with
+// small = false only the listed tiles of more than kTileSortSmall pairs: the forward blend sorts
+// the others) and writes the records in that order into vals. Tiles with more than
 // kTileSortCap pairs are sorted in runs merged through `scratch` ([P], null when max_count is
 // at most kTileSortCap).
 constexpr int kScanThreads = 256;
@@ -271,7 +275,7 @@ void launch_tile_scan(uint32_t* tile_ctr, uint2* ranges, int n_tiles, unsigned l
                       int* err, WaitCfg wait, int grid_cap, cudaStream_t s);
 void launch_tile_sort(unsigned long long* keys, const uint2* ranges, int n_tiles, uint32_t* vals,
                       unsigned long long* scratch, uint32_t max_count, const uint32_t* big, const uint32_t* n_big,
-                      int grid_cap, cudaStream_t s);
+                      bool small, int grid_cap, cudaStream_t s);
 
 // The global-sort binning (gsr_opts.global_sort). pair_offsets_scan: exclusive scan of per-record
 // tile counts in depth order (counts[i] = touched[order[i]], or cnt_sorted[i] when given) into
@@ -298,8 +302,11 @@ struct BlendFwdOut {
   float2* D_state;  // per pixel: depth of the first contributor, sum of (z - that depth) w
 };
 // counters (nullable): [0] evaluations, [1] contributions (forward), [2], [3] (backward)
-void launch_blend_fwd(const Rec* rec, const uint32_t* pair_vals, const uint2* ranges, const CamBatch& cams,
-                      const float* bg, const BlendFwdOut& out, unsigned long long* counters, cudaStream_t s);
+// tile_keys (nullable): sort the lists of at most kTileSortSmall pairs in the blend from these
+// unsorted keys (max_count: the longest list) and write their record order to pair_vals.
+void launch_blend_fwd(const Rec* rec, uint32_t* pair_vals, const unsigned long long* tile_keys, uint32_t max_count,
+                      const uint2* ranges, const CamBatch& cams, const float* bg, const BlendFwdOut& out,
+                      unsigned long long* counters, cudaStream_t s);
 
 struct BlendBwdIn {
   const float* d_rgb;

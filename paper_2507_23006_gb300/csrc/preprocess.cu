@@ -8,11 +8,12 @@
 //   harmonics. Culled: z outside (near, far), a zero or non-finite quaternion, det <= 0, an
 //   empty rectangle, any non-finite output.
 //
-// One thread owns one Gaussian and loops over the cameras, so each attribute is read from HBM
-// once per launch. Visible (camera, Gaussian) records are written compacted, in (block, thread,
-// camera) order, with the block offsets from a single-pass chained scan (Merrill & Garland
-// decoupled look-back) whose waits are bounded; within one camera the compacted index grows
-// with the Gaussian index, which gives the depth sort its tie-break.
+// The cull pass: one thread owns one Gaussian and loops over the cameras, so the means and
+// scales are read from HBM once per launch. Visible (Gaussian, camera) records are numbered
+// compacted, in (Gaussian, camera) order, from the scanned per-block counts (three passes, no
+// block waits on another); within one camera the compacted index grows with the Gaussian index,
+// which gives the depth sort its tie-break. The record pass (preprocess_rec.cu) then makes each
+// numbered record with a thread of its own.
 #include <algorithm>
 #include <atomic>
 
@@ -376,9 +377,6 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_bwd_kernel(GaussArgs A, CamBa
   }
 }
 
-// The variant for launches where few Gaussians survive the culls (an aerial view of a large
-// scene): more resident blocks for the scan over all Gaussians. The one for dense launches is
-// in preprocess_dense.cu.
 // The transform of Gaussians [0, n) for one image embedding (A.iemb points at its row).
 __global__ void __launch_bounds__(256) mlp_cache_kernel(GaussArgs A, long long n, float4* __restrict__ out) {
   __shared__ MlpSmem M;
@@ -393,13 +391,10 @@ __global__ void __launch_bounds__(256) mlp_cache_kernel(GaussArgs A, long long n
   }
 }
 
-template <typename AT, typename ST>
-void launch_fwd_t(const GaussArgs& g, const CamBatch& cams, float eps, int aa, const PreOut& out, int blocks,
-                  cudaStream_t s) {
-  if (g.mlp || g.mlp_cached)
-    preprocess_fwd_kernel<AT, ST, true, 4><<<blocks, kPreThreads, 0, s>>>(g, cams, eps, aa, out);
-  else
-    preprocess_fwd_kernel<AT, ST, false, 5><<<blocks, kPreThreads, 0, s>>>(g, cams, eps, aa, out);
+template <typename AT>
+void launch_cull_t(const GaussArgs& g, const CamBatch& cams, float eps, int aa, const PreOut& out, int blocks,
+                   cudaStream_t s) {
+  preprocess_cull_kernel<AT, 5><<<blocks, kPreThreads, 0, s>>>(g, cams, eps, aa, out);
 }
 
 template <typename AT, typename ST>
@@ -413,23 +408,15 @@ void launch_bwd_t(const GaussArgs& g, const CamBatch& cams, float eps, int aa, l
 }  // namespace
 
 void launch_preprocess_fwd(const GaussArgs& g, const CamBatch& cams, float eps2d, int antialiased,
-                           const PreOut& out, int blocks, bool dense, cudaStream_t s) {
+                           const PreOut& out, int blocks, int rec_blocks, cudaStream_t s) {
   if (blocks <= 0) return;
-  if (dense) {
-    launch_preprocess_fwd_dense(g, cams, eps2d, antialiased, out, blocks, s);
-    return;
-  }
-#define GSR_PRE(AT, ST) launch_fwd_t<AT, ST>(g, cams, eps2d, antialiased, out, blocks, s)
-  if (g.attr_dtype == 0 && g.sh_dtype == 0) GSR_PRE(float, float);
-  else if (g.attr_dtype == 0 && g.sh_dtype == 1) GSR_PRE(float, __half);
-  else if (g.attr_dtype == 0 && g.sh_dtype == 2) GSR_PRE(float, __nv_bfloat16);
-  else if (g.attr_dtype == 1 && g.sh_dtype == 1) GSR_PRE(__half, __half);
-  else if (g.attr_dtype == 2 && g.sh_dtype == 2) GSR_PRE(__nv_bfloat16, __nv_bfloat16);
-  else if (g.attr_dtype == 1 && g.sh_dtype == 0) GSR_PRE(__half, float);
-  else if (g.attr_dtype == 2 && g.sh_dtype == 0) GSR_PRE(__nv_bfloat16, float);
-  else if (g.attr_dtype == 1 && g.sh_dtype == 2) GSR_PRE(__half, __nv_bfloat16);
-  else GSR_PRE(__nv_bfloat16, __half);
-#undef GSR_PRE
+  if (g.attr_dtype == 0) launch_cull_t<float>(g, cams, eps2d, antialiased, out, blocks, s);
+  else if (g.attr_dtype == 1) launch_cull_t<__half>(g, cams, eps2d, antialiased, out, blocks, s);
+  else launch_cull_t<__nv_bfloat16>(g, cams, eps2d, antialiased, out, blocks, s);
+  preprocess_offsets_kernel<<<1, kOffsetsThreads, 0, s>>>(out.counts, blocks, out.v_total, out.err);
+  preprocess_compact_kernel<<<blocks, kPreThreads, 0, s>>>(g.n_render, out.vis, out.counts, out.v_total, out.owner,
+                                                           out.rcam);
+  launch_preprocess_rec(g, cams, eps2d, antialiased, out, rec_blocks, s);
 }
 
 // Zero fill of up to kFillSpans float arrays in one launch: each block writes 16 KB chunks (16-byte

@@ -1,12 +1,13 @@
 // Device code shared by the preprocess kernels: spherical harmonics, attribute loads, the
 // projection (Sec. 3.1, Eq. 1) and its culls, the record layout, the appearance transform
-// (Sec. 3.5.1) and the forward preprocess kernel template. Included by the translation units
-// that instantiate the forward kernel (two occupancy targets) and by the backward kernels.
+// (Sec. 3.5.1) and the two forward preprocess kernel templates. Included by the translation units
+// that instantiate the forward kernels and by the backward kernels.
 #pragma once
 #include <type_traits>
 
 #include "gsr_internal.cuh"
 #include "scan_util.cuh"
+#include "tile_util.cuh"
 
 namespace gsr {
 namespace {
@@ -280,6 +281,40 @@ __device__ __forceinline__ void eval_color(const GaussArgs& A, long long g, cons
   rgb[0] = fmaxf(v0, 0.f); rgb[1] = fmaxf(v1, 0.f); rgb[2] = fmaxf(v2, 0.f);
 }
 
+// eval_color with the SH row read as twelve 16-byte loads when it is FP32 and 16-byte aligned
+// (A.sh_vec4); each channel sums its terms in the same order as eval_color, so the bits agree.
+template <typename ST>
+__device__ __forceinline__ void eval_color_vec(const GaussArgs& A, long long g, const Geo& G, const DevCam& c,
+                                               float rgb[3], float dir[3], float& dnorm, float Y[16],
+                                               bool clamped[3]) {
+  if (!(std::is_same<ST, float>::value && A.sh_vec4)) {
+    eval_color<ST>(A, g, G, c, rgb, dir, dnorm, Y, clamped);
+    return;
+  }
+  const float dx = G.m[0] - c.center[0], dy = G.m[1] - c.center[1], dz = G.m[2] - c.center[2];
+  dnorm = sqrtf(dx * dx + dy * dy + dz * dz);
+  const float inv = 1.f / dnorm;
+  dir[0] = dx * inv; dir[1] = dy * inv; dir[2] = dz * inv;
+  sh_basis(A.deg, dir[0], dir[1], dir[2], Y);
+  const int n3 = (A.deg + 1) * (A.deg + 1) * 3;
+  const float4* row = reinterpret_cast<const float4*>(static_cast<const float*>(A.sh) + g * A.K * 3);
+  float v[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+  for (int q = 0; q < 12; ++q) {
+    if (4 * q < n3) {
+      const float4 w = __ldg(row + q);
+      const float e[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int el = 4 * q + r;  // coefficient el / 3, channel el % 3
+        if (el < n3) v[el % 3] = fmaf(e[r], Y[el / 3], v[el % 3]);
+      }
+    }
+  }
+  clamped[0] = v[0] < 0.f; clamped[1] = v[1] < 0.f; clamped[2] = v[2] < 0.f;
+  rgb[0] = fmaxf(v[0], 0.f); rgb[1] = fmaxf(v[1], 0.f); rgb[2] = fmaxf(v[2], 0.f);
+}
+
 // The Gaussian's SH coefficients of degree <= deg, in registers (zero beyond them).
 template <typename ST>
 __device__ __forceinline__ void load_sh_row(const GaussArgs& A, long long g, float shv[48]) {
@@ -347,9 +382,9 @@ __device__ __forceinline__ Rec record_geometry(const Proj& P, int c, float eps) 
   return rr;
 }
 
-__device__ __forceinline__ void write_record(const PreOut& out, long long v, const Rec& rr, long long i) {
+// The record (its owner was written by the cull pass) and the global-sort inputs.
+__device__ __forceinline__ void write_record(const PreOut& out, long long v, const Rec& rr) {
   out.rec[v] = rr;
-  out.owner[v] = static_cast<uint32_t>(i);
   if (out.depth_keys) {  // the global-sort binning's inputs
     const uint32_t lo = __float_as_uint(rr.c.z), hi = __float_as_uint(rr.c.w);
     out.depth_keys[v] = __float_as_uint(rr.a.w);
@@ -480,49 +515,37 @@ __device__ __forceinline__ void list_append(bool pred, uint32_t slot, uint32_t* 
   if (pred) list[base + __popc(bal & ((1u << lane) - 1u))] = slot;
 }
 
-constexpr int kPreStage = 256;  // records a block keeps in shared memory between its phases
-
-// One block covers kPreTile = 1024 consecutive Gaussians, four per thread (thread t owns slot
-// j * 256 + t, i = base + slot, so each load instruction is coalesced).
-//   1a: a cheap conservative test per (Gaussian, camera) drops what is certainly outside; the
-//       survivors' slots go to a block-wide list.
-//   1b: the block's threads share out the list for the exact projection (full warps however
-//       sparse the survivors are); the geometry of each visible (Gaussian, camera) record is
-//       staged in shared memory.
-//   The block's record counts are scanned in slot order and the block total is published for
-//   its successors at once. The colour of the staged records is evaluated while the
-//   predecessors finish; then one warp takes the block's offset (decoupled look-back) and the
-//   staged records are written at their places, so the records are in (i, camera) order.
-//   Records beyond the stage's capacity are computed again in full after the offset is known.
-// kMlp: with the appearance transform (A.mlp and the embeddings are set).
-// kMinBlocks: resident blocks per SM the registers are budgeted for (more blocks hide more of
-// the scan over all Gaussians; fewer leave more registers for the per-record work).
-template <typename AT, typename ST, bool kMlp, int kMinBlocks>
-__global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_fwd_kernel(GaussArgs A, CamBatch cams, float eps, int aa,
-                                                                       PreOut out) {
-  __shared__ unsigned s_bid;
-  __shared__ unsigned long long s_excl;
-  __shared__ uint32_t s_count[2];         // survivors of the cheap test; visible records
-  __shared__ uint32_t s_list[kPreTile];   // slots of the survivors
-  __shared__ uint32_t s_aux[kPreTile];    // 1a: cameras surviving the cheap test; then first record per slot
-  __shared__ uint32_t s_mask[kPreTile];   // exact visibility bits per slot
-  __shared__ uint32_t s_unstaged[kPreTile / 32];
-  __shared__ float4 s_rec[kPreStage][4];
-  __shared__ uint32_t s_meta[kPreStage];  // slot | camera << 16
-  __shared__ MlpSmem s_mlp;                // appearance transform, when on
-  __shared__ uint32_t s_digits[4 * 256];   // digit counts of the block's depth keys (global sort)
-  if (threadIdx.x == 0) {
-    s_bid = atomicAdd(out.counter, 1u);
-    s_count[0] = 0;
-    s_count[1] = 0;
-  }
-  if (kMlp && !A.mlp_cached) mlp_load_smem(A, cams.C, s_mlp);  // read after the barrier that ends phase 1a
-  if (threadIdx.x < kPreTile / 32) s_unstaged[threadIdx.x] = 0;
-  if (out.key_counts)
-    for (int k = threadIdx.x; k < 4 * 256; k += kPreThreads) s_digits[k] = 0;
+// The forward preprocess runs as four kernels, none of which waits on another block.
+//
+// preprocess_cull_kernel: block b covers kPreTile = 1024 consecutive Gaussians, four per thread
+// (thread t owns slot j * 256 + t, i = b * 1024 + slot, so each load instruction is coalesced).
+//   1a: a cheap conservative test per (Gaussian, camera) on the means and scales drops what is
+//       certainly outside; the survivors' slots go to a block-wide list.
+//   1b: the block's threads share out the list for the exact projection test (full warps however
+//       sparse the survivors are), which decides visibility per camera.
+//   Each Gaussian's camera bits go to vis[i], the block's record count to counts[b].
+// preprocess_offsets_kernel (one block): counts[] becomes each block's first record index, the
+//   total is V.
+// preprocess_compact_kernel: block b scans its Gaussians' record counts in slot order and writes
+//   the (Gaussian, camera) of each of its records at the record's index, so the records are in
+//   (i, camera) order.
+// preprocess_rec_kernel: one thread per visible record (grid-stride) loads its Gaussian again,
+//   repeats the projection (the same computation, so the same bits), evaluates the colour (and
+//   the appearance transform) and writes the 64-byte record. Every thread of this pass has a
+//   record to make, so its scattered loads of the attribute and SH rows overlap across the
+//   whole GPU. With out.tile_ctr set it also counts the records' (tile, record) pairs per tile
+//   for the per-tile binning (warp_bin_pairs).
+template <typename AT, int kMinBlocks>
+__global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_cull_kernel(GaussArgs A, CamBatch cams,
+                                                                                  float eps, int aa, PreOut out) {
+  __shared__ uint32_t s_count;
+  __shared__ uint32_t s_list[kPreTile];  // slots of the survivors of the cheap test
+  __shared__ uint32_t s_aux[kPreTile];   // cameras surviving the cheap test
+  __shared__ uint32_t s_mask[kPreTile];  // exact visibility bits per slot
+  __shared__ uint32_t s_warp[kPreThreads / 32];
+  if (threadIdx.x == 0) s_count = 0;
   __syncthreads();
-  const unsigned bid = s_bid;
-  const long long base_i = static_cast<long long>(bid) * kPreTile;
+  const long long base_i = static_cast<long long>(blockIdx.x) * kPreTile;
   const int lane = threadIdx.x & 31;
   {
     Geo G[kPreItems];
@@ -544,132 +567,133 @@ __global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_fwd_kernel
           if (((seg_cams[j] >> c) & 1u) && !surely_culled(G[j], cams.cam[c], eps)) maybe |= 1u << c;
       s_aux[slot] = maybe;
       s_mask[slot] = 0;
-      list_append(maybe != 0, slot, s_list, &s_count[0], lane);
+      list_append(maybe != 0, slot, s_list, &s_count, lane);
     }
   }
   __syncthreads();
-  const uint32_t n_maybe = s_count[0];
+  const uint32_t n_maybe = s_count;
   for (uint32_t k = threadIdx.x; k < n_maybe; k += kPreThreads) {
     const uint32_t slot = s_list[k];
     const uint32_t maybe = s_aux[slot];
     Geo G;
     uint32_t vis = 0;
-    const long long gi = seg_map(A.segs, base_i + slot);
-    if (load_geo<AT>(A, gi, G)) {
+    if (load_geo<AT>(A, seg_map(A.segs, base_i + slot), G)) {
       for (int c = 0; c < cams.C; ++c) {
         if (!(maybe & (1u << c))) continue;
         Proj P;
-        if (!project(G, cams.cam[c], eps, aa, P)) continue;
-        vis |= 1u << c;
-        const uint32_t e = atomicAdd(&s_count[1], 1u);
-        if (e < kPreStage) {
-          Rec rr = record_geometry(P, c, eps);
-          rr.b.w = rr.c.x = rr.c.y = 1.f;  // colour gains until the colour is evaluated
-          // with the appearance transform the opacity (and so the alpha box) is final only
-          // after the colour phase: keep the dilated variances the box is made from
-          if (kMlp) rr.d = make_float4(P.ar + eps, P.cr + eps, 0.f, 0.f);
-          s_rec[e][0] = rr.a;
-          s_rec[e][1] = rr.b;
-          s_rec[e][2] = rr.c;
-          s_rec[e][3] = rr.d;
-          s_meta[e] = slot | (static_cast<uint32_t>(c) << 16);
-        } else {
-          atomicOr(&s_unstaged[slot >> 5], 1u << (slot & 31));
-        }
+        if (project(G, cams.cam[c], eps, aa, P)) vis |= 1u << c;
       }
     }
     s_mask[slot] = vis;
   }
   __syncthreads();
+  uint32_t n = 0;
+#pragma unroll
+  for (int j = 0; j < kPreItems; ++j) {
+    const long long i = base_i + j * kPreThreads + threadIdx.x;
+    const uint32_t m = s_mask[j * kPreThreads + threadIdx.x];
+    if (i < A.n_render) out.vis[i] = m;
+    n += __popc(m);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+  if (lane == 0) s_warp[threadIdx.x >> 5] = n;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int w = 0; w < kPreThreads / 32; ++w) tot += s_warp[w];
+    out.counts[blockIdx.x] = tot;
+  }
+}
+
+// One block of kOffsetsThreads: counts[0, nb) become exclusive prefix sums (each cull block's
+// first record), *v_total = V. A record index past 2^32 sets kErrOverflow.
+constexpr int kOffsetsThreads = 1024;
+__global__ void __launch_bounds__(kOffsetsThreads) preprocess_offsets_kernel(uint32_t* __restrict__ counts, int nb,
+                                                                             uint32_t* v_total, int* err) {
+  const int per = (nb + kOffsetsThreads - 1) / kOffsetsThreads;
+  const int first = threadIdx.x * per;
+  unsigned long long sum = 0;
+#pragma unroll 4
+  for (int k = first; k < min(first + per, nb); ++k) sum += counts[k];
+  unsigned long long tot;
+  unsigned long long run = block_excl_scan64(sum, &tot);
+  for (int k = first; k < min(first + per, nb); ++k) {
+    const uint32_t c = counts[k];
+    counts[k] = static_cast<uint32_t>(run);
+    run += c;
+  }
+  if (threadIdx.x == 0) {
+    if (tot > 0xffffffffull) atomicOr(err, kErrOverflow);
+    *v_total = static_cast<uint32_t>(tot);
+  }
+}
+
+// Block b: the records of its Gaussians, numbered in (i, camera) order from offsets[b]; a block
+// with none (offsets[b] equal to the next block's first record, or to V) reads nothing more.
+__global__ void __launch_bounds__(kPreThreads) preprocess_compact_kernel(long long n_render,
+                                                                         const uint32_t* __restrict__ vis,
+                                                                         const uint32_t* __restrict__ offsets,
+                                                                         const uint32_t* __restrict__ v_total,
+                                                                         uint32_t* __restrict__ owner,
+                                                                         uint8_t* __restrict__ rcam) {
+  const uint32_t next = blockIdx.x + 1 < gridDim.x ? offsets[blockIdx.x + 1] : *v_total;
+  if (next == offsets[blockIdx.x]) return;  // block-uniform
+  const long long base_i = static_cast<long long>(blockIdx.x) * kPreTile;
   uint32_t mask[kPreItems];
   unsigned long long packed = 0;
 #pragma unroll
   for (int j = 0; j < kPreItems; ++j) {
-    mask[j] = s_mask[j * kPreThreads + threadIdx.x];
+    const long long i = base_i + j * kPreThreads + threadIdx.x;
+    mask[j] = i < n_render ? vis[i] : 0u;
     packed |= static_cast<unsigned long long>(__popc(mask[j])) << (16 * j);
   }
   unsigned long long tot_packed;
   const unsigned long long excl_packed = block_excl_scan64(packed, &tot_packed);
-  uint32_t total = 0;
+  long long v = offsets[blockIdx.x];
 #pragma unroll
   for (int j = 0; j < kPreItems; ++j) {
-    s_aux[j * kPreThreads + threadIdx.x] = total + static_cast<uint32_t>((excl_packed >> (16 * j)) & 0xffffu);
-    total += static_cast<uint32_t>((tot_packed >> (16 * j)) & 0xffffu);
-  }
-  if (threadIdx.x == 0) publish_aggregate(out.status, bid, total, out.epoch);
-  __syncthreads();
-  // colour of the staged records, while the predecessors finish
-  const uint32_t n_rec = s_count[1];
-  const uint32_t n_staged = n_rec < kPreStage ? n_rec : kPreStage;
-  for (uint32_t e = threadIdx.x; e < n_staged; e += kPreThreads) {
-    const uint32_t meta = s_meta[e];
-    const long long g = seg_map(A.segs, base_i + (meta & 0xffffu));
-    Geo G;
-    G.m[0] = __ldg(A.means + 3 * g + 0);
-    G.m[1] = __ldg(A.means + 3 * g + 1);
-    G.m[2] = __ldg(A.means + 3 * g + 2);
-    float mo[kMlpOut];
-    if (kMlp) mlp_outputs(A, s_mlp, g, static_cast<int>(meta >> 16), mo);  // only the four outputs stay live
-    float rgb[3], dir[3], dn, Y[16];
-    bool cl[3];
-    eval_color<ST>(A, g, G, cams.cam[meta >> 16], rgb, dir, dn, Y, cl);
-    if (kMlp) {
-      const float4 a = s_rec[e][0], d = s_rec[e][3];
-      const float op = a.z * (1.f - mo[3]);
-      s_rec[e][0].z = op;
-      s_rec[e][3] = alpha_box(a.x, a.y, op, d.x, d.y);
-      rgb[0] *= 2.f * mo[0];
-      rgb[1] *= 2.f * mo[1];
-      rgb[2] *= 2.f * mo[2];
+    long long r = v + static_cast<long long>((excl_packed >> (16 * j)) & 0xffffu);
+    uint32_t m = mask[j];
+    const uint32_t i = static_cast<uint32_t>(base_i + j * kPreThreads + threadIdx.x);
+    while (m) {
+      const int c = __ffs(m) - 1;
+      m &= m - 1u;
+      owner[r] = i;
+      rcam[r] = static_cast<uint8_t>(c);
+      ++r;
     }
-    s_rec[e][1].w = rgb[0];
-    s_rec[e][2].x = rgb[1];
-    s_rec[e][2].y = rgb[2];
+    v += static_cast<long long>((tot_packed >> (16 * j)) & 0xffffu);
   }
-  if (threadIdx.x < 32) {
-    const unsigned long long ex = warp_lookback(out.status, bid, total, out.epoch, out.err, out.wait);
-    if (threadIdx.x == 0) s_excl = ex;
-  }
-  __syncthreads();
-  const unsigned long long block_base = s_excl;
-  if (threadIdx.x == 0 && base_i <= A.n_render - 1 && A.n_render - 1 < base_i + kPreTile)
-    *out.v_total = static_cast<uint32_t>(block_base + total);
-  for (uint32_t e = threadIdx.x; e < n_staged; e += kPreThreads) {
-    const uint32_t meta = s_meta[e];
-    const uint32_t slot = meta & 0xffffu, c = meta >> 16;
-    // a Gaussian with a record that did not fit the stage has all of its records written below
-    if ((s_unstaged[slot >> 5] >> (slot & 31)) & 1u) continue;
-    const long long v = block_base + s_aux[slot] + __popc(s_mask[slot] & ((1u << c) - 1u));
-    Rec rr;
-    rr.a = s_rec[e][0];
-    rr.b = s_rec[e][1];
-    rr.c = s_rec[e][2];
-    rr.d = s_rec[e][3];
-    write_record(out, v, rr, base_i + slot);
-    if (out.key_counts) count_digits(__float_as_uint(rr.a.w), 0, 32, 4, s_digits);
-  }
-  if (n_rec <= kPreStage) {  // block-uniform
-    if (out.key_counts) {
-      __syncthreads();
-      flush_digit_counts(s_digits, 4, out.key_counts);
-    }
-    return;
-  }
-  // records that did not fit the stage: every record of those Gaussians is computed again
-  for (uint32_t k = threadIdx.x; k < n_maybe; k += kPreThreads) {
-    const uint32_t slot = s_list[k];
-    if (!((s_unstaged[slot >> 5] >> (slot & 31)) & 1u)) continue;
-    const uint32_t vis = s_mask[slot];
-    const long long i = base_i + slot;
-    const long long g = seg_map(A.segs, i);
-    Geo G;
-    load_geo<AT>(A, g, G);
-    long long v = block_base + s_aux[slot];
-    for (int c = 0; c < cams.C; ++c) {
-      if (!(vis & (1u << c))) continue;
+}
+
+template <typename AT, typename ST, bool kMlp>
+__global__ void __launch_bounds__(kPreThreads, 4) preprocess_rec_kernel(GaussArgs A, CamBatch cams, float eps, int aa,
+                                                                     PreOut out) {
+  __shared__ MlpSmem s_mlp;                // appearance transform, when on
+  __shared__ uint32_t s_digits[4 * 256];   // digit counts of the block's depth keys (global sort)
+  if (kMlp && !A.mlp_cached) mlp_load_smem(A, cams.C, s_mlp);
+  if (out.key_counts)
+    for (int k = threadIdx.x; k < 4 * 256; k += kPreThreads) s_digits[k] = 0;
+  if (kMlp || out.key_counts) __syncthreads();
+  const long long V = static_cast<long long>(*out.v_total);
+  const int lane = threadIdx.x & 31;
+  const long long stride = static_cast<long long>(gridDim.x) * kPreThreads;
+  // warps stride over the records 32 at a time, so the pair count below has whole warps
+  for (long long base = static_cast<long long>(blockIdx.x) * kPreThreads + (threadIdx.x & ~31); base < V;
+       base += stride) {
+    const long long v = base + lane;
+    const bool has = v < V;
+    Rec rr{};
+    if (has) {
+      const uint32_t i = out.owner[v];
+      const int c = out.rcam[v];
+      const long long g = seg_map(A.segs, i);
       const DevCam& cam = cams.cam[c];
+      Geo G;
+      load_geo<AT>(A, g, G);
       Proj P;
-      project(G, cam, eps, aa, P);
+      project(G, cam, eps, aa, P);  // visible: the cull pass made the same decision
       float mo[kMlpOut] = {0.5f, 0.5f, 0.5f, 0.f};
       if (kMlp) {
         mlp_outputs(A, s_mlp, g, c, mo);
@@ -677,14 +701,21 @@ __global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_fwd_kernel
       }
       float rgb[3], dir[3], dn, Y[16];
       bool cl[3];
-      eval_color<ST>(A, g, G, cam, rgb, dir, dn, Y, cl);
-      Rec rr = record_geometry(P, c, eps);
+      eval_color_vec<ST>(A, g, G, cam, rgb, dir, dn, Y, cl);
+      rr = record_geometry(P, c, eps);
       rr.b.w = 2.f * mo[0] * rgb[0];
       rr.c.x = 2.f * mo[1] * rgb[1];
       rr.c.y = 2.f * mo[2] * rgb[2];
-      write_record(out, v, rr, i);
+      write_record(out, v, rr);
       if (out.key_counts) count_digits(__float_as_uint(rr.a.w), 0, 32, 4, s_digits);
-      ++v;
+    }
+    if (out.tile_ctr) {  // the per-tile binning's counting pass, on the records just made
+      if (out.tile_cull)
+        warp_bin_pairs<true, false>(lane, has, rr, static_cast<uint32_t>(base), cams, out.tile_ctr, nullptr, nullptr,
+                                    out.err);
+      else
+        warp_bin_pairs<false, false>(lane, has, rr, static_cast<uint32_t>(base), cams, out.tile_ctr, nullptr, nullptr,
+                                     out.err);
     }
   }
   if (out.key_counts) {

@@ -542,7 +542,8 @@ def appearance_cache(ctx: Context, g: Gaussians, image: int = 0, out: Optional[t
 
 def zero_param_grads(ctx: Context, g: Gaussians, grads: dict, stream=None):
     """Requests the zero fill of the gradient arrays ahead of the backward (see
-    gsr_param_grads_zero): called before render_forward, the fill runs beside that forward."""
+    gsr_param_grads_zero): the next backward given these arrays queues the fill right before its
+    blend, which it runs beside."""
     cg, seg_keep = g.c_struct()
     pg = _c_param_grads(grads)
     _check(ctx, load().gsr_param_grads_zero(ctx.handle, ctypes.byref(cg), ctypes.byref(pg), _stream(stream)))

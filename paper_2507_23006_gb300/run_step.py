@@ -67,7 +67,7 @@ def main():
 
     def step():
         if not a.fwd_only:
-            native.zero_param_grads(ctx, g, grads)  # beside the forward pass
+            native.zero_param_grads(ctx, g, grads)  # the backward zeroes them beside its blend
         out, st = native.render_forward(ctx, g, [cam], opts, want_state=not a.fwd_only)
         if st is not None:
             native.render_backward(ctx, g, [cam], st, d_out, opts, grads=grads)

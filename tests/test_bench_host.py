@@ -35,11 +35,15 @@ def test_stage_rooflines_pick_the_binding_resource():
 
 
 def test_kernels_per_step():
-    # preprocess, per-tile counts, tile scan, placing, per-tile sort, forward blend, gradient fill,
-    # backward blend, projection backward
-    assert bench.kernels_per_step(True, {"n_tiles": 8160, "n_visible": 10, "n_pairs": 20}) == 9
-    # nothing visible: no counting, placing or sorting
-    assert bench.kernels_per_step(False, {"n_tiles": 256, "n_visible": 0, "n_pairs": 0}) == 6
+    # preprocess (cull and record passes, the latter counting the pairs per tile), tile scan,
+    # placing, forward blend (which sorts the tiles' lists), gradient fill, backward blend,
+    # projection backward
+    assert bench.kernels_per_step(True, {"n_tiles": 8160, "n_visible": 10, "n_pairs": 20, "max_tile_pairs": 5}) == 8
+    # a list of more than 1024 pairs is sorted by a launch of its own before the blend
+    assert bench.kernels_per_step(True, {"n_tiles": 8160, "n_visible": 10, "n_pairs": 2000,
+                                         "max_tile_pairs": 1500}) == 9
+    # nothing visible: no placing or sorting
+    assert bench.kernels_per_step(False, {"n_tiles": 256, "n_visible": 0, "n_pairs": 0}) == 7
 
 
 def test_stored_counters_are_keyed_to_their_kernel_sources():

@@ -1,6 +1,7 @@
 """Failure detection without a GPU fault.
 
-* Device waits: every decoupled look-back of the chained scans and of the sort is bounded. A test
+* Device waits: every decoupled look-back of the chained scans (the tile scan, the global-sort
+  binning's scans) and of the sort is bounded. A test
   switch of the context (gsr_set_wait_limit) makes each look-back wait on status words that no
   block publishes, with a short limit: the kernels give up, finish, and the call that checks the
   context's error word reports GSR_ERR_DEVICE_TIMEOUT. Nothing hangs and nothing faults (a wait
@@ -13,7 +14,7 @@ import numpy as np
 import pytest
 import torch
 
-from paper_2507_23006_gb300 import native
+from paper_2507_23006_gb300 import native, scenes
 from tests import parity_util as pu
 
 pytestmark = pytest.mark.gpu
@@ -33,7 +34,9 @@ def _upstream(npix):
 
 
 def test_device_wait_timeout_is_reported_and_context_recovers(ctx):
-    scene, cam = pu.scene_box(6000, seed=31)
+    scene, _ = pu.scene_box(6000, seed=31)
+    # 4096 tiles: the tile scan runs as two blocks, so the second one looks back
+    cam = scenes.box_camera(1024, 1024, f=1200.0)
     g = native.Gaussians.from_scene(scene)
     opts = native.Options(tile_cull=True)
     ref, _ = native.render_forward(ctx, g, [cam], opts, want_state=False)

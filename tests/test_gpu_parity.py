@@ -315,9 +315,9 @@ def test_gradient_rows_unaligned_and_prefilled(ctx, shift):
 
 
 def test_param_grads_zeroed_ahead_of_the_forward(ctx):
-    """gsr_param_grads_zero before the forward: the backward with the same arrays skips its own
-    fill; a backward given other arrays fills them itself. Both are checked on NaN-prefilled
-    arrays against the oracle."""
+    """gsr_param_grads_zero before the forward: the backward with the same arrays zeroes them
+    (one fill); a backward given other arrays zeroes the requested ones too and fills its own.
+    Both are checked on NaN-prefilled arrays against the oracle."""
     scene, cam = pu.scene_box(8000, seed=22)
     m = np.array(scene.means, np.float64)
     m[::4, 2] = -5.0
@@ -352,7 +352,7 @@ def test_param_grads_zeroed_ahead_of_the_forward(ctx):
             assert (arr[hidden] == 0).all(), (k, same)
             pu.grad_close(arr, np.asarray(ref[k]).reshape(g.n, -1), f"{k} (same arrays: {same})",
                           mag=np.asarray(ref["mag"][k]).reshape(g.n, -1))
-        if not same:  # the arrays zeroed ahead were not used by the backward, but are zero
+        if not same:  # the arrays requested for zeroing were not used by the backward, but are zero
             assert all((a[k] == 0).all() for k in ("means", "scales", "quats", "opacities", "sh"))
 
 
@@ -501,24 +501,69 @@ def test_global_sort_gives_the_same_bits(ctx, which):
                       cancel_rel=1e-5)
 
 
-def test_preprocess_variants_agree():
-    """The preprocess has two register budgets (for launches where few Gaussians survive the
-    culls, and for dense ones), picked from the previous launch's survivor ratio: a fresh context
-    renders a dense scene first with the sparse variant, then with the dense one; the records
-    and images are the same bits."""
+@pytest.mark.parametrize("scale,size,f", [(4.0, (256, 256), 300.0), (25.0, (96, 80), 100.0)])
+def test_long_tile_lists(ctx, scale, size, f):
+    """Tile lists of more than 1024 pairs are sorted by a launch of their own before the forward
+    blend (lists over 16384 in runs merged through global memory), the shorter ones by the blend
+    itself. The first scene mixes both kinds, the second has lists of up to 19k pairs. Every list
+    is in (depth, record) order and has the same bits as the global radix-sort binning (records,
+    lists, ranges, last contributors, images); on the mixed scene the image matches the oracle."""
+    scene, _ = pu.scene_box(20_000, seed=21)
+    scene.scales = (np.asarray(scene.scales) * scale).astype(np.float32)
+    cam = scenes.box_camera(size[0], size[1], f=f)
+    g = native.Gaussians.from_scene(scene)
+    res = {}
+    for glob in (False, True):
+        opts = native.Options(tile_cull=True, global_sort=glob)
+        out, st = native.render_forward(ctx, g, [cam], opts)
+        ctx.sync_check()
+        res[glob] = (out, pu.state_arrays(st))
+    (o0, s0), (o1, s1) = res[False], res[True]
+    counts = np.diff(s0["ranges"], axis=1)[:, 0]
+    if scale < 10:
+        assert (counts > 1024).sum() > 0 and ((counts > 0) & (counts <= 1024)).sum() > 0
+    else:
+        assert counts.max() > 16384
+    assert s0["info"]["max_tile_pairs"] == counts.max()
+    depth_bits = s0["rec"][:, 3].view(np.uint32).astype(np.uint64)
+    for t in np.nonzero(counts)[0]:
+        v = s0["pair_vals"][s0["ranges"][t, 0]:s0["ranges"][t, 1]].astype(np.uint64)
+        key = (depth_bits[v] << np.uint64(32)) | v
+        assert np.all(key[1:] > key[:-1]), t
+    for k in ("rec", "g_of", "pair_vals", "ranges", "n_contrib", "T_final"):
+        np.testing.assert_array_equal(s0[k], s1[k], err_msg=k)
+    for k in ("rgb", "depth_acc", "depth_exp", "alpha"):
+        assert torch.equal(o0[k], o1[k]), k
+    if scale < 10:
+        ref = oracle.render(scene, [cam], oracle.Opts(tile_cull=True), want_pairs=False)
+        um = ref.mark == 0
+        assert um.mean() > 0.7
+        np.testing.assert_allclose(o0["rgb"].cpu().numpy()[um], ref.img[um, :3], atol=1e-4)
+        np.testing.assert_allclose(o0["alpha"].cpu().numpy()[um], ref.img[um, 5], atol=1e-4)
+
+
+def test_preprocess_record_order_and_repeatability():
+    """The cull pass numbers the visible (Gaussian, camera) records in (Gaussian, camera) order and
+    the record pass fills them in: over three cameras the owners never decrease and the cameras
+    of one Gaussian's records increase; a second launch gives the same bits."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     c2 = native.Context(0)
     scene, cam = pu.scene_box(6000, seed=23)
+    cams = [cam, scenes.box_camera(200, 120, f=250.0), scenes.box_camera(64, 64, f=120.0)]
     nopts, _ = pu.opts_pair(bg=(0.1, 0.2, 0.3))
     g = native.Gaussians.from_scene(scene)
-    out1, st1 = native.render_forward(c2, g, [cam], nopts)
-    rec1 = pu.state_arrays(st1)["rec"]
-    out2, st2 = native.render_forward(c2, g, [cam], nopts)
-    rec2 = pu.state_arrays(st2)["rec"]
+    out1, st1 = native.render_forward(c2, g, cams, nopts)
+    sa1 = pu.state_arrays(st1)
+    out2, st2 = native.render_forward(c2, g, cams, nopts)
+    sa2 = pu.state_arrays(st2)
     c2.sync_check()
-    assert st1.info()["n_visible"] > 0.25 * scene.n  # dense: the second launch took the other variant
-    np.testing.assert_array_equal(rec1.view(np.uint32), rec2.view(np.uint32))
+    own, cam_of = sa1["g_of"], sa1["cam_of"]
+    assert own.size > 0.25 * scene.n and np.unique(cam_of).size == 3
+    key = own * 4 + cam_of
+    assert np.all(key[1:] > key[:-1])
+    np.testing.assert_array_equal(sa1["rec"].view(np.uint32), sa2["rec"].view(np.uint32))
+    np.testing.assert_array_equal(sa1["g_of"], sa2["g_of"])
     for k in ("rgb", "alpha", "depth_acc"):
         assert torch.equal(out1[k], out2[k]), k
     c2.close()
