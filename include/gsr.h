@@ -273,6 +273,14 @@ gsr_status gsr_sync_check(gsr_ctx* ctx, gsr_stream stream);
  * Results are the same either way; only the timing changes. Errors: GSR_ERR_INVALID_ARG. */
 gsr_status gsr_set_fill_rate(gsr_ctx* ctx, float gb_per_s, int32_t blocks);
 
+/* Where a requested gradient fill (gsr_param_grads_zero) runs (no counterpart in the paper):
+ * the first early_share of its bytes (in the arrays' order: means, scales, quats, opacities, sh,
+ * absgrad, gauss_embed) is queued by the next forward right after its preprocess, beside the
+ * binning and the forward blend; the rest by the backward right before its blend. 0 (the
+ * default) queues all of it with the backward. Results are the same either way; only the
+ * timing changes. Errors: GSR_ERR_INVALID_ARG (outside [0, 1]). */
+gsr_status gsr_set_fill_split(gsr_ctx* ctx, float early_share);
+
 /* Failure detection (no counterpart in the paper). Every device wait of this context's kernels
  * (the decoupled look-backs of the chained scans and of the sort) gives up after `polls` polls
  * (0: the default, 2^20, well under a second), sets the context's error word and lets the kernel

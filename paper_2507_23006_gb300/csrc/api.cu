@@ -63,13 +63,16 @@ struct gsr_ctx {
   uint32_t epoch = 0;  // tag of the chained-scan status words of the latest launch
   // a second stream for work that overlaps the caller's (joined back before returning)
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_prezero = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_prezero = nullptr, ev_prezero_early = nullptr;
   FillSpans prezero{};           // gradient arrays to zero ahead (gsr_param_grads_zero)
-  bool prezero_requested = false;  // recorded, the fill not queued yet
-  bool prezero_pending = false;    // fill queued (ev_prezero marks its end), not used yet
+  bool prezero_requested = false;  // recorded, the rest of the fill not queued yet
+  bool prezero_pending = false;    // the rest queued (ev_prezero marks its end), not used yet
+  bool prezero_early = false;      // the first part queued by a forward (ev_prezero_early marks its end)
+  size_t prezero_queued = 0;       // floats of the requested fill queued so far
   int grid_cap = 304;  // resident blocks of the looping scan / sort kernels (2 per SM)
   int fill_blocks = 95;  // blocks of the gradient zero fill (5/8 of the SMs)
   float fill_gbs = 0.f;  // pace of the gradient zero fill in GB/s (0: unpaced); gsr_set_fill_rate
+  float fill_early = 0.f;  // share of a requested fill queued after the forward's preprocess
   WaitCfg wait;  // how the look-backs of this context's kernels wait (gsr_set_wait_limit)
   // default allocator: a context-owned stream-ordered pool (growth and release never
   // synchronise the device, which matters when several contexts serve concurrently)
@@ -344,13 +347,68 @@ cudaError_t enqueue_fill(gsr_ctx* ctx, const FillSpans& f, cudaStream_t s, cudaE
   return e;
 }
 
-// Queues a requested gradient fill (gsr_param_grads_zero) after the work queued on `s`.
+size_t spans_total(const FillSpans& f) {
+  size_t n = 0;
+  for (int k = 0; k < f.count; ++k) n += f.len[k];
+  return n;
+}
+
+// Floats [from, to) of the spans taken one after another.
+FillSpans slice_spans(const FillSpans& f, size_t from, size_t to) {
+  FillSpans out{};
+  size_t base = 0;
+  for (int k = 0; k < f.count; ++k) {
+    const size_t lo = std::max(from, base), hi = std::min(to, base + f.len[k]);
+    if (lo < hi) {
+      out.ptr[out.count] = f.ptr[k] + (lo - base);
+      out.len[out.count] = hi - lo;
+      ++out.count;
+    }
+    base += f.len[k];
+  }
+  return out;
+}
+
+// The first part (ctx->fill_early of the bytes) of a requested gradient fill
+// (gsr_param_grads_zero), queued after the work queued on `s` by a forward.
+cudaError_t start_prezero_early(gsr_ctx* ctx, cudaStream_t s) {
+  if (!ctx->prezero_requested || ctx->prezero_early || !(ctx->fill_early > 0.f)) return cudaSuccess;
+  const size_t total = spans_total(ctx->prezero);
+  const size_t to = std::min(total, static_cast<size_t>(static_cast<double>(total) * ctx->fill_early));
+  if (to == 0) return cudaSuccess;
+  const cudaError_t e = enqueue_fill(ctx, slice_spans(ctx->prezero, 0, to), s, ctx->ev_prezero_early);
+  if (e == cudaSuccess) {
+    ctx->prezero_early = true;
+    ctx->prezero_queued = to;
+  }
+  return e;
+}
+
+// The rest of a requested gradient fill, queued after the work queued on `s`.
 cudaError_t start_prezero(gsr_ctx* ctx, cudaStream_t s) {
   if (!ctx->prezero_requested) return cudaSuccess;
   ctx->prezero_requested = false;
-  const cudaError_t e = enqueue_fill(ctx, ctx->prezero, s, ctx->ev_prezero);
-  ctx->prezero_pending = e == cudaSuccess;
+  const size_t total = spans_total(ctx->prezero);
+  cudaError_t e = cudaSuccess;
+  if (ctx->prezero_queued < total) {
+    e = enqueue_fill(ctx, slice_spans(ctx->prezero, ctx->prezero_queued, total), s, ctx->ev_prezero);
+    ctx->prezero_pending = e == cudaSuccess;
+  }
+  ctx->prezero_queued = total;
   return e;
+}
+
+// Orders every queued part of a requested fill before the work queued on `s` next.
+cudaError_t join_prezero(gsr_ctx* ctx, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (ctx->prezero_early) e = cudaStreamWaitEvent(s, ctx->ev_prezero_early, 0);
+  if (e == cudaSuccess && ctx->prezero_pending) e = cudaStreamWaitEvent(s, ctx->ev_prezero, 0);
+  return e;
+}
+
+void clear_prezero(gsr_ctx* ctx) {
+  ctx->prezero_requested = ctx->prezero_pending = ctx->prezero_early = false;
+  ctx->prezero_queued = 0;
 }
 
 // The per-Gaussian fields of GaussArgs (everything but the count and the segment map).
@@ -484,8 +542,14 @@ gsr_status run_binning(gsr_ctx* ctx, const gsr_gaussians* g, const CamBatch& cb,
   }
   {
     StageTimer tm(ctx, GSR_STAGE_PREPROCESS, s);
-    launch_preprocess_fwd(ga, cb, o->eps2d, o->antialiased, po, pre_blocks, 4 * ctx->grid_cap, s);
+    // the record pass: a grid of 8 blocks per SM (twice the resident ones; 16 per SM was measured
+    // slower on the 6M city), never more than the records can use
+    const int rec_blocks = static_cast<int>(std::min<long long>((capv + kPreThreads - 1) / kPreThreads,
+                                                                 4LL * ctx->grid_cap));
+    launch_preprocess_fwd(ga, cb, o->eps2d, o->antialiased, po, pre_blocks, rec_blocks, s);
   }
+  e = start_prezero_early(ctx, s);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
   if (global) {
     // records by depth, then (tile-culled) counts and pair offsets in depth order
     if (N * C > 0) {
@@ -661,7 +725,8 @@ gsr_status gsr_create(gsr_ctx** out, int device, const gsr_allocator* alloc) {
   if (cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_prezero, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&ctx->ev_prezero, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_prezero_early, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     gsr_destroy(ctx);
     return GSR_ERR_CUDA;
@@ -695,6 +760,7 @@ void gsr_destroy(gsr_ctx* ctx) {
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->ev_prezero) cudaEventDestroy(ctx->ev_prezero);
+  if (ctx->ev_prezero_early) cudaEventDestroy(ctx->ev_prezero_early);
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->d_err) cudaFree(ctx->d_err);
@@ -860,12 +926,9 @@ gsr_status gsr_param_grads_zero(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
   // a fill queued for an earlier request still writes its arrays: order it before what follows
-  if (ctx->prezero_pending) {
-    e = cudaStreamWaitEvent(reinterpret_cast<cudaStream_t>(stream), ctx->ev_prezero, 0);
-    if (e != cudaSuccess) return cuda_err(ctx, e, "join");
-  }
-  ctx->prezero_pending = false;
-  ctx->prezero_requested = false;
+  e = join_prezero(ctx, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_err(ctx, e, "join");
+  clear_prezero(ctx);
   if (g->n == 0) return GSR_OK;
   ctx->prezero = grad_spans(g, grads);
   ctx->prezero_requested = true;
@@ -920,29 +983,23 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
   // runs beside (an ALU-bound kernel that leaves the memory bandwidth to it). Queued earlier, at
   // the end of the forward, it was measured four times slower: started alone, it then ran beside
   // the blend backward at a fraction of its speed and kept the projection backward waiting.
+  bool join_requested = false;  // the projection backward waits for the requested fill
   cudaEvent_t join = nullptr;
-  if (g->n > 0) {
-    const FillSpans f = grad_spans(g, grads);
-    if ((ctx->prezero_requested || ctx->prezero_pending) && same_spans(f, ctx->prezero)) {
-      e = start_prezero(ctx, s);
-      if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
-      join = ctx->ev_prezero;
-    } else {
-      // arrays requested for zeroing other than these: zero them too, ordered before what follows
-      e = start_prezero(ctx, s);
-      if (e == cudaSuccess && ctx->prezero_pending) e = cudaStreamWaitEvent(s, ctx->ev_prezero, 0);
-      if (e == cudaSuccess) e = enqueue_fill(ctx, f, s, ctx->ev_join);
-      if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
-      join = ctx->ev_join;
-    }
-  }
-  if (g->n == 0) {
+  const bool requested = ctx->prezero_requested || ctx->prezero_pending || ctx->prezero_early;
+  if (g->n > 0 && requested && same_spans(grad_spans(g, grads), ctx->prezero)) {
+    e = start_prezero(ctx, s);  // the rest of it, beside the blend
+    if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
+    join_requested = true;
+  } else {
+    // arrays requested for zeroing other than these (or none to fill here): zero them too,
+    // ordered before what follows
     e = start_prezero(ctx, s);
-    if (e == cudaSuccess && ctx->prezero_pending) e = cudaStreamWaitEvent(s, ctx->ev_prezero, 0);
-    if (e != cudaSuccess) return cuda_err(ctx, e, "join");
+    if (e == cudaSuccess) e = join_prezero(ctx, s);
+    if (e == cudaSuccess && g->n > 0) e = enqueue_fill(ctx, grad_spans(g, grads), s, ctx->ev_join);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
+    if (g->n > 0) join = ctx->ev_join;
+    clear_prezero(ctx);
   }
-  ctx->prezero_pending = false;  // the request is done with
-  ctx->prezero_requested = false;
   BlendBwdIn bi;
   bi.d_rgb = dout->rgb;
   bi.d_depth_acc = dout->depth_acc;
@@ -956,10 +1013,12 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
     launch_blend_bwd(as<Rec>(*bo.rec), as<uint32_t>(*bo.pvals_s), as<uint2>(*bo.ranges), cb, opts->bg, bi,
                      as<Grad2D>(ctx->g2d), grads->appearance, opts->absgrad && grads->absgrad, counters_of(ctx), s);
   }
-  if (join) {
-    e = cudaStreamWaitEvent(s, join, 0);
-    if (e != cudaSuccess) return cuda_err(ctx, e, "join");
+  if (join) e = cudaStreamWaitEvent(s, join, 0);
+  if (e == cudaSuccess && join_requested) {
+    e = join_prezero(ctx, s);
+    clear_prezero(ctx);
   }
+  if (e != cudaSuccess) return cuda_err(ctx, e, "join");
   GaussArgs ga;
   ga.n_render = N;
   // the segment table may have been overwritten by another call since the forward: upload it
@@ -1069,6 +1128,12 @@ gsr_status gsr_set_fill_rate(gsr_ctx* ctx, float gb_per_s, int32_t blocks) {
   if (!ctx || !(gb_per_s >= 0.f) || blocks < 0) return GSR_ERR_INVALID_ARG;
   ctx->fill_gbs = gb_per_s;
   if (blocks > 0) ctx->fill_blocks = blocks;
+  return GSR_OK;
+}
+
+gsr_status gsr_set_fill_split(gsr_ctx* ctx, float early_share) {
+  if (!ctx || !(early_share >= 0.f && early_share <= 1.f)) return GSR_ERR_INVALID_ARG;
+  ctx->fill_early = early_share;
   return GSR_OK;
 }
 

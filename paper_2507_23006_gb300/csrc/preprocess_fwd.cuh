@@ -95,6 +95,13 @@ __device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z
 
 constexpr int kBwdThreads = 128;
 
+// Starts moving the 32-byte sectors of [p, p + bytes) into L2 without waiting for them (no
+// registers are held): a later load of the same bytes then waits for L2 instead of DRAM.
+__device__ __forceinline__ void prefetch_l2(const void* p, int bytes) {
+  const char* c = static_cast<const char*>(p);
+  for (int o = 0; o < bytes; o += 64) asm volatile("prefetch.global.L2 [%0];" ::"l"(c + o));
+}
+
 // Camera-independent part of a Gaussian.
 struct Geo {
   float m[3];
@@ -245,12 +252,14 @@ __device__ __forceinline__ bool surely_culled(const Geo& G, const DevCam& c, flo
   if (!(tz > c.znear && tz < c.zfar)) return true;
   const float tx = fmaf(W[0], G.m[0], fmaf(W[1], G.m[1], fmaf(W[2], G.m[2], c.t[0])));
   const float ty = fmaf(W[3], G.m[0], fmaf(W[4], G.m[1], fmaf(W[5], G.m[2], c.t[1])));
-  const float iz = 1.f / tz;
+  // approximate reciprocal and square root (a few ulp): far inside the bound's 1% slack
+  const float iz = __fdividef(1.f, tz);
   const float uc = fminf(fmaxf(tx * iz, -c.limx), c.limx);
   const float wc = fminf(fmaxf(ty * iz, -c.limy), c.limy);
   const float smax = fmaxf(G.s[0], fmaxf(G.s[1], G.s[2]));
   const float jf2 = (c.fx * c.fx * (1.f + uc * uc) + c.fy * c.fy * (1.f + wc * wc)) * iz * iz;
-  const float rb = 3.f * sqrtf(jf2 * smax * smax + eps + 0.31623f) * 1.01f + 2.f;
+  const float r2 = jf2 * smax * smax + eps + 0.31623f;  // > 0
+  const float rb = 3.f * (r2 * rsqrtf(r2)) * 1.01f + 2.f;
   const float mx = c.fx * tx * iz + c.cx;
   const float my = c.fy * ty * iz + c.cy;
   return (mx + rb < 1.f) || (mx - rb >= static_cast<float>(kTile * c.tiles_x)) || (my + rb < 1.f) ||
@@ -567,6 +576,11 @@ __global__ void __launch_bounds__(kPreThreads, kMinBlocks) preprocess_cull_kerne
           if (((seg_cams[j] >> c) & 1u) && !surely_culled(G[j], cams.cam[c], eps)) maybe |= 1u << c;
       s_aux[slot] = maybe;
       s_mask[slot] = 0;
+      if (maybe) {  // the exact test below reads the quaternion and opacity
+        const long long g = seg_map(A.segs, base_i + slot);
+        prefetch_l2(static_cast<const AT*>(A.quats) + 4 * g, 4 * sizeof(AT));
+        prefetch_l2(static_cast<const AT*>(A.opac) + g, sizeof(AT));
+      }
       list_append(maybe != 0, slot, s_list, &s_count, lane);
     }
   }

@@ -38,7 +38,7 @@ EXPORTED = [
     "gsr_state_get_info", "gsr_state_copy", "gsr_sync_check", "gsr_sort_pairs_u32", "gsr_select_lod",
     "gsr_appearance_cache",
     "gsr_profile_enable", "gsr_profile_collect", "gsr_sort_pairs_u32_noalloc", "gsr_profile_select",
-    "gsr_param_grads_zero", "gsr_set_wait_limit", "gsr_set_fill_rate",
+    "gsr_param_grads_zero", "gsr_set_wait_limit", "gsr_set_fill_rate", "gsr_set_fill_split",
 ]
 
 STAGES = ["preprocess", "tile_count", "tile_scan", "readback", "place", "tile_sort", "blend_fwd", "blend_bwd",
@@ -181,6 +181,7 @@ def load(build_if_missing: bool = True):
         L.gsr_param_grads_zero.argtypes = [vp, vp, vp, vp]
         L.gsr_set_wait_limit.argtypes = [vp, ctypes.c_uint32, ctypes.c_int32]
         L.gsr_set_fill_rate.argtypes = [vp, ctypes.c_float, ctypes.c_int32]
+        L.gsr_set_fill_split.argtypes = [vp, ctypes.c_float]
         L.gsr_appearance_cache.argtypes = [vp, ctypes.POINTER(CGaussians), ctypes.c_int32, vp, vp]
         for name in EXPORTED:
             getattr(L, name)
@@ -188,7 +189,8 @@ def load(build_if_missing: bool = True):
                      "gsr_state_get_info", "gsr_state_copy", "gsr_sync_check", "gsr_sort_pairs_u32",
                      "gsr_select_lod", "gsr_profile_enable", "gsr_profile_collect",
                      "gsr_sort_pairs_u32_noalloc", "gsr_profile_select", "gsr_param_grads_zero",
-                     "gsr_appearance_cache", "gsr_set_wait_limit", "gsr_set_fill_rate"):
+                     "gsr_appearance_cache", "gsr_set_wait_limit", "gsr_set_fill_rate",
+                     "gsr_set_fill_split"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -449,6 +451,11 @@ class Context:
         """Pace of the gradient zero fill in GB/s (0: unpaced) and its block count (0: keep).
         See gsr_set_fill_rate."""
         _check(self, load().gsr_set_fill_rate(self.handle, float(gb_per_s), int(blocks)))
+
+    def set_fill_split(self, early_share: float = 0.0):
+        """Share of a requested gradient fill queued by the forward after its preprocess (the
+        rest by the backward before its blend). See gsr_set_fill_split."""
+        _check(self, load().gsr_set_fill_split(self.handle, float(early_share)))
 
     def sync_check(self, stream=None):
         _check(self, load().gsr_sync_check(self.handle, _stream(stream)))

@@ -314,10 +314,13 @@ def test_gradient_rows_unaligned_and_prefilled(ctx, shift):
                       mag=None if k == "absgrad" else np.asarray(ref["mag"][k]).reshape(n, -1))
 
 
-def test_param_grads_zeroed_ahead_of_the_forward(ctx):
+@pytest.mark.parametrize("early", [0.0, 0.37, 1.0])
+def test_param_grads_zeroed_ahead_of_the_forward(ctx, early):
     """gsr_param_grads_zero before the forward: the backward with the same arrays zeroes them
-    (one fill); a backward given other arrays zeroes the requested ones too and fills its own.
-    Both are checked on NaN-prefilled arrays against the oracle."""
+    (one fill, of which the forward queued the first `early` share: none, a part ending inside the
+    SH array's span, or all); a backward given other arrays zeroes the requested ones too and
+    fills its own. Both are checked on NaN-prefilled arrays against the oracle."""
+    ctx.set_fill_split(early)
     scene, cam = pu.scene_box(8000, seed=22)
     m = np.array(scene.means, np.float64)
     m[::4, 2] = -5.0
@@ -354,6 +357,7 @@ def test_param_grads_zeroed_ahead_of_the_forward(ctx):
                           mag=np.asarray(ref["mag"][k]).reshape(g.n, -1))
         if not same:  # the arrays requested for zeroing were not used by the backward, but are zero
             assert all((a[k] == 0).all() for k in ("means", "scales", "quats", "opacities", "sh"))
+    ctx.set_fill_split(0.0)
 
 
 def test_backward_batched_with_appearance_and_recompute(ctx):
