@@ -980,14 +980,13 @@ gsr_status gsr_render_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_c
   if (e != cudaSuccess) return cuda_err(ctx, e, "memset");
   // Every parameter-gradient row starts at zero; only rows of Gaussians with a record are then
   // written. The fill is queued on the side stream right before the blend backward, which it
-  // runs beside (an ALU-bound kernel that leaves the memory bandwidth to it). Queued earlier, at
-  // the end of the forward, it was measured four times slower: started alone, it then ran beside
-  // the blend backward at a fraction of its speed and kept the projection backward waiting.
+  // runs beside (measured against other placements: see gsr_set_fill_split); a share of a
+  // requested fill that a forward already queued is waited for before the projection backward.
   bool join_requested = false;  // the projection backward waits for the requested fill
   cudaEvent_t join = nullptr;
   const bool requested = ctx->prezero_requested || ctx->prezero_pending || ctx->prezero_early;
   if (g->n > 0 && requested && same_spans(grad_spans(g, grads), ctx->prezero)) {
-    e = start_prezero(ctx, s);  // the rest of it, beside the blend
+    e = start_prezero(ctx, s);  // what is left of it, beside the blend
     if (e != cudaSuccess) return cuda_err(ctx, e, "gradient fill");
     join_requested = true;
   } else {

@@ -65,8 +65,9 @@ __host__ __device__ constexpr int transpose_shared_bits() {
   return 2 * bit - 1;
 }
 
-// kAbs: also accumulate |dL/dmean2D| per pixel (AbsGS densification statistics).
-template <bool kCount, bool kAbs>
+// kAbs: also accumulate |dL/dmean2D| per pixel (AbsGS densification statistics). kAff: the
+// gradient of the per-image 3x4 colour transform is wanted (the colour sums are then kept).
+template <bool kCount, bool kAbs, bool kAff>
 __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* __restrict__ rec,
                                                                   const uint32_t* __restrict__ pvals,
                                                                   const uint2* __restrict__ ranges, CamBatch cams,
@@ -104,7 +105,10 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
   const float bb0 = A ? A[3] : 0.f, bb1 = A ? A[7] : 0.f, bb2 = A ? A[11] : 0.f;
   // per pixel: upstream gradients of C = sum c a T, of the depth part and of T_final
   float Tf[2], T[2], g0[2], g1[2], g2[2], aout[2], GC0[2], GC1[2], GC2[2], GD[2], GTz[2], zr[2], zrl[2];
-  float S0[2] = {0.f, 0.f}, S1[2] = {0.f, 0.f}, S2[2] = {0.f, 0.f}, SD[2] = {0.f, 0.f};
+  // R = dL/dT_final-like remainder: GTz T_final minus the sum, over the contributors behind the
+  // current one, of X_k w_k with X_k = GC . c_k + GD dz_k (w_k = alpha_k T_k); S: the colour sums
+  // behind it (only for the transform's gradient)
+  float R[2], S0[2] = {0.f, 0.f}, S1[2] = {0.f, 0.f}, S2[2] = {0.f, 0.f};
   uint32_t last[2];
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
@@ -145,6 +149,7 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
     zrl[q] = zrel;
     GTz[q] = gda * (zf + zrel) + gal - (g0[q] * (bg.x - bb0) + g1[q] * (bg.y - bb1) + g2[q] * (bg.z - bb2));
     T[q] = Tf[q];
+    R[q] = GTz[q] * Tf[q];
   }
   __syncthreads();
   const int n = static_cast<int>(s_max);
@@ -215,12 +220,14 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
         const float Ti = T[q] * rom;
         const float wgt = c ? alpha * Ti : 0.f;
         const float dz = (a.w - zr[q]) - zrl[q];
-        const float dal = Ti * (GC0[q] * b.w + GC1[q] * cc.x + GC2[q] * cc.y + GD[q] * dz) +
-                          (GTz[q] * Tf[q] - (GC0[q] * S0[q] + GC1[q] * S1[q] + GC2[q] * S2[q] + GD[q] * SD[q])) * rom;
-        S0[q] = fmaf(b.w, wgt, S0[q]);
-        S1[q] = fmaf(cc.x, wgt, S1[q]);
-        S2[q] = fmaf(cc.y, wgt, S2[q]);
-        SD[q] = fmaf(dz, wgt, SD[q]);
+        const float X = GC0[q] * b.w + GC1[q] * cc.x + GC2[q] * cc.y + GD[q] * dz;
+        const float dal = Ti * X + R[q] * rom;
+        R[q] = fmaf(-X, wgt, R[q]);
+        if (kAff) {
+          S0[q] = fmaf(b.w, wgt, S0[q]);
+          S1[q] = fmaf(cc.x, wgt, S1[q]);
+          S2[q] = fmaf(cc.y, wgt, S2[q]);
+        }
         T[q] = c ? Ti : T[q];
         const float draw = (c && araw <= kAlphaMax) ? dal : 0.f;  // the clamp at 0.99 passes no gradient
         const float dsig = -draw * araw;
@@ -268,7 +275,7 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
       atomicAdd(counters + 5, static_cast<unsigned long long>(n_iter_c));
     }
   }
-  if (g_aff) {
+  if (kAff) {
     // dA = g C^T, db = g (1 - T_final), per pixel, summed over the tile
     float a12[12];
 #pragma unroll
@@ -301,14 +308,17 @@ void launch_blend_bwd(const Rec* rec, const uint32_t* pair_vals, const uint2* ra
                       unsigned long long* counters, cudaStream_t s) {
   if (cams.total_tiles <= 0) return;
   const float3 b3 = make_float3(bg[0], bg[1], bg[2]);
-#define GSR_BWD(C, A)                                                                                  \
-  blend_bwd_kernel<C, A><<<cams.total_tiles, kBlendThreads, 0, s>>>(rec, pair_vals, ranges, cams, b3, in, g2d, \
-                                                                    g_aff, counters)
+#define GSR_BWD(C, A, F)                                                                                  \
+  blend_bwd_kernel<C, A, F><<<cams.total_tiles, kBlendThreads, 0, s>>>(rec, pair_vals, ranges, cams, b3, in, g2d, \
+                                                                       g_aff, counters)
+#define GSR_BWD_AFF(C, A) \
+  if (g_aff) GSR_BWD(C, A, true); else GSR_BWD(C, A, false)
   if (counters) {
-    if (absgrad) GSR_BWD(true, true); else GSR_BWD(true, false);
+    if (absgrad) { GSR_BWD_AFF(true, true); } else { GSR_BWD_AFF(true, false); }
   } else {
-    if (absgrad) GSR_BWD(false, true); else GSR_BWD(false, false);
+    if (absgrad) { GSR_BWD_AFF(false, true); } else { GSR_BWD_AFF(false, false); }
   }
+#undef GSR_BWD_AFF
 #undef GSR_BWD
 }
 

@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_compact_kernel(long lo
 }
 
 template <typename AT, typename ST, bool kMlp>
-__global__ void __launch_bounds__(kPreThreads, 4) preprocess_rec_kernel(GaussArgs A, CamBatch cams, float eps, int aa,
+__global__ void __launch_bounds__(kPreThreads, 3) preprocess_rec_kernel(GaussArgs A, CamBatch cams, float eps, int aa,
                                                                      PreOut out) {
   __shared__ MlpSmem s_mlp;                // appearance transform, when on
   __shared__ uint32_t s_digits[4 * 256];   // digit counts of the block's depth keys (global sort)
