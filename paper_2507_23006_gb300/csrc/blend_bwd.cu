@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
       float gv[kGradVals];
 #pragma unroll
       for (int m = 0; m < kGradVals; ++m) gv[m] = 0.f;
+      const float dx2 = dx * dx;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {  // branch-free within a row: contributions are masked
         if (!(q ? any1 : any0)) continue;  // warp-uniform: no pixel of this row takes it
@@ -231,21 +232,22 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
         T[q] = c ? Ti : T[q];
         const float draw = (c && araw <= kAlphaMax) ? dal : 0.f;  // the clamp at 0.99 passes no gradient
         const float dsig = -draw * araw;
-        const float dmx = (b.x * dx + b.y * dy) * dsig;
-        const float dmy = (b.y * dx + b.z * dy) * dsig;
-        gv[0] += dmx;
-        gv[1] += dmy;
+        // the pixel offsets weighted by dL/dsigma: the mean's gradient is (a, b; b, c) times the
+        // first moments and the conic's is (1/2, 1, 1/2) times the second moments, applied once
+        // per (tile, Gaussian) when the sums are flushed
+        gv[0] = fmaf(dsig, dx, gv[0]);
+        gv[1] = fmaf(dsig, dy, gv[1]);
         gv[2] += draw * G;
         gv[3] += GD[q] * wgt;
-        gv[4] += 0.5f * dx * dx * dsig;
-        gv[5] += dx * dy * dsig;
-        gv[6] += 0.5f * dy * dy * dsig;
+        gv[4] = fmaf(dsig, dx2, gv[4]);
+        gv[5] = fmaf(dsig, dx * dy, gv[5]);
+        gv[6] = fmaf(dsig, dy * dy, gv[6]);
         gv[7] += GC0[q] * wgt;
         gv[8] += GC1[q] * wgt;
         gv[9] += GC2[q] * wgt;
-        if (kAbs) {
-          gv[10] += fabsf(dmx);
-          gv[11] += fabsf(dmy);
+        if (kAbs) {  // AbsGS sums |dL/dmean2D| per pixel
+          gv[10] += fabsf((b.x * dx + b.y * dy) * dsig);
+          gv[11] += fabsf((b.y * dx + b.z * dy) * dsig);
         }
       }
       const float tot = TransposeSum<kVals, 16>::run(gv, lane);
@@ -254,11 +256,18 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
     __syncthreads();
     for (int k = tid; k < cnt; k += kBlendThreads) {
       float* f = reinterpret_cast<float*>(g2d + sV[k]);
+      float v[kVals];
 #pragma unroll
-      for (int m = 0; m < kVals; ++m) {
-        const float val = sAcc[k][m];
-        if (val != 0.f) atomicAdd(f + m, val);
-      }
+      for (int m = 0; m < kVals; ++m) v[m] = sAcc[k][m];
+      const float4 cb = sB[k];  // the Gaussian's conic (a, b, c)
+      const float mx = v[0], my = v[1];
+      v[0] = cb.x * mx + cb.y * my;
+      v[1] = cb.y * mx + cb.z * my;
+      v[4] *= 0.5f;
+      v[6] *= 0.5f;
+#pragma unroll
+      for (int m = 0; m < kVals; ++m)
+        if (v[m] != 0.f) atomicAdd(f + m, v[m]);
     }
   }
   if (kCount) {
