@@ -167,6 +167,23 @@ def stored_traffic(kernel, workload):
     return float(k["dram_bytes_per_launch"])
 
 
+def stored_ncu_us(kernel, workload):
+    """The kernel's duration in the committed ncu capture (launched alone, cold), or None when
+    there is none for its current sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    k = rec.get("kernels", {}).get(kernel)
+    if rec.get("workload") != workload or k is None or kernel not in KERNEL_SOURCES:
+        return None
+    if k.get("sources_sha256") != sources_sha256(kernel):
+        return None
+    return float(k["ncu_us"])
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -784,6 +801,12 @@ def run_ours(args, rank, world, local_rank):
         roof = dict(kernel=dom, launch_ms=dom_ms, bound="alu", achieved=achieved, peak=fp32_peak, unit="TFLOP/s",
                     frac=achieved / fp32_peak, traffic=stored_traffic(dom, workload_name(n, cam.height)),
                     peak_source=f"{sms} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sampled)")
+        alone_us = stored_ncu_us(dom, workload_name(n, cam.height))
+        if dom == "blend_bwd" and alone_us:
+            # live, the gradient zero fill runs beside this kernel; the same launch alone (ncu,
+            # cold, no fill beside it) for comparison
+            roof["alone_ms_ncu"] = alone_us * 1e-3
+            roof["frac_alone_ncu"] = flops / (alone_us * 1e-6) / 1e12 / fp32_peak
     else:
         work = stage_work(n, V, P, info["n_tiles"], cam.width * cam.height, counts)
         per_unit = {k: w.get("bytes", 0.0) for k, w in work.items()}
