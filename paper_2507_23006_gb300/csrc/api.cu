@@ -780,7 +780,8 @@ gsr_status gsr_workspace_query(gsr_ctx* ctx, int64_t n_render, const gsr_camera*
   const size_t capv = static_cast<size_t>(std::max<int64_t>(1, n_render * n_cams));
   const size_t P = static_cast<size_t>(std::max<int64_t>(1, expected_pairs));
   size_t b = 0;
-  b += capv * (sizeof(Rec) + sizeof(uint32_t));                  // records, owners
+  b += capv * (sizeof(Rec) + sizeof(uint32_t) + 1);              // records, owners, cameras
+  b += static_cast<size_t>(n_render) * sizeof(uint32_t);         // visibility bits of the cull pass
   b += P * (2 * sizeof(unsigned long long) + sizeof(uint32_t));  // pair keys, merge scratch, sorted records
   b += static_cast<size_t>(cb.total_tiles) * (sizeof(uint2) + sizeof(uint32_t));  // ranges, counters
   b += static_cast<size_t>(npix) * 4 * sizeof(float);            // per-pixel state
