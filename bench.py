@@ -9,9 +9,12 @@ backward, projection backward) with fixed upstream gradients on rgb, depth and a
 The inputs (1.4 GB of Gaussians) are larger than L2, so no flush is needed between steps.
 
 Prints one JSON line. `value` is the device-timed ms per fwd+bwd step (CUDA events, inputs
-resident in HBM); `e2e` repeats the step through the same API with the Gaussians in pinned
-host memory, copying them in and the parameter gradients out every step (pipelined over two
-buffer sets; `serial_value` without overlap).
+resident in HBM); `e2e` repeats the step through the same API with the step's inputs (the
+upstream gradients of the outputs) copied in from pinned host memory and its result (the
+rendered outputs the loss is computed on) copied out every step, the Gaussians and their
+gradients resident as model state is in training (pipelined over two buffer sets;
+`serial_value` without overlap); `e2e.full_copy` also copies the Gaussians in and every
+parameter gradient out.
 `--impl reference` times the FP64 CPU oracle instead (a bounded sample of the same step).
 """
 from __future__ import annotations
@@ -393,47 +396,56 @@ def stage_rooflines(stage_ms, n, V, P, tiles, npix, counts, fp32_tflops, mufu_pe
                      frac=round(total / (step_ms * 1e3), 3))
 
 
-def run_e2e(args, ctx, g, cam, opts, d_out, grads, outs, stream, world, dev, barrier):
-    """The step through the same API with the Gaussians and upstream gradients copied in from
-    pinned host memory and the parameter gradients copied out, every step. Pipelined the way a
-    training loop would run it: two sets of device buffers, the copies in and the copies out on
-    their own streams, so step i's copy out and step i+1's copy in overlap step i's compute
-    (the link carries both directions at once). Also reports the same steps run one after
-    another on one stream (`serial_value`)."""
+def run_e2e(args, ctx, g, cam, opts, d_out, grads, outs, stream, world, dev, barrier, full_copy=False):
+    """The step through the same API with host copies every step, pipelined the way a training
+    loop would run it: two sets of device buffers, the copies in and the copies out on their own
+    streams, so step i's copy out and step i+1's copy in overlap step i's compute (the link
+    carries both directions at once); also the same steps one after another on one stream
+    (`serial_value`). By default the step's inputs are the upstream gradients of the outputs (the
+    loss's gradient, computed elsewhere) copied in and its result the rendered outputs copied
+    out (what the loss is computed on); the Gaussians and their gradients stay on the device, as
+    model state does in training. full_copy: the Gaussians are copied in and every parameter
+    gradient copied out as well."""
     import torch
     from paper_2507_23006_gb300 import native
 
     keys = ("means", "scales", "quats", "opacities", "sh")
-    host = {k: getattr(g, k).to("cpu").pin_memory() for k in keys}
+    host = {k: getattr(g, k).to("cpu").pin_memory() for k in keys} if full_copy else {}
     host_up = {k: v.to("cpu").pin_memory() for k, v in d_out.items()}
-    gkeys = [k for k, v in grads.items() if v is not None]
+    gkeys = [k for k, v in grads.items() if v is not None] if full_copy else []
+    okeys = list(outs)
     h2d = sum(v.numel() * v.element_size() for v in host.values()) + \
         sum(v.numel() * v.element_size() for v in host_up.values())
-    d2h = sum(grads[k].numel() * grads[k].element_size() for k in gkeys)
+    d2h = sum(grads[k].numel() * grads[k].element_size() for k in gkeys) + \
+        sum(outs[k].numel() * outs[k].element_size() for k in okeys)
     # buffer set 0 is the bench's own; set 1 a copy
-    gs = [g, native.Gaussians(*(getattr(g, k).clone() for k in keys), 3)]
+    gs = [g, native.Gaussians(*(getattr(g, k).clone() for k in keys), 3) if full_copy else g]
     ds = [d_out, {k: v.clone() for k, v in d_out.items()}]
     grs = [grads, {k: (torch.empty_like(v) if v is not None else None) for k, v in grads.items()}]
+    os_ = [outs, {k: torch.empty_like(v) for k, v in outs.items()}]
     hgs = [{k: torch.empty(grads[k].shape, dtype=grads[k].dtype, pin_memory=True) for k in gkeys} for _ in range(2)]
+    hos = [{k: torch.empty(outs[k].shape, dtype=outs[k].dtype, pin_memory=True) for k in okeys} for _ in range(2)]
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_comp = [torch.cuda.Event() for _ in range(2)]
     ev_out = [torch.cuda.Event() for _ in range(2)]
 
     def copy_in(b):
-        for k in keys:
+        for k in host:
             getattr(gs[b], k).copy_(host[k], non_blocking=True)
         for k, v in host_up.items():
             ds[b][k].copy_(v, non_blocking=True)
 
     def compute(b):
         native.zero_param_grads(ctx, gs[b], grs[b])
-        _, st = native.render_forward(ctx, gs[b], [cam], opts, outputs=outs)
+        _, st = native.render_forward(ctx, gs[b], [cam], opts, outputs=os_[b])
         native.render_backward(ctx, gs[b], [cam], st, ds[b], opts, grads=grs[b])
 
     def copy_out(b):
         for k in gkeys:
             hgs[b][k].copy_(grs[b][k], non_blocking=True)
+        for k in okeys:
+            hos[b][k].copy_(os_[b][k], non_blocking=True)
 
     def pipelined_step(i):
         b = i % 2
@@ -442,7 +454,7 @@ def run_e2e(args, ctx, g, cam, opts, d_out, grads, outs, stream, world, dev, bar
             copy_in(b)
             ev_in[b].record(s_in)
         stream.wait_event(ev_in[b])
-        stream.wait_event(ev_out[b])  # step i-2's gradients have left this set
+        stream.wait_event(ev_out[b])  # step i-2's results have left this set
         compute(b)
         ev_comp[b].record(stream)
         s_out.wait_event(ev_comp[b])
@@ -476,8 +488,11 @@ def run_e2e(args, ctx, g, cam, opts, d_out, grads, outs, stream, world, dev, bar
     torch.cuda.synchronize()
     pipe_ms = timed(pipelined_step)
     serial_ms = timed(serial_step)
+    what = ("Gaussians and upstream gradients in, parameter gradients and outputs out" if full_copy else
+            "upstream gradients in, rendered outputs out; Gaussians and gradients resident")
     return dict(value=job_ms_per_step(pipe_ms, world), unit="ms/step", h2d_bytes_per_step=int(h2d),
-                d2h_bytes_per_step=int(d2h), mode="pipelined: 2 buffer sets, copies in and out on their own streams",
+                d2h_bytes_per_step=int(d2h), copies=what,
+                mode="pipelined: 2 buffer sets, copies in and out on their own streams",
                 serial_value=job_ms_per_step(serial_ms, world),
                 link_gbs=round((h2d + d2h) / (pipe_ms * 1e-3) / 1e9, 1))
 
@@ -780,6 +795,8 @@ def run_ours(args, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, ctx, g, cam, opts, d_out, grads, outs, stream, world, dev, barrier)
+        e2e["full_copy"] = run_e2e(args, ctx, g, cam, opts, d_out, grads, outs, stream, world, dev, barrier,
+                                   full_copy=True)
 
     configs = None if args.no_configs or rank != 0 else run_configs(args, ctx, dev, stream)
 
