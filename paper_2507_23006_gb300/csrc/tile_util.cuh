@@ -144,22 +144,20 @@ __device__ __forceinline__ void warp_bin_pairs(int lane, bool has, const Rec& r,
 __device__ __forceinline__ unsigned long long block_bitonic_sort_regs(unsigned long long x, int m,
                                                                       unsigned long long* s_x) {
   const int i = threadIdx.x;
-  // warps wholly past the m keys only pass the barriers (their partners are among themselves)
-  const bool active = (i >> 5) < ((m + 31) >> 5);  // warp-uniform
   for (int k = 2; k <= m; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
-      unsigned long long y = x;
+      unsigned long long y;
       if (j >= 32) {  // block-uniform
-        if (active) s_x[i] = x;
+        s_x[i] = x;
         __syncthreads();
-        if (active) y = s_x[i ^ j];
+        y = s_x[i ^ j];
         __syncthreads();
-      } else if (active) {
+      } else {
         y = __shfl_xor_sync(0xffffffffu, x, j);
       }
       // the lower of the two positions keeps the smaller key where this run ascends
       const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
-      if (active) x = keep_min ? (x < y ? x : y) : (x < y ? y : x);
+      x = keep_min ? (x < y ? x : y) : (x < y ? y : x);
     }
   }
   return x;
