@@ -70,7 +70,12 @@ def parse():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region: a sample every
+    5 ms once the sampler is running (start() waits for its first sample), each stamped with the
+    host time it arrived; mark() brackets the timed region (the host and the GPU move together
+    there, each step's forward synchronising once), and only the samples inside it count. When
+    the region is shorter than the sampling interval, the nearest sample after it stands in and
+    `samples` says 0."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -79,34 +84,51 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []  # (host time, line)
+        self.window = None
 
-    def start(self):
+    def start(self, ready_timeout=5.0):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "5"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except OSError:
             self.proc = None
+            return
+        t_end = time.perf_counter() + ready_timeout
+        while not self.lines and time.perf_counter() < t_end:
+            time.sleep(0.005)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
 
     def stop(self):
         if self.proc is None:
             return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        time.sleep(0.02)  # the sample that follows the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
+        lines = self.lines
+        inside = lines
+        if self.window is not None:
+            t0, t1 = self.window
+            inside = [x for x in lines if t0 <= x[0] <= t1]
+            if not inside:
+                inside = [x for x in lines if x[0] > t1][:1]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        n_in = 0
+        for t, ln in inside:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -115,12 +137,14 @@ class ClockSampler:
                 smax.append(float(f[2]))
             except ValueError:
                 continue
+            if self.window is None or self.window[0] <= t <= self.window[1]:
+                n_in += 1
             for name, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(name)
         if not sm:
             return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"], samples=0)
-        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons), samples=len(sm))
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons), samples=n_in)
 
 
 # CUDA sources each stage's kernels are built from (besides the shared headers): a stored DRAM
@@ -702,12 +726,14 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    t_host0 = time.perf_counter()
     e0.record(stream)
     for _ in range(args.steps):
         st = step()
         del st
     e1.record(stream)
     torch.cuda.synchronize()
+    sampler.mark(t_host0, time.perf_counter())
     barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
