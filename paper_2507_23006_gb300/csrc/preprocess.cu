@@ -22,203 +22,6 @@
 namespace gsr {
 namespace {
 
-// The geometry part of one record's backward (everything but the colour): the 2D gradients
-// gd of the record's conic, opacity', mean2d and depth, through the dilated 2D covariance, the
-// opacity compensation, T = J W and t = W mu + t_cam, added to dm (means), ds (scales), dR (the
-// rotation matrix) and dopac.
-__device__ __forceinline__ void record_geom_backward(const Geo& G, const DevCam& cam, const Proj& P,
-                                                     const Grad2D& gd, float eps, int aa, float dm[3],
-                                                     float ds[3], float dR[9], float& dopac) {
-  const float dmx = gd.a.x, dmy = gd.a.y, dop = gd.a.z, ddepth = gd.a.w;
-  const float dca = gd.b.x, dcb = gd.b.y, dcc = gd.b.z;
-  // conic = inverse of the dilated Sigma2D: dSigma2D = -M G M
-  const float g00 = dca, g01 = 0.5f * dcb, g11 = dcc;
-  const float mg00 = P.ca * g00 + P.cb * g01, mg01 = P.ca * g01 + P.cb * g11;
-  const float mg10 = P.cb * g00 + P.cc * g01, mg11 = P.cb * g01 + P.cc * g11;
-  float da = -(mg00 * P.ca + mg01 * P.cb);
-  float db = -2.f * (mg00 * P.cb + mg01 * P.cc);
-  float dc = -(mg10 * P.cb + mg11 * P.cc);
-  // opacity' = opacity * sqrt(det_raw / det)
-  dopac += dop * P.comp;
-  if (aa && P.comp > 0.f) {
-    const float ratio = P.comp * P.comp;
-    const float dratio = dop * G.opac * 0.5f / P.comp;
-    const float ddr = dratio * P.idet;           // d det_raw
-    const float ddt = -dratio * ratio * P.idet;  // d det
-    const float a = P.ar + eps, cc = P.cr + eps;
-    da += ddr * P.cr + ddt * cc;
-    dc += ddr * P.ar + ddt * a;
-    db += -2.f * P.br * (ddr + ddt);
-  }
-  // Sigma2D_raw = T Sigma T^T with T = J W
-  float dT0[3], dT1[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    dT0[k] = 2.f * da * P.ST0[k] + db * P.ST1[k];
-    dT1[k] = db * P.ST0[k] + 2.f * dc * P.ST1[k];
-  }
-  // dSigma (symmetrised) = 2 da T0 T0^T + db (T0 T1^T + T1 T0^T) + 2 dc T1 T1^T; Sigma = M M^T
-  float dS[9];
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-      dS[r * 3 + q] = 2.f * da * P.T0[r] * P.T0[q] + db * (P.T0[r] * P.T1[q] + P.T1[r] * P.T0[q]) +
-                      2.f * dc * P.T1[r] * P.T1[q];
-  float Mx[9];
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) Mx[r * 3 + q] = G.R[r * 3 + q] * G.s[q];
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const float dM = dS[r * 3 + 0] * Mx[0 * 3 + q] + dS[r * 3 + 1] * Mx[1 * 3 + q] + dS[r * 3 + 2] * Mx[2 * 3 + q];
-      dR[r * 3 + q] += dM * G.s[q];
-      ds[q] += dM * G.R[r * 3 + q];
-    }
-  // T = J W: dJ
-  const float* W = cam.R;
-  const float dJ00 = dT0[0] * W[0] + dT0[1] * W[1] + dT0[2] * W[2];
-  const float dJ02 = dT0[0] * W[6] + dT0[1] * W[7] + dT0[2] * W[8];
-  const float dJ11 = dT1[0] * W[3] + dT1[1] * W[4] + dT1[2] * W[5];
-  const float dJ12 = dT1[0] * W[6] + dT1[1] * W[7] + dT1[2] * W[8];
-  const float uc = fminf(fmaxf(P.u, -cam.limx), cam.limx);
-  const float wc = fminf(fmaxf(P.w, -cam.limy), cam.limy);
-  const float iz2 = P.iz * P.iz;
-  float dt[3] = {0.f, 0.f, 0.f};
-  dt[2] += -cam.fx * iz2 * dJ00 + cam.fx * uc * iz2 * dJ02 - cam.fy * iz2 * dJ11 + cam.fy * wc * iz2 * dJ12;
-  const float duc = -cam.fx * P.iz * dJ02, dwc = -cam.fy * P.iz * dJ12;
-  if (!P.clx) { dt[0] += duc * P.iz; dt[2] -= duc * P.u * P.iz; }
-  if (!P.cly) { dt[1] += dwc * P.iz; dt[2] -= dwc * P.w * P.iz; }
-  // mean2d = (fx X/Z + cx, fy Y/Z + cy); depth = Z
-  dt[0] += cam.fx * P.iz * dmx;
-  dt[1] += cam.fy * P.iz * dmy;
-  dt[2] += -cam.fx * P.t[0] * iz2 * dmx - cam.fy * P.t[1] * iz2 * dmy + ddepth;
-  // t = W mu + t_cam
-  dm[0] += W[0] * dt[0] + W[3] * dt[1] + W[6] * dt[2];
-  dm[1] += W[1] * dt[0] + W[4] * dt[1] + W[7] * dt[2];
-  dm[2] += W[2] * dt[0] + W[5] * dt[1] + W[8] * dt[2];
-}
-
-// The quaternion's gradient (through R and the normalisation) and the Gaussian's non-SH
-// gradient rows.
-__device__ __forceinline__ void write_param_rows(const Geo& G, long long g, const float dm[3], const float ds[3],
-                                                 const float dR[9], float dopac, const float dabs[2],
-                                                 const ParamGrads& out) {
-  // rotation from the normalised quaternion, then through the normalisation
-  const float w = G.q[0], x = G.q[1], y = G.q[2], z = G.q[3];
-  float dqn[4];
-  dqn[0] = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
-  dqn[1] = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
-                  2.f * x * dR[8]);
-  dqn[2] = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] -
-                  2.f * y * dR[8]);
-  dqn[3] = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
-                  x * dR[6] + y * dR[7]);
-  const float qd = w * dqn[0] + x * dqn[1] + y * dqn[2] + z * dqn[3];
-  float dq[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) dq[k] = (dqn[k] - G.q[k] * qd) * G.qinv;
-  out.means[3 * g + 0] = dm[0];
-  out.means[3 * g + 1] = dm[1];
-  out.means[3 * g + 2] = dm[2];
-  out.scales[3 * g + 0] = ds[0];
-  out.scales[3 * g + 1] = ds[1];
-  out.scales[3 * g + 2] = ds[2];
-  out.opac[g] = dopac;
-  if (out.vec4)
-    reinterpret_cast<float4*>(out.quats)[g] = make_float4(dq[0], dq[1], dq[2], dq[3]);
-  else
-    for (int k = 0; k < 4; ++k) out.quats[4 * g + k] = dq[k];
-  if (out.absgrad) {
-    out.absgrad[2 * g] = dabs[0];
-    out.absgrad[2 * g + 1] = dabs[1];
-  }
-}
-
-// Element e of an SH row, as FP32 (through the read-only cache).
-template <typename ST>
-__device__ __forceinline__ float sh_at(const ST* sh, int e) {
-  return ldf(sh, e);
-}
-
-// The backward for launches with one camera (every Gaussian has at most one record), one thread
-// per record: the same arithmetic in the same order as preprocess_bwd_kernel, but the SH row is
-// read twice from the cache (once to redo the colour's clamp decisions, once for the SH and
-// direction gradients, whose row is written as it is formed) instead of holding it and its
-// gradient in 96 registers, which leaves room for twice the resident warps (six blocks per SM).
-template <typename AT, typename ST>
-__global__ void __launch_bounds__(kBwdThreads, 6) preprocess_bwd_single_kernel(
-    GaussArgs A, CamBatch cams, float eps, int aa, long long V, const Rec* __restrict__ rec,
-    const uint32_t* __restrict__ owner, const Grad2D* __restrict__ g2d, ParamGrads out) {
-  const long long v = static_cast<long long>(blockIdx.x) * kBwdThreads + threadIdx.x;
-  if (v >= V) return;
-  const long long g = seg_map(A.segs, owner[v]);
-  Geo G;
-  if (!load_geo<AT>(A, g, G)) return;  // cannot happen for a Gaussian with a record
-  const DevCam& cam = cams.cam[rec_cam(rec[v])];
-  Proj P;
-  project(G, cam, eps, aa, P);
-  const Grad2D gd = g2d[v];
-  float drgb[3] = {gd.b.w, gd.c.x, gd.c.y};
-  const float dabs[2] = {gd.c.z, gd.c.w};
-  const int KC = A.K * 3;
-  const int nb = (A.deg + 1) * (A.deg + 1);
-  const ST* sh = static_cast<const ST*>(A.sh) + g * KC;
-  // colour: rgb = max(0, sum_k sh_k Y_k(dir) + 0.5), summed as eval_color_regs does
-  const float dx = G.m[0] - cam.center[0], dy = G.m[1] - cam.center[1], dz = G.m[2] - cam.center[2];
-  const float dn = sqrtf(dx * dx + dy * dy + dz * dz);
-  const float inv = 1.f / dn;
-  const float dir[3] = {dx * inv, dy * inv, dz * inv};
-  float Y[16];
-#pragma unroll
-  for (int k = 0; k < 16; ++k) Y[k] = 0.f;
-  sh_basis(A.deg, dir[0], dir[1], dir[2], Y);
-  float c0 = 0.5f, c1 = 0.5f, c2 = 0.5f;
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    if (k < nb) {
-      c0 = fmaf(sh_at(sh, 3 * k + 0), Y[k], c0);
-      c1 = fmaf(sh_at(sh, 3 * k + 1), Y[k], c1);
-      c2 = fmaf(sh_at(sh, 3 * k + 2), Y[k], c2);
-    }
-  }
-  if (c0 < 0.f) drgb[0] = 0.f;
-  if (c1 < 0.f) drgb[1] = 0.f;
-  if (c2 < 0.f) drgb[2] = 0.f;
-  float wY[16];
-  float* row = out.sh + g * KC;
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    wY[k] = 0.f;
-    float d0 = 0.f, d1 = 0.f, d2 = 0.f;
-    if (k < nb) {
-      d0 = Y[k] * drgb[0];
-      d1 = Y[k] * drgb[1];
-      d2 = Y[k] * drgb[2];
-      wY[k] = sh_at(sh, 3 * k) * drgb[0] + sh_at(sh, 3 * k + 1) * drgb[1] + sh_at(sh, 3 * k + 2) * drgb[2];
-    }
-    if (3 * k < KC) {
-      row[3 * k] = d0;
-      row[3 * k + 1] = d1;
-      row[3 * k + 2] = d2;
-    }
-  }
-  float gx, gy, gz;
-  sh_basis_grad(A.deg, dir[0], dir[1], dir[2], wY, gx, gy, gz);
-  const float proj = gx * dir[0] + gy * dir[1] + gz * dir[2];
-  const float idn = 1.f / dn;
-  float dm[3] = {0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f}, dopac = 0.f;
-  float dR[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  dm[0] += (gx - dir[0] * proj) * idn;
-  dm[1] += (gy - dir[1] * proj) * idn;
-  dm[2] += (gz - dir[2] * proj) * idn;
-  record_geom_backward(G, cam, P, gd, eps, aa, dm, ds, dR, dopac);
-  write_param_rows(G, g, dm, ds, dR, dopac, dabs, out);
-}
-
 // Backward of the projection and colour. One thread per visible record; the thread holding a
 // Gaussian's first record walks all of that Gaussian's cameras (its records are consecutive),
 // accumulates the parameter gradients in registers and writes the Gaussian's rows once.
@@ -249,6 +52,8 @@ __global__ void __launch_bounds__(kBwdThreads, 3) preprocess_bwd_kernel(
     Proj P;
     project(G, cam, eps, aa, P);
     const Grad2D gd = g2d[v];
+    const float dmx = gd.a.x, dmy = gd.a.y, dop = gd.a.z, ddepth = gd.a.w;
+    const float dca = gd.b.x, dcb = gd.b.y, dcc = gd.b.z;
     float drgb[3] = {gd.b.w, gd.c.x, gd.c.y};
     dabs[0] += gd.c.z;
     dabs[1] += gd.c.w;
@@ -276,19 +81,114 @@ __global__ void __launch_bounds__(kBwdThreads, 3) preprocess_bwd_kernel(
     dm[0] += (gx - dir[0] * proj) * idn;
     dm[1] += (gy - dir[1] * proj) * idn;
     dm[2] += (gz - dir[2] * proj) * idn;
-    record_geom_backward(G, cam, P, gd, eps, aa, dm, ds, dR, dopac);
+    // conic = inverse of the dilated Sigma2D: dSigma2D = -M G M
+    const float g00 = dca, g01 = 0.5f * dcb, g11 = dcc;
+    const float mg00 = P.ca * g00 + P.cb * g01, mg01 = P.ca * g01 + P.cb * g11;
+    const float mg10 = P.cb * g00 + P.cc * g01, mg11 = P.cb * g01 + P.cc * g11;
+    float da = -(mg00 * P.ca + mg01 * P.cb);
+    float db = -2.f * (mg00 * P.cb + mg01 * P.cc);
+    float dc = -(mg10 * P.cb + mg11 * P.cc);
+    // opacity' = opacity * sqrt(det_raw / det)
+    dopac += dop * P.comp;
+    if (aa && P.comp > 0.f) {
+      const float ratio = P.comp * P.comp;
+      const float dratio = dop * G.opac * 0.5f / P.comp;
+      const float ddr = dratio * P.idet;           // d det_raw
+      const float ddt = -dratio * ratio * P.idet;  // d det
+      const float a = P.ar + eps, cc = P.cr + eps;
+      da += ddr * P.cr + ddt * cc;
+      dc += ddr * P.ar + ddt * a;
+      db += -2.f * P.br * (ddr + ddt);
+    }
+    // Sigma2D_raw = T Sigma T^T with T = J W
+    float dT0[3], dT1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      dT0[k] = 2.f * da * P.ST0[k] + db * P.ST1[k];
+      dT1[k] = db * P.ST0[k] + 2.f * dc * P.ST1[k];
+    }
+    // dSigma (symmetrised) = 2 da T0 T0^T + db (T0 T1^T + T1 T0^T) + 2 dc T1 T1^T; Sigma = M M^T
+    float dS[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        dS[r * 3 + q] = 2.f * da * P.T0[r] * P.T0[q] + db * (P.T0[r] * P.T1[q] + P.T1[r] * P.T0[q]) +
+                        2.f * dc * P.T1[r] * P.T1[q];
+    float Mx[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) Mx[r * 3 + q] = G.R[r * 3 + q] * G.s[q];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float dM = dS[r * 3 + 0] * Mx[0 * 3 + q] + dS[r * 3 + 1] * Mx[1 * 3 + q] + dS[r * 3 + 2] * Mx[2 * 3 + q];
+        dR[r * 3 + q] += dM * G.s[q];
+        ds[q] += dM * G.R[r * 3 + q];
+      }
+    // T = J W: dJ
+    const float* W = cam.R;
+    const float dJ00 = dT0[0] * W[0] + dT0[1] * W[1] + dT0[2] * W[2];
+    const float dJ02 = dT0[0] * W[6] + dT0[1] * W[7] + dT0[2] * W[8];
+    const float dJ11 = dT1[0] * W[3] + dT1[1] * W[4] + dT1[2] * W[5];
+    const float dJ12 = dT1[0] * W[6] + dT1[1] * W[7] + dT1[2] * W[8];
+    const float uc = fminf(fmaxf(P.u, -cam.limx), cam.limx);
+    const float wc = fminf(fmaxf(P.w, -cam.limy), cam.limy);
+    const float iz2 = P.iz * P.iz;
+    float dt[3] = {0.f, 0.f, 0.f};
+    dt[2] += -cam.fx * iz2 * dJ00 + cam.fx * uc * iz2 * dJ02 - cam.fy * iz2 * dJ11 + cam.fy * wc * iz2 * dJ12;
+    const float duc = -cam.fx * P.iz * dJ02, dwc = -cam.fy * P.iz * dJ12;
+    if (!P.clx) { dt[0] += duc * P.iz; dt[2] -= duc * P.u * P.iz; }
+    if (!P.cly) { dt[1] += dwc * P.iz; dt[2] -= dwc * P.w * P.iz; }
+    // mean2d = (fx X/Z + cx, fy Y/Z + cy); depth = Z
+    dt[0] += cam.fx * P.iz * dmx;
+    dt[1] += cam.fy * P.iz * dmy;
+    dt[2] += -cam.fx * P.t[0] * iz2 * dmx - cam.fy * P.t[1] * iz2 * dmy + ddepth;
+    // t = W mu + t_cam
+    dm[0] += W[0] * dt[0] + W[3] * dt[1] + W[6] * dt[2];
+    dm[1] += W[1] * dt[0] + W[4] * dt[1] + W[7] * dt[2];
+    dm[2] += W[2] * dt[0] + W[5] * dt[1] + W[8] * dt[2];
   }
-  write_param_rows(G, g, dm, ds, dR, dopac, dabs, out);
+  // rotation from the normalised quaternion, then through the normalisation
+  const float w = G.q[0], x = G.q[1], y = G.q[2], z = G.q[3];
+  float dqn[4];
+  dqn[0] = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+  dqn[1] = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
+                  2.f * x * dR[8]);
+  dqn[2] = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] -
+                  2.f * y * dR[8]);
+  dqn[3] = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
+                  x * dR[6] + y * dR[7]);
+  const float qd = w * dqn[0] + x * dqn[1] + y * dqn[2] + z * dqn[3];
+  float dq[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) dq[k] = (dqn[k] - G.q[k] * qd) * G.qinv;
+  out.means[3 * g + 0] = dm[0];
+  out.means[3 * g + 1] = dm[1];
+  out.means[3 * g + 2] = dm[2];
+  out.scales[3 * g + 0] = ds[0];
+  out.scales[3 * g + 1] = ds[1];
+  out.scales[3 * g + 2] = ds[2];
+  out.opac[g] = dopac;
   if (out.vec4) {
+    reinterpret_cast<float4*>(out.quats)[g] = make_float4(dq[0], dq[1], dq[2], dq[3]);
     float4* row = reinterpret_cast<float4*>(out.sh + g * KC);
 #pragma unroll
     for (int k = 0; k < 12; ++k)
       if (4 * k < KC) row[k] = make_float4(dsh[4 * k], dsh[4 * k + 1], dsh[4 * k + 2], dsh[4 * k + 3]);
   } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out.quats[4 * g + k] = dq[k];
     float* row = out.sh + g * KC;
 #pragma unroll
     for (int k = 0; k < 48; ++k)
       if (k < KC) row[k] = dsh[k];
+  }
+  if (out.absgrad) {
+    out.absgrad[2 * g] = dabs[0];
+    out.absgrad[2 * g + 1] = dabs[1];
   }
 }
 
@@ -501,10 +401,7 @@ template <typename AT, typename ST>
 void launch_bwd_t(const GaussArgs& g, const CamBatch& cams, float eps, int aa, long long V, const Rec* rec,
                   const uint32_t* owner, const Grad2D* g2d, const ParamGrads& out, cudaStream_t s) {
   const int blocks = static_cast<int>((V + kBwdThreads - 1) / kBwdThreads);
-  if (blocks <= 0) return;
-  if (cams.C == 1)  // at most one record per Gaussian
-    preprocess_bwd_single_kernel<AT, ST><<<blocks, kBwdThreads, 0, s>>>(g, cams, eps, aa, V, rec, owner, g2d, out);
-  else
+  if (blocks > 0)
     preprocess_bwd_kernel<AT, ST><<<blocks, kBwdThreads, 0, s>>>(g, cams, eps, aa, V, rec, owner, g2d, out);
 }
 
