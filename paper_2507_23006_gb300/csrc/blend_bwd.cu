@@ -1,7 +1,7 @@
 // Backward pass of the alpha blending of Sec. 3.1, Eq. 2: the forward's tiling, contributors
 // walked back to front recovering T_i = T_{i+1} / (1 - a_i); per-Gaussian gradients are summed
-// over the warp with shuffles, over the CTA in shared memory, and added to global memory once per
-// (tile, Gaussian).
+// over the warp through a row exchange in shared memory, over the CTA with shared atomics, and
+// added to global memory once per (tile, Gaussian).
 #include "gsr_internal.cuh"
 #include "tile_util.cuh"
 
@@ -16,53 +16,22 @@ __device__ __forceinline__ float warp_sum(float x) {
 
 constexpr int kGradVals = 12;
 
-// Sums N (<= 16) per-lane values over the warp with about N + 2 shuffles instead of 5 N. Each
-// round halves the vector: a lane sends the half it gives up to its partner across `kBit` and
-// keeps the sum of the other half (an odd length is padded with a zero). Once one value is
-// left, the remaining lane bits are summed directly. index() gives the value each lane ends up
-// holding (-1: padding).
-template <int N, int kBit>
-struct TransposeSum {
-  static __device__ __forceinline__ float run(const float* v, int lane) {
-    constexpr int H = (N + 1) / 2;
-    const bool up = lane & kBit;
-    float w[H];
+// Each lane of a warp holds two pixels of the warp's 8x8 block (column lane & 7; row lane >> 3 of
+// the upper half and the row four below it in the lower half). Bit 2w + h is set when the
+// Gaussian's alpha >= 1/255 box (record field d) meets the pixel centres of half h of warp w's
+// block; (x0, y0) is the tile's first pixel centre, (x_max, y_max) the image's last.
+__device__ __forceinline__ uint32_t warp_half_mask(const float4 d, float x0, float y0, float x_max, float y_max) {
+  uint32_t m = 0;
 #pragma unroll
-    for (int k = 0; k < H; ++k) {
-      const float lo = v[k];
-      const float hi = (k + H < N) ? v[k + H] : 0.f;
-      const float send = up ? lo : hi;
-      const float keep = up ? hi : lo;
-      w[k] = keep + __shfl_xor_sync(0xffffffffu, send, kBit);
+  for (int w = 0; w < kBlendWarps; ++w) {
+    const float xl = x0 + 8.f * (w & 1), xh = fminf(xl + 7.f, x_max);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float yl = y0 + 8.f * (w >> 1) + 4.f * h, yh = fminf(yl + 3.f, y_max);
+      if (d.y >= xl && d.x <= xh && d.w >= yl && d.z <= yh) m |= 1u << (2 * w + h);
     }
-    return TransposeSum<H, kBit / 2>::run(w, lane);
   }
-  static __device__ __forceinline__ int index(int lane) {
-    constexpr int H = (N + 1) / 2;
-    const int r = TransposeSum<H, kBit / 2>::index(lane);
-    if (r < 0) return -1;
-    if (lane & kBit) return r < N - H ? H + r : -1;  // the upper half holds N - H values
-    return r;
-  }
-};
-template <int kBit>
-struct TransposeSum<1, kBit> {
-  static __device__ __forceinline__ float run(const float* v, int) {
-    float x = v[0];
-#pragma unroll
-    for (int b = kBit; b > 0; b >>= 1) x += __shfl_xor_sync(0xffffffffu, x, b);
-    return x;
-  }
-  static __device__ __forceinline__ int index(int) { return 0; }
-};
-
-// Lane bits still summed directly after the halving rounds of an N-value transpose sum: lanes
-// that differ only in these bits hold the same total.
-template <int N>
-__host__ __device__ constexpr int transpose_shared_bits() {
-  int n = N, bit = 16;
-  while (n > 1 && bit > 0) { n = (n + 1) / 2; bit >>= 1; }
-  return 2 * bit - 1;
+  return m;
 }
 
 // kAbs: also accumulate |dL/dmean2D| per pixel (AbsGS densification statistics). kAff: the
@@ -81,6 +50,12 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
   __shared__ uint32_t sV[kBatch];
   __shared__ uint32_t sM[kBatch];
   __shared__ float sAcc[kBatch][kGradVals + 1];
+  // per-Gaussian sums of a warp: each lane writes its kVals values as one row, then lane
+  // (m, part) adds value m over every kParts-th row from row `part` (row stride kVals + 1, an odd
+  // number of words, so that neither the row writes nor the column reads meet a bank twice)
+  constexpr int kStride = kVals + 1;
+  constexpr int kParts = kVals <= 10 ? 3 : 2;
+  __shared__ float sRed[kBlendWarps][32 * kStride];
   __shared__ uint32_t s_max;
   __shared__ float s_aff[kBlendWarps][12];
   const int t = blockIdx.x;
@@ -89,13 +64,15 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
   const int lt = t - cam.tile_off;
   const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int t_idx = TransposeSum<kVals, 16>::index(lane);  // the gradient value this lane sums
-  const bool t_keep = t_idx >= 0 && (lane & transpose_shared_bits<kVals>()) == 0;
+  float* const red_row = &sRed[wid][lane * kStride];
+  const int red_m = lane % kVals, red_part = lane / kVals;  // the value and the rows this lane sums
+  const float* const red_col = &sRed[wid][red_part * kStride + red_m];
+  // the lane's pixels: the upper and the lower half of the warp's 8x8 block (warp_half_mask)
   const int px = tx * kTile + 8 * (wid & 1) + (tid & 7);
-  const int py0 = ty * kTile + 8 * (wid >> 1) + 2 * ((tid & 31) >> 3);
+  const int py0 = ty * kTile + 8 * (wid >> 1) + ((tid & 31) >> 3);
   const float fx = px + 0.5f;
-  const float fy[2] = {py0 + 0.5f, py0 + 1.5f};
-  const bool inside[2] = {px < cam.W && py0 < cam.H, px < cam.W && py0 + 1 < cam.H};
+  const float fy[2] = {py0 + 0.5f, py0 + 4.5f};
+  const bool inside[2] = {px < cam.W && py0 < cam.H, px < cam.W && py0 + 4 < cam.H};
   const float x0 = tx * kTile + 0.5f, y0 = ty * kTile + 0.5f;
   const float x_max = cam.W - 0.5f, y_max = cam.H - 0.5f;
   const uint2 range = ranges[t];
@@ -117,7 +94,7 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
     last[q] = 0;
     g0[q] = g1[q] = g2[q] = 0.f;
     if (inside[q]) {
-      const long long pix = cam.pix_off + static_cast<long long>(py0 + q) * cam.W + px;
+      const long long pix = cam.pix_off + static_cast<long long>(py0 + 4 * q) * cam.W + px;
       Tf[q] = in.T_final[pix];
       last[q] = in.n_contrib[pix];
       const float2 ds = in.D_state[pix];  // first contributor's depth, sum of (z - it) w
@@ -168,16 +145,17 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
         sB[k] = r.b;
         sC[k] = make_float2(r.c.x, r.c.y);
         sV[k] = v;
-        sM[k] = warp_block_mask(r.d, x0, y0, x_max, y_max);
-      }
+        sM[k] = warp_half_mask(r.d, x0, y0, x_max, y_max);
 #pragma unroll
-      for (int m = 0; m < kGradVals; ++m) sAcc[k][m] = 0.f;
+        for (int m = 0; m < kGradVals; ++m) sAcc[k][m] = 0.f;
+      }
     }
     __syncthreads();
     const int cnt = min(kBatch, n - base);
     for (int j = 0; j < cnt; ++j) {
       const uint32_t pos = static_cast<uint32_t>(n - 1 - base - j);
-      if (pos >= warp_last || !((sM[j] >> wid) & 1u)) continue;  // warp-uniform: nothing of this warp
+      const uint32_t halves = (sM[j] >> (2 * wid)) & 3u;  // halves of the warp's block the box meets
+      if (pos >= warp_last || halves == 0u) continue;     // warp-uniform: nothing of this warp
       const float4 a = sA[j];
       const float4 b = sB[j];
       const float2 cc = sC[j];
@@ -189,11 +167,15 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
         const bool vis = inside[q] && pos < last[q];
         if (kCount) n_visit += vis;
         dyq[q] = a.y - fy[q];
-        const float sigma = 0.5f * (b.x * dx * dx + b.z * dyq[q] * dyq[q]) + b.y * dx * dyq[q];
-        Gq[q] = __expf(-sigma);
-        arawq[q] = a.z * Gq[q];
-        alphaq[q] = fminf(kAlphaMax, arawq[q]);
-        cq[q] = vis && sigma >= 0.f && alphaq[q] >= kAlphaMin;
+        Gq[q] = arawq[q] = alphaq[q] = 0.f;
+        cq[q] = false;
+        if ((halves >> q) & 1u) {  // warp-uniform: no pixel of a half outside the box takes it
+          const float sigma = 0.5f * (b.x * dx * dx + b.z * dyq[q] * dyq[q]) + b.y * dx * dyq[q];
+          Gq[q] = __expf(-sigma);
+          arawq[q] = a.z * Gq[q];
+          alphaq[q] = fminf(kAlphaMax, arawq[q]);
+          cq[q] = vis && sigma >= 0.f && alphaq[q] >= kAlphaMin;
+        }
         if (kCount) n_contrib += cq[q];
       }
       // warp-uniform: where no pixel of the warp takes the Gaussian, nothing below changes
@@ -250,8 +232,21 @@ __global__ void __launch_bounds__(kBlendThreads, 6) blend_bwd_kernel(const Rec* 
           gv[11] += fabsf((b.y * dx + b.z * dy) * dsig);
         }
       }
-      const float tot = TransposeSum<kVals, 16>::run(gv, lane);
-      if (t_keep) atomicAdd(&sAcc[j][t_idx], tot);
+#pragma unroll
+      for (int m = 0; m < kVals; ++m) red_row[m] = gv[m];
+      __syncwarp();
+      float tot = 0.f;
+      if (red_part < kParts) {
+#pragma unroll
+        for (int i = 0; i < (32 + kParts - 1) / kParts; ++i)
+          if (red_part + kParts * i < 32) tot += red_col[kParts * kStride * i];
+      }
+      // the parts of value m are in lanes m, m + kVals (and m + 2 kVals); each lane's reads are
+      // complete once its sum enters the shuffles, before any lane writes the next row
+      const float t1 = __shfl_down_sync(0xffffffffu, tot, kVals);
+      if (kParts == 3) tot += __shfl_down_sync(0xffffffffu, tot, 2 * kVals);
+      tot += t1;
+      if (lane < kVals) atomicAdd(&sAcc[j][lane], tot);
     }
     __syncthreads();
     for (int k = tid; k < cnt; k += kBlendThreads) {
