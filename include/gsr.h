@@ -267,9 +267,11 @@ gsr_status gsr_sync_check(gsr_ctx* ctx, gsr_stream stream);
  * arrays (gsr_param_grads_zero, or the backward's own) runs on the context's side stream beside the
  * backward's blend; at full speed it takes most of the memory bandwidth from the stages it
  * overlaps. gb_per_s > 0 spreads it out at about that rate (each fill block starts a 16 KB chunk
- * only when it is due on the GPU's nanosecond timer); 0 (the default) writes as fast as possible.
- * blocks > 0 sets how many blocks fill (0 keeps the current number; the default is 5/8 of the
- * SM count).
+ * only when it is due on the GPU's nanosecond timer); 0 writes as fast as possible. The default,
+ * 5600 GB/s, is just under what the fill reaches alone on a GB300; so paced, it leaves the blend
+ * backward beside it its memory latency (measured on a 6M-Gaussian 1080p step: 730 us against
+ * 776 unpaced). blocks > 0 sets how many blocks fill (0 keeps the current number; the default is
+ * one per SM).
  * Results are the same either way; only the timing changes. Errors: GSR_ERR_INVALID_ARG. */
 gsr_status gsr_set_fill_rate(gsr_ctx* ctx, float gb_per_s, int32_t blocks);
 
