@@ -489,6 +489,33 @@ def test_gradient_magnitude_bounds_and_single_pixel_equality():
     assert res.img.shape[0] == 64 * 64
 
 
+def test_absgrad_is_the_sum_over_pixels_of_the_mean2d_gradient_magnitudes():
+    """AbsGS (Sec. 3.5.4) accumulates, per Gaussian and image axis, |dL_p / dmean2d| over the
+    pixels p, L_p being the loss's part at pixel p. Brute force from that definition: a backward
+    with the upstream gradient of one pixel alone gives dL_p / dmean2d (the 2D gradient the oracle
+    returns per camera and Gaussian); the magnitudes summed over every pixel must equal the
+    statistic, which in turn bounds the full 2D mean gradient, their signed sum."""
+    W, H = 24, 20
+    sc, cam = scenes.tiny_scene(3, 40, W, H, depth=(2.0, 6.0), log_scale_mean=-2.0)
+    opts = oracle.Opts(bg=(0.1, 0.2, 0.3))
+    up = np.random.default_rng(4).normal(size=(W * H, 6))
+    full = oracle.backward(sc, [cam], up, opts, want_g2d=True)
+    per_pixel = np.zeros((sc.n, 2))
+    signed = np.zeros((sc.n, 2))
+    for p in range(W * H):
+        u = np.zeros_like(up)
+        u[p] = up[p]
+        g2d = oracle.backward(sc, [cam], u, opts, want_g2d=True)["g2d"][:, 0:2]
+        per_pixel += np.abs(g2d)
+        signed += g2d
+    assert (per_pixel > 0).sum() >= sc.n // 2  # most Gaussians reach some pixel
+    np.testing.assert_allclose(full["absgrad"], per_pixel, rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(full["g2d"][:, 0:2], signed, rtol=1e-9, atol=1e-12)
+    assert np.all(np.abs(full["g2d"][:, 0:2]) <= full["absgrad"] * (1 + 1e-12) + 1e-15)
+    # cancelling pixels make the statistic strictly larger than the gradient somewhere
+    assert np.any(full["absgrad"] > np.abs(full["g2d"][:, 0:2]) * 1.01 + 1e-12)
+
+
 # --- appearance transform (Sec. 3.5.1) ---------------------------------------------------------------
 
 def test_appearance_transform_limits():
