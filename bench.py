@@ -4,8 +4,9 @@ Workload ("city6m_1080p"): the seeded synthetic city (1x1 km grid of 100 m block
 streets, 3-6 box buildings per block, heights 10-80 m; 60% of the Gaussians on the ground,
 40% on facades; 6,000,000 Gaussians; SH degree 3; FP32) seen by one 1920x1080 camera 150 m
 above the ground with a 45-degree pitch. A step is one training pass of the rasterizer:
-render_forward (preprocess, depth sort, binning, tile sort, blend) and render_backward (blend
-backward, projection backward) with fixed upstream gradients on rgb, depth and alpha.
+render_forward (preprocess, binning, per-tile sorts inside the blend, blend) and render_backward
+(blend backward beside the gradient zero fill, projection backward) with fixed upstream gradients
+on rgb, depth and alpha.
 The inputs (1.4 GB of Gaussians) are larger than L2, so no flush is needed between steps.
 
 Prints one JSON line. `value` is the device-timed ms per fwd+bwd step (CUDA events, inputs
@@ -37,8 +38,10 @@ if ROOT not in sys.path:
 
 METRIC = "render FPS and fwd+bwd ms/step at 6M Gaussians 1080p; serve p50/p99 latency"
 
-# Algorithmic work per unit (see the design notes): FP32 operations of one (pixel, Gaussian)
-# evaluation in the forward and backward blends, and bytes per unit of the HBM-bound stages.
+# Algorithmic work per unit: FP32 operations of one (pixel, Gaussian) evaluation in the forward
+# blend (the quadratic form, the exponent's argument, alpha, the clamp and tests, the transmittance
+# update and the colour and depth sums) and in the backward blend (the same evaluation, the
+# transmittance recovered by a division, the remainder update and the ten per-Gaussian sums).
 FLOPS_PER_FWD_EVAL = 20.0
 FLOPS_PER_BWD_EVAL = 60.0
 
@@ -366,8 +369,8 @@ def run_mlp_leg(args, ctx, g, cam, opts, d_out, outs, stream, dev, rank):
                                              peak_source="152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"))
 
 
-# Algorithmic work of each stage of one step (the design notes derive each figure): bytes that
-# must cross HBM, FP32 operations and MUFU operations (ex2, reciprocal) of the blends.
+# Algorithmic work of each stage of one step, each figure derived beside it: bytes that must
+# cross HBM, FP32 operations and MUFU operations (ex2, reciprocal) of the blends.
 def stage_work(n, V, P, tiles, npix, counts):
     fe, be = counts["fwd_evals"], counts["bwd_evals"]
     return {
