@@ -160,6 +160,10 @@ def test_two_gaussians_over_operator():
     np.testing.assert_allclose(res["rgb"][y, x], c1 * a[0] + c2 * a[1] * (1 - a[0]), rtol=1e-13)
     np.testing.assert_allclose(res["T"][y, x], (1 - a[0]) * (1 - a[1]), rtol=1e-13)
     np.testing.assert_allclose(res["depth_acc"][y, x], 3.0 * a[0] + 5.0 * a[1] * (1 - a[0]), rtol=1e-13)
+    # expected depth (Sec. 3.5.3): the blend weights' mean of the depths, 3 and 5 here
+    w0, w1 = a[0], a[1] * (1 - a[0])
+    np.testing.assert_allclose(res["depth_exp"][y, x], (3.0 * w0 + 5.0 * w1) / (w0 + w1), rtol=1e-13)
+    np.testing.assert_allclose(res["alpha"][y, x], w0 + w1, rtol=1e-13)
 
 
 @pytest.mark.parametrize("o", [0.5, 0.3, 0.999])
